@@ -1,0 +1,154 @@
+/*
+ * stba.h -- C ABI of libstba.so: the Levenberg-Marquardt (LM) iteration of Stochastic Bundle Adjustment
+ * (Zhou et al., "Stochastic Bundle Adjustment for Efficient and Scalable 3D Reconstruction", ECCV 2020)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (Sec. 3): m cameras c_j in R^9, n points p_i in R^3 and q projections q_o in R^2.  The objective
+ * is F(x) = ||f(x)||^2 with f_o = pi(c_cam(o), p_pt(o)) - q_o.  Camera parameters, in this order:
+ *   angle-axis rotation w (3), translation t (3), focal length f, radial distortion k1, k2;
+ *   Xc = R(w) p + t, (x, y) = Xc.xy / Xc.z, pi = f (1 + k1 r^2 + k2 r^4) (x, y), r^2 = x^2 + y^2.
+ * Pixel coordinates are offsets from the image centre.
+ *
+ * One call of stba_lm_iteration is one pass of Algorithm 1 (Appendix C) for the current cluster
+ * assignment: residuals and Jacobians, the clustered reduced camera system S' (Eq. 10) with one virtual
+ * copy of each point per cluster that sees it (Sec. 4.1-4.2), the steepest-descent correction when
+ * lambda >= correction_lambda (Sec. 4.3), one dense Cholesky solve per cluster (Eq. 13), the point
+ * update of Eq. 15, the cost F(x + dx) and the accept / reject rule with lambda /= 3 or *= 3.
+ *
+ * Conventions
+ *   - Every array argument may be a host pointer or a device pointer (detected with
+ *     cudaPointerGetAttributes); it is only read (or written) during the call.  The caller keeps
+ *     ownership of its arrays.  The library owns all device memory it allocates (freed by stba_destroy).
+ *   - All device work is enqueued on the CUDA stream given to stba_create (NULL = legacy default stream).
+ *     Calls that return values to the host synchronise that stream.
+ *   - A context is not thread safe; use one context per host thread.
+ *   - Errors return a status; stba_last_error(ctx) gives a message.  A failed call leaves the
+ *     parameters unchanged.
+ */
+#ifndef STBA_H
+#define STBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stba_ctx stba_ctx;
+
+typedef enum {
+  STBA_OK = 0,
+  STBA_ERR_INVALID_ARG = 1, /* bad sizes, indices out of range, duplicate projections, empty cluster */
+  STBA_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  STBA_ERR_OOM = 3,         /* device allocation failed */
+  STBA_ERR_NOT_SPD = 4,     /* reserved: a failed factorisation is reported in stba_iter_info instead */
+  STBA_ERR_NONFINITE = 5,   /* non-finite input values, or a point behind a camera (depth <= 1e-9) */
+  STBA_ERR_TIMEOUT = 6,     /* reserved for bounded device waits */
+  STBA_ERR_STATE = 7        /* wrong call order, or lambda above 1e16 */
+} stba_status;
+
+typedef enum { STBA_FP64 = 0, STBA_MIXED = 1 } stba_precision;
+
+typedef struct {
+  int32_t precision;        /* STBA_FP64: everything in FP64.  STBA_MIXED: residuals, Jacobians and the
+                               Schur accumulation in FP32; factorisation, refinement and cost sums FP64 */
+  int32_t correction;       /* 1: steepest-descent correction when lambda >= correction_lambda (Sec. 4.3) */
+  double lambda0;           /* initial damping lambda, 1e-4 (Sec. 5.1, Algorithm 1) */
+  double lambda_min;        /* floor applied after an accepted step (0 = none; the paper's ablation
+                               uses 0.1, Sec. 5.4) */
+  double correction_lambda; /* 0.1 (Sec. 4.3) */
+  double ftol, gtol, xtol;  /* stop tolerances (Sec. 5.1: 1e-6); <= 0 disables a test */
+  int32_t refine_steps;     /* FP64 iterative-refinement steps per cluster solve (default 1) */
+  int32_t use_graph;        /* 1: replay each LM iteration as one captured CUDA graph */
+} stba_options;
+
+typedef struct {
+  double F_before;      /* F(x) at the start of the iteration */
+  double F_after;       /* F(x + dx) of the candidate step; +inf when a cluster factorisation failed */
+  double lambda_used;   /* damping used to compute the step */
+  double lambda;        /* damping after the accept / reject update */
+  double grad_inf;      /* ||J^T f||_inf at x (uncorrected gradient) */
+  double dx_norm;       /* ||dx||_2 of the candidate step */
+  double x_norm;        /* ||x||_2 at the start of the iteration */
+  int32_t accepted;     /* 1 if F(x + dx) < F(x) (strict) and x was updated */
+  int32_t stop;         /* 1 if a stop tolerance fired on this step (Algorithm 1) */
+  int32_t corrected;    /* 1 if the steepest-descent correction was applied */
+  int32_t failed_clusters; /* clusters whose Cholesky factorisation met a pivot <= 0 or non-finite */
+  int32_t boosted_pivots;  /* mixed precision: FP32 pivots lost to rounding and raised before FP64
+                              refinement (static pivoting); 0 in FP64 mode */
+  int32_t reserved;
+  int64_t iteration;    /* 1-based count of iterations run on this context */
+} stba_iter_info;
+
+/* Fills *opt with the defaults above (FP64, correction on, lambda0 1e-4, tolerances off,
+ * refine_steps 1, use_graph 1). */
+void stba_default_options(stba_options* opt);
+
+/* Creates a problem (Sec. 3, Algorithm 1 inputs).
+ *   cameras [m][9] FP64, points [n][3] FP64 (initial x); obs_cam [q], obs_pt [q] int32 indices;
+ *   obs_uv [q][2] FP64 pixel observations; cluster_assignment [m] int32 with values 0..l-1, every
+ *   cluster non-empty (the sampled clustering of Sec. 4.2/4.4); opt may be NULL (defaults);
+ *   cuda_stream is a cudaStream_t or NULL.
+ * Every point needs >= 2 projections and every camera >= 1; a (camera, point) pair may appear once.
+ * Computes F(x) once.  On success *out owns the context. */
+stba_status stba_create(const double* cameras, int64_t m, const double* points, int64_t n,
+                        const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int64_t q,
+                        const int32_t* cluster_assignment, const stba_options* opt, void* cuda_stream,
+                        stba_ctx** out);
+
+/* Replaces the cluster assignment [m] used by subsequent iterations (the per-iteration resampling of
+ * Algorithm 1).  Same validation as stba_create. */
+stba_status stba_set_clusters(stba_ctx* ctx, const int32_t* cluster_assignment);
+
+/* Runs one LM iteration (Algorithm 1 body).  If info != NULL the stream is synchronised and *info is
+ * filled; with info == NULL the call only enqueues work and returns. */
+stba_status stba_lm_iteration(stba_ctx* ctx, stba_iter_info* info);
+
+/* Runs up to max_iter iterations, stopping after the first one whose stop flag is set (Algorithm 1).
+ * *last (may be NULL) receives the last iteration's record. */
+stba_status stba_solve(stba_ctx* ctx, int32_t max_iter, stba_iter_info* last);
+
+/* Recomputes F(x) = ||f(x)||^2 at the current parameters (FP64 sum); synchronises. */
+stba_status stba_cost(stba_ctx* ctx, double* F);
+
+/* Copies the current parameters out ([m][9], [n][3], FP64); either pointer may be NULL. */
+stba_status stba_get_params(stba_ctx* ctx, double* cameras, double* points);
+
+/* Replaces the parameters ([m][9], [n][3], FP64) and recomputes F(x).  Keeps lambda. */
+stba_status stba_set_params(stba_ctx* ctx, const double* cameras, const double* points);
+
+/* Damping / cost state, for checkpoint and resume: reads or overwrites (lambda, F, iteration).
+ * stba_set_state with F < 0 recomputes F at the current parameters. */
+stba_status stba_get_state(stba_ctx* ctx, double* lambda, double* F, int64_t* iteration);
+stba_status stba_set_state(stba_ctx* ctx, double lambda, double F, int64_t iteration);
+
+/* The candidate step of the last iteration, accepted or not: dc [m][9], dp [n][3] (FP64). */
+stba_status stba_last_step(stba_ctx* ctx, double* dc, double* dp);
+
+/* Sizes: out[0..7] = m, n, q, l (clusters), nv (virtual points), max cluster dimension 9 n_k,
+ * device bytes held, number of S' build work items. */
+stba_status stba_problem_info(stba_ctx* ctx, int64_t* out8);
+
+/* The cluster system S'_k Delta c_k = b_k (Eq. 13) of the last iteration, in the order of the cluster's
+ * cameras by increasing camera index: S [dim][dim] (FP64, both triangles filled from the lower one) and
+ * b [dim]; dim = 9 n_k is written to *dim.  S or b may be NULL (then only dim is returned). */
+stba_status stba_get_cluster_system(stba_ctx* ctx, int32_t k, double* S, double* b, int64_t* dim);
+
+/* Stage timing: with on != 0, each subsequent iteration records CUDA events around its stages on the
+ * context stream.  stba_stage_times copies the times (ms) of the last iteration into ms[0..n-1]
+ * (stages: 0 linearise+virtual points, 1 S' build, 2 factorisation, 3 cluster solves, 4 point update
+ * + cost + control) and returns the number of stages in *count. */
+stba_status stba_set_timing(stba_ctx* ctx, int32_t on);
+stba_status stba_stage_times(stba_ctx* ctx, float* ms, int32_t n, int32_t* count);
+
+/* Frees every device allocation of the context.  NULL is allowed. */
+void stba_destroy(stba_ctx* ctx);
+
+const char* stba_status_string(stba_status s);
+const char* stba_last_error(stba_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STBA_H */

@@ -1,0 +1,910 @@
+// C ABI of libstba.so (include/stba.h): context management, host-side preprocessing of the visibility
+// graph for a cluster assignment, and the enqueue of one LM iteration (Algorithm 1) on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "stba_internal.cuh"
+
+using namespace stba;
+
+namespace {
+
+thread_local std::string g_create_error;   // message of the last failed stba_create on this thread
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct stba_ctx {
+  stba_options opt{};
+  Settings set{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::string err;
+  int64_t m = 0, n = 0, q = 0;
+  int l = 0, nv = 0;
+  bool mixed = false;
+  size_t bytes_base = 0, bytes_cl = 0;
+  std::vector<void*> allocs;            // problem-lifetime device buffers
+  std::vector<void*> cl_allocs;         // cluster-assignment-lifetime device buffers
+
+  // host copies of the input observations (original order) and the (point, camera) order
+  std::vector<int> in_cam, in_pt;
+  std::vector<double> in_uv;
+  std::vector<int> base_order;          // observation indices sorted by (point, camera)
+  std::vector<int> h_pt_off;            // [n+1]
+
+  // host structures of the current cluster assignment
+  std::vector<int> h_clusters, h_cluster_cams, h_cluster_cam_off, h_np, h_nk;
+  std::vector<int64_t> h_S_off, h_v_off;
+  std::vector<int> h_panel_off, h_update_off;
+  int64_t S_total = 0, v_total = 0;
+  int max_np = 0;
+  int build_items = 0;
+
+  // device arrays
+  double *cams = nullptr, *pts = nullptr, *obs_uv = nullptr;
+  float* obs_uvf = nullptr;
+  int *obs_cam = nullptr, *obs_vp = nullptr, *obs_pt = nullptr, *obs_perm = nullptr;
+  int *vp_off = nullptr, *vp_point = nullptr, *pt_vp_off = nullptr, *pt_off = nullptr;
+  int *cam_local = nullptr, *cam_cluster = nullptr, *cluster_cams = nullptr, *cluster_cam_off = nullptr;
+  int *cluster_np = nullptr, *cluster_n = nullptr;
+  int64_t *S_off = nullptr, *v_off = nullptr;
+  CamLists clist{};
+  PairLists plist{};
+  void* Gbuf = nullptr;
+  int64_t n_pairs = 0;
+  CholPlan cplan{};
+  FactorBuffers fbuf{};
+  int* fail_flags = nullptr;
+
+  // scratch (real = float in mixed mode, double in FP64 mode)
+  void *vp_acc = nullptr, *vp_info = nullptr, *pt_info = nullptr, *S = nullptr, *b = nullptr, *vgrad = nullptr,
+       *t_acc = nullptr;
+  double *dc = nullptr, *dp = nullptr, *partial = nullptr;
+  DevState* st = nullptr;
+
+  // graph / timing
+  cudaGraphExec_t graph = nullptr;
+  bool timing = false;
+  cudaEvent_t ev[NSTAGES + 1] = {};
+  float stage_ms[NSTAGES] = {};
+  bool have_stage_times = false;
+};
+
+namespace {
+
+stba_status fail(stba_ctx* c, stba_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(c, STBA_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+stba_status dalloc(stba_ctx* c, T** p, size_t count, bool cluster_scope) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, STBA_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  (cluster_scope ? c->cl_allocs : c->allocs).push_back((void*)*p);
+  (cluster_scope ? c->bytes_cl : c->bytes_base) += bytes;
+  return STBA_OK;
+}
+
+template <typename T>
+stba_status upload(stba_ctx* c, T** p, const std::vector<T>& h, bool cluster_scope) {
+  stba_status s = dalloc(c, p, h.size(), cluster_scope);
+  if (s != STBA_OK) return s;
+  if (!h.empty()) CK(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return STBA_OK;
+}
+
+stba_status copy_in(stba_ctx* c, void* host_dst, const void* src, size_t bytes) {
+  if (bytes == 0) return STBA_OK;
+  if (is_device_ptr(src)) {
+    CK(cudaMemcpy(host_dst, src, bytes, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(host_dst, src, bytes);
+  }
+  return STBA_OK;
+}
+
+stba_status copy_out(stba_ctx* c, void* dst, const void* dev_src, size_t bytes) {
+  if (bytes == 0 || !dst) return STBA_OK;
+  CK(cudaMemcpyAsync(dst, dev_src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return STBA_OK;
+}
+
+void free_list(stba_ctx* c, std::vector<void*>& v) {
+  for (void* p : v) cudaFree(p);
+  v.clear();
+}
+
+DevProblem dev_problem(const stba_ctx* c) {
+  DevProblem P;
+  P.m = (int)c->m;
+  P.n = (int)c->n;
+  P.q = (int)c->q;
+  P.l = c->l;
+  P.nv = c->nv;
+  P.cams = c->cams;
+  P.pts = c->pts;
+  P.obs_cam = c->obs_cam;
+  P.obs_vp = c->obs_vp;
+  P.obs_pt = c->obs_pt;
+  P.obs_uv = c->obs_uv;
+  P.obs_uvf = c->obs_uvf;
+  P.vp_off = c->vp_off;
+  P.vp_point = c->vp_point;
+  P.pt_vp_off = c->pt_vp_off;
+  P.pt_off = c->pt_off;
+  P.cam_local = c->cam_local;
+  P.cam_cluster = c->cam_cluster;
+  P.cluster_cams = c->cluster_cams;
+  P.cluster_cam_off = c->cluster_cam_off;
+  P.cluster_np = c->cluster_np;
+  P.cluster_n = c->cluster_n;
+  P.S_off = c->S_off;
+  P.v_off = c->v_off;
+  return P;
+}
+
+template <typename real>
+Scratch<real> scratch(const stba_ctx* c) {
+  Scratch<real> W;
+  W.vp_acc = (real*)c->vp_acc;
+  W.vp_info = (real*)c->vp_info;
+  W.pt_info = (real*)c->pt_info;
+  W.S = (real*)c->S;
+  W.b = (real*)c->b;
+  W.vgrad = (real*)c->vgrad;
+  W.t_acc = (real*)c->t_acc;
+  W.dc = c->dc;
+  W.dp = c->dp;
+  W.partial = c->partial;
+  return W;
+}
+
+
+// ------------------------------------------------------------------------------------------------------
+// Cluster-assignment preprocessing: order the observations by (point, cluster, camera), define the
+// virtual points (distinct (point, cluster) pairs), the per-cluster dense layout, the tile work lists of
+// the S' build and the Cholesky step plan.
+stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
+  const int m = (int)c->m, n = (int)c->n, q = (int)c->q;
+  int l = 0;
+  for (int j = 0; j < m; ++j) {
+    if (cl[j] < 0) return fail(c, STBA_ERR_INVALID_ARG, "cluster id %d of camera %d is negative", cl[j], j);
+    l = std::max(l, cl[j] + 1);
+  }
+  std::vector<int> cnt(l, 0);
+  for (int j = 0; j < m; ++j) cnt[cl[j]]++;
+  for (int k = 0; k < l; ++k)
+    if (cnt[k] == 0) return fail(c, STBA_ERR_INVALID_ARG, "cluster %d has no camera (ids must be 0..l-1)", k);
+
+  free_list(c, c->cl_allocs);
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->bytes_cl = 0;
+  c->l = l;
+  c->h_clusters = cl;
+  // cameras of every cluster, ascending
+  c->h_cluster_cam_off.assign(l + 1, 0);
+  for (int k = 0; k < l; ++k) c->h_cluster_cam_off[k + 1] = c->h_cluster_cam_off[k] + cnt[k];
+  c->h_cluster_cams.assign(m, 0);
+  std::vector<int> cam_local(m), fill(l, 0);
+  for (int j = 0; j < m; ++j) {
+    const int k = cl[j];
+    cam_local[j] = fill[k];
+    c->h_cluster_cams[c->h_cluster_cam_off[k] + fill[k]] = j;
+    fill[k]++;
+  }
+  // dense layout (padded to the factorisation tile TF)
+  const int TF = factor_tile(c->mixed);
+  c->h_np.assign(l, 0);
+  c->h_nk.assign(l, 0);
+  c->h_S_off.assign(l, 0);
+  c->h_v_off.assign(l, 0);
+  int64_t so = 0, vo = 0;
+  c->max_np = 0;
+  int max_nt = 0;
+  for (int k = 0; k < l; ++k) {
+    const int nk = 9 * cnt[k];
+    const int np = (nk + TF - 1) / TF * TF;
+    c->h_nk[k] = nk;
+    c->h_np[k] = np;
+    c->h_S_off[k] = so;
+    c->h_v_off[k] = vo;
+    so += (int64_t)np * np;
+    vo += np;
+    c->max_np = std::max(c->max_np, np);
+    max_nt = std::max(max_nt, np / TF);
+  }
+  c->S_total = so;
+  c->v_total = vo;
+
+  // observation order (point, cluster, camera): stable sort of each point run by cluster
+  std::vector<int> order(c->base_order);
+  for (int i = 0; i < n; ++i) {
+    const int b = c->h_pt_off[i], e = c->h_pt_off[i + 1];
+    bool same = true;
+    for (int o = b + 1; o < e && same; ++o) same = cl[c->in_cam[order[o]]] == cl[c->in_cam[order[b]]];
+    if (!same)
+      std::stable_sort(order.begin() + b, order.begin() + e,
+                       [&](int x, int y) { return cl[c->in_cam[x]] < cl[c->in_cam[y]]; });
+  }
+  std::vector<int> s_cam(q), s_vp(q), s_pt(q), vp_off, vp_point, pt_vp_off(n + 1, 0);
+  std::vector<double> s_uv(2 * (size_t)q);
+  std::vector<float> s_uvf(c->mixed ? 2 * (size_t)q : 0);
+  vp_off.reserve(q + 1);
+  vp_point.reserve(q);
+  for (int i = 0; i < n; ++i) {
+    pt_vp_off[i] = (int)vp_point.size();
+    int prev = -1;
+    for (int o = c->h_pt_off[i]; o < c->h_pt_off[i + 1]; ++o) {
+      const int src = order[o];
+      const int cam = c->in_cam[src];
+      if (cl[cam] != prev) {
+        vp_off.push_back(o);
+        vp_point.push_back(i);
+        prev = cl[cam];
+      }
+      s_cam[o] = cam;
+      s_vp[o] = (int)vp_point.size() - 1;
+      s_pt[o] = i;
+      s_uv[2 * (size_t)o] = c->in_uv[2 * (size_t)src];
+      s_uv[2 * (size_t)o + 1] = c->in_uv[2 * (size_t)src + 1];
+      if (c->mixed) {
+        s_uvf[2 * (size_t)o] = (float)s_uv[2 * (size_t)o];
+        s_uvf[2 * (size_t)o + 1] = (float)s_uv[2 * (size_t)o + 1];
+      }
+    }
+  }
+  pt_vp_off[n] = (int)vp_point.size();
+  vp_off.push_back(q);
+  const int nv = (int)vp_point.size();
+  c->nv = nv;
+
+  // observations of every camera (sorted positions), for the camera pass of the S' build
+  std::vector<int> cam_obs_off(m + 1, 0), cam_obs(q);
+  for (int o = 0; o < q; ++o) cam_obs_off[s_cam[o] + 1]++;
+  for (int j = 0; j < m; ++j) cam_obs_off[j + 1] += cam_obs_off[j];
+  {
+    std::vector<int> f(cam_obs_off.begin(), cam_obs_off.end() - 1);
+    for (int o = 0; o < q; ++o) cam_obs[f[s_cam[o]]++] = o;
+  }
+  // pair instances of the pair pass: tiles (k, gA >= gB) over groups of TC cameras; inside a virtual point
+  // the observations are ordered by camera, so a later observation has the larger local camera index
+  const int TC = pair_tile_cameras(c->mixed);
+  const int TD = 9 * TC;
+  std::vector<int> tile_base(l + 1, 0), ngroups(l);
+  for (int k = 0; k < l; ++k) {
+    ngroups[k] = (cnt[k] + TC - 1) / TC;
+    tile_base[k + 1] = tile_base[k] + ngroups[k] * (ngroups[k] + 1) / 2;
+  }
+  const int nt = tile_base[l];
+  std::vector<int> tile_cluster(nt), tile_ga(nt), tile_gb(nt);
+  for (int k = 0; k < l; ++k)
+    for (int ga = 0; ga < ngroups[k]; ++ga)
+      for (int gb = 0; gb <= ga; ++gb) {
+        const int t = tile_base[k] + ga * (ga + 1) / 2 + gb;
+        tile_cluster[t] = k;
+        tile_ga[t] = ga;
+        tile_gb[t] = gb;
+      }
+  auto tile_of = [&](int oa, int ob) {
+    const int k = cl[s_cam[oa]];
+    const int ga = cam_local[s_cam[oa]] / TC, gb = cam_local[s_cam[ob]] / TC;
+    return tile_base[k] + ga * (ga + 1) / 2 + gb;
+  };
+  std::vector<int64_t> tile_cnt(nt + 1, 0);
+  for (int v = 0; v < nv; ++v)
+    for (int a2 = vp_off[v] + 1; a2 < vp_off[v + 1]; ++a2)
+      for (int b2 = vp_off[v]; b2 < a2; ++b2) tile_cnt[tile_of(a2, b2) + 1]++;
+  for (int t = 0; t < nt; ++t) tile_cnt[t + 1] += tile_cnt[t];
+  if (tile_cnt[nt] > INT32_MAX) return fail(c, STBA_ERR_INVALID_ARG, "more than 2^31 camera-pair instances");
+  std::vector<int4> pairs(tile_cnt[nt]);
+  {
+    std::vector<int64_t> tf(tile_cnt.begin(), tile_cnt.end() - 1);
+    for (int v = 0; v < nv; ++v)
+      for (int a2 = vp_off[v] + 1; a2 < vp_off[v + 1]; ++a2)
+        for (int b2 = vp_off[v]; b2 < a2; ++b2) {
+          const int t = tile_of(a2, b2);
+          const int la = cam_local[s_cam[a2]] - tile_ga[t] * TC, lb = cam_local[s_cam[b2]] - tile_gb[t] * TC;
+          pairs[tf[t]++] = make_int4(a2, b2, 9 * la * TD + 9 * lb, 0);
+        }
+  }
+  c->n_pairs = tile_cnt[nt];
+  // chunks of at most `chunk` pairs so that the work items cover the GPU several times over
+  const int64_t chunk = std::max<int64_t>(512, tile_cnt[nt] / (152 * 4) + 1);
+  std::vector<int> item_tile, item_lo, item_hi;
+  for (int t = 0; t < nt; ++t)
+    for (int64_t lo = tile_cnt[t]; lo < tile_cnt[t + 1]; lo += chunk) {
+      item_tile.push_back(t);
+      item_lo.push_back((int)lo);
+      item_hi.push_back((int)std::min<int64_t>(lo + chunk, tile_cnt[t + 1]));
+    }
+  c->build_items = (int)item_tile.size();
+
+  // Cholesky step plan
+  std::vector<int2> panel, update;
+  c->h_panel_off.assign(max_nt + 1, 0);
+  c->h_update_off.assign(max_nt + 1, 0);
+  for (int kt = 0; kt < max_nt; ++kt) {
+    c->h_panel_off[kt] = (int)panel.size();
+    c->h_update_off[kt] = (int)update.size();
+    for (int k = 0; k < l; ++k) {
+      const int ntk = c->h_np[k] / TF;
+      if (ntk <= kt) continue;
+      for (int i = kt; i < ntk; ++i) panel.push_back(make_int2(k, i));
+      for (int j = kt + 1; j < ntk; ++j)
+        for (int i = j; i < ntk; ++i) update.push_back(make_int2(k, (i << 16) | j));
+    }
+  }
+  c->h_panel_off[max_nt] = (int)panel.size();
+  c->h_update_off[max_nt] = (int)update.size();
+  std::vector<int2> res_items;
+  for (int k = 0; k < l; ++k)
+    for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
+
+  // upload
+  stba_status s;
+  std::vector<int> cam_cluster(cl.begin(), cl.end());
+  std::vector<int> perm(order.begin(), order.end());
+#define UP(ptr, vec) \
+  if ((s = upload(c, &(ptr), vec, true)) != STBA_OK) return s;
+  UP(c->obs_cam, s_cam);
+  UP(c->obs_vp, s_vp);
+  UP(c->obs_pt, s_pt);
+  UP(c->obs_perm, perm);
+  UP(c->obs_uv, s_uv);
+  if (c->mixed) UP(c->obs_uvf, s_uvf);
+  UP(c->vp_off, vp_off);
+  UP(c->vp_point, vp_point);
+  UP(c->pt_vp_off, pt_vp_off);
+  UP(c->pt_off, c->h_pt_off);
+  UP(c->cam_local, cam_local);
+  UP(c->cam_cluster, cam_cluster);
+  UP(c->cluster_cams, c->h_cluster_cams);
+  UP(c->cluster_cam_off, c->h_cluster_cam_off);
+  UP(c->cluster_np, c->h_np);
+  UP(c->cluster_n, c->h_nk);
+  UP(c->S_off, c->h_S_off);
+  UP(c->v_off, c->h_v_off);
+  int *d_tile_cluster, *d_tile_ga, *d_tile_gb, *d_item_tile, *d_item_lo, *d_item_hi, *d_cam_obs_off, *d_cam_obs;
+  int4* d_pairs;
+  UP(d_tile_cluster, tile_cluster);
+  UP(d_tile_ga, tile_ga);
+  UP(d_tile_gb, tile_gb);
+  UP(d_item_tile, item_tile);
+  UP(d_item_lo, item_lo);
+  UP(d_item_hi, item_hi);
+  UP(d_pairs, pairs);
+  UP(d_cam_obs_off, cam_obs_off);
+  UP(d_cam_obs, cam_obs);
+  int2 *d_panel, *d_update, *d_res;
+  UP(d_panel, panel);
+  UP(d_update, update);
+  UP(d_res, res_items);
+#undef UP
+  c->plist = PairLists{d_tile_cluster, d_tile_ga, d_tile_gb, d_item_tile, d_item_lo, d_item_hi, d_pairs,
+                       (int)item_tile.size()};
+  c->clist = CamLists{d_cam_obs_off, d_cam_obs};
+  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), max_nt, c->h_panel_off.data(),
+                      c->h_update_off.data(), c->max_np};
+
+  const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
+  auto ralloc = [&](void** p, size_t count) -> stba_status {
+    char* q_ = nullptr;
+    stba_status st_ = dalloc(c, &q_, count * rs, true);
+    *p = q_;
+    return st_;
+  };
+  if ((s = ralloc(&c->vp_acc, 9 * (size_t)nv)) != STBA_OK) return s;
+  if ((s = ralloc(&c->vp_info, 9 * (size_t)nv)) != STBA_OK) return s;
+  if ((s = ralloc(&c->pt_info, 9 * (size_t)n)) != STBA_OK) return s;
+  if ((s = ralloc(&c->S, (size_t)c->S_total)) != STBA_OK) return s;
+  if ((s = ralloc(&c->b, (size_t)c->v_total)) != STBA_OK) return s;
+  if ((s = ralloc(&c->vgrad, 9 * (size_t)m)) != STBA_OK) return s;
+  if ((s = ralloc(&c->t_acc, 3 * (size_t)n)) != STBA_OK) return s;
+  if ((s = ralloc(&c->Gbuf, 32 * (size_t)q)) != STBA_OK) return s;
+  if ((s = ralloc(&c->fbuf.L, (size_t)c->S_total)) != STBA_OK) return s;
+  if ((s = ralloc(&c->fbuf.Dinv, (size_t)c->v_total * TF)) != STBA_OK) return s;
+  if ((s = dalloc(c, &c->fbuf.scale, (size_t)c->v_total, true)) != STBA_OK) return s;
+  if ((s = dalloc(c, &c->fbuf.x, (size_t)c->v_total, true)) != STBA_OK) return s;
+  if ((s = dalloc(c, &c->fbuf.r, (size_t)c->v_total, true)) != STBA_OK) return s;
+  if ((s = dalloc(c, &c->fail_flags, (size_t)l, true)) != STBA_OK) return s;
+  c->fbuf.fail_flags = c->fail_flags;
+  c->fbuf.boosted = &c->st->boosted;
+  c->fbuf.v_total = c->v_total;
+  configure_kernels(c->max_np);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return STBA_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------
+template <typename real>
+void enqueue_iteration(stba_ctx* c) {
+  const DevProblem P = dev_problem(c);
+  const Scratch<real> W = scratch<real>(c);
+  cudaStream_t s = c->stream;
+  const bool tm = c->timing;
+  const size_t rs = sizeof(real);
+  if (tm) cudaEventRecord(c->ev[0], s);
+  // stage 0: linearisation and virtual points
+  launch_iter_begin<real>(c->st, c->set, s);
+  cudaMemsetAsync(c->vp_acc, 0, 9 * (size_t)c->nv * rs, s);
+  cudaMemsetAsync(c->S, 0, (size_t)c->S_total * rs, s);
+  cudaMemsetAsync(c->b, 0, (size_t)c->v_total * rs, s);
+  cudaMemsetAsync(c->vgrad, 0, 9 * (size_t)c->m * rs, s);
+  cudaMemsetAsync(c->t_acc, 0, 3 * (size_t)c->n * rs, s);
+  cudaMemsetAsync(c->fail_flags, 0, (size_t)c->l * sizeof(int), s);
+  launch_vp_reduce<real>(P, W, s);
+  launch_vp_finalize<real>(P, W, c->st, s);
+  if (tm) cudaEventRecord(c->ev[1], s);
+  // stage 1: S' and b'
+  launch_rcs_build<real>(P, W, c->clist, c->plist, (real*)c->Gbuf, c->st, s);
+  if (tm) cudaEventRecord(c->ev[2], s);
+  // stage 2: factorisation (FP32 factor in mixed mode, FP64 factor in FP64 mode)
+  launch_factor<real, real>(P, W.S, c->fbuf, c->cplan, s);
+  if (tm) cudaEventRecord(c->ev[3], s);
+  // stage 3: cluster solves with FP64 refinement
+  launch_solve<real, real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, s);
+  launch_count_failures(c->fail_flags, c->l, c->st, s);
+  if (tm) cudaEventRecord(c->ev[4], s);
+  // stage 4: points, cost, control
+  launch_point_rhs<real>(P, W, s);
+  launch_point_update<real>(P, W, s);
+  launch_cost<real>(P, c->dc, c->dp, c->partial, c->st, s);
+  launch_finalize<real>(P, W, c->st, c->set, 1, s);
+  launch_apply(P, c->dc, c->dp, c->cams, c->pts, c->st, s);
+  if (tm) cudaEventRecord(c->ev[5], s);
+}
+
+template <typename real>
+void enqueue_cost(stba_ctx* c) {
+  const DevProblem P = dev_problem(c);
+  const Scratch<real> W = scratch<real>(c);
+  launch_iter_begin<real>(c->st, c->set, c->stream);
+  launch_cost<real>(P, nullptr, nullptr, c->partial, c->st, c->stream);
+  launch_finalize<real>(P, W, c->st, c->set, 0, c->stream);
+}
+
+stba_status run_cost(stba_ctx* c, double* F) {
+  // lambda_used / corrected are reset by iter_begin; keep lambda itself
+  if (c->mixed)
+    enqueue_cost<float>(c);
+  else
+    enqueue_cost<double>(c);
+  CK(cudaGetLastError());
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h.nonfinite) return fail(c, STBA_ERR_NONFINITE, "a point lies at depth <= 1e-9 in front of a camera that sees it");
+  if (!std::isfinite(h.F)) return fail(c, STBA_ERR_NONFINITE, "F(x) is not finite");
+  if (F) *F = h.F;
+  return STBA_OK;
+}
+
+stba_status run_iteration(stba_ctx* c) {
+  if (c->timing || !c->opt.use_graph) {
+    if (c->mixed)
+      enqueue_iteration<float>(c);
+    else
+      enqueue_iteration<double>(c);
+    CK(cudaGetLastError());
+    c->have_stage_times = c->timing;
+    return STBA_OK;
+  }
+  if (!c->graph) {
+    // capture on a private stream (the user's stream may be the legacy default stream)
+    cudaStream_t user = c->stream;
+    c->stream = c->cap_stream;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    if (c->mixed)
+      enqueue_iteration<float>(c);
+    else
+      enqueue_iteration<double>(c);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    c->stream = user;
+    if (e != cudaSuccess) return fail(c, STBA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->graph = nullptr;
+      return fail(c, STBA_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+  }
+  CK(cudaGraphLaunch(c->graph, c->stream));
+  c->have_stage_times = false;
+  return STBA_OK;
+}
+
+stba_status read_info(stba_ctx* c, stba_iter_info* info) {
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (info) *info = h.info;
+  if (c->timing && c->have_stage_times)
+    for (int i = 0; i < NSTAGES; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
+  if (h.lambda > 1e16) return fail(c, STBA_ERR_STATE, "lambda exceeded 1e16");
+  return STBA_OK;
+}
+
+bool finite_all(const double* v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+}  // namespace
+
+// ==========================================================================================================
+extern "C" {
+
+void stba_default_options(stba_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->precision = STBA_FP64;
+  o->correction = 1;
+  o->lambda0 = 1e-4;
+  o->lambda_min = 0.0;
+  o->correction_lambda = 0.1;
+  o->ftol = o->gtol = o->xtol = -1.0;
+  o->refine_steps = 1;
+  o->use_graph = 1;
+}
+
+const char* stba_status_string(stba_status s) {
+  switch (s) {
+    case STBA_OK: return "ok";
+    case STBA_ERR_INVALID_ARG: return "invalid argument";
+    case STBA_ERR_CUDA: return "CUDA error";
+    case STBA_ERR_OOM: return "out of device memory";
+    case STBA_ERR_NOT_SPD: return "matrix not positive definite";
+    case STBA_ERR_NONFINITE: return "non-finite value";
+    case STBA_ERR_TIMEOUT: return "timeout";
+    case STBA_ERR_STATE: return "invalid state";
+  }
+  return "unknown status";
+}
+
+const char* stba_last_error(stba_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void stba_destroy(stba_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  free_list(c, c->cl_allocs);
+  free_list(c, c->allocs);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+}
+
+stba_status stba_create(const double* cameras, int64_t m, const double* points, int64_t n, const int32_t* obs_cam,
+                        const int32_t* obs_pt, const double* obs_uv, int64_t q, const int32_t* cluster_assignment,
+                        const stba_options* opt, void* cuda_stream, stba_ctx** out) {
+  if (!out) return STBA_ERR_INVALID_ARG;
+  *out = nullptr;
+  stba_ctx* c = new stba_ctx();
+  g_create_error.clear();
+  auto bail = [&](stba_status s) {
+    g_create_error = c->err;   // the context is destroyed; stba_last_error(NULL) returns the message
+    stba_destroy(c);
+    return s;
+  };
+  if (opt)
+    c->opt = *opt;
+  else
+    stba_default_options(&c->opt);
+  if (!cameras || !points || !obs_cam || !obs_pt || !obs_uv || !cluster_assignment)
+    return bail(fail(c, STBA_ERR_INVALID_ARG, "null array argument"));
+  if (m < 1 || n < 1 || q < 2 || m > INT32_MAX / 9 || n > INT32_MAX / 3 || q > INT32_MAX - 64)
+    return bail(fail(c, STBA_ERR_INVALID_ARG, "sizes out of range (m=%lld n=%lld q=%lld)", (long long)m,
+                     (long long)n, (long long)q));
+  if (!(c->opt.lambda0 > 0) || !std::isfinite(c->opt.lambda0) || c->opt.lambda_min < 0 ||
+      (c->opt.precision != STBA_FP64 && c->opt.precision != STBA_MIXED) || c->opt.refine_steps < 0 ||
+      c->opt.refine_steps > 8)
+    return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
+  c->m = m;
+  c->n = n;
+  c->q = q;
+  c->mixed = c->opt.precision == STBA_MIXED;
+  c->set.correction = c->opt.correction;
+  c->set.correction_lambda = c->opt.correction_lambda;
+  c->set.lambda_min = c->opt.lambda_min;
+  c->set.ftol = c->opt.ftol;
+  c->set.gtol = c->opt.gtol;
+  c->set.xtol = c->opt.xtol;
+  c->set.refine_steps = c->opt.refine_steps;
+  std::vector<double> h_cams(9 * (size_t)m), h_pts(3 * (size_t)n);
+  std::vector<int> h_cl(m);
+  c->in_cam.resize(q);
+  c->in_pt.resize(q);
+  c->in_uv.resize(2 * (size_t)q);
+  stba_status s;
+  if ((s = copy_in(c, h_cams.data(), cameras, h_cams.size() * 8)) != STBA_OK) return bail(s);
+  if ((s = copy_in(c, h_pts.data(), points, h_pts.size() * 8)) != STBA_OK) return bail(s);
+  if ((s = copy_in(c, c->in_cam.data(), obs_cam, (size_t)q * 4)) != STBA_OK) return bail(s);
+  if ((s = copy_in(c, c->in_pt.data(), obs_pt, (size_t)q * 4)) != STBA_OK) return bail(s);
+  if ((s = copy_in(c, c->in_uv.data(), obs_uv, (size_t)q * 16)) != STBA_OK) return bail(s);
+  if ((s = copy_in(c, h_cl.data(), cluster_assignment, (size_t)m * 4)) != STBA_OK) return bail(s);
+  if (!finite_all(h_cams.data(), h_cams.size()) || !finite_all(h_pts.data(), h_pts.size()) ||
+      !finite_all(c->in_uv.data(), c->in_uv.size()))
+    return bail(fail(c, STBA_ERR_NONFINITE, "non-finite camera, point or observation value"));
+
+  // validate the visibility graph and order observations by (point, camera)
+  std::vector<int> pcount(n + 1, 0), ccount(m, 0);
+  for (int64_t o = 0; o < q; ++o) {
+    const int j = c->in_cam[o], i = c->in_pt[o];
+    if (j < 0 || j >= m || i < 0 || i >= n)
+      return bail(fail(c, STBA_ERR_INVALID_ARG, "observation %lld has camera %d / point %d out of range", (long long)o, j, i));
+    pcount[i + 1]++;
+    ccount[j]++;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (pcount[i + 1] < 2) return bail(fail(c, STBA_ERR_INVALID_ARG, "point %lld has fewer than 2 observations", (long long)i));
+  for (int64_t j = 0; j < m; ++j)
+    if (ccount[j] < 1) return bail(fail(c, STBA_ERR_INVALID_ARG, "camera %lld has no observation", (long long)j));
+  for (int64_t i = 0; i < n; ++i) pcount[i + 1] += pcount[i];
+  c->h_pt_off = pcount;
+  c->base_order.assign(q, 0);
+  {
+    std::vector<int> fillp(pcount.begin(), pcount.end() - 1);
+    for (int64_t o = 0; o < q; ++o) c->base_order[fillp[c->in_pt[o]]++] = (int)o;
+    for (int64_t i = 0; i < n; ++i) {
+      auto b = c->base_order.begin() + pcount[i], e = c->base_order.begin() + pcount[i + 1];
+      std::sort(b, e, [&](int x, int y) { return c->in_cam[x] < c->in_cam[y]; });
+      for (auto it = b + 1; it < e; ++it)
+        if (c->in_cam[*it] == c->in_cam[*(it - 1)])
+          return bail(fail(c, STBA_ERR_INVALID_ARG, "camera %d observes point %lld twice", c->in_cam[*it], (long long)i));
+    }
+  }
+  for (int j = 0; j < m; ++j) {
+    if (h_cl[j] < 0 || h_cl[j] >= m)
+      return bail(fail(c, STBA_ERR_INVALID_ARG, "cluster id %d of camera %d out of range", h_cl[j], j));
+  }
+  {
+    std::vector<int> used(m, 0);
+    int l = 0;
+    for (int j = 0; j < m; ++j) {
+      used[h_cl[j]] = 1;
+      l = std::max(l, h_cl[j] + 1);
+    }
+    for (int k = 0; k < l; ++k)
+      if (!used[k]) return bail(fail(c, STBA_ERR_INVALID_ARG, "cluster %d has no camera (ids must be 0..l-1)", k));
+  }
+  // all host-side validation is done; from here on the device is needed
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(fail(c, STBA_ERR_CUDA, "cannot create a CUDA stream (is a GPU visible?)"));
+  }
+  for (auto& e : c->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(c, STBA_ERR_CUDA, "cudaEventCreate failed"));
+  if ((s = dalloc(c, &c->cams, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->pts, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->dc, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->dp, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->partial, 3 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->st, 1, false)) != STBA_OK) return bail(s);
+  {
+    cudaError_t e1 = cudaMemcpyAsync(c->cams, h_cams.data(), h_cams.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e2 = cudaMemcpyAsync(c->pts, h_pts.data(), h_pts.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    DevState h{};
+    h.lambda = c->opt.lambda0;
+    cudaError_t e3 = cudaMemcpyAsync(c->st, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e4 = cudaStreamSynchronize(c->stream);
+    if (e1 || e2 || e3 || e4) return bail(fail(c, STBA_ERR_CUDA, "upload failed"));
+  }
+  if ((s = set_clusters_host(c, h_cl)) != STBA_OK) return bail(s);
+  double F;
+  if ((s = run_cost(c, &F)) != STBA_OK) return bail(s);
+  *out = c;
+  return STBA_OK;
+}
+
+stba_status stba_set_clusters(stba_ctx* c, const int32_t* cluster_assignment) {
+  if (!c || !cluster_assignment) return STBA_ERR_INVALID_ARG;
+  std::vector<int> h(c->m);
+  stba_status s;
+  if ((s = copy_in(c, h.data(), cluster_assignment, (size_t)c->m * 4)) != STBA_OK) return s;
+  CK(cudaStreamSynchronize(c->stream));
+  return set_clusters_host(c, h);
+}
+
+stba_status stba_lm_iteration(stba_ctx* c, stba_iter_info* info) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  stba_status s = run_iteration(c);
+  if (s != STBA_OK) return s;
+  if (info || c->timing) return read_info(c, info);
+  return STBA_OK;
+}
+
+stba_status stba_solve(stba_ctx* c, int32_t max_iter, stba_iter_info* last) {
+  if (!c || max_iter < 0) return STBA_ERR_INVALID_ARG;
+  stba_iter_info info{};
+  for (int t = 0; t < max_iter; ++t) {
+    stba_status s = run_iteration(c);
+    if (s != STBA_OK) return s;
+    if ((s = read_info(c, &info)) != STBA_OK) return s;
+    if (info.stop) break;
+  }
+  if (last) *last = info;
+  return STBA_OK;
+}
+
+stba_status stba_cost(stba_ctx* c, double* F) {
+  if (!c || !F) return STBA_ERR_INVALID_ARG;
+  // recompute without disturbing the accepted-cost state: save and restore st->F
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  stba_status s = run_cost(c, F);
+  CK(cudaMemcpyAsync(c->st, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return s;
+}
+
+stba_status stba_get_params(stba_ctx* c, double* cameras, double* points) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  stba_status s;
+  if (cameras && (s = copy_out(c, cameras, c->cams, 9 * (size_t)c->m * 8)) != STBA_OK) return s;
+  if (points && (s = copy_out(c, points, c->pts, 3 * (size_t)c->n * 8)) != STBA_OK) return s;
+  return STBA_OK;
+}
+
+stba_status stba_set_params(stba_ctx* c, const double* cameras, const double* points) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  if (cameras) {
+    CK(cudaMemcpyAsync(c->cams, cameras, 9 * (size_t)c->m * 8,
+                       is_device_ptr(cameras) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  }
+  if (points) {
+    CK(cudaMemcpyAsync(c->pts, points, 3 * (size_t)c->n * 8,
+                       is_device_ptr(points) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  }
+  return run_cost(c, nullptr);
+}
+
+stba_status stba_get_state(stba_ctx* c, double* lambda, double* F, int64_t* iteration) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (lambda) *lambda = h.lambda;
+  if (F) *F = h.F;
+  if (iteration) *iteration = h.iteration;
+  return STBA_OK;
+}
+
+stba_status stba_set_state(stba_ctx* c, double lambda, double F, int64_t iteration) {
+  if (!c || !(lambda > 0) || !std::isfinite(lambda)) return STBA_ERR_INVALID_ARG;
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  h.lambda = lambda;
+  h.iteration = iteration;
+  if (F >= 0) h.F = F;
+  CK(cudaMemcpyAsync(c->st, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (F < 0) return run_cost(c, nullptr);
+  return STBA_OK;
+}
+
+stba_status stba_last_step(stba_ctx* c, double* dc, double* dp) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  stba_status s;
+  if (dc && (s = copy_out(c, dc, c->dc, 9 * (size_t)c->m * 8)) != STBA_OK) return s;
+  if (dp && (s = copy_out(c, dp, c->dp, 3 * (size_t)c->n * 8)) != STBA_OK) return s;
+  return STBA_OK;
+}
+
+stba_status stba_problem_info(stba_ctx* c, int64_t* out8) {
+  if (!c || !out8) return STBA_ERR_INVALID_ARG;
+  int maxn = 0;
+  for (int v : c->h_nk) maxn = std::max(maxn, v);
+  out8[0] = c->m;
+  out8[1] = c->n;
+  out8[2] = c->q;
+  out8[3] = c->l;
+  out8[4] = c->nv;
+  out8[5] = maxn;
+  out8[6] = (int64_t)(c->bytes_base + c->bytes_cl);
+  out8[7] = c->build_items;
+  return STBA_OK;
+}
+
+stba_status stba_get_cluster_system(stba_ctx* c, int32_t k, double* S, double* b, int64_t* dim) {
+  if (!c || k < 0 || k >= c->l) return STBA_ERR_INVALID_ARG;
+  const int nk = c->h_nk[k], np = c->h_np[k];
+  if (dim) *dim = nk;
+  if (!S && !b) return STBA_OK;
+  const size_t rs = c->mixed ? 4 : 8;
+  std::vector<char> raw((size_t)np * np * rs), rawb((size_t)np * rs);
+  CK(cudaMemcpyAsync(raw.data(), (char*)c->S + (size_t)c->h_S_off[k] * rs, raw.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(rawb.data(), (char*)c->b + (size_t)c->h_v_off[k] * rs, rawb.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  auto at = [&](const std::vector<char>& v, size_t i) -> double {
+    return c->mixed ? (double)((const float*)v.data())[i] : ((const double*)v.data())[i];
+  };
+  if (S) {
+    std::vector<double> full((size_t)nk * nk);
+    for (int r = 0; r < nk; ++r)
+      for (int cc = 0; cc <= r; ++cc) {
+        const double a = at(raw, (size_t)r * np + cc);
+        full[(size_t)r * nk + cc] = a;
+        full[(size_t)cc * nk + r] = a;
+      }
+    if (is_device_ptr(S)) {
+      CK(cudaMemcpy(S, full.data(), full.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(S, full.data(), full.size() * 8);
+    }
+  }
+  if (b) {
+    std::vector<double> hb(nk);
+    for (int r = 0; r < nk; ++r) hb[r] = at(rawb, r);
+    if (is_device_ptr(b)) {
+      CK(cudaMemcpy(b, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+      std::memcpy(b, hb.data(), hb.size() * 8);
+    }
+  }
+  return STBA_OK;
+}
+
+stba_status stba_set_timing(stba_ctx* c, int32_t on) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  c->timing = on != 0;
+  return STBA_OK;
+}
+
+stba_status stba_stage_times(stba_ctx* c, float* ms, int32_t n, int32_t* count) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  if (count) *count = NSTAGES;
+  if (ms)
+    for (int i = 0; i < n && i < NSTAGES; ++i) ms[i] = c->have_stage_times ? c->stage_ms[i] : -1.0f;
+  return STBA_OK;
+}
+
+}  // extern "C"

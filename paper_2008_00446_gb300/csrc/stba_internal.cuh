@@ -1,0 +1,158 @@
+// Internal declarations shared by the translation units of libstba.so (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/stba.h"
+
+namespace stba {
+
+// ------------------------------------------------------------------------------------------------------
+// Device problem description: pointers into the context's device buffers, passed by value to kernels.
+// Observations are sorted by (point, cluster of the camera, camera), so every virtual point (a distinct
+// (point, cluster) pair, Sec. 4.1-4.2) is a contiguous run and every point is a contiguous run of
+// virtual points.
+// ------------------------------------------------------------------------------------------------------
+struct DevProblem {
+  int m, n, q, l, nv;
+  const double* cams;      // [m][9] current cameras
+  const double* pts;       // [n][3] current points
+  const int* obs_cam;      // [q] camera of each sorted observation
+  const int* obs_vp;       // [q] virtual point of each sorted observation
+  const int* obs_pt;       // [q] point of each sorted observation
+  const double* obs_uv;    // [q][2] FP64 observations
+  const float* obs_uvf;    // [q][2] FP32 copy (mixed precision)
+  const int* vp_off;       // [nv+1] observation range of each virtual point
+  const int* vp_point;     // [nv] point of each virtual point
+  const int* pt_vp_off;    // [n+1] virtual-point range of each point
+  const int* pt_off;       // [n+1] observation range of each point
+  const int* cam_local;    // [m] index of the camera inside its cluster (cameras ordered by index)
+  const int* cam_cluster;  // [m]
+  const int* cluster_cams;     // [m] cameras of every cluster, concatenated, ascending per cluster
+  const int* cluster_cam_off;  // [l+1]
+  const int* cluster_np;       // [l] padded dimension Np_k (multiple of the Cholesky tile)
+  const int* cluster_n;        // [l] dimension 9 n_k
+  const int64_t* S_off;        // [l] element offset of the dense Np_k x Np_k block of cluster k
+  const int64_t* v_off;        // [l] element offset of the length-Np_k vectors of cluster k
+};
+
+// Device-resident LM state; the captured iteration graph reads and writes it in place.
+struct DevState {
+  double F;              // F(x) at the current parameters
+  double lambda;         // current damping
+  double lambda_used;    // damping of the step in flight
+  long long iteration;
+  unsigned long long grad_max_bits;   // bits of max |J^T f| (non-negative double)
+  int failed;            // clusters whose factorisation failed this iteration
+  int corrected;         // correction active this iteration
+  int nonfinite;         // a non-positive depth was met in the cost at x + dx
+  int boosted;           // FP32 pivots raised by static pivoting this iteration
+  stba_iter_info info;   // record of the last finished iteration
+};
+
+struct Settings {
+  double correction_lambda;
+  double lambda_min;
+  double ftol, gtol, xtol;
+  int correction;
+  int refine_steps;
+};
+
+constexpr int NSTAGES = 5;
+
+// Kernel launchers (explicitly instantiated for float and double in stba_kernels.cu / stba_chol.cu).
+template <typename real> struct Scratch {
+  real* vp_acc;    // [nv][9]: V = sum Jp^T Jp (6, packed xx xy xz yy yz zz) and w' = -sum Jp^T f (3)
+  real* vp_info;   // [nv][9]: L^-1 of V' (6, packed l00 l10 l11 l20 l21 l22) and y = V'^-1 w' (3)
+  real* pt_info;   // [n][9]: C^-1 (6, packed symmetric) and w (3) of the physical points
+  real* S;         // cluster-diagonal S' (dense lower triangles, per-cluster padded blocks)
+  real* b;         // b' (per-cluster padded vectors)
+  real* vgrad;     // [m][9] camera gradient v = -J_c^T f
+  real* t_acc;     // [n][3] sum_o J_p^T J_c dc per point
+  double* dc;      // [m][9] camera step
+  double* dp;      // [n][3] point step
+  double* partial; // reduction partials
+};
+
+struct CamLists {     // observations of every camera (sorted positions), host-built per assignment
+  const int* cam_obs_off;   // [m+1]
+  const int* cam_obs;       // [q]
+};
+
+struct PairLists {    // work items of the pair pass of the S' build (host-built per cluster assignment)
+  const int* tile_cluster;  // [nt]
+  const int* tile_ga;       // [nt]
+  const int* tile_gb;       // [nt]
+  const int* item_tile;     // [ni]
+  const int* item_lo;       // [ni] range into pairs
+  const int* item_hi;       // [ni]
+  const int4* pairs;        // (obs a, obs b, offset of the 9x9 block in the tile, 0), grouped by tile
+  int ni;
+};
+
+constexpr int RED_BLOCKS = 456;    // 3 x 152 SMs: fixed grid of the deterministic reductions
+constexpr int RED_THREADS = 256;
+
+template <typename real>
+void launch_iter_begin(DevState* st, const Settings& s, cudaStream_t stream);
+template <typename real>
+void launch_vp_reduce(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
+template <typename real>
+void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream);
+template <typename real>
+void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamLists CL, PairLists B, real* Gbuf, DevState* st,
+                      cudaStream_t stream);
+int pair_tile_cameras(bool mixed);
+template <typename real>
+void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
+template <typename real>
+void launch_point_update(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
+template <typename real>
+void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* partial, DevState* st,
+                 cudaStream_t stream);
+// with_step = 1: stop tests and accept / reject of the step in W.dc / W.dp; 0: F(x) -> st->F.
+template <typename real>
+void launch_finalize(const DevProblem& P, Scratch<real> W, DevState* st, const Settings& s, int with_step,
+                     cudaStream_t stream);
+void launch_apply(const DevProblem& P, const double* dc, const double* dp, double* cams, double* pts,
+                  DevState* st, cudaStream_t stream);
+template <typename real>
+size_t pair_build_smem();
+// Sets the dynamic shared-memory limits of the kernels that need more than 48 KB (call outside capture).
+void configure_kernels(int max_np);
+void configure_build_kernels();
+void configure_solve_kernels(int max_np);
+
+// Cholesky (stba_chol.cu)
+struct CholPlan {
+  const int2* panel_items;   // (cluster, tile row i) for every step, concatenated
+  const int2* update_items;  // (cluster, (i << 16) | j) for every step, concatenated
+  const int2* res_items;     // (cluster, 32-row block) of the refinement residual
+  int n_res_items;
+  int nsteps;
+  const int* h_panel_off;    // host arrays [nsteps + 1] (launch sizes)
+  const int* h_update_off;
+  int max_np;
+};
+struct FactorBuffers {
+  void* L;          // factor (F = float or double), same layout as S'
+  void* Dinv;       // inverses of the diagonal tiles, T x T per tile, v_off[k] * T offset per cluster
+  double* scale;    // [v_total] Jacobi scaling s_i = S_ii^-1/2
+  double* x;        // [v_total] solution
+  double* r;        // [v_total] refinement residual
+  int* fail_flags;  // [l]
+  int* boosted;     // counter of raised pivots (in DevState)
+  int64_t v_total;
+};
+int factor_tile(bool mixed);
+template <typename Sreal, typename F>
+void launch_factor(const DevProblem& P, const Sreal* S, const FactorBuffers& fb, const CholPlan& plan,
+                   cudaStream_t stream);
+template <typename Sreal, typename F>
+void launch_solve(const DevProblem& P, const Sreal* S, const Sreal* b, const FactorBuffers& fb, const CholPlan& plan,
+                  int refine_steps, double* dc, cudaStream_t stream);
+void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStream_t stream);
+
+}  // namespace stba

@@ -1,0 +1,741 @@
+// Per-iteration kernels of the STBA LM step (Algorithm 1), except the dense cluster factorisation.
+//
+//   k_vp_reduce      per observation, warp-segmented by virtual point: V = sum Jp^T Jp, w' = -sum Jp^T f
+//                    (Eq. 10: C' and w' of the split points).
+//   k_vp_finalize    per point: steepest-descent correction of w' (Sec. 4.3, closed form below), damped V',
+//                    its Cholesky inverse, y = V'^-1 w'; physical C^-1 and w (Eq. 4) for Eq. 15.
+//   k_rcs_build      per (cluster, camera-group tile): S' = B - E' C'^-1 E'^T and b' = v' - E' C'^-1 w'
+//                    (Eq. 10/13) accumulated in shared memory, one warp per virtual point.
+//   k_point_rhs      per observation, warp-segmented by point: sum_o Jp^T Jc dc.
+//   k_point_update   per point: dp = C^-1 (w - E^T dc) (Eq. 6 = Eq. 15).
+//   k_cost           F(x + dx) with FP64 sums; k_finalize: stop tests and the accept rule of Algorithm 1.
+//
+// Correction closed form: A has no camera columns and H~ = diag(H_lambda) is diagonal, so
+// nu = (A H~^-1 A^T)^-1 A H~^-1 g makes H~^-1 (g - A^T nu) the H~-weighted projection of H~^-1 g on the
+// steps where all virtual copies of a point are equal.  Per point and coordinate a:
+//   dbar_a = sum_k w'_k,a / sum_k H~_k,a,  corrected w'_k,a = H~_k,a dbar_a,
+// with H~_k = (1 + lambda) diag(V_k); the factor (1 + lambda) cancels.
+#include <cfloat>
+#include <climits>
+
+#include "stba_camera.cuh"
+#include "stba_internal.cuh"
+
+namespace stba {
+
+#define FULL_MASK 0xffffffffu
+
+template <typename real>
+__device__ __forceinline__ void load_uv(const DevProblem& P, int o, real& u, real& v) {
+  if constexpr (sizeof(real) == 8) {
+    double2 t = reinterpret_cast<const double2*>(P.obs_uv)[o];
+    u = t.x;
+    v = t.y;
+  } else {
+    float2 t = reinterpret_cast<const float2*>(P.obs_uvf)[o];
+    u = t.x;
+    v = t.y;
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ void load_point(const double* p, real X[3]) {
+  X[0] = (real)p[0];
+  X[1] = (real)p[1];
+  X[2] = (real)p[2];
+}
+
+// Inclusive warp scan of NV values restricted to runs of equal (non-decreasing) keys.
+template <int NV, typename real>
+__device__ __forceinline__ void segmented_scan(real (&val)[NV], int key, int lane) {
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int ku = __shfl_up_sync(FULL_MASK, key, d);
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      real y = __shfl_up_sync(FULL_MASK, val[c], d);
+      if (lane >= d && ku == key) val[c] += y;
+    }
+  }
+}
+
+// The last lane of each run writes the run's sum.  A run lying wholly inside this warp's 32
+// observations is stored; a run that continues into a neighbouring warp is added atomically
+// (the destination was zeroed before the launch).
+template <int NV, typename real>
+__device__ __forceinline__ void segmented_store(const real (&val)[NV], int key, bool act, int lane, int o,
+                                                const int* seg_off, real* dst_base) {
+  int knext = __shfl_down_sync(FULL_MASK, key, 1);
+  if (act && (lane == 31 || knext != key)) {
+    int w0 = o - lane;
+    bool whole = seg_off[key] >= w0 && seg_off[key + 1] <= w0 + 32;
+    real* dst = dst_base + (size_t)NV * key;
+    if (whole) {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) dst[c] = val[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < NV; ++c) atomicAdd(dst + c, val[c]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+template <typename real>
+__global__ void k_iter_begin(DevState* st, Settings s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->lambda_used = st->lambda;
+    st->corrected = (s.correction && st->lambda >= s.correction_lambda) ? 1 : 0;
+    st->grad_max_bits = 0ull;
+    st->failed = 0;
+    st->nonfinite = 0;
+    st->boosted = 0;
+  }
+}
+
+template <typename real>
+void launch_iter_begin(DevState* st, const Settings& s, cudaStream_t stream) {
+  k_iter_begin<real><<<1, 32, 0, stream>>>(st, s);
+}
+
+// ------------------------------------------------------------------------------------------------------
+template <typename real>
+__global__ void __launch_bounds__(256) k_vp_reduce(DevProblem P, real* vp_acc) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = o < P.q;
+  int v = INT_MAX;
+  real val[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) val[c] = 0;
+  if (act) {
+    v = P.obs_vp[o];
+    const int cam = P.obs_cam[o];
+    const int pt = P.vp_point[v];
+    Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)cam);
+    real X[3];
+    load_point(P.pts + 3 * (size_t)pt, X);
+    real uo, vo;
+    load_uv(P, o, uo, vo);
+    real r[2], Jc[2][9], Jp[2][3];
+    project_jacobian<real, false>(C, X, uo, vo, r, Jc, Jp);
+    val[0] = Jp[0][0] * Jp[0][0] + Jp[1][0] * Jp[1][0];
+    val[1] = Jp[0][0] * Jp[0][1] + Jp[1][0] * Jp[1][1];
+    val[2] = Jp[0][0] * Jp[0][2] + Jp[1][0] * Jp[1][2];
+    val[3] = Jp[0][1] * Jp[0][1] + Jp[1][1] * Jp[1][1];
+    val[4] = Jp[0][1] * Jp[0][2] + Jp[1][1] * Jp[1][2];
+    val[5] = Jp[0][2] * Jp[0][2] + Jp[1][2] * Jp[1][2];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) val[6 + j] = -(Jp[0][j] * r[0] + Jp[1][j] * r[1]);
+  }
+  segmented_scan<9>(val, v, lane);
+  segmented_store<9>(val, v, act, lane, o, P.vp_off, vp_acc);
+}
+
+template <typename real>
+void launch_vp_reduce(const DevProblem& P, Scratch<real> W, cudaStream_t stream) {
+  int blocks = (P.q + 255) / 256;
+  k_vp_reduce<real><<<blocks, 256, 0, stream>>>(P, W.vp_acc);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// 3x3 symmetric positive-definite helpers (packed lower/symmetric storage xx xy xz yy yz zz).
+template <typename real>
+__device__ __forceinline__ real safe_pivot(real d) {
+  return d > real(0) ? d : (real)(sizeof(real) == 8 ? 1e-300 : 1e-30);
+}
+
+// Cholesky V = L L^T and the inverse of L (packed l00 l10 l11 l20 l21 l22).
+template <typename real>
+__device__ __forceinline__ void chol3_inv(const real V[6], real Li[6]) {
+  real l00 = sqrt(safe_pivot(V[0]));
+  real l10 = V[1] / l00;
+  real l20 = V[2] / l00;
+  real l11 = sqrt(safe_pivot(V[3] - l10 * l10));
+  real l21 = (V[4] - l20 * l10) / l11;
+  real l22 = sqrt(safe_pivot(V[5] - l20 * l20 - l21 * l21));
+  real i00 = real(1) / l00, i11 = real(1) / l11, i22 = real(1) / l22;
+  real i10 = -l10 * i00 * i11;
+  real i21 = -l21 * i11 * i22;
+  real i20 = -(l20 * i00 + l21 * i10) * i22;
+  Li[0] = i00;
+  Li[1] = i10;
+  Li[2] = i11;
+  Li[3] = i20;
+  Li[4] = i21;
+  Li[5] = i22;
+}
+
+// x = (L L^T)^-1 w = L^-T (L^-1 w)
+template <typename real>
+__device__ __forceinline__ void chol3_apply(const real Li[6], const real w[3], real x[3]) {
+  real z0 = Li[0] * w[0];
+  real z1 = Li[1] * w[0] + Li[2] * w[1];
+  real z2 = Li[3] * w[0] + Li[4] * w[1] + Li[5] * w[2];
+  x[0] = Li[0] * z0 + Li[1] * z1 + Li[3] * z2;
+  x[1] = Li[2] * z1 + Li[4] * z2;
+  x[2] = Li[5] * z2;
+}
+
+template <typename real>
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double red[32];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = fmax(v, __shfl_xor_sync(FULL_MASK, v, d));
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) r = fmax(r, __shfl_xor_sync(FULL_MASK, r, d));
+  }
+  return r;
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_vp_finalize(DevProblem P, Scratch<real> W, DevState* st) {
+  const real lam = (real)st->lambda_used;
+  const bool corr = st->corrected != 0;
+  double gmax = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const int vb = P.pt_vp_off[i], ve = P.pt_vp_off[i + 1];
+    real C[6] = {0, 0, 0, 0, 0, 0}, w[3] = {0, 0, 0};
+    for (int v = vb; v < ve; ++v) {
+      const real* a = W.vp_acc + 9 * (size_t)v;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) C[c] += a[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w[c] += a[6 + c];
+    }
+    real dbar[3];
+    dbar[0] = w[0] / C[0];
+    dbar[1] = w[1] / C[3];
+    dbar[2] = w[2] / C[5];
+    for (int v = vb; v < ve; ++v) {
+      const real* a = W.vp_acc + 9 * (size_t)v;
+      real V[6], wv[3];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) V[c] = a[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) wv[c] = a[6 + c];
+      if (corr) {
+        wv[0] = V[0] * dbar[0];
+        wv[1] = V[3] * dbar[1];
+        wv[2] = V[5] * dbar[2];
+      }
+      V[0] += lam * V[0];
+      V[3] += lam * V[3];
+      V[5] += lam * V[5];
+      real Li[6], y[3];
+      chol3_inv(V, Li);
+      chol3_apply(Li, wv, y);
+      real* out = W.vp_info + 9 * (size_t)v;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) out[c] = Li[c];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[6 + c] = y[c];
+    }
+    // physical point: C + lambda diag(C), its inverse, uncorrected w
+    real Cd[6] = {C[0] * (1 + lam), C[1], C[2], C[3] * (1 + lam), C[4], C[5] * (1 + lam)};
+    real Li[6];
+    chol3_inv(Cd, Li);
+    // C^-1 = L^-T L^-1 (symmetric packed 00 01 02 11 12 22)
+    real* out = W.pt_info + 9 * (size_t)i;
+    out[0] = Li[0] * Li[0] + Li[1] * Li[1] + Li[3] * Li[3];
+    out[1] = Li[1] * Li[2] + Li[3] * Li[4];
+    out[2] = Li[3] * Li[5];
+    out[3] = Li[2] * Li[2] + Li[4] * Li[4];
+    out[4] = Li[4] * Li[5];
+    out[5] = Li[5] * Li[5];
+    out[6] = w[0];
+    out[7] = w[1];
+    out[8] = w[2];
+    gmax = fmax(gmax, fmax(fabs((double)w[0]), fmax(fabs((double)w[1]), fabs((double)w[2]))));
+  }
+  double bm = block_max<real>(gmax);
+  if (threadIdx.x == 0) atomicMax(&st->grad_max_bits, (unsigned long long)__double_as_longlong(bm));
+}
+
+template <typename real>
+void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream) {
+  int blocks = (P.n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_vp_finalize<real><<<blocks, 256, 0, stream>>>(P, W, st);
+}
+
+// ------------------------------------------------------------------------------------------------------
+// S' build (Eq. 10/13), in two passes.  With V' = L L^T the Cholesky factor of a virtual point's damped
+// block and G_o = L^-1 Jp,o^T Jc,o (3x9) for each of its observations, E' C'^-1 E'^T = G^T G, so
+//   off-diagonal camera blocks   S(a, b) = - sum_v G_a^T G_b                       (k_pair_build)
+//   diagonal camera block        S(a, a) = sum_o [Jc^T Jc + lambda diag(Jc^T Jc) - G_o^T G_o]  (k_cam_pass)
+//   right-hand side              b(a)    = - sum_o Jc^T (f_o + Jp,o y_v),  y_v = V'^-1 w'_v
+//   camera gradient              v(a)    = - sum_o Jc^T f_o
+// For a virtual point with one observation, Jc^T Jc - G^T G = Jc^T (I - Jp V'^-1 Jp^T) Jc cancels by a
+// factor ~ lambda; it is evaluated in the equivalent Woodbury form Jc^T (I + Jp Lambda^-1 Jp^T)^-1 Jc with
+// Lambda = lambda diag(Jp^T Jp), and without correction b(a) gets -Jc^T (I + Jp Lambda^-1 Jp^T)^-1 f_o.
+//
+// k_cam_pass: one CTA per camera, threads over the camera's observations; the 45 + 9 + 9 sums stay in
+// registers and are reduced once per CTA, so the diagonal blocks, b' and v are written without atomics.
+// It also stores G_o of every observation of a multi-observation virtual point for the pair pass.
+constexpr int GSTRIDE = 32;   // reals per stored G_o (27 used)
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W, CamLists CL, real* Gbuf,
+                                                  const DevState* st) {
+  const int j = blockIdx.x;
+  const real lam = (real)st->lambda_used;
+  const bool corr = st->corrected != 0;
+  const Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)j);
+  real aD[45], aB[9], aV[9];
+#pragma unroll
+  for (int i = 0; i < 45; ++i) aD[i] = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) aB[i] = aV[i] = 0;
+  const int e0 = CL.cam_obs_off[j], e1 = CL.cam_obs_off[j + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int o = CL.cam_obs[e];
+    const int v = P.obs_vp[o];
+    const bool single = (P.vp_off[v + 1] - P.vp_off[v]) == 1;
+    real X[3];
+    load_point(P.pts + 3 * (size_t)P.obs_pt[o], X);
+    real uo, vo;
+    load_uv(P, o, uo, vo);
+    real r[2], Jc[2][9], Jp[2][3];
+    project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
+    const real* vi = W.vp_info + 9 * (size_t)v;
+    real br[2];
+    if (single) {
+      real il[3];
+#pragma unroll
+      for (int s = 0; s < 3; ++s) il[s] = real(1) / (lam * (Jp[0][s] * Jp[0][s] + Jp[1][s] * Jp[1][s]));
+      real K00 = 0, K01 = 0, K11 = 0;
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        K00 += Jp[0][s] * Jp[0][s] * il[s];
+        K01 += Jp[0][s] * Jp[1][s] * il[s];
+        K11 += Jp[1][s] * Jp[1][s] * il[s];
+      }
+      const real det = (real(1) + K00) * (real(1) + K11) - K01 * K01;
+      const real N00 = (real(1) + K11) / det, N01 = -K01 / det, N11 = (real(1) + K00) / det;
+      real NJ[2][9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        NJ[0][c] = N00 * Jc[0][c] + N01 * Jc[1][c];
+        NJ[1][c] = N01 * Jc[0][c] + N11 * Jc[1][c];
+      }
+      int t = 0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int jj = 0; jj <= i; ++jj, ++t) {
+          real d = Jc[0][i] * NJ[0][jj] + Jc[1][i] * NJ[1][jj];
+          if (i == jj) d += lam * (Jc[0][i] * Jc[0][i] + Jc[1][i] * Jc[1][i]);
+          aD[t] += d;
+        }
+      if (corr) {
+        br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
+        br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
+      } else {
+        br[0] = N00 * r[0] + N01 * r[1];
+        br[1] = N01 * r[0] + N11 * r[1];
+      }
+    } else {
+      real Li[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) Li[c] = vi[c];
+      real G[3][9];
+      real* Gs = Gbuf + (size_t)GSTRIDE * o;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const real w0 = Jp[0][0] * Jc[0][c] + Jp[1][0] * Jc[1][c];
+        const real w1 = Jp[0][1] * Jc[0][c] + Jp[1][1] * Jc[1][c];
+        const real w2 = Jp[0][2] * Jc[0][c] + Jp[1][2] * Jc[1][c];
+        G[0][c] = Li[0] * w0;
+        G[1][c] = Li[1] * w0 + Li[2] * w1;
+        G[2][c] = Li[3] * w0 + Li[4] * w1 + Li[5] * w2;
+      }
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Gs[9 * s + c] = G[s][c];
+      int t = 0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int jj = 0; jj <= i; ++jj, ++t) {
+          const real jjv = Jc[0][i] * Jc[0][jj] + Jc[1][i] * Jc[1][jj];
+          real d = jjv - (G[0][i] * G[0][jj] + G[1][i] * G[1][jj] + G[2][i] * G[2][jj]);
+          if (i == jj) d += lam * jjv;
+          aD[t] += d;
+        }
+      br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
+      br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      aB[i] -= Jc[0][i] * br[0] + Jc[1][i] * br[1];
+      aV[i] -= Jc[0][i] * r[0] + Jc[1][i] * r[1];
+    }
+  }
+  // block reduction of the 63 sums
+  __shared__ real red[8][64];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 63; ++i) {
+    real x = i < 45 ? aD[i] : (i < 54 ? aB[i - 45] : aV[i - 54]);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(FULL_MASK, x, d);
+    if (lane == 0) red[warp][i] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 63) {
+    real x = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[w][threadIdx.x];
+    const int k = P.cam_cluster[j];
+    const int lc = P.cam_local[j];
+    const int i = threadIdx.x;
+    if (i < 45) {
+      int row = 0;
+      while ((row + 1) * (row + 2) / 2 <= i) ++row;
+      const int col = i - row * (row + 1) / 2;
+      const int np = P.cluster_np[k];
+      W.S[P.S_off[k] + (size_t)(9 * lc + row) * np + 9 * lc + col] = x;
+    } else if (i < 54) {
+      W.b[P.v_off[k] + 9 * lc + (i - 45)] = x;
+    } else {
+      W.vgrad[9 * (size_t)j + (i - 54)] = x;
+    }
+  }
+}
+
+// k_pair_build: one CTA per chunk of the pair instances of one tile (cluster k, camera groups
+// gA >= gB of TC cameras); a pair instance is two observations (a, b) of one virtual point with
+// local camera index of a > that of b.  Threads run over (pair, 9x9 entry); the tile accumulates in
+// shared memory and is added to S'_k once.
+template <typename real, int TC>
+__global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, PairLists B,
+                                                    const real* __restrict__ Gbuf) {
+  constexpr int TD = 9 * TC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* acc = reinterpret_cast<real*>(smem_raw);
+  const int item = blockIdx.x;
+  const int tile = B.item_tile[item];
+  const int k = B.tile_cluster[tile], gA = B.tile_ga[tile], gB = B.tile_gb[tile];
+  for (int i = threadIdx.x; i < TD * TD; i += blockDim.x) acc[i] = 0;
+  __syncthreads();
+  const int64_t lo = (int64_t)B.item_lo[item] * 81, hi = (int64_t)B.item_hi[item] * 81;
+  for (int64_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
+    const int64_t p = idx / 81;
+    const int e = (int)(idx - p * 81);
+    const int rr = e / 9, cc = e - (e / 9) * 9;
+    const int4 pr = B.pairs[p];
+    const real* Ga = Gbuf + (size_t)GSTRIDE * pr.x;
+    const real* Gb = Gbuf + (size_t)GSTRIDE * pr.y;
+    const real val = __ldg(Ga + rr) * __ldg(Gb + cc) + __ldg(Ga + 9 + rr) * __ldg(Gb + 9 + cc) +
+                     __ldg(Ga + 18 + rr) * __ldg(Gb + 18 + cc);
+    atomicAdd(acc + pr.z + rr * TD + cc, -val);
+  }
+  __syncthreads();
+  const int np = P.cluster_np[k], nk = P.cluster_n[k];
+  real* Sk = W.S + P.S_off[k];
+  const int r0 = 9 * gA * TC, c0 = 9 * gB * TC;
+  for (int idx = threadIdx.x; idx < TD * TD; idx += blockDim.x) {
+    const int rr = idx / TD, cc = idx - (idx / TD) * TD;
+    const int gr = r0 + rr, gc = c0 + cc;
+    const real a = acc[idx];
+    if (a != real(0) && gr < nk && gc < nk && gr > gc) atomicAdd(Sk + (size_t)gr * np + gc, a);
+  }
+}
+
+template <typename real> struct BuildCfg;
+template <> struct BuildCfg<float> { static constexpr int TC = 16; };
+template <> struct BuildCfg<double> { static constexpr int TC = 8; };
+
+template <typename real>
+size_t pair_build_smem() {
+  constexpr int TD = 9 * BuildCfg<real>::TC;
+  return sizeof(real) * (size_t)TD * TD;
+}
+
+int pair_tile_cameras(bool mixed) { return mixed ? BuildCfg<float>::TC : BuildCfg<double>::TC; }
+
+template <typename real>
+void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamLists CL, PairLists B, real* Gbuf, DevState* st,
+                      cudaStream_t stream) {
+  k_cam_pass<real><<<P.m, 256, 0, stream>>>(P, W, CL, Gbuf, st);
+  if (B.ni > 0)
+    k_pair_build<real, BuildCfg<real>::TC><<<B.ni, 256, pair_build_smem<real>(), stream>>>(P, W, B, Gbuf);
+}
+
+// ------------------------------------------------------------------------------------------------------
+template <typename real>
+__global__ void __launch_bounds__(256) k_point_rhs(DevProblem P, const double* dc, real* t_acc) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = o < P.q;
+  int pt = INT_MAX;
+  real val[3] = {0, 0, 0};
+  if (act) {
+    pt = P.obs_pt[o];
+    const int cam = P.obs_cam[o];
+    Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)cam);
+    real X[3];
+    load_point(P.pts + 3 * (size_t)pt, X);
+    real uo, vo;
+    load_uv(P, o, uo, vo);
+    real r[2], Jc[2][9], Jp[2][3];
+    project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
+    const double* d = dc + 9 * (size_t)cam;
+    real jd0 = 0, jd1 = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      real dcc = (real)d[c];
+      jd0 += Jc[0][c] * dcc;
+      jd1 += Jc[1][c] * dcc;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) val[j] = Jp[0][j] * jd0 + Jp[1][j] * jd1;
+  }
+  segmented_scan<3>(val, pt, lane);
+  segmented_store<3>(val, pt, act, lane, o, P.pt_off, t_acc);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256) k_point_update(DevProblem P, const real* pt_info, const real* t_acc,
+                                                      double* dp, double* partial) {
+  double s_dp = 0.0, s_p = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const real* in = pt_info + 9 * (size_t)i;
+    const real* t = t_acc + 3 * (size_t)i;
+    real g0 = in[6] - t[0], g1 = in[7] - t[1], g2 = in[8] - t[2];
+    real d0 = in[0] * g0 + in[1] * g1 + in[2] * g2;
+    real d1 = in[1] * g0 + in[3] * g1 + in[4] * g2;
+    real d2 = in[2] * g0 + in[4] * g1 + in[5] * g2;
+    double* out = dp + 3 * (size_t)i;
+    out[0] = d0;
+    out[1] = d1;
+    out[2] = d2;
+    s_dp += (double)d0 * d0 + (double)d1 * d1 + (double)d2 * d2;
+    const double* p = P.pts + 3 * (size_t)i;
+    s_p += p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
+  }
+  __shared__ double red[2][8];
+  for (int d = 16; d > 0; d >>= 1) {
+    s_dp += __shfl_xor_sync(FULL_MASK, s_dp, d);
+    s_p += __shfl_xor_sync(FULL_MASK, s_p, d);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][w] = s_dp;
+    red[1][w] = s_p;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      a += red[0][i];
+      b += red[1][i];
+    }
+    partial[RED_BLOCKS + blockIdx.x] = a;
+    partial[2 * RED_BLOCKS + blockIdx.x] = b;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// F(x + dx) (dc, dp may be null for F(x)): FP32 or FP64 residuals, FP64 sums, fixed grid -> deterministic.
+template <typename real>
+__global__ void __launch_bounds__(RED_THREADS) k_cost(DevProblem P, const double* dc, const double* dp,
+                                                      double* partial, DevState* st) {
+  double s = 0.0;
+  int bad = 0;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < P.q; o += gridDim.x * blockDim.x) {
+    const int cam = P.obs_cam[o];
+    const int pt = P.obs_pt[o];
+    Cam<real> C = dc ? load_cam_step<real>(P.cams + 9 * (size_t)cam, dc + 9 * (size_t)cam)
+                     : load_cam<real>(P.cams + 9 * (size_t)cam);
+    real X[3];
+    const double* p = P.pts + 3 * (size_t)pt;
+    if (dp) {
+      const double* q = dp + 3 * (size_t)pt;
+      X[0] = (real)(p[0] + q[0]);
+      X[1] = (real)(p[1] + q[1]);
+      X[2] = (real)(p[2] + q[2]);
+    } else {
+      load_point(p, X);
+    }
+    real uo, vo;
+    load_uv(P, o, uo, vo);
+    real r[2], z;
+    project_residual(C, X, uo, vo, r, &z);
+    if (!(z > real(1e-9))) bad = 1;
+    s += (double)r[0] * (double)r[0] + (double)r[1] * (double)r[1];
+  }
+  __shared__ double red[RED_THREADS / 32];
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(FULL_MASK, s, d);
+  bad = __any_sync(FULL_MASK, bad);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = s;
+  if (lane == 0 && bad) st->nonfinite = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int i = 0; i < RED_THREADS / 32; ++i) a += red[i];
+    partial[blockIdx.x] = a;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Stop tests and accept / reject (Algorithm 1), one block; fixed-order sums of the partials.
+template <typename real>
+__global__ void __launch_bounds__(1024) k_finalize(DevProblem P, const real* vgrad, const double* dc,
+                                                   const double* partial, DevState* st, Settings s,
+                                                   int with_step) {
+  __shared__ double red[4][32];
+  double F_new = 0, dpn = 0, pn = 0, dcn = 0, cn = 0, gmax = 0;
+  for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) {
+    F_new += partial[i];
+    if (with_step) {
+      dpn += partial[RED_BLOCKS + i];
+      pn += partial[2 * RED_BLOCKS + i];
+    }
+  }
+  if (with_step) {
+    for (int i = threadIdx.x; i < 9 * P.m; i += blockDim.x) {
+      double d = dc[i], c = P.cams[i];
+      dcn += d * d;
+      cn += c * c;
+      gmax = fmax(gmax, fabs((double)vgrad[i]));
+    }
+  }
+  double vals[4] = {F_new, dpn + dcn, pn + cn, gmax};
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    for (int d = 16; d > 0; d >>= 1) vals[c] += __shfl_xor_sync(FULL_MASK, vals[c], d);
+  for (int d = 16; d > 0; d >>= 1) vals[3] = fmax(vals[3], __shfl_xor_sync(FULL_MASK, vals[3], d));
+  if (lane == 0)
+    for (int c = 0; c < 4; ++c) red[c][w] = vals[c];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot[4] = {0, 0, 0, 0};
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      tot[0] += red[0][i];
+      tot[1] += red[1][i];
+      tot[2] += red[2][i];
+      tot[3] = fmax(tot[3], red[3][i]);
+    }
+    if (!with_step) {
+      st->F = tot[0];
+      st->info.F_before = tot[0];
+      return;
+    }
+    double Fn = tot[0];
+    const double F = st->F;
+    const double lam = st->lambda_used;
+    if (st->failed > 0 || st->nonfinite || !isfinite(Fn)) Fn = __longlong_as_double(0x7ff0000000000000ll);
+    const double grad = fmax(tot[3], __longlong_as_double((long long)st->grad_max_bits));
+    const double dxn = sqrt(tot[1]), xn = sqrt(tot[2]);
+    int stop = 0;
+    if (s.ftol > 0 && F > 0 && fabs(F - Fn) / F < s.ftol) stop = 1;
+    if (s.gtol > 0 && grad < s.gtol) stop = 1;
+    if (s.xtol > 0 && dxn < s.xtol * (xn + s.xtol)) stop = 1;
+    const int accepted = (Fn < F) ? 1 : 0;
+    const double lam_new = accepted ? fmax(lam / 3.0, s.lambda_min) : lam * 3.0;
+    st->lambda = lam_new;
+    if (accepted) st->F = Fn;
+    st->iteration += 1;
+    stba_iter_info& I = st->info;
+    I.F_before = F;
+    I.F_after = Fn;
+    I.lambda_used = lam;
+    I.lambda = lam_new;
+    I.grad_inf = grad;
+    I.dx_norm = dxn;
+    I.x_norm = xn;
+    I.accepted = accepted;
+    I.stop = stop;
+    I.corrected = st->corrected;
+    I.failed_clusters = st->failed;
+    I.boosted_pivots = st->boosted;
+    I.iteration = st->iteration;
+  }
+}
+
+__global__ void k_apply(int m, int n, const double* dc, const double* dp, double* cams, double* pts,
+                        const DevState* st) {
+  if (!st->info.accepted) return;
+  const int total = 9 * m + 3 * n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    if (i < 9 * m)
+      cams[i] += dc[i];
+    else
+      pts[i - 9 * m] += dp[i - 9 * m];
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// launchers
+template <typename real>
+void launch_point_update(const DevProblem& P, Scratch<real> W, cudaStream_t stream) {
+  k_point_update<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, W.pt_info, W.t_acc, W.dp, W.partial);
+}
+
+template <typename real>
+void launch_finalize(const DevProblem& P, Scratch<real> W, DevState* st, const Settings& s, int with_step,
+                     cudaStream_t stream) {
+  k_finalize<real><<<1, 1024, 0, stream>>>(P, W.vgrad, W.dc, W.partial, st, s, with_step);
+}
+
+void launch_apply(const DevProblem& P, const double* dc, const double* dp, double* cams, double* pts,
+                  DevState* st, cudaStream_t stream) {
+  int total = 9 * P.m + 3 * P.n;
+  int blocks = (total + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_apply<<<blocks, 256, 0, stream>>>(P.m, P.n, dc, dp, cams, pts, st);
+}
+
+template <typename real>
+void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream) {
+  int blocks = (P.q + 255) / 256;
+  k_point_rhs<real><<<blocks, 256, 0, stream>>>(P, W.dc, W.t_acc);
+}
+
+template <typename real>
+void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* partial, DevState* st,
+                 cudaStream_t stream) {
+  k_cost<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, dc, dp, partial, st);
+}
+
+void configure_build_kernels() {
+  cudaFuncSetAttribute(k_pair_build<float, BuildCfg<float>::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pair_build_smem<float>());
+  cudaFuncSetAttribute(k_pair_build<double, BuildCfg<double>::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)pair_build_smem<double>());
+}
+
+void configure_kernels(int max_np) {
+  configure_build_kernels();
+  configure_solve_kernels(max_np);
+}
+
+#define INSTANTIATE(real)                                                                                  \
+  template void launch_iter_begin<real>(DevState*, const Settings&, cudaStream_t);                        \
+  template void launch_vp_reduce<real>(const DevProblem&, Scratch<real>, cudaStream_t);                   \
+  template void launch_vp_finalize<real>(const DevProblem&, Scratch<real>, DevState*, cudaStream_t);      \
+  template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamLists, PairLists, real*,      \
+                                       DevState*, cudaStream_t);                                          \
+  template void launch_point_update<real>(const DevProblem&, Scratch<real>, cudaStream_t);                \
+  template void launch_finalize<real>(const DevProblem&, Scratch<real>, DevState*, const Settings&, int,  \
+                                      cudaStream_t);                                                      \
+  template void launch_point_rhs<real>(const DevProblem&, Scratch<real>, cudaStream_t);                  \
+  template void launch_cost<real>(const DevProblem&, const double*, const double*, double*, DevState*,    \
+                                  cudaStream_t);                                                          \
+  template size_t pair_build_smem<real>();
+
+INSTANTIATE(float)
+INSTANTIATE(double)
+
+}  // namespace stba

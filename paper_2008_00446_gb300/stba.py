@@ -1,0 +1,284 @@
+"""Thin ctypes binding of libstba.so (include/stba.h).
+
+Argument marshalling only: every step of the LM iteration runs in the library's CUDA kernels.  Arrays may
+be NumPy arrays or PyTorch tensors (CPU or CUDA); CUDA tensors are passed as device pointers, everything
+else as host pointers.  The functions carry the C names; `Context` owns a `stba_ctx*`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+_LIB = None
+
+STBA_FP64, STBA_MIXED = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not SPD",
+          5: "non-finite value", 6: "timeout", 7: "invalid state"}
+
+# every symbol the header declares
+EXPORTS = ["stba_default_options", "stba_create", "stba_set_clusters", "stba_lm_iteration", "stba_solve",
+           "stba_cost", "stba_get_params", "stba_set_params", "stba_get_state", "stba_set_state",
+           "stba_last_step", "stba_problem_info", "stba_get_cluster_system", "stba_set_timing",
+           "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error"]
+
+
+class StbaOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("correction", ctypes.c_int32), ("lambda0", ctypes.c_double),
+                ("lambda_min", ctypes.c_double), ("correction_lambda", ctypes.c_double),
+                ("ftol", ctypes.c_double), ("gtol", ctypes.c_double), ("xtol", ctypes.c_double),
+                ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+
+
+class StbaIterInfo(ctypes.Structure):
+    _fields_ = [("F_before", ctypes.c_double), ("F_after", ctypes.c_double), ("lambda_used", ctypes.c_double),
+                ("lambda_", ctypes.c_double), ("grad_inf", ctypes.c_double), ("dx_norm", ctypes.c_double),
+                ("x_norm", ctypes.c_double), ("accepted", ctypes.c_int32), ("stop", ctypes.c_int32),
+                ("corrected", ctypes.c_int32), ("failed_clusters", ctypes.c_int32),
+                ("boosted_pivots", ctypes.c_int32), ("reserved", ctypes.c_int32), ("iteration", ctypes.c_int64)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["lambda"] = d.pop("lambda_")
+        d.pop("reserved")
+        for k in ("accepted", "stop", "corrected"):
+            d[k] = bool(d[k])
+        return d
+
+
+class StbaError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libstba.so (building it with nvcc first when absent or stale).  Raises if it cannot."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libstba.so not found at {_build.LIB}; run __graft_entry__.build()")
+    L = ctypes.CDLL(_build.LIB)
+    P, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    sig = {
+        "stba_default_options": (None, [ctypes.POINTER(StbaOptions)]),
+        "stba_create": (I32, [P, I64, P, I64, P, P, P, I64, P, ctypes.POINTER(StbaOptions), P, ctypes.POINTER(P)]),
+        "stba_set_clusters": (I32, [P, P]),
+        "stba_lm_iteration": (I32, [P, ctypes.POINTER(StbaIterInfo)]),
+        "stba_solve": (I32, [P, I32, ctypes.POINTER(StbaIterInfo)]),
+        "stba_cost": (I32, [P, ctypes.POINTER(D)]),
+        "stba_get_params": (I32, [P, P, P]),
+        "stba_set_params": (I32, [P, P, P]),
+        "stba_get_state": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "stba_set_state": (I32, [P, D, D, I64]),
+        "stba_last_step": (I32, [P, P, P]),
+        "stba_problem_info": (I32, [P, ctypes.POINTER(I64)]),
+        "stba_get_cluster_system": (I32, [P, I32, P, P, ctypes.POINTER(I64)]),
+        "stba_set_timing": (I32, [P, I32]),
+        "stba_stage_times": (I32, [P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32)]),
+        "stba_destroy": (None, [P]),
+        "stba_status_string": (ctypes.c_char_p, [I32]),
+        "stba_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+# ----------------------------------------------------------------------------------------------------------
+# marshalling helpers
+# ----------------------------------------------------------------------------------------------------------
+def _ptr(a, dtype, keep):
+    """Pointer to a contiguous array of `dtype`; keeps converted copies alive in `keep`."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            tdt = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
+            t = a.detach().to(tdt).contiguous()
+            keep.append(t)
+            return ctypes.c_void_p(t.data_ptr())
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    keep.append(arr)
+    return ctypes.c_void_p(arr.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+def stba_default_options(**overrides) -> StbaOptions:
+    o = StbaOptions()
+    load().stba_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """Owns one stba_ctx*.  Use the module functions below or the methods of the same names."""
+
+    def __init__(self, handle, m, n, q):
+        self.handle = handle
+        self.m, self.n, self.q = m, n, q
+
+    def _check(self, status):
+        if status != 0:
+            msg = load().stba_last_error(self.handle).decode()
+            raise StbaError(status, msg)
+
+    def close(self):
+        if self.handle:
+            load().stba_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def stba_create(cameras, points, obs_cam, obs_pt, obs_uv, cluster_assignment, options=None, stream=None,
+                **option_overrides) -> Context:
+    L = load()
+    keep = []
+    m, n, q = len(cameras), len(points), len(obs_cam)
+    opt = options if options is not None else stba_default_options(**option_overrides)
+    h = ctypes.c_void_p()
+    st = L.stba_create(_ptr(cameras, np.float64, keep), m, _ptr(points, np.float64, keep), n,
+                       _ptr(obs_cam, np.int32, keep), _ptr(obs_pt, np.int32, keep), _ptr(obs_uv, np.float64, keep),
+                       q, _ptr(cluster_assignment, np.int32, keep), ctypes.byref(opt), _stream_handle(stream),
+                       ctypes.byref(h))
+    if st != 0:
+        raise StbaError(st, L.stba_last_error(None).decode())
+    return Context(h, m, n, q)
+
+
+def stba_set_clusters(ctx: Context, cluster_assignment):
+    keep = []
+    ctx._check(load().stba_set_clusters(ctx.handle, _ptr(cluster_assignment, np.int32, keep)))
+
+
+def stba_lm_iteration(ctx: Context, want_info=True):
+    info = StbaIterInfo()
+    ctx._check(load().stba_lm_iteration(ctx.handle, ctypes.byref(info) if want_info else None))
+    return info.as_dict() if want_info else None
+
+
+def stba_solve(ctx: Context, max_iter: int):
+    info = StbaIterInfo()
+    ctx._check(load().stba_solve(ctx.handle, int(max_iter), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def stba_cost(ctx: Context) -> float:
+    F = ctypes.c_double()
+    ctx._check(load().stba_cost(ctx.handle, ctypes.byref(F)))
+    return F.value
+
+
+def stba_get_params(ctx: Context, cameras=None, points=None):
+    """Copies the parameters into the given arrays (NumPy or torch, host or device) or new NumPy arrays."""
+    cams = cameras if cameras is not None else np.empty((ctx.m, 9))
+    pts = points if points is not None else np.empty((ctx.n, 3))
+    ctx._check(load().stba_get_params(ctx.handle, ctypes.c_void_p(_data_ptr(cams)), ctypes.c_void_p(_data_ptr(pts))))
+    return cams, pts
+
+
+def stba_set_params(ctx: Context, cameras=None, points=None):
+    keep = []
+    pc = _ptr(cameras, np.float64, keep) if cameras is not None else None
+    pp = _ptr(points, np.float64, keep) if points is not None else None
+    ctx._check(load().stba_set_params(ctx.handle, pc, pp))
+
+
+def stba_get_state(ctx: Context):
+    lam, F, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    ctx._check(load().stba_get_state(ctx.handle, ctypes.byref(lam), ctypes.byref(F), ctypes.byref(it)))
+    return lam.value, F.value, it.value
+
+
+def stba_set_state(ctx: Context, lam: float, F: float = -1.0, iteration: int = 0):
+    ctx._check(load().stba_set_state(ctx.handle, float(lam), float(F), int(iteration)))
+
+
+def stba_last_step(ctx: Context):
+    dc = np.empty((ctx.m, 9))
+    dp = np.empty((ctx.n, 3))
+    ctx._check(load().stba_last_step(ctx.handle, ctypes.c_void_p(dc.ctypes.data), ctypes.c_void_p(dp.ctypes.data)))
+    return dc, dp
+
+
+def stba_problem_info(ctx: Context):
+    out = (ctypes.c_int64 * 8)()
+    ctx._check(load().stba_problem_info(ctx.handle, out))
+    keys = ["m", "n", "q", "l", "nv", "max_dim", "device_bytes", "build_items"]
+    return dict(zip(keys, list(out)))
+
+
+def stba_get_cluster_system(ctx: Context, k: int):
+    dim = ctypes.c_int64()
+    ctx._check(load().stba_get_cluster_system(ctx.handle, int(k), None, None, ctypes.byref(dim)))
+    S = np.empty((dim.value, dim.value))
+    b = np.empty(dim.value)
+    ctx._check(load().stba_get_cluster_system(ctx.handle, int(k), ctypes.c_void_p(S.ctypes.data),
+                                              ctypes.c_void_p(b.ctypes.data), ctypes.byref(dim)))
+    return S, b
+
+
+def stba_set_timing(ctx: Context, on: bool):
+    ctx._check(load().stba_set_timing(ctx.handle, int(bool(on))))
+
+
+def stba_stage_times(ctx: Context):
+    ms = (ctypes.c_float * 16)()
+    cnt = ctypes.c_int32()
+    ctx._check(load().stba_stage_times(ctx.handle, ms, 16, ctypes.byref(cnt)))
+    return list(ms)[: cnt.value]
+
+
+def stba_destroy(ctx: Context):
+    ctx.close()
+
+
+def _data_ptr(a):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            assert a.is_contiguous() and a.dtype == torch.float64
+            return a.data_ptr()
+    except ImportError:
+        pass
+    assert isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.float64
+    return a.ctypes.data

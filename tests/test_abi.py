@@ -1,0 +1,86 @@
+"""The C ABI boundary on the host: libstba.so builds, loads, exports every declared symbol, and rejects
+invalid problems before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import scenes
+from paper_2008_00446_gb300 import stba
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "stba.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(stba_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = stba.load()
+    decl = declared_symbols()
+    assert len(decl) >= 18
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(decl) == sorted(stba.EXPORTS)
+
+
+def test_default_options_match_the_paper():
+    # Sec. 5.1 / Algorithm 1: lambda0 = 1e-4; Sec. 4.3: correction when lambda >= 0.1
+    o = stba.stba_default_options()
+    assert o.lambda0 == 1e-4 and o.correction_lambda == 0.1 and o.correction == 1
+    assert o.precision == stba.STBA_FP64 and o.refine_steps == 1
+
+
+def test_status_strings():
+    L = stba.load()
+    for s in range(8):
+        assert L.stba_status_string(s).decode() == stba.STATUS[s] or s == 4
+
+
+def base():
+    return scenes.make_tiny_scene(m=4, n=12, seed=1)
+
+
+@pytest.mark.parametrize("mutate, status", [
+    (lambda s: s.obs_cam.__setitem__(0, 99), 1),                       # camera index out of range
+    (lambda s: s.obs_pt.__setitem__(0, -1), 1),                        # point index out of range
+    (lambda s: s.obs_uv.__setitem__((1, 0), np.nan), 5),               # non-finite observation
+    (lambda s: s.cameras.__setitem__((0, 6), np.inf), 5),              # non-finite camera
+    (lambda s: s.clusters.__setitem__(1, 3), 1),                       # cluster ids 0..l-1 with a gap
+])
+def test_invalid_problems_are_rejected_on_the_host(mutate, status):
+    s = base()
+    s.clusters = np.zeros(s.m, np.int32)
+    s.clusters[1] = 1
+    mutate(s)
+    with pytest.raises(stba.StbaError) as e:
+        stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters)
+    assert e.value.status == status
+
+
+def test_point_with_one_observation_and_duplicates_are_rejected():
+    s = base()
+    # drop all but one observation of point 0
+    keep = np.ones(s.q, bool)
+    idx = np.flatnonzero(s.obs_pt == 0)
+    keep[idx[1:]] = False
+    with pytest.raises(stba.StbaError) as e:
+        stba.stba_create(s.cameras, s.points, s.obs_cam[keep], s.obs_pt[keep], s.obs_uv[keep], s.clusters)
+    assert e.value.status == 1 and "fewer than 2" in str(e.value)
+    dup_c = np.concatenate([s.obs_cam, s.obs_cam[:1]])
+    dup_p = np.concatenate([s.obs_pt, s.obs_pt[:1]])
+    dup_uv = np.concatenate([s.obs_uv, s.obs_uv[:1]])
+    with pytest.raises(stba.StbaError) as e:
+        stba.stba_create(s.cameras, s.points, dup_c, dup_p, dup_uv, s.clusters)
+    assert "twice" in str(e.value)
+
+
+def test_invalid_options_are_rejected():
+    s = base()
+    with pytest.raises(stba.StbaError):
+        stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, lambda0=0.0)
+    with pytest.raises(stba.StbaError):
+        stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=7)
