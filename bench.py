@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the STBA LM iteration on one GB300 (or N replicas under torchrun).
+
+Workload: the unordered Internet-like scene -- 1000 cameras on a hemisphere of radius 20, 200k points in
+a 10^3 box, Zipf(2) tracks on [2, 50] (1.11M observations), 10 clusters of 100 cameras, mixed precision
+(FP32 Jacobians and Schur accumulation, FP32 factorisation with FP64 refinement, FP64 cost sums).
+A step is one full LM iteration (residuals and Jacobians, virtual points and correction, S' build,
+per-cluster factorisation and solve, point update, cost, accept / reject).  L2 is flushed between timed
+steps (a 512 MB write outside the timed events).
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "STBA LM iter/s and obs/s vs full-RCS LM on 1 GB300 at equal final RMSE"
+CONFIG = "c1_internet"
+WORKLOAD = ("c1_internet: 1000 cameras (hemisphere r=20), 200k points (10^3 box), Zipf(2) tracks on [2,50], "
+            "10 clusters of 100 cameras, mixed precision")
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline leg)
+# ----------------------------------------------------------------------------------------------------------
+ORACLE_CHILD = r"""
+import json, os, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import scenes
+from oracle import camera, stba
+s = scenes.make_config(sys.argv[2])
+iters = int(sys.argv[3])
+F = camera.cost(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv)
+t = time.perf_counter()
+c, p, lam, F, hist = stba.solve(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, iters)
+dt = time.perf_counter() - t
+print(json.dumps({"seconds": dt, "iters": iters, "q": int(s.q), "F": F}))
+"""
+
+
+def run_oracle(config, iters, threads=1):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    env.pop("CUDA_VISIBLE_DEVICES", None)
+    r = subprocess.run([sys.executable, "-c", ORACLE_CHILD, ROOT, config, str(iters)], capture_output=True,
+                       text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    secs = []
+    q = None
+    # each step is one oracle LM iteration of the full workload (tens of seconds); stop adding steps once
+    # the run would exceed about three minutes
+    t_start = time.perf_counter()
+    for i in range(args.steps):
+        out = run_oracle(CONFIG, 1)
+        secs.append(out["seconds"])
+        q = out["q"]
+        el = time.perf_counter() - t_start
+        if el + el / (i + 1) > 180.0:
+            break
+    steps = len(secs)
+    tot = sum(secs)
+    v = steps / tot
+    sample = (f"{steps} step(s), each one STBA LM iteration of the full workload "
+              "(FP64 SciPy-sparse oracle, 1 thread)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2_flush": False},
+        "obs_per_s": v * q,
+        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=CONFIG)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the full-RCS LM comparison")
+    ap.add_argument("--compare-iters", type=int, default=20)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    import scenes
+    from paper_2008_00446_gb300 import stba
+
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    s = scenes.make_config(args.config)
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                           precision=stba.STBA_MIXED, stream=stream)
+    info0 = stba.stba_problem_info(ctx)
+    for _ in range(max(args.warmup, 3)):
+        stba.stba_lm_iteration(ctx, want_info=False)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_tot = np.zeros(5)
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        stba.stba_lm_iteration(ctx, want_info=False)
+        ev[i][1].record(stream)
+        stage_tot += np.array(stba.stba_stage_times(ctx))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([tot_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    lam, F_end, it_end = stba.stba_get_state(ctx)
+    value = world * args.steps / (tot_ms / 1e3)
+    stage_ms = stage_tot / args.steps
+
+    # roofline of the dominant stage (stage averages over the timed steps)
+    q, n, m = s.q, s.n, s.m
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    names = ["linearise", "s_build", "factorisation", "cluster_solve", "point_update_cost"]
+    dom = int(np.argmax(stage_ms))
+    s_lower = info0["s_lower_elems"]
+    # algorithmic bytes per stage (inputs read once, outputs written once)
+    bytes_stage = {
+        0: q * (8 + 4 + 4) + n * 24 + m * 72 + info0["nv"] * 9 * 4 * 2 + n * 9 * 4,
+        1: q * (8 + 4 + 4) + n * 24 + m * 72 + info0["nv"] * 9 * 4 + s_lower * 4 + m * 9 * 4 * 2,
+        3: s_lower * 4 * (1 + 2 * 1) + m * 9 * 8,
+        4: q * (8 + 4 + 4) * 2 + n * 24 * 2 + m * 72 * 2 + n * 9 * 4 + n * 24,
+    }
+    if dom == 2:
+        achieved = info0["factor_flops"] / (stage_ms[2] / 1e3) / 1e12
+        roofline = {"bound": "alu", "stage": names[2], "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (FP32 SIMT)"}
+    else:
+        achieved = bytes_stage[dom] / (stage_ms[dom] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "stage": names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roofline["stage_ms"] = {nm: float(v) for nm, v in zip(names, stage_ms)}
+
+    # end to end through the C ABI with host buffers: parameters in, one iteration, parameters out
+    cams_h = torch.from_numpy(s.cameras.copy()).pin_memory()
+    pts_h = torch.from_numpy(s.points.copy()).pin_memory()
+    cams_o = torch.empty_like(cams_h).pin_memory()
+    pts_o = torch.empty_like(pts_h).pin_memory()
+    stba.stba_get_params(ctx, cams_h, pts_h)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        stba.stba_set_params(ctx, cams_h, pts_h)
+        stba.stba_lm_iteration(ctx, want_info=False)
+        stba.stba_get_params(ctx, cams_o, pts_o)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    nbytes = 8 * (cams_h.numel() + pts_h.numel())
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cameras": m, "points": n, "observations": q, "clusters": int(info0["l"]),
+                   "virtual_points": int(info0["nv"]), "l2_flush": True, "parallelism": f"replicas{world}"},
+        "obs_per_s": value * q,
+        "roofline": roofline,
+        "e2e": {"value": world / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "gpu_launches": int(info0["launches_per_iter"]) * args.steps,
+        "clocks": clocks,
+        "final": {"rmse_px": float(np.sqrt(F_end / (2 * q))), "lambda": lam, "iterations": it_end},
+    }
+
+    if rank == 0 and world == 1 and not args.no_compare:
+        out["full_rcs"] = compare_full_rcs(s, stba, stream, args.compare_iters, torch)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = run_oracle(args.config, 1)
+        v = 1.0 / t["seconds"]
+        out["cpu_baseline"] = {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
+                               "sample": "one STBA LM iteration of the full workload (FP64 SciPy-sparse oracle, 1 thread)"}
+    stba.stba_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def compare_full_rcs(s, stba, stream, iters, torch):
+    """Full-RCS LM on the same GPU (all cameras in one cluster: STBA with l = 1 is exactly LM) against
+    STBA with a fresh azimuth-wedge clustering each iteration, both from the same start: per-iteration
+    time, final RMSE, and the time STBA needs to reach 1.001 x the full-RCS final RMSE."""
+    import numpy as np
+
+    import scenes
+    res = {}
+    one = np.zeros(s.m, np.int32)
+    for name, clusters in (("full_rcs_lm", None), ("stba_resampled", "seq")):
+        ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv,
+                               one if clusters is None else s.clusters, precision=stba.STBA_MIXED, stream=stream)
+        seq = scenes.cluster_sequence(s, iters, seed=s.meta["seed"] + 1) if clusters == "seq" else None
+        rm, ts = [], []
+        for t in range(iters):
+            if seq is not None:
+                stba.stba_set_clusters(ctx, seq[t])
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            info = stba.stba_lm_iteration(ctx, want_info=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+            _, F, _ = stba.stba_get_state(ctx)
+            rm.append(float(np.sqrt(F / (2 * s.q))))
+        res[name] = {"ms_per_iter": float(np.median(ts)), "rmse": rm, "cum_ms": list(np.cumsum(ts))}
+        stba.stba_destroy(ctx)
+    target = 1.001 * res["full_rcs_lm"]["rmse"][-1]
+    st = res["stba_resampled"]
+    hit = [i for i, r in enumerate(st["rmse"]) if r <= target]
+    out = {"iters": iters, "full_rcs_ms_per_iter": res["full_rcs_lm"]["ms_per_iter"],
+           "stba_ms_per_iter": st["ms_per_iter"], "full_rcs_final_rmse": res["full_rcs_lm"]["rmse"][-1],
+           "stba_final_rmse": st["rmse"][-1], "rmse_target": target,
+           "full_rcs_time_ms": res["full_rcs_lm"]["cum_ms"][-1],
+           "stba_time_to_target_ms": (st["cum_ms"][hit[0]] if hit else None),
+           "stba_iters_to_target": (hit[0] + 1 if hit else None)}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -125,19 +125,22 @@ stba_status stba_set_state(stba_ctx* ctx, double lambda, double F, int64_t itera
 /* The candidate step of the last iteration, accepted or not: dc [m][9], dp [n][3] (FP64). */
 stba_status stba_last_step(stba_ctx* ctx, double* dc, double* dp);
 
-/* Sizes: out[0..7] = m, n, q, l (clusters), nv (virtual points), max cluster dimension 9 n_k,
- * device bytes held, number of S' build work items. */
-stba_status stba_problem_info(stba_ctx* ctx, int64_t* out8);
+/* Sizes, first n of: m, n, q, l (clusters), nv (virtual points), max cluster dimension 9 n_k, device
+ * bytes held, S' pair-pass work items, kernel launches per LM iteration, camera-pair instances
+ * (observation pairs of one virtual point), factorisation flops sum_k (9 n_k)^3 / 3, and elements of the
+ * lower triangles of all S'_k. */
+stba_status stba_problem_info(stba_ctx* ctx, int64_t* out, int32_t n);
 
 /* The cluster system S'_k Delta c_k = b_k (Eq. 13) of the last iteration, in the order of the cluster's
  * cameras by increasing camera index: S [dim][dim] (FP64, both triangles filled from the lower one) and
  * b [dim]; dim = 9 n_k is written to *dim.  S or b may be NULL (then only dim is returned). */
 stba_status stba_get_cluster_system(stba_ctx* ctx, int32_t k, double* S, double* b, int64_t* dim);
 
-/* Stage timing: with on != 0, each subsequent iteration records CUDA events around its stages on the
- * context stream.  stba_stage_times copies the times (ms) of the last iteration into ms[0..n-1]
- * (stages: 0 linearise+virtual points, 1 S' build, 2 factorisation, 3 cluster solves, 4 point update
- * + cost + control) and returns the number of stages in *count. */
+/* Stage timing: every iteration records CUDA events around its stages on the context stream (inside
+ * the captured graph as event nodes).  stba_stage_times waits for the last iteration and copies its
+ * stage times (ms) into ms[0..n-1] (stages: 0 linearisation + virtual points, 1 S' build,
+ * 2 factorisation, 3 cluster solves with refinement, 4 point update + cost + control); *count gets the
+ * number of stages.  stba_set_timing is kept for compatibility and has no effect. */
 stba_status stba_set_timing(stba_ctx* ctx, int32_t on);
 stba_status stba_stage_times(stba_ctx* ctx, float* ms, int32_t n, int32_t* count);
 

@@ -77,12 +77,16 @@ struct stba_ctx {
   // scratch (real = float in mixed mode, double in FP64 mode)
   void *vp_acc = nullptr, *vp_info = nullptr, *pt_info = nullptr, *S = nullptr, *b = nullptr, *vgrad = nullptr,
        *t_acc = nullptr;
-  double *dc = nullptr, *dp = nullptr, *partial = nullptr;
+  double *dc = nullptr, *dp = nullptr, *partial = nullptr, *cam_rt = nullptr;
+  void *res_cur = nullptr, *res_cand = nullptr;   // residuals at x and at x + dx (working precision)
   DevState* st = nullptr;
 
   // graph / timing
   cudaGraphExec_t graph = nullptr;
+  bool capturing = false;
   bool timing = false;
+  int launches_per_iter = 0;
+  double factor_flops = 0;
   cudaEvent_t ev[NSTAGES + 1] = {};
   float stage_ms[NSTAGES] = {};
   bool have_stage_times = false;
@@ -179,6 +183,8 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.cluster_n = c->cluster_n;
   P.S_off = c->S_off;
   P.v_off = c->v_off;
+  P.res_f = c->mixed ? (const float*)c->res_cur : nullptr;
+  P.res_d = c->mixed ? nullptr : (const double*)c->res_cur;
   return P;
 }
 
@@ -188,8 +194,8 @@ Scratch<real> scratch(const stba_ctx* c) {
   W.vp_acc = (real*)c->vp_acc;
   W.vp_info = (real*)c->vp_info;
   W.pt_info = (real*)c->pt_info;
-  W.S = (real*)c->S;
-  W.b = (real*)c->b;
+  W.S = (double*)c->S;
+  W.b = (double*)c->b;
   W.vgrad = (real*)c->vgrad;
   W.t_acc = (real*)c->t_acc;
   W.dc = c->dc;
@@ -308,58 +314,25 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     std::vector<int> f(cam_obs_off.begin(), cam_obs_off.end() - 1);
     for (int o = 0; o < q; ++o) cam_obs[f[s_cam[o]]++] = o;
   }
-  // pair instances of the pair pass: tiles (k, gA >= gB) over groups of TC cameras; inside a virtual point
-  // the observations are ordered by camera, so a later observation has the larger local camera index
-  const int TC = pair_tile_cameras(c->mixed);
-  const int TD = 9 * TC;
-  std::vector<int> tile_base(l + 1, 0), ngroups(l);
-  for (int k = 0; k < l; ++k) {
-    ngroups[k] = (cnt[k] + TC - 1) / TC;
-    tile_base[k + 1] = tile_base[k] + ngroups[k] * (ngroups[k] + 1) / 2;
+  // camera-pair instances of the pair pass, sorted by (cluster, la, lb): inside a virtual point the
+  // observations are ordered by camera, so a later observation has the larger local camera index
+  int64_t npairs = 0;
+  for (int v = 0; v < nv; ++v) {
+    const int64_t len = vp_off[v + 1] - vp_off[v];
+    npairs += len * (len - 1) / 2;
   }
-  const int nt = tile_base[l];
-  std::vector<int> tile_cluster(nt), tile_ga(nt), tile_gb(nt);
-  for (int k = 0; k < l; ++k)
-    for (int ga = 0; ga < ngroups[k]; ++ga)
-      for (int gb = 0; gb <= ga; ++gb) {
-        const int t = tile_base[k] + ga * (ga + 1) / 2 + gb;
-        tile_cluster[t] = k;
-        tile_ga[t] = ga;
-        tile_gb[t] = gb;
-      }
-  auto tile_of = [&](int oa, int ob) {
-    const int k = cl[s_cam[oa]];
-    const int ga = cam_local[s_cam[oa]] / TC, gb = cam_local[s_cam[ob]] / TC;
-    return tile_base[k] + ga * (ga + 1) / 2 + gb;
-  };
-  std::vector<int64_t> tile_cnt(nt + 1, 0);
+  if (npairs > INT32_MAX) return fail(c, STBA_ERR_INVALID_ARG, "more than 2^31 camera-pair instances");
+  std::vector<int4> pairs;
+  pairs.reserve(npairs);
   for (int v = 0; v < nv; ++v)
     for (int a2 = vp_off[v] + 1; a2 < vp_off[v + 1]; ++a2)
-      for (int b2 = vp_off[v]; b2 < a2; ++b2) tile_cnt[tile_of(a2, b2) + 1]++;
-  for (int t = 0; t < nt; ++t) tile_cnt[t + 1] += tile_cnt[t];
-  if (tile_cnt[nt] > INT32_MAX) return fail(c, STBA_ERR_INVALID_ARG, "more than 2^31 camera-pair instances");
-  std::vector<int4> pairs(tile_cnt[nt]);
-  {
-    std::vector<int64_t> tf(tile_cnt.begin(), tile_cnt.end() - 1);
-    for (int v = 0; v < nv; ++v)
-      for (int a2 = vp_off[v] + 1; a2 < vp_off[v + 1]; ++a2)
-        for (int b2 = vp_off[v]; b2 < a2; ++b2) {
-          const int t = tile_of(a2, b2);
-          const int la = cam_local[s_cam[a2]] - tile_ga[t] * TC, lb = cam_local[s_cam[b2]] - tile_gb[t] * TC;
-          pairs[tf[t]++] = make_int4(a2, b2, 9 * la * TD + 9 * lb, 0);
-        }
-  }
-  c->n_pairs = tile_cnt[nt];
-  // chunks of at most `chunk` pairs so that the work items cover the GPU several times over
-  const int64_t chunk = std::max<int64_t>(512, tile_cnt[nt] / (152 * 4) + 1);
-  std::vector<int> item_tile, item_lo, item_hi;
-  for (int t = 0; t < nt; ++t)
-    for (int64_t lo = tile_cnt[t]; lo < tile_cnt[t + 1]; lo += chunk) {
-      item_tile.push_back(t);
-      item_lo.push_back((int)lo);
-      item_hi.push_back((int)std::min<int64_t>(lo + chunk, tile_cnt[t + 1]));
-    }
-  c->build_items = (int)item_tile.size();
+      for (int b2 = vp_off[v]; b2 < a2; ++b2)
+        pairs.push_back(make_int4(a2, b2, cl[s_cam[a2]], (cam_local[s_cam[a2]] << 16) | cam_local[s_cam[b2]]));
+  std::sort(pairs.begin(), pairs.end(), [](const int4& x, const int4& y) {
+    return x.z != y.z ? x.z < y.z : (x.w != y.w ? x.w < y.w : x.x < y.x);
+  });
+  c->n_pairs = npairs;
+  c->build_items = (int)((npairs + 63) / 64);
 
   // Cholesky step plan
   std::vector<int2> panel, update;
@@ -378,9 +351,23 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   }
   c->h_panel_off[max_nt] = (int)panel.size();
   c->h_update_off[max_nt] = (int)update.size();
-  std::vector<int2> res_items;
+  std::vector<int2> res_items, diag_items;
   for (int k = 0; k < l; ++k)
     for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
+  for (int k = 0; k < l; ++k)
+    for (int t = 0; t < c->h_np[k] / TF; ++t) diag_items.push_back(make_int2(k, t));
+  {
+    int factor_launches = 3;
+    for (int kt = 0; kt < max_nt; ++kt)
+      factor_launches += (c->h_panel_off[kt + 1] > c->h_panel_off[kt]) + (c->h_update_off[kt + 1] > c->h_update_off[kt]);
+    const int build_launches = 1 + (npairs > 0 ? 1 : 0);
+    const int solve_launches = 2 + c->set.refine_steps * (2 + (res_items.empty() ? 0 : 1));
+    // iter_begin, vp_reduce, vp_finalize | build | factor | solve, count | rhs, update, cam_rt, cost, finalize,
+    // apply
+    c->launches_per_iter = 3 + build_launches + factor_launches + solve_launches + 1 + 6;
+    c->factor_flops = 0;
+    for (int k = 0; k < l; ++k) c->factor_flops += std::pow((double)c->h_nk[k], 3) / 3.0;
+  }
 
   // upload
   stba_status s;
@@ -406,27 +393,21 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(c->cluster_n, c->h_nk);
   UP(c->S_off, c->h_S_off);
   UP(c->v_off, c->h_v_off);
-  int *d_tile_cluster, *d_tile_ga, *d_tile_gb, *d_item_tile, *d_item_lo, *d_item_hi, *d_cam_obs_off, *d_cam_obs;
+  int *d_cam_obs_off, *d_cam_obs;
   int4* d_pairs;
-  UP(d_tile_cluster, tile_cluster);
-  UP(d_tile_ga, tile_ga);
-  UP(d_tile_gb, tile_gb);
-  UP(d_item_tile, item_tile);
-  UP(d_item_lo, item_lo);
-  UP(d_item_hi, item_hi);
   UP(d_pairs, pairs);
   UP(d_cam_obs_off, cam_obs_off);
   UP(d_cam_obs, cam_obs);
-  int2 *d_panel, *d_update, *d_res;
+  int2 *d_panel, *d_update, *d_res, *d_diag;
   UP(d_panel, panel);
   UP(d_update, update);
   UP(d_res, res_items);
+  UP(d_diag, diag_items);
 #undef UP
-  c->plist = PairLists{d_tile_cluster, d_tile_ga, d_tile_gb, d_item_tile, d_item_lo, d_item_hi, d_pairs,
-                       (int)item_tile.size()};
+  c->plist = PairLists{d_pairs, (int)npairs};
   c->clist = CamLists{d_cam_obs_off, d_cam_obs};
-  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), max_nt, c->h_panel_off.data(),
-                      c->h_update_off.data(), c->max_np};
+  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
+                      c->h_panel_off.data(), c->h_update_off.data(), c->max_np};
 
   const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
   auto ralloc = [&](void** p, size_t count) -> stba_status {
@@ -438,8 +419,13 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   if ((s = ralloc(&c->vp_acc, 9 * (size_t)nv)) != STBA_OK) return s;
   if ((s = ralloc(&c->vp_info, 9 * (size_t)nv)) != STBA_OK) return s;
   if ((s = ralloc(&c->pt_info, 9 * (size_t)n)) != STBA_OK) return s;
-  if ((s = ralloc(&c->S, (size_t)c->S_total)) != STBA_OK) return s;
-  if ((s = ralloc(&c->b, (size_t)c->v_total)) != STBA_OK) return s;
+  {
+    double *S_, *b_;
+    if ((s = dalloc(c, &S_, (size_t)c->S_total, true)) != STBA_OK) return s;
+    if ((s = dalloc(c, &b_, (size_t)c->v_total, true)) != STBA_OK) return s;
+    c->S = S_;
+    c->b = b_;
+  }
   if ((s = ralloc(&c->vgrad, 9 * (size_t)m)) != STBA_OK) return s;
   if ((s = ralloc(&c->t_acc, 3 * (size_t)n)) != STBA_OK) return s;
   if ((s = ralloc(&c->Gbuf, 32 * (size_t)q)) != STBA_OK) return s;
@@ -459,42 +445,46 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
 }
 
 // ------------------------------------------------------------------------------------------------------
+void record_stage(stba_ctx* c, int i) {
+  // inside a capture the record becomes an event node of the graph, so every replay times its stages
+  cudaEventRecordWithFlags(c->ev[i], c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+}
+
 template <typename real>
 void enqueue_iteration(stba_ctx* c) {
   const DevProblem P = dev_problem(c);
   const Scratch<real> W = scratch<real>(c);
   cudaStream_t s = c->stream;
-  const bool tm = c->timing;
   const size_t rs = sizeof(real);
-  if (tm) cudaEventRecord(c->ev[0], s);
+  record_stage(c, 0);
   // stage 0: linearisation and virtual points
   launch_iter_begin<real>(c->st, c->set, s);
   cudaMemsetAsync(c->vp_acc, 0, 9 * (size_t)c->nv * rs, s);
-  cudaMemsetAsync(c->S, 0, (size_t)c->S_total * rs, s);
-  cudaMemsetAsync(c->b, 0, (size_t)c->v_total * rs, s);
+  cudaMemsetAsync(c->S, 0, (size_t)c->S_total * sizeof(double), s);
+  cudaMemsetAsync(c->b, 0, (size_t)c->v_total * sizeof(double), s);
   cudaMemsetAsync(c->vgrad, 0, 9 * (size_t)c->m * rs, s);
   cudaMemsetAsync(c->t_acc, 0, 3 * (size_t)c->n * rs, s);
   cudaMemsetAsync(c->fail_flags, 0, (size_t)c->l * sizeof(int), s);
   launch_vp_reduce<real>(P, W, s);
   launch_vp_finalize<real>(P, W, c->st, s);
-  if (tm) cudaEventRecord(c->ev[1], s);
+  record_stage(c, 1);
   // stage 1: S' and b'
   launch_rcs_build<real>(P, W, c->clist, c->plist, (real*)c->Gbuf, c->st, s);
-  if (tm) cudaEventRecord(c->ev[2], s);
+  record_stage(c, 2);
   // stage 2: factorisation (FP32 factor in mixed mode, FP64 factor in FP64 mode)
-  launch_factor<real, real>(P, W.S, c->fbuf, c->cplan, s);
-  if (tm) cudaEventRecord(c->ev[3], s);
+  launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
+  record_stage(c, 3);
   // stage 3: cluster solves with FP64 refinement
-  launch_solve<real, real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, s);
+  launch_solve<real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, s);
   launch_count_failures(c->fail_flags, c->l, c->st, s);
-  if (tm) cudaEventRecord(c->ev[4], s);
+  record_stage(c, 4);
   // stage 4: points, cost, control
   launch_point_rhs<real>(P, W, s);
   launch_point_update<real>(P, W, s);
-  launch_cost<real>(P, c->dc, c->dp, c->partial, c->st, s);
+  launch_cost<real>(P, c->dc, c->dp, c->cam_rt, c->partial, c->st, (real*)c->res_cand, s);
   launch_finalize<real>(P, W, c->st, c->set, 1, s);
-  launch_apply(P, c->dc, c->dp, c->cams, c->pts, c->st, s);
-  if (tm) cudaEventRecord(c->ev[5], s);
+  launch_apply<real>(P, c->dc, c->dp, c->cams, c->pts, (const real*)c->res_cand, (real*)c->res_cur, c->st, s);
+  record_stage(c, 5);
 }
 
 template <typename real>
@@ -502,7 +492,7 @@ void enqueue_cost(stba_ctx* c) {
   const DevProblem P = dev_problem(c);
   const Scratch<real> W = scratch<real>(c);
   launch_iter_begin<real>(c->st, c->set, c->stream);
-  launch_cost<real>(P, nullptr, nullptr, c->partial, c->st, c->stream);
+  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, c->partial, c->st, (real*)c->res_cur, c->stream);
   launch_finalize<real>(P, W, c->st, c->set, 0, c->stream);
 }
 
@@ -523,13 +513,13 @@ stba_status run_cost(stba_ctx* c, double* F) {
 }
 
 stba_status run_iteration(stba_ctx* c) {
-  if (c->timing || !c->opt.use_graph) {
+  if (!c->opt.use_graph) {
     if (c->mixed)
       enqueue_iteration<float>(c);
     else
       enqueue_iteration<double>(c);
     CK(cudaGetLastError());
-    c->have_stage_times = c->timing;
+    c->have_stage_times = true;
     return STBA_OK;
   }
   if (!c->graph) {
@@ -537,10 +527,12 @@ stba_status run_iteration(stba_ctx* c) {
     cudaStream_t user = c->stream;
     c->stream = c->cap_stream;
     CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
     if (c->mixed)
       enqueue_iteration<float>(c);
     else
       enqueue_iteration<double>(c);
+    c->capturing = false;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     c->stream = user;
@@ -553,7 +545,7 @@ stba_status run_iteration(stba_ctx* c) {
     }
   }
   CK(cudaGraphLaunch(c->graph, c->stream));
-  c->have_stage_times = false;
+  c->have_stage_times = true;
   return STBA_OK;
 }
 
@@ -562,8 +554,6 @@ stba_status read_info(stba_ctx* c, stba_iter_info* info) {
   CK(cudaMemcpyAsync(&h, c->st, sizeof h, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (info) *info = h.info;
-  if (c->timing && c->have_stage_times)
-    for (int i = 0; i < NSTAGES; ++i) cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]);
   if (h.lambda > 1e16) return fail(c, STBA_ERR_STATE, "lambda exceeded 1e16");
   return STBA_OK;
 }
@@ -726,6 +716,15 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   if ((s = dalloc(c, &c->dc, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->dp, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->partial, 3 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->cam_rt, 15 * (size_t)m, false)) != STBA_OK) return bail(s);
+  {
+    char *r1, *r2;
+    const size_t rsz = 2 * (size_t)q * (c->mixed ? sizeof(float) : sizeof(double));
+    if ((s = dalloc(c, &r1, rsz, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &r2, rsz, false)) != STBA_OK) return bail(s);
+    c->res_cur = r1;
+    c->res_cand = r2;
+  }
   if ((s = dalloc(c, &c->st, 1, false)) != STBA_OK) return bail(s);
   {
     cudaError_t e1 = cudaMemcpyAsync(c->cams, h_cams.data(), h_cams.size() * 8, cudaMemcpyHostToDevice, c->stream);
@@ -749,14 +748,17 @@ stba_status stba_set_clusters(stba_ctx* c, const int32_t* cluster_assignment) {
   stba_status s;
   if ((s = copy_in(c, h.data(), cluster_assignment, (size_t)c->m * 4)) != STBA_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
-  return set_clusters_host(c, h);
+  if ((s = set_clusters_host(c, h)) != STBA_OK) return s;
+  // the stored residuals follow the observation order, which depends on the clusters: recompute them
+  double F;
+  return stba_cost(c, &F);
 }
 
 stba_status stba_lm_iteration(stba_ctx* c, stba_iter_info* info) {
   if (!c) return STBA_ERR_INVALID_ARG;
   stba_status s = run_iteration(c);
   if (s != STBA_OK) return s;
-  if (info || c->timing) return read_info(c, info);
+  if (info) return read_info(c, info);
   return STBA_OK;
 }
 
@@ -839,18 +841,18 @@ stba_status stba_last_step(stba_ctx* c, double* dc, double* dp) {
   return STBA_OK;
 }
 
-stba_status stba_problem_info(stba_ctx* c, int64_t* out8) {
-  if (!c || !out8) return STBA_ERR_INVALID_ARG;
+stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {
+  if (!c || !out || n < 0) return STBA_ERR_INVALID_ARG;
   int maxn = 0;
-  for (int v : c->h_nk) maxn = std::max(maxn, v);
-  out8[0] = c->m;
-  out8[1] = c->n;
-  out8[2] = c->q;
-  out8[3] = c->l;
-  out8[4] = c->nv;
-  out8[5] = maxn;
-  out8[6] = (int64_t)(c->bytes_base + c->bytes_cl);
-  out8[7] = c->build_items;
+  double s_elems = 0;
+  for (int v : c->h_nk) {
+    maxn = std::max(maxn, v);
+    s_elems += 0.5 * (double)v * (v + 1);
+  }
+  const int64_t vals[12] = {c->m, c->n, c->q, c->l, c->nv, maxn, (int64_t)(c->bytes_base + c->bytes_cl),
+                            c->build_items, c->launches_per_iter, c->n_pairs, (int64_t)c->factor_flops,
+                            (int64_t)s_elems};
+  for (int i = 0; i < n && i < 12; ++i) out[i] = vals[i];
   return STBA_OK;
 }
 
@@ -859,14 +861,12 @@ stba_status stba_get_cluster_system(stba_ctx* c, int32_t k, double* S, double* b
   const int nk = c->h_nk[k], np = c->h_np[k];
   if (dim) *dim = nk;
   if (!S && !b) return STBA_OK;
-  const size_t rs = c->mixed ? 4 : 8;
+  const size_t rs = 8;
   std::vector<char> raw((size_t)np * np * rs), rawb((size_t)np * rs);
   CK(cudaMemcpyAsync(raw.data(), (char*)c->S + (size_t)c->h_S_off[k] * rs, raw.size(), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(rawb.data(), (char*)c->b + (size_t)c->h_v_off[k] * rs, rawb.size(), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  auto at = [&](const std::vector<char>& v, size_t i) -> double {
-    return c->mixed ? (double)((const float*)v.data())[i] : ((const double*)v.data())[i];
-  };
+  auto at = [&](const std::vector<char>& v, size_t i) -> double { return ((const double*)v.data())[i]; };
   if (S) {
     std::vector<double> full((size_t)nk * nk);
     for (int r = 0; r < nk; ++r)
@@ -902,8 +902,12 @@ stba_status stba_set_timing(stba_ctx* c, int32_t on) {
 stba_status stba_stage_times(stba_ctx* c, float* ms, int32_t n, int32_t* count) {
   if (!c) return STBA_ERR_INVALID_ARG;
   if (count) *count = NSTAGES;
-  if (ms)
-    for (int i = 0; i < n && i < NSTAGES; ++i) ms[i] = c->have_stage_times ? c->stage_ms[i] : -1.0f;
+  if (!ms) return STBA_OK;
+  if (c->have_stage_times) {
+    CK(cudaEventSynchronize(c->ev[NSTAGES]));
+    for (int i = 0; i < NSTAGES; ++i) CK(cudaEventElapsedTime(&c->stage_ms[i], c->ev[i], c->ev[i + 1]));
+  }
+  for (int i = 0; i < n && i < NSTAGES; ++i) ms[i] = c->have_stage_times ? c->stage_ms[i] : -1.0f;
   return STBA_OK;
 }
 

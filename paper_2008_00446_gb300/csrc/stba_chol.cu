@@ -60,100 +60,196 @@ __global__ void k_scaled_copy(DevProblem P, const Sreal* S, const double* scale,
   }
 }
 
-// Unblocked LL^T of the diagonal tile in shared memory (lower triangle).
+// Register-blocked tile kernels.  256 threads form a 16 x 16 grid; thread (bi, bj) holds the R x R block
+// (R = T / 16) of rows bi R .. and columns bj R .. in registers.  Column j is broadcast through a double
+// buffer in shared memory, so each of the T steps costs one barrier.
+//
+// factor_tile_regs: right-looking LL^T of the diagonal tile with the unscaled column,
+// a_rc -= a_rj a_cj / a_jj; the pivots a_jj are kept and the columns scaled at the end.
 template <typename F, int T>
-__device__ void factor_diag_tile(F (*D)[T + 1], int row0, int nk, int* fail, int* boosted) {
+__device__ __forceinline__ void factor_tile_regs(F (&a)[T / 16][T / 16], int bi, int bj, F* colbuf, F* piv, int row0, int nk,
+                                 int* fail, int* boosted) {
+  constexpr int R = T / 16;
   for (int j = 0; j < T; ++j) {
-    if (threadIdx.x == 0) {
-      F d = D[j][j];
-      if (row0 + j >= nk) {
-        d = F(1);
-      } else if (!isfinite(d)) {
-        *fail = 1;
-        d = F(1);
-      } else if (sizeof(F) == 8) {
-        if (!(d > F(0))) {
-          *fail = 1;
-          d = F(1);
-        }
-      } else if (d < F(1.0 / 1048576)) {
-        atomicAdd(boosted, 1);
-        d = F(1.0 / 4096);
+    F* col = colbuf + (j & 1) * T;
+    if (bj == j / R) {
+#pragma unroll
+      for (int ii = 0; ii < R; ++ii) {
+        const int jr = j % R;
+        F v = a[ii][0];
+#pragma unroll
+        for (int jj = 1; jj < R; ++jj) v = (jj == jr) ? a[ii][jj] : v;
+        col[bi * R + ii] = v;
       }
-      D[j][j] = sqrt(d);
     }
     __syncthreads();
-    const F djj = D[j][j];
-    for (int r = j + 1 + threadIdx.x; r < T; r += blockDim.x) D[r][j] /= djj;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-      const int r = idx / T, c = idx - (idx / T) * T;
-      if (c > j && r >= c) D[r][c] -= D[r][j] * D[c][j];
+    F d = col[j];
+    bool bad = false, boost = false;
+    if (row0 + j >= nk) {
+      d = F(1);
+    } else if (!isfinite(d)) {
+      bad = true;
+      d = F(1);
+    } else if (sizeof(F) == 8) {
+      if (!(d > F(0))) {
+        bad = true;
+        d = F(1);
+      }
+    } else if (d < F(1.0 / 1048576)) {
+      boost = true;
+      d = F(1.0 / 4096);
+    }
+    if (threadIdx.x == 0) {
+      piv[j] = d;
+      if (bad) *fail = 1;
+      if (boost && boosted) atomicAdd(boosted, 1);
+    }
+    const F inv = F(1) / d;
+    if (bi >= bj) {
+      F cr[R], cc[R];
+#pragma unroll
+      for (int ii = 0; ii < R; ++ii) cr[ii] = col[bi * R + ii] * inv;
+#pragma unroll
+      for (int jj = 0; jj < R; ++jj) cc[jj] = col[bj * R + jj];
+#pragma unroll
+      for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < R; ++jj) {
+          const int r = bi * R + ii, cl = bj * R + jj;
+          if (cl > j && r >= cl) a[ii][jj] -= cr[ii] * cc[jj];
+        }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < R; ++jj) {
+      const int r = bi * R + ii, cl = bj * R + jj;
+      a[ii][jj] = (r > cl) ? a[ii][jj] / sqrt(piv[cl]) : ((r == cl) ? sqrt(piv[cl]) : F(0));
+    }
+}
+
+// trsm_tile_regs: X L^T = A for a full tile X (registers), L lower triangular in shared memory; the
+// columns of X are finished left to right and each finished column updates the ones to its right.
+template <typename F, int T>
+__device__ __forceinline__ void trsm_tile_regs(F (&x)[T / 16][T / 16], int bi, int bj, const F (*Ls)[T + 1], F* colbuf) {
+  constexpr int R = T / 16;
+  for (int c = 0; c < T; ++c) {
+    F* col = colbuf + (c & 1) * T;
+    if (bj == c / R) {
+      const F inv = F(1) / Ls[c][c];
+      const int cr_ = c % R;
+#pragma unroll
+      for (int ii = 0; ii < R; ++ii) {
+        F v = F(0);
+#pragma unroll
+        for (int jj = 0; jj < R; ++jj) {
+          const F nv = x[ii][jj] * inv;
+          x[ii][jj] = (jj == cr_) ? nv : x[ii][jj];
+          v = (jj == cr_) ? nv : v;
+        }
+        col[bi * R + ii] = v;
+      }
     }
     __syncthreads();
+    F cr[R], lc[R];
+#pragma unroll
+    for (int ii = 0; ii < R; ++ii) cr[ii] = col[bi * R + ii];
+#pragma unroll
+    for (int jj = 0; jj < R; ++jj) lc[jj] = Ls[bj * R + jj][c];
+#pragma unroll
+    for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < R; ++jj)
+        if (bj * R + jj > c) x[ii][jj] -= cr[ii] * lc[jj];
   }
 }
 
 template <typename F, int T>
-__global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P, const int2* items, int kt,
+__global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const int2* items, int kt,
                                                     int* fail_flags, int* boosted) {
-  __shared__ F D[T][T + 1];
-  __shared__ F X[T][T + 1];
+  constexpr int R = T / 16;
+  __shared__ F Ls[T][T + 1];
+  __shared__ F colbuf[2 * T];
+  __shared__ F piv[T];
   const int2 it = items[blockIdx.x];
   const int k = it.x, i = it.y;
   const int np = P.cluster_np[k], nk = P.cluster_n[k];
   F* A = L + P.S_off[k];
+  const int bi = threadIdx.x >> 4, bj = threadIdx.x & 15;
   const size_t base_kk = (size_t)(kt * T) * np + kt * T;
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int r = idx / T, c = idx - (idx / T) * T;
-    D[r][c] = (c <= r) ? A[base_kk + (size_t)r * np + c] : F(0);
+  F a[R][R];
+#pragma unroll
+  for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < R; ++jj) {
+      const int r = bi * R + ii, cl = bj * R + jj;
+      a[ii][jj] = (cl <= r) ? A[base_kk + (size_t)r * np + cl] : F(0);
+    }
+  F x[R][R];
+  const size_t base_ik = (size_t)(i * T) * np + kt * T;
+  if (i != kt) {
+#pragma unroll
+    for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < R; ++jj) x[ii][jj] = A[base_ik + (size_t)(bi * R + ii) * np + bj * R + jj];
   }
-  __syncthreads();
-  factor_diag_tile<F, T>(D, kt * T, nk, fail_flags + k, boosted);
+  factor_tile_regs<F, T>(a, bi, bj, colbuf, piv, kt * T, nk, fail_flags + k, (i == kt) ? boosted : nullptr);
   if (i == kt) {
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-      const int r = idx / T, c = idx - (idx / T) * T;
-      if (c <= r) A[base_kk + (size_t)r * np + c] = D[r][c];
-    }
-    // inverse of the lower-triangular tile, one column per thread: L Y = I
-    for (int c = threadIdx.x; c < T; c += blockDim.x) {
-      for (int r = 0; r < T; ++r) {
-        if (r < c) {
-          X[r][c] = F(0);
-          continue;
-        }
-        F s = (r == c) ? F(1) : F(0);
-        for (int j = c; j < r; ++j) s -= D[r][j] * X[j][c];
-        X[r][c] = s / D[r][r];
+#pragma unroll
+    for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < R; ++jj) {
+        const int r = bi * R + ii, cl = bj * R + jj;
+        if (cl <= r) A[base_kk + (size_t)r * np + cl] = a[ii][jj];
       }
-    }
-    __syncthreads();
-    F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-      const int r = idx / T, c = idx - (idx / T) * T;
-      Di[idx] = X[r][c];
-    }
     return;
   }
-  const size_t base_ik = (size_t)(i * T) * np + kt * T;
+#pragma unroll
+  for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < R; ++jj) Ls[bi * R + ii][bj * R + jj] = a[ii][jj];
+  __syncthreads();
+  trsm_tile_regs<F, T>(x, bi, bj, Ls, colbuf);
+#pragma unroll
+  for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+    for (int jj = 0; jj < R; ++jj) A[base_ik + (size_t)(bi * R + ii) * np + bj * R + jj] = x[ii][jj];
+}
+
+// Inverse of every diagonal tile of the factor (for the solves), one CTA per tile: L Y = I column by
+// column, four threads per column splitting each dot product.
+template <typename F, int T>
+__global__ void __launch_bounds__(256) k_diag_inverse(const F* L, F* Dinv, DevProblem P, const int2* items) {
+  __shared__ F D[T][T + 1];
+  __shared__ F Y[T][T + 1];
+  const int2 it = items[blockIdx.x];
+  const int k = it.x, t = it.y;
+  const int np = P.cluster_np[k];
+  const F* A = L + P.S_off[k];
+  const size_t base = (size_t)(t * T) * np + t * T;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int r = idx / T, c = idx - (idx / T) * T;
-    X[r][c] = A[base_ik + (size_t)r * np + c];
+    D[r][c] = (c <= r) ? A[base + (size_t)r * np + c] : F(0);
   }
   __syncthreads();
-  // X L_kk^T = A  ->  X[r][c] = (A[r][c] - sum_{j<c} X[r][j] L[c][j]) / L[c][c], rows independent
-  for (int r = threadIdx.x; r < T; r += blockDim.x) {
-    for (int c = 0; c < T; ++c) {
-      F s = X[r][c];
-      for (int j = 0; j < c; ++j) s -= X[r][j] * D[c][j];
-      X[r][c] = s / D[c][c];
+  const int cl = threadIdx.x >> 2, part = threadIdx.x & 3;
+  for (int cb = cl; cb < T; cb += blockDim.x >> 2) {
+    for (int r = 0; r < T; ++r) {
+      F s = F(0);
+      for (int j = cb + part; j < r; j += 4) s += D[r][j] * Y[j][cb];
+      s += __shfl_xor_sync(FULL_MASK, s, 1);
+      s += __shfl_xor_sync(FULL_MASK, s, 2);
+      const F v = (r < cb) ? F(0) : (((r == cb) ? F(1) : F(0)) - s) / D[r][r];
+      __syncwarp();
+      if (part == 0) Y[r][cb] = v;
+      __syncwarp();
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int r = idx / T, c = idx - (idx / T) * T;
-    A[base_ik + (size_t)r * np + c] = X[r][c];
-  }
+  F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)t * T * T;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) Di[idx] = Y[idx / T][idx - (idx / T) * T];
 }
 
 // A_ij -= L_i,kt L_j,kt^T on a T x T tile; 256 threads, each an (T/16) x (T/16) register block.
@@ -208,11 +304,15 @@ __device__ F warp_sum(F v) {
 }
 
 // x := D^-1/2 (L L^T)^-1 D^-1/2 rhs  (accumulate = 0) or x += ... (accumulate = 1); one CTA per cluster.
+// Each tile step: the off-diagonal part as a matrix-vector product (every warp keeps T / 8 rows in
+// flight), then the diagonal tile through its stored inverse, staged in shared memory.
 template <typename F, int T, typename Rreal>
 __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, const F* Dinv, const double* scale,
                                                    const Rreal* rhs, double* x, int accumulate) {
+  constexpr int RW = T / 8;   // rows per warp
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F* y = reinterpret_cast<F*>(smem_raw);
+  __shared__ F Ds[T][T + 1];
   __shared__ F t[T];
   __shared__ F part[8][T];
   const int k = blockIdx.x;
@@ -222,25 +322,39 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   const double* sk = scale + P.v_off[k];
   const Rreal* rk = rhs + P.v_off[k];
   double* xk = x + P.v_off[k];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = np / T;
   for (int i = threadIdx.x; i < np; i += blockDim.x) y[i] = (F)((double)rk[i] * sk[i]);
   __syncthreads();
   // forward: L y = s o rhs
   for (int it = 0; it < nt; ++it) {
     const int r0 = it * T;
-    for (int rr = warp; rr < T; rr += nwarps) {
-      const F* row = A + (size_t)(r0 + rr) * np;
-      F s = F(0);
-      for (int c = lane; c < r0; c += 32) s += row[c] * y[c];
-      s = warp_sum(s);
-      if (lane == 0) t[rr] = y[r0 + rr] - s;
+    const F* Dt = Di + (size_t)it * T * T;
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) Ds[idx / T][idx - (idx / T) * T] = Dt[idx];
+    F acc[RW];
+#pragma unroll
+    for (int q = 0; q < RW; ++q) acc[q] = F(0);
+    const F* rows = A + (size_t)(r0 + warp * RW) * np;
+    int c = lane;
+    for (; c + 32 < r0; c += 64) {
+      const F y0 = y[c], y1 = y[c + 32];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) acc[q] += rows[(size_t)q * np + c] * y0 + rows[(size_t)q * np + c + 32] * y1;
+    }
+    for (; c < r0; c += 32) {
+      const F yc = y[c];
+#pragma unroll
+      for (int q = 0; q < RW; ++q) acc[q] += rows[(size_t)q * np + c] * yc;
+    }
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const F s = warp_sum(acc[q]);
+      if (lane == 0) t[warp * RW + q] = y[r0 + warp * RW + q] - s;
     }
     __syncthreads();
-    const F* Dt = Di + (size_t)it * T * T;
-    for (int rr = warp; rr < T; rr += nwarps) {
+    for (int rr = warp; rr < T; rr += 8) {
       F s = F(0);
-      for (int c = lane; c <= rr; c += 32) s += Dt[rr * T + c] * t[c];
+      for (int c = lane; c <= rr; c += 32) s += Ds[rr][c] * t[c];
       s = warp_sum(s);
       if (lane == 0) y[r0 + rr] = s;
     }
@@ -249,24 +363,48 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   // backward: L^T z = y
   for (int it = nt - 1; it >= 0; --it) {
     const int r0 = it * T;
-    for (int cc = lane; cc < T; cc += 32) {
-      F p = F(0);
-      for (int c = r0 + T + warp; c < np; c += nwarps) p += A[(size_t)c * np + r0 + cc] * y[c];
-      part[warp][cc] = p;
+    const F* Dt = Di + (size_t)it * T * T;
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) Ds[idx / T][idx - (idx / T) * T] = Dt[idx];
+    {
+      constexpr int NC = T / 32;   // columns per lane
+      F p[NC][4];
+#pragma unroll
+      for (int u = 0; u < NC; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) p[u][v] = F(0);
+      int c = r0 + T + warp;
+      for (; c + 24 < np; c += 32) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const F yc = y[c + 8 * v];
+          const F* row = A + (size_t)(c + 8 * v) * np + r0 + lane;
+#pragma unroll
+          for (int u = 0; u < NC; ++u) p[u][v] += row[32 * u] * yc;
+        }
+      }
+      for (; c < np; c += 8) {
+        const F yc = y[c];
+        const F* row = A + (size_t)c * np + r0 + lane;
+#pragma unroll
+        for (int u = 0; u < NC; ++u) p[u][0] += row[32 * u] * yc;
+      }
+#pragma unroll
+      for (int u = 0; u < NC; ++u) part[warp][lane + 32 * u] = (p[u][0] + p[u][1]) + (p[u][2] + p[u][3]);
     }
     __syncthreads();
     for (int cc = threadIdx.x; cc < T; cc += blockDim.x) {
       F s = F(0);
-      for (int w = 0; w < nwarps; ++w) s += part[w][cc];
+#pragma unroll
+      for (int w = 0; w < 8; ++w) s += part[w][cc];
       t[cc] = y[r0 + cc] - s;
     }
     __syncthreads();
-    const F* Dt = Di + (size_t)it * T * T;
     // z_tile = Dinv^T t: z[c] = sum_{r >= c} Dinv[r][c] t[r]
-    for (int cc = threadIdx.x; cc < T; cc += blockDim.x) {
+    for (int cc = warp; cc < T; cc += 8) {
       F s = F(0);
-      for (int r = cc; r < T; ++r) s += Dt[r * T + cc] * t[r];
-      y[r0 + cc] = s;
+      for (int r = cc + lane; r < T; r += 32) s += Ds[r][cc] * t[r];
+      s = warp_sum(s);
+      if (lane == 0) y[r0 + cc] = s;
     }
     __syncthreads();
   }
@@ -346,9 +484,10 @@ __global__ void k_count_failures(const int* fail_flags, int l, DevState* st) {
 
 // ------------------------------------------------------------------------------------------------------
 // Host launchers
-template <typename Sreal, typename F>
-void launch_factor(const DevProblem& P, const Sreal* S, const FactorBuffers& fb, const CholPlan& plan,
+template <typename F>
+void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
                    cudaStream_t stream) {
+  using Sreal = double;
   constexpr int T = FactorCfg<F>::T;
   F* L = reinterpret_cast<F*>(fb.L);
   F* Dinv = reinterpret_cast<F*>(fb.Dinv);
@@ -359,16 +498,18 @@ void launch_factor(const DevProblem& P, const Sreal* S, const FactorBuffers& fb,
   for (int kt = 0; kt < plan.nsteps; ++kt) {
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
     if (npn > 0)
-      k_chol_panel<F, T><<<npn, 256, 0, stream>>>(L, Dinv, P, plan.panel_items + plan.h_panel_off[kt], kt,
-                                                   fb.fail_flags, fb.boosted);
+      k_chol_panel<F, T><<<npn, 256, 0, stream>>>(L, P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags,
+                                                   fb.boosted);
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];
     if (nu > 0) k_chol_update<F, T><<<nu, 256, 0, stream>>>(L, P, plan.update_items + plan.h_update_off[kt], kt);
   }
+  if (plan.n_diag_items > 0) k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(L, Dinv, P, plan.diag_items);
 }
 
-template <typename Sreal, typename F>
-void launch_solve(const DevProblem& P, const Sreal* S, const Sreal* b, const FactorBuffers& fb, const CholPlan& plan,
-                  int refine_steps, double* dc, cudaStream_t stream) {
+template <typename F>
+void launch_solve(const DevProblem& P, const double* S, const double* b, const FactorBuffers& fb,
+                  const CholPlan& plan, int refine_steps, double* dc, cudaStream_t stream) {
+  using Sreal = double;
   constexpr int T = FactorCfg<F>::T;
   const F* L = reinterpret_cast<const F*>(fb.L);
   const F* Dinv = reinterpret_cast<const F*>(fb.Dinv);
@@ -385,7 +526,6 @@ void launch_solve(const DevProblem& P, const Sreal* S, const Sreal* b, const Fac
 
 void configure_solve_kernels(int max_np) {
   const int s32 = (int)(sizeof(float) * (size_t)max_np), s64 = (int)(sizeof(double) * (size_t)max_np);
-  cudaFuncSetAttribute(k_tri_solve<float, 64, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
   cudaFuncSetAttribute(k_tri_solve<float, 64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
   cudaFuncSetAttribute(k_tri_solve<double, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
 }
@@ -394,13 +534,13 @@ void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStrea
   k_count_failures<<<1, 256, 0, stream>>>(fail_flags, l, st);
 }
 
-template void launch_factor<float, float>(const DevProblem&, const float*, const FactorBuffers&, const CholPlan&,
-                                          cudaStream_t);
-template void launch_factor<double, double>(const DevProblem&, const double*, const FactorBuffers&,
-                                            const CholPlan&, cudaStream_t);
-template void launch_solve<float, float>(const DevProblem&, const float*, const float*, const FactorBuffers&,
-                                         const CholPlan&, int, double*, cudaStream_t);
-template void launch_solve<double, double>(const DevProblem&, const double*, const double*, const FactorBuffers&,
-                                           const CholPlan&, int, double*, cudaStream_t);
+template void launch_factor<float>(const DevProblem&, const double*, const FactorBuffers&, const CholPlan&,
+                                   cudaStream_t);
+template void launch_factor<double>(const DevProblem&, const double*, const FactorBuffers&, const CholPlan&,
+                                    cudaStream_t);
+template void launch_solve<float>(const DevProblem&, const double*, const double*, const FactorBuffers&,
+                                  const CholPlan&, int, double*, cudaStream_t);
+template void launch_solve<double>(const DevProblem&, const double*, const double*, const FactorBuffers&,
+                                   const CholPlan&, int, double*, cudaStream_t);
 
 }  // namespace stba

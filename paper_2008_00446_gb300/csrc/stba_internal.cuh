@@ -36,7 +36,13 @@ struct DevProblem {
   const int* cluster_n;        // [l] dimension 9 n_k
   const int64_t* S_off;        // [l] element offset of the dense Np_k x Np_k block of cluster k
   const int64_t* v_off;        // [l] element offset of the length-Np_k vectors of cluster k
+  const float* res_f;          // [q][2] residuals f_o at the current x, computed in FP64, stored in the
+  const double* res_d;         //        working precision (res_f in mixed mode, res_d in FP64 mode)
 };
+
+template <typename real> __host__ __device__ inline const real* res_ptr(const DevProblem& P);
+template <> __host__ __device__ inline const float* res_ptr<float>(const DevProblem& P) { return P.res_f; }
+template <> __host__ __device__ inline const double* res_ptr<double>(const DevProblem& P) { return P.res_d; }
 
 // Device-resident LM state; the captured iteration graph reads and writes it in place.
 struct DevState {
@@ -67,8 +73,8 @@ template <typename real> struct Scratch {
   real* vp_acc;    // [nv][9]: V = sum Jp^T Jp (6, packed xx xy xz yy yz zz) and w' = -sum Jp^T f (3)
   real* vp_info;   // [nv][9]: L^-1 of V' (6, packed l00 l10 l11 l20 l21 l22) and y = V'^-1 w' (3)
   real* pt_info;   // [n][9]: C^-1 (6, packed symmetric) and w (3) of the physical points
-  real* S;         // cluster-diagonal S' (dense lower triangles, per-cluster padded blocks)
-  real* b;         // b' (per-cluster padded vectors)
+  double* S;       // cluster-diagonal S' (dense lower triangles, per-cluster padded blocks); FP64 sums
+  double* b;       // b' (per-cluster padded vectors); FP64 sums
   real* vgrad;     // [m][9] camera gradient v = -J_c^T f
   real* t_acc;     // [n][3] sum_o J_p^T J_c dc per point
   double* dc;      // [m][9] camera step
@@ -81,15 +87,9 @@ struct CamLists {     // observations of every camera (sorted positions), host-b
   const int* cam_obs;       // [q]
 };
 
-struct PairLists {    // work items of the pair pass of the S' build (host-built per cluster assignment)
-  const int* tile_cluster;  // [nt]
-  const int* tile_ga;       // [nt]
-  const int* tile_gb;       // [nt]
-  const int* item_tile;     // [ni]
-  const int* item_lo;       // [ni] range into pairs
-  const int* item_hi;       // [ni]
-  const int4* pairs;        // (obs a, obs b, offset of the 9x9 block in the tile, 0), grouped by tile
-  int ni;
+struct PairLists {    // camera-pair instances of the S' build (host-built per cluster assignment)
+  const int4* pairs;        // (obs a, obs b, cluster k, (la << 16) | lb), sorted by (k, la, lb)
+  int npairs;
 };
 
 constexpr int RED_BLOCKS = 456;    // 3 x 152 SMs: fixed grid of the deterministic reductions
@@ -104,25 +104,23 @@ void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cuda
 template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamLists CL, PairLists B, real* Gbuf, DevState* st,
                       cudaStream_t stream);
-int pair_tile_cameras(bool mixed);
 template <typename real>
 void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
 template <typename real>
 void launch_point_update(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
+// k_cam_rt + k_cost: rt is a [m][15] FP64 scratch (R, t, f, k1, k2 of x + dx); residuals go to rout.
 template <typename real>
-void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* partial, DevState* st,
-                 cudaStream_t stream);
+void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, double* partial, DevState* st,
+                 real* rout, cudaStream_t stream);
 // with_step = 1: stop tests and accept / reject of the step in W.dc / W.dp; 0: F(x) -> st->F.
 template <typename real>
 void launch_finalize(const DevProblem& P, Scratch<real> W, DevState* st, const Settings& s, int with_step,
                      cudaStream_t stream);
-void launch_apply(const DevProblem& P, const double* dc, const double* dp, double* cams, double* pts,
-                  DevState* st, cudaStream_t stream);
 template <typename real>
-size_t pair_build_smem();
+void launch_apply(const DevProblem& P, const double* dc, const double* dp, double* cams, double* pts,
+                  const real* r_cand, real* r_cur, DevState* st, cudaStream_t stream);
 // Sets the dynamic shared-memory limits of the kernels that need more than 48 KB (call outside capture).
 void configure_kernels(int max_np);
-void configure_build_kernels();
 void configure_solve_kernels(int max_np);
 
 // Cholesky (stba_chol.cu)
@@ -131,6 +129,8 @@ struct CholPlan {
   const int2* update_items;  // (cluster, (i << 16) | j) for every step, concatenated
   const int2* res_items;     // (cluster, 32-row block) of the refinement residual
   int n_res_items;
+  const int2* diag_items;    // (cluster, diagonal tile) for the inverses of the diagonal tiles
+  int n_diag_items;
   int nsteps;
   const int* h_panel_off;    // host arrays [nsteps + 1] (launch sizes)
   const int* h_update_off;
@@ -147,12 +147,12 @@ struct FactorBuffers {
   int64_t v_total;
 };
 int factor_tile(bool mixed);
-template <typename Sreal, typename F>
-void launch_factor(const DevProblem& P, const Sreal* S, const FactorBuffers& fb, const CholPlan& plan,
+template <typename F>
+void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
                    cudaStream_t stream);
-template <typename Sreal, typename F>
-void launch_solve(const DevProblem& P, const Sreal* S, const Sreal* b, const FactorBuffers& fb, const CholPlan& plan,
-                  int refine_steps, double* dc, cudaStream_t stream);
+template <typename F>
+void launch_solve(const DevProblem& P, const double* S, const double* b, const FactorBuffers& fb,
+                  const CholPlan& plan, int refine_steps, double* dc, cudaStream_t stream);
 void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStream_t stream);
 
 }  // namespace stba

@@ -119,6 +119,8 @@ __global__ void __launch_bounds__(256) k_vp_reduce(DevProblem P, real* vp_acc) {
     load_uv(P, o, uo, vo);
     real r[2], Jc[2][9], Jp[2][3];
     project_jacobian<real, false>(C, X, uo, vo, r, Jc, Jp);
+    r[0] = res_ptr<real>(P)[2 * (size_t)o];
+    r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
     val[0] = Jp[0][0] * Jp[0][0] + Jp[1][0] * Jp[1][0];
     val[1] = Jp[0][0] * Jp[0][1] + Jp[1][0] * Jp[1][1];
     val[2] = Jp[0][0] * Jp[0][2] + Jp[1][0] * Jp[1][2];
@@ -305,6 +307,8 @@ __global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W,
     load_uv(P, o, uo, vo);
     real r[2], Jc[2][9], Jp[2][3];
     project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
+    r[0] = res_ptr<real>(P)[2 * (size_t)o];
+    r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
     const real* vi = W.vp_info + 9 * (size_t)v;
     real br[2];
     if (single) {
@@ -380,19 +384,20 @@ __global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W,
       aV[i] -= Jc[0][i] * r[0] + Jc[1][i] * r[1];
     }
   }
-  // block reduction of the 63 sums
-  __shared__ real red[8][64];
+  // block reduction of the 63 sums: each thread summed a few terms in the working precision; the
+  // partial sums are combined in FP64
+  __shared__ double red[8][64];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < 63; ++i) {
-    real x = i < 45 ? aD[i] : (i < 54 ? aB[i - 45] : aV[i - 54]);
+    double x = (double)(i < 45 ? aD[i] : (i < 54 ? aB[i - 45] : aV[i - 54]));
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(FULL_MASK, x, d);
     if (lane == 0) red[warp][i] = x;
   }
   __syncthreads();
   if (threadIdx.x < 63) {
-    real x = 0;
+    double x = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[w][threadIdx.x];
     const int k = P.cam_cluster[j];
     const int lc = P.cam_local[j];
@@ -406,68 +411,70 @@ __global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W,
     } else if (i < 54) {
       W.b[P.v_off[k] + 9 * lc + (i - 45)] = x;
     } else {
-      W.vgrad[9 * (size_t)j + (i - 54)] = x;
+      W.vgrad[9 * (size_t)j + (i - 54)] = (real)x;
     }
   }
 }
 
-// k_pair_build: one CTA per chunk of the pair instances of one tile (cluster k, camera groups
-// gA >= gB of TC cameras); a pair instance is two observations (a, b) of one virtual point with
-// local camera index of a > that of b.  Threads run over (pair, 9x9 entry); the tile accumulates in
-// shared memory and is added to S'_k once.
-template <typename real, int TC>
-__global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, PairLists B,
-                                                    const real* __restrict__ Gbuf) {
-  constexpr int TD = 9 * TC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* acc = reinterpret_cast<real*>(smem_raw);
-  const int item = blockIdx.x;
-  const int tile = B.item_tile[item];
-  const int k = B.tile_cluster[tile], gA = B.tile_ga[tile], gB = B.tile_gb[tile];
-  for (int i = threadIdx.x; i < TD * TD; i += blockDim.x) acc[i] = 0;
-  __syncthreads();
-  const int64_t lo = (int64_t)B.item_lo[item] * 81, hi = (int64_t)B.item_hi[item] * 81;
-  for (int64_t idx = lo + threadIdx.x; idx < hi; idx += blockDim.x) {
-    const int64_t p = idx / 81;
-    const int e = (int)(idx - p * 81);
-    const int rr = e / 9, cc = e - (e / 9) * 9;
-    const int4 pr = B.pairs[p];
-    const real* Ga = Gbuf + (size_t)GSTRIDE * pr.x;
-    const real* Gb = Gbuf + (size_t)GSTRIDE * pr.y;
-    const real val = __ldg(Ga + rr) * __ldg(Gb + cc) + __ldg(Ga + 9 + rr) * __ldg(Gb + 9 + cc) +
-                     __ldg(Ga + 18 + rr) * __ldg(Gb + 18 + cc);
-    atomicAdd(acc + pr.z + rr * TD + cc, -val);
-  }
-  __syncthreads();
-  const int np = P.cluster_np[k], nk = P.cluster_n[k];
-  real* Sk = W.S + P.S_off[k];
-  const int r0 = 9 * gA * TC, c0 = 9 * gB * TC;
-  for (int idx = threadIdx.x; idx < TD * TD; idx += blockDim.x) {
-    const int rr = idx / TD, cc = idx - (idx / TD) * TD;
-    const int gr = r0 + rr, gc = c0 + cc;
-    const real a = acc[idx];
-    if (a != real(0) && gr < nk && gc < nk && gr > gc) atomicAdd(Sk + (size_t)gr * np + gc, a);
-  }
-}
-
-template <typename real> struct BuildCfg;
-template <> struct BuildCfg<float> { static constexpr int TC = 16; };
-template <> struct BuildCfg<double> { static constexpr int TC = 8; };
+// k_pair_build: the camera-pair instances (observations a, b of one virtual point, local camera index
+// of a > that of b) are sorted by (cluster, camera block).  Each warp walks a contiguous range of them;
+// 27 lanes own a row and three columns of the 9x9 block and accumulate -G_a^T G_b in registers while the
+// block stays the same, so each run of equal blocks costs one atomic add per entry into the FP64 S'_k.
+constexpr int PAIRS_PER_WARP = 64;
 
 template <typename real>
-size_t pair_build_smem() {
-  constexpr int TD = 9 * BuildCfg<real>::TC;
-  return sizeof(real) * (size_t)TD * TD;
+__global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, const int4* __restrict__ pairs,
+                                                    int npairs, const real* __restrict__ Gbuf) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int p0 = warp * PAIRS_PER_WARP;
+  if (p0 >= npairs) return;
+  const int p1 = min(p0 + PAIRS_PER_WARP, npairs);
+  const int r = lane / 3, cg = lane - (lane / 3) * 3;   // lanes 0..26: row r, columns 3cg .. 3cg+2
+  const bool act = lane < 27;
+  real acc0 = 0, acc1 = 0, acc2 = 0;
+  int4 cur = pairs[p0];
+  for (int p = p0; p < p1; ++p) {
+    const int4 pr = pairs[p];
+    if (pr.z != cur.z || pr.w != cur.w) {
+      if (act) {   // flush the finished run
+        const int k = cur.z, la = cur.w >> 16, lb = cur.w & 0xffff;
+        double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
+        atomicAdd(dst, -(double)acc0);
+        atomicAdd(dst + 1, -(double)acc1);
+        atomicAdd(dst + 2, -(double)acc2);
+      }
+      acc0 = acc1 = acc2 = 0;
+      cur = pr;
+    }
+    if (act) {
+      const real* Ga = Gbuf + (size_t)GSTRIDE * pr.x;
+      const real* Gb = Gbuf + (size_t)GSTRIDE * pr.y + 3 * cg;
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const real a = __ldg(Ga + 9 * s + r);
+        acc0 += a * __ldg(Gb + 9 * s);
+        acc1 += a * __ldg(Gb + 9 * s + 1);
+        acc2 += a * __ldg(Gb + 9 * s + 2);
+      }
+    }
+  }
+  if (act) {
+    const int k = cur.z, la = cur.w >> 16, lb = cur.w & 0xffff;
+    double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
+    atomicAdd(dst, -(double)acc0);
+    atomicAdd(dst + 1, -(double)acc1);
+    atomicAdd(dst + 2, -(double)acc2);
+  }
 }
-
-int pair_tile_cameras(bool mixed) { return mixed ? BuildCfg<float>::TC : BuildCfg<double>::TC; }
 
 template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamLists CL, PairLists B, real* Gbuf, DevState* st,
                       cudaStream_t stream) {
   k_cam_pass<real><<<P.m, 256, 0, stream>>>(P, W, CL, Gbuf, st);
-  if (B.ni > 0)
-    k_pair_build<real, BuildCfg<real>::TC><<<B.ni, 256, pair_build_smem<real>(), stream>>>(P, W, B, Gbuf);
+  if (B.npairs > 0) {
+    const int warps = (B.npairs + PAIRS_PER_WARP - 1) / PAIRS_PER_WARP;
+    k_pair_build<real><<<(warps + 7) / 8, 256, 0, stream>>>(P, W, B.pairs, B.npairs, Gbuf);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -545,33 +552,65 @@ __global__ void __launch_bounds__(256) k_point_update(DevProblem P, const real* 
 }
 
 // ------------------------------------------------------------------------------------------------------
-// F(x + dx) (dc, dp may be null for F(x)): FP32 or FP64 residuals, FP64 sums, fixed grid -> deterministic.
+// Residuals in FP64 (both precisions): the cost F(x + dx) and the accept test need them to FP64 accuracy,
+// and the stored residuals drive the next linearisation (FP32 projections of pixel coordinates of a few
+// hundred px carry ~3e-5 px of rounding, which the conditioning of S' amplifies in the step).
+// k_cam_rt precomputes per camera R(w + dw) (Rodrigues in FP64), t + dt and the intrinsics.
+__global__ void k_cam_rt(int m, const double* cams, const double* dc, double* rt) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    double c[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) c[i] = cams[9 * (size_t)j + i] + (dc ? dc[9 * (size_t)j + i] : 0.0);
+    const double s = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+    double a, b, da, db;
+    rodrigues_coeffs(s, a, b, da, db);
+    const double* w = c;
+    double* o = rt + 15 * (size_t)j;
+    o[0] = 1.0 + b * (w[0] * w[0] - s);
+    o[1] = -a * w[2] + b * w[0] * w[1];
+    o[2] = a * w[1] + b * w[0] * w[2];
+    o[3] = a * w[2] + b * w[0] * w[1];
+    o[4] = 1.0 + b * (w[1] * w[1] - s);
+    o[5] = -a * w[0] + b * w[1] * w[2];
+    o[6] = -a * w[1] + b * w[0] * w[2];
+    o[7] = a * w[0] + b * w[1] * w[2];
+    o[8] = 1.0 + b * (w[2] * w[2] - s);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) o[9 + i] = c[3 + i];
+  }
+}
+
+// F = sum |f_o|^2 at the parameters described by rt and pts (+ dp); writes f_o to rout (working precision).
 template <typename real>
-__global__ void __launch_bounds__(RED_THREADS) k_cost(DevProblem P, const double* dc, const double* dp,
-                                                      double* partial, DevState* st) {
+__global__ void __launch_bounds__(RED_THREADS) k_cost(DevProblem P, const double* rt, const double* dp,
+                                                      double* partial, DevState* st, real* rout) {
   double s = 0.0;
   int bad = 0;
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < P.q; o += gridDim.x * blockDim.x) {
     const int cam = P.obs_cam[o];
     const int pt = P.obs_pt[o];
-    Cam<real> C = dc ? load_cam_step<real>(P.cams + 9 * (size_t)cam, dc + 9 * (size_t)cam)
-                     : load_cam<real>(P.cams + 9 * (size_t)cam);
-    real X[3];
+    const double* C = rt + 15 * (size_t)cam;
     const double* p = P.pts + 3 * (size_t)pt;
+    double X0 = p[0], X1 = p[1], X2 = p[2];
     if (dp) {
       const double* q = dp + 3 * (size_t)pt;
-      X[0] = (real)(p[0] + q[0]);
-      X[1] = (real)(p[1] + q[1]);
-      X[2] = (real)(p[2] + q[2]);
-    } else {
-      load_point(p, X);
+      X0 += q[0];
+      X1 += q[1];
+      X2 += q[2];
     }
-    real uo, vo;
-    load_uv(P, o, uo, vo);
-    real r[2], z;
-    project_residual(C, X, uo, vo, r, &z);
-    if (!(z > real(1e-9))) bad = 1;
-    s += (double)r[0] * (double)r[0] + (double)r[1] * (double)r[1];
+    const double xc = C[0] * X0 + C[1] * X1 + C[2] * X2 + C[9];
+    const double yc = C[3] * X0 + C[4] * X1 + C[5] * X2 + C[10];
+    const double zc = C[6] * X0 + C[7] * X1 + C[8] * X2 + C[11];
+    const double iz = 1.0 / zc;
+    const double x = xc * iz, y = yc * iz;
+    const double r2 = x * x + y * y;
+    const double fd = C[12] * (1.0 + r2 * (C[13] + C[14] * r2));
+    const double2 uv = reinterpret_cast<const double2*>(P.obs_uv)[o];
+    const double r0 = fd * x - uv.x, r1 = fd * y - uv.y;
+    if (!(zc > 1e-9)) bad = 1;
+    s += r0 * r0 + r1 * r1;
+    rout[2 * (size_t)o] = (real)r0;
+    rout[2 * (size_t)o + 1] = (real)r1;
   }
   __shared__ double red[RED_THREADS / 32];
   for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(FULL_MASK, s, d);
@@ -664,8 +703,9 @@ __global__ void __launch_bounds__(1024) k_finalize(DevProblem P, const real* vgr
   }
 }
 
-__global__ void k_apply(int m, int n, const double* dc, const double* dp, double* cams, double* pts,
-                        const DevState* st) {
+template <typename real>
+__global__ void k_apply(int m, int n, int q, const double* dc, const double* dp, double* cams, double* pts,
+                        const real* r_cand, real* r_cur, const DevState* st) {
   if (!st->info.accepted) return;
   const int total = 9 * m + 3 * n;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -674,6 +714,7 @@ __global__ void k_apply(int m, int n, const double* dc, const double* dp, double
     else
       pts[i - 9 * m] += dp[i - 9 * m];
   }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * q; i += gridDim.x * blockDim.x) r_cur[i] = r_cand[i];
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -689,12 +730,13 @@ void launch_finalize(const DevProblem& P, Scratch<real> W, DevState* st, const S
   k_finalize<real><<<1, 1024, 0, stream>>>(P, W.vgrad, W.dc, W.partial, st, s, with_step);
 }
 
+template <typename real>
 void launch_apply(const DevProblem& P, const double* dc, const double* dp, double* cams, double* pts,
-                  DevState* st, cudaStream_t stream) {
-  int total = 9 * P.m + 3 * P.n;
+                  const real* r_cand, real* r_cur, DevState* st, cudaStream_t stream) {
+  int total = std::max(9 * P.m + 3 * P.n, 2 * P.q);
   int blocks = (total + 255) / 256;
   if (blocks > 2048) blocks = 2048;
-  k_apply<<<blocks, 256, 0, stream>>>(P.m, P.n, dc, dp, cams, pts, st);
+  k_apply<real><<<blocks, 256, 0, stream>>>(P.m, P.n, P.q, dc, dp, cams, pts, r_cand, r_cur, st);
 }
 
 template <typename real>
@@ -704,22 +746,14 @@ void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream)
 }
 
 template <typename real>
-void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* partial, DevState* st,
-                 cudaStream_t stream) {
-  k_cost<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, dc, dp, partial, st);
+void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, double* partial, DevState* st,
+                 real* rout, cudaStream_t stream) {
+  k_cam_rt<<<(P.m + 127) / 128, 128, 0, stream>>>(P.m, P.cams, dc, rt);
+  k_cost<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, rt, dp, partial, st, rout);
 }
 
-void configure_build_kernels() {
-  cudaFuncSetAttribute(k_pair_build<float, BuildCfg<float>::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pair_build_smem<float>());
-  cudaFuncSetAttribute(k_pair_build<double, BuildCfg<double>::TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)pair_build_smem<double>());
-}
 
-void configure_kernels(int max_np) {
-  configure_build_kernels();
-  configure_solve_kernels(max_np);
-}
+void configure_kernels(int max_np) { configure_solve_kernels(max_np); }
 
 #define INSTANTIATE(real)                                                                                  \
   template void launch_iter_begin<real>(DevState*, const Settings&, cudaStream_t);                        \
@@ -731,9 +765,11 @@ void configure_kernels(int max_np) {
   template void launch_finalize<real>(const DevProblem&, Scratch<real>, DevState*, const Settings&, int,  \
                                       cudaStream_t);                                                      \
   template void launch_point_rhs<real>(const DevProblem&, Scratch<real>, cudaStream_t);                  \
-  template void launch_cost<real>(const DevProblem&, const double*, const double*, double*, DevState*,    \
-                                  cudaStream_t);                                                          \
-  template size_t pair_build_smem<real>();
+  template void launch_cost<real>(const DevProblem&, const double*, const double*, double*, double*,      \
+                                  DevState*, real*, cudaStream_t);                                        \
+  template void launch_apply<real>(const DevProblem&, const double*, const double*, double*, double*,     \
+                                   const real*, real*, DevState*, cudaStream_t);                          \
+
 
 INSTANTIATE(float)
 INSTANTIATE(double)

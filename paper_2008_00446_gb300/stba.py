@@ -82,7 +82,7 @@ def load(build_if_missing: bool = True):
         "stba_get_state": (I32, [P, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "stba_set_state": (I32, [P, D, D, I64]),
         "stba_last_step": (I32, [P, P, P]),
-        "stba_problem_info": (I32, [P, ctypes.POINTER(I64)]),
+        "stba_problem_info": (I32, [P, ctypes.POINTER(I64), I32]),
         "stba_get_cluster_system": (I32, [P, I32, P, P, ctypes.POINTER(I64)]),
         "stba_set_timing": (I32, [P, I32]),
         "stba_stage_times": (I32, [P, ctypes.POINTER(ctypes.c_float), I32, ctypes.POINTER(I32)]),
@@ -241,9 +241,10 @@ def stba_last_step(ctx: Context):
 
 
 def stba_problem_info(ctx: Context):
-    out = (ctypes.c_int64 * 8)()
-    ctx._check(load().stba_problem_info(ctx.handle, out))
-    keys = ["m", "n", "q", "l", "nv", "max_dim", "device_bytes", "build_items"]
+    keys = ["m", "n", "q", "l", "nv", "max_dim", "device_bytes", "build_items", "launches_per_iter",
+            "pair_instances", "factor_flops", "s_lower_elems"]
+    out = (ctypes.c_int64 * len(keys))()
+    ctx._check(load().stba_problem_info(ctx.handle, out, len(keys)))
     return dict(zip(keys, list(out)))
 
 

@@ -172,3 +172,28 @@ def test_solve_stops_on_function_tolerance(ring):
     ctx = make_ctx(s, s.clusters, ftol=0.5)
     info = stba.stba_solve(ctx, 20)
     assert info["stop"] and info["iteration"] < 20
+
+
+def test_mixed_precision_cluster_systems_and_solve(ring):
+    """Mixed mode, first iteration on the ring: the FP32-term / FP64-sum S'_k and b_k against the oracle,
+    and the device solve against an FP64 solve of the device's own S'_k (isolates factorisation error)."""
+    s = ring
+    c, p, lam, F, hist = run_oracle(s, s.clusters, 1)
+    st = ostba.lm_iteration(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, 1e-4,
+                            ocam.cost(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv), ostba.Options(),
+                            keep=True)[4]["step"]
+    ctx = make_ctx(s, s.clusters, precision=stba.STBA_MIXED)
+    stba.stba_lm_iteration(ctx)
+    dc, _ = stba.stba_last_step(ctx)
+    errs = []
+    for k in range(3):
+        S, b = stba.stba_get_cluster_system(ctx, k)
+        cams_k = np.flatnonzero(s.clusters == k)
+        x_own = np.linalg.solve(S, b)
+        x_dev = dc[cams_k].ravel()
+        errs.append((k, rel(S, st["S_blocks"][k]), rel(b, st["b_blocks"][k]), rel(x_dev, x_own),
+                     rel(x_own, np.linalg.solve(st["S_blocks"][k], st["b_blocks"][k]))))
+    print("mixed cluster systems (k, S err, b err, device-solve vs own-S FP64 solve, own-S solve vs oracle):", errs)
+    for k, eS, eb, esolve, eown in errs:
+        assert eS < 1e-5 and eb < 1e-5, errs
+        assert esolve < 1e-4, errs
