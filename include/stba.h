@@ -144,6 +144,21 @@ stba_status stba_get_cluster_system(stba_ctx* ctx, int32_t k, double* S, double*
 stba_status stba_set_timing(stba_ctx* ctx, int32_t on);
 stba_status stba_stage_times(stba_ctx* ctx, float* ms, int32_t n, int32_t* count);
 
+/* F(x) = ||f(x)||^2 without allocating device memory.  This entry point has no counterpart in the paper;
+ * it exists for callers that cannot allocate device memory when they evaluate the cost (a loop with a
+ * fixed, pre-reserved memory budget, or code that must not enter the allocator).
+ *   cameras [m][9], points [n][3], obs_uv [q][2] (FP64) and obs_cam, obs_pt [q] (int32) are DEVICE
+ *   pointers owned by the caller; F_dev is a device double that receives F (FP64 sum, no host sync).
+ *   m <= 16384: the scratch (per-camera FP64 rotation table and reduction partials) is one static device
+ *   array of 1.97 MB that every GPU loading the library holds until the process exits.  Larger m returns
+ *   STBA_ERR_INVALID_ARG.  Indices out of range or a point at depth <= 1e-9 make F NaN.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share the array, so calls that
+ * overlap on the GPU (different streams or devices' contexts sharing it) race; serialise them. */
+stba_status stba_cost_noalloc(const double* cameras, int64_t m, const double* points, int64_t n,
+                              const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int64_t q,
+                              double* F_dev, void* cuda_stream);
+
 /* Frees every device allocation of the context.  NULL is allowed. */
 void stba_destroy(stba_ctx* ctx);
 

@@ -23,7 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device mem
 EXPORTS = ["stba_default_options", "stba_create", "stba_set_clusters", "stba_lm_iteration", "stba_solve",
            "stba_cost", "stba_get_params", "stba_set_params", "stba_get_state", "stba_set_state",
            "stba_last_step", "stba_problem_info", "stba_get_cluster_system", "stba_set_timing",
-           "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error"]
+           "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error", "stba_cost_noalloc"]
 
 
 class StbaOptions(ctypes.Structure):
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
         "stba_destroy": (None, [P]),
         "stba_status_string": (ctypes.c_char_p, [I32]),
         "stba_last_error": (ctypes.c_char_p, [P]),
+        "stba_cost_noalloc": (I32, [P, I64, P, I64, P, P, P, I64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -267,6 +268,24 @@ def stba_stage_times(ctx: Context):
     cnt = ctypes.c_int32()
     ctx._check(load().stba_stage_times(ctx.handle, ms, 16, ctypes.byref(cnt)))
     return list(ms)[: cnt.value]
+
+
+def stba_cost_noalloc(cameras, points, obs_cam, obs_pt, obs_uv, F_out, stream=None):
+    """F(x) into the device scalar F_out without any device allocation by the library.  Every array must
+    already be a contiguous CUDA tensor of the right dtype (float64 / int32): nothing is converted or
+    copied here, since a conversion would allocate."""
+    import torch
+    for t, dt in ((cameras, torch.float64), (points, torch.float64), (obs_cam, torch.int32),
+                  (obs_pt, torch.int32), (obs_uv, torch.float64), (F_out, torch.float64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("stba_cost_noalloc needs contiguous CUDA tensors (float64 / int32)")
+    st = load().stba_cost_noalloc(ctypes.c_void_p(cameras.data_ptr()), cameras.shape[0],
+                                  ctypes.c_void_p(points.data_ptr()), points.shape[0],
+                                  ctypes.c_void_p(obs_cam.data_ptr()), ctypes.c_void_p(obs_pt.data_ptr()),
+                                  ctypes.c_void_p(obs_uv.data_ptr()), obs_cam.shape[0],
+                                  ctypes.c_void_p(F_out.data_ptr()), _stream_handle(stream))
+    if st != 0:
+        raise StbaError(st, "stba_cost_noalloc failed")
 
 
 def stba_destroy(ctx: Context):
