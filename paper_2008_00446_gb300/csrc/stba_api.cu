@@ -311,8 +311,15 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   for (int o = 0; o < q; ++o) cam_obs_off[s_cam[o] + 1]++;
   for (int j = 0; j < m; ++j) cam_obs_off[j + 1] += cam_obs_off[j];
   {
+    // per camera, observations of single-observation virtual points first (they take the Woodbury branch
+    // of the camera pass), then the others, so that warps mostly run one branch
     std::vector<int> f(cam_obs_off.begin(), cam_obs_off.end() - 1);
-    for (int o = 0; o < q; ++o) cam_obs[f[s_cam[o]]++] = o;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int o = 0; o < q; ++o) {
+        const int v = s_vp[o];
+        const bool single = vp_off[v + 1] - vp_off[v] == 1;
+        if (single == (pass == 0)) cam_obs[f[s_cam[o]]++] = o;
+      }
   }
   // camera-pair instances of the pair pass, sorted by (cluster, la, lb): inside a virtual point the
   // observations are ordered by camera, so a later observation has the larger local camera index
@@ -430,7 +437,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   if ((s = ralloc(&c->t_acc, 3 * (size_t)n)) != STBA_OK) return s;
   if ((s = ralloc(&c->Gbuf, 32 * (size_t)q)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.L, (size_t)c->S_total)) != STBA_OK) return s;
-  if ((s = ralloc(&c->fbuf.Dinv, (size_t)c->v_total * TF)) != STBA_OK) return s;
+  if ((s = ralloc(&c->fbuf.Dinv, 2 * (size_t)c->v_total * TF)) != STBA_OK) return s;
   if ((s = dalloc(c, &c->fbuf.scale, (size_t)c->v_total, true)) != STBA_OK) return s;
   if ((s = dalloc(c, &c->fbuf.x, (size_t)c->v_total, true)) != STBA_OK) return s;
   if ((s = dalloc(c, &c->fbuf.r, (size_t)c->v_total, true)) != STBA_OK) return s;

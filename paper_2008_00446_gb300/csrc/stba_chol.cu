@@ -20,6 +20,8 @@
 // Solves: one CTA per cluster; with the inverted diagonal tiles every tile step is two parallel
 // matrix-vector products.  Refinement: r = b - S x in FP64 over many CTAs (S symmetric, lower stored),
 // then x += D^-1/2 (L L^T)^-1 D^-1/2 r.
+#include <cooperative_groups.h>
+
 #include "stba_internal.cuh"
 
 namespace stba {
@@ -60,109 +62,197 @@ __global__ void k_scaled_copy(DevProblem P, const Sreal* S, const double* scale,
   }
 }
 
-// Register-blocked tile kernels.  256 threads form a 16 x 16 grid; thread (bi, bj) holds the R x R block
-// (R = T / 16) of rows bi R .. and columns bj R .. in registers.  Column j is broadcast through a double
-// buffer in shared memory, so each of the T steps costs one barrier.
+// Correctly rounded reciprocal (one special-function instruction plus fix-up instead of a division).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
+// Named barriers: the producer warp arrives without waiting, the consumer warps wait.
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Register-blocked tile kernels.  256 threads form a 16 x 16 grid; thread (bi, bj) = (tid % 16, tid / 16)
+// holds the R x R block (R = T / 16) of rows bi R .. and columns bj R .. in registers.  Warp w therefore
+// owns the 2R consecutive columns 2R w ..; lane l of it holds rows R (l % 16) .. of half l / 16 of them.
+// Both kernels sweep the tile in T / 2R blocked steps: warp w finishes its own columns with shuffles only,
+// publishes them in shared memory (one buffer per step) and arrives on named barrier 1 + w; the warps to
+// its right wait on that barrier and apply a rank-2R update from registers.  A warp starts its own step
+// as soon as it has applied the steps before it, so the updates of distant warps overlap the next step.
 //
-// factor_tile_regs: right-looking LL^T of the diagonal tile with the unscaled column,
-// a_rc -= a_rj a_cj / a_jj; the pivots a_jj are kept and the columns scaled at the end.
+// factor_tile_regs: LL^T of the diagonal tile.  Inside a block the updates use the unscaled columns,
+// a_rc -= a_rj a_cj / a_jj; the pivots a_jj are kept, the published columns are scaled by a_jj^-1/2, and
+// every column is scaled once at the end.
 template <typename F, int T>
-__device__ __forceinline__ void factor_tile_regs(F (&a)[T / 16][T / 16], int bi, int bj, F* colbuf, F* piv, int row0, int nk,
-                                 int* fail, int* boosted) {
-  constexpr int R = T / 16;
-  for (int j = 0; j < T; ++j) {
-    F* col = colbuf + (j & 1) * T;
-    if (bj == j / R) {
+__device__ __forceinline__ void factor_tile_regs(F (&a)[T / 16][T / 16], F (*U)[T][T / 8], F* piv, F* tab,
+                                                 int row0, int nk, int* fail, int* boosted) {
+  constexpr int R = T / 16, W = 2 * R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bi = threadIdx.x & 15, bj = threadIdx.x >> 4, h = lane >> 4;
+  for (int w = 0; w < 8; ++w) {
+    const int c0 = W * w;
+    if (warp == w) {
 #pragma unroll
-      for (int ii = 0; ii < R; ++ii) {
-        const int jr = j % R;
-        F v = a[ii][0];
+      for (int jj = 0; jj < W; ++jj) {
+        const int hj = jj / R, cj = jj % R;
+        const int cg = c0 + jj;
+        F d = __shfl_sync(0xffffffffu, a[cj][cj], hj * 16 + 2 * w + hj);
+        bool bad = false, boost = false;
+        if (row0 + cg >= nk) {
+          d = F(1);
+        } else if (!isfinite(d)) {
+          bad = true;
+          d = F(1);
+        } else if (sizeof(F) == 8) {
+          if (!(d > F(0))) {
+            bad = true;
+            d = F(1);
+          }
+        } else if (d < F(1.0 / 1048576)) {
+          boost = true;
+          d = F(1.0 / 4096);
+        }
+        if (lane == 0) {
+          piv[cg] = d;
+          if (bad) *fail = 1;
+          if (boost && boosted) atomicAdd(boosted, 1);
+        }
+        const F inv = rcp_rn(d);
+        F colr[R], rowc[R];
 #pragma unroll
-        for (int jj = 1; jj < R; ++jj) v = (jj == jr) ? a[ii][jj] : v;
-        col[bi * R + ii] = v;
+        for (int ii = 0; ii < R; ++ii) colr[ii] = __shfl_sync(0xffffffffu, a[ii][cj], bi + 16 * hj);
+#pragma unroll
+        for (int j2 = 0; j2 < R; ++j2) rowc[j2] = __shfl_sync(0xffffffffu, a[j2][cj], (2 * w + h) + 16 * hj);
+#pragma unroll
+        for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+          for (int j2 = 0; j2 < R; ++j2) {
+            const int r = R * bi + ii, cl = c0 + R * h + j2;
+            if (cl > cg && r >= cl) a[ii][j2] -= colr[ii] * rowc[j2] * inv;
+          }
       }
-    }
-    __syncthreads();
-    F d = col[j];
-    bool bad = false, boost = false;
-    if (row0 + j >= nk) {
-      d = F(1);
-    } else if (!isfinite(d)) {
-      bad = true;
-      d = F(1);
-    } else if (sizeof(F) == 8) {
-      if (!(d > F(0))) {
-        bad = true;
-        d = F(1);
-      }
-    } else if (d < F(1.0 / 1048576)) {
-      boost = true;
-      d = F(1.0 / 4096);
-    }
-    if (threadIdx.x == 0) {
-      piv[j] = d;
-      if (bad) *fail = 1;
-      if (boost && boosted) atomicAdd(boosted, 1);
-    }
-    const F inv = F(1) / d;
-    if (bi >= bj) {
-      F cr[R], cc[R];
-#pragma unroll
-      for (int ii = 0; ii < R; ++ii) cr[ii] = col[bi * R + ii] * inv;
-#pragma unroll
-      for (int jj = 0; jj < R; ++jj) cc[jj] = col[bj * R + jj];
+      __syncwarp();
 #pragma unroll
       for (int ii = 0; ii < R; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < R; ++jj) {
-          const int r = bi * R + ii, cl = bj * R + jj;
-          if (cl > j && r >= cl) a[ii][jj] -= cr[ii] * cc[jj];
+        for (int j2 = 0; j2 < R; ++j2) {
+          const int cl = c0 + R * h + j2;
+          U[w][R * bi + ii][R * h + j2] = a[ii][j2] * rsqrt(piv[cl]);
         }
+      if (w < 7) named_arrive(1 + w, 32 * (8 - w));
+    } else if (warp > w) {
+      named_sync(1 + w, 32 * (8 - w));
+      if (bi >= bj) {
+        F ur[R][W], uc[R][W];
+#pragma unroll
+        for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+          for (int k = 0; k < W; ++k) {
+            ur[ii][k] = U[w][R * bi + ii][k];
+            uc[ii][k] = U[w][R * bj + ii][k];
+          }
+        if (bi > bj) {
+#pragma unroll
+          for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < R; ++jj) {
+              F s = F(0);
+#pragma unroll
+              for (int k = 0; k < W; ++k) s += ur[ii][k] * uc[jj][k];
+              a[ii][jj] -= s;
+            }
+        } else {
+#pragma unroll
+          for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+            for (int jj = 0; jj <= ii; ++jj) {
+              F s = F(0);
+#pragma unroll
+              for (int k = 0; k < W; ++k) s += ur[ii][k] * uc[jj][k];
+              a[ii][jj] -= s;
+            }
+        }
+      }
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < T) {
+    const F sq = sqrt(piv[threadIdx.x]);
+    tab[threadIdx.x] = rcp_rn(sq);
+    tab[T + threadIdx.x] = sq;
   }
   __syncthreads();
 #pragma unroll
   for (int ii = 0; ii < R; ++ii)
 #pragma unroll
     for (int jj = 0; jj < R; ++jj) {
-      const int r = bi * R + ii, cl = bj * R + jj;
-      a[ii][jj] = (r > cl) ? a[ii][jj] / sqrt(piv[cl]) : ((r == cl) ? sqrt(piv[cl]) : F(0));
+      const int r = R * bi + ii, cl = R * bj + jj;
+      a[ii][jj] = (r > cl) ? a[ii][jj] * tab[cl] : ((r == cl) ? tab[T + cl] : F(0));
     }
+  __syncthreads();
 }
 
-// trsm_tile_regs: X L^T = A for a full tile X (registers), L lower triangular in shared memory; the
-// columns of X are finished left to right and each finished column updates the ones to its right.
+// trsm_tile_regs: X L^T = A for a full tile X (registers), L lower triangular in shared memory (Ls) with
+// the reciprocals of its diagonal in rcp.  Warp w solves its 2R columns (rows are independent; the two
+// halves of the warp exchange their solved values by shuffles), publishes them, and the warps to its
+// right subtract X[:, block] L[c, block]^T.
 template <typename F, int T>
-__device__ __forceinline__ void trsm_tile_regs(F (&x)[T / 16][T / 16], int bi, int bj, const F (*Ls)[T + 1], F* colbuf) {
-  constexpr int R = T / 16;
-  for (int c = 0; c < T; ++c) {
-    F* col = colbuf + (c & 1) * T;
-    if (bj == c / R) {
-      const F inv = F(1) / Ls[c][c];
-      const int cr_ = c % R;
+__device__ __forceinline__ void trsm_tile_regs(F (&x)[T / 16][T / 16], const F (*Ls)[T + 1], const F* rcp,
+                                               F (*U)[T][T / 8]) {
+  constexpr int R = T / 16, W = 2 * R;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int bi = threadIdx.x & 15, bj = threadIdx.x >> 4, h = lane >> 4;
+  for (int w = 0; w < 8; ++w) {
+    const int c0 = W * w;
+    if (warp == w) {
 #pragma unroll
-      for (int ii = 0; ii < R; ++ii) {
-        F v = F(0);
+      for (int jj = 0; jj < W; ++jj) {
+        const int hj = jj / R, cj = jj % R;
+        const int cg = c0 + jj;
+        if (h == hj) {
+#pragma unroll
+          for (int ii = 0; ii < R; ++ii) x[ii][cj] *= rcp[cg];
+        }
+        F xs[R];
+#pragma unroll
+        for (int ii = 0; ii < R; ++ii) xs[ii] = __shfl_sync(0xffffffffu, x[ii][cj], bi + 16 * hj);
+#pragma unroll
+        for (int j2 = 0; j2 < R; ++j2) {
+          const int cl = c0 + R * h + j2;
+          if (cl > cg) {
+            const F l = Ls[cl][cg];
+#pragma unroll
+            for (int ii = 0; ii < R; ++ii) x[ii][j2] -= xs[ii] * l;
+          }
+        }
+      }
+#pragma unroll
+      for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+        for (int j2 = 0; j2 < R; ++j2) U[w][R * bi + ii][R * h + j2] = x[ii][j2];
+      if (w < 7) named_arrive(1 + w, 32 * (8 - w));
+    } else if (warp > w) {
+      named_sync(1 + w, 32 * (8 - w));
+      F ux[R][W], lc[R][W];
+#pragma unroll
+      for (int ii = 0; ii < R; ++ii)
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          ux[ii][k] = U[w][R * bi + ii][k];
+          lc[ii][k] = Ls[R * bj + ii][c0 + k];
+        }
+#pragma unroll
+      for (int ii = 0; ii < R; ++ii)
 #pragma unroll
         for (int jj = 0; jj < R; ++jj) {
-          const F nv = x[ii][jj] * inv;
-          x[ii][jj] = (jj == cr_) ? nv : x[ii][jj];
-          v = (jj == cr_) ? nv : v;
+          F s = F(0);
+#pragma unroll
+          for (int k = 0; k < W; ++k) s += ux[ii][k] * lc[jj][k];
+          x[ii][jj] -= s;
         }
-        col[bi * R + ii] = v;
-      }
     }
-    __syncthreads();
-    F cr[R], lc[R];
-#pragma unroll
-    for (int ii = 0; ii < R; ++ii) cr[ii] = col[bi * R + ii];
-#pragma unroll
-    for (int jj = 0; jj < R; ++jj) lc[jj] = Ls[bj * R + jj][c];
-#pragma unroll
-    for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-      for (int jj = 0; jj < R; ++jj)
-        if (bj * R + jj > c) x[ii][jj] -= cr[ii] * lc[jj];
   }
 }
 
@@ -171,13 +261,14 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const in
                                                     int* fail_flags, int* boosted) {
   constexpr int R = T / 16;
   __shared__ F Ls[T][T + 1];
-  __shared__ F colbuf[2 * T];
+  __shared__ __align__(16) F U[8][T][T / 8];
   __shared__ F piv[T];
+  __shared__ F tab[2 * T];
   const int2 it = items[blockIdx.x];
   const int k = it.x, i = it.y;
   const int np = P.cluster_np[k], nk = P.cluster_n[k];
   F* A = L + P.S_off[k];
-  const int bi = threadIdx.x >> 4, bj = threadIdx.x & 15;
+  const int bj = threadIdx.x >> 4, bi = threadIdx.x & 15;
   const size_t base_kk = (size_t)(kt * T) * np + kt * T;
   F a[R][R];
 #pragma unroll
@@ -195,7 +286,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const in
 #pragma unroll
       for (int jj = 0; jj < R; ++jj) x[ii][jj] = A[base_ik + (size_t)(bi * R + ii) * np + bj * R + jj];
   }
-  factor_tile_regs<F, T>(a, bi, bj, colbuf, piv, kt * T, nk, fail_flags + k, (i == kt) ? boosted : nullptr);
+  factor_tile_regs<F, T>(a, U, piv, tab, kt * T, nk, fail_flags + k, (i == kt) ? boosted : nullptr);
   if (i == kt) {
 #pragma unroll
     for (int ii = 0; ii < R; ++ii)
@@ -211,7 +302,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const in
 #pragma unroll
     for (int jj = 0; jj < R; ++jj) Ls[bi * R + ii][bj * R + jj] = a[ii][jj];
   __syncthreads();
-  trsm_tile_regs<F, T>(x, bi, bj, Ls, colbuf);
+  trsm_tile_regs<F, T>(x, Ls, tab, U);
 #pragma unroll
   for (int ii = 0; ii < R; ++ii)
 #pragma unroll
@@ -221,7 +312,8 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const in
 // Inverse of every diagonal tile of the factor (for the solves), one CTA per tile: L Y = I column by
 // column, four threads per column splitting each dot product.
 template <typename F, int T>
-__global__ void __launch_bounds__(256) k_diag_inverse(const F* L, F* Dinv, DevProblem P, const int2* items) {
+__global__ void __launch_bounds__(256) k_diag_inverse(const F* L, F* Dinv, DevProblem P, const int2* items,
+                                                      int64_t v_total) {
   __shared__ F D[T][T + 1];
   __shared__ F Y[T][T + 1];
   const int2 it = items[blockIdx.x];
@@ -249,7 +341,31 @@ __global__ void __launch_bounds__(256) k_diag_inverse(const F* L, F* Dinv, DevPr
   }
   __syncthreads();
   F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)t * T * T;
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) Di[idx] = Y[idx / T][idx - (idx / T) * T];
+  F* DiT = Di + v_total * T;   // transposed copy in the second half of the buffer
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    Di[idx] = Y[r][c];
+    DiT[idx] = Y[c][r];
+  }
+}
+
+// R consecutive elements from 16-byte aligned shared memory in one vector load where the width allows.
+template <typename F, int R>
+__device__ __forceinline__ void load_vec(const F* p, F (&v)[R]) {
+  if constexpr (sizeof(F) == 4 && R == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  } else if constexpr (sizeof(F) == 8 && R == 2) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < R; ++a) v[a] = p[a];
+  }
 }
 
 // A_ij -= L_i,kt L_j,kt^T on a T x T tile; 256 threads, each an (T/16) x (T/16) register block.
@@ -279,10 +395,8 @@ __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const i
 #pragma unroll 4
   for (int kk = 0; kk < T; ++kk) {
     F av[R], bv[R];
-#pragma unroll
-    for (int a = 0; a < R; ++a) av[a] = LiT[kk][tr * R + a];
-#pragma unroll
-    for (int b = 0; b < R; ++b) bv[b] = LjT[kk][tc * R + b];
+    load_vec<F, R>(&LiT[kk][tr * R], av);
+    load_vec<F, R>(&LjT[kk][tc * R], bv);
 #pragma unroll
     for (int a = 0; a < R; ++a)
 #pragma unroll
@@ -303,19 +417,41 @@ __device__ F warp_sum(F v) {
   return v;
 }
 
-// x := D^-1/2 (L L^T)^-1 D^-1/2 rhs  (accumulate = 0) or x += ... (accumulate = 1); one CTA per cluster.
-// Each tile step: the off-diagonal part as a matrix-vector product (every warp keeps T / 8 rows in
-// flight), then the diagonal tile through its stored inverse, staged in shared memory.
+// x := D^-1/2 (L L^T)^-1 D^-1/2 rhs  (accumulate = 0) or x += ... (accumulate = 1).
+// One thread-block cluster of CS CTAs per camera cluster.  Each CTA keeps the whole vector in shared
+// memory; at tile step `it` CTA `rank` forms the partial product of the tiles it owns (tile columns j <
+// it with j = rank mod CS for the forward pass, tile rows j > it for the backward pass), the partials are
+// exchanged through distributed shared memory after one cluster barrier, and every CTA applies the stored
+// inverse of the diagonal tile redundantly, so the next step needs no further synchronisation.
+constexpr int SOLVE_CS = 8;
+
+// out[r] = sum_c M[r][c] v[c] for a T x T row-major tile M (global) and v in shared memory; 256 threads,
+// 256 / T threads per row, each a contiguous slice of the row.
+template <typename F, int T>
+__device__ __forceinline__ void tile_matvec(const F* __restrict__ M, const F* v, F* out) {
+  constexpr int PARTS = 256 / T, LEN = T / PARTS;
+  const int r = threadIdx.x / PARTS, part = threadIdx.x - (threadIdx.x / PARTS) * PARTS;
+  const F* row = M + (size_t)r * T + part * LEN;
+  F s = F(0);
+#pragma unroll
+  for (int c = 0; c < LEN; ++c) s += __ldg(row + c) * v[part * LEN + c];
+#pragma unroll
+  for (int d = PARTS / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if (part == 0) out[r] = s;
+}
+
 template <typename F, int T, typename Rreal>
 __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, const F* Dinv, const double* scale,
-                                                   const Rreal* rhs, double* x, int accumulate) {
-  constexpr int RW = T / 8;   // rows per warp
+                                                   const Rreal* rhs, double* x, int accumulate, int64_t v_total) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F* y = reinterpret_cast<F*>(smem_raw);
-  __shared__ F Ds[T][T + 1];
+  __shared__ F partial[2][T];
   __shared__ F t[T];
-  __shared__ F part[8][T];
-  const int k = blockIdx.x;
+  __shared__ F part8[8][T];
+  const int rank = (int)cluster.block_rank();
+  const int k = blockIdx.x / SOLVE_CS;
   const int np = P.cluster_np[k];
   const F* A = L + P.S_off[k];
   const F* Di = Dinv + (size_t)P.v_off[k] * T;
@@ -324,94 +460,102 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   double* xk = x + P.v_off[k];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = np / T;
+  constexpr int RW = T / 8;   // rows per warp within a tile
   for (int i = threadIdx.x; i < np; i += blockDim.x) y[i] = (F)((double)rk[i] * sk[i]);
   __syncthreads();
+  int step = 0;
   // forward: L y = s o rhs
-  for (int it = 0; it < nt; ++it) {
+  for (int it = 0; it < nt; ++it, ++step) {
     const int r0 = it * T;
-    const F* Dt = Di + (size_t)it * T * T;
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) Ds[idx / T][idx - (idx / T) * T] = Dt[idx];
     F acc[RW];
 #pragma unroll
     for (int q = 0; q < RW; ++q) acc[q] = F(0);
-    const F* rows = A + (size_t)(r0 + warp * RW) * np;
-    int c = lane;
-    for (; c + 32 < r0; c += 64) {
-      const F y0 = y[c], y1 = y[c + 32];
+    for (int j = rank; j < it; j += SOLVE_CS) {
+      const F* blk = A + (size_t)(r0 + warp * RW) * np + j * T;
 #pragma unroll
-      for (int q = 0; q < RW; ++q) acc[q] += rows[(size_t)q * np + c] * y0 + rows[(size_t)q * np + c + 32] * y1;
-    }
-    for (; c < r0; c += 32) {
-      const F yc = y[c];
+      for (int cc = 0; cc < T; cc += 32) {
+        const F yc = y[j * T + cc + lane];
 #pragma unroll
-      for (int q = 0; q < RW; ++q) acc[q] += rows[(size_t)q * np + c] * yc;
+        for (int q = 0; q < RW; ++q) acc[q] += blk[(size_t)q * np + cc + lane] * yc;
+      }
     }
 #pragma unroll
     for (int q = 0; q < RW; ++q) {
       const F s = warp_sum(acc[q]);
-      if (lane == 0) t[warp * RW + q] = y[r0 + warp * RW + q] - s;
+      if (lane == 0) partial[step & 1][warp * RW + q] = s;
+    }
+    cluster.sync();
+    for (int r = threadIdx.x; r < T; r += blockDim.x) {
+      F s = F(0);
+#pragma unroll
+      for (int c = 0; c < SOLVE_CS; ++c) s += cluster.map_shared_rank(&partial[step & 1][0], c)[r];
+      t[r] = y[r0 + r] - s;
     }
     __syncthreads();
-    for (int rr = warp; rr < T; rr += 8) {
-      F s = F(0);
-      for (int c = lane; c <= rr; c += 32) s += Ds[rr][c] * t[c];
-      s = warp_sum(s);
-      if (lane == 0) y[r0 + rr] = s;
-    }
+    tile_matvec<F, T>(Di + (size_t)it * T * T, t, y + r0);
     __syncthreads();
   }
   // backward: L^T z = y
-  for (int it = nt - 1; it >= 0; --it) {
+  for (int it = nt - 1; it >= 0; --it, ++step) {
     const int r0 = it * T;
-    const F* Dt = Di + (size_t)it * T * T;
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) Ds[idx / T][idx - (idx / T) * T] = Dt[idx];
-    {
-      constexpr int NC = T / 32;   // columns per lane
-      F p[NC][4];
+    constexpr int NC = T / 32;
+    F p[NC];
 #pragma unroll
-      for (int u = 0; u < NC; ++u)
+    for (int u = 0; u < NC; ++u) p[u] = F(0);
+    for (int j = it + 1 + rank; j < nt; j += SOLVE_CS) {
+      const F* blk = A + (size_t)(j * T) * np + r0;
+#pragma unroll 4
+      for (int rr = warp; rr < T; rr += 8) {
+        const F zc = y[j * T + rr];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) p[u][v] = F(0);
-      int c = r0 + T + warp;
-      for (; c + 24 < np; c += 32) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const F yc = y[c + 8 * v];
-          const F* row = A + (size_t)(c + 8 * v) * np + r0 + lane;
-#pragma unroll
-          for (int u = 0; u < NC; ++u) p[u][v] += row[32 * u] * yc;
-        }
+        for (int u = 0; u < NC; ++u) p[u] += blk[(size_t)rr * np + lane + 32 * u] * zc;
       }
-      for (; c < np; c += 8) {
-        const F yc = y[c];
-        const F* row = A + (size_t)c * np + r0 + lane;
-#pragma unroll
-        for (int u = 0; u < NC; ++u) p[u][0] += row[32 * u] * yc;
-      }
-#pragma unroll
-      for (int u = 0; u < NC; ++u) part[warp][lane + 32 * u] = (p[u][0] + p[u][1]) + (p[u][2] + p[u][3]);
     }
+#pragma unroll
+    for (int u = 0; u < NC; ++u) part8[warp][lane + 32 * u] = p[u];
     __syncthreads();
     for (int cc = threadIdx.x; cc < T; cc += blockDim.x) {
       F s = F(0);
 #pragma unroll
-      for (int w = 0; w < 8; ++w) s += part[w][cc];
-      t[cc] = y[r0 + cc] - s;
+      for (int w = 0; w < 8; ++w) s += part8[w][cc];
+      partial[step & 1][cc] = s;
     }
-    __syncthreads();
-    // z_tile = Dinv^T t: z[c] = sum_{r >= c} Dinv[r][c] t[r]
-    for (int cc = warp; cc < T; cc += 8) {
+    cluster.sync();
+    for (int r = threadIdx.x; r < T; r += blockDim.x) {
       F s = F(0);
-      for (int r = cc + lane; r < T; r += 32) s += Ds[r][cc] * t[r];
-      s = warp_sum(s);
-      if (lane == 0) y[r0 + cc] = s;
+#pragma unroll
+      for (int c = 0; c < SOLVE_CS; ++c) s += cluster.map_shared_rank(&partial[step & 1][0], c)[r];
+      t[r] = y[r0 + r] - s;
     }
     __syncthreads();
+    // z_tile = Dinv^T t through the stored transpose
+    tile_matvec<F, T>(Di + v_total * T + (size_t)it * T * T, t, y + r0);
+    __syncthreads();
   }
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    const double v = (double)y[i] * sk[i];
-    xk[i] = accumulate ? xk[i] + v : v;
-  }
+  if (rank == 0)
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+      const double v = (double)y[i] * sk[i];
+      xk[i] = accumulate ? xk[i] + v : v;
+    }
+  cluster.sync();   // keep this CTA's shared memory alive until every peer has read it
+}
+
+template <typename F, int T, typename Rreal>
+void launch_tri_solve(const DevProblem& P, const F* L, const F* Dinv, const double* scale, const Rreal* rhs,
+                      double* x, int accumulate, int max_np, int64_t v_total, cudaStream_t stream) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(P.l * SOLVE_CS);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = sizeof(F) * (size_t)max_np;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = SOLVE_CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal>, P, L, Dinv, scale, rhs, x, accumulate, v_total);
 }
 
 // r = b - S x (FP64), rows [r0, r0 + 32) of one cluster per CTA; r was set to b before.
@@ -503,7 +647,8 @@ void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];
     if (nu > 0) k_chol_update<F, T><<<nu, 256, 0, stream>>>(L, P, plan.update_items + plan.h_update_off[kt], kt);
   }
-  if (plan.n_diag_items > 0) k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(L, Dinv, P, plan.diag_items);
+  if (plan.n_diag_items > 0)
+    k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(L, Dinv, P, plan.diag_items, fb.v_total);
 }
 
 template <typename F>
@@ -513,13 +658,12 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
   constexpr int T = FactorCfg<F>::T;
   const F* L = reinterpret_cast<const F*>(fb.L);
   const F* Dinv = reinterpret_cast<const F*>(fb.Dinv);
-  const size_t smem = sizeof(F) * (size_t)plan.max_np;
-  k_tri_solve<F, T, Sreal><<<P.l, 256, smem, stream>>>(P, L, Dinv, fb.scale, b, fb.x, 0);
+  launch_tri_solve<F, T, Sreal>(P, L, Dinv, fb.scale, b, fb.x, 0, plan.max_np, fb.v_total, stream);
   const int nblk = (int)std::min<int64_t>(fb.v_total / 256 + 1, 152 * 8);
   for (int s = 0; s < refine_steps; ++s) {
     k_copy_vec<Sreal><<<nblk, 256, 0, stream>>>(b, fb.r, fb.v_total);
     if (plan.n_res_items > 0) k_residual<Sreal><<<plan.n_res_items, 256, 0, stream>>>(P, S, fb.x, fb.r, plan.res_items);
-    k_tri_solve<F, T, double><<<P.l, 256, smem, stream>>>(P, L, Dinv, fb.scale, fb.r, fb.x, 1);
+    launch_tri_solve<F, T, double>(P, L, Dinv, fb.scale, fb.r, fb.x, 1, plan.max_np, fb.v_total, stream);
   }
   k_scatter_dc<<<P.l, 256, 0, stream>>>(P, fb.x, dc);
 }

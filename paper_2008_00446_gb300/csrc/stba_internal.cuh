@@ -138,7 +138,8 @@ struct CholPlan {
 };
 struct FactorBuffers {
   void* L;          // factor (F = float or double), same layout as S'
-  void* Dinv;       // inverses of the diagonal tiles, T x T per tile, v_off[k] * T offset per cluster
+  void* Dinv;       // inverses of the diagonal tiles, T x T per tile, v_off[k] * T offset per cluster;
+                    // their transposes follow at offset v_total * T
   double* scale;    // [v_total] Jacobi scaling s_i = S_ii^-1/2
   double* x;        // [v_total] solution
   double* r;        // [v_total] refinement residual

@@ -285,7 +285,7 @@ void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cuda
 constexpr int GSTRIDE = 32;   // reals per stored G_o (27 used)
 
 template <typename real>
-__global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W, CamLists CL, real* Gbuf,
+__global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real> W, CamLists CL, real* Gbuf,
                                                   const DevState* st) {
   const int j = blockIdx.x;
   const real lam = (real)st->lambda_used;
@@ -310,7 +310,10 @@ __global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W,
     r[0] = res_ptr<real>(P)[2 * (size_t)o];
     r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
     const real* vi = W.vp_info + 9 * (size_t)v;
-    real br[2];
+    // Both cases reduce to Jc^T N Jc with a 2x2 N:
+    //   single observation  N = (I + Jp Lambda^-1 Jp^T)^-1                 (Woodbury, no cancellation)
+    //   several             N = I - Jp V'^-1 Jp^T = I - P^T P, P = L^-1 Jp^T  (V' = L L^T)
+    real N00, N01, N11, br[2];
     if (single) {
       real il[3];
 #pragma unroll
@@ -322,8 +325,43 @@ __global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W,
         K01 += Jp[0][s] * Jp[1][s] * il[s];
         K11 += Jp[1][s] * Jp[1][s] * il[s];
       }
-      const real det = (real(1) + K00) * (real(1) + K11) - K01 * K01;
-      const real N00 = (real(1) + K11) / det, N01 = -K01 / det, N11 = (real(1) + K00) / det;
+      const real idet = real(1) / ((real(1) + K00) * (real(1) + K11) - K01 * K01);
+      N00 = (real(1) + K11) * idet;
+      N01 = -K01 * idet;
+      N11 = (real(1) + K00) * idet;
+      if (corr) {
+        br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
+        br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
+      } else {
+        br[0] = N00 * r[0] + N01 * r[1];
+        br[1] = N01 * r[0] + N11 * r[1];
+      }
+    } else {
+      real Li[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) Li[c] = vi[c];
+      // P = L^-1 Jp^T (3x2)
+      real Pm[3][2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        Pm[0][t] = Li[0] * Jp[t][0];
+        Pm[1][t] = Li[1] * Jp[t][0] + Li[2] * Jp[t][1];
+        Pm[2][t] = Li[3] * Jp[t][0] + Li[4] * Jp[t][1] + Li[5] * Jp[t][2];
+      }
+      N00 = real(1) - (Pm[0][0] * Pm[0][0] + Pm[1][0] * Pm[1][0] + Pm[2][0] * Pm[2][0]);
+      N01 = -(Pm[0][0] * Pm[0][1] + Pm[1][0] * Pm[1][1] + Pm[2][0] * Pm[2][1]);
+      N11 = real(1) - (Pm[0][1] * Pm[0][1] + Pm[1][1] * Pm[1][1] + Pm[2][1] * Pm[2][1]);
+      // G = P^T... stored for the pair pass: G = L^-1 Jp^T Jc = P Jc (3x9)
+      real* Gs = Gbuf + (size_t)GSTRIDE * o;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) Gs[9 * s + c] = Pm[s][0] * Jc[0][c] + Pm[s][1] * Jc[1][c];
+      }
+      br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
+      br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
+    }
+    {
       real NJ[2][9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
@@ -339,44 +377,6 @@ __global__ void __launch_bounds__(256) k_cam_pass(DevProblem P, Scratch<real> W,
           if (i == jj) d += lam * (Jc[0][i] * Jc[0][i] + Jc[1][i] * Jc[1][i]);
           aD[t] += d;
         }
-      if (corr) {
-        br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
-        br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
-      } else {
-        br[0] = N00 * r[0] + N01 * r[1];
-        br[1] = N01 * r[0] + N11 * r[1];
-      }
-    } else {
-      real Li[6];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) Li[c] = vi[c];
-      real G[3][9];
-      real* Gs = Gbuf + (size_t)GSTRIDE * o;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        const real w0 = Jp[0][0] * Jc[0][c] + Jp[1][0] * Jc[1][c];
-        const real w1 = Jp[0][1] * Jc[0][c] + Jp[1][1] * Jc[1][c];
-        const real w2 = Jp[0][2] * Jc[0][c] + Jp[1][2] * Jc[1][c];
-        G[0][c] = Li[0] * w0;
-        G[1][c] = Li[1] * w0 + Li[2] * w1;
-        G[2][c] = Li[3] * w0 + Li[4] * w1 + Li[5] * w2;
-      }
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-#pragma unroll
-        for (int c = 0; c < 9; ++c) Gs[9 * s + c] = G[s][c];
-      int t = 0;
-#pragma unroll
-      for (int i = 0; i < 9; ++i)
-#pragma unroll
-        for (int jj = 0; jj <= i; ++jj, ++t) {
-          const real jjv = Jc[0][i] * Jc[0][jj] + Jc[1][i] * Jc[1][jj];
-          real d = jjv - (G[0][i] * G[0][jj] + G[1][i] * G[1][jj] + G[2][i] * G[2][jj]);
-          if (i == jj) d += lam * jjv;
-          aD[t] += d;
-        }
-      br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
-      br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
