@@ -125,6 +125,33 @@ stba_status stba_set_state(stba_ctx* ctx, double lambda, double F, int64_t itera
 /* The candidate step of the last iteration, accepted or not: dc [m][9], dp [n][3] (FP64). */
 stba_status stba_last_step(stba_ctx* ctx, double* dc, double* dp);
 
+/* Differentiation (the paper has none; the derivative of the solver's executed iterations).
+ *
+ * stba_record(ctx, max_iter) starts a tape: each of the next max_iter LM iterations (stba_lm_iteration,
+ * stba_solve) stores the parameters x_t it starts from ((9m + 3n) FP64 values in device memory, held by
+ * the context) and, after it, its record (damping, accept flag, correction flag), with the cluster
+ * assignment it used.  A further iteration returns STBA_ERR_STATE; stba_record restarts the tape and
+ * max_iter = 0 frees it. */
+stba_status stba_record(stba_ctx* ctx, int32_t max_iter);
+
+/* Reverse-mode derivative of the recorded iterations.  Given the gradient of a loss L at the final
+ * parameters, dL_dcams [m][9] and dL_dpts [n][3] (NULL = zero), writes dL/d obs_uv [q][2] (in the order
+ * given to stba_create), dL/d cameras [m][9] and dL/d points [n][3] at the start of the tape; any output
+ * may be NULL.  FP64 arrays, host or device pointers.
+ * Meaning: the derivative of the executed map x_{t+1} = x_t + Delta_t (accepted steps; a rejected step
+ * is the identity) with the damping, the cluster assignments and the accept flags held at their recorded
+ * values.  Each accepted step is recomputed from its stored x_t with the same kernels and precision as
+ * the forward pass; its adjoint solves with that step's cluster factors (z_c = S'^-1 a^_c, the implicit
+ * derivative of Eq. 10/13), back-substitutes through the virtual points and Eq. 15, and adds the
+ * second-derivative products of the reprojection error.
+ * Errors: STBA_ERR_STATE if nothing was recorded, if stba_set_params replaced the parameters during the
+ * recording, or if an accepted step used the steepest-descent correction (lambda >= correction_lambda,
+ * Sec. 4.3), which this adjoint does not cover.  On return the parameters, the cluster assignment and the
+ * LM state are those before the call.  The call synchronises the stream and allocates, then frees, about
+ * 160 q + 216 m + 72 n bytes of device memory. */
+stba_status stba_adjoint(stba_ctx* ctx, const double* dL_dcams, const double* dL_dpts, double* dL_dobs,
+                         double* dL_dcams0, double* dL_dpts0);
+
 /* Sizes, first n of: m, n, q, l (clusters), nv (virtual points), max cluster dimension 9 n_k, device
  * bytes held, S' pair-pass work items, kernel launches per LM iteration, camera-pair instances
  * (observation pairs of one virtual point), factorisation flops sum_k (9 n_k)^3 / 3, and elements of the

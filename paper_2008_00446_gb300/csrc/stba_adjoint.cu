@@ -1,0 +1,369 @@
+// Adjoint of one accepted STBA step (reverse mode through the executed LM iteration).
+//
+// The paper has no derivative of its solver; the adjoint differentiates the computed map x_{t+1} = x_t + Delta_t
+// with the damping lambda, the cluster assignment and the accept flag held at their forward values.  An
+// accepted step is defined implicitly by the damped, cluster-split normal equations (Eq. 10, Eq. 13):
+//   camera part   Delta c = the camera part of H' dx' = -J'^T f, H' = J'^T J' + lambda diag(J'^T J')
+//                 (virtual points p', one per (point, cluster) pair),
+//   point part    Delta p = C^-1 (w - E^T Delta c) (Eq. 15, physical uncorrected C, E, w).
+// For an upstream adjoint a = (a_c, a_p) of x_{t+1}, with every forward quantity recomputed at x_t:
+//   u   = C^-1 a_p                       a^_c = a_c - E u
+//   z_c = S'^-1 a^_c (same cluster factors as the forward solve)
+//   z_v = -C'_v^-1 E'_v^T z_c            (z' = [z_c; z_v] = H'^-1 [a^_c; 0])
+//   q_bar_o += g_o = J_o (z'_o + U_o)    (f_o = pi_o - q_o, so the observation enters with a minus sign
+//                                         that cancels the one of Delta = -M f)
+//   x_bar = a - sum_o [J_o^T g_o + second-derivative terms]
+// where, per observation, with local 12-vectors (camera 9, point 3) z'_o, dx'_o = [Delta c; Delta p'_v],
+// U_o = [0; u], DP_o = [0; Delta p], DC_o = [Delta c; 0], rho_o = f_o + J_c Delta c, and
+// (alpha, beta) = sum_s alpha_s H_s beta (H_s the Hessian of residual component s), the terms are
+//   (f + J dx', z') + (J z', dx') + (J DP + rho, U) + (J U, DP + DC)
+//   + sum_s (e_s, 2 lambda J[s,:] o (z' o dx' + U o DP))          (the lambda diag(J^T J) damping)
+// The (alpha, beta) products come from the Jacobian evaluated on dual numbers (stba_dual.cuh).
+#include <climits>
+
+#include "stba_camera.cuh"
+#include "stba_device.cuh"
+#include "stba_dual.cuh"
+#include "stba_internal.cuh"
+
+namespace stba {
+
+namespace {
+
+constexpr int ADJ_THREADS = 128;
+
+__device__ __forceinline__ void load_obs64(const DevProblem& P, int o, Cam<double>& C, double X[3], double& uo,
+                                           double& vo) {
+  C = load_cam<double>(P.cams + 9 * (size_t)P.obs_cam[o]);
+  const double* p = P.pts + 3 * (size_t)P.obs_pt[o];
+  X[0] = p[0];
+  X[1] = p[1];
+  X[2] = p[2];
+  const double2 uv = reinterpret_cast<const double2*>(P.obs_uv)[o];
+  uo = uv.x;
+  vo = uv.y;
+}
+
+template <typename real>
+__global__ void k_adj_point_u(int n, const real* __restrict__ pt_info, const double* __restrict__ a_p,
+                              double* __restrict__ u) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const real* in = pt_info + 9 * (size_t)i;   // C^-1, packed symmetric 00 01 02 11 12 22
+    const double* a = a_p + 3 * (size_t)i;
+    const double c00 = in[0], c01 = in[1], c02 = in[2], c11 = in[3], c12 = in[4], c22 = in[5];
+    double* o = u + 3 * (size_t)i;
+    o[0] = c00 * a[0] + c01 * a[1] + c02 * a[2];
+    o[1] = c01 * a[0] + c11 * a[1] + c12 * a[2];
+    o[2] = c02 * a[0] + c12 * a[1] + c22 * a[2];
+  }
+}
+
+// Block sum of NV per-thread values; thread i < NV of the block gets sum i in the return value.
+template <int NV>
+__device__ __forceinline__ double block_sum_to_thread(const double (&v)[NV]) {
+  __shared__ double red[ADJ_THREADS / 32][NV];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(FULL_MASK, x, d);
+    if (lane == 0) red[warp][i] = x;
+  }
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < NV)
+    for (int w = 0; w < ADJ_THREADS / 32; ++w) s += red[w][threadIdx.x];
+  return s;
+}
+
+// a^_c = a_c - E u, one CTA per camera, written into the per-cluster padded vector layout of b'.
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_cam_rhs(DevProblem P, CamLists CL, const double* __restrict__ u,
+                                                             const double* __restrict__ a_c, double* __restrict__ bhat) {
+  const int j = blockIdx.x;
+  double acc[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) acc[i] = 0.0;
+  for (int e = CL.cam_obs_off[j] + threadIdx.x; e < CL.cam_obs_off[j + 1]; e += blockDim.x) {
+    const int o = CL.cam_obs[e];
+    Cam<double> C;
+    double X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
+    load_obs64(P, o, C, X, uo, vo);
+    project_jacobian<double, true>(C, X, uo, vo, r, Jc, Jp);
+    const double* up = u + 3 * (size_t)P.obs_pt[o];
+    const double t0 = Jp[0][0] * up[0] + Jp[0][1] * up[1] + Jp[0][2] * up[2];
+    const double t1 = Jp[1][0] * up[0] + Jp[1][1] * up[1] + Jp[1][2] * up[2];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc[i] += Jc[0][i] * t0 + Jc[1][i] * t1;
+  }
+  const double s = block_sum_to_thread<9>(acc);
+  if (threadIdx.x < 9) {
+    const int k = P.cam_cluster[j], lc = P.cam_local[j];
+    bhat[P.v_off[k] + 9 * lc + threadIdx.x] = a_c[9 * (size_t)j + threadIdx.x] - s;
+  }
+}
+
+// Per observation, warp-segmented by virtual point: E'_v^T z_c and E'_v^T Delta c (3 + 3 sums).
+__global__ void __launch_bounds__(256) k_adj_vp(DevProblem P, const double* __restrict__ zc,
+                                                const double* __restrict__ dc, double* __restrict__ vpz) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = o < P.q;
+  int v = INT_MAX;
+  double val[6] = {0, 0, 0, 0, 0, 0};
+  if (act) {
+    v = P.obs_vp[o];
+    Cam<double> C;
+    double X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
+    load_obs64(P, o, C, X, uo, vo);
+    project_jacobian<double, true>(C, X, uo, vo, r, Jc, Jp);
+    const double* z = zc + 9 * (size_t)P.obs_cam[o];
+    const double* d = dc + 9 * (size_t)P.obs_cam[o];
+    double jz0 = 0, jz1 = 0, jd0 = 0, jd1 = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      jz0 += Jc[0][c] * z[c];
+      jz1 += Jc[1][c] * z[c];
+      jd0 += Jc[0][c] * d[c];
+      jd1 += Jc[1][c] * d[c];
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      val[s] = Jp[0][s] * jz0 + Jp[1][s] * jz1;
+      val[3 + s] = Jp[0][s] * jd0 + Jp[1][s] * jd1;
+    }
+  }
+  segmented_scan<6>(val, v, lane);
+  segmented_store<6>(val, v, act, lane, o, P.vp_off, vpz);
+}
+
+// Per virtual point: z_v = -C'_v^-1 (E'^T z_c)_v and the expanded point step dp'_v = C'_v^-1 (w'_v - (E'^T dc)_v)
+// = y_v - C'_v^-1 (E'^T dc)_v (uncorrected w').
+template <typename real>
+__global__ void k_adj_vp_final(int nv, const real* __restrict__ vp_info, double* __restrict__ vpz) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
+    const real* in = vp_info + 9 * (size_t)v;
+    double Li[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) Li[c] = (double)in[c];
+    double* e = vpz + 6 * (size_t)v;
+    const double e1[3] = {e[0], e[1], e[2]}, e2[3] = {e[3], e[4], e[5]};
+    double x1[3], x2[3];
+    chol3_apply(Li, e1, x1);
+    chol3_apply(Li, e2, x2);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      e[s] = -x1[s];
+      e[3 + s] = (double)in[6 + s] - x2[s];
+    }
+  }
+}
+
+// out += sum_s alpha_s d/de J_s(theta + e beta) (12 entries: camera 9, point 3) for one observation.
+__device__ __forceinline__ void hess_vec(const Cam<double>& C0, const double X0[3], double uo, double vo,
+                                         double al0, double al1, const double beta[12], double out[12]) {
+  Cam<Dual> C;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    C.w[k] = Dual(C0.w[k], beta[k]);
+    C.t[k] = Dual(C0.t[k], beta[3 + k]);
+  }
+  C.f = Dual(C0.f, beta[6]);
+  C.k1 = Dual(C0.k1, beta[7]);
+  C.k2 = Dual(C0.k2, beta[8]);
+  const Dual X[3] = {Dual(X0[0], beta[9]), Dual(X0[1], beta[10]), Dual(X0[2], beta[11])};
+  Dual r[2], Jc[2][9], Jp[2][3];
+  project_jacobian<Dual, true>(C, X, Dual(uo), Dual(vo), r, Jc, Jp);
+#pragma unroll
+  for (int c = 0; c < 9; ++c) out[c] += al0 * Jc[0][c].d + al1 * Jc[1][c].d;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[9 + c] += al0 * Jp[0][c].d + al1 * Jp[1][c].d;
+}
+
+// Per observation: g_o (added to q_bar in input order) and the 12 local terms T_o of x_bar.
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int* __restrict__ perm, double lam,
+                                                         const double* __restrict__ dc, const double* __restrict__ dp,
+                                                         const double* __restrict__ zc, const double* __restrict__ u,
+                                                         const double* __restrict__ vpz, double* __restrict__ T,
+                                                         double* __restrict__ qbar) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= P.q) return;
+  const int cam = P.obs_cam[o], pt = P.obs_pt[o], v = P.obs_vp[o];
+  Cam<double> C;
+  double X[3], uo, vo, f[2], Jc[2][9], Jp[2][3];
+  load_obs64(P, o, C, X, uo, vo);
+  project_jacobian<double, true>(C, X, uo, vo, f, Jc, Jp);
+  double z[12], dx[12], uu[3], dpp[3];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    z[c] = zc[9 * (size_t)cam + c];
+    dx[c] = dc[9 * (size_t)cam + c];
+  }
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    z[9 + s] = vpz[6 * (size_t)v + s];
+    dx[9 + s] = vpz[6 * (size_t)v + 3 + s];
+    uu[s] = u[3 * (size_t)pt + s];
+    dpp[s] = dp[3 * (size_t)pt + s];
+  }
+  // J z', J dx', J U, J DP, rho = f + J_c dc
+  double Jz[2], Jdx[2], JU[2], JDP[2], rho[2];
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    double a = 0, cdc = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      a += Jc[t][c] * z[c];
+      cdc += Jc[t][c] * dx[c];
+    }
+    double pz = 0, pdx = 0, pu = 0, pdp = 0;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      pz += Jp[t][s] * z[9 + s];
+      pdx += Jp[t][s] * dx[9 + s];
+      pu += Jp[t][s] * uu[s];
+      pdp += Jp[t][s] * dpp[s];
+    }
+    Jz[t] = a + pz;
+    Jdx[t] = cdc + pdx;
+    JU[t] = pu;
+    JDP[t] = pdp;
+    rho[t] = f[t] + cdc;
+  }
+  const double g0 = Jz[0] + JU[0], g1 = Jz[1] + JU[1];
+  {
+    double* qb = qbar + 2 * (size_t)perm[o];
+    qb[0] += g0;
+    qb[1] += g1;
+  }
+  double acc[12];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) acc[c] = Jc[0][c] * g0 + Jc[1][c] * g1;
+#pragma unroll
+  for (int s = 0; s < 3; ++s) acc[9 + s] = Jp[0][s] * g0 + Jp[1][s] * g1;
+  // damping weights 2 lambda (z' o dx' + U o DP), times the rows of J below
+  double wdm[12];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) wdm[c] = 2.0 * lam * z[c] * dx[c];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) wdm[9 + s] = 2.0 * lam * (z[9 + s] * dx[9 + s] + uu[s] * dpp[s]);
+  double al0, al1, beta[12];
+#pragma unroll 1
+  for (int dir = 0; dir < 6; ++dir) {
+    switch (dir) {
+      case 0:   // (f + J dx', z')
+        al0 = f[0] + Jdx[0];
+        al1 = f[1] + Jdx[1];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) beta[c] = z[c];
+        break;
+      case 1:   // (J z', dx')
+        al0 = Jz[0];
+        al1 = Jz[1];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) beta[c] = dx[c];
+        break;
+      case 2:   // (J DP + rho, U)
+        al0 = JDP[0] + rho[0];
+        al1 = JDP[1] + rho[1];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) beta[c] = 0.0;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) beta[9 + s] = uu[s];
+        break;
+      case 3:   // (J U, DP + DC)
+        al0 = JU[0];
+        al1 = JU[1];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) beta[c] = dx[c];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) beta[9 + s] = dpp[s];
+        break;
+      default: {   // (e_s, 2 lambda J[s,:] o (z' o dx' + U o DP)), s = dir - 4
+        const int s = dir - 4;
+        al0 = s == 0 ? 1.0 : 0.0;
+        al1 = s == 0 ? 0.0 : 1.0;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) beta[c] = (s == 0 ? Jc[0][c] : Jc[1][c]) * wdm[c];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) beta[9 + k] = (s == 0 ? Jp[0][k] : Jp[1][k]) * wdm[9 + k];
+      }
+    }
+    hess_vec(C, X, uo, vo, al0, al1, beta, acc);
+  }
+  double* To = T + 12 * (size_t)o;
+#pragma unroll
+  for (int c = 0; c < 12; ++c) To[c] = acc[c];
+}
+
+// a_c -= sum_o T_o[0:9] over the camera's observations (one CTA per camera, fixed-order reduction).
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_cam_reduce(CamLists CL, const double* __restrict__ T,
+                                                                double* __restrict__ a_c) {
+  const int j = blockIdx.x;
+  double acc[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) acc[i] = 0.0;
+  for (int e = CL.cam_obs_off[j] + threadIdx.x; e < CL.cam_obs_off[j + 1]; e += blockDim.x) {
+    const double* t = T + 12 * (size_t)CL.cam_obs[e];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) acc[i] += t[i];
+  }
+  const double s = block_sum_to_thread<9>(acc);
+  if (threadIdx.x < 9) a_c[9 * (size_t)j + threadIdx.x] -= s;
+}
+
+// a_p -= sum_o T_o[9:12] over the point's observations (contiguous in the sorted order).
+__global__ void k_adj_pt_reduce(DevProblem P, const double* __restrict__ T, double* __restrict__ a_p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int o = P.pt_off[i]; o < P.pt_off[i + 1]; ++o) {
+      const double* t = T + 12 * (size_t)o + 9;
+      s0 += t[0];
+      s1 += t[1];
+      s2 += t[2];
+    }
+    double* a = a_p + 3 * (size_t)i;
+    a[0] -= s0;
+    a[1] -= s1;
+    a[2] -= s2;
+  }
+}
+
+__global__ void k_adj_set_lambda(DevState* st, double lam) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) st->lambda = lam;
+}
+
+}  // namespace
+
+void launch_set_lambda(DevState* st, double lam, cudaStream_t stream) {
+  k_adj_set_lambda<<<1, 32, 0, stream>>>(st, lam);
+}
+
+template <typename real>
+void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, const FactorBuffers& fb,
+                         const CholPlan& plan, int refine_steps, const int* perm, double lam,
+                         const AdjointBuffers& A, cudaStream_t stream) {
+  const int pblocks = std::min((P.n + 255) / 256, 4096);
+  k_adj_point_u<real><<<pblocks, 256, 0, stream>>>(P.n, W.pt_info, A.a_p, A.u);
+  // a^_c into the padded layout of b' (its padding rows stay zero), then z_c = S'^-1 a^_c
+  int64_t v_total = fb.v_total;
+  cudaMemsetAsync(W.b, 0, (size_t)v_total * sizeof(double), stream);
+  k_adj_cam_rhs<<<P.m, ADJ_THREADS, 0, stream>>>(P, CL, A.u, A.a_c, W.b);
+  launch_solve<real>(P, W.S, W.b, fb, plan, refine_steps, A.zc, stream);
+  cudaMemsetAsync(A.vpz, 0, 6 * (size_t)P.nv * sizeof(double), stream);
+  k_adj_vp<<<(P.q + 255) / 256, 256, 0, stream>>>(P, A.zc, W.dc, A.vpz);
+  k_adj_vp_final<real><<<std::min((P.nv + 255) / 256, 4096), 256, 0, stream>>>(P.nv, W.vp_info, A.vpz);
+  k_adj_obs<<<(P.q + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, stream>>>(P, perm, lam, W.dc, W.dp, A.zc, A.u,
+                                                                             A.vpz, A.T, A.qbar);
+  k_adj_cam_reduce<<<P.m, ADJ_THREADS, 0, stream>>>(CL, A.T, A.a_c);
+  k_adj_pt_reduce<<<pblocks, 256, 0, stream>>>(P, A.T, A.a_p);
+}
+
+template void launch_adjoint_step<float>(const DevProblem&, Scratch<float>, CamLists, const FactorBuffers&,
+                                         const CholPlan&, int, const int*, double, const AdjointBuffers&,
+                                         cudaStream_t);
+template void launch_adjoint_step<double>(const DevProblem&, Scratch<double>, CamLists, const FactorBuffers&,
+                                          const CholPlan&, int, const int*, double, const AdjointBuffers&,
+                                          cudaStream_t);
+
+}  // namespace stba

@@ -81,6 +81,16 @@ struct stba_ctx {
   void *res_cur = nullptr, *res_cand = nullptr;   // residuals at x and at x + dx (working precision)
   DevState* st = nullptr;
 
+  // tape of recorded iterations for stba_adjoint: x_t before every iteration, its record after it, and
+  // the cluster assignment it used
+  int tape_cap = 0, tape_len = 0;
+  bool tape_broken = false;             // parameters or damping were replaced between recorded iterations
+  double* tape_x = nullptr;             // [tape_cap][9m + 3n]
+  stba_iter_info* tape_info = nullptr;  // [tape_cap]
+  std::vector<int> tape_cluster_id;     // per recorded iteration, index into tape_clusters
+  std::vector<std::vector<int>> tape_clusters;
+  std::vector<void*> tape_allocs;
+
   // graph / timing
   cudaGraphExec_t graph = nullptr;
   bool capturing = false;
@@ -123,6 +133,19 @@ stba_status dalloc(stba_ctx* c, T** p, size_t count, bool cluster_scope) {
   }
   (cluster_scope ? c->cl_allocs : c->allocs).push_back((void*)*p);
   (cluster_scope ? c->bytes_cl : c->bytes_base) += bytes;
+  return STBA_OK;
+}
+
+template <typename T>
+stba_status dalloc_into(stba_ctx* c, T** p, size_t count, std::vector<void*>& list) {
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  cudaError_t e = cudaMalloc((void**)p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(c, STBA_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  list.push_back((void*)*p);
   return STBA_OK;
 }
 
@@ -457,13 +480,18 @@ void record_stage(stba_ctx* c, int i) {
   cudaEventRecordWithFlags(c->ev[i], c->stream, c->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
+// The LM step at the current parameters and c->st->lambda: S', the cluster factors, dc and dp (stages 0-3
+// and the point update of Algorithm 1).  With stages, records the stage events 0..4.
 template <typename real>
-void enqueue_iteration(stba_ctx* c) {
+void enqueue_step(stba_ctx* c, bool stages) {
   const DevProblem P = dev_problem(c);
   const Scratch<real> W = scratch<real>(c);
   cudaStream_t s = c->stream;
   const size_t rs = sizeof(real);
-  record_stage(c, 0);
+  auto mark = [&](int i) {
+    if (stages) record_stage(c, i);
+  };
+  mark(0);
   // stage 0: linearisation and virtual points
   launch_iter_begin<real>(c->st, c->set, s);
   cudaMemsetAsync(c->vp_acc, 0, 9 * (size_t)c->nv * rs, s);
@@ -474,20 +502,28 @@ void enqueue_iteration(stba_ctx* c) {
   cudaMemsetAsync(c->fail_flags, 0, (size_t)c->l * sizeof(int), s);
   launch_vp_reduce<real>(P, W, s);
   launch_vp_finalize<real>(P, W, c->st, s);
-  record_stage(c, 1);
+  mark(1);
   // stage 1: S' and b'
   launch_rcs_build<real>(P, W, c->clist, c->plist, (real*)c->Gbuf, c->st, s);
-  record_stage(c, 2);
+  mark(2);
   // stage 2: factorisation (FP32 factor in mixed mode, FP64 factor in FP64 mode)
   launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
-  record_stage(c, 3);
+  mark(3);
   // stage 3: cluster solves with FP64 refinement
   launch_solve<real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, s);
   launch_count_failures(c->fail_flags, c->l, c->st, s);
-  record_stage(c, 4);
+  mark(4);
   // stage 4: points, cost, control
   launch_point_rhs<real>(P, W, s);
   launch_point_update<real>(P, W, s);
+}
+
+template <typename real>
+void enqueue_iteration(stba_ctx* c) {
+  const DevProblem P = dev_problem(c);
+  const Scratch<real> W = scratch<real>(c);
+  cudaStream_t s = c->stream;
+  enqueue_step<real>(c, true);
   launch_cost<real>(P, c->dc, c->dp, c->cam_rt, c->partial, c->st, (real*)c->res_cand, s);
   launch_finalize<real>(P, W, c->st, c->set, 1, s);
   launch_apply<real>(P, c->dc, c->dp, c->cams, c->pts, (const real*)c->res_cand, (real*)c->res_cur, c->st, s);
@@ -519,7 +555,7 @@ stba_status run_cost(stba_ctx* c, double* F) {
   return STBA_OK;
 }
 
-stba_status run_iteration(stba_ctx* c) {
+stba_status launch_iteration(stba_ctx* c) {
   if (!c->opt.use_graph) {
     if (c->mixed)
       enqueue_iteration<float>(c);
@@ -554,6 +590,48 @@ stba_status run_iteration(stba_ctx* c) {
   CK(cudaGraphLaunch(c->graph, c->stream));
   c->have_stage_times = true;
   return STBA_OK;
+}
+
+// One LM iteration; while recording, x_t goes to the tape before it and its record after it (both are
+// device-to-device copies on the context stream, outside the captured graph).
+stba_status run_iteration(stba_ctx* c) {
+  if (c->tape_cap == 0) return launch_iteration(c);
+  if (c->tape_len >= c->tape_cap)
+    return fail(c, STBA_ERR_STATE, "the tape holds %d iterations; call stba_record again to restart it", c->tape_cap);
+  const size_t nx = 9 * (size_t)c->m + 3 * (size_t)c->n;
+  double* slot = c->tape_x + nx * (size_t)c->tape_len;
+  CK(cudaMemcpyAsync(slot, c->cams, 9 * (size_t)c->m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(slot + 9 * (size_t)c->m, c->pts, 3 * (size_t)c->n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  stba_status s = launch_iteration(c);
+  if (s != STBA_OK) return s;
+  CK(cudaMemcpyAsync(c->tape_info + c->tape_len, &c->st->info, sizeof(stba_iter_info), cudaMemcpyDeviceToDevice,
+                     c->stream));
+  if (c->tape_clusters.empty() || c->tape_clusters.back() != c->h_clusters) c->tape_clusters.push_back(c->h_clusters);
+  c->tape_cluster_id.push_back((int)c->tape_clusters.size() - 1);
+  c->tape_len++;
+  return STBA_OK;
+}
+
+void free_tape(stba_ctx* c) {
+  free_list(c, c->tape_allocs);
+  c->tape_x = nullptr;
+  c->tape_info = nullptr;
+  c->tape_cap = c->tape_len = 0;
+  c->tape_broken = false;
+  c->tape_clusters.clear();
+  c->tape_cluster_id.clear();
+}
+
+template <typename real>
+void enqueue_adjoint_step(stba_ctx* c, double lam, const AdjointBuffers& A) {
+  // recompute the forward step at x_t with the recorded damping, then its adjoint
+  launch_set_lambda(c->st, lam, c->stream);
+  launch_iter_begin<real>(c->st, c->set, c->stream);
+  const DevProblem P = dev_problem(c);
+  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, c->partial, c->st, (real*)c->res_cur, c->stream);
+  enqueue_step<real>(c, false);
+  launch_adjoint_step<real>(P, scratch<real>(c), c->clist, c->fbuf, c->cplan, c->set.refine_steps, c->obs_perm, lam,
+                            A, c->stream);
 }
 
 stba_status read_info(stba_ctx* c, stba_iter_info* info) {
@@ -611,6 +689,7 @@ void stba_destroy(stba_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   free_list(c, c->cl_allocs);
   free_list(c, c->allocs);
+  free_list(c, c->tape_allocs);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -804,6 +883,7 @@ stba_status stba_get_params(stba_ctx* c, double* cameras, double* points) {
 
 stba_status stba_set_params(stba_ctx* c, const double* cameras, const double* points) {
   if (!c) return STBA_ERR_INVALID_ARG;
+  if (c->tape_len > 0) c->tape_broken = true;
   if (cameras) {
     CK(cudaMemcpyAsync(c->cams, cameras, 9 * (size_t)c->m * 8,
                        is_device_ptr(cameras) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
@@ -846,6 +926,110 @@ stba_status stba_last_step(stba_ctx* c, double* dc, double* dp) {
   if (dc && (s = copy_out(c, dc, c->dc, 9 * (size_t)c->m * 8)) != STBA_OK) return s;
   if (dp && (s = copy_out(c, dp, c->dp, 3 * (size_t)c->n * 8)) != STBA_OK) return s;
   return STBA_OK;
+}
+
+stba_status stba_record(stba_ctx* c, int32_t max_iter) {
+  if (!c || max_iter < 0) return STBA_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  free_tape(c);
+  if (max_iter == 0) return STBA_OK;
+  const size_t nx = 9 * (size_t)c->m + 3 * (size_t)c->n;
+  stba_status s;
+  if ((s = dalloc_into(c, &c->tape_x, nx * (size_t)max_iter, c->tape_allocs)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &c->tape_info, (size_t)max_iter, c->tape_allocs)) != STBA_OK) {
+    free_tape(c);
+    return s;
+  }
+  c->tape_cap = max_iter;
+  return STBA_OK;
+}
+
+stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_dpts, double* dL_dobs,
+                         double* dL_dcams0, double* dL_dpts0) {
+  if (!c || !dL_dcams) return STBA_ERR_INVALID_ARG;
+  if (c->tape_len == 0) return fail(c, STBA_ERR_STATE, "no recorded iteration (call stba_record before iterating)");
+  if (c->tape_broken)
+    return fail(c, STBA_ERR_STATE, "the parameters were replaced between recorded iterations; record again");
+  const int T = c->tape_len;
+  const int64_t m = c->m, n = c->n, q = c->q;
+  std::vector<stba_iter_info> info(T);
+  CK(cudaMemcpyAsync(info.data(), c->tape_info, T * sizeof(stba_iter_info), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int t = 0; t < T; ++t)
+    if (info[t].accepted && info[t].corrected)
+      return fail(c, STBA_ERR_STATE,
+                  "recorded iteration %d was accepted with the steepest-descent correction (lambda %g >= %g); the "
+                  "adjoint covers uncorrected steps", t, info[t].lambda_used, c->set.correction_lambda);
+  // adjoint buffers and the saved final state, freed on every return path
+  struct Guard {
+    stba_ctx* c;
+    std::vector<void*> list;
+    ~Guard() {
+      cudaStreamSynchronize(c->stream);
+      free_list(c, list);
+    }
+  } g{c, {}};
+  AdjointBuffers A{};
+  double* save_x = nullptr;
+  stba_status s;
+  const size_t nx = 9 * (size_t)m + 3 * (size_t)n;
+  if ((s = dalloc_into(c, &A.a_c, 9 * (size_t)m, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &A.a_p, 3 * (size_t)n, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &A.u, 3 * (size_t)n, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &A.zc, 9 * (size_t)m, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &A.vpz, 6 * (size_t)q, g.list)) != STBA_OK) return s;   // nv <= q
+  if ((s = dalloc_into(c, &A.T, 12 * (size_t)q, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &A.qbar, 2 * (size_t)q, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &save_x, nx, g.list)) != STBA_OK) return s;
+  DevState saved;
+  CK(cudaMemcpyAsync(&saved, c->st, sizeof saved, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(save_x, c->cams, 9 * (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(save_x + 9 * m, c->pts, 3 * (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(A.a_c, dL_dcams, 9 * (size_t)m * 8, cudaMemcpyDefault, c->stream));
+  if (dL_dpts) {
+    CK(cudaMemcpyAsync(A.a_p, dL_dpts, 3 * (size_t)n * 8, cudaMemcpyDefault, c->stream));
+  } else {
+    CK(cudaMemsetAsync(A.a_p, 0, 3 * (size_t)n * 8, c->stream));
+  }
+  CK(cudaMemsetAsync(A.qbar, 0, 2 * (size_t)q * 8, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const std::vector<int> final_clusters = c->h_clusters;
+  auto reverse_pass = [&]() -> stba_status {
+    stba_status s2;
+    for (int t = T - 1; t >= 0; --t) {
+      if (!info[t].accepted) continue;   // a rejected step leaves x unchanged: the adjoint passes through
+      const std::vector<int>& cl = c->tape_clusters[c->tape_cluster_id[t]];
+      if (cl != c->h_clusters && (s2 = set_clusters_host(c, cl)) != STBA_OK) return s2;
+      const double* slot = c->tape_x + nx * (size_t)t;
+      CK(cudaMemcpyAsync(c->cams, slot, 9 * (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(c->pts, slot + 9 * m, 3 * (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
+      if (c->mixed)
+        enqueue_adjoint_step<float>(c, info[t].lambda_used, A);
+      else
+        enqueue_adjoint_step<double>(c, info[t].lambda_used, A);
+      CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    // outputs (qbar is in the input order of the observations)
+    if (dL_dcams0) CK(cudaMemcpyAsync(dL_dcams0, A.a_c, 9 * (size_t)m * 8, cudaMemcpyDefault, c->stream));
+    if (dL_dpts0) CK(cudaMemcpyAsync(dL_dpts0, A.a_p, 3 * (size_t)n * 8, cudaMemcpyDefault, c->stream));
+    if (dL_dobs) CK(cudaMemcpyAsync(dL_dobs, A.qbar, 2 * (size_t)q * 8, cudaMemcpyDefault, c->stream));
+    return STBA_OK;
+  };
+  const stba_status s_pass = reverse_pass();
+  const std::string pass_err = c->err;
+  // restore the final state on every path: clusters, parameters, their residuals, and the LM state
+  if (final_clusters != c->h_clusters && (s = set_clusters_host(c, final_clusters)) != STBA_OK) return s;
+  CK(cudaMemcpyAsync(c->cams, save_x, 9 * (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemcpyAsync(c->pts, save_x + 9 * m, 3 * (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  s = run_cost(c, nullptr);
+  CK(cudaMemcpyAsync(c->st, &saved, sizeof saved, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (s_pass != STBA_OK) {
+    c->err = pass_err;
+    return s_pass;
+  }
+  return s;
 }
 
 stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {

@@ -20,6 +20,13 @@ template <typename real> struct RodSeries;
 template <> struct RodSeries<double> { static constexpr double cut = 1e-4; };
 template <> struct RodSeries<float> { static constexpr float cut = 1e-1f; };
 
+// sqrt and sincos in the working precision; rodrigues_coeffs calls them unqualified, so other number
+// types (the dual numbers of the adjoint) supply their own overloads, found by argument-dependent lookup.
+__device__ __forceinline__ float sq_root(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sq_root(double x) { return sqrt(x); }
+__device__ __forceinline__ void sin_cos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sin_cos(double x, double* s, double* c) { sincos(x, s, c); }
+
 template <typename real>
 __device__ __forceinline__ void rodrigues_coeffs(real s, real& a, real& b, real& da, real& db) {
   if (s < RodSeries<real>::cut) {
@@ -29,15 +36,10 @@ __device__ __forceinline__ void rodrigues_coeffs(real s, real& a, real& b, real&
     da = -real(1) / 6 + s * (real(1) / 60 - s * (real(1) / 1680 - s * (real(1) / 90720)));
     db = -real(1) / 24 + s * (real(1) / 360 - s * (real(1) / 13440 - s * (real(1) / 907200)));
   } else {
-    real th = sqrt(s);
+    real th = sq_root(s);
     real sn, cs, sh, ch;
-    if constexpr (sizeof(real) == 8) {
-      sincos(th, &sn, &cs);
-      sincos(real(0.5) * th, &sh, &ch);
-    } else {
-      sincosf(th, &sn, &cs);
-      sincosf(real(0.5) * th, &sh, &ch);
-    }
+    sin_cos(th, &sn, &cs);
+    sin_cos(real(0.5) * th, &sh, &ch);
     a = sn / th;
     b = real(2) * sh * sh / s;
     da = (cs - a) / (real(2) * s);

@@ -156,4 +156,23 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
                   const CholPlan& plan, int refine_steps, double* dc, cudaStream_t stream);
 void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStream_t stream);
 
+// Adjoint of one accepted step (stba_adjoint.cu).  With the forward step at x_t recomputed in W and fb
+// (dc, dp, vp_info, pt_info, S', the cluster factors), maps the upstream adjoint (a_c, a_p) of x_{t+1} in
+// place to that of x_t and adds the observation adjoint to qbar, indexed by input order through perm.
+// W.b is overwritten (it carries the right-hand side of the adjoint cluster solve).
+struct AdjointBuffers {
+  double* a_c;    // [m][9] in / out
+  double* a_p;    // [n][3] in / out
+  double* u;      // [n][3] C^-1 a_p
+  double* zc;     // [m][9] S'^-1 a^_c
+  double* vpz;    // [nv][6] z_v and the expanded point step of every virtual point
+  double* T;      // [q][12] per-observation terms
+  double* qbar;   // [q][2] observation adjoint, input order
+};
+template <typename real>
+void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, const FactorBuffers& fb,
+                         const CholPlan& plan, int refine_steps, const int* perm, double lam,
+                         const AdjointBuffers& A, cudaStream_t stream);
+void launch_set_lambda(DevState* st, double lam, cudaStream_t stream);
+
 }  // namespace stba

@@ -19,66 +19,10 @@
 #include <climits>
 
 #include "stba_camera.cuh"
+#include "stba_device.cuh"
 #include "stba_internal.cuh"
 
 namespace stba {
-
-#define FULL_MASK 0xffffffffu
-
-template <typename real>
-__device__ __forceinline__ void load_uv(const DevProblem& P, int o, real& u, real& v) {
-  if constexpr (sizeof(real) == 8) {
-    double2 t = reinterpret_cast<const double2*>(P.obs_uv)[o];
-    u = t.x;
-    v = t.y;
-  } else {
-    float2 t = reinterpret_cast<const float2*>(P.obs_uvf)[o];
-    u = t.x;
-    v = t.y;
-  }
-}
-
-template <typename real>
-__device__ __forceinline__ void load_point(const double* p, real X[3]) {
-  X[0] = (real)p[0];
-  X[1] = (real)p[1];
-  X[2] = (real)p[2];
-}
-
-// Inclusive warp scan of NV values restricted to runs of equal (non-decreasing) keys.
-template <int NV, typename real>
-__device__ __forceinline__ void segmented_scan(real (&val)[NV], int key, int lane) {
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    int ku = __shfl_up_sync(FULL_MASK, key, d);
-#pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      real y = __shfl_up_sync(FULL_MASK, val[c], d);
-      if (lane >= d && ku == key) val[c] += y;
-    }
-  }
-}
-
-// The last lane of each run writes the run's sum.  A run lying wholly inside this warp's 32
-// observations is stored; a run that continues into a neighbouring warp is added atomically
-// (the destination was zeroed before the launch).
-template <int NV, typename real>
-__device__ __forceinline__ void segmented_store(const real (&val)[NV], int key, bool act, int lane, int o,
-                                                const int* seg_off, real* dst_base) {
-  int knext = __shfl_down_sync(FULL_MASK, key, 1);
-  if (act && (lane == 31 || knext != key)) {
-    int w0 = o - lane;
-    bool whole = seg_off[key] >= w0 && seg_off[key + 1] <= w0 + 32;
-    real* dst = dst_base + (size_t)NV * key;
-    if (whole) {
-#pragma unroll
-      for (int c = 0; c < NV; ++c) dst[c] = val[c];
-    } else {
-#pragma unroll
-      for (int c = 0; c < NV; ++c) atomicAdd(dst + c, val[c]);
-    }
-  }
-}
 
 // ------------------------------------------------------------------------------------------------------
 template <typename real>
@@ -141,44 +85,6 @@ void launch_vp_reduce(const DevProblem& P, Scratch<real> W, cudaStream_t stream)
 }
 
 // ------------------------------------------------------------------------------------------------------
-// 3x3 symmetric positive-definite helpers (packed lower/symmetric storage xx xy xz yy yz zz).
-template <typename real>
-__device__ __forceinline__ real safe_pivot(real d) {
-  return d > real(0) ? d : (real)(sizeof(real) == 8 ? 1e-300 : 1e-30);
-}
-
-// Cholesky V = L L^T and the inverse of L (packed l00 l10 l11 l20 l21 l22).
-template <typename real>
-__device__ __forceinline__ void chol3_inv(const real V[6], real Li[6]) {
-  real l00 = sqrt(safe_pivot(V[0]));
-  real l10 = V[1] / l00;
-  real l20 = V[2] / l00;
-  real l11 = sqrt(safe_pivot(V[3] - l10 * l10));
-  real l21 = (V[4] - l20 * l10) / l11;
-  real l22 = sqrt(safe_pivot(V[5] - l20 * l20 - l21 * l21));
-  real i00 = real(1) / l00, i11 = real(1) / l11, i22 = real(1) / l22;
-  real i10 = -l10 * i00 * i11;
-  real i21 = -l21 * i11 * i22;
-  real i20 = -(l20 * i00 + l21 * i10) * i22;
-  Li[0] = i00;
-  Li[1] = i10;
-  Li[2] = i11;
-  Li[3] = i20;
-  Li[4] = i21;
-  Li[5] = i22;
-}
-
-// x = (L L^T)^-1 w = L^-T (L^-1 w)
-template <typename real>
-__device__ __forceinline__ void chol3_apply(const real Li[6], const real w[3], real x[3]) {
-  real z0 = Li[0] * w[0];
-  real z1 = Li[1] * w[0] + Li[2] * w[1];
-  real z2 = Li[3] * w[0] + Li[4] * w[1] + Li[5] * w[2];
-  x[0] = Li[0] * z0 + Li[1] * z1 + Li[3] * z2;
-  x[1] = Li[2] * z1 + Li[4] * z2;
-  x[2] = Li[5] * z2;
-}
-
 template <typename real>
 __device__ __forceinline__ double block_max(double v) {
   __shared__ double red[32];

@@ -23,7 +23,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device mem
 EXPORTS = ["stba_default_options", "stba_create", "stba_set_clusters", "stba_lm_iteration", "stba_solve",
            "stba_cost", "stba_get_params", "stba_set_params", "stba_get_state", "stba_set_state",
            "stba_last_step", "stba_problem_info", "stba_get_cluster_system", "stba_set_timing",
-           "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error", "stba_cost_noalloc"]
+           "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error", "stba_cost_noalloc",
+           "stba_record", "stba_adjoint"]
 
 
 class StbaOptions(ctypes.Structure):
@@ -90,6 +91,8 @@ def load(build_if_missing: bool = True):
         "stba_status_string": (ctypes.c_char_p, [I32]),
         "stba_last_error": (ctypes.c_char_p, [P]),
         "stba_cost_noalloc": (I32, [P, I64, P, I64, P, P, P, I64, P, P]),
+        "stba_record": (I32, [P, I32]),
+        "stba_adjoint": (I32, [P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -288,6 +291,38 @@ def stba_cost_noalloc(cameras, points, obs_cam, obs_pt, obs_uv, F_out, stream=No
         raise StbaError(st, "stba_cost_noalloc failed")
 
 
+def stba_record(ctx: Context, max_iter: int):
+    """Start (or restart, or with 0 free) the tape of the next `max_iter` iterations for stba_adjoint."""
+    ctx._check(load().stba_record(ctx.handle, int(max_iter)))
+
+
+def stba_adjoint(ctx: Context, dL_dcams, dL_dpts=None):
+    """Reverse-mode derivative of the recorded iterations.  Returns (dL/d obs_uv [q][2] in input order,
+    dL/d cameras0 [m][9], dL/d points0 [n][3]) as float64 arrays: CUDA tensors on the device of dL_dcams
+    when it is a CUDA tensor, NumPy arrays otherwise."""
+    keep = []
+    pc = _ptr(dL_dcams, np.float64, keep)
+    pp = _ptr(dL_dpts, np.float64, keep) if dL_dpts is not None else None
+    on_cuda = False
+    try:
+        import torch
+        on_cuda = isinstance(dL_dcams, torch.Tensor) and dL_dcams.is_cuda
+    except ImportError:
+        pass
+    if on_cuda:
+        import torch
+        dev = dL_dcams.device
+        gq = torch.empty((ctx.q, 2), dtype=torch.float64, device=dev)
+        gc = torch.empty((ctx.m, 9), dtype=torch.float64, device=dev)
+        gp = torch.empty((ctx.n, 3), dtype=torch.float64, device=dev)
+        ptrs = [ctypes.c_void_p(t.data_ptr()) for t in (gq, gc, gp)]
+    else:
+        gq, gc, gp = np.empty((ctx.q, 2)), np.empty((ctx.m, 9)), np.empty((ctx.n, 3))
+        ptrs = [ctypes.c_void_p(a.ctypes.data) for a in (gq, gc, gp)]
+    ctx._check(load().stba_adjoint(ctx.handle, pc, pp, *ptrs))
+    return gq, gc, gp
+
+
 def stba_destroy(ctx: Context):
     ctx.close()
 
@@ -302,3 +337,59 @@ def _data_ptr(a):
         pass
     assert isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.float64
     return a.ctypes.data
+
+
+# ----------------------------------------------------------------------------------------------------------
+# autograd
+# ----------------------------------------------------------------------------------------------------------
+def _autograd_function():
+    import torch
+
+    class STBAFunction(torch.autograd.Function):
+        """(cameras_K, points_K) = K STBA LM iterations from (cameras0, points0) on the observations obs_uv.
+
+        forward: one context, a tape of K iterations (the cluster assignment of iteration t is
+        cluster_seq[t], or cluster_seq itself when it is one assignment).  backward: stba_adjoint, the
+        derivative with the damping, clusters and accept flags of the forward run held fixed.  Gradients
+        come back in the dtype of each input."""
+
+        @staticmethod
+        def forward(fctx, cameras0, points0, obs_uv, obs_cam, obs_pt, cluster_seq, iters, options):
+            seq = cluster_seq
+            per_iter = getattr(seq, "ndim", 1) == 2
+            first = seq[0] if per_iter else seq
+            sctx = stba_create(cameras0, points0, obs_cam, obs_pt, obs_uv, first, options=options)
+            stba_record(sctx, int(iters))
+            for t in range(int(iters)):
+                if per_iter and t > 0:
+                    stba_set_clusters(sctx, seq[t])
+                stba_lm_iteration(sctx, want_info=False)
+            dev = cameras0.device
+            cams = torch.empty((sctx.m, 9), dtype=torch.float64, device=dev)
+            pts = torch.empty((sctx.n, 3), dtype=torch.float64, device=dev)
+            stba_get_params(sctx, cams, pts)
+            fctx.stba = sctx
+            fctx.dtypes = (cameras0.dtype, points0.dtype, obs_uv.dtype)
+            return cams.to(cameras0.dtype), pts.to(points0.dtype)
+
+        @staticmethod
+        def backward(fctx, g_cams, g_pts):
+            dev = g_cams.device if g_cams is not None else g_pts.device
+            gc_in = (g_cams if g_cams is not None else torch.zeros((fctx.stba.m, 9), device=dev)).to(torch.float64)
+            gp_in = g_pts.to(torch.float64) if g_pts is not None else None
+            gq, gc, gp = stba_adjoint(fctx.stba, gc_in.contiguous(), gp_in.contiguous() if gp_in is not None else None)
+            tc, tp, tq = fctx.dtypes
+            return gc.to(tc), gp.to(tp), gq.to(tq), None, None, None, None, None
+
+    return STBAFunction
+
+
+def stba_differentiable(cameras0, points0, obs_uv, obs_cam, obs_pt, cluster_seq, iters, options=None):
+    """K STBA iterations as a differentiable function of (cameras0, points0, obs_uv) (torch tensors)."""
+    global _STBA_FN
+    if _STBA_FN is None:
+        _STBA_FN = _autograd_function()
+    return _STBA_FN.apply(cameras0, points0, obs_uv, obs_cam, obs_pt, cluster_seq, iters, options)
+
+
+_STBA_FN = None
