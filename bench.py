@@ -189,6 +189,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the full-RCS LM comparison")
     ap.add_argument("--compare-iters", type=int, default=20)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on the 500-camera scene")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -301,6 +302,8 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_compare:
         out["full_rcs"] = compare_full_rcs(s, stba, stream, args.compare_iters, torch)
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        out["adjoint"] = time_adjoint(stba, stream, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t = run_oracle(args.config, 1)
         v = 1.0 / t["seconds"]
@@ -358,6 +361,41 @@ def compare_full_rcs(s, stba, stream, iters, torch):
            "stba_time_to_target_ms": (st["cum_ms"][hit[0]] if hit else None),
            "stba_iters_to_target": (hit[0] + 1 if hit else None)}
     return out
+
+
+def time_adjoint(stba, stream, torch, reps=3):
+    """The differentiable configuration: 500 cameras, 50k points (about 280k observations), 5 recorded
+    STBA iterations in mixed precision, then stba_adjoint of the camera-centre loss (recomputes each
+    accepted step and runs the adjoint kernels).  Medians over `reps` runs after one warm-up."""
+    import numpy as np
+
+    import scenes
+    s = scenes.make_config("c3_diff")
+    iters = scenes.CONFIGS["c3_diff"][3]
+    rng = np.random.default_rng(7)
+    a_c = torch.tensor(rng.normal(0, 1, (s.m, 9)), device="cuda")
+    fw, bw, acc = [], [], []
+    for r in range(reps + 1):
+        ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                               precision=stba.STBA_MIXED, stream=stream)
+        stba.stba_record(ctx, iters)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(iters):
+            stba.stba_lm_iteration(ctx, want_info=False)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        stba.stba_adjoint(ctx, a_c)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        stba.stba_destroy(ctx)
+        if r > 0:
+            fw.append(t1 - t0)
+            bw.append(t2 - t1)
+    return {"workload": "c3_diff: 500 cameras, 50k points, Zipf(2) tracks on [2,50], 5 clusters, mixed precision",
+            "observations": int(s.q), "iterations": iters, "forward_ms": 1e3 * float(np.median(fw)),
+            "adjoint_ms": 1e3 * float(np.median(bw)),
+            "timing": "host wall clock around synchronous calls (the adjoint call allocates and frees its buffers)"}
 
 
 if __name__ == "__main__":

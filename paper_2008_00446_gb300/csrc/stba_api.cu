@@ -67,6 +67,7 @@ struct stba_ctx {
   int *cluster_np = nullptr, *cluster_n = nullptr;
   int64_t *S_off = nullptr, *v_off = nullptr;
   CamLists clist{};
+  CamSlots cslots{};
   PairLists plist{};
   void* Gbuf = nullptr;
   int64_t n_pairs = 0;
@@ -344,6 +345,19 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
         if (single == (pass == 0)) cam_obs[f[s_cam[o]]++] = o;
       }
   }
+  // the same lists padded to whole warps (32 slots, -1 = padding) for the camera pass
+  std::vector<int> cam_slots, warp_cam;
+  for (int j = 0; j < m; ++j) {
+    const int cnt_j = cam_obs_off[j + 1] - cam_obs_off[j];
+    const int nw = (cnt_j + 31) / 32;
+    for (int w = 0; w < nw; ++w) {
+      warp_cam.push_back(j);
+      for (int l = 0; l < 32; ++l) {
+        const int e = 32 * w + l;
+        cam_slots.push_back(e < cnt_j ? cam_obs[cam_obs_off[j] + e] : -1);
+      }
+    }
+  }
   // camera-pair instances of the pair pass, sorted by (cluster, la, lb): inside a virtual point the
   // observations are ordered by camera, so a later observation has the larger local camera index
   int64_t npairs = 0;
@@ -423,11 +437,13 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(c->cluster_n, c->h_nk);
   UP(c->S_off, c->h_S_off);
   UP(c->v_off, c->h_v_off);
-  int *d_cam_obs_off, *d_cam_obs;
+  int *d_cam_obs_off, *d_cam_obs, *d_cam_slots, *d_warp_cam;
   int4* d_pairs;
   UP(d_pairs, pairs);
   UP(d_cam_obs_off, cam_obs_off);
   UP(d_cam_obs, cam_obs);
+  UP(d_cam_slots, cam_slots);
+  UP(d_warp_cam, warp_cam);
   int2 *d_panel, *d_update, *d_res, *d_diag;
   UP(d_panel, panel);
   UP(d_update, update);
@@ -436,6 +452,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
 #undef UP
   c->plist = PairLists{d_pairs, (int)npairs};
   c->clist = CamLists{d_cam_obs_off, d_cam_obs};
+  c->cslots = CamSlots{d_cam_slots, d_warp_cam, (int)warp_cam.size()};
   c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
                       c->h_panel_off.data(), c->h_update_off.data(), c->max_np};
 
@@ -504,7 +521,7 @@ void enqueue_step(stba_ctx* c, bool stages) {
   launch_vp_finalize<real>(P, W, c->st, s);
   mark(1);
   // stage 1: S' and b'
-  launch_rcs_build<real>(P, W, c->clist, c->plist, (real*)c->Gbuf, c->st, s);
+  launch_rcs_build<real>(P, W, c->cslots, c->plist, (real*)c->Gbuf, c->st, s);
   mark(2);
   // stage 2: factorisation (FP32 factor in mixed mode, FP64 factor in FP64 mode)
   launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);

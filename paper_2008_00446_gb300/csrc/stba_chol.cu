@@ -558,41 +558,60 @@ void launch_tri_solve(const DevProblem& P, const F* L, const F* Dinv, const doub
   cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal>, P, L, Dinv, scale, rhs, x, accumulate, v_total);
 }
 
-// r = b - S x (FP64), rows [r0, r0 + 32) of one cluster per CTA; r was set to b before.
+// r = b - S x (FP64) with S symmetric, lower triangle stored; r was set to b before.  One CTA per
+// (cluster, 32-row tile row I); its 4 warps take the tiles (I, J), J <= I, in turn.  A warp stages the
+// 32 x 32 tile in shared memory with coalesced row loads, then lane l forms both the row sum of tile row l
+// (S_IJ x_J, kept in registers over the warp's tiles) and the column sum of tile column l (S_IJ^T x_I,
+// added atomically to r_J; on the diagonal tile only below the diagonal).
+constexpr int RES_WARPS = 4;
+
 template <typename Sreal>
-__global__ void __launch_bounds__(256) k_residual(DevProblem P, const Sreal* S, const double* x, double* r,
-                                                  const int2* items) {
-  __shared__ double colacc[4096];
+__global__ void __launch_bounds__(32 * RES_WARPS) k_residual(DevProblem P, const Sreal* S, const double* x,
+                                                             double* r, const int2* items) {
+  __shared__ double T[RES_WARPS][32][33];
+  __shared__ double xs[RES_WARPS][32];
+  __shared__ double xi[32];
+  __shared__ double red[RES_WARPS][32];
   const int2 it = items[blockIdx.x];
-  const int k = it.x, r0 = it.y * 32;
+  const int k = it.x, I = it.y;
   const int np = P.cluster_np[k], nk = P.cluster_n[k];
   const Sreal* Sk = S + P.S_off[k];
   const double* xk = x + P.v_off[k];
   double* rk = r + P.v_off[k];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int rend = min(r0 + 32, nk);
-  // lower part: rk[row] -= sum_{c <= row} S[row][c] x[c]; transposed part: rk[c] -= S[row][c] x[row], c < row
-  for (int cb = 0; cb < rend; cb += 4096) {
-    const int cend = min(cb + 4096, rend);
-    for (int i = threadIdx.x; i < cend - cb; i += blockDim.x) colacc[i] = 0.0;
-    __syncthreads();
-    for (int row = r0 + warp; row < rend; row += nwarps) {
-      const Sreal* srow = Sk + (size_t)row * np;
-      const double xr = xk[row];
-      double s = 0.0;
-      const int cmax = min(row, cend - 1);
-      for (int c = cb + lane; c <= cmax; c += 32) {
-        const double a = (double)srow[c];
-        s += a * xk[c];
-        if (c < row) atomicAdd(colacc + (c - cb), a * xr);
-      }
-      s = warp_sum(s);
-      if (lane == 0) atomicAdd(rk + row, -s);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i0 = 32 * I;
+  if (warp == 0) xi[lane] = (i0 + lane < nk) ? xk[i0 + lane] : 0.0;
+  __syncthreads();
+  double rowacc = 0.0;
+  for (int J = warp; J <= I; J += RES_WARPS) {
+    const int j0 = 32 * J;
+    const int col = j0 + lane;
+    for (int rr = 0; rr < 32; ++rr) {
+      const int row = i0 + rr;
+      T[warp][rr][lane] = (row < nk && col < nk && col <= row) ? (double)Sk[(size_t)row * np + col] : 0.0;
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < cend - cb; i += blockDim.x)
-      if (colacc[i] != 0.0) atomicAdd(rk + cb + i, -colacc[i]);
-    __syncthreads();
+    xs[warp][lane] = (col < nk) ? xk[col] : 0.0;
+    __syncwarp();
+    double rs = 0.0, cs = 0.0;
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) rs += T[warp][lane][c] * xs[warp][c];
+    if (J < I) {
+#pragma unroll 8
+      for (int rr = 0; rr < 32; ++rr) cs += T[warp][rr][lane] * xi[rr];
+    } else {
+      for (int rr = lane + 1; rr < 32; ++rr) cs += T[warp][rr][lane] * xi[rr];
+    }
+    rowacc += rs;
+    if (col < nk && cs != 0.0) atomicAdd(rk + col, -cs);
+    __syncwarp();
+  }
+  red[warp][lane] = rowacc;
+  __syncthreads();
+  if (warp == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < RES_WARPS; ++w) t += red[w][lane];
+    if (i0 + lane < nk) atomicAdd(rk + i0 + lane, -t);
   }
 }
 
@@ -662,7 +681,8 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
   const int nblk = (int)std::min<int64_t>(fb.v_total / 256 + 1, 152 * 8);
   for (int s = 0; s < refine_steps; ++s) {
     k_copy_vec<Sreal><<<nblk, 256, 0, stream>>>(b, fb.r, fb.v_total);
-    if (plan.n_res_items > 0) k_residual<Sreal><<<plan.n_res_items, 256, 0, stream>>>(P, S, fb.x, fb.r, plan.res_items);
+    if (plan.n_res_items > 0)
+      k_residual<Sreal><<<plan.n_res_items, 32 * RES_WARPS, 0, stream>>>(P, S, fb.x, fb.r, plan.res_items);
     launch_tri_solve<F, T, double>(P, L, Dinv, fb.scale, fb.r, fb.x, 1, plan.max_np, fb.v_total, stream);
   }
   k_scatter_dc<<<P.l, 256, 0, stream>>>(P, fb.x, dc);

@@ -87,6 +87,12 @@ struct CamLists {     // observations of every camera (sorted positions), host-b
   const int* cam_obs;       // [q]
 };
 
+struct CamSlots {     // per-camera observation lists padded to whole warps, for the camera pass
+  const int* slots;         // [32 * nwarps] sorted observation position, or -1 (padding)
+  const int* warp_cam;      // [nwarps] camera of each warp's 32 slots
+  int nwarps;
+};
+
 struct PairLists {    // camera-pair instances of the S' build (host-built per cluster assignment)
   const int4* pairs;        // (obs a, obs b, cluster k, (la << 16) | lb), sorted by (k, la, lb)
   int npairs;
@@ -102,7 +108,7 @@ void launch_vp_reduce(const DevProblem& P, Scratch<real> W, cudaStream_t stream)
 template <typename real>
 void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream);
 template <typename real>
-void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamLists CL, PairLists B, real* Gbuf, DevState* st,
+void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairLists B, real* Gbuf, DevState* st,
                       cudaStream_t stream);
 template <typename real>
 void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream);

@@ -185,33 +185,55 @@ void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cuda
 // factor ~ lambda; it is evaluated in the equivalent Woodbury form Jc^T (I + Jp Lambda^-1 Jp^T)^-1 Jc with
 // Lambda = lambda diag(Jp^T Jp), and without correction b(a) gets -Jc^T (I + Jp Lambda^-1 Jp^T)^-1 f_o.
 //
-// k_cam_pass: one CTA per camera, threads over the camera's observations; the 45 + 9 + 9 sums stay in
-// registers and are reduced once per CTA, so the diagonal blocks, b' and v are written without atomics.
-// It also stores G_o of every observation of a multi-observation virtual point for the pair pass.
+// k_cam_pass: one warp per 32 observations of one camera (each camera's observation list is padded to
+// whole warps on the host, single-observation virtual points first so that warps mostly run one branch).
+// Every thread forms the 45 + 9 + 9 terms of its observation; the warp sums them in the working precision
+// with a transposed reduction (62 shuffles leave lane L with the sums of terms L and 32 + L; a tree sum of
+// 32 terms, error <= 5 ulp of the sum of magnitudes) and adds them atomically into the FP64 S', b' and v
+// (zeroed before the launch): FP32 terms, FP64 accumulation across warps.  The per-observation arithmetic
+// stays off the FP64 pipe, which on this GPU runs at 1/64 of the FP32 rate.  It also stores G_o of every
+// observation of a multi-observation virtual point for the pair pass.
 constexpr int GSTRIDE = 32;   // reals per stored G_o (27 used)
 
+// On return lane L holds the sum over the warp's lanes of v[L].  Each halving step keeps one half of the
+// values (lanes whose bit s is set keep the upper half) and adds the partner's copy of it.
 template <typename real>
-__global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real> W, CamLists CL, real* Gbuf,
+__device__ __forceinline__ real warp_transpose_sum32(real (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const real send = up ? v[i] : v[i + s];
+      const real keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(FULL_MASK, send, s);
+    }
+  }
+  return v[0];
+}
+
+template <typename real>
+__global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real> W, CamSlots CS, real* Gbuf,
                                                   const DevState* st) {
-  const int j = blockIdx.x;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= CS.nwarps) return;   // uniform per warp
+  const int lane = threadIdx.x & 31;
+  const int j = CS.warp_cam[gw];
+  const int o = CS.slots[32 * (size_t)gw + lane];
   const real lam = (real)st->lambda_used;
   const bool corr = st->corrected != 0;
-  const Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)j);
-  real aD[45], aB[9], aV[9];
+  real Jc[2][9], N00 = 0, N01 = 0, N11 = 0, br[2] = {0, 0}, r[2] = {0, 0};
 #pragma unroll
-  for (int i = 0; i < 45; ++i) aD[i] = 0;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) aB[i] = aV[i] = 0;
-  const int e0 = CL.cam_obs_off[j], e1 = CL.cam_obs_off[j + 1];
-  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const int o = CL.cam_obs[e];
+  for (int c = 0; c < 9; ++c) Jc[0][c] = Jc[1][c] = 0;
+  if (o >= 0) {
+    const Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)j);
     const int v = P.obs_vp[o];
     const bool single = (P.vp_off[v + 1] - P.vp_off[v]) == 1;
     real X[3];
     load_point(P.pts + 3 * (size_t)P.obs_pt[o], X);
-    real uo, vo;
+    real uo, vo, Jp[2][3];
     load_uv(P, o, uo, vo);
-    real r[2], Jc[2][9], Jp[2][3];
     project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
     r[0] = res_ptr<real>(P)[2 * (size_t)o];
     r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
@@ -219,7 +241,6 @@ __global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real>
     // Both cases reduce to Jc^T N Jc with a 2x2 N:
     //   single observation  N = (I + Jp Lambda^-1 Jp^T)^-1                 (Woodbury, no cancellation)
     //   several             N = I - Jp V'^-1 Jp^T = I - P^T P, P = L^-1 Jp^T  (V' = L L^T)
-    real N00, N01, N11, br[2];
     if (single) {
       real il[3];
 #pragma unroll
@@ -246,8 +267,7 @@ __global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real>
       real Li[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) Li[c] = vi[c];
-      // P = L^-1 Jp^T (3x2)
-      real Pm[3][2];
+      real Pm[3][2];   // P = L^-1 Jp^T (3x2)
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         Pm[0][t] = Li[0] * Jp[t][0];
@@ -257,67 +277,74 @@ __global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real>
       N00 = real(1) - (Pm[0][0] * Pm[0][0] + Pm[1][0] * Pm[1][0] + Pm[2][0] * Pm[2][0]);
       N01 = -(Pm[0][0] * Pm[0][1] + Pm[1][0] * Pm[1][1] + Pm[2][0] * Pm[2][1]);
       N11 = real(1) - (Pm[0][1] * Pm[0][1] + Pm[1][1] * Pm[1][1] + Pm[2][1] * Pm[2][1]);
-      // G = P^T... stored for the pair pass: G = L^-1 Jp^T Jc = P Jc (3x9)
+      // G = L^-1 Jp^T Jc = P Jc (3x9), stored row-major (9 s + c) with 16-byte vector stores
+      real g[GSTRIDE];
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+#pragma unroll
+        for (int c = 0; c < 9; ++c) g[9 * s + c] = Pm[s][0] * Jc[0][c] + Pm[s][1] * Jc[1][c];
+#pragma unroll
+      for (int c = 27; c < GSTRIDE; ++c) g[c] = 0;
       real* Gs = Gbuf + (size_t)GSTRIDE * o;
+      if constexpr (sizeof(real) == 4) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
+        for (int q4 = 0; q4 < 7; ++q4)
+          reinterpret_cast<float4*>(Gs)[q4] = make_float4(g[4 * q4], g[4 * q4 + 1], g[4 * q4 + 2], g[4 * q4 + 3]);
+      } else {
 #pragma unroll
-        for (int s = 0; s < 3; ++s) Gs[9 * s + c] = Pm[s][0] * Jc[0][c] + Pm[s][1] * Jc[1][c];
+        for (int q2 = 0; q2 < 14; ++q2) reinterpret_cast<double2*>(Gs)[q2] = make_double2(g[2 * q2], g[2 * q2 + 1]);
       }
       br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
       br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
     }
-    {
-      real NJ[2][9];
+  }
+  // terms: 0..44 diagonal block (packed lower, row-major), 45..53 b', 54..62 v, 63 unused
+  real NJ[2][9];
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        NJ[0][c] = N00 * Jc[0][c] + N01 * Jc[1][c];
-        NJ[1][c] = N01 * Jc[0][c] + N11 * Jc[1][c];
-      }
-      int t = 0;
+  for (int c = 0; c < 9; ++c) {
+    NJ[0][c] = N00 * Jc[0][c] + N01 * Jc[1][c];
+    NJ[1][c] = N01 * Jc[0][c] + N11 * Jc[1][c];
+  }
+  real sums[2];
 #pragma unroll
-      for (int i = 0; i < 9; ++i)
+  for (int half = 0; half < 2; ++half) {
+    real v[32];
+    int t = 0;
 #pragma unroll
-        for (int jj = 0; jj <= i; ++jj, ++t) {
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+      for (int jj = 0; jj <= i; ++jj, ++t) {
+        if (t / 32 == half) {
           real d = Jc[0][i] * NJ[0][jj] + Jc[1][i] * NJ[1][jj];
           if (i == jj) d += lam * (Jc[0][i] * Jc[0][i] + Jc[1][i] * Jc[1][i]);
-          aD[t] += d;
+          v[t - 32 * half] = d;
         }
+      }
+    if (half == 1) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        v[45 - 32 + i] = -(Jc[0][i] * br[0] + Jc[1][i] * br[1]);
+        v[54 - 32 + i] = -(Jc[0][i] * r[0] + Jc[1][i] * r[1]);
+      }
+      v[31] = real(0);
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      aB[i] -= Jc[0][i] * br[0] + Jc[1][i] * br[1];
-      aV[i] -= Jc[0][i] * r[0] + Jc[1][i] * r[1];
-    }
+    sums[half] = warp_transpose_sum32(v);
   }
-  // block reduction of the 63 sums: each thread summed a few terms in the working precision; the
-  // partial sums are combined in FP64
-  __shared__ double red[8][64];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = P.cam_cluster[j], lc = P.cam_local[j];
+  const int np = P.cluster_np[k];
 #pragma unroll
-  for (int i = 0; i < 63; ++i) {
-    double x = (double)(i < 45 ? aD[i] : (i < 54 ? aB[i - 45] : aV[i - 54]));
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(FULL_MASK, x, d);
-    if (lane == 0) red[warp][i] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < 63) {
-    double x = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[w][threadIdx.x];
-    const int k = P.cam_cluster[j];
-    const int lc = P.cam_local[j];
-    const int i = threadIdx.x;
-    if (i < 45) {
+  for (int half = 0; half < 2; ++half) {
+    const int e = lane + 32 * half;
+    const double x = (double)sums[half];
+    if (e < 45) {
       int row = 0;
-      while ((row + 1) * (row + 2) / 2 <= i) ++row;
-      const int col = i - row * (row + 1) / 2;
-      const int np = P.cluster_np[k];
-      W.S[P.S_off[k] + (size_t)(9 * lc + row) * np + 9 * lc + col] = x;
-    } else if (i < 54) {
-      W.b[P.v_off[k] + 9 * lc + (i - 45)] = x;
-    } else {
-      W.vgrad[9 * (size_t)j + (i - 54)] = (real)x;
+      while ((row + 1) * (row + 2) / 2 <= e) ++row;
+      const int col = e - row * (row + 1) / 2;
+      atomicAdd(W.S + P.S_off[k] + (size_t)(9 * lc + row) * np + 9 * lc + col, x);
+    } else if (e < 54) {
+      atomicAdd(W.b + P.v_off[k] + 9 * lc + (e - 45), x);
+    } else if (e < 63) {
+      atomicAdd(W.vgrad + 9 * (size_t)j + (e - 54), sums[half]);
     }
   }
 }
@@ -374,9 +401,9 @@ __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> 
 }
 
 template <typename real>
-void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamLists CL, PairLists B, real* Gbuf, DevState* st,
+void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairLists B, real* Gbuf, DevState* st,
                       cudaStream_t stream) {
-  k_cam_pass<real><<<P.m, 256, 0, stream>>>(P, W, CL, Gbuf, st);
+  k_cam_pass<real><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
   if (B.npairs > 0) {
     const int warps = (B.npairs + PAIRS_PER_WARP - 1) / PAIRS_PER_WARP;
     k_pair_build<real><<<(warps + 7) / 8, 256, 0, stream>>>(P, W, B.pairs, B.npairs, Gbuf);
@@ -665,7 +692,7 @@ void configure_kernels(int max_np) { configure_solve_kernels(max_np); }
   template void launch_iter_begin<real>(DevState*, const Settings&, cudaStream_t);                        \
   template void launch_vp_reduce<real>(const DevProblem&, Scratch<real>, cudaStream_t);                   \
   template void launch_vp_finalize<real>(const DevProblem&, Scratch<real>, DevState*, cudaStream_t);      \
-  template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamLists, PairLists, real*,      \
+  template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamSlots, PairLists, real*,      \
                                        DevState*, cudaStream_t);                                          \
   template void launch_point_update<real>(const DevProblem&, Scratch<real>, cudaStream_t);                \
   template void launch_finalize<real>(const DevProblem&, Scratch<real>, DevState*, const Settings&, int,  \
