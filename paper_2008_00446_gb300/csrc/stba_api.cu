@@ -36,6 +36,9 @@ struct stba_ctx {
   Settings set{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side_stream = nullptr;           // trailing updates of the factorisation
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<cudaEvent_t> ev_panel, ev_update;  // one per tile step (grown, never shrunk)
   std::string err;
   int64_t m = 0, n = 0, q = 0;
   int l = 0, nv = 0;
@@ -389,19 +392,25 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
       const int ntk = c->h_np[k] / TF;
       if (ntk <= kt) continue;
       for (int i = kt; i < ntk; ++i) panel.push_back(make_int2(k, i));
-      for (int j = kt + 1; j < ntk; ++j)
+      for (int j = kt + 2; j < ntk; ++j)   // column kt + 1 is updated by panel kt + 1 itself
         for (int i = j; i < ntk; ++i) update.push_back(make_int2(k, (i << 16) | j));
     }
   }
   c->h_panel_off[max_nt] = (int)panel.size();
   c->h_update_off[max_nt] = (int)update.size();
-  std::vector<int2> res_items, diag_items;
+  std::vector<int2> res_items;
   for (int k = 0; k < l; ++k)
     for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
-  for (int k = 0; k < l; ++k)
-    for (int t = 0; t < c->h_np[k] / TF; ++t) diag_items.push_back(make_int2(k, t));
+  while ((int)c->ev_panel.size() < max_nt) {
+    cudaEvent_t e1, e2;
+    if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess)
+      return fail(c, STBA_ERR_CUDA, "cudaEventCreate failed");
+    c->ev_panel.push_back(e1);
+    c->ev_update.push_back(e2);
+  }
   {
-    int factor_launches = 3;
+    int factor_launches = 2;
     for (int kt = 0; kt < max_nt; ++kt)
       factor_launches += (c->h_panel_off[kt + 1] > c->h_panel_off[kt]) + (c->h_update_off[kt + 1] > c->h_update_off[kt]);
     const int build_launches = 1 + (npairs > 0 ? 1 : 0);
@@ -444,17 +453,17 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(d_cam_obs, cam_obs);
   UP(d_cam_slots, cam_slots);
   UP(d_warp_cam, warp_cam);
-  int2 *d_panel, *d_update, *d_res, *d_diag;
+  int2 *d_panel, *d_update, *d_res;
   UP(d_panel, panel);
   UP(d_update, update);
   UP(d_res, res_items);
-  UP(d_diag, diag_items);
 #undef UP
   c->plist = PairLists{d_pairs, (int)npairs};
   c->clist = CamLists{d_cam_obs_off, d_cam_obs};
   c->cslots = CamSlots{d_cam_slots, d_warp_cam, (int)warp_cam.size()};
-  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
-                      c->h_panel_off.data(), c->h_update_off.data(), c->max_np};
+  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), max_nt, c->h_panel_off.data(),
+                      c->h_update_off.data(), c->max_np, c->side_stream, c->ev_fork, c->ev_join,
+                      c->ev_panel.data(), c->ev_update.data()};
 
   const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
   auto ralloc = [&](void** p, size_t count) -> stba_status {
@@ -710,6 +719,11 @@ void stba_destroy(stba_ctx* c) {
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->side_stream) cudaStreamDestroy(c->side_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (auto e : c->ev_panel) cudaEventDestroy(e);
+  for (auto e : c->ev_update) cudaEventDestroy(e);
   delete c;
 }
 
@@ -814,6 +828,10 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   }
   for (auto& e : c->ev)
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(c, STBA_ERR_CUDA, "cudaEventCreate failed"));
+  if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(c, STBA_ERR_CUDA, "cannot create the factorisation stream or its events"));
   if ((s = dalloc(c, &c->cams, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->pts, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->dc, 9 * (size_t)m, false)) != STBA_OK) return bail(s);

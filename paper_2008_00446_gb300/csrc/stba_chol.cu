@@ -6,11 +6,13 @@
 // so the padded system is block diagonal with an identity block and solves to zero there.
 //
 // The factorised matrix is the Jacobi-scaled  S~ = D^-1/2 S D^-1/2, D = diag(S) (s_i = S_ii^-1/2), so that
-// S x = b becomes S~ z = s o b, x = s o z.  Right-looking tiled algorithm, step kt:
-//   panel   for every tile row i >= kt: factor the diagonal tile (kt, kt) in shared memory (redundantly in
-//           each CTA, T^3/3 flops); the CTA of i = kt also stores the inverse of L_kt,kt; the CTAs of
-//           i > kt solve L_i,kt L_kt,kt^T = A_i,kt;
-//   update  for every kt < j <= i: A_i,j -= L_i,kt L_j,kt^T.
+// S x = b becomes S~ z = s o b, x = s o z.  Right-looking tiled algorithm with a look-ahead of one column,
+// step kt:
+//   panel   for every tile row i >= kt: apply step kt - 1's update to tiles (kt, kt) and (i, kt), factor
+//           the diagonal tile with its inverse (redundantly in each CTA); the CTA of i = kt stores
+//           L_kt,kt and L_kt,kt^-1 (for the solves), the others L_i,kt = A_i,kt L_kt,kt^-T;
+//   update  for every kt + 1 < j <= i: A_i,j -= L_i,kt L_j,kt^T, on a second stream, overlapping the
+//           next panel.
 // FP64 factor (FP64 mode): a pivot that is not positive and finite marks the cluster as failed, and the
 // LM step is rejected (lambda *= 3).  FP32 factor (mixed mode): a pivot that rounding has made vanish
 // (below 2^-20 of the unit scaled diagonal; legitimate pivots of the damped system are about lambda or
@@ -66,289 +68,6 @@ __global__ void k_scaled_copy(DevProblem P, const Sreal* S, const double* scale,
 __device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
-// Named barriers: the producer warp arrives without waiting, the consumer warps wait.
-__device__ __forceinline__ void named_arrive(int id, int nthreads) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-__device__ __forceinline__ void named_sync(int id, int nthreads) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// Register-blocked tile kernels.  256 threads form a 16 x 16 grid; thread (bi, bj) = (tid % 16, tid / 16)
-// holds the R x R block (R = T / 16) of rows bi R .. and columns bj R .. in registers.  Warp w therefore
-// owns the 2R consecutive columns 2R w ..; lane l of it holds rows R (l % 16) .. of half l / 16 of them.
-// Both kernels sweep the tile in T / 2R blocked steps: warp w finishes its own columns with shuffles only,
-// publishes them in shared memory (one buffer per step) and arrives on named barrier 1 + w; the warps to
-// its right wait on that barrier and apply a rank-2R update from registers.  A warp starts its own step
-// as soon as it has applied the steps before it, so the updates of distant warps overlap the next step.
-//
-// factor_tile_regs: LL^T of the diagonal tile.  Inside a block the updates use the unscaled columns,
-// a_rc -= a_rj a_cj / a_jj; the pivots a_jj are kept, the published columns are scaled by a_jj^-1/2, and
-// every column is scaled once at the end.
-template <typename F, int T>
-__device__ __forceinline__ void factor_tile_regs(F (&a)[T / 16][T / 16], F (*U)[T][T / 8], F* piv, F* tab,
-                                                 int row0, int nk, int* fail, int* boosted) {
-  constexpr int R = T / 16, W = 2 * R;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int bi = threadIdx.x & 15, bj = threadIdx.x >> 4, h = lane >> 4;
-  for (int w = 0; w < 8; ++w) {
-    const int c0 = W * w;
-    if (warp == w) {
-#pragma unroll
-      for (int jj = 0; jj < W; ++jj) {
-        const int hj = jj / R, cj = jj % R;
-        const int cg = c0 + jj;
-        F d = __shfl_sync(0xffffffffu, a[cj][cj], hj * 16 + 2 * w + hj);
-        bool bad = false, boost = false;
-        if (row0 + cg >= nk) {
-          d = F(1);
-        } else if (!isfinite(d)) {
-          bad = true;
-          d = F(1);
-        } else if (sizeof(F) == 8) {
-          if (!(d > F(0))) {
-            bad = true;
-            d = F(1);
-          }
-        } else if (d < F(1.0 / 1048576)) {
-          boost = true;
-          d = F(1.0 / 4096);
-        }
-        if (lane == 0) {
-          piv[cg] = d;
-          if (bad) *fail = 1;
-          if (boost && boosted) atomicAdd(boosted, 1);
-        }
-        const F inv = rcp_rn(d);
-        F colr[R], rowc[R];
-#pragma unroll
-        for (int ii = 0; ii < R; ++ii) colr[ii] = __shfl_sync(0xffffffffu, a[ii][cj], bi + 16 * hj);
-#pragma unroll
-        for (int j2 = 0; j2 < R; ++j2) rowc[j2] = __shfl_sync(0xffffffffu, a[j2][cj], (2 * w + h) + 16 * hj);
-#pragma unroll
-        for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-          for (int j2 = 0; j2 < R; ++j2) {
-            const int r = R * bi + ii, cl = c0 + R * h + j2;
-            if (cl > cg && r >= cl) a[ii][j2] -= colr[ii] * rowc[j2] * inv;
-          }
-      }
-      __syncwarp();
-#pragma unroll
-      for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-        for (int j2 = 0; j2 < R; ++j2) {
-          const int cl = c0 + R * h + j2;
-          U[w][R * bi + ii][R * h + j2] = a[ii][j2] * rsqrt(piv[cl]);
-        }
-      if (w < 7) named_arrive(1 + w, 32 * (8 - w));
-    } else if (warp > w) {
-      named_sync(1 + w, 32 * (8 - w));
-      if (bi >= bj) {
-        F ur[R][W], uc[R][W];
-#pragma unroll
-        for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-          for (int k = 0; k < W; ++k) {
-            ur[ii][k] = U[w][R * bi + ii][k];
-            uc[ii][k] = U[w][R * bj + ii][k];
-          }
-        if (bi > bj) {
-#pragma unroll
-          for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-            for (int jj = 0; jj < R; ++jj) {
-              F s = F(0);
-#pragma unroll
-              for (int k = 0; k < W; ++k) s += ur[ii][k] * uc[jj][k];
-              a[ii][jj] -= s;
-            }
-        } else {
-#pragma unroll
-          for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-            for (int jj = 0; jj <= ii; ++jj) {
-              F s = F(0);
-#pragma unroll
-              for (int k = 0; k < W; ++k) s += ur[ii][k] * uc[jj][k];
-              a[ii][jj] -= s;
-            }
-        }
-      }
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < T) {
-    const F sq = sqrt(piv[threadIdx.x]);
-    tab[threadIdx.x] = rcp_rn(sq);
-    tab[T + threadIdx.x] = sq;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-    for (int jj = 0; jj < R; ++jj) {
-      const int r = R * bi + ii, cl = R * bj + jj;
-      a[ii][jj] = (r > cl) ? a[ii][jj] * tab[cl] : ((r == cl) ? tab[T + cl] : F(0));
-    }
-  __syncthreads();
-}
-
-// trsm_tile_regs: X L^T = A for a full tile X (registers), L lower triangular in shared memory (Ls) with
-// the reciprocals of its diagonal in rcp.  Warp w solves its 2R columns (rows are independent; the two
-// halves of the warp exchange their solved values by shuffles), publishes them, and the warps to its
-// right subtract X[:, block] L[c, block]^T.
-template <typename F, int T>
-__device__ __forceinline__ void trsm_tile_regs(F (&x)[T / 16][T / 16], const F (*Ls)[T + 1], const F* rcp,
-                                               F (*U)[T][T / 8]) {
-  constexpr int R = T / 16, W = 2 * R;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int bi = threadIdx.x & 15, bj = threadIdx.x >> 4, h = lane >> 4;
-  for (int w = 0; w < 8; ++w) {
-    const int c0 = W * w;
-    if (warp == w) {
-#pragma unroll
-      for (int jj = 0; jj < W; ++jj) {
-        const int hj = jj / R, cj = jj % R;
-        const int cg = c0 + jj;
-        if (h == hj) {
-#pragma unroll
-          for (int ii = 0; ii < R; ++ii) x[ii][cj] *= rcp[cg];
-        }
-        F xs[R];
-#pragma unroll
-        for (int ii = 0; ii < R; ++ii) xs[ii] = __shfl_sync(0xffffffffu, x[ii][cj], bi + 16 * hj);
-#pragma unroll
-        for (int j2 = 0; j2 < R; ++j2) {
-          const int cl = c0 + R * h + j2;
-          if (cl > cg) {
-            const F l = Ls[cl][cg];
-#pragma unroll
-            for (int ii = 0; ii < R; ++ii) x[ii][j2] -= xs[ii] * l;
-          }
-        }
-      }
-#pragma unroll
-      for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-        for (int j2 = 0; j2 < R; ++j2) U[w][R * bi + ii][R * h + j2] = x[ii][j2];
-      if (w < 7) named_arrive(1 + w, 32 * (8 - w));
-    } else if (warp > w) {
-      named_sync(1 + w, 32 * (8 - w));
-      F ux[R][W], lc[R][W];
-#pragma unroll
-      for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-        for (int k = 0; k < W; ++k) {
-          ux[ii][k] = U[w][R * bi + ii][k];
-          lc[ii][k] = Ls[R * bj + ii][c0 + k];
-        }
-#pragma unroll
-      for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-        for (int jj = 0; jj < R; ++jj) {
-          F s = F(0);
-#pragma unroll
-          for (int k = 0; k < W; ++k) s += ux[ii][k] * lc[jj][k];
-          x[ii][jj] -= s;
-        }
-    }
-  }
-}
-
-template <typename F, int T>
-__global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const int2* items, int kt,
-                                                    int* fail_flags, int* boosted) {
-  constexpr int R = T / 16;
-  __shared__ F Ls[T][T + 1];
-  __shared__ __align__(16) F U[8][T][T / 8];
-  __shared__ F piv[T];
-  __shared__ F tab[2 * T];
-  const int2 it = items[blockIdx.x];
-  const int k = it.x, i = it.y;
-  const int np = P.cluster_np[k], nk = P.cluster_n[k];
-  F* A = L + P.S_off[k];
-  const int bj = threadIdx.x >> 4, bi = threadIdx.x & 15;
-  const size_t base_kk = (size_t)(kt * T) * np + kt * T;
-  F a[R][R];
-#pragma unroll
-  for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-    for (int jj = 0; jj < R; ++jj) {
-      const int r = bi * R + ii, cl = bj * R + jj;
-      a[ii][jj] = (cl <= r) ? A[base_kk + (size_t)r * np + cl] : F(0);
-    }
-  F x[R][R];
-  const size_t base_ik = (size_t)(i * T) * np + kt * T;
-  if (i != kt) {
-#pragma unroll
-    for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-      for (int jj = 0; jj < R; ++jj) x[ii][jj] = A[base_ik + (size_t)(bi * R + ii) * np + bj * R + jj];
-  }
-  factor_tile_regs<F, T>(a, U, piv, tab, kt * T, nk, fail_flags + k, (i == kt) ? boosted : nullptr);
-  if (i == kt) {
-#pragma unroll
-    for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-      for (int jj = 0; jj < R; ++jj) {
-        const int r = bi * R + ii, cl = bj * R + jj;
-        if (cl <= r) A[base_kk + (size_t)r * np + cl] = a[ii][jj];
-      }
-    return;
-  }
-#pragma unroll
-  for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-    for (int jj = 0; jj < R; ++jj) Ls[bi * R + ii][bj * R + jj] = a[ii][jj];
-  __syncthreads();
-  trsm_tile_regs<F, T>(x, Ls, tab, U);
-#pragma unroll
-  for (int ii = 0; ii < R; ++ii)
-#pragma unroll
-    for (int jj = 0; jj < R; ++jj) A[base_ik + (size_t)(bi * R + ii) * np + bj * R + jj] = x[ii][jj];
-}
-
-// Inverse of every diagonal tile of the factor (for the solves), one CTA per tile: L Y = I column by
-// column, four threads per column splitting each dot product.
-template <typename F, int T>
-__global__ void __launch_bounds__(256) k_diag_inverse(const F* L, F* Dinv, DevProblem P, const int2* items,
-                                                      int64_t v_total) {
-  __shared__ F D[T][T + 1];
-  __shared__ F Y[T][T + 1];
-  const int2 it = items[blockIdx.x];
-  const int k = it.x, t = it.y;
-  const int np = P.cluster_np[k];
-  const F* A = L + P.S_off[k];
-  const size_t base = (size_t)(t * T) * np + t * T;
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int r = idx / T, c = idx - (idx / T) * T;
-    D[r][c] = (c <= r) ? A[base + (size_t)r * np + c] : F(0);
-  }
-  __syncthreads();
-  const int cl = threadIdx.x >> 2, part = threadIdx.x & 3;
-  for (int cb = cl; cb < T; cb += blockDim.x >> 2) {
-    for (int r = 0; r < T; ++r) {
-      F s = F(0);
-      for (int j = cb + part; j < r; j += 4) s += D[r][j] * Y[j][cb];
-      s += __shfl_xor_sync(FULL_MASK, s, 1);
-      s += __shfl_xor_sync(FULL_MASK, s, 2);
-      const F v = (r < cb) ? F(0) : (((r == cb) ? F(1) : F(0)) - s) / D[r][r];
-      __syncwarp();
-      if (part == 0) Y[r][cb] = v;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)t * T * T;
-  F* DiT = Di + v_total * T;   // transposed copy in the second half of the buffer
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int r = idx / T, c = idx - (idx / T) * T;
-    Di[idx] = Y[r][c];
-    DiT[idx] = Y[c][r];
-  }
-}
-
 // R consecutive elements from 16-byte aligned shared memory in one vector load where the width allows.
 template <typename F, int R>
 __device__ __forceinline__ void load_vec(const F* p, F (&v)[R]) {
@@ -368,6 +87,291 @@ __device__ __forceinline__ void load_vec(const F* p, F (&v)[R]) {
   }
 }
 
+// Asynchronous global -> shared copies of one element (4 or 8 bytes), so that all the loads of a tile are
+// in flight at once and may land at transposed positions.
+template <typename F>
+__device__ __forceinline__ void cp_async_elem(F* smem_dst, const F* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(F) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_w(double x) { return rsqrt(x); }
+
+// ------------------------------------------------------------------------------------------------------
+// Panel of tile step kt, one CTA per tile row i >= kt of a cluster (256 threads):
+//   1. fused update from step kt - 1 (kt > 0):  A_kt,kt -= L_kt,kt-1 L_kt,kt-1^T,  A_i,kt -= L_i,kt-1 L_kt,kt-1^T
+//      (the trailing update of the other tiles of step kt - 1 runs concurrently in k_chol_update);
+//   2. LL^T of the stacked panel [A_kt,kt; A_i,kt] in blocks of 8 columns (the diagonal tile redundantly
+//      in every CTA of the step): per block one thread factors the 8 x 8 diagonal block, eight threads
+//      invert it (Yb), the block column below becomes A Yb^T, and the columns to its right get the
+//      rank-8 update; rows of A_i,kt are just more rows below the diagonal, so they come out as L_i,kt;
+//   3. the CTA of i = kt also builds Y = L_kt,kt^-1 block row by block row (Y_b,<b = -Yb L_b,<b Y_<b,<b)
+//      and stores it, with its transpose, for the solves.
+// Dynamic shared memory: Ad, Ax (T x (T + 1)) and two T x LDV buffers that hold the transposed tiles of
+// the fused update, then Y and the block-row scratch.
+template <typename F, int T>
+struct PanelLayout {
+  static constexpr int LDA = T + 1;
+  static constexpr int LDV = T + (sizeof(F) == 4 ? 4 : 2);   // 16-byte rows for vector loads
+  static constexpr size_t bytes = sizeof(F) * (2 * (size_t)T * LDA + 2 * (size_t)T * LDV);
+};
+
+template <typename F, int T>
+__global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P, const int2* items, int kt,
+                                                    int* fail_flags, int* boosted, int64_t v_total) {
+  using PL = PanelLayout<F, T>;
+  constexpr int R = T / 16, LDA = PL::LDA, LDV = PL::LDV, NB = T / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F(*Ad)[LDA] = reinterpret_cast<F(*)[LDA]>(smem_raw);
+  F(*Ax)[LDA] = Ad + T;
+  F* bufV = reinterpret_cast<F*>(Ax + T);
+  F(*LkT)[LDV] = reinterpret_cast<F(*)[LDV]>(bufV);
+  F(*LiT)[LDV] = LkT + T;
+  __shared__ F rinv[8];
+  __shared__ F Yb[8][9];
+  const int2 it = items[blockIdx.x];
+  const int k = it.x, i = it.y;
+  const bool diag = (i == kt);
+  const int np = P.cluster_np[k], nk = P.cluster_n[k];
+  F* A = L + P.S_off[k];
+  const int tid = threadIdx.x;
+  const int bi = tid & 15, bj = tid >> 4;
+  const size_t base_kk = (size_t)(kt * T) * np + kt * T;
+  const size_t base_ik = (size_t)(i * T) * np + kt * T;
+  // 1. loads; the upper part of the diagonal tile is never stored, so it is set to zero
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    if (c <= r)
+      cp_async_elem(&Ad[r][c], A + base_kk + (size_t)r * np + c);
+    else
+      Ad[r][c] = F(0);
+    if (!diag) cp_async_elem(&Ax[r][c], A + base_ik + (size_t)r * np + c);
+    if (kt > 0) {
+      cp_async_elem(&LkT[c][r], A + base_kk - T + (size_t)r * np + c);
+      if (!diag) cp_async_elem(&LiT[c][r], A + base_ik - T + (size_t)r * np + c);
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (kt > 0) {
+    F accD[R][R], accX[R][R];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) accD[a][b] = accX[a][b] = F(0);
+#pragma unroll 4
+    for (int m = 0; m < T; ++m) {
+      F lr[R], lc[R];
+      load_vec<F, R>(&LkT[m][bi * R], lr);
+      load_vec<F, R>(&LkT[m][bj * R], lc);
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) accD[a][b] += lr[a] * lc[b];
+      if (!diag) {
+        F xr[R];
+        load_vec<F, R>(&LiT[m][bi * R], xr);
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+          for (int b = 0; b < R; ++b) accX[a][b] += xr[a] * lc[b];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        const int r = bi * R + a, c = bj * R + b;
+        if (c <= r) Ad[r][c] -= accD[a][b];
+        if (!diag) Ax[r][c] -= accX[a][b];
+      }
+    __syncthreads();
+  }
+  // the transposed-tile buffers are free: Y (T x LDA) and the block-row scratch W (8 x T), diagonal CTA only
+  F(*Y)[LDA] = reinterpret_cast<F(*)[LDA]>(bufV);
+  F(*W)[T] = reinterpret_cast<F(*)[T]>(bufV + (size_t)T * LDA);
+  if (diag) {
+    for (int idx = tid; idx < T * LDA; idx += 256) (&Y[0][0])[idx] = F(0);
+  }
+  // 2. blocked LL^T of the stacked panel
+  for (int b = 0; b < NB; ++b) {
+    const int b0 = 8 * b;
+    if (tid == 0) {
+      F d[8][8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) d[r][c] = (c <= r) ? Ad[b0 + r][b0 + c] : F(0);
+      int bad = 0, nboost = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        F pv = d[j][j];
+        if (kt * T + b0 + j >= nk) {
+          pv = F(1);   // padding row: identity
+        } else if (!isfinite(pv)) {
+          bad = 1;
+          pv = F(1);
+        } else if (sizeof(F) == 8) {
+          if (!(pv > F(0))) {
+            bad = 1;
+            pv = F(1);
+          }
+        } else if (pv < F(1.0 / 1048576)) {
+          ++nboost;   // static pivoting: a pivot that FP32 rounding made vanish
+          pv = F(1.0 / 4096);
+        }
+        const F is = rsqrt_w(pv);
+        d[j][j] = pv * is;
+        rinv[j] = is;
+#pragma unroll
+        for (int r = j + 1; r < 8; ++r) d[r][j] *= is;
+#pragma unroll
+        for (int c = j + 1; c < 8; ++c)
+#pragma unroll
+          for (int r = c; r < 8; ++r) d[r][c] -= d[r][j] * d[c][j];
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) Ad[b0 + r][b0 + c] = d[r][c];
+      if (bad) fail_flags[k] = 1;
+      if (nboost && diag && boosted) atomicAdd(boosted, nboost);
+    }
+    __syncthreads();
+    if (tid < 8) {
+      // column j = tid of Yb = L_bb^-1 by forward substitution (with 1 / l_rr = rinv[r])
+      const int j = tid;
+      F y[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        F s = (r == j) ? F(1) : F(0);
+#pragma unroll
+        for (int m = 0; m < r; ++m) s -= Ad[b0 + r][b0 + m] * y[m];
+        y[r] = (r < j) ? F(0) : s * rinv[r];
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        Yb[r][j] = y[r];
+        if (diag) Y[b0 + r][b0 + j] = y[r];
+      }
+    }
+    __syncthreads();
+    // block column below the diagonal block: L_rb = A_rb Yb^T, one row per thread (Ad rows, then Ax rows)
+    const int rows_d = T - b0 - 8;
+    const int rows_tot = rows_d + (diag ? 0 : T);
+    if (tid < rows_tot) {
+      F* row = (tid < rows_d) ? &Ad[b0 + 8 + tid][0] : &Ax[tid - rows_d][0];
+      F a8[8], o8[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) a8[t] = row[b0 + t];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        F s = F(0);
+#pragma unroll
+        for (int t = 0; t <= c; ++t) s += a8[t] * Yb[c][t];
+        o8[c] = s;
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) row[b0 + c] = o8[c];
+    }
+    if (diag) {   // block row of Y, first half: W = L_b,<b Y_<b,<b (8 x b0)
+      for (int e = tid; e < 8 * b0; e += 256) {
+        const int row = e / b0, col = e - (e / b0) * b0;
+        F s = F(0);
+        for (int t = col; t < b0; ++t) s += Ad[b0 + row][t] * Y[t][col];
+        W[row][col] = s;
+      }
+    }
+    __syncthreads();
+    if (b + 1 < NB) {
+      // rank-8 update of the columns right of the block, register-blocked R x R: Ad (lower), then Ax
+      const int c0 = bj * R;
+      if (c0 + R > b0 + 8) {
+        F lc[R][8];
+#pragma unroll
+        for (int cc = 0; cc < R; ++cc)
+#pragma unroll
+          for (int t = 0; t < 8; ++t) lc[cc][t] = Ad[c0 + cc][b0 + t];
+        const int r0 = bi * R;
+        if (bj <= bi && r0 + R > b0 + 8) {
+#pragma unroll
+          for (int a = 0; a < R; ++a) {
+            F lr[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) lr[t] = Ad[r0 + a][b0 + t];
+#pragma unroll
+            for (int cc = 0; cc < R; ++cc) {
+              const int r = r0 + a, c = c0 + cc;
+              if (c <= r && c >= b0 + 8) {
+                F s = F(0);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) s += lr[t] * lc[cc][t];
+                Ad[r][c] -= s;
+              }
+            }
+          }
+        }
+        if (!diag) {
+#pragma unroll
+          for (int a = 0; a < R; ++a) {
+            F xr[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) xr[t] = Ax[r0 + a][b0 + t];
+#pragma unroll
+            for (int cc = 0; cc < R; ++cc) {
+              const int c = c0 + cc;
+              if (c >= b0 + 8) {
+                F s = F(0);
+#pragma unroll
+                for (int t = 0; t < 8; ++t) s += xr[t] * lc[cc][t];
+                Ax[r0 + a][c] -= s;
+              }
+            }
+          }
+        }
+      }
+    }
+    if (diag) {   // block row of Y, second half: Y_b,<b = -Yb W
+      for (int e = tid; e < 8 * b0; e += 256) {
+        const int row = e / b0, col = e - (e / b0) * b0;
+        F s = F(0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t <= row) s += Yb[row][t] * W[t][col];
+        Y[b0 + row][col] = -s;
+      }
+    }
+    __syncthreads();
+  }
+  // 3. outputs
+  if (diag) {
+    for (int idx = tid; idx < T * T; idx += 256) {
+      const int r = idx / T, c = idx - (idx / T) * T;
+      if (c <= r) A[base_kk + (size_t)r * np + c] = Ad[r][c];
+    }
+    F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
+    F* DiT = Di + v_total * T;
+    for (int idx = tid; idx < T * T; idx += 256) {
+      const int r = idx / T, c = idx - (idx / T) * T;
+      Di[idx] = Y[r][c];
+      DiT[idx] = Y[c][r];
+    }
+    return;
+  }
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    A[base_ik + (size_t)r * np + c] = Ax[r][c];
+  }
+}
+
 // A_ij -= L_i,kt L_j,kt^T on a T x T tile; 256 threads, each an (T/16) x (T/16) register block.
 template <typename F, int T>
 __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const int2* items, int kt) {
@@ -382,9 +386,10 @@ __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const i
   const size_t bi = (size_t)(i * T) * np + kt * T, bj = (size_t)(j * T) * np + kt * T;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int r = idx / T, c = idx - (idx / T) * T;
-    LiT[c][r] = A[bi + (size_t)r * np + c];
-    LjT[c][r] = A[bj + (size_t)r * np + c];
+    cp_async_elem(&LiT[c][r], A + bi + (size_t)r * np + c);
+    cp_async_elem(&LjT[c][r], A + bj + (size_t)r * np + c);
   }
+  cp_async_wait_all();
   __syncthreads();
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   F acc[R][R];
@@ -658,16 +663,25 @@ void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb
   k_diag_scale<Sreal><<<g1, 256, 0, stream>>>(P, S, fb.scale);
   dim3 g2(std::min(plan.max_np, 1024), P.l);
   k_scaled_copy<Sreal, F><<<g2, 256, 0, stream>>>(P, S, fb.scale, L);
+  // panels on `stream`; the trailing updates (all tiles but the next column, which the next panel updates
+  // itself) on the side stream, so that update kt overlaps panel kt + 1.  Panel kt + 2 waits for update kt.
+  cudaStream_t side = plan.side_stream;
+  cudaEventRecord(plan.ev_fork, stream);
+  cudaStreamWaitEvent(side, plan.ev_fork, 0);
   for (int kt = 0; kt < plan.nsteps; ++kt) {
+    if (kt >= 2) cudaStreamWaitEvent(stream, plan.ev_update[kt - 2], 0);
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
     if (npn > 0)
-      k_chol_panel<F, T><<<npn, 256, 0, stream>>>(L, P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags,
-                                                   fb.boosted);
+      k_chol_panel<F, T><<<npn, 256, PanelLayout<F, T>::bytes, stream>>>(
+          L, Dinv, P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags, fb.boosted, fb.v_total);
+    cudaEventRecord(plan.ev_panel[kt], stream);
+    cudaStreamWaitEvent(side, plan.ev_panel[kt], 0);
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];
-    if (nu > 0) k_chol_update<F, T><<<nu, 256, 0, stream>>>(L, P, plan.update_items + plan.h_update_off[kt], kt);
+    if (nu > 0) k_chol_update<F, T><<<nu, 256, 0, side>>>(L, P, plan.update_items + plan.h_update_off[kt], kt);
+    cudaEventRecord(plan.ev_update[kt], side);
   }
-  if (plan.n_diag_items > 0)
-    k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(L, Dinv, P, plan.diag_items, fb.v_total);
+  cudaEventRecord(plan.ev_join, side);
+  cudaStreamWaitEvent(stream, plan.ev_join, 0);
 }
 
 template <typename F>
@@ -689,6 +703,10 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
 }
 
 void configure_solve_kernels(int max_np) {
+  cudaFuncSetAttribute(k_chol_panel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)PanelLayout<float, 64>::bytes);
+  cudaFuncSetAttribute(k_chol_panel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)PanelLayout<double, 32>::bytes);
   const int s32 = (int)(sizeof(float) * (size_t)max_np), s64 = (int)(sizeof(double) * (size_t)max_np);
   cudaFuncSetAttribute(k_tri_solve<float, 64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
   cudaFuncSetAttribute(k_tri_solve<double, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
