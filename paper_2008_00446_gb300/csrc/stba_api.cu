@@ -398,9 +398,11 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   }
   c->h_panel_off[max_nt] = (int)panel.size();
   c->h_update_off[max_nt] = (int)update.size();
-  std::vector<int2> res_items;
+  std::vector<int2> res_items, diag_items;
   for (int k = 0; k < l; ++k)
     for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
+  for (int k = 0; k < l; ++k)
+    for (int t = 0; t < c->h_np[k] / TF; ++t) diag_items.push_back(make_int2(k, t));
   while ((int)c->ev_panel.size() < max_nt) {
     cudaEvent_t e1, e2;
     if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
@@ -410,7 +412,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->ev_update.push_back(e2);
   }
   {
-    int factor_launches = 2;
+    int factor_launches = 3;
     for (int kt = 0; kt < max_nt; ++kt)
       factor_launches += (c->h_panel_off[kt + 1] > c->h_panel_off[kt]) + (c->h_update_off[kt + 1] > c->h_update_off[kt]);
     const int build_launches = 1 + (npairs > 0 ? 1 : 0);
@@ -453,17 +455,25 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(d_cam_obs, cam_obs);
   UP(d_cam_slots, cam_slots);
   UP(d_warp_cam, warp_cam);
-  int2 *d_panel, *d_update, *d_res;
+  int2 *d_panel, *d_update, *d_res, *d_diag;
   UP(d_panel, panel);
   UP(d_update, update);
   UP(d_res, res_items);
+  UP(d_diag, diag_items);
 #undef UP
   c->plist = PairLists{d_pairs, (int)npairs};
   c->clist = CamLists{d_cam_obs_off, d_cam_obs};
   c->cslots = CamSlots{d_cam_slots, d_warp_cam, (int)warp_cam.size()};
-  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), max_nt, c->h_panel_off.data(),
-                      c->h_update_off.data(), c->max_np, c->side_stream, c->ev_fork, c->ev_join,
+  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
+                      c->h_panel_off.data(),
+                      c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
                       c->ev_panel.data(), c->ev_update.data()};
+  {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) cudaGetLastError();
+    c->cplan.prio_high = greatest;
+    c->cplan.prio_low = least;
+  }
 
   const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
   auto ralloc = [&](void** p, size_t count) -> stba_status {

@@ -105,18 +105,65 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_w(double x) { return rsqrt(x); }
 
+// LL^T of the 8 x 8 diagonal block at (b0, b0) of a shared-memory tile, by one thread in registers; the
+// reciprocal pivots go to rinv.  Pivot rules: padding rows (global row >= nk) get 1; FP64 -- a pivot that is
+// not positive and finite fails the cluster; FP32 -- a non-finite pivot fails it, and a pivot that
+// rounding made vanish (< 2^-20 of the unit scaled diagonal) is raised to 2^-12 and counted (static
+// pivoting; the FP64 refinement solves the unmodified system).
+template <typename F, int LDA>
+__device__ __forceinline__ void chol8(F (*Ad)[LDA], int b0, int row0, int nk, F* rinv, int* fail, int* boosted) {
+  F d[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) d[r][c] = (c <= r) ? Ad[b0 + r][b0 + c] : F(0);
+  int bad = 0, nboost = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    F pv = d[j][j];
+    if (row0 + b0 + j >= nk) {
+      pv = F(1);
+    } else if (!isfinite(pv)) {
+      bad = 1;
+      pv = F(1);
+    } else if (sizeof(F) == 8) {
+      if (!(pv > F(0))) {
+        bad = 1;
+        pv = F(1);
+      }
+    } else if (pv < F(1.0 / 1048576)) {
+      ++nboost;
+      pv = F(1.0 / 4096);
+    }
+    const F is = rsqrt_w(pv);
+    d[j][j] = pv * is;
+    rinv[j] = is;
+#pragma unroll
+    for (int r = j + 1; r < 8; ++r) d[r][j] *= is;
+#pragma unroll
+    for (int c = j + 1; c < 8; ++c)
+#pragma unroll
+      for (int r = c; r < 8; ++r) d[r][c] -= d[r][j] * d[c][j];
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c) Ad[b0 + r][b0 + c] = d[r][c];
+  if (bad) *fail = 1;
+  if (nboost && boosted) atomicAdd(boosted, nboost);
+}
+
 // ------------------------------------------------------------------------------------------------------
 // Panel of tile step kt, one CTA per tile row i >= kt of a cluster (256 threads):
 //   1. fused update from step kt - 1 (kt > 0):  A_kt,kt -= L_kt,kt-1 L_kt,kt-1^T,  A_i,kt -= L_i,kt-1 L_kt,kt-1^T
 //      (the trailing update of the other tiles of step kt - 1 runs concurrently in k_chol_update);
 //   2. LL^T of the stacked panel [A_kt,kt; A_i,kt] in blocks of 8 columns (the diagonal tile redundantly
-//      in every CTA of the step): per block one thread factors the 8 x 8 diagonal block, eight threads
-//      invert it (Yb), the block column below becomes A Yb^T, and the columns to its right get the
-//      rank-8 update; rows of A_i,kt are just more rows below the diagonal, so they come out as L_i,kt;
-//   3. the CTA of i = kt also builds Y = L_kt,kt^-1 block row by block row (Y_b,<b = -Yb L_b,<b Y_<b,<b)
-//      and stores it, with its transpose, for the solves.
-// Dynamic shared memory: Ad, Ax (T x (T + 1)) and two T x LDV buffers that hold the transposed tiles of
-// the fused update, then Y and the block-row scratch.
+//      in every CTA of the step): per block one thread factors the 8 x 8 diagonal block, the block
+//      column below is solved against it row by row (forward substitution), and the columns to its
+//      right get the rank-8 update; rows of A_i,kt are just more rows below the diagonal, so they come
+//      out as L_i,kt.  The CTA of i = kt stores L_kt,kt, the others L_i,kt.
+// Dynamic shared memory: Ad, Ax (T x (T + 1)) and two T x LDV buffers for the transposed tiles of the
+// fused update.
 template <typename F, int T>
 struct PanelLayout {
   static constexpr int LDA = T + 1;
@@ -125,8 +172,8 @@ struct PanelLayout {
 };
 
 template <typename F, int T>
-__global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P, const int2* items, int kt,
-                                                    int* fail_flags, int* boosted, int64_t v_total) {
+__global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const int2* items, int kt, int* fail_flags,
+                                                    int* boosted) {
   using PL = PanelLayout<F, T>;
   constexpr int R = T / 16, LDA = PL::LDA, LDV = PL::LDV, NB = T / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -135,8 +182,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P,
   F* bufV = reinterpret_cast<F*>(Ax + T);
   F(*LkT)[LDV] = reinterpret_cast<F(*)[LDV]>(bufV);
   F(*LiT)[LDV] = LkT + T;
-  __shared__ F rinv[8];
-  __shared__ F Yb[8][9];
+  __shared__ F rinv2[2][8];   // reciprocal pivots of block b in rinv2[b & 1]
   const int2 it = items[blockIdx.x];
   const int k = it.x, i = it.y;
   const bool diag = (i == kt);
@@ -195,113 +241,58 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P,
       }
     __syncthreads();
   }
-  // the transposed-tile buffers are free: Y (T x LDA) and the block-row scratch W (8 x T), diagonal CTA only
-  F(*Y)[LDA] = reinterpret_cast<F(*)[LDA]>(bufV);
-  F(*W)[T] = reinterpret_cast<F(*)[T]>(bufV + (size_t)T * LDA);
-  if (diag) {
-    for (int idx = tid; idx < T * LDA; idx += 256) (&Y[0][0])[idx] = F(0);
-  }
-  // 2. blocked LL^T of the stacked panel
+  // 2. blocked LL^T of the stacked panel.  Per block b: the rows below are solved against L_bb; then warp 0
+  //    applies block b's rank-8 update to the next 8 x 8 diagonal block and lane 0 factors it, while warps
+  //    1..7 apply the update to the rest of the tile (look-ahead of one block).
+  if (tid == 0) chol8<F, LDA>(Ad, 0, kt * T, nk, rinv2[0], fail_flags + k, diag ? boosted : nullptr);
+  __syncthreads();
   for (int b = 0; b < NB; ++b) {
     const int b0 = 8 * b;
-    if (tid == 0) {
-      F d[8][8];
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) d[r][c] = (c <= r) ? Ad[b0 + r][b0 + c] : F(0);
-      int bad = 0, nboost = 0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        F pv = d[j][j];
-        if (kt * T + b0 + j >= nk) {
-          pv = F(1);   // padding row: identity
-        } else if (!isfinite(pv)) {
-          bad = 1;
-          pv = F(1);
-        } else if (sizeof(F) == 8) {
-          if (!(pv > F(0))) {
-            bad = 1;
-            pv = F(1);
-          }
-        } else if (pv < F(1.0 / 1048576)) {
-          ++nboost;   // static pivoting: a pivot that FP32 rounding made vanish
-          pv = F(1.0 / 4096);
-        }
-        const F is = rsqrt_w(pv);
-        d[j][j] = pv * is;
-        rinv[j] = is;
-#pragma unroll
-        for (int r = j + 1; r < 8; ++r) d[r][j] *= is;
-#pragma unroll
-        for (int c = j + 1; c < 8; ++c)
-#pragma unroll
-          for (int r = c; r < 8; ++r) d[r][c] -= d[r][j] * d[c][j];
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c <= r; ++c) Ad[b0 + r][b0 + c] = d[r][c];
-      if (bad) fail_flags[k] = 1;
-      if (nboost && diag && boosted) atomicAdd(boosted, nboost);
-    }
-    __syncthreads();
-    if (tid < 8) {
-      // column j = tid of Yb = L_bb^-1 by forward substitution (with 1 / l_rr = rinv[r])
-      const int j = tid;
-      F y[8];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        F s = (r == j) ? F(1) : F(0);
-#pragma unroll
-        for (int m = 0; m < r; ++m) s -= Ad[b0 + r][b0 + m] * y[m];
-        y[r] = (r < j) ? F(0) : s * rinv[r];
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        Yb[r][j] = y[r];
-        if (diag) Y[b0 + r][b0 + j] = y[r];
-      }
-    }
-    __syncthreads();
-    // block column below the diagonal block: L_rb = A_rb Yb^T, one row per thread (Ad rows, then Ax rows)
+    const F* rinv = rinv2[b & 1];
+    // block column below the diagonal block: L_rb L_bb^T = A_rb, one row per thread (Ad rows, then Ax rows)
     const int rows_d = T - b0 - 8;
     const int rows_tot = rows_d + (diag ? 0 : T);
     if (tid < rows_tot) {
       F* row = (tid < rows_d) ? &Ad[b0 + 8 + tid][0] : &Ax[tid - rows_d][0];
-      F a8[8], o8[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) a8[t] = row[b0 + t];
+      F o8[8];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
-        F s = F(0);
+        F s = row[b0 + c];
 #pragma unroll
-        for (int t = 0; t <= c; ++t) s += a8[t] * Yb[c][t];
-        o8[c] = s;
+        for (int t = 0; t < c; ++t) s -= o8[t] * Ad[b0 + c][b0 + t];
+        o8[c] = s * rinv[c];
       }
 #pragma unroll
       for (int c = 0; c < 8; ++c) row[b0 + c] = o8[c];
     }
-    if (diag) {   // block row of Y, first half: W = L_b,<b Y_<b,<b (8 x b0)
-      for (int e = tid; e < 8 * b0; e += 256) {
-        const int row = e / b0, col = e - (e / b0) * b0;
-        F s = F(0);
-        for (int t = col; t < b0; ++t) s += Ad[b0 + row][t] * Y[t][col];
-        W[row][col] = s;
-      }
-    }
     __syncthreads();
-    if (b + 1 < NB) {
-      // rank-8 update of the columns right of the block, register-blocked R x R: Ad (lower), then Ax
-      const int c0 = bj * R;
-      if (c0 + R > b0 + 8) {
+    if (b + 1 == NB) break;
+    const int n0 = b0 + 8;   // first column of the next block
+    if (tid < 32) {
+      // next diagonal block: entries (r, c), n0 <= c <= r < n0 + 8 (36 of them)
+      for (int e = tid; e < 36; e += 32) {
+        int rr = 0;
+        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+        const int cc = e - rr * (rr + 1) / 2;
+        F s = F(0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) s += Ad[n0 + rr][b0 + t] * Ad[n0 + cc][b0 + t];
+        Ad[n0 + rr][n0 + cc] -= s;
+      }
+      __syncwarp();
+      if (tid == 0) chol8<F, LDA>(Ad, n0, kt * T, nk, rinv2[(b + 1) & 1], fail_flags + k, diag ? boosted : nullptr);
+    } else {
+      // rank-8 update of the other columns right of the block, register-blocked R x R cells
+      for (int cell = tid - 32; cell < 256; cell += 224) {
+        const int ci = cell & 15, cj = cell >> 4;
+        const int c0 = cj * R, r0 = ci * R;
+        if (c0 + R <= n0) continue;
         F lc[R][8];
 #pragma unroll
         for (int cc = 0; cc < R; ++cc)
 #pragma unroll
           for (int t = 0; t < 8; ++t) lc[cc][t] = Ad[c0 + cc][b0 + t];
-        const int r0 = bi * R;
-        if (bj <= bi && r0 + R > b0 + 8) {
+        if (cj <= ci && r0 + R > n0) {
 #pragma unroll
           for (int a = 0; a < R; ++a) {
             F lr[8];
@@ -310,7 +301,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P,
 #pragma unroll
             for (int cc = 0; cc < R; ++cc) {
               const int r = r0 + a, c = c0 + cc;
-              if (c <= r && c >= b0 + 8) {
+              if (c <= r && c >= n0 && r >= n0 + 8) {
                 F s = F(0);
 #pragma unroll
                 for (int t = 0; t < 8; ++t) s += lr[t] * lc[cc][t];
@@ -328,7 +319,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P,
 #pragma unroll
             for (int cc = 0; cc < R; ++cc) {
               const int c = c0 + cc;
-              if (c >= b0 + 8) {
+              if (c >= n0) {
                 F s = F(0);
 #pragma unroll
                 for (int t = 0; t < 8; ++t) s += xr[t] * lc[cc][t];
@@ -339,16 +330,6 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P,
         }
       }
     }
-    if (diag) {   // block row of Y, second half: Y_b,<b = -Yb W
-      for (int e = tid; e < 8 * b0; e += 256) {
-        const int row = e / b0, col = e - (e / b0) * b0;
-        F s = F(0);
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-          if (t <= row) s += Yb[row][t] * W[t][col];
-        Y[b0 + row][col] = -s;
-      }
-    }
     __syncthreads();
   }
   // 3. outputs
@@ -357,18 +338,75 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Dinv, DevProblem P,
       const int r = idx / T, c = idx - (idx / T) * T;
       if (c <= r) A[base_kk + (size_t)r * np + c] = Ad[r][c];
     }
-    F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
-    F* DiT = Di + v_total * T;
-    for (int idx = tid; idx < T * T; idx += 256) {
-      const int r = idx / T, c = idx - (idx / T) * T;
-      Di[idx] = Y[r][c];
-      DiT[idx] = Y[c][r];
-    }
     return;
   }
   for (int idx = tid; idx < T * T; idx += 256) {
     const int r = idx / T, c = idx - (idx / T) * T;
     A[base_ik + (size_t)r * np + c] = Ax[r][c];
+  }
+}
+
+// Inverse Y of every diagonal tile of the factor (for the solves), one CTA per tile, by recursive doubling:
+// the inverses of the 8 x 8 diagonal blocks by forward substitution (8 threads per block), then for
+// h = 8, 16, .. T/2 the off-diagonal block of every 2h x 2h diagonal block, Y21 = -Y22 (L21 Y11), as two
+// parallel products.  Writes Y row-major and its transpose at offset v_total * T.
+template <typename F, int T>
+__global__ void __launch_bounds__(256) k_diag_inverse(const F* L, F* Dinv, DevProblem P, const int2* items,
+                                                      int64_t v_total) {
+  __shared__ F D[T][T + 1];
+  __shared__ F Y[T][T + 1];
+  __shared__ F Z[T * T / 2];
+  const int2 it = items[blockIdx.x];
+  const int k = it.x, t = it.y;
+  const int np = P.cluster_np[k];
+  const F* A = L + P.S_off[k];
+  const size_t base = (size_t)(t * T) * np + t * T;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    D[r][c] = (c <= r) ? A[base + (size_t)r * np + c] : F(0);
+    Y[r][c] = F(0);
+  }
+  __syncthreads();
+  if (tid < T) {   // column j of the inverse of diagonal block blk
+    const int blk = tid >> 3, j = tid & 7, b0 = 8 * blk;
+    F y[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      F s = (r == j) ? F(1) : F(0);
+#pragma unroll
+      for (int m = 0; m < r; ++m) s -= D[b0 + r][b0 + m] * y[m];
+      y[r] = (r < j) ? F(0) : s / D[b0 + r][b0 + r];
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) Y[b0 + r][b0 + j] = y[r];
+  }
+  __syncthreads();
+  for (int h = 8; h < T; h *= 2) {
+    const int n_out = T * h / 2;   // (T / 2h) pairs x h x h
+    for (int e = tid; e < n_out; e += 256) {
+      const int p = e / (h * h), rr = (e / h) % h, cc = e % h;
+      const int r2 = (2 * p + 1) * h + rr, c1 = 2 * p * h + cc;
+      F s = F(0);
+      for (int q = cc; q < h; ++q) s += D[r2][2 * p * h + q] * Y[2 * p * h + q][c1];
+      Z[e] = s;   // (L21 Y11)[rr][cc]
+    }
+    __syncthreads();
+    for (int e = tid; e < n_out; e += 256) {
+      const int p = e / (h * h), rr = (e / h) % h, cc = e % h;
+      const int r2 = (2 * p + 1) * h + rr, c1 = 2 * p * h + cc;
+      F s = F(0);
+      for (int q = 0; q <= rr; ++q) s += Y[r2][(2 * p + 1) * h + q] * Z[p * h * h + q * h + cc];
+      Y[r2][c1] = -s;
+    }
+    __syncthreads();
+  }
+  F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)t * T * T;
+  F* DiT = Di + v_total * T;
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    Di[idx] = Y[r][c];
+    DiT[idx] = Y[c][r];
   }
 }
 
@@ -652,6 +690,23 @@ __global__ void k_count_failures(const int* fail_flags, int l, DevState* st) {
 
 // ------------------------------------------------------------------------------------------------------
 // Host launchers
+
+// A 256-thread launch with a scheduling priority (kept by graph capture as a node attribute): the panels
+// on the critical path go first, the trailing updates fill the remaining SMs.
+template <typename... KArgs, typename... Args>
+void launch_prio(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t stream, int prio, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = prio;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 template <typename F>
 void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
                    cudaStream_t stream) {
@@ -672,16 +727,19 @@ void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb
     if (kt >= 2) cudaStreamWaitEvent(stream, plan.ev_update[kt - 2], 0);
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
     if (npn > 0)
-      k_chol_panel<F, T><<<npn, 256, PanelLayout<F, T>::bytes, stream>>>(
-          L, Dinv, P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags, fb.boosted, fb.v_total);
+      launch_prio(k_chol_panel<F, T>, npn, PanelLayout<F, T>::bytes, stream, plan.prio_high, L, P,
+                  plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags, fb.boosted);
     cudaEventRecord(plan.ev_panel[kt], stream);
     cudaStreamWaitEvent(side, plan.ev_panel[kt], 0);
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];
-    if (nu > 0) k_chol_update<F, T><<<nu, 256, 0, side>>>(L, P, plan.update_items + plan.h_update_off[kt], kt);
+    if (nu > 0)
+      launch_prio(k_chol_update<F, T>, nu, 0, side, plan.prio_low, L, P, plan.update_items + plan.h_update_off[kt], kt);
     cudaEventRecord(plan.ev_update[kt], side);
   }
   cudaEventRecord(plan.ev_join, side);
   cudaStreamWaitEvent(stream, plan.ev_join, 0);
+  if (plan.n_diag_items > 0)
+    k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(L, Dinv, P, plan.diag_items, fb.v_total);
 }
 
 template <typename F>

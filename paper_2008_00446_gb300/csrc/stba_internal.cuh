@@ -135,11 +135,14 @@ struct CholPlan {
   const int2* update_items;  // (cluster, (i << 16) | j) for every step, concatenated
   const int2* res_items;     // (cluster, 32-row block) of the refinement residual
   int n_res_items;
+  const int2* diag_items;    // (cluster, diagonal tile) for the inverses of the diagonal tiles
+  int n_diag_items;
   int nsteps;
   const int* h_panel_off;    // host arrays [nsteps + 1] (launch sizes)
   const int* h_update_off;
   int max_np;
   cudaStream_t side_stream;  // second stream of the trailing updates, joined back before the solves
+  int prio_high, prio_low;   // launch priorities of the panels and of the trailing updates
   cudaEvent_t ev_fork, ev_join;
   const cudaEvent_t* ev_panel;    // [nsteps]
   const cudaEvent_t* ev_update;   // [nsteps]
