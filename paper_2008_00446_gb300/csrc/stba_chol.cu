@@ -465,19 +465,47 @@ __device__ F warp_sum(F v) {
 // memory; at tile step `it` CTA `rank` forms the partial product of the tiles it owns (tile columns j <
 // it with j = rank mod CS for the forward pass, tile rows j > it for the backward pass), the partials are
 // exchanged through distributed shared memory after one cluster barrier, and every CTA applies the stored
-// inverse of the diagonal tile redundantly, so the next step needs no further synchronisation.
+// inverse of the diagonal tile redundantly, so the next step needs no further synchronisation.  The tiles
+// do not depend on the vector: the owned tiles of step it + 1 (up to SOLVE_PF of them) and its diagonal
+// inverse are copied into shared memory (cp.async, double-buffered) while step it computes.
 constexpr int SOLVE_CS = 8;
+constexpr int SOLVE_PF = 2;
 
-// out[r] = sum_c M[r][c] v[c] for a T x T row-major tile M (global) and v in shared memory; 256 threads,
-// 256 / T threads per row, each a contiguous slice of the row.
 template <typename F, int T>
-__device__ __forceinline__ void tile_matvec(const F* __restrict__ M, const F* v, F* out) {
-  constexpr int PARTS = 256 / T, LEN = T / PARTS;
+struct SolveLayout {
+  static constexpr int LDT = T + 16 / (int)sizeof(F);   // padded rows, 16-byte aligned
+  static constexpr size_t tile_elems = (size_t)T * LDT;
+  // [2 buffers][SOLVE_PF tiles + 1 diagonal inverse][T][LDT], then the vector y
+  static constexpr size_t fixed_bytes = sizeof(F) * 2 * (SOLVE_PF + 1) * tile_elems;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// T x T tile at src (row stride ld elements) into padded shared rows
+template <typename F, int T>
+__device__ __forceinline__ void prefetch_tile(F* dst, const F* src, size_t ld) {
+  constexpr int CH = T * (int)sizeof(F) / 16;   // 16-byte chunks per row
+  constexpr int LDT = SolveLayout<F, T>::LDT;
+  for (int q = threadIdx.x; q < T * CH; q += blockDim.x) {
+    const int r = q / CH, c = q - (q / CH) * CH;
+    cp_async16(dst + (size_t)r * LDT + c * (16 / sizeof(F)), src + (size_t)r * ld + c * (16 / sizeof(F)));
+  }
+}
+
+// out[r] = sum_c M[r][c] v[c], M a padded shared tile; 256 / T threads per row
+template <typename F, int T>
+__device__ __forceinline__ void smem_matvec(const F* M, const F* v, F* out) {
+  constexpr int PARTS = 256 / T, LEN = T / PARTS, LDT = SolveLayout<F, T>::LDT;
   const int r = threadIdx.x / PARTS, part = threadIdx.x - (threadIdx.x / PARTS) * PARTS;
-  const F* row = M + (size_t)r * T + part * LEN;
+  const F* row = M + (size_t)r * LDT + part * LEN;
   F s = F(0);
 #pragma unroll
-  for (int c = 0; c < LEN; ++c) s += __ldg(row + c) * v[part * LEN + c];
+  for (int c = 0; c < LEN; ++c) s += row[c] * v[part * LEN + c];
 #pragma unroll
   for (int d = PARTS / 2; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
   if (part == 0) out[r] = s;
@@ -487,96 +515,113 @@ template <typename F, int T, typename Rreal>
 __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, const F* Dinv, const double* scale,
                                                    const Rreal* rhs, double* x, int accumulate, int64_t v_total) {
   namespace cg = cooperative_groups;
+  using SL = SolveLayout<F, T>;
+  constexpr int PARTS = 256 / T, LEN = T / PARTS, LDT = SL::LDT;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  F* y = reinterpret_cast<F*>(smem_raw);
+  F* buf = reinterpret_cast<F*>(smem_raw);                   // [2][SOLVE_PF + 1][T][LDT]
+  F* y = buf + 2 * (SOLVE_PF + 1) * SL::tile_elems;
   __shared__ F partial[2][T];
   __shared__ F t[T];
-  __shared__ F part8[8][T];
+  __shared__ F pcol[PARTS][T];
   const int rank = (int)cluster.block_rank();
   const int k = blockIdx.x / SOLVE_CS;
   const int np = P.cluster_np[k];
   const F* A = L + P.S_off[k];
   const F* Di = Dinv + (size_t)P.v_off[k] * T;
+  const F* DiT = Di + v_total * T;
   const double* sk = scale + P.v_off[k];
   const Rreal* rk = rhs + P.v_off[k];
   double* xk = x + P.v_off[k];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = np / T;
-  constexpr int RW = T / 8;   // rows per warp within a tile
-  for (int i = threadIdx.x; i < np; i += blockDim.x) y[i] = (F)((double)rk[i] * sk[i]);
-  __syncthreads();
-  int step = 0;
-  // forward: L y = s o rhs
-  for (int it = 0; it < nt; ++it, ++step) {
+  const int tid = threadIdx.x;
+  auto tile_buf = [&](int parity, int slot) { return buf + ((size_t)parity * (SOLVE_PF + 1) + slot) * SL::tile_elems; };
+  // step s = 0 .. 2 nt - 1: forward steps it = s, backward steps it = 2 nt - 1 - s
+  auto issue = [&](int s) {
+    if (s < 2 * nt) {
+      const bool fwd = s < nt;
+      const int it = fwd ? s : 2 * nt - 1 - s;
+      int m = 0;
+      if (fwd) {
+        for (int j = rank; j < it && m < SOLVE_PF; j += SOLVE_CS, ++m)
+          prefetch_tile<F, T>(tile_buf(s & 1, m), A + (size_t)(it * T) * np + j * T, np);
+      } else {
+        for (int j = it + 1 + rank; j < nt && m < SOLVE_PF; j += SOLVE_CS, ++m)
+          prefetch_tile<F, T>(tile_buf(s & 1, m), A + (size_t)(j * T) * np + it * T, np);
+      }
+      prefetch_tile<F, T>(tile_buf(s & 1, SOLVE_PF), (fwd ? Di : DiT) + (size_t)it * T * T, T);
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  for (int i = tid; i < np; i += blockDim.x) y[i] = (F)((double)rk[i] * sk[i]);
+  for (int s = 0; s < 2 * nt; ++s) {
+    issue(s + 1);
+    cp_async_wait1();
+    __syncthreads();
+    const bool fwd = s < nt;
+    const int it = fwd ? s : 2 * nt - 1 - s;
     const int r0 = it * T;
-    F acc[RW];
+    if (fwd) {
+      // partial[r] = sum over owned tiles j of L[it][j] y_j: thread (row, part)
+      const int r = tid / PARTS, part = tid - (tid / PARTS) * PARTS;
+      F acc = F(0);
+      int m = 0;
+      for (int j = rank; j < it; j += SOLVE_CS, ++m) {
+        const F* yj = y + j * T + part * LEN;
+        if (m < SOLVE_PF) {
+          const F* row = tile_buf(s & 1, m) + (size_t)r * LDT + part * LEN;
 #pragma unroll
-    for (int q = 0; q < RW; ++q) acc[q] = F(0);
-    for (int j = rank; j < it; j += SOLVE_CS) {
-      const F* blk = A + (size_t)(r0 + warp * RW) * np + j * T;
+          for (int c = 0; c < LEN; ++c) acc += row[c] * yj[c];
+        } else {
+          const F* row = A + (size_t)(r0 + r) * np + j * T + part * LEN;
 #pragma unroll
-      for (int cc = 0; cc < T; cc += 32) {
-        const F yc = y[j * T + cc + lane];
+          for (int c = 0; c < LEN; ++c) acc += __ldg(row + c) * yj[c];
+        }
+      }
 #pragma unroll
-        for (int q = 0; q < RW; ++q) acc[q] += blk[(size_t)q * np + cc + lane] * yc;
+      for (int d = PARTS / 2; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+      if (part == 0) partial[s & 1][r] = acc;
+    } else {
+      // partial[c] = sum over owned tiles j of L[j][it]^T z_j: thread (column, part of the rows)
+      const int c = tid % T, part = tid / T;
+      F acc = F(0);
+      int m = 0;
+      for (int j = it + 1 + rank; j < nt; j += SOLVE_CS, ++m) {
+        const F* zj = y + j * T + part * LEN;
+        if (m < SOLVE_PF) {
+          const F* col = tile_buf(s & 1, m) + (size_t)(part * LEN) * LDT + c;
+#pragma unroll
+          for (int rr = 0; rr < LEN; ++rr) acc += col[(size_t)rr * LDT] * zj[rr];
+        } else {
+          const F* col = A + (size_t)(j * T + part * LEN) * np + r0 + c;
+#pragma unroll
+          for (int rr = 0; rr < LEN; ++rr) acc += __ldg(col + (size_t)rr * np) * zj[rr];
+        }
+      }
+      pcol[part][c] = acc;
+      __syncthreads();
+      if (tid < T) {
+        F v = F(0);
+#pragma unroll
+        for (int q = 0; q < PARTS; ++q) v += pcol[q][tid];
+        partial[s & 1][tid] = v;
       }
     }
-#pragma unroll
-    for (int q = 0; q < RW; ++q) {
-      const F s = warp_sum(acc[q]);
-      if (lane == 0) partial[step & 1][warp * RW + q] = s;
-    }
     cluster.sync();
-    for (int r = threadIdx.x; r < T; r += blockDim.x) {
-      F s = F(0);
+    for (int r = tid; r < T; r += blockDim.x) {
+      F sum = F(0);
 #pragma unroll
-      for (int c = 0; c < SOLVE_CS; ++c) s += cluster.map_shared_rank(&partial[step & 1][0], c)[r];
-      t[r] = y[r0 + r] - s;
+      for (int q = 0; q < SOLVE_CS; ++q) sum += cluster.map_shared_rank(&partial[s & 1][0], q)[r];
+      t[r] = y[r0 + r] - sum;
     }
     __syncthreads();
-    tile_matvec<F, T>(Di + (size_t)it * T * T, t, y + r0);
-    __syncthreads();
-  }
-  // backward: L^T z = y
-  for (int it = nt - 1; it >= 0; --it, ++step) {
-    const int r0 = it * T;
-    constexpr int NC = T / 32;
-    F p[NC];
-#pragma unroll
-    for (int u = 0; u < NC; ++u) p[u] = F(0);
-    for (int j = it + 1 + rank; j < nt; j += SOLVE_CS) {
-      const F* blk = A + (size_t)(j * T) * np + r0;
-#pragma unroll 4
-      for (int rr = warp; rr < T; rr += 8) {
-        const F zc = y[j * T + rr];
-#pragma unroll
-        for (int u = 0; u < NC; ++u) p[u] += blk[(size_t)rr * np + lane + 32 * u] * zc;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < NC; ++u) part8[warp][lane + 32 * u] = p[u];
-    __syncthreads();
-    for (int cc = threadIdx.x; cc < T; cc += blockDim.x) {
-      F s = F(0);
-#pragma unroll
-      for (int w = 0; w < 8; ++w) s += part8[w][cc];
-      partial[step & 1][cc] = s;
-    }
-    cluster.sync();
-    for (int r = threadIdx.x; r < T; r += blockDim.x) {
-      F s = F(0);
-#pragma unroll
-      for (int c = 0; c < SOLVE_CS; ++c) s += cluster.map_shared_rank(&partial[step & 1][0], c)[r];
-      t[r] = y[r0 + r] - s;
-    }
-    __syncthreads();
-    // z_tile = Dinv^T t through the stored transpose
-    tile_matvec<F, T>(Di + v_total * T + (size_t)it * T * T, t, y + r0);
+    // y_it = D_it^-1 t (forward) or D_it^-T t (backward, through the stored transpose)
+    smem_matvec<F, T>(tile_buf(s & 1, SOLVE_PF), t, y + r0);
     __syncthreads();
   }
   if (rank == 0)
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    for (int i = tid; i < np; i += blockDim.x) {
       const double v = (double)y[i] * sk[i];
       xk[i] = accumulate ? xk[i] + v : v;
     }
@@ -589,7 +634,7 @@ void launch_tri_solve(const DevProblem& P, const F* L, const F* Dinv, const doub
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(P.l * SOLVE_CS);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = sizeof(F) * (size_t)max_np;
+  cfg.dynamicSmemBytes = SolveLayout<F, T>::fixed_bytes + sizeof(F) * (size_t)max_np;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -765,7 +810,8 @@ void configure_solve_kernels(int max_np) {
                        (int)PanelLayout<float, 64>::bytes);
   cudaFuncSetAttribute(k_chol_panel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)PanelLayout<double, 32>::bytes);
-  const int s32 = (int)(sizeof(float) * (size_t)max_np), s64 = (int)(sizeof(double) * (size_t)max_np);
+  const int s32 = (int)(SolveLayout<float, 64>::fixed_bytes + sizeof(float) * (size_t)max_np);
+  const int s64 = (int)(SolveLayout<double, 32>::fixed_bytes + sizeof(double) * (size_t)max_np);
   cudaFuncSetAttribute(k_tri_solve<float, 64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
   cudaFuncSetAttribute(k_tri_solve<double, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
 }
