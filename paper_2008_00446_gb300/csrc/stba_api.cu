@@ -82,6 +82,8 @@ struct stba_ctx {
   void *vp_acc = nullptr, *vp_info = nullptr, *pt_info = nullptr, *S = nullptr, *b = nullptr, *vgrad = nullptr,
        *t_acc = nullptr;
   double *dc = nullptr, *dp = nullptr, *partial = nullptr, *cam_rt = nullptr;
+  float *cam_df = nullptr, *pt_df = nullptr;   // double-float tables of the mixed-mode cost
+  float4* obs_uvdf = nullptr;
   void *res_cur = nullptr, *res_cand = nullptr;   // residuals at x and at x + dx (working precision)
   DevState* st = nullptr;
 
@@ -198,6 +200,7 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.obs_pt = c->obs_pt;
   P.obs_uv = c->obs_uv;
   P.obs_uvf = c->obs_uvf;
+  P.obs_uvdf = c->obs_uvdf;
   P.vp_off = c->vp_off;
   P.vp_point = c->vp_point;
   P.pt_vp_off = c->pt_vp_off;
@@ -304,6 +307,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   std::vector<int> s_cam(q), s_vp(q), s_pt(q), vp_off, vp_point, pt_vp_off(n + 1, 0);
   std::vector<double> s_uv(2 * (size_t)q);
   std::vector<float> s_uvf(c->mixed ? 2 * (size_t)q : 0);
+  std::vector<float4> s_uvdf(c->mixed ? (size_t)q : 0);
   vp_off.reserve(q + 1);
   vp_point.reserve(q);
   for (int i = 0; i < n; ++i) {
@@ -323,8 +327,11 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
       s_uv[2 * (size_t)o] = c->in_uv[2 * (size_t)src];
       s_uv[2 * (size_t)o + 1] = c->in_uv[2 * (size_t)src + 1];
       if (c->mixed) {
-        s_uvf[2 * (size_t)o] = (float)s_uv[2 * (size_t)o];
-        s_uvf[2 * (size_t)o + 1] = (float)s_uv[2 * (size_t)o + 1];
+        const double u = s_uv[2 * (size_t)o], v = s_uv[2 * (size_t)o + 1];
+        s_uvf[2 * (size_t)o] = (float)u;
+        s_uvf[2 * (size_t)o + 1] = (float)v;
+        const float uh = (float)u, vh = (float)v;
+        s_uvdf[o] = make_float4(uh, (float)(u - (double)uh), vh, (float)(v - (double)vh));
       }
     }
   }
@@ -417,9 +424,9 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
       factor_launches += (c->h_panel_off[kt + 1] > c->h_panel_off[kt]) + (c->h_update_off[kt + 1] > c->h_update_off[kt]);
     const int build_launches = 1 + (npairs > 0 ? 1 : 0);
     const int solve_launches = 2 + c->set.refine_steps * (2 + (res_items.empty() ? 0 : 1));
-    // iter_begin, vp_reduce, vp_finalize | build | factor | solve, count | rhs, update, cam_rt, cost, finalize,
-    // apply
-    c->launches_per_iter = 3 + build_launches + factor_launches + solve_launches + 1 + 6;
+    // iter_begin, vp_reduce, vp_finalize | build | factor | solve, count | rhs, update, cam_rt, (cam_df,
+    // point_df,) cost, finalize, apply
+    c->launches_per_iter = 3 + build_launches + factor_launches + solve_launches + 1 + 6 + (c->mixed ? 2 : 0);
     c->factor_flops = 0;
     for (int k = 0; k < l; ++k) c->factor_flops += std::pow((double)c->h_nk[k], 3) / 3.0;
   }
@@ -436,6 +443,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(c->obs_perm, perm);
   UP(c->obs_uv, s_uv);
   if (c->mixed) UP(c->obs_uvf, s_uvf);
+  if (c->mixed) UP(c->obs_uvdf, s_uvdf);
   UP(c->vp_off, vp_off);
   UP(c->vp_point, vp_point);
   UP(c->pt_vp_off, pt_vp_off);
@@ -494,7 +502,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   }
   if ((s = ralloc(&c->vgrad, 9 * (size_t)m)) != STBA_OK) return s;
   if ((s = ralloc(&c->t_acc, 3 * (size_t)n)) != STBA_OK) return s;
-  if ((s = ralloc(&c->Gbuf, 32 * (size_t)q)) != STBA_OK) return s;
+  if ((s = ralloc(&c->Gbuf, 36 * (size_t)q)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.L, (size_t)c->S_total)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.Dinv, 2 * (size_t)c->v_total * TF)) != STBA_OK) return s;
   if ((s = dalloc(c, &c->fbuf.scale, (size_t)c->v_total, true)) != STBA_OK) return s;
@@ -560,7 +568,7 @@ void enqueue_iteration(stba_ctx* c) {
   const Scratch<real> W = scratch<real>(c);
   cudaStream_t s = c->stream;
   enqueue_step<real>(c, true);
-  launch_cost<real>(P, c->dc, c->dp, c->cam_rt, c->partial, c->st, (real*)c->res_cand, s);
+  launch_cost<real>(P, c->dc, c->dp, c->cam_rt, c->cam_df, c->pt_df, c->partial, c->st, (real*)c->res_cand, s);
   launch_finalize<real>(P, W, c->st, c->set, 1, s);
   launch_apply<real>(P, c->dc, c->dp, c->cams, c->pts, (const real*)c->res_cand, (real*)c->res_cur, c->st, s);
   record_stage(c, 5);
@@ -571,7 +579,8 @@ void enqueue_cost(stba_ctx* c) {
   const DevProblem P = dev_problem(c);
   const Scratch<real> W = scratch<real>(c);
   launch_iter_begin<real>(c->st, c->set, c->stream);
-  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, c->partial, c->st, (real*)c->res_cur, c->stream);
+  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, nullptr, nullptr, c->partial, c->st, (real*)c->res_cur,
+                    c->stream);
   launch_finalize<real>(P, W, c->st, c->set, 0, c->stream);
 }
 
@@ -664,7 +673,8 @@ void enqueue_adjoint_step(stba_ctx* c, double lam, const AdjointBuffers& A) {
   launch_set_lambda(c->st, lam, c->stream);
   launch_iter_begin<real>(c->st, c->set, c->stream);
   const DevProblem P = dev_problem(c);
-  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, c->partial, c->st, (real*)c->res_cur, c->stream);
+  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, nullptr, nullptr, c->partial, c->st, (real*)c->res_cur,
+                    c->stream);
   enqueue_step<real>(c, false);
   launch_adjoint_step<real>(P, scratch<real>(c), c->clist, c->fbuf, c->cplan, c->set.refine_steps, c->obs_perm, lam,
                             A, c->stream);
@@ -846,8 +856,10 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   if ((s = dalloc(c, &c->pts, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->dc, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->dp, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->partial, 3 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->partial, 6 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->cam_rt, 15 * (size_t)m, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->cam_df, 28 * (size_t)m, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->pt_df, 6 * (size_t)n, false)) != STBA_OK) return bail(s);
   {
     char *r1, *r2;
     const size_t rsz = 2 * (size_t)q * (c->mixed ? sizeof(float) : sizeof(double));

@@ -24,6 +24,7 @@ struct DevProblem {
   const int* obs_pt;       // [q] point of each sorted observation
   const double* obs_uv;    // [q][2] FP64 observations
   const float* obs_uvf;    // [q][2] FP32 copy (mixed precision)
+  const float4* obs_uvdf;  // [q] double-float copy (u_hi, u_lo, v_hi, v_lo) (mixed precision)
   const int* vp_off;       // [nv+1] observation range of each virtual point
   const int* vp_point;     // [nv] point of each virtual point
   const int* pt_vp_off;    // [n+1] virtual-point range of each point
@@ -114,10 +115,12 @@ template <typename real>
 void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
 template <typename real>
 void launch_point_update(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
-// k_cam_rt + k_cost: rt is a [m][15] FP64 scratch (R, t, f, k1, k2 of x + dx); residuals go to rout.
+// k_cam_rt + k_cost: rt is a [m][15] FP64 scratch (R, t, f, k1, k2 of x + dx); residuals go to rout.  In mixed
+// mode with a step, the cost runs in double-float arithmetic with the scratch tables cam_df [m][28] and
+// pt_df [n][6] (floats).
 template <typename real>
-void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, double* partial, DevState* st,
-                 real* rout, cudaStream_t stream);
+void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, float* cam_df, float* pt_df,
+                 double* partial, DevState* st, real* rout, cudaStream_t stream);
 // with_step = 1: stop tests and accept / reject of the step in W.dc / W.dp; 0: F(x) -> st->F.
 template <typename real>
 void launch_finalize(const DevProblem& P, Scratch<real> W, DevState* st, const Settings& s, int with_step,

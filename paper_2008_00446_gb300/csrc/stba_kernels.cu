@@ -193,7 +193,24 @@ void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cuda
 // (zeroed before the launch): FP32 terms, FP64 accumulation across warps.  The per-observation arithmetic
 // stays off the FP64 pipe, which on this GPU runs at 1/64 of the FP32 rate.  It also stores G_o of every
 // observation of a multi-observation virtual point for the pair pass.
-constexpr int GSTRIDE = 32;   // reals per stored G_o (27 used)
+// G_o is stored column by column, four reals per camera-parameter column c (G[0][c], G[1][c], G[2][c], 0),
+// so that the pair pass reads a column with one 16-byte (FP32) load.
+constexpr int GSTRIDE = 36;   // reals per stored G_o
+
+template <typename real>
+__device__ __forceinline__ void load_gcol(const real* p, real (&v)[3]) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+  } else {
+    const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = __ldg(p + 2);
+  }
+}
 
 // On return lane L holds the sum over the warp's lanes of v[L].  Each halving step keeps one half of the
 // values (lanes whose bit s is set keep the upper half) and adds the partner's copy of it.
@@ -277,22 +294,19 @@ __global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real>
       N00 = real(1) - (Pm[0][0] * Pm[0][0] + Pm[1][0] * Pm[1][0] + Pm[2][0] * Pm[2][0]);
       N01 = -(Pm[0][0] * Pm[0][1] + Pm[1][0] * Pm[1][1] + Pm[2][0] * Pm[2][1]);
       N11 = real(1) - (Pm[0][1] * Pm[0][1] + Pm[1][1] * Pm[1][1] + Pm[2][1] * Pm[2][1]);
-      // G = L^-1 Jp^T Jc = P Jc (3x9), stored row-major (9 s + c) with 16-byte vector stores
-      real g[GSTRIDE];
-#pragma unroll
-      for (int s = 0; s < 3; ++s)
-#pragma unroll
-        for (int c = 0; c < 9; ++c) g[9 * s + c] = Pm[s][0] * Jc[0][c] + Pm[s][1] * Jc[1][c];
-#pragma unroll
-      for (int c = 27; c < GSTRIDE; ++c) g[c] = 0;
+      // G = L^-1 Jp^T Jc = P Jc (3x9), stored by columns with 16-byte vector stores
       real* Gs = Gbuf + (size_t)GSTRIDE * o;
-      if constexpr (sizeof(real) == 4) {
 #pragma unroll
-        for (int q4 = 0; q4 < 7; ++q4)
-          reinterpret_cast<float4*>(Gs)[q4] = make_float4(g[4 * q4], g[4 * q4 + 1], g[4 * q4 + 2], g[4 * q4 + 3]);
-      } else {
-#pragma unroll
-        for (int q2 = 0; q2 < 14; ++q2) reinterpret_cast<double2*>(Gs)[q2] = make_double2(g[2 * q2], g[2 * q2 + 1]);
+      for (int c = 0; c < 9; ++c) {
+        const real g0 = Pm[0][0] * Jc[0][c] + Pm[0][1] * Jc[1][c];
+        const real g1 = Pm[1][0] * Jc[0][c] + Pm[1][1] * Jc[1][c];
+        const real g2 = Pm[2][0] * Jc[0][c] + Pm[2][1] * Jc[1][c];
+        if constexpr (sizeof(real) == 4) {
+          reinterpret_cast<float4*>(Gs)[c] = make_float4(g0, g1, g2, 0.f);
+        } else {
+          reinterpret_cast<double2*>(Gs)[2 * c] = make_double2(g0, g1);
+          reinterpret_cast<double2*>(Gs)[2 * c + 1] = make_double2(g2, 0.0);
+        }
       }
       br[0] = r[0] + Jp[0][0] * vi[6] + Jp[0][1] * vi[7] + Jp[0][2] * vi[8];
       br[1] = r[1] + Jp[1][0] * vi[6] + Jp[1][1] * vi[7] + Jp[1][2] * vi[8];
@@ -380,14 +394,18 @@ __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> 
       cur = pr;
     }
     if (act) {
-      const real* Ga = Gbuf + (size_t)GSTRIDE * pr.x;
-      const real* Gb = Gbuf + (size_t)GSTRIDE * pr.y + 3 * cg;
+      const real* Ga = Gbuf + (size_t)GSTRIDE * pr.x + 4 * r;
+      const real* Gb = Gbuf + (size_t)GSTRIDE * pr.y + 4 * (3 * cg);
+      real a[3], b0[3], b1[3], b2[3];
+      load_gcol(Ga, a);
+      load_gcol(Gb, b0);
+      load_gcol(Gb + 4, b1);
+      load_gcol(Gb + 8, b2);
 #pragma unroll
       for (int s = 0; s < 3; ++s) {
-        const real a = __ldg(Ga + 9 * s + r);
-        acc0 += a * __ldg(Gb + 9 * s);
-        acc1 += a * __ldg(Gb + 9 * s + 1);
-        acc2 += a * __ldg(Gb + 9 * s + 2);
+        acc0 += a[s] * b0[s];
+        acc1 += a[s] * b1[s];
+        acc2 += a[s] * b2[s];
       }
     }
   }
@@ -443,10 +461,14 @@ __global__ void __launch_bounds__(256) k_point_rhs(DevProblem P, const double* d
   segmented_store<3>(val, pt, act, lane, o, P.pt_off, t_acc);
 }
 
+// dp = C^-1 (w - t) per point; the same grid also forms the partial sums of the stop tests: |dp|^2, |p|^2,
+// |dc|^2, |c|^2 and max |v| (camera gradient), one partial per block at partial[RED_BLOCKS * (1..5) + block].
 template <typename real>
 __global__ void __launch_bounds__(256) k_point_update(DevProblem P, const real* pt_info, const real* t_acc,
-                                                      double* dp, double* partial) {
-  double s_dp = 0.0, s_p = 0.0;
+                                                      const double* dc, const real* vgrad, double* dp,
+                                                      double* partial) {
+  double s_dp = 0.0, s_p = 0.0, s_dc = 0.0, s_c = 0.0;
+  real gmax = real(0);   // max |v| in the working precision (exact)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
     const real* in = pt_info + 9 * (size_t)i;
     const real* t = t_acc + 3 * (size_t)i;
@@ -462,25 +484,39 @@ __global__ void __launch_bounds__(256) k_point_update(DevProblem P, const real* 
     const double* p = P.pts + 3 * (size_t)i;
     s_p += p[0] * p[0] + p[1] * p[1] + p[2] * p[2];
   }
-  __shared__ double red[2][8];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * P.m; i += gridDim.x * blockDim.x) {
+    const double d = dc[i], c = P.cams[i];
+    s_dc += d * d;
+    s_c += c * c;
+    gmax = fmax(gmax, fabs(vgrad[i]));
+  }
+  __shared__ double red[4][8];
+  __shared__ real redm[8];
   for (int d = 16; d > 0; d >>= 1) {
     s_dp += __shfl_xor_sync(FULL_MASK, s_dp, d);
     s_p += __shfl_xor_sync(FULL_MASK, s_p, d);
+    s_dc += __shfl_xor_sync(FULL_MASK, s_dc, d);
+    s_c += __shfl_xor_sync(FULL_MASK, s_c, d);
+    gmax = fmax(gmax, __shfl_xor_sync(FULL_MASK, gmax, d));
   }
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     red[0][w] = s_dp;
     red[1][w] = s_p;
+    red[2][w] = s_dc;
+    red[3][w] = s_c;
+    redm[w] = gmax;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0;
+    double a[4] = {0, 0, 0, 0};
+    real mx = real(0);
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-      a += red[0][i];
-      b += red[1][i];
+      for (int c = 0; c < 4; ++c) a[c] += red[c][i];
+      mx = fmax(mx, redm[i]);
     }
-    partial[RED_BLOCKS + blockIdx.x] = a;
-    partial[2 * RED_BLOCKS + blockIdx.x] = b;
+    for (int c = 0; c < 4; ++c) partial[(1 + c) * RED_BLOCKS + blockIdx.x] = a[c];
+    partial[5 * RED_BLOCKS + blockIdx.x] = (double)mx;
   }
 }
 
@@ -560,6 +596,121 @@ __global__ void __launch_bounds__(RED_THREADS) k_cost(DevProblem P, const double
 }
 
 // ------------------------------------------------------------------------------------------------------
+// Cost of the candidate step in mixed mode, in double-float arithmetic (a value is an unevaluated sum
+// hi + lo of two floats, ~48-bit significand; Dekker's and Knuth's error-free transformations, with the
+// product error taken by an FMA).  The FP64 pipe of this GPU runs at 1/64 of the FP32 rate; double-float
+// keeps the residuals accurate to ~1e-12 px at pixel offsets of a few hundred px on the FP32 pipe.
+// Per camera the FP64 table of k_cam_rt is split into double-float (R, t, f; k1 and k2 as floats, since
+// they scale the small distortion term only); per point the candidate p + dp is split in k_point_df.
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 df_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+  const float2 s = df_two_sum(x.x, y.x);
+  return df_fast_two_sum(s.x, s.y + (x.y + y.y));
+}
+__device__ __forceinline__ float2 df_sub(float2 x, float2 y) { return df_add(x, make_float2(-y.x, -y.y)); }
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+  const float p = x.x * y.x;
+  const float e = fmaf(x.x, y.y, fmaf(x.y, y.x, fmaf(x.x, y.x, -p)));
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ float2 df_rcp(float2 y) {   // one Newton correction of the FP32 reciprocal
+  const float q = __frcp_rn(y.x);
+  const float2 r = df_sub(make_float2(1.f, 0.f), df_mul(make_float2(q, 0.f), y));
+  return df_fast_two_sum(q, r.x * q);
+}
+__device__ __forceinline__ float2 df_split(double d) {
+  const float hi = __double2float_rn(d);
+  return make_float2(hi, __double2float_rn(d - (double)hi));
+}
+
+constexpr int CAM_DF = 28;   // floats per camera: R (9 x 2), t (3 x 2), f (2), k1, k2
+
+__global__ void k_cam_df(int m, const double* __restrict__ rt, float* __restrict__ cdf) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    const double* c = rt + 15 * (size_t)j;
+    float* o = cdf + CAM_DF * (size_t)j;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+      const float2 v = df_split(c[i]);
+      o[2 * i] = v.x;
+      o[2 * i + 1] = v.y;
+    }
+    o[26] = (float)c[13];
+    o[27] = (float)c[14];
+  }
+}
+
+__global__ void k_point_df(int n, const double* __restrict__ pts, const double* __restrict__ dp,
+                           float* __restrict__ pdf) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += gridDim.x * blockDim.x) {
+    const float2 v = df_split(pts[i] + dp[i]);
+    reinterpret_cast<float2*>(pdf)[i] = v;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_cost_df(DevProblem P, const float* __restrict__ cdf,
+                                                         const float* __restrict__ pdf, double* partial,
+                                                         DevState* st, float* rout) {
+  float2 acc = make_float2(0.f, 0.f);
+  int bad = 0;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < P.q; o += gridDim.x * blockDim.x) {
+    const float4* C4 = reinterpret_cast<const float4*>(cdf + CAM_DF * (size_t)P.obs_cam[o]);
+    float cv[CAM_DF];
+#pragma unroll
+    for (int q4 = 0; q4 < CAM_DF / 4; ++q4) {
+      const float4 t4 = __ldg(C4 + q4);
+      cv[4 * q4] = t4.x;
+      cv[4 * q4 + 1] = t4.y;
+      cv[4 * q4 + 2] = t4.z;
+      cv[4 * q4 + 3] = t4.w;
+    }
+    const float2* X2 = reinterpret_cast<const float2*>(pdf) + 3 * (size_t)P.obs_pt[o];
+    const float2 X[3] = {X2[0], X2[1], X2[2]};
+    float2 Xc[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float2 a = df_mul(make_float2(cv[6 * r], cv[6 * r + 1]), X[0]);
+      const float2 b = df_mul(make_float2(cv[6 * r + 2], cv[6 * r + 3]), X[1]);
+      const float2 c = df_mul(make_float2(cv[6 * r + 4], cv[6 * r + 5]), X[2]);
+      Xc[r] = df_add(df_add(a, b), df_add(c, make_float2(cv[18 + 2 * r], cv[19 + 2 * r])));
+    }
+    if (!(Xc[2].x > 1e-9f)) bad = 1;
+    const float2 iz = df_rcp(Xc[2]);
+    const float2 x = df_mul(Xc[0], iz), y = df_mul(Xc[1], iz);
+    const float r2 = x.x * x.x + y.x * y.x;
+    const float2 d = df_fast_two_sum(1.f, r2 * (cv[26] + cv[27] * r2));
+    const float2 fd = df_mul(make_float2(cv[24], cv[25]), d);
+    const float4 uv = P.obs_uvdf[o];
+    const float2 r0 = df_sub(df_mul(fd, x), make_float2(uv.x, uv.y));
+    const float2 r1 = df_sub(df_mul(fd, y), make_float2(uv.z, uv.w));
+    acc = df_add(acc, df_add(df_mul(r0, r0), df_mul(r1, r1)));
+    rout[2 * (size_t)o] = r0.x + r0.y;
+    rout[2 * (size_t)o + 1] = r1.x + r1.y;
+  }
+  double s = (double)acc.x + (double)acc.y;
+  __shared__ double red[RED_THREADS / 32];
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(FULL_MASK, s, d);
+  bad = __any_sync(FULL_MASK, bad);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[w] = s;
+  if (lane == 0 && bad) st->nonfinite = 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0;
+    for (int i = 0; i < RED_THREADS / 32; ++i) a += red[i];
+    partial[blockIdx.x] = a;
+  }
+}
+
+// ------------------------------------------------------------------------------------------------------
 // Stop tests and accept / reject (Algorithm 1), one block; fixed-order sums of the partials.
 template <typename real>
 __global__ void __launch_bounds__(1024) k_finalize(DevProblem P, const real* vgrad, const double* dc,
@@ -572,14 +723,9 @@ __global__ void __launch_bounds__(1024) k_finalize(DevProblem P, const real* vgr
     if (with_step) {
       dpn += partial[RED_BLOCKS + i];
       pn += partial[2 * RED_BLOCKS + i];
-    }
-  }
-  if (with_step) {
-    for (int i = threadIdx.x; i < 9 * P.m; i += blockDim.x) {
-      double d = dc[i], c = P.cams[i];
-      dcn += d * d;
-      cn += c * c;
-      gmax = fmax(gmax, fabs((double)vgrad[i]));
+      dcn += partial[3 * RED_BLOCKS + i];
+      cn += partial[4 * RED_BLOCKS + i];
+      gmax = fmax(gmax, partial[5 * RED_BLOCKS + i]);
     }
   }
   double vals[4] = {F_new, dpn + dcn, pn + cn, gmax};
@@ -654,7 +800,8 @@ __global__ void k_apply(int m, int n, int q, const double* dc, const double* dp,
 // launchers
 template <typename real>
 void launch_point_update(const DevProblem& P, Scratch<real> W, cudaStream_t stream) {
-  k_point_update<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, W.pt_info, W.t_acc, W.dp, W.partial);
+  k_point_update<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, W.pt_info, W.t_acc, W.dc, W.vgrad, W.dp,
+                                                               W.partial);
 }
 
 template <typename real>
@@ -679,10 +826,16 @@ void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream)
 }
 
 template <typename real>
-void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, double* partial, DevState* st,
-                 real* rout, cudaStream_t stream) {
+void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, float* cam_df, float* pt_df,
+                 double* partial, DevState* st, real* rout, cudaStream_t stream) {
   k_cam_rt<<<(P.m + 127) / 128, 128, 0, stream>>>(P.m, P.cams, dc, rt);
-  k_cost<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, rt, dp, partial, st, rout);
+  if (sizeof(real) == 4 && dp && cam_df && pt_df && P.obs_uvdf) {
+    k_cam_df<<<(P.m + 127) / 128, 128, 0, stream>>>(P.m, rt, cam_df);
+    k_point_df<<<std::min((3 * P.n + 255) / 256, 2048), 256, 0, stream>>>(P.n, P.pts, dp, pt_df);
+    k_cost_df<<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, cam_df, pt_df, partial, st, (float*)rout);
+  } else {
+    k_cost<real><<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, rt, dp, partial, st, rout);
+  }
 }
 
 
@@ -698,8 +851,8 @@ void configure_kernels(int max_np) { configure_solve_kernels(max_np); }
   template void launch_finalize<real>(const DevProblem&, Scratch<real>, DevState*, const Settings&, int,  \
                                       cudaStream_t);                                                      \
   template void launch_point_rhs<real>(const DevProblem&, Scratch<real>, cudaStream_t);                  \
-  template void launch_cost<real>(const DevProblem&, const double*, const double*, double*, double*,      \
-                                  DevState*, real*, cudaStream_t);                                        \
+  template void launch_cost<real>(const DevProblem&, const double*, const double*, double*, float*, float*, \
+                                  double*, DevState*, real*, cudaStream_t);                               \
   template void launch_apply<real>(const DevProblem&, const double*, const double*, double*, double*,     \
                                    const real*, real*, DevState*, cudaStream_t);                          \
 
