@@ -349,7 +349,7 @@ void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, cons
   int64_t v_total = fb.v_total;
   cudaMemsetAsync(W.b, 0, (size_t)v_total * sizeof(double), stream);
   k_adj_cam_rhs<<<P.m, ADJ_THREADS, 0, stream>>>(P, CL, A.u, A.a_c, W.b);
-  launch_solve<real>(P, W.S, W.b, fb, plan, refine_steps, A.zc, stream);
+  launch_solve<real>(P, W.S, W.b, fb, plan, refine_steps, A.zc, nullptr, stream);
   cudaMemsetAsync(A.vpz, 0, 6 * (size_t)P.nv * sizeof(double), stream);
   k_adj_vp<<<(P.q + 255) / 256, 256, 0, stream>>>(P, A.zc, W.dc, A.vpz);
   k_adj_vp_final<real><<<std::min((P.nv + 255) / 256, 4096), 256, 0, stream>>>(P.nv, W.vp_info, A.vpz);

@@ -83,6 +83,7 @@ struct stba_ctx {
        *t_acc = nullptr;
   double *dc = nullptr, *dp = nullptr, *partial = nullptr, *cam_rt = nullptr;
   float *cam_df = nullptr, *pt_df = nullptr;   // double-float tables of the mixed-mode cost
+  float *cams_f = nullptr, *pts_f = nullptr, *dcf = nullptr;   // FP32 copies (mixed precision)
   float4* obs_uvdf = nullptr;
   void *res_cur = nullptr, *res_cand = nullptr;   // residuals at x and at x + dx (working precision)
   DevState* st = nullptr;
@@ -201,6 +202,8 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.obs_uv = c->obs_uv;
   P.obs_uvf = c->obs_uvf;
   P.obs_uvdf = c->obs_uvdf;
+  P.cams_f = c->cams_f;
+  P.pts_f = c->pts_f;
   P.vp_off = c->vp_off;
   P.vp_point = c->vp_point;
   P.pt_vp_off = c->pt_vp_off;
@@ -229,6 +232,7 @@ Scratch<real> scratch(const stba_ctx* c) {
   W.vgrad = (real*)c->vgrad;
   W.t_acc = (real*)c->t_acc;
   W.dc = c->dc;
+  W.dcf = c->dcf;
   W.dp = c->dp;
   W.partial = c->partial;
   return W;
@@ -426,7 +430,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     const int solve_launches = 2 + c->set.refine_steps * (2 + (res_items.empty() ? 0 : 1));
     // iter_begin, vp_reduce, vp_finalize | build | factor | solve, count | rhs, update, cam_rt, (cam_df,
     // point_df,) cost, finalize, apply
-    c->launches_per_iter = 3 + build_launches + factor_launches + solve_launches + 1 + 6 + (c->mixed ? 2 : 0);
+    c->launches_per_iter = 3 + build_launches + factor_launches + solve_launches + 1 + 6 + (c->mixed ? 3 : 0);
     c->factor_flops = 0;
     for (int k = 0; k < l; ++k) c->factor_flops += std::pow((double)c->h_nk[k], 3) / 3.0;
   }
@@ -538,6 +542,7 @@ void enqueue_step(stba_ctx* c, bool stages) {
   mark(0);
   // stage 0: linearisation and virtual points
   launch_iter_begin<real>(c->st, c->set, s);
+  if (c->mixed) launch_params_to_float(P, c->cams_f, c->pts_f, s);
   cudaMemsetAsync(c->vp_acc, 0, 9 * (size_t)c->nv * rs, s);
   cudaMemsetAsync(c->S, 0, (size_t)c->S_total * sizeof(double), s);
   cudaMemsetAsync(c->b, 0, (size_t)c->v_total * sizeof(double), s);
@@ -554,7 +559,7 @@ void enqueue_step(stba_ctx* c, bool stages) {
   launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
   mark(3);
   // stage 3: cluster solves with FP64 refinement
-  launch_solve<real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, s);
+  launch_solve<real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
   launch_count_failures(c->fail_flags, c->l, c->st, s);
   mark(4);
   // stage 4: points, cost, control
@@ -860,6 +865,11 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   if ((s = dalloc(c, &c->cam_rt, 15 * (size_t)m, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->cam_df, 28 * (size_t)m, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->pt_df, 6 * (size_t)n, false)) != STBA_OK) return bail(s);
+  if (c->mixed) {
+    if ((s = dalloc(c, &c->cams_f, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->pts_f, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->dcf, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
+  }
   {
     char *r1, *r2;
     const size_t rsz = 2 * (size_t)q * (c->mixed ? sizeof(float) : sizeof(double));

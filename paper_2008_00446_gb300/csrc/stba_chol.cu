@@ -709,13 +709,14 @@ __global__ void k_copy_vec(const Rreal* src, double* dst, int64_t n) {
     dst[i] = (double)src[i];
 }
 
-__global__ void k_scatter_dc(DevProblem P, const double* x, double* dc) {
+__global__ void k_scatter_dc(DevProblem P, const double* x, double* dc, float* dcf) {
   const int k = blockIdx.x;
   const int nk = P.cluster_n[k], cbase = P.cluster_cam_off[k];
   const double* xk = x + P.v_off[k];
   for (int i = threadIdx.x; i < nk; i += blockDim.x) {
     const int cam = P.cluster_cams[cbase + i / 9];
     dc[9 * (size_t)cam + i % 9] = xk[i];
+    if (dcf) dcf[9 * (size_t)cam + i % 9] = (float)xk[i];
   }
 }
 
@@ -789,7 +790,7 @@ void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb
 
 template <typename F>
 void launch_solve(const DevProblem& P, const double* S, const double* b, const FactorBuffers& fb,
-                  const CholPlan& plan, int refine_steps, double* dc, cudaStream_t stream) {
+                  const CholPlan& plan, int refine_steps, double* dc, float* dcf, cudaStream_t stream) {
   using Sreal = double;
   constexpr int T = FactorCfg<F>::T;
   const F* L = reinterpret_cast<const F*>(fb.L);
@@ -802,7 +803,7 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
       k_residual<Sreal><<<plan.n_res_items, 32 * RES_WARPS, 0, stream>>>(P, S, fb.x, fb.r, plan.res_items);
     launch_tri_solve<F, T, double>(P, L, Dinv, fb.scale, fb.r, fb.x, 1, plan.max_np, fb.v_total, stream);
   }
-  k_scatter_dc<<<P.l, 256, 0, stream>>>(P, fb.x, dc);
+  k_scatter_dc<<<P.l, 256, 0, stream>>>(P, fb.x, dc, dcf);
 }
 
 void configure_solve_kernels(int max_np) {
@@ -825,8 +826,8 @@ template void launch_factor<float>(const DevProblem&, const double*, const Facto
 template void launch_factor<double>(const DevProblem&, const double*, const FactorBuffers&, const CholPlan&,
                                     cudaStream_t);
 template void launch_solve<float>(const DevProblem&, const double*, const double*, const FactorBuffers&,
-                                  const CholPlan&, int, double*, cudaStream_t);
+                                  const CholPlan&, int, double*, float*, cudaStream_t);
 template void launch_solve<double>(const DevProblem&, const double*, const double*, const FactorBuffers&,
-                                   const CholPlan&, int, double*, cudaStream_t);
+                                   const CholPlan&, int, double*, float*, cudaStream_t);
 
 }  // namespace stba

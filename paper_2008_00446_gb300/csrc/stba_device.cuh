@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "stba_camera.cuh"
 #include "stba_internal.cuh"
 
 namespace stba {
@@ -27,6 +28,37 @@ __device__ __forceinline__ void load_point(const double* p, real X[3]) {
   X[0] = (real)p[0];
   X[1] = (real)p[1];
   X[2] = (real)p[2];
+}
+
+// Camera and point in the working precision: FP64 from the parameters, FP32 from the per-iteration copies.
+template <typename real>
+__device__ __forceinline__ Cam<real> load_cam_w(const DevProblem& P, int j) {
+  Cam<real> C;
+  if constexpr (sizeof(real) == 8) {
+    C = load_cam<real>(P.cams + 9 * (size_t)j);
+  } else {
+    const float* c = P.cams_f + 9 * (size_t)j;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      C.w[k] = c[k];
+      C.t[k] = c[3 + k];
+    }
+    C.f = c[6];
+    C.k1 = c[7];
+    C.k2 = c[8];
+  }
+  return C;
+}
+template <typename real>
+__device__ __forceinline__ void load_point_w(const DevProblem& P, int i, real X[3]) {
+  if constexpr (sizeof(real) == 8) {
+    load_point(P.pts + 3 * (size_t)i, X);
+  } else {
+    const float* p = P.pts_f + 3 * (size_t)i;
+    X[0] = p[0];
+    X[1] = p[1];
+    X[2] = p[2];
+  }
 }
 
 // Inclusive warp scan of NV values restricted to runs of equal (non-decreasing) keys.

@@ -19,6 +19,8 @@ struct DevProblem {
   int m, n, q, l, nv;
   const double* cams;      // [m][9] current cameras
   const double* pts;       // [n][3] current points
+  const float* cams_f;     // [m][9], [n][3] FP32 copies made once per iteration (mixed precision), so
+  const float* pts_f;      //   that the per-observation kernels convert nothing on the FP64 pipe
   const int* obs_cam;      // [q] camera of each sorted observation
   const int* obs_vp;       // [q] virtual point of each sorted observation
   const int* obs_pt;       // [q] point of each sorted observation
@@ -79,6 +81,7 @@ template <typename real> struct Scratch {
   real* vgrad;     // [m][9] camera gradient v = -J_c^T f
   real* t_acc;     // [n][3] sum_o J_p^T J_c dc per point
   double* dc;      // [m][9] camera step
+  float* dcf;      // [m][9] FP32 copy of the camera step (mixed precision)
   double* dp;      // [n][3] point step
   double* partial; // reduction partials
 };
@@ -113,6 +116,8 @@ void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairLis
                       cudaStream_t stream);
 template <typename real>
 void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
+// FP32 copies of the cameras and points (mixed precision, once per iteration)
+void launch_params_to_float(const DevProblem& P, float* cams_f, float* pts_f, cudaStream_t stream);
 template <typename real>
 void launch_point_update(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
 // k_cam_rt + k_cost: rt is a [m][15] FP64 scratch (R, t, f, k1, k2 of x + dx); residuals go to rout.  In mixed
@@ -165,9 +170,10 @@ int factor_tile(bool mixed);
 template <typename F>
 void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
                    cudaStream_t stream);
+// x = S'^-1 b per cluster, scattered to dc [m][9] (and to its FP32 copy dcf when not null)
 template <typename F>
 void launch_solve(const DevProblem& P, const double* S, const double* b, const FactorBuffers& fb,
-                  const CholPlan& plan, int refine_steps, double* dc, cudaStream_t stream);
+                  const CholPlan& plan, int refine_steps, double* dc, float* dcf, cudaStream_t stream);
 void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStream_t stream);
 
 // Adjoint of one accepted step (stba_adjoint.cu).  With the forward step at x_t recomputed in W and fb

@@ -56,9 +56,9 @@ __global__ void __launch_bounds__(256) k_vp_reduce(DevProblem P, real* vp_acc) {
     v = P.obs_vp[o];
     const int cam = P.obs_cam[o];
     const int pt = P.vp_point[v];
-    Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)cam);
+    Cam<real> C = load_cam_w<real>(P, cam);
     real X[3];
-    load_point(P.pts + 3 * (size_t)pt, X);
+    load_point_w(P, pt, X);
     real uo, vo;
     load_uv(P, o, uo, vo);
     real r[2], Jc[2][9], Jp[2][3];
@@ -244,11 +244,11 @@ __global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real>
 #pragma unroll
   for (int c = 0; c < 9; ++c) Jc[0][c] = Jc[1][c] = 0;
   if (o >= 0) {
-    const Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)j);
+    const Cam<real> C = load_cam_w<real>(P, j);
     const int v = P.obs_vp[o];
     const bool single = (P.vp_off[v + 1] - P.vp_off[v]) == 1;
     real X[3];
-    load_point(P.pts + 3 * (size_t)P.obs_pt[o], X);
+    load_point_w(P, P.obs_pt[o], X);
     real uo, vo, Jp[2][3];
     load_uv(P, o, uo, vo);
     project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
@@ -372,6 +372,11 @@ constexpr int PAIRS_PER_WARP = 64;
 template <typename real>
 __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, const int4* __restrict__ pairs,
                                                     int npairs, const real* __restrict__ Gbuf) {
+  // Each warp stages the G blocks of CH pairs in shared memory (one G_o per lane, all loads in flight),
+  // then its 27 lanes accumulate the chunk from there.
+  constexpr int CH = 64 / (int)sizeof(real);
+  __shared__ __align__(16) real Gs[8][CH][2][GSTRIDE];
+  const int wib = threadIdx.x >> 5;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   const int p0 = warp * PAIRS_PER_WARP;
   if (p0 >= npairs) return;
@@ -379,43 +384,59 @@ __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> 
   const int r = lane / 3, cg = lane - (lane / 3) * 3;   // lanes 0..26: row r, columns 3cg .. 3cg+2
   const bool act = lane < 27;
   real acc0 = 0, acc1 = 0, acc2 = 0;
-  int4 cur = pairs[p0];
-  for (int p = p0; p < p1; ++p) {
-    const int4 pr = pairs[p];
-    if (pr.z != cur.z || pr.w != cur.w) {
-      if (act) {   // flush the finished run
-        const int k = cur.z, la = cur.w >> 16, lb = cur.w & 0xffff;
-        double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
-        atomicAdd(dst, -(double)acc0);
-        atomicAdd(dst + 1, -(double)acc1);
-        atomicAdd(dst + 2, -(double)acc2);
-      }
-      acc0 = acc1 = acc2 = 0;
-      cur = pr;
-    }
+  int cur_k = pairs[p0].z, cur_w = pairs[p0].w;
+  auto flush = [&]() {
     if (act) {
-      const real* Ga = Gbuf + (size_t)GSTRIDE * pr.x + 4 * r;
-      const real* Gb = Gbuf + (size_t)GSTRIDE * pr.y + 4 * (3 * cg);
-      real a[3], b0[3], b1[3], b2[3];
-      load_gcol(Ga, a);
-      load_gcol(Gb, b0);
-      load_gcol(Gb + 4, b1);
-      load_gcol(Gb + 8, b2);
+      const int la = cur_w >> 16, lb = cur_w & 0xffff;
+      double* dst = W.S + P.S_off[cur_k] + (size_t)(9 * la + r) * P.cluster_np[cur_k] + 9 * lb + 3 * cg;
+      atomicAdd(dst, -(double)acc0);
+      atomicAdd(dst + 1, -(double)acc1);
+      atomicAdd(dst + 2, -(double)acc2);
+    }
+    acc0 = acc1 = acc2 = 0;
+  };
+  for (int c0 = p0; c0 < p1; c0 += CH) {
+    const int cn = min(CH, p1 - c0);
+    const int j = lane % CH, side = lane / CH;
+    int pk = 0, pw = 0;
+    if (side < 2 && j < cn) {
+      const int4 pr = pairs[c0 + j];
+      pk = pr.z;
+      pw = pr.w;
+      const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
+      real* dst = &Gs[wib][j][side][0];
+      if constexpr (sizeof(real) == 4) {
 #pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        acc0 += a[s] * b0[s];
-        acc1 += a[s] * b1[s];
-        acc2 += a[s] * b2[s];
+        for (int q = 0; q < GSTRIDE / 4; ++q)
+          reinterpret_cast<float4*>(dst)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
+      } else {
+#pragma unroll
+        for (int q = 0; q < GSTRIDE / 2; ++q)
+          reinterpret_cast<double2*>(dst)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
       }
     }
+    __syncwarp();
+    for (int jj = 0; jj < cn; ++jj) {
+      const int k = __shfl_sync(FULL_MASK, pk, jj), w = __shfl_sync(FULL_MASK, pw, jj);
+      if (k != cur_k || w != cur_w) {   // the run of equal camera blocks ended
+        flush();
+        cur_k = k;
+        cur_w = w;
+      }
+      if (act) {
+        const real* ga = &Gs[wib][jj][0][4 * r];
+        const real* gb = &Gs[wib][jj][1][4 * (3 * cg)];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+          acc0 += ga[s] * gb[s];
+          acc1 += ga[s] * gb[4 + s];
+          acc2 += ga[s] * gb[8 + s];
+        }
+      }
+    }
+    __syncwarp();
   }
-  if (act) {
-    const int k = cur.z, la = cur.w >> 16, lb = cur.w & 0xffff;
-    double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
-    atomicAdd(dst, -(double)acc0);
-    atomicAdd(dst + 1, -(double)acc1);
-    atomicAdd(dst + 2, -(double)acc2);
-  }
+  flush();
 }
 
 template <typename real>
@@ -430,7 +451,7 @@ void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairLis
 
 // ------------------------------------------------------------------------------------------------------
 template <typename real>
-__global__ void __launch_bounds__(256) k_point_rhs(DevProblem P, const double* dc, real* t_acc) {
+__global__ void __launch_bounds__(256) k_point_rhs(DevProblem P, const double* dc, const float* dcf, real* t_acc) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool act = o < P.q;
@@ -439,18 +460,17 @@ __global__ void __launch_bounds__(256) k_point_rhs(DevProblem P, const double* d
   if (act) {
     pt = P.obs_pt[o];
     const int cam = P.obs_cam[o];
-    Cam<real> C = load_cam<real>(P.cams + 9 * (size_t)cam);
+    Cam<real> C = load_cam_w<real>(P, cam);
     real X[3];
-    load_point(P.pts + 3 * (size_t)pt, X);
+    load_point_w(P, pt, X);
     real uo, vo;
     load_uv(P, o, uo, vo);
     real r[2], Jc[2][9], Jp[2][3];
     project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
-    const double* d = dc + 9 * (size_t)cam;
     real jd0 = 0, jd1 = 0;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      real dcc = (real)d[c];
+      const real dcc = (sizeof(real) == 4) ? (real)dcf[9 * (size_t)cam + c] : (real)dc[9 * (size_t)cam + c];
       jd0 += Jc[0][c] * dcc;
       jd1 += Jc[1][c] * dcc;
     }
@@ -822,7 +842,7 @@ void launch_apply(const DevProblem& P, const double* dc, const double* dp, doubl
 template <typename real>
 void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream) {
   int blocks = (P.q + 255) / 256;
-  k_point_rhs<real><<<blocks, 256, 0, stream>>>(P, W.dc, W.t_acc);
+  k_point_rhs<real><<<blocks, 256, 0, stream>>>(P, W.dc, W.dcf, W.t_acc);
 }
 
 template <typename real>
@@ -838,6 +858,21 @@ void launch_cost(const DevProblem& P, const double* dc, const double* dp, double
   }
 }
 
+
+__global__ void k_params_to_float(int m, int n, const double* __restrict__ cams, const double* __restrict__ pts,
+                                  float* __restrict__ cams_f, float* __restrict__ pts_f) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 9 * m + 3 * n; i += gridDim.x * blockDim.x) {
+    if (i < 9 * m)
+      cams_f[i] = (float)cams[i];
+    else
+      pts_f[i - 9 * m] = (float)pts[i - 9 * m];
+  }
+}
+
+void launch_params_to_float(const DevProblem& P, float* cams_f, float* pts_f, cudaStream_t stream) {
+  const int total = 9 * P.m + 3 * P.n;
+  k_params_to_float<<<std::min((total + 255) / 256, 2048), 256, 0, stream>>>(P.m, P.n, P.cams, P.pts, cams_f, pts_f);
+}
 
 void configure_kernels(int max_np) { configure_solve_kernels(max_np); }
 
