@@ -197,6 +197,22 @@ void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cuda
 // so that the pair pass reads a column with one 16-byte (FP32) load.
 constexpr int GSTRIDE = 36;   // reals per stored G_o
 
+// one stored G column from 16-byte aligned shared memory
+template <typename real>
+__device__ __forceinline__ void load_gcol_s(const real* p, real (&v)[3]) {
+  if constexpr (sizeof(real) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = p[2];
+  }
+}
+
 template <typename real>
 __device__ __forceinline__ void load_gcol(const real* p, real (&v)[3]) {
   if constexpr (sizeof(real) == 4) {
@@ -231,7 +247,7 @@ __device__ __forceinline__ real warp_transpose_sum32(real (&v)[32]) {
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256, 2) k_cam_pass(DevProblem P, Scratch<real> W, CamSlots CS, real* Gbuf,
+__global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real> W, CamSlots CS, real* Gbuf,
                                                   const DevState* st) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= CS.nwarps) return;   // uniform per warp
@@ -398,7 +414,7 @@ __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> 
   for (int c0 = p0; c0 < p1; c0 += CH) {
     const int cn = min(CH, p1 - c0);
     const int j = lane % CH, side = lane / CH;
-    int pk = 0, pw = 0;
+    int pk = -1, pw = -1;
     if (side < 2 && j < cn) {
       const int4 pr = pairs[c0 + j];
       pk = pr.z;
@@ -415,22 +431,28 @@ __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> 
           reinterpret_cast<double2*>(dst)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
       }
     }
+    // run starts inside the chunk: bit jj set when pair c0 + jj differs in camera block from its predecessor
+    const int prev_k = __shfl_up_sync(FULL_MASK, pk, 1), prev_w = __shfl_up_sync(FULL_MASK, pw, 1);
+    const bool starts = (lane < cn) && (lane == 0 ? (pk != cur_k || pw != cur_w) : (pk != prev_k || pw != prev_w));
+    const unsigned run_mask = __ballot_sync(FULL_MASK, starts);
     __syncwarp();
     for (int jj = 0; jj < cn; ++jj) {
-      const int k = __shfl_sync(FULL_MASK, pk, jj), w = __shfl_sync(FULL_MASK, pw, jj);
-      if (k != cur_k || w != cur_w) {   // the run of equal camera blocks ended
+      if ((run_mask >> jj) & 1u) {   // the run of equal camera blocks ended
         flush();
-        cur_k = k;
-        cur_w = w;
+        cur_k = __shfl_sync(FULL_MASK, pk, jj);
+        cur_w = __shfl_sync(FULL_MASK, pw, jj);
       }
       if (act) {
-        const real* ga = &Gs[wib][jj][0][4 * r];
-        const real* gb = &Gs[wib][jj][1][4 * (3 * cg)];
+        real a[3], b0[3], b1[3], b2[3];
+        load_gcol_s(&Gs[wib][jj][0][4 * r], a);
+        load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg)], b0);
+        load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 4], b1);
+        load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 8], b2);
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-          acc0 += ga[s] * gb[s];
-          acc1 += ga[s] * gb[4 + s];
-          acc2 += ga[s] * gb[8 + s];
+          acc0 += a[s] * b0[s];
+          acc1 += a[s] * b1[s];
+          acc2 += a[s] * b2[s];
         }
       }
     }
