@@ -509,6 +509,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   if ((s = ralloc(&c->Gbuf, 36 * (size_t)q)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.L, (size_t)c->S_total)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.Dinv, 2 * (size_t)c->v_total * TF)) != STBA_OK) return s;
+  if ((s = ralloc(&c->fbuf.Ldiag, (size_t)c->v_total * TF)) != STBA_OK) return s;
   if ((s = dalloc(c, &c->fbuf.scale, (size_t)c->v_total, true)) != STBA_OK) return s;
   if ((s = dalloc(c, &c->fbuf.x, (size_t)c->v_total, true)) != STBA_OK) return s;
   if ((s = dalloc(c, &c->fbuf.r, (size_t)c->v_total, true)) != STBA_OK) return s;

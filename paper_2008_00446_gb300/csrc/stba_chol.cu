@@ -172,8 +172,8 @@ struct PanelLayout {
 };
 
 template <typename F, int T>
-__global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const int2* items, int kt, int* fail_flags,
-                                                    int* boosted) {
+__global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P, const int2* items, int kt,
+                                                    int* fail_flags, int* boosted) {
   using PL = PanelLayout<F, T>;
   constexpr int R = T / 16, LDA = PL::LDA, LDV = PL::LDV, NB = T / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -332,11 +332,12 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const in
     }
     __syncthreads();
   }
-  // 3. outputs
+  // 3. outputs.  L_kk goes to its own buffer: later CTAs of this step may still be loading A_kk from L.
   if (diag) {
+    F* Lkk = Ldiag + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
     for (int idx = tid; idx < T * T; idx += 256) {
       const int r = idx / T, c = idx - (idx / T) * T;
-      if (c <= r) A[base_kk + (size_t)r * np + c] = Ad[r][c];
+      Lkk[idx] = (c <= r) ? Ad[r][c] : F(0);
     }
     return;
   }
@@ -351,20 +352,18 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, DevProblem P, const in
 // h = 8, 16, .. T/2 the off-diagonal block of every 2h x 2h diagonal block, Y21 = -Y22 (L21 Y11), as two
 // parallel products.  Writes Y row-major and its transpose at offset v_total * T.
 template <typename F, int T>
-__global__ void __launch_bounds__(256) k_diag_inverse(const F* L, F* Dinv, DevProblem P, const int2* items,
+__global__ void __launch_bounds__(256) k_diag_inverse(const F* Ldiag, F* Dinv, DevProblem P, const int2* items,
                                                       int64_t v_total) {
   __shared__ F D[T][T + 1];
   __shared__ F Y[T][T + 1];
   __shared__ F Z[T * T / 2];
   const int2 it = items[blockIdx.x];
   const int k = it.x, t = it.y;
-  const int np = P.cluster_np[k];
-  const F* A = L + P.S_off[k];
-  const size_t base = (size_t)(t * T) * np + t * T;
+  const F* Lkk = Ldiag + (size_t)P.v_off[k] * T + (size_t)t * T * T;
   const int tid = threadIdx.x;
   for (int idx = tid; idx < T * T; idx += 256) {
     const int r = idx / T, c = idx - (idx / T) * T;
-    D[r][c] = (c <= r) ? A[base + (size_t)r * np + c] : F(0);
+    D[r][c] = (c <= r) ? Lkk[idx] : F(0);
     Y[r][c] = F(0);
   }
   __syncthreads();
@@ -773,8 +772,9 @@ void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb
     if (kt >= 2) cudaStreamWaitEvent(stream, plan.ev_update[kt - 2], 0);
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
     if (npn > 0)
-      launch_prio(k_chol_panel<F, T>, npn, PanelLayout<F, T>::bytes, stream, plan.prio_high, L, P,
-                  plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags, fb.boosted);
+      launch_prio(k_chol_panel<F, T>, npn, PanelLayout<F, T>::bytes, stream, plan.prio_high, L,
+                  reinterpret_cast<F*>(fb.Ldiag), P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags,
+                  fb.boosted);
     cudaEventRecord(plan.ev_panel[kt], stream);
     cudaStreamWaitEvent(side, plan.ev_panel[kt], 0);
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];
@@ -785,7 +785,8 @@ void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb
   cudaEventRecord(plan.ev_join, side);
   cudaStreamWaitEvent(stream, plan.ev_join, 0);
   if (plan.n_diag_items > 0)
-    k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(L, Dinv, P, plan.diag_items, fb.v_total);
+    k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(reinterpret_cast<const F*>(fb.Ldiag), Dinv, P,
+                                                                plan.diag_items, fb.v_total);
 }
 
 template <typename F>

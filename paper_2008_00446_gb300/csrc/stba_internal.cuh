@@ -159,6 +159,8 @@ struct FactorBuffers {
   void* L;          // factor (F = float or double), same layout as S'
   void* Dinv;       // inverses of the diagonal tiles, T x T per tile, v_off[k] * T offset per cluster;
                     // their transposes follow at offset v_total * T
+  void* Ldiag;      // factored diagonal tiles L_kk (same tile layout as Dinv).  Kept out of L: every CTA of a
+                    // panel step reads the unfactored A_kk from L, so it must not be overwritten in place
   double* scale;    // [v_total] Jacobi scaling s_i = S_ii^-1/2
   double* x;        // [v_total] solution
   double* r;        // [v_total] refinement residual

@@ -110,7 +110,11 @@ def zipf_lengths(rng, n, s, lo, hi):
 
 
 def finish_scene(name, rng, cams_true, pts_true, obs_cam, obs_pt, clusters, meta, noise=1.0,
-                 rot_sigma=0.01, trans_sigma=0.05, point_sigma=0.05):
+                 rot_sigma=0.01, trans_sigma=0.05, point_sigma=0.05, rotate_about_center=False):
+    """Sorts the observations, synthesises noisy pixels and perturbs the initial parameters.  The rotation
+    noise is composed on the world side of R (so it turns the scene about the world origin), or, with
+    rotate_about_center, about each camera's own centre (t recomputed from the centre), as a large scene
+    far from the origin needs."""
     order = np.lexsort((obs_cam, obs_pt))
     obs_cam = obs_cam[order].astype(np.int32)
     obs_pt = obs_pt[order].astype(np.int32)
@@ -121,7 +125,12 @@ def finish_scene(name, rng, cams_true, pts_true, obs_cam, obs_pt, clusters, meta
     cams = cams_true.copy()
     if rot_sigma > 0:
         dR = Rotation.from_rotvec(rng.normal(0.0, rot_sigma, (m, 3)))
-        cams[:, 0:3] = (dR * Rotation.from_rotvec(cams_true[:, 0:3])).as_rotvec()
+        R0 = Rotation.from_rotvec(cams_true[:, 0:3])
+        R1 = dR * R0
+        cams[:, 0:3] = R1.as_rotvec()
+        if rotate_about_center:
+            centers = -R0.inv().apply(cams_true[:, 3:6])
+            cams[:, 3:6] = -R1.apply(centers)
     cams[:, 3:6] += rng.normal(0.0, trans_sigma, (m, 3)) if trans_sigma > 0 else 0.0
     pts = pts_true + (rng.normal(0.0, point_sigma, pts_true.shape) if point_sigma > 0 else 0.0)
     meta = dict(meta)
@@ -292,6 +301,11 @@ def trefoil_path(s):
     return np.stack([np.sin(s) + 2.0 * np.sin(2.0 * s), np.cos(s) - 2.0 * np.cos(2.0 * s)], axis=-1)
 
 
+# Forward-moving frames pass close to the points they tracked; a minimum depth of 1 m at the true poses keeps
+# every observed point in front of its camera after the initial perturbation (0.01 rad at up to 30 m).
+SLAM_ZMIN = 1.0
+
+
 def make_slam_scene(m=5000, n=500_000, length=2000.0, lmin=2, lmax=20, reach=30.0, cmin=20, cmax=300,
                     seed=1002, noise=1.0, height=1.5):
     """Forward-facing cameras at equal spacing along a closed 2D trajectory with three self-crossings.
@@ -341,7 +355,7 @@ def make_slam_scene(m=5000, n=500_000, length=2000.0, lmin=2, lmax=20, reach=30.
             cj = np.mod(start + j, m)
             act = j < L
             uv, z = proj(cj, X)
-            vis = act & visible(uv, z)
+            vis = act & visible(uv, z, zmin=SLAM_ZMIN)
             obs_c.append(np.where(vis, cj, -1))
         oc_mat = np.stack(obs_c, axis=1)
         good = (oc_mat >= 0).sum(1) >= 2
@@ -372,7 +386,7 @@ def make_slam_scene(m=5000, n=500_000, length=2000.0, lmin=2, lmax=20, reach=30.
         sizes.pop()
     meta = dict(kind="slam", seed=seed, max_cluster=int(max(sizes)), cluster_sizes=sizes)
     return finish_scene("slam", rng, cams_true, pts_true, obs_cam, obs_pt, cluster_contiguous(sizes), meta,
-                        noise=noise)
+                        noise=noise, rotate_about_center=True)
 
 
 def add_revisit_observations(rng, P2, pts, obs_cam, obs_pt, proj, m, reach, lmax):
@@ -396,7 +410,7 @@ def add_revisit_observations(rng, P2, pts, obs_cam, obs_pt, proj, m, reach, lmax
             continue
         other = np.sort(other)[:lmax]
         uv, z = proj(other, np.repeat(pts[i][None], len(other), 0))
-        vis = other[visible(uv, z)]
+        vis = other[visible(uv, z, zmin=SLAM_ZMIN)]
         if len(vis) >= 2:
             add_c.append(vis)
             add_p.append(np.full(len(vis), i))

@@ -1,0 +1,39 @@
+"""Many camera clusters at once: a tile step of the factorisation then has more panel CTAs than the GPU
+holds at a time, so CTAs of one step run in several waves (the 1000-camera scene fits one wave).  Every
+cluster's step is checked against a dense solve of the cluster system the device built (a property that
+holds at any size): dc_k = S'_k^-1 b'_k.  Tolerances: FP64 1e-8 relative (conditioning ~1e4 after Jacobi
+scaling at lambda = 1e-4); mixed 1e-5 (FP32 factor, one FP64 refinement step: (kappa eps_32)^2 ~ 1e-7)."""
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2008_00446_gb300 import stba  # noqa: E402
+
+
+def scene():
+    return scenes.make_hemisphere_scene(m=4000, n=40_000, radius=40.0, half=10.0, lmax=30, max_cluster=100,
+                                        seed=77, name="many")
+
+
+@pytest.mark.parametrize("precision,tol", [(stba.STBA_FP64, 1e-8), (stba.STBA_MIXED, 1e-5)])
+def test_every_cluster_step_solves_its_system(precision, tol):
+    s = scene()
+    l = int(s.clusters.max()) + 1
+    assert l >= 40
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=precision)
+    info = stba.stba_lm_iteration(ctx)
+    assert info["failed_clusters"] == 0
+    dc, _ = stba.stba_last_step(ctx)
+    assert np.isfinite(dc).all()
+    errs = []
+    for k in range(l):
+        S, b = stba.stba_get_cluster_system(ctx, k)
+        cams = np.nonzero(s.clusters == k)[0]
+        x = np.linalg.solve(S, b)
+        errs.append(np.linalg.norm(dc[cams].ravel() - x) / np.linalg.norm(x))
+    assert max(errs) < tol, max(errs)
+    ctx.close()
