@@ -49,6 +49,13 @@ typedef enum {
 
 typedef enum { STBA_FP64 = 0, STBA_MIXED = 1 } stba_precision;
 
+typedef enum {
+  STBA_SOLVER_CLUSTERS = 0, /* the method: one dense LL^T per cluster system S'_k (Eq. 13) */
+  STBA_SOLVER_PCG_FULL = 1  /* the comparator: plain LM on the full reduced camera system of all cameras
+                               (Eq. 5, clusters ignored), solved by block-Jacobi preconditioned conjugate
+                               gradients, matrix-free; not captured in a graph (the host checks the residual) */
+} stba_linear_solver;
+
 typedef struct {
   int32_t precision;        /* STBA_FP64: everything in FP64.  STBA_MIXED: residuals, Jacobians and the
                                Schur accumulation in FP32; factorisation, refinement and cost sums FP64 */
@@ -60,6 +67,9 @@ typedef struct {
   double ftol, gtol, xtol;  /* stop tolerances (Sec. 5.1: 1e-6); <= 0 disables a test */
   int32_t refine_steps;     /* FP64 iterative-refinement steps per cluster solve (default 1) */
   int32_t use_graph;        /* 1: replay each LM iteration as one captured CUDA graph */
+  int32_t linear_solver;    /* stba_linear_solver (default STBA_SOLVER_CLUSTERS) */
+  int32_t pcg_max_iter;     /* conjugate-gradient iteration limit per LM step (default 500) */
+  double pcg_tol;           /* CG stops at ||S dc - b|| <= pcg_tol ||b|| (default 1e-6) */
 } stba_options;
 
 typedef struct {
@@ -76,12 +86,12 @@ typedef struct {
   int32_t failed_clusters; /* clusters whose Cholesky factorisation met a pivot <= 0 or non-finite */
   int32_t boosted_pivots;  /* mixed precision: FP32 pivots lost to rounding and raised before FP64
                               refinement (static pivoting); 0 in FP64 mode */
-  int32_t reserved;
+  int32_t linear_iterations; /* conjugate-gradient iterations of the step (STBA_SOLVER_PCG_FULL), else 0 */
   int64_t iteration;    /* 1-based count of iterations run on this context */
 } stba_iter_info;
 
 /* Fills *opt with the defaults above (FP64, correction on, lambda0 1e-4, tolerances off,
- * refine_steps 1, use_graph 1). */
+ * refine_steps 1, use_graph 1, cluster solver, pcg_max_iter 500, pcg_tol 1e-6). */
 void stba_default_options(stba_options* opt);
 
 /* Creates a problem (Sec. 3, Algorithm 1 inputs).
@@ -144,7 +154,7 @@ stba_status stba_record(stba_ctx* ctx, int32_t max_iter);
  * the forward pass; its adjoint solves with that step's cluster factors (z_c = S'^-1 a^_c, the implicit
  * derivative of Eq. 10/13), back-substitutes through the virtual points and Eq. 15, and adds the
  * second-derivative products of the reprojection error.
- * Errors: STBA_ERR_STATE if nothing was recorded, if stba_set_params replaced the parameters during the
+ * Errors: STBA_ERR_STATE with the PCG solver, if nothing was recorded, if stba_set_params replaced the parameters during the
  * recording, or if an accepted step used the steepest-descent correction (lambda >= correction_lambda,
  * Sec. 4.3), which this adjoint does not cover.  On return the parameters, the cluster assignment and the
  * LM state are those before the call.  The call synchronises the stream and allocates, then frees, about
@@ -160,7 +170,8 @@ stba_status stba_problem_info(stba_ctx* ctx, int64_t* out, int32_t n);
 
 /* The cluster system S'_k Delta c_k = b_k (Eq. 13) of the last iteration, in the order of the cluster's
  * cameras by increasing camera index: S [dim][dim] (FP64, both triangles filled from the lower one) and
- * b [dim]; dim = 9 n_k is written to *dim.  S or b may be NULL (then only dim is returned). */
+ * b [dim]; dim = 9 n_k is written to *dim.  S or b may be NULL (then only dim is returned).
+ * STBA_ERR_STATE with the PCG solver (no cluster systems are formed). */
 stba_status stba_get_cluster_system(stba_ctx* ctx, int32_t k, double* S, double* b, int64_t* dim);
 
 /* Stage timing: every iteration records CUDA events around its stages on the context stream (inside

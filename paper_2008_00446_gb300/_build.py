@@ -10,7 +10,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libstba.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["stba_api.cu", "stba_kernels.cu", "stba_chol.cu", "stba_noalloc.cu", "stba_adjoint.cu"]
+SOURCES = ["stba_api.cu", "stba_kernels.cu", "stba_chol.cu", "stba_noalloc.cu", "stba_adjoint.cu", "stba_pcg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -76,6 +76,8 @@ struct stba_ctx {
   int64_t n_pairs = 0;
   CholPlan cplan{};
   FactorBuffers fbuf{};
+  bool use_pcg = false;                 // STBA_SOLVER_PCG_FULL: no cluster systems, CG on the full system
+  PcgBuffers pcg{};
   int* fail_flags = nullptr;
 
   // scratch (real = float in mixed mode, double in FP64 mode)
@@ -375,14 +377,14 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   // camera-pair instances of the pair pass, sorted by (cluster, la, lb): inside a virtual point the
   // observations are ordered by camera, so a later observation has the larger local camera index
   int64_t npairs = 0;
-  for (int v = 0; v < nv; ++v) {
+  for (int v = 0; v < nv && !c->use_pcg; ++v) {   // the PCG solver forms no cluster system
     const int64_t len = vp_off[v + 1] - vp_off[v];
     npairs += len * (len - 1) / 2;
   }
   if (npairs > INT32_MAX) return fail(c, STBA_ERR_INVALID_ARG, "more than 2^31 camera-pair instances");
   std::vector<int4> pairs;
   pairs.reserve(npairs);
-  for (int v = 0; v < nv; ++v)
+  for (int v = 0; v < nv && !c->use_pcg; ++v)
     for (int a2 = vp_off[v] + 1; a2 < vp_off[v + 1]; ++a2)
       for (int b2 = vp_off[v]; b2 < a2; ++b2)
         pairs.push_back(make_int4(a2, b2, cl[s_cam[a2]], (cam_local[s_cam[a2]] << 16) | cam_local[s_cam[b2]]));
@@ -392,7 +394,13 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   c->n_pairs = npairs;
   c->build_items = (int)((npairs + 63) / 64);
 
-  // Cholesky step plan
+  // Cholesky step plan (none for the PCG solver)
+  if (c->use_pcg) {
+    max_nt = 0;
+    c->max_np = 0;
+    c->S_total = 0;
+    c->v_total = 0;
+  }
   std::vector<int2> panel, update;
   c->h_panel_off.assign(max_nt + 1, 0);
   c->h_update_off.assign(max_nt + 1, 0);
@@ -410,9 +418,9 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   c->h_panel_off[max_nt] = (int)panel.size();
   c->h_update_off[max_nt] = (int)update.size();
   std::vector<int2> res_items, diag_items;
-  for (int k = 0; k < l; ++k)
+  for (int k = 0; k < l && !c->use_pcg; ++k)
     for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
-  for (int k = 0; k < l; ++k)
+  for (int k = 0; k < l && !c->use_pcg; ++k)
     for (int t = 0; t < c->h_np[k] / TF; ++t) diag_items.push_back(make_int2(k, t));
   while ((int)c->ev_panel.size() < max_nt) {
     cudaEvent_t e1, e2;
@@ -506,7 +514,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   }
   if ((s = ralloc(&c->vgrad, 9 * (size_t)m)) != STBA_OK) return s;
   if ((s = ralloc(&c->t_acc, 3 * (size_t)n)) != STBA_OK) return s;
-  if ((s = ralloc(&c->Gbuf, 36 * (size_t)q)) != STBA_OK) return s;
+  if ((s = ralloc(&c->Gbuf, c->use_pcg ? 1 : 36 * (size_t)q)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.L, (size_t)c->S_total)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.Dinv, 2 * (size_t)c->v_total * TF)) != STBA_OK) return s;
   if ((s = ralloc(&c->fbuf.Ldiag, (size_t)c->v_total * TF)) != STBA_OK) return s;
@@ -517,7 +525,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   c->fbuf.fail_flags = c->fail_flags;
   c->fbuf.boosted = &c->st->boosted;
   c->fbuf.v_total = c->v_total;
-  configure_kernels(c->max_np);
+  if (!c->use_pcg) configure_kernels(c->max_np);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   return STBA_OK;
@@ -580,6 +588,35 @@ void enqueue_iteration(stba_ctx* c) {
   record_stage(c, 5);
 }
 
+// One LM iteration of the full-RCS comparator: the physical point blocks, then S dc = b over all cameras by
+// PCG (host-controlled loop), then the same point update, cost and accept / reject as the method.
+template <typename real>
+int enqueue_pcg_iteration(stba_ctx* c) {
+  const DevProblem P = dev_problem(c);
+  const Scratch<real> W = scratch<real>(c);
+  cudaStream_t s = c->stream;
+  record_stage(c, 0);
+  launch_iter_begin<real>(c->st, c->set, s);
+  if (c->mixed) launch_params_to_float(P, c->cams_f, c->pts_f, s);
+  cudaMemsetAsync(c->vp_acc, 0, 9 * (size_t)c->nv * sizeof(real), s);
+  cudaMemsetAsync(c->t_acc, 0, 3 * (size_t)c->n * sizeof(real), s);
+  launch_vp_reduce<real>(P, W, s);
+  launch_vp_finalize<real>(P, W, c->st, s);
+  record_stage(c, 1);
+  pcg_prepare<real>(P, W, c->cslots, c->pcg, c->st, s);
+  record_stage(c, 2);
+  record_stage(c, 3);
+  const int iters = pcg_iterate<real>(P, W, c->cslots, c->pcg, c->opt.pcg_max_iter, c->opt.pcg_tol, c->st, s);
+  record_stage(c, 4);
+  launch_point_rhs<real>(P, W, s);
+  launch_point_update<real>(P, W, s);
+  launch_cost<real>(P, c->dc, c->dp, c->cam_rt, c->cam_df, c->pt_df, c->partial, c->st, (real*)c->res_cand, s);
+  launch_finalize<real>(P, W, c->st, c->set, 1, s);
+  launch_apply<real>(P, c->dc, c->dp, c->cams, c->pts, (const real*)c->res_cand, (real*)c->res_cur, c->st, s);
+  record_stage(c, 5);
+  return iters;
+}
+
 template <typename real>
 void enqueue_cost(stba_ctx* c) {
   const DevProblem P = dev_problem(c);
@@ -607,6 +644,14 @@ stba_status run_cost(stba_ctx* c, double* F) {
 }
 
 stba_status launch_iteration(stba_ctx* c) {
+  if (c->use_pcg) {
+    const int32_t iters = c->mixed ? enqueue_pcg_iteration<float>(c) : enqueue_pcg_iteration<double>(c);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&c->st->info.linear_iterations, &iters, sizeof iters, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_stage_times = true;
+    return STBA_OK;
+  }
   if (!c->opt.use_graph) {
     if (c->mixed)
       enqueue_iteration<float>(c);
@@ -717,6 +762,9 @@ void stba_default_options(stba_options* o) {
   o->ftol = o->gtol = o->xtol = -1.0;
   o->refine_steps = 1;
   o->use_graph = 1;
+  o->linear_solver = STBA_SOLVER_CLUSTERS;
+  o->pcg_max_iter = 500;
+  o->pcg_tol = 1e-6;
 }
 
 const char* stba_status_string(stba_status s) {
@@ -776,12 +824,15 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
                      (long long)n, (long long)q));
   if (!(c->opt.lambda0 > 0) || !std::isfinite(c->opt.lambda0) || c->opt.lambda_min < 0 ||
       (c->opt.precision != STBA_FP64 && c->opt.precision != STBA_MIXED) || c->opt.refine_steps < 0 ||
-      c->opt.refine_steps > 8)
+      c->opt.refine_steps > 8 ||
+      (c->opt.linear_solver != STBA_SOLVER_CLUSTERS && c->opt.linear_solver != STBA_SOLVER_PCG_FULL) ||
+      (c->opt.linear_solver == STBA_SOLVER_PCG_FULL && (c->opt.pcg_max_iter < 1 || !(c->opt.pcg_tol > 0))))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
   c->m = m;
   c->n = n;
   c->q = q;
   c->mixed = c->opt.precision == STBA_MIXED;
+  c->use_pcg = c->opt.linear_solver == STBA_SOLVER_PCG_FULL;
   c->set.correction = c->opt.correction;
   c->set.correction_lambda = c->opt.correction_lambda;
   c->set.lambda_min = c->opt.lambda_min;
@@ -880,6 +931,28 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     c->res_cand = r2;
   }
   if ((s = dalloc(c, &c->st, 1, false)) != STBA_OK) return bail(s);
+  if (c->use_pcg) {
+    const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
+    char *J, *pw, *tpt, *upt;
+    PcgBuffers& B = c->pcg;
+    if ((s = dalloc(c, &J, 24 * (size_t)q * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &pw, 9 * (size_t)m * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &tpt, 3 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &upt, 3 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
+    B.J = J;
+    B.pw = pw;
+    B.tpt = tpt;
+    B.upt = upt;
+    double** vecs[] = {&B.x, &B.r, &B.z, &B.p, &B.q};
+    for (double** v : vecs)
+      if ((s = dalloc(c, v, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.Mblk, 45 * (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.Bdiag, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.Minv, 81 * (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.scal, 8, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.partial, 3 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.partial2, 3 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
+  }
   {
     cudaError_t e1 = cudaMemcpyAsync(c->cams, h_cams.data(), h_cams.size() * 8, cudaMemcpyHostToDevice, c->stream);
     cudaError_t e2 = cudaMemcpyAsync(c->pts, h_pts.data(), h_pts.size() * 8, cudaMemcpyHostToDevice, c->stream);
@@ -1015,6 +1088,7 @@ stba_status stba_record(stba_ctx* c, int32_t max_iter) {
 stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_dpts, double* dL_dobs,
                          double* dL_dcams0, double* dL_dpts0) {
   if (!c || !dL_dcams) return STBA_ERR_INVALID_ARG;
+  if (c->use_pcg) return fail(c, STBA_ERR_STATE, "the adjoint covers the cluster solver only");
   if (c->tape_len == 0) return fail(c, STBA_ERR_STATE, "no recorded iteration (call stba_record before iterating)");
   if (c->tape_broken)
     return fail(c, STBA_ERR_STATE, "the parameters were replaced between recorded iterations; record again");
@@ -1117,6 +1191,7 @@ stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {
 
 stba_status stba_get_cluster_system(stba_ctx* c, int32_t k, double* S, double* b, int64_t* dim) {
   if (!c || k < 0 || k >= c->l) return STBA_ERR_INVALID_ARG;
+  if (c->use_pcg) return fail(c, STBA_ERR_STATE, "the PCG solver forms no cluster systems");
   const int nk = c->h_nk[k], np = c->h_np[k];
   if (dim) *dim = nk;
   if (!S && !b) return STBA_OK;

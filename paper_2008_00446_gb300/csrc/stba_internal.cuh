@@ -197,4 +197,28 @@ void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, cons
                          const AdjointBuffers& A, cudaStream_t stream);
 void launch_set_lambda(DevState* st, double lam, cudaStream_t stream);
 
+// Full-RCS comparator (stba_pcg.cu): block-Jacobi preconditioned CG on S dc = b over all cameras, matrix-free.
+struct PcgBuffers {
+  void* J;          // [q][24] J_c and J_p of every observation (working precision)
+  double* Mblk;     // [m][45] diagonal blocks of S (lower, undamped B part)
+  double* Bdiag;    // [m][9] diag(J_c^T J_c)
+  double* Minv;     // [m][81] inverse damped diagonal blocks (the preconditioner)
+  double *x, *r, *z, *p, *q;   // [m][9] CG vectors (q also carries the right-hand side at the start)
+  void* pw;         // [m][9] p in the working precision
+  void* tpt;        // [n][3] E^T p
+  void* upt;        // [n][3] C^-1 E^T p
+  double* scal;     // b.b, r.z (two parity slots), r.r
+  double* partial;  // [3][RED_BLOCKS]
+  double* partial2; // [3][RED_BLOCKS]
+};
+// Jacobians, preconditioner and right-hand side; x = 0, r = b, p = M^-1 b.
+template <typename real>
+void pcg_prepare(const DevProblem& P, Scratch<real> W, CamSlots CS, const PcgBuffers& B, DevState* st,
+                 cudaStream_t stream);
+// Iterates until ||r|| <= tol ||b|| or max_iter (the host reads the residual every few iterations), then
+// writes dc (and its FP32 copy).  Returns the number of iterations.
+template <typename real>
+int pcg_iterate(const DevProblem& P, Scratch<real> W, CamSlots CS, const PcgBuffers& B, int max_iter, double tol,
+                DevState* st, cudaStream_t stream);
+
 }  // namespace stba

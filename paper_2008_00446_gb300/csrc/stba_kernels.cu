@@ -820,6 +820,7 @@ __global__ void __launch_bounds__(1024) k_finalize(DevProblem P, const real* vgr
     I.corrected = st->corrected;
     I.failed_clusters = st->failed;
     I.boosted_pivots = st->boosted;
+    I.linear_iterations = 0;
     I.iteration = st->iteration;
   }
 }

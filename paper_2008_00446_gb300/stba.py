@@ -16,6 +16,7 @@ from . import _build
 _LIB = None
 
 STBA_FP64, STBA_MIXED = 0, 1
+STBA_SOLVER_CLUSTERS, STBA_SOLVER_PCG_FULL = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not SPD",
           5: "non-finite value", 6: "timeout", 7: "invalid state"}
 
@@ -31,7 +32,8 @@ class StbaOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("correction", ctypes.c_int32), ("lambda0", ctypes.c_double),
                 ("lambda_min", ctypes.c_double), ("correction_lambda", ctypes.c_double),
                 ("ftol", ctypes.c_double), ("gtol", ctypes.c_double), ("xtol", ctypes.c_double),
-                ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double)]
 
 
 class StbaIterInfo(ctypes.Structure):
@@ -39,12 +41,12 @@ class StbaIterInfo(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("grad_inf", ctypes.c_double), ("dx_norm", ctypes.c_double),
                 ("x_norm", ctypes.c_double), ("accepted", ctypes.c_int32), ("stop", ctypes.c_int32),
                 ("corrected", ctypes.c_int32), ("failed_clusters", ctypes.c_int32),
-                ("boosted_pivots", ctypes.c_int32), ("reserved", ctypes.c_int32), ("iteration", ctypes.c_int64)]
+                ("boosted_pivots", ctypes.c_int32), ("linear_iterations", ctypes.c_int32),
+                ("iteration", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_}
         d["lambda"] = d.pop("lambda_")
-        d.pop("reserved")
         for k in ("accepted", "stop", "corrected"):
             d[k] = bool(d[k])
         return d

@@ -221,12 +221,16 @@ def make_ring_scene(m=30, n=2000, radius=10.0, half=2.0, max_angle_deg=60.0, clu
 
 
 def make_hemisphere_scene(m=1000, n=200_000, radius=20.0, half=5.0, zipf_s=2.0, lmin=2, lmax=50,
-                          max_cluster=100, seed=1001, noise=1.0, name="hemisphere"):
+                          max_cluster=100, seed=1001, noise=1.0, name="hemisphere", tracks="local"):
     """Cameras uniform on the upper hemisphere looking at the origin; points uniform in a cube; Zipf tracks.
 
-    Each point draws a track length L ~ Zipf(s) on [lmin, lmax] and takes the first L distinct cameras that
-    see it (in front, inside the image) from a uniformly random candidate sequence, i.e. L cameras chosen
-    uniformly among those that see it.  A point with fewer than two such cameras is redrawn."""
+    Each point draws a track length L ~ Zipf(s) on [lmin, lmax].  tracks="local" (Internet photo collections:
+    a point is matched across nearby viewpoints): an anchor camera is drawn uniformly and the track takes the
+    first L cameras that see the point (in front, inside the image) in order of distance from the anchor.
+    tracks="uniform": the first L cameras that see it from a uniformly random candidate sequence.  A point
+    with fewer than two such cameras is redrawn."""
+    if tracks == "local":
+        return _hemisphere_local(m, n, radius, half, zipf_s, lmin, lmax, max_cluster, seed, noise, name)
     rng = np.random.default_rng(seed)
     cz = rng.uniform(0.0, 1.0, m)
     phi = rng.uniform(0.0, 2 * np.pi, m)
@@ -293,6 +297,59 @@ def make_hemisphere_scene(m=1000, n=200_000, radius=20.0, half=5.0, zipf_s=2.0, 
     obs_cam = np.concatenate(oc_list)
     clusters = cluster_by_azimuth(C, max_cluster)
     meta = dict(kind="hemisphere", seed=seed, max_cluster=max_cluster, zipf=(zipf_s, lmin, lmax))
+    return finish_scene(name, rng, cams_true, pts_true, obs_cam, obs_pt, clusters, meta, noise=noise)
+
+
+def _hemisphere_cameras(rng, m, radius):
+    cz = rng.uniform(0.0, 1.0, m)
+    phi = rng.uniform(0.0, 2 * np.pi, m)
+    sz = np.sqrt(1.0 - cz * cz)
+    C = radius * np.stack([sz * np.cos(phi), sz * np.sin(phi), cz], axis=1)
+    f, k1, k2 = draw_intrinsics(rng, m)
+    return C, assemble_cameras(look_at(C), C, f, k1, k2)
+
+
+def _hemisphere_local(m, n, radius, half, zipf_s, lmin, lmax, max_cluster, seed, noise, name):
+    rng = np.random.default_rng(seed)
+    C, cams_true = _hemisphere_cameras(rng, m, radius)
+    Rm = Rotation.from_rotvec(cams_true[:, 0:3]).as_matrix()
+    tv = cams_true[:, 3:6]
+    f, k1, k2 = cams_true[:, 6], cams_true[:, 7], cams_true[:, 8]
+    K = int(min(m, 4 * lmax))
+    # K nearest cameras of every camera (itself first), by centre distance, in blocks
+    nn = np.empty((m, K), dtype=np.int64)
+    for s0 in range(0, m, 2048):
+        d2 = np.sum((C[s0:s0 + 2048, None, :] - C[None, :, :]) ** 2, -1)
+        part = np.argpartition(d2, K - 1, axis=1)[:, :K]
+        order = np.argsort(np.take_along_axis(d2, part, 1), axis=1, kind="stable")
+        nn[s0:s0 + 2048] = np.take_along_axis(part, order, 1)
+    pts_list, oc_list, op_list = [], [], []
+    count = 0
+    while count < n:
+        need = min(n - count, 50_000)
+        P = rng.uniform(-half, half, (need, 3))
+        L = zipf_lengths(rng, need, zipf_s, lmin, lmax)
+        cand = nn[rng.integers(0, m, need)]                       # (need, K), nearest first
+        Xc = np.einsum("pkij,pj->pki", Rm[cand], P) + tv[cand]
+        z = Xc[..., 2]
+        xy = Xc[..., :2] / np.where(z > 1e-9, z, 1e-9)[..., None]
+        r2 = np.sum(xy * xy, -1)
+        d = 1.0 + k1[cand] * r2 + k2[cand] * r2 * r2
+        uv = f[cand][..., None] * d[..., None] * xy
+        ok = (z > 0.1) & (np.abs(uv[..., 0]) < HALF_W) & (np.abs(uv[..., 1]) < HALF_H)
+        take = ok & (np.cumsum(ok, axis=1) <= L[:, None])
+        good = take.sum(1) >= 2
+        sel = np.nonzero(good)[0][: n - count]
+        rows, cols = np.nonzero(take[sel])
+        pts_list.append(P[sel])
+        op_list.append(count + rows)
+        oc_list.append(cand[sel][rows, cols])
+        count += len(sel)
+    pts_true = np.concatenate(pts_list)
+    obs_pt = np.concatenate(op_list)
+    obs_cam = np.concatenate(oc_list)
+    clusters = cluster_by_azimuth(C, max_cluster)
+    meta = dict(kind="hemisphere", seed=seed, max_cluster=max_cluster, zipf=(zipf_s, lmin, lmax), tracks="local")
     return finish_scene(name, rng, cams_true, pts_true, obs_cam, obs_pt, clusters, meta, noise=noise)
 
 
