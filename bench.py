@@ -25,8 +25,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "STBA LM iter/s and obs/s vs full-RCS LM on 1 GB300 at equal final RMSE"
 CONFIG = "c1_internet"
-WORKLOAD = ("c1_internet: 1000 cameras (hemisphere r=20), 200k points (10^3 box), Zipf(2) tracks on [2,50], "
-            "10 clusters of 100 cameras, mixed precision")
+WORKLOADS = {
+    "c1_internet": ("c1_internet: 1000 cameras (hemisphere r=20), 200k points (10^3 box), Zipf(2) tracks on [2,50] "
+                    "over nearby viewpoints, 10 clusters of 100 cameras, mixed precision"),
+    "c4_large": ("c4_large: 20000 cameras (hemisphere r=60), 4M points (30^3 box), Zipf(2) tracks on [2,80] over "
+                 "nearby viewpoints, 200 clusters of 100 cameras, mixed precision"),
+    "c2_slam": ("c2_slam: 5000 cameras along a 2 km closed trajectory with 3 crossings, 500k points, tracks of "
+                "2-20 consecutive frames, 27 clusters of 45-297 cameras, mixed precision"),
+}
+WORKLOAD = WORKLOADS[CONFIG]
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
 
 
@@ -182,13 +189,13 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=CONFIG)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the full-RCS LM comparison")
-    ap.add_argument("--compare-iters", type=int, default=20)
+    ap.add_argument("--compare-iters", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on the 500-camera scene")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -290,7 +297,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cameras": m, "points": n, "observations": q, "clusters": int(info0["l"]),
+        "config": {"workload": WORKLOADS.get(args.config, args.config), "cameras": m, "points": n, "observations": q,
+                   "clusters": int(info0["l"]),
                    "virtual_points": int(info0["nv"]), "l2_flush": True, "parallelism": f"replicas{world}"},
         "obs_per_s": value * q,
         "roofline": roofline,
@@ -304,7 +312,7 @@ def main():
         out["full_rcs"] = compare_full_rcs(s, stba, stream, args.compare_iters, torch)
     if rank == 0 and world == 1 and not args.no_adjoint:
         out["adjoint"] = time_adjoint(stba, stream, torch)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == CONFIG:
         t = run_oracle(args.config, 1)
         v = 1.0 / t["seconds"]
         out["cpu_baseline"] = {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
@@ -316,22 +324,20 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def compare_full_rcs(s, stba, stream, iters, torch):
-    """Full-RCS LM on the same GPU (all cameras in one cluster: STBA with l = 1 is exactly LM) against
-    STBA with a fresh azimuth-wedge clustering each iteration, both from the same start: per-iteration
-    time, final RMSE, and the time STBA needs to reach 1.001 x the full-RCS final RMSE."""
+def compare_full_rcs(s, stba, stream, iters, torch, max_stba_iters=100):
+    """Full-RCS LM on the same GPU against STBA, from the same start.  Full RCS runs `iters` iterations as
+    (a) one cluster holding every camera (the dense reduced camera system, when it fits: 9 m <= 27000) and
+    (b) block-Jacobi preconditioned CG on the full Schur system (matrix-free).  STBA takes a fresh
+    azimuth-wedge clustering every iteration and runs until its RMSE reaches 1.001 x the better full-RCS
+    final RMSE (or max_stba_iters).  Per-iteration device time, final RMSE and time to the target."""
     import numpy as np
 
     import scenes
-    res = {}
-    one = np.zeros(s.m, np.int32)
-    target = None
-    for name, clusters in (("full_rcs_lm", None), ("stba_resampled", "seq")):
-        n_it = iters if clusters is None else 5 * iters
-        ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv,
-                               one if clusters is None else s.clusters, precision=stba.STBA_MIXED, stream=stream)
-        seq = scenes.cluster_sequence(s, n_it, seed=s.meta["seed"] + 1) if clusters == "seq" else None
-        rm, ts = [], []
+
+    def run(clusters, seq, n_it, target=None, **kw):
+        ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, clusters,
+                               precision=stba.STBA_MIXED, stream=stream, **kw)
+        rm, ts, cg = [], [], []
         for t in range(n_it):
             if seq is not None:
                 stba.stba_set_clusters(ctx, seq[t])
@@ -339,27 +345,38 @@ def compare_full_rcs(s, stba, stream, iters, torch):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            info = stba.stba_lm_iteration(ctx, want_info=False)
+            info = stba.stba_lm_iteration(ctx)
             b.record(stream)
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
+            cg.append(info["linear_iterations"])
             _, F, _ = stba.stba_get_state(ctx)
             rm.append(float(np.sqrt(F / (2 * s.q))))
             if target is not None and rm[-1] <= target:
                 break
-        res[name] = {"ms_per_iter": float(np.median(ts)), "rmse": rm, "cum_ms": list(np.cumsum(ts))}
         stba.stba_destroy(ctx)
-        if clusters is None:
-            target = 1.001 * rm[-1]
-    st = res["stba_resampled"]
+        return {"ms_per_iter": float(np.median(ts)), "rmse": rm, "cum_ms": [float(x) for x in np.cumsum(ts)],
+                "cg_iters": cg}
+
+    res = {}
+    one = np.zeros(s.m, np.int32)
+    if 9 * s.m <= 27000:
+        res["full_rcs_dense"] = run(one, None, iters)
+    res["full_rcs_pcg"] = run(one, None, iters, linear_solver=stba.STBA_SOLVER_PCG_FULL)
+    best = min(r["rmse"][-1] for r in res.values())
+    target = 1.001 * best
+    seq = scenes.cluster_sequence(s, max_stba_iters, seed=s.meta["seed"] + 1)
+    st = run(s.clusters, seq, max_stba_iters, target=target)
+    out = {"rmse_target": target, "stba_iters_run": len(st["rmse"]), "stba_ms_per_iter": st["ms_per_iter"],
+           "stba_final_rmse": st["rmse"][-1]}
     hit = [i for i, r in enumerate(st["rmse"]) if r <= target]
-    out = {"full_rcs_iters": iters, "stba_iters_run": len(st["rmse"]),
-           "full_rcs_ms_per_iter": res["full_rcs_lm"]["ms_per_iter"],
-           "stba_ms_per_iter": st["ms_per_iter"], "full_rcs_final_rmse": res["full_rcs_lm"]["rmse"][-1],
-           "stba_final_rmse": st["rmse"][-1], "rmse_target": target,
-           "full_rcs_time_ms": res["full_rcs_lm"]["cum_ms"][-1],
-           "stba_time_to_target_ms": (st["cum_ms"][hit[0]] if hit else None),
-           "stba_iters_to_target": (hit[0] + 1 if hit else None)}
+    out["stba_time_to_target_ms"] = st["cum_ms"][hit[0]] if hit else None
+    out["stba_iters_to_target"] = hit[0] + 1 if hit else None
+    for name, r in res.items():
+        h = [i for i, x in enumerate(r["rmse"]) if x <= target]
+        out[name] = {"iters": len(r["rmse"]), "ms_per_iter": r["ms_per_iter"], "final_rmse": r["rmse"][-1],
+                     "time_ms": r["cum_ms"][-1], "time_to_target_ms": r["cum_ms"][h[0]] if h else None,
+                     "cg_iters": r["cg_iters"] if name.endswith("pcg") else None}
     return out
 
 
