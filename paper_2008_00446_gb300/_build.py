@@ -10,7 +10,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libstba.so")
 BUILD = os.path.join(PKG, "_build")
-SOURCES = ["stba_api.cu", "stba_kernels.cu", "stba_chol.cu", "stba_noalloc.cu", "stba_adjoint.cu", "stba_pcg.cu"]
+SOURCES = ["stba_api.cu", "stba_kernels.cu", "stba_chol.cu", "stba_noalloc.cu", "stba_adjoint.cu", "stba_pcg.cu",
+           "stba_graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -63,7 +64,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + ".tmp"
     libdir = cuda_lib_dir()
-    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-lpthread",
         "-L", libdir, "-Xlinker", f"-rpath,{libdir}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -64,14 +64,15 @@ struct stba_ctx {
   // device arrays
   double *cams = nullptr, *pts = nullptr, *obs_uv = nullptr;
   float* obs_uvf = nullptr;
-  int *obs_cam = nullptr, *obs_vp = nullptr, *obs_pt = nullptr, *obs_perm = nullptr;
+  int *obs_cam = nullptr, *obs_vp = nullptr, *obs_pt = nullptr, *obs_perm = nullptr, *obs_base = nullptr;
   int *vp_off = nullptr, *vp_point = nullptr, *pt_vp_off = nullptr, *pt_off = nullptr;
   int *cam_local = nullptr, *cam_cluster = nullptr, *cluster_cams = nullptr, *cluster_cam_off = nullptr;
   int *cluster_np = nullptr, *cluster_n = nullptr;
   int64_t *S_off = nullptr, *v_off = nullptr;
   CamLists clist{};
   CamSlots cslots{};
-  PairLists plist{};
+  PairChunks pchunks{};
+  CameraGraph cgraph;                   // camera graph with its observation pairs (host copy)
   void* Gbuf = nullptr;
   int64_t n_pairs = 0;
   CholPlan cplan{};
@@ -201,6 +202,7 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.obs_cam = c->obs_cam;
   P.obs_vp = c->obs_vp;
   P.obs_pt = c->obs_pt;
+  P.obs_base = c->obs_base;
   P.obs_uv = c->obs_uv;
   P.obs_uvf = c->obs_uvf;
   P.obs_uvdf = c->obs_uvdf;
@@ -300,16 +302,21 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   c->S_total = so;
   c->v_total = vo;
 
-  // observation order (point, cluster, camera): stable sort of each point run by cluster
-  std::vector<int> order(c->base_order);
+  // observation order (point, cluster, camera): stable sort of each point run by cluster; bpos holds the
+  // position of every sorted observation in the (point, camera) order
+  std::vector<int> bpos(q);
+  std::iota(bpos.begin(), bpos.end(), 0);
   for (int i = 0; i < n; ++i) {
     const int b = c->h_pt_off[i], e = c->h_pt_off[i + 1];
     bool same = true;
-    for (int o = b + 1; o < e && same; ++o) same = cl[c->in_cam[order[o]]] == cl[c->in_cam[order[b]]];
+    for (int o = b + 1; o < e && same; ++o) same = cl[c->in_cam[c->base_order[o]]] == cl[c->in_cam[c->base_order[b]]];
     if (!same)
-      std::stable_sort(order.begin() + b, order.begin() + e,
-                       [&](int x, int y) { return cl[c->in_cam[x]] < cl[c->in_cam[y]]; });
+      std::stable_sort(bpos.begin() + b, bpos.begin() + e, [&](int x, int y) {
+        return cl[c->in_cam[c->base_order[x]]] < cl[c->in_cam[c->base_order[y]]];
+      });
   }
+  std::vector<int> order(q);
+  for (int o = 0; o < q; ++o) order[o] = c->base_order[bpos[o]];
   std::vector<int> s_cam(q), s_vp(q), s_pt(q), vp_off, vp_point, pt_vp_off(n + 1, 0);
   std::vector<double> s_uv(2 * (size_t)q);
   std::vector<float> s_uvf(c->mixed ? 2 * (size_t)q : 0);
@@ -374,25 +381,14 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
       }
     }
   }
-  // camera-pair instances of the pair pass, sorted by (cluster, la, lb): inside a virtual point the
-  // observations are ordered by camera, so a later observation has the larger local camera index
+  // camera-pair instances of this assignment (for the record; the pair pass walks the camera graph)
   int64_t npairs = 0;
-  for (int v = 0; v < nv && !c->use_pcg; ++v) {   // the PCG solver forms no cluster system
+  for (int v = 0; v < nv; ++v) {
     const int64_t len = vp_off[v + 1] - vp_off[v];
     npairs += len * (len - 1) / 2;
   }
-  if (npairs > INT32_MAX) return fail(c, STBA_ERR_INVALID_ARG, "more than 2^31 camera-pair instances");
-  std::vector<int4> pairs;
-  pairs.reserve(npairs);
-  for (int v = 0; v < nv && !c->use_pcg; ++v)
-    for (int a2 = vp_off[v] + 1; a2 < vp_off[v + 1]; ++a2)
-      for (int b2 = vp_off[v]; b2 < a2; ++b2)
-        pairs.push_back(make_int4(a2, b2, cl[s_cam[a2]], (cam_local[s_cam[a2]] << 16) | cam_local[s_cam[b2]]));
-  std::sort(pairs.begin(), pairs.end(), [](const int4& x, const int4& y) {
-    return x.z != y.z ? x.z < y.z : (x.w != y.w ? x.w < y.w : x.x < y.x);
-  });
   c->n_pairs = npairs;
-  c->build_items = (int)((npairs + 63) / 64);
+  c->build_items = c->use_pcg ? 0 : c->pchunks.nchunks;
 
   // Cholesky step plan (none for the PCG solver)
   if (c->use_pcg) {
@@ -434,7 +430,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     int factor_launches = 3;
     for (int kt = 0; kt < max_nt; ++kt)
       factor_launches += (c->h_panel_off[kt + 1] > c->h_panel_off[kt]) + (c->h_update_off[kt + 1] > c->h_update_off[kt]);
-    const int build_launches = 1 + (npairs > 0 ? 1 : 0);
+    const int build_launches = 1 + (c->pchunks.nchunks > 0 && l < m ? 1 : 0);
     const int solve_launches = 2 + c->set.refine_steps * (2 + (res_items.empty() ? 0 : 1));
     // iter_begin, vp_reduce, vp_finalize | build | factor | solve, count | rhs, update, cam_rt, (cam_df,
     // point_df,) cost, finalize, apply
@@ -452,6 +448,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(c->obs_cam, s_cam);
   UP(c->obs_vp, s_vp);
   UP(c->obs_pt, s_pt);
+  UP(c->obs_base, bpos);
   UP(c->obs_perm, perm);
   UP(c->obs_uv, s_uv);
   if (c->mixed) UP(c->obs_uvf, s_uvf);
@@ -469,8 +466,6 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(c->S_off, c->h_S_off);
   UP(c->v_off, c->h_v_off);
   int *d_cam_obs_off, *d_cam_obs, *d_cam_slots, *d_warp_cam;
-  int4* d_pairs;
-  UP(d_pairs, pairs);
   UP(d_cam_obs_off, cam_obs_off);
   UP(d_cam_obs, cam_obs);
   UP(d_cam_slots, cam_slots);
@@ -481,7 +476,6 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   UP(d_res, res_items);
   UP(d_diag, diag_items);
 #undef UP
-  c->plist = PairLists{d_pairs, (int)npairs};
   c->clist = CamLists{d_cam_obs_off, d_cam_obs};
   c->cslots = CamSlots{d_cam_slots, d_warp_cam, (int)warp_cam.size()};
   c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
@@ -562,7 +556,7 @@ void enqueue_step(stba_ctx* c, bool stages) {
   launch_vp_finalize<real>(P, W, c->st, s);
   mark(1);
   // stage 1: S' and b'
-  launch_rcs_build<real>(P, W, c->cslots, c->plist, (real*)c->Gbuf, c->st, s);
+  launch_rcs_build<real>(P, W, c->cslots, c->pchunks, (real*)c->Gbuf, c->st, s);
   mark(2);
   // stage 2: factorisation (FP32 factor in mixed mode, FP64 factor in FP64 mode)
   launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
@@ -961,6 +955,27 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     cudaError_t e3 = cudaMemcpyAsync(c->st, &h, sizeof h, cudaMemcpyHostToDevice, c->stream);
     cudaError_t e4 = cudaStreamSynchronize(c->stream);
     if (e1 || e2 || e3 || e4) return bail(fail(c, STBA_ERR_CUDA, "upload failed"));
+  }
+  // camera graph and the chunks of its observation pairs for the off-diagonal S' build
+  {
+    std::vector<int> base_cam(q);
+    for (int64_t o = 0; o < q; ++o) base_cam[o] = c->in_cam[c->base_order[o]];
+    build_camera_graph((int)m, (int)n, c->h_pt_off, base_cam, c->cgraph);
+    const CameraGraph& g = c->cgraph;
+    if ((int64_t)g.pairs.size() > INT32_MAX - PAIR_CHUNK)
+      return bail(fail(c, STBA_ERR_INVALID_ARG, "more than 2^31 co-visible observation pairs"));
+    if (!c->use_pcg && !g.pairs.empty()) {
+      std::vector<int4> chunks;
+      for (int x = 0; x < (int)m; ++x)
+        for (int e = g.edge_off[x]; e < g.edge_off[x + 1]; ++e)
+          for (int64_t p0 = g.pair_off[e]; p0 < g.pair_off[e + 1]; p0 += PAIR_CHUNK)
+            chunks.push_back(make_int4(x, g.edge_y[e], (int)p0, (int)std::min<int64_t>(PAIR_CHUNK, g.pair_off[e + 1] - p0)));
+      int4* d_chunks = nullptr;
+      int2* d_pairs = nullptr;
+      if ((s = upload(c, &d_chunks, chunks, false)) != STBA_OK) return bail(s);
+      if ((s = upload(c, &d_pairs, g.pairs, false)) != STBA_OK) return bail(s);
+      c->pchunks = PairChunks{d_chunks, d_pairs, (int)chunks.size()};
+    }
   }
   if ((s = set_clusters_host(c, h_cl)) != STBA_OK) return bail(s);
   double F;

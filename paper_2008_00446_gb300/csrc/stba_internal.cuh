@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "../../include/stba.h"
 
@@ -24,6 +25,7 @@ struct DevProblem {
   const int* obs_cam;      // [q] camera of each sorted observation
   const int* obs_vp;       // [q] virtual point of each sorted observation
   const int* obs_pt;       // [q] point of each sorted observation
+  const int* obs_base;     // [q] position of each sorted observation in the (point, camera) order
   const double* obs_uv;    // [q][2] FP64 observations
   const float* obs_uvf;    // [q][2] FP32 copy (mixed precision)
   const float4* obs_uvdf;  // [q] double-float copy (u_hi, u_lo, v_hi, v_lo) (mixed precision)
@@ -97,10 +99,25 @@ struct CamSlots {     // per-camera observation lists padded to whole warps, for
   int nwarps;
 };
 
-struct PairLists {    // camera-pair instances of the S' build (host-built per cluster assignment)
-  const int4* pairs;        // (obs a, obs b, cluster k, (la << 16) | lb), sorted by (k, la, lb)
-  int npairs;
+struct PairChunks {   // observation pairs of the camera graph, by edge, cut into chunks (built at create)
+  const int4* chunks;       // (camera x, camera y < x, first pair, number of pairs <= PAIR_CHUNK)
+  const int2* pairs;        // (base position of the observation by x, base position of the one by y)
+  int nchunks;
 };
+constexpr int PAIR_CHUNK = 64;
+
+// Camera graph (stba_graph.cu): edges (x, y), y < x, grouped by x with y ascending; weight = number of
+// common points; the observation pairs of each edge (base positions, observations sorted by (point,
+// camera)), ordered by point.
+struct CameraGraph {
+  std::vector<int> edge_off;       // [m+1]
+  std::vector<int> edge_y;         // [E]
+  std::vector<int> edge_w;         // [E]
+  std::vector<int64_t> pair_off;   // [E+1]
+  std::vector<int2> pairs;         // [P]
+};
+void build_camera_graph(int m, int n, const std::vector<int>& pt_off, const std::vector<int>& base_cam,
+                        CameraGraph& g);
 
 constexpr int RED_BLOCKS = 456;    // 3 x 152 SMs: fixed grid of the deterministic reductions
 constexpr int RED_THREADS = 256;
@@ -112,7 +129,7 @@ void launch_vp_reduce(const DevProblem& P, Scratch<real> W, cudaStream_t stream)
 template <typename real>
 void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream);
 template <typename real>
-void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairLists B, real* Gbuf, DevState* st,
+void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
                       cudaStream_t stream);
 template <typename real>
 void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream);

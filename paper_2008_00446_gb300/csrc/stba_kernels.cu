@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real>
       N01 = -(Pm[0][0] * Pm[0][1] + Pm[1][0] * Pm[1][1] + Pm[2][0] * Pm[2][1]);
       N11 = real(1) - (Pm[0][1] * Pm[0][1] + Pm[1][1] * Pm[1][1] + Pm[2][1] * Pm[2][1]);
       // G = L^-1 Jp^T Jc = P Jc (3x9), stored by columns with 16-byte vector stores
-      real* Gs = Gbuf + (size_t)GSTRIDE * o;
+      real* Gs = Gbuf + (size_t)GSTRIDE * P.obs_base[o];   // indexed like the camera graph's pairs
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         const real g0 = Pm[0][0] * Jc[0][c] + Pm[0][1] * Jc[1][c];
@@ -379,46 +379,32 @@ __global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real>
   }
 }
 
-// k_pair_build: the camera-pair instances (observations a, b of one virtual point, local camera index
-// of a > that of b) are sorted by (cluster, camera block).  Each warp walks a contiguous range of them;
-// 27 lanes own a row and three columns of the 9x9 block and accumulate -G_a^T G_b in registers while the
-// block stays the same, so each run of equal blocks costs one atomic add per entry into the FP64 S'_k.
-constexpr int PAIRS_PER_WARP = 64;
-
+// k_pair_build: the off-diagonal blocks S'_k(la, lb) = -sum over the points seen by both cameras x > y of
+// one cluster of G_x^T G_y (Eq. 10, 13).  The observation pairs of the camera graph are listed once, at
+// create, by edge (x, y) and cut into chunks of at most PAIR_CHUNK; under a cluster assignment an edge
+// contributes exactly when both cameras are in one cluster (its two observations of a point are then in
+// one virtual point), and a chunk adds to one block only.  One warp per chunk: it stages the G rows of CH
+// pairs at a time in shared memory (one row per lane, all loads in flight), its 27 lanes accumulate the
+// 9x9 block in registers (row r, columns 3cg .. 3cg+2) and add it once into the FP64 S'_k.
 template <typename real>
-__global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, const int4* __restrict__ pairs,
-                                                    int npairs, const real* __restrict__ Gbuf) {
-  // Each warp stages the G blocks of CH pairs in shared memory (one G_o per lane, all loads in flight),
-  // then its 27 lanes accumulate the chunk from there.
+__global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, PairChunks B,
+                                                    const real* __restrict__ Gbuf) {
   constexpr int CH = 64 / (int)sizeof(real);
   __shared__ __align__(16) real Gs[8][CH][2][GSTRIDE];
   const int wib = threadIdx.x >> 5;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int p0 = warp * PAIRS_PER_WARP;
-  if (p0 >= npairs) return;
-  const int p1 = min(p0 + PAIRS_PER_WARP, npairs);
-  const int r = lane / 3, cg = lane - (lane / 3) * 3;   // lanes 0..26: row r, columns 3cg .. 3cg+2
+  if (warp >= B.nchunks) return;
+  const int4 ch = B.chunks[warp];
+  const int k = P.cam_cluster[ch.x];
+  if (P.cam_cluster[ch.y] != k) return;   // uniform per warp: the edge is cut by the clustering
+  const int r = lane / 3, cg = lane - (lane / 3) * 3;
   const bool act = lane < 27;
   real acc0 = 0, acc1 = 0, acc2 = 0;
-  int cur_k = pairs[p0].z, cur_w = pairs[p0].w;
-  auto flush = [&]() {
-    if (act) {
-      const int la = cur_w >> 16, lb = cur_w & 0xffff;
-      double* dst = W.S + P.S_off[cur_k] + (size_t)(9 * la + r) * P.cluster_np[cur_k] + 9 * lb + 3 * cg;
-      atomicAdd(dst, -(double)acc0);
-      atomicAdd(dst + 1, -(double)acc1);
-      atomicAdd(dst + 2, -(double)acc2);
-    }
-    acc0 = acc1 = acc2 = 0;
-  };
-  for (int c0 = p0; c0 < p1; c0 += CH) {
-    const int cn = min(CH, p1 - c0);
-    const int j = lane % CH, side = lane / CH;
-    int pk = -1, pw = -1;
+  const int j = lane % CH, side = lane / CH;
+  for (int c0 = 0; c0 < ch.w; c0 += CH) {
+    const int cn = min(CH, ch.w - c0);
     if (side < 2 && j < cn) {
-      const int4 pr = pairs[c0 + j];
-      pk = pr.z;
-      pw = pr.w;
+      const int2 pr = B.pairs[ch.z + c0 + j];
       const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
       real* dst = &Gs[wib][j][side][0];
       if constexpr (sizeof(real) == 4) {
@@ -431,18 +417,9 @@ __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> 
           reinterpret_cast<double2*>(dst)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
       }
     }
-    // run starts inside the chunk: bit jj set when pair c0 + jj differs in camera block from its predecessor
-    const int prev_k = __shfl_up_sync(FULL_MASK, pk, 1), prev_w = __shfl_up_sync(FULL_MASK, pw, 1);
-    const bool starts = (lane < cn) && (lane == 0 ? (pk != cur_k || pw != cur_w) : (pk != prev_k || pw != prev_w));
-    const unsigned run_mask = __ballot_sync(FULL_MASK, starts);
     __syncwarp();
-    for (int jj = 0; jj < cn; ++jj) {
-      if ((run_mask >> jj) & 1u) {   // the run of equal camera blocks ended
-        flush();
-        cur_k = __shfl_sync(FULL_MASK, pk, jj);
-        cur_w = __shfl_sync(FULL_MASK, pw, jj);
-      }
-      if (act) {
+    if (act) {
+      for (int jj = 0; jj < cn; ++jj) {
         real a[3], b0[3], b1[3], b2[3];
         load_gcol_s(&Gs[wib][jj][0][4 * r], a);
         load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg)], b0);
@@ -458,17 +435,20 @@ __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> 
     }
     __syncwarp();
   }
-  flush();
+  if (act) {
+    const int la = P.cam_local[ch.x], lb = P.cam_local[ch.y];   // la > lb: local order follows camera order
+    double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
+    atomicAdd(dst, -(double)acc0);
+    atomicAdd(dst + 1, -(double)acc1);
+    atomicAdd(dst + 2, -(double)acc2);
+  }
 }
 
 template <typename real>
-void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairLists B, real* Gbuf, DevState* st,
+void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
                       cudaStream_t stream) {
   k_cam_pass<real><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
-  if (B.npairs > 0) {
-    const int warps = (B.npairs + PAIRS_PER_WARP - 1) / PAIRS_PER_WARP;
-    k_pair_build<real><<<(warps + 7) / 8, 256, 0, stream>>>(P, W, B.pairs, B.npairs, Gbuf);
-  }
+  if (B.nchunks > 0 && P.l < P.m) k_pair_build<real><<<(B.nchunks + 7) / 8, 256, 0, stream>>>(P, W, B, Gbuf);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -903,7 +883,7 @@ void configure_kernels(int max_np) { configure_solve_kernels(max_np); }
   template void launch_iter_begin<real>(DevState*, const Settings&, cudaStream_t);                        \
   template void launch_vp_reduce<real>(const DevProblem&, Scratch<real>, cudaStream_t);                   \
   template void launch_vp_finalize<real>(const DevProblem&, Scratch<real>, DevState*, cudaStream_t);      \
-  template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamSlots, PairLists, real*,      \
+  template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamSlots, PairChunks, real*,     \
                                        DevState*, cudaStream_t);                                          \
   template void launch_point_update<real>(const DevProblem&, Scratch<real>, cudaStream_t);                \
   template void launch_finalize<real>(const DevProblem&, Scratch<real>, DevState*, const Settings&, int,  \
