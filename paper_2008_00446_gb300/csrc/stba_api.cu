@@ -29,6 +29,11 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+struct GrowBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
 }  // namespace
 
 struct stba_ctx {
@@ -74,6 +79,15 @@ struct stba_ctx {
   PairChunks pchunks{};
   CameraGraph cgraph;                   // camera graph with its observation pairs (host copy)
   void* Gbuf = nullptr;
+  // re-ordering for new assignments: fixed arguments, the two inverse maps (previous / current), scratch
+  ReorderArgs reorder{};
+  int* inv[2] = {nullptr, nullptr};
+  int inv_cur = 0;
+  bool have_order = false;               // an assignment is in place (its residual order is defined)
+  int *key = nullptr, *tile_sum = nullptr;
+  long long* counts = nullptr;
+  // buffers sized by the cluster layout, kept while the next layout fits
+  GrowBuf g_panel, g_update, g_res, g_diag, g_S, g_b, g_L, g_Dinv, g_Ldiag, g_scale, g_x, g_r;
   int64_t n_pairs = 0;
   CholPlan cplan{};
   FactorBuffers fbuf{};
@@ -244,14 +258,42 @@ Scratch<real> scratch(const stba_ctx* c) {
 
 
 // ------------------------------------------------------------------------------------------------------
-// Cluster-assignment preprocessing: order the observations by (point, cluster, camera), define the
-// virtual points (distinct (point, cluster) pairs), the per-cluster dense layout, the tile work lists of
-// the S' build and the Cholesky step plan.
+// Device buffer that keeps its allocation while a new size fits (grown by a quarter when it does not).
+template <typename T>
+stba_status ensure(stba_ctx* c, GrowBuf& g, T** p, size_t count) {
+  const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+  if (bytes > g.bytes) {
+    if (g.ptr) cudaFree(g.ptr);
+    g.ptr = nullptr;
+    g.bytes = 0;
+    const size_t want = bytes + bytes / 4;
+    if (cudaMalloc(&g.ptr, want) != cudaSuccess) {
+      cudaGetLastError();
+      g.ptr = nullptr;
+      return fail(c, STBA_ERR_OOM, "cudaMalloc of %zu bytes failed", want);
+    }
+    g.bytes = want;
+  }
+  *p = reinterpret_cast<T*>(g.ptr);
+  return STBA_OK;
+}
+
+template <typename T>
+stba_status put(stba_ctx* c, T* dst, const std::vector<T>& h) {
+  if (!h.empty()) CK(cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
+  return STBA_OK;
+}
+
+// ------------------------------------------------------------------------------------------------------
+// A new cluster assignment.  The host validates it and lays out the clusters (camera lists, the dense
+// blocks of S'_k, the Cholesky step plan: O(m + l + plan) work); the device re-orders the observations
+// by (point, cluster, camera), numbers the virtual points (distinct (point, cluster) pairs) and rebuilds
+// the camera lists (stba_order.cu), carrying the stored residuals over to the new order.
 stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   const int m = (int)c->m, n = (int)c->n, q = (int)c->q;
   int l = 0;
   for (int j = 0; j < m; ++j) {
-    if (cl[j] < 0) return fail(c, STBA_ERR_INVALID_ARG, "cluster id %d of camera %d is negative", cl[j], j);
+    if (cl[j] < 0 || cl[j] >= m) return fail(c, STBA_ERR_INVALID_ARG, "cluster id %d of camera %d out of range", cl[j], j);
     l = std::max(l, cl[j] + 1);
   }
   std::vector<int> cnt(l, 0);
@@ -259,12 +301,10 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   for (int k = 0; k < l; ++k)
     if (cnt[k] == 0) return fail(c, STBA_ERR_INVALID_ARG, "cluster %d has no camera (ids must be 0..l-1)", k);
 
-  free_list(c, c->cl_allocs);
   if (c->graph) {
     cudaGraphExecDestroy(c->graph);
     c->graph = nullptr;
   }
-  c->bytes_cl = 0;
   c->l = l;
   c->h_clusters = cl;
   // cameras of every cluster, ascending
@@ -301,93 +341,6 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   }
   c->S_total = so;
   c->v_total = vo;
-
-  // observation order (point, cluster, camera): stable sort of each point run by cluster; bpos holds the
-  // position of every sorted observation in the (point, camera) order
-  std::vector<int> bpos(q);
-  std::iota(bpos.begin(), bpos.end(), 0);
-  for (int i = 0; i < n; ++i) {
-    const int b = c->h_pt_off[i], e = c->h_pt_off[i + 1];
-    bool same = true;
-    for (int o = b + 1; o < e && same; ++o) same = cl[c->in_cam[c->base_order[o]]] == cl[c->in_cam[c->base_order[b]]];
-    if (!same)
-      std::stable_sort(bpos.begin() + b, bpos.begin() + e, [&](int x, int y) {
-        return cl[c->in_cam[c->base_order[x]]] < cl[c->in_cam[c->base_order[y]]];
-      });
-  }
-  std::vector<int> order(q);
-  for (int o = 0; o < q; ++o) order[o] = c->base_order[bpos[o]];
-  std::vector<int> s_cam(q), s_vp(q), s_pt(q), vp_off, vp_point, pt_vp_off(n + 1, 0);
-  std::vector<double> s_uv(2 * (size_t)q);
-  std::vector<float> s_uvf(c->mixed ? 2 * (size_t)q : 0);
-  std::vector<float4> s_uvdf(c->mixed ? (size_t)q : 0);
-  vp_off.reserve(q + 1);
-  vp_point.reserve(q);
-  for (int i = 0; i < n; ++i) {
-    pt_vp_off[i] = (int)vp_point.size();
-    int prev = -1;
-    for (int o = c->h_pt_off[i]; o < c->h_pt_off[i + 1]; ++o) {
-      const int src = order[o];
-      const int cam = c->in_cam[src];
-      if (cl[cam] != prev) {
-        vp_off.push_back(o);
-        vp_point.push_back(i);
-        prev = cl[cam];
-      }
-      s_cam[o] = cam;
-      s_vp[o] = (int)vp_point.size() - 1;
-      s_pt[o] = i;
-      s_uv[2 * (size_t)o] = c->in_uv[2 * (size_t)src];
-      s_uv[2 * (size_t)o + 1] = c->in_uv[2 * (size_t)src + 1];
-      if (c->mixed) {
-        const double u = s_uv[2 * (size_t)o], v = s_uv[2 * (size_t)o + 1];
-        s_uvf[2 * (size_t)o] = (float)u;
-        s_uvf[2 * (size_t)o + 1] = (float)v;
-        const float uh = (float)u, vh = (float)v;
-        s_uvdf[o] = make_float4(uh, (float)(u - (double)uh), vh, (float)(v - (double)vh));
-      }
-    }
-  }
-  pt_vp_off[n] = (int)vp_point.size();
-  vp_off.push_back(q);
-  const int nv = (int)vp_point.size();
-  c->nv = nv;
-
-  // observations of every camera (sorted positions), for the camera pass of the S' build
-  std::vector<int> cam_obs_off(m + 1, 0), cam_obs(q);
-  for (int o = 0; o < q; ++o) cam_obs_off[s_cam[o] + 1]++;
-  for (int j = 0; j < m; ++j) cam_obs_off[j + 1] += cam_obs_off[j];
-  {
-    // per camera, observations of single-observation virtual points first (they take the Woodbury branch
-    // of the camera pass), then the others, so that warps mostly run one branch
-    std::vector<int> f(cam_obs_off.begin(), cam_obs_off.end() - 1);
-    for (int pass = 0; pass < 2; ++pass)
-      for (int o = 0; o < q; ++o) {
-        const int v = s_vp[o];
-        const bool single = vp_off[v + 1] - vp_off[v] == 1;
-        if (single == (pass == 0)) cam_obs[f[s_cam[o]]++] = o;
-      }
-  }
-  // the same lists padded to whole warps (32 slots, -1 = padding) for the camera pass
-  std::vector<int> cam_slots, warp_cam;
-  for (int j = 0; j < m; ++j) {
-    const int cnt_j = cam_obs_off[j + 1] - cam_obs_off[j];
-    const int nw = (cnt_j + 31) / 32;
-    for (int w = 0; w < nw; ++w) {
-      warp_cam.push_back(j);
-      for (int l = 0; l < 32; ++l) {
-        const int e = 32 * w + l;
-        cam_slots.push_back(e < cnt_j ? cam_obs[cam_obs_off[j] + e] : -1);
-      }
-    }
-  }
-  // camera-pair instances of this assignment (for the record; the pair pass walks the camera graph)
-  int64_t npairs = 0;
-  for (int v = 0; v < nv; ++v) {
-    const int64_t len = vp_off[v + 1] - vp_off[v];
-    npairs += len * (len - 1) / 2;
-  }
-  c->n_pairs = npairs;
   c->build_items = c->use_pcg ? 0 : c->pchunks.nchunks;
 
   // Cholesky step plan (none for the PCG solver)
@@ -439,45 +392,25 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     for (int k = 0; k < l; ++k) c->factor_flops += std::pow((double)c->h_nk[k], 3) / 3.0;
   }
 
-  // upload
+  // cluster arrays and plan on the device
   stba_status s;
-  std::vector<int> cam_cluster(cl.begin(), cl.end());
-  std::vector<int> perm(order.begin(), order.end());
-#define UP(ptr, vec) \
-  if ((s = upload(c, &(ptr), vec, true)) != STBA_OK) return s;
-  UP(c->obs_cam, s_cam);
-  UP(c->obs_vp, s_vp);
-  UP(c->obs_pt, s_pt);
-  UP(c->obs_base, bpos);
-  UP(c->obs_perm, perm);
-  UP(c->obs_uv, s_uv);
-  if (c->mixed) UP(c->obs_uvf, s_uvf);
-  if (c->mixed) UP(c->obs_uvdf, s_uvdf);
-  UP(c->vp_off, vp_off);
-  UP(c->vp_point, vp_point);
-  UP(c->pt_vp_off, pt_vp_off);
-  UP(c->pt_off, c->h_pt_off);
-  UP(c->cam_local, cam_local);
-  UP(c->cam_cluster, cam_cluster);
-  UP(c->cluster_cams, c->h_cluster_cams);
-  UP(c->cluster_cam_off, c->h_cluster_cam_off);
-  UP(c->cluster_np, c->h_np);
-  UP(c->cluster_n, c->h_nk);
-  UP(c->S_off, c->h_S_off);
-  UP(c->v_off, c->h_v_off);
-  int *d_cam_obs_off, *d_cam_obs, *d_cam_slots, *d_warp_cam;
-  UP(d_cam_obs_off, cam_obs_off);
-  UP(d_cam_obs, cam_obs);
-  UP(d_cam_slots, cam_slots);
-  UP(d_warp_cam, warp_cam);
+  if ((s = put(c, c->cam_local, cam_local)) != STBA_OK) return s;
+  if ((s = put(c, c->cam_cluster, cl)) != STBA_OK) return s;
+  if ((s = put(c, c->cluster_cams, c->h_cluster_cams)) != STBA_OK) return s;
+  if ((s = put(c, c->cluster_cam_off, c->h_cluster_cam_off)) != STBA_OK) return s;
+  if ((s = put(c, c->cluster_np, c->h_np)) != STBA_OK) return s;
+  if ((s = put(c, c->cluster_n, c->h_nk)) != STBA_OK) return s;
+  if ((s = put(c, c->S_off, c->h_S_off)) != STBA_OK) return s;
+  if ((s = put(c, c->v_off, c->h_v_off)) != STBA_OK) return s;
   int2 *d_panel, *d_update, *d_res, *d_diag;
-  UP(d_panel, panel);
-  UP(d_update, update);
-  UP(d_res, res_items);
-  UP(d_diag, diag_items);
-#undef UP
-  c->clist = CamLists{d_cam_obs_off, d_cam_obs};
-  c->cslots = CamSlots{d_cam_slots, d_warp_cam, (int)warp_cam.size()};
+  if ((s = ensure(c, c->g_panel, &d_panel, panel.size())) != STBA_OK) return s;
+  if ((s = ensure(c, c->g_update, &d_update, update.size())) != STBA_OK) return s;
+  if ((s = ensure(c, c->g_res, &d_res, res_items.size())) != STBA_OK) return s;
+  if ((s = ensure(c, c->g_diag, &d_diag, diag_items.size())) != STBA_OK) return s;
+  if ((s = put(c, d_panel, panel)) != STBA_OK) return s;
+  if ((s = put(c, d_update, update)) != STBA_OK) return s;
+  if ((s = put(c, d_res, res_items)) != STBA_OK) return s;
+  if ((s = put(c, d_diag, diag_items)) != STBA_OK) return s;
   c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
                       c->h_panel_off.data(),
                       c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
@@ -488,40 +421,55 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->cplan.prio_high = greatest;
     c->cplan.prio_low = least;
   }
-
+  // cluster systems and factor storage
   const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
-  auto ralloc = [&](void** p, size_t count) -> stba_status {
-    char* q_ = nullptr;
-    stba_status st_ = dalloc(c, &q_, count * rs, true);
-    *p = q_;
-    return st_;
-  };
-  if ((s = ralloc(&c->vp_acc, 9 * (size_t)nv)) != STBA_OK) return s;
-  if ((s = ralloc(&c->vp_info, 9 * (size_t)nv)) != STBA_OK) return s;
-  if ((s = ralloc(&c->pt_info, 9 * (size_t)n)) != STBA_OK) return s;
   {
     double *S_, *b_;
-    if ((s = dalloc(c, &S_, (size_t)c->S_total, true)) != STBA_OK) return s;
-    if ((s = dalloc(c, &b_, (size_t)c->v_total, true)) != STBA_OK) return s;
+    char *L_, *Dinv_, *Ldiag_;
+    if ((s = ensure(c, c->g_S, &S_, (size_t)c->S_total)) != STBA_OK) return s;
+    if ((s = ensure(c, c->g_b, &b_, (size_t)c->v_total)) != STBA_OK) return s;
+    if ((s = ensure(c, c->g_L, &L_, (size_t)c->S_total * rs)) != STBA_OK) return s;
+    if ((s = ensure(c, c->g_Dinv, &Dinv_, 2 * (size_t)c->v_total * TF * rs)) != STBA_OK) return s;
+    if ((s = ensure(c, c->g_Ldiag, &Ldiag_, (size_t)c->v_total * TF * rs)) != STBA_OK) return s;
+    if ((s = ensure(c, c->g_scale, &c->fbuf.scale, (size_t)c->v_total)) != STBA_OK) return s;
+    if ((s = ensure(c, c->g_x, &c->fbuf.x, (size_t)c->v_total)) != STBA_OK) return s;
+    if ((s = ensure(c, c->g_r, &c->fbuf.r, (size_t)c->v_total)) != STBA_OK) return s;
     c->S = S_;
     c->b = b_;
+    c->fbuf.L = L_;
+    c->fbuf.Dinv = Dinv_;
+    c->fbuf.Ldiag = Ldiag_;
   }
-  if ((s = ralloc(&c->vgrad, 9 * (size_t)m)) != STBA_OK) return s;
-  if ((s = ralloc(&c->t_acc, 3 * (size_t)n)) != STBA_OK) return s;
-  if ((s = ralloc(&c->Gbuf, c->use_pcg ? 1 : 36 * (size_t)q)) != STBA_OK) return s;
-  if ((s = ralloc(&c->fbuf.L, (size_t)c->S_total)) != STBA_OK) return s;
-  if ((s = ralloc(&c->fbuf.Dinv, 2 * (size_t)c->v_total * TF)) != STBA_OK) return s;
-  if ((s = ralloc(&c->fbuf.Ldiag, (size_t)c->v_total * TF)) != STBA_OK) return s;
-  if ((s = dalloc(c, &c->fbuf.scale, (size_t)c->v_total, true)) != STBA_OK) return s;
-  if ((s = dalloc(c, &c->fbuf.x, (size_t)c->v_total, true)) != STBA_OK) return s;
-  if ((s = dalloc(c, &c->fbuf.r, (size_t)c->v_total, true)) != STBA_OK) return s;
-  if ((s = dalloc(c, &c->fail_flags, (size_t)l, true)) != STBA_OK) return s;
   c->fbuf.fail_flags = c->fail_flags;
   c->fbuf.boosted = &c->st->boosted;
   c->fbuf.v_total = c->v_total;
+
+  // observation order, virtual points and camera lists on the device; the stored residuals follow
+  {
+    ReorderArgs A = c->reorder;
+    A.inv_old = c->inv[c->inv_cur];
+    A.inv_new = c->inv[1 - c->inv_cur];
+    const bool carry = c->have_order;
+    if (c->mixed)
+      launch_reorder<float>(A, c->key, c->tile_sum, c->counts, carry ? (const float*)c->res_cur : nullptr,
+                            (float*)c->res_cand, c->stream);
+    else
+      launch_reorder<double>(A, c->key, c->tile_sum, c->counts, carry ? (const double*)c->res_cur : nullptr,
+                             (double*)c->res_cand, c->stream);
+    CK(cudaGetLastError());
+    if (carry) std::swap(c->res_cur, c->res_cand);
+    c->inv_cur = 1 - c->inv_cur;
+    c->have_order = true;
+    long long h_counts[2];
+    CK(cudaMemcpyAsync(h_counts, c->counts, sizeof h_counts, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->nv = (int)h_counts[0];
+    c->n_pairs = h_counts[1];
+  }
+  (void)n;
+  (void)q;
   if (!c->use_pcg) configure_kernels(c->max_np);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(c->stream));
   return STBA_OK;
 }
 
@@ -784,6 +732,9 @@ void stba_destroy(stba_ctx* c) {
   free_list(c, c->cl_allocs);
   free_list(c, c->allocs);
   free_list(c, c->tape_allocs);
+  for (GrowBuf* g : {&c->g_panel, &c->g_update, &c->g_res, &c->g_diag, &c->g_S, &c->g_b, &c->g_L, &c->g_Dinv,
+                     &c->g_Ldiag, &c->g_scale, &c->g_x, &c->g_r})
+    if (g->ptr) cudaFree(g->ptr);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -977,6 +928,130 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       c->pchunks = PairChunks{d_chunks, d_pairs, (int)chunks.size()};
     }
   }
+  // observation data in the (point, camera) base order, the camera lists, and every buffer whose size does
+  // not depend on the cluster assignment
+  {
+    const size_t Q = (size_t)q;
+    std::vector<int> base_cam(Q), base_src(Q), base_pt(Q);
+    std::vector<double> base_uv(2 * Q);
+    std::vector<float> base_uvf(c->mixed ? 2 * Q : 0);
+    std::vector<float4> base_uvdf(c->mixed ? Q : 0);
+    for (size_t bo = 0; bo < Q; ++bo) {
+      const int src = c->base_order[bo];
+      base_cam[bo] = c->in_cam[src];
+      base_src[bo] = src;
+      base_pt[bo] = c->in_pt[src];
+      const double u = c->in_uv[2 * (size_t)src], v = c->in_uv[2 * (size_t)src + 1];
+      base_uv[2 * bo] = u;
+      base_uv[2 * bo + 1] = v;
+      if (c->mixed) {
+        const float uh = (float)u, vh = (float)v;
+        base_uvf[2 * bo] = uh;
+        base_uvf[2 * bo + 1] = vh;
+        base_uvdf[bo] = make_float4(uh, (float)(u - (double)uh), vh, (float)(v - (double)vh));
+      }
+    }
+    std::vector<int> cam_off(m + 1, 0), cam_base(Q), cam_warp_off(m + 1, 0), warp_cam;
+    for (size_t bo = 0; bo < Q; ++bo) cam_off[base_cam[bo] + 1]++;
+    for (int64_t j = 0; j < m; ++j) cam_off[j + 1] += cam_off[j];
+    {
+      std::vector<int> f(cam_off.begin(), cam_off.end() - 1);
+      for (size_t bo = 0; bo < Q; ++bo) cam_base[f[base_cam[bo]]++] = (int)bo;
+    }
+    for (int64_t j = 0; j < m; ++j) {
+      const int nw = (cam_off[j + 1] - cam_off[j] + 31) / 32;
+      cam_warp_off[j + 1] = cam_warp_off[j] + nw;
+      for (int w = 0; w < nw; ++w) warp_cam.push_back((int)j);
+    }
+    const int nwarps = cam_warp_off[m];
+    ReorderArgs& A = c->reorder;
+    A.q = (int)q;
+    A.n = (int)n;
+    A.m = (int)m;
+    int *d_base_cam, *d_base_src, *d_cam_off, *d_cam_base, *d_cam_warp_off, *d_warp_cam, *d_cam_obs, *d_slots;
+    double* d_base_uv;
+    if ((s = upload(c, &c->obs_pt, base_pt, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &c->pt_off, c->h_pt_off, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_base_cam, base_cam, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_base_src, base_src, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_base_uv, base_uv, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_cam_off, cam_off, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_cam_base, cam_base, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_cam_warp_off, cam_warp_off, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_warp_cam, warp_cam, false)) != STBA_OK) return bail(s);
+    A.base_uvf = nullptr;
+    A.base_uvdf = nullptr;
+    if (c->mixed) {
+      float* d_uvf;
+      float4* d_uvdf;
+      if ((s = upload(c, &d_uvf, base_uvf, false)) != STBA_OK) return bail(s);
+      if ((s = upload(c, &d_uvdf, base_uvdf, false)) != STBA_OK) return bail(s);
+      A.base_uvf = d_uvf;
+      A.base_uvdf = d_uvdf;
+      if ((s = dalloc(c, &c->obs_uvf, 2 * Q, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &c->obs_uvdf, Q, false)) != STBA_OK) return bail(s);
+    }
+    int* const* ints_q[] = {&c->obs_cam, &c->obs_vp, &c->obs_perm, &c->obs_base, &c->vp_point, &c->inv[0], &c->inv[1],
+                            &c->key};
+    for (int* const* pp : ints_q)
+      if ((s = dalloc(c, const_cast<int**>(pp), Q, false)) != STBA_OK) return bail(s);
+    int* d_start;
+    if ((s = dalloc(c, &d_start, Q + 1, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->vp_off, Q + 1, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->pt_vp_off, (size_t)n + 1, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->obs_uv, 2 * Q, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &d_cam_obs, Q, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &d_slots, 32 * (size_t)nwarps, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->tile_sum, Q / 2048 + 2, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->counts, 2, false)) != STBA_OK) return bail(s);
+    // cluster arrays at their largest size (l <= m)
+    int* const* ints_m[] = {&c->cam_local, &c->cam_cluster, &c->cluster_cams, &c->cluster_np, &c->cluster_n,
+                            &c->fail_flags};
+    for (int* const* pp : ints_m)
+      if ((s = dalloc(c, const_cast<int**>(pp), (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->cluster_cam_off, (size_t)m + 1, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->S_off, (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->v_off, (size_t)m, false)) != STBA_OK) return bail(s);
+    // per-iteration scratch (virtual-point arrays at their largest size, nv <= q)
+    const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
+    char *vpa, *vpi, *pti, *vg, *ta, *gb;
+    if ((s = dalloc(c, &vpa, 9 * Q * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &vpi, 9 * Q * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &pti, 9 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &vg, 9 * (size_t)m * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &ta, 3 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &gb, (c->use_pcg ? 1 : 36 * Q) * rs, false)) != STBA_OK) return bail(s);
+    c->vp_acc = vpa;
+    c->vp_info = vpi;
+    c->pt_info = pti;
+    c->vgrad = vg;
+    c->t_acc = ta;
+    c->Gbuf = gb;
+    A.obs_pt = c->obs_pt;
+    A.pt_off = c->pt_off;
+    A.base_cam = d_base_cam;
+    A.base_src = d_base_src;
+    A.base_uv = d_base_uv;
+    A.cam_cluster = c->cam_cluster;
+    A.start = d_start;
+    A.obs_base = c->obs_base;
+    A.obs_cam = c->obs_cam;
+    A.obs_perm = c->obs_perm;
+    A.obs_uv = c->obs_uv;
+    A.obs_uvf = c->obs_uvf;
+    A.obs_uvdf = c->obs_uvdf;
+    A.obs_vp = c->obs_vp;
+    A.vp_off = c->vp_off;
+    A.vp_point = c->vp_point;
+    A.pt_vp_off = c->pt_vp_off;
+    A.cam_off = d_cam_off;
+    A.cam_base = d_cam_base;
+    A.cam_warp_off = d_cam_warp_off;
+    A.cam_obs = d_cam_obs;
+    A.slots = d_slots;
+    c->clist = CamLists{d_cam_off, d_cam_obs};
+    c->cslots = CamSlots{d_slots, d_warp_cam, nwarps};
+  }
   if ((s = set_clusters_host(c, h_cl)) != STBA_OK) return bail(s);
   double F;
   if ((s = run_cost(c, &F)) != STBA_OK) return bail(s);
@@ -990,10 +1065,8 @@ stba_status stba_set_clusters(stba_ctx* c, const int32_t* cluster_assignment) {
   stba_status s;
   if ((s = copy_in(c, h.data(), cluster_assignment, (size_t)c->m * 4)) != STBA_OK) return s;
   CK(cudaStreamSynchronize(c->stream));
-  if ((s = set_clusters_host(c, h)) != STBA_OK) return s;
-  // the stored residuals follow the observation order, which depends on the clusters: recompute them
-  double F;
-  return stba_cost(c, &F);
+  // the stored residuals follow the observation order; set_clusters_host carries them over
+  return set_clusters_host(c, h);
 }
 
 stba_status stba_lm_iteration(stba_ctx* c, stba_iter_info* info) {
@@ -1197,7 +1270,11 @@ stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {
     maxn = std::max(maxn, v);
     s_elems += 0.5 * (double)v * (v + 1);
   }
-  const int64_t vals[12] = {c->m, c->n, c->q, c->l, c->nv, maxn, (int64_t)(c->bytes_base + c->bytes_cl),
+  size_t grown = 0;
+  for (const GrowBuf* g : {&c->g_panel, &c->g_update, &c->g_res, &c->g_diag, &c->g_S, &c->g_b, &c->g_L, &c->g_Dinv,
+                           &c->g_Ldiag, &c->g_scale, &c->g_x, &c->g_r})
+    grown += g->bytes;
+  const int64_t vals[12] = {c->m, c->n, c->q, c->l, c->nv, maxn, (int64_t)(c->bytes_base + c->bytes_cl + grown),
                             c->build_items, c->launches_per_iter, c->n_pairs, (int64_t)c->factor_flops,
                             (int64_t)s_elems};
   for (int i = 0; i < n && i < 12; ++i) out[i] = vals[i];

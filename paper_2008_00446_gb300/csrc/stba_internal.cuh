@@ -119,6 +119,37 @@ struct CameraGraph {
 void build_camera_graph(int m, int n, const std::vector<int>& pt_off, const std::vector<int>& base_cam,
                         CameraGraph& g);
 
+// Re-ordering for a new cluster assignment (stba_order.cu).  Base = the (point, camera) order of create.
+struct ReorderArgs {
+  int q, n, m;
+  const int* obs_pt;        // [q] point of every position (the same in both orders)
+  const int* pt_off;        // [n+1]
+  const int* base_cam;      // [q] camera, original index and observation of every base position
+  const int* base_src;
+  const double* base_uv;    // [q][2]
+  const float* base_uvf;    // [q][2] or null
+  const float4* base_uvdf;  // [q] or null
+  const int* cam_cluster;   // [m] the new assignment
+  const int* inv_old;       // [q] new position of every base position under the previous assignment
+  int* inv_new;             // [q] ... under the new one
+  int* start;               // [q] 1 where a virtual point starts
+  int *obs_base, *obs_cam, *obs_perm;
+  double* obs_uv;
+  float* obs_uvf;
+  float4* obs_uvdf;
+  int *obs_vp, *vp_off, *vp_point, *pt_vp_off;
+  const int* cam_off;       // [m+1] observations of every camera
+  const int* cam_base;      // [q]   their base positions, ascending
+  const int* cam_warp_off;  // [m+1] warps of every camera in the camera pass
+  int* cam_obs;             // [q] new positions, single-observation virtual points first
+  int* slots;               // [32 * warps] the same padded to whole warps (-1)
+};
+// key: [q] scratch; tile_sum: [q / 2048 + 1] scratch; counts: [2] -> number of virtual points, number of
+// camera-pair instances.  With res_old, the residuals are carried over into res_new in the new order.
+template <typename real>
+void launch_reorder(const ReorderArgs& A, int* key, int* tile_sum, long long* counts, const real* res_old,
+                    real* res_new, cudaStream_t stream);
+
 constexpr int RED_BLOCKS = 456;    // 3 x 152 SMs: fixed grid of the deterministic reductions
 constexpr int RED_THREADS = 256;
 
