@@ -11,9 +11,11 @@ paper's matrices:
   stba.py    -- the normal-equation blocks of Eq. 4, the Schur step of Eq. 5-6 (full-RCS LM), the
                 clustered system of Eq. 10 with point splitting/binding (Sec. 4.1-4.2), the per-cluster
                 solves of Eq. 13, the point update of Eq. 15, the steepest-descent correction of Sec. 4.3,
-                and the LM control of Algorithm 1 (Appendix C), plus brute-force solvers for pins.
+                and the LM control of Algorithm 1 (Appendix C), plus brute-force solvers for pins;
+  sgc.py     -- stochastic graph clustering of Sec. 4.4 (modularity, Eq. 16 join probabilities, the
+                sampler, and the exact distribution of final clusterings on tiny graphs).
 
 Every function is pinned by `tests/test_oracle_*.py` against something other than itself: finite
 differences, library rotations, brute-force dense solves of Eq. 3 and Eq. 9, closed forms and invariants.
 """
-from . import camera, stba  # noqa: F401
+from . import camera, sgc, stba  # noqa: F401
