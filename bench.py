@@ -25,6 +25,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "STBA LM iter/s and obs/s vs full-RCS LM on 1 GB300 at equal final RMSE"
 CONFIG = "c1_internet"
+SGC_GAMMA, SGC_BETA = 100, 10.0
+REORDER_LAUNCHES = 11  # kernels of one stba_set_clusters (device re-ordering)
 WORKLOADS = {
     "c1_internet": ("c1_internet: 1000 cameras (hemisphere r=20), 200k points (10^3 box), Zipf(2) tracks on [2,50] "
                     "over nearby viewpoints, 10 clusters of 100 cameras, mixed precision"),
@@ -219,24 +221,35 @@ def main():
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
                            precision=stba.STBA_MIXED, stream=stream)
     info0 = stba.stba_problem_info(ctx)
-    for _ in range(max(args.warmup, 3)):
+    # Algorithm 1 draws a new clustering every iteration (stochastic graph clustering, Sec. 4.4, with the
+    # paper's beta = 10, Gamma = 100).  The camera graph is fixed, so the draws do not depend on the
+    # iterations: they are made ahead on host threads, like a data loader, and timed separately.
+    e2e_steps = max(3, min(args.steps, 10))
+    n_draw = max(args.warmup, 3) + args.steps + e2e_steps
+    t0 = time.perf_counter()
+    seq, seq_l = stba.stba_cluster_sgc(ctx, count=n_draw, gamma=SGC_GAMMA, beta=SGC_BETA, seed=s.meta["seed"] + 1)
+    sgc_s = time.perf_counter() - t0
+    sgc = {"gamma": SGC_GAMMA, "beta": SGC_BETA, "draws": n_draw, "host_threads": min(os.cpu_count() or 1, 16),
+           "ms_per_draw": 1e3 * sgc_s / n_draw, "clusters_mean": float(np.mean(seq_l))}
+    for i in range(max(args.warmup, 3)):
+        stba.stba_set_clusters(ctx, seq[i])
         stba.stba_lm_iteration(ctx, want_info=False)
     torch.cuda.synchronize()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_tot = np.zeros(5)
     sampler = ClockSampler(local)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.start()
     t_wall = time.perf_counter()
-    for i in range(args.steps):
+    w0 = max(args.warmup, 3)
+    for i in range(args.steps):   # nothing in the loop waits for the device
         flush.fill_(float(i))
         ev[i][0].record(stream)
+        stba.stba_set_clusters(ctx, seq[w0 + i])
         stba.stba_lm_iteration(ctx, want_info=False)
         ev[i][1].record(stream)
-        stage_tot += np.array(stba.stba_stage_times(ctx))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
@@ -248,7 +261,32 @@ def main():
         tot_ms = float(t.item())
     lam, F_end, it_end = stba.stba_get_state(ctx)
     value = world * args.steps / (tot_ms / 1e3)
-    stage_ms = stage_tot / args.steps
+
+    # stage times and sizes: the same steps again (their clusterings), reading the stage events after each
+    stage_tot = np.zeros(5)
+    info_tot = {}
+    n_stage = min(args.steps, 50)
+    for i in range(n_stage):
+        flush.fill_(float(i))
+        stba.stba_set_clusters(ctx, seq[w0 + i])
+        stba.stba_lm_iteration(ctx, want_info=False)
+        stage_tot += np.array(stba.stba_stage_times(ctx))
+        for k_, v_ in stba.stba_problem_info(ctx).items():
+            info_tot[k_] = info_tot.get(k_, 0) + v_
+    stage_ms = stage_tot / n_stage
+    info0 = {k_: v_ / n_stage for k_, v_ in info_tot.items()}   # per-step means over the clusterings
+
+    # the same iterations without re-clustering (one fixed assignment), for reference
+    fixed_ms = []
+    for i in range(min(args.steps, 50)):
+        flush.fill_(float(i))
+        a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_ev.record(stream)
+        stba.stba_lm_iteration(ctx, want_info=False)
+        b_ev.record(stream)
+        fixed_ms.append((a_ev, b_ev))
+    torch.cuda.synchronize()
+    fixed_ms = float(np.mean([a.elapsed_time(b) for a, b in fixed_ms]))
 
     # roofline of the dominant stage (stage averages over the timed steps)
     q, n, m = s.q, s.n, s.m
@@ -276,34 +314,40 @@ def main():
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roofline["stage_ms"] = {nm: float(v) for nm, v in zip(names, stage_ms)}
 
-    # end to end through the C ABI with host buffers: parameters in, one iteration, parameters out
+    # end to end through the C ABI with host buffers: parameters and the iteration's clustering in, one
+    # iteration, parameters out
     cams_h = torch.from_numpy(s.cameras.copy()).pin_memory()
     pts_h = torch.from_numpy(s.points.copy()).pin_memory()
     cams_o = torch.empty_like(cams_h).pin_memory()
     pts_o = torch.empty_like(pts_h).pin_memory()
     stba.stba_get_params(ctx, cams_h, pts_h)
-    e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for i in range(e2e_steps):
         stba.stba_set_params(ctx, cams_h, pts_h)
+        stba.stba_set_clusters(ctx, seq[w0 + args.steps + i])
         stba.stba_lm_iteration(ctx, want_info=False)
         stba.stba_get_params(ctx, cams_o, pts_o)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    nbytes = 8 * (cams_h.numel() + pts_h.numel())
+    nbytes_in = 8 * (cams_h.numel() + pts_h.numel()) + 4 * s.m
+    nbytes_out = 8 * (cams_h.numel() + pts_h.numel())
 
     out = {
         "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOADS.get(args.config, args.config), "cameras": m, "points": n, "observations": q,
-                   "clusters": int(info0["l"]),
-                   "virtual_points": int(info0["nv"]), "l2_flush": True, "parallelism": f"replicas{world}"},
+                   "clusters_mean": sgc["clusters_mean"],
+                   "virtual_points_mean": float(info0["nv"]), "l2_flush": True, "parallelism": f"replicas{world}"},
         "obs_per_s": value * q,
         "roofline": roofline,
-        "e2e": {"value": world / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-        "gpu_launches": int(info0["launches_per_iter"]) * args.steps,
+        "e2e": {"value": world / e2e_s, "unit": "iter/s", "h2d_bytes_per_step": nbytes_in,
+                "d2h_bytes_per_step": nbytes_out},
+        "step": "set_clusters (a stochastic-graph-clustering draw) + one LM iteration (Algorithm 1)",
+        "sgc": sgc,
+        "fixed_clusters_ms_per_iter": fixed_ms,
+        "gpu_launches": int(round((info0["launches_per_iter"] + REORDER_LAUNCHES) * args.steps)),
         "clocks": clocks,
         "final": {"rmse_px": float(np.sqrt(F_end / (2 * q))), "lambda": lam, "iterations": it_end},
     }
@@ -327,9 +371,11 @@ def main():
 def compare_full_rcs(s, stba, stream, iters, torch, max_stba_iters=100):
     """Full-RCS LM on the same GPU against STBA, from the same start.  Full RCS runs `iters` iterations as
     (a) one cluster holding every camera (the dense reduced camera system, when it fits: 9 m <= 27000) and
-    (b) block-Jacobi preconditioned CG on the full Schur system (matrix-free).  STBA takes a fresh
-    azimuth-wedge clustering every iteration and runs until its RMSE reaches 1.001 x the better full-RCS
-    final RMSE (or max_stba_iters).  Per-iteration device time, final RMSE and time to the target."""
+    (b) block-Jacobi preconditioned CG on the full Schur system (matrix-free).  STBA takes a new clustering
+    every iteration (Algorithm 1) -- stochastic graph clustering draws (Sec. 4.4, beta = 10, Gamma = 100),
+    and, for comparison, spatial partitions (azimuth wedges with a random phase) -- and runs until its RMSE
+    reaches 1.001 x the better full-RCS final RMSE (or max_stba_iters).  Every timed STBA iteration
+    includes its stba_set_clusters.  Per-iteration device time, final RMSE and time to the target."""
     import numpy as np
 
     import scenes
@@ -339,12 +385,12 @@ def compare_full_rcs(s, stba, stream, iters, torch, max_stba_iters=100):
                                precision=stba.STBA_MIXED, stream=stream, **kw)
         rm, ts, cg = [], [], []
         for t in range(n_it):
-            if seq is not None:
-                stba.stba_set_clusters(ctx, seq[t])
             torch.cuda.synchronize()
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
+            if seq is not None:
+                stba.stba_set_clusters(ctx, seq[t])
             info = stba.stba_lm_iteration(ctx)
             b.record(stream)
             torch.cuda.synchronize()
@@ -365,13 +411,19 @@ def compare_full_rcs(s, stba, stream, iters, torch, max_stba_iters=100):
     res["full_rcs_pcg"] = run(one, None, iters, linear_solver=stba.STBA_SOLVER_PCG_FULL)
     best = min(r["rmse"][-1] for r in res.values())
     target = 1.001 * best
-    seq = scenes.cluster_sequence(s, max_stba_iters, seed=s.meta["seed"] + 1)
-    st = run(s.clusters, seq, max_stba_iters, target=target)
-    out = {"rmse_target": target, "stba_iters_run": len(st["rmse"]), "stba_ms_per_iter": st["ms_per_iter"],
-           "stba_final_rmse": st["rmse"][-1]}
-    hit = [i for i, r in enumerate(st["rmse"]) if r <= target]
-    out["stba_time_to_target_ms"] = st["cum_ms"][hit[0]] if hit else None
-    out["stba_iters_to_target"] = hit[0] + 1 if hit else None
+    out = {"rmse_target": target}
+    g = stba.stba_graph_create(s.m, s.n, s.obs_cam, s.obs_pt)
+    seq_sgc, _ = stba.stba_graph_cluster_batch(g, max_stba_iters, gamma=100, beta=10.0, seed=s.meta["seed"] + 2)
+    g.close()
+    seqs = {"stba_sgc": seq_sgc}
+    if s.meta.get("kind") in ("ring", "hemisphere"):
+        seqs["stba_spatial"] = scenes.cluster_sequence(s, max_stba_iters, seed=s.meta["seed"] + 1)
+    for name, seq in seqs.items():
+        st = run(seq[0], seq, max_stba_iters, target=target)
+        hit = [i for i, r in enumerate(st["rmse"]) if r <= target]
+        out[name] = {"iters_run": len(st["rmse"]), "ms_per_iter": st["ms_per_iter"], "final_rmse": st["rmse"][-1],
+                     "time_to_target_ms": st["cum_ms"][hit[0]] if hit else None,
+                     "iters_to_target": hit[0] + 1 if hit else None}
     for name, r in res.items():
         h = [i for i, x in enumerate(r["rmse"]) if x <= target]
         out[name] = {"iters": len(r["rmse"]), "ms_per_iter": r["ms_per_iter"], "final_rmse": r["rmse"][-1],

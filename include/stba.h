@@ -197,6 +197,38 @@ stba_status stba_cost_noalloc(const double* cameras, int64_t m, const double* po
                               const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int64_t q,
                               double* F_dev, void* cuda_stream);
 
+/* Camera graph and stochastic graph clustering (Sec. 4.4).  These calls run on the host and use no GPU.
+ *
+ * The camera graph joins cameras i and j when they observe a common point; the weight w_ij is the number of
+ * such points.  Stochastic graph clustering starts from single cameras and joins two neighbouring clusters
+ * at a time, drawing the join with probability proportional to exp(beta dQ) (Eq. 16), dQ being the increase
+ * of the modularity Q = 1/(2s) sum over edges e_ij of delta(nu_i, nu_j) (w_ij - k_i k_j / (2s)) (the sum runs
+ * over the edges of the graph, s = sum of the weights, k_i = weight at camera i).  A join is allowed when
+ * the joined cluster has at most gamma cameras; clustering ends when no join is allowed.  The paper uses
+ * beta = 10, gamma = 100.  The result is an assignment [m] with ids 0..l-1 numbered by the smallest camera
+ * of each cluster; the same seed gives the same assignment.  Errors: STBA_ERR_INVALID_ARG (message from
+ * stba_last_error(NULL)). */
+typedef struct stba_graph stba_graph;
+
+/* Builds the camera graph of q observations.  obs_cam, obs_pt [q] are HOST arrays (cameras 0..m-1, points
+ * 0..n-1); a camera may observe a point at most once.  *out is owned by the caller (stba_graph_destroy). */
+stba_status stba_graph_create(int64_t m, int64_t n, const int32_t* obs_cam, const int32_t* obs_pt, int64_t q,
+                              stba_graph** out);
+/* *E = number of edges; with non-NULL HOST arrays of length *E, the edges (i < j, ordered by j then i) and
+ * their weights. */
+stba_status stba_graph_edges(const stba_graph* g, int64_t* E, int32_t* i, int32_t* j, int64_t* w);
+/* One clustering: cluster_assignment [m] (HOST) and *l.  gamma >= 1, beta finite and >= 0. */
+stba_status stba_graph_cluster(const stba_graph* g, int32_t gamma, double beta, uint64_t seed,
+                               int32_t* cluster_assignment, int32_t* l);
+/* count clusterings with seeds seed, seed + 1, ..., drawn in parallel host threads:
+ * cluster_assignments [count][m], l [count] (HOST). */
+stba_status stba_graph_cluster_batch(const stba_graph* g, int32_t gamma, double beta, uint64_t seed, int32_t count,
+                                     int32_t* cluster_assignments, int32_t* l);
+void stba_graph_destroy(stba_graph* g);
+/* The same as stba_graph_cluster_batch on the camera graph of a context (built by stba_create). */
+stba_status stba_cluster_sgc(stba_ctx* ctx, int32_t gamma, double beta, uint64_t seed, int32_t count,
+                             int32_t* cluster_assignments, int32_t* l);
+
 /* Frees every device allocation of the context.  NULL is allowed. */
 void stba_destroy(stba_ctx* ctx);
 

@@ -87,7 +87,13 @@ struct stba_ctx {
   int *key = nullptr, *tile_sum = nullptr;
   long long* counts = nullptr;
   // buffers sized by the cluster layout, kept while the next layout fits
-  GrowBuf g_panel, g_update, g_res, g_diag, g_S, g_b, g_L, g_Dinv, g_Ldiag, g_scale, g_x, g_r;
+  GrowBuf g_panel, g_update, g_res, g_diag, g_S, g_b, g_L, g_Dinv, g_Ldiag, g_scale, g_x, g_r, g_blob;
+  // pinned staging of the per-assignment arrays (two, used in turn; an event marks each one's copy)
+  void* stage_h[2] = {nullptr, nullptr};
+  size_t stage_bytes[2] = {0, 0};
+  cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+  int stage_cur = 0;
+  bool counts_known = true;             // c->nv and c->n_pairs read back since the last assignment
   int64_t n_pairs = 0;
   CholPlan cplan{};
   FactorBuffers fbuf{};
@@ -117,6 +123,7 @@ struct stba_ctx {
 
   // graph / timing
   cudaGraphExec_t graph = nullptr;
+  bool graph_stale = false;             // the cluster layout changed since the graph was captured
   bool capturing = false;
   bool timing = false;
   int launches_per_iter = 0;
@@ -284,6 +291,19 @@ stba_status put(stba_ctx* c, T* dst, const std::vector<T>& h) {
   return STBA_OK;
 }
 
+// The number of virtual points and of camera-pair instances of the current assignment (device counters
+// written by the re-ordering); synchronises the stream the first time after a new assignment.
+stba_status refresh_counts(stba_ctx* c) {
+  if (c->counts_known) return STBA_OK;
+  long long h[2];
+  CK(cudaMemcpyAsync(h, c->counts, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->nv = (int)h[0];
+  c->n_pairs = h[1];
+  c->counts_known = true;
+  return STBA_OK;
+}
+
 // ------------------------------------------------------------------------------------------------------
 // A new cluster assignment.  The host validates it and lays out the clusters (camera lists, the dense
 // blocks of S'_k, the Cholesky step plan: O(m + l + plan) work); the device re-orders the observations
@@ -301,10 +321,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   for (int k = 0; k < l; ++k)
     if (cnt[k] == 0) return fail(c, STBA_ERR_INVALID_ARG, "cluster %d has no camera (ids must be 0..l-1)", k);
 
-  if (c->graph) {
-    cudaGraphExecDestroy(c->graph);
-    c->graph = nullptr;
-  }
+  c->graph_stale = true;   // recaptured by the next iteration (and updated in place when its shape allows)
   c->l = l;
   c->h_clusters = cl;
   // cameras of every cluster, ascending
@@ -392,29 +409,75 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     for (int k = 0; k < l; ++k) c->factor_flops += std::pow((double)c->h_nk[k], 3) / 3.0;
   }
 
-  // cluster arrays and plan on the device
+  // cluster arrays and plan: packed into one pinned staging buffer and copied with one transfer into a
+  // device blob; the arrays are views of the blob
   stba_status s;
-  if ((s = put(c, c->cam_local, cam_local)) != STBA_OK) return s;
-  if ((s = put(c, c->cam_cluster, cl)) != STBA_OK) return s;
-  if ((s = put(c, c->cluster_cams, c->h_cluster_cams)) != STBA_OK) return s;
-  if ((s = put(c, c->cluster_cam_off, c->h_cluster_cam_off)) != STBA_OK) return s;
-  if ((s = put(c, c->cluster_np, c->h_np)) != STBA_OK) return s;
-  if ((s = put(c, c->cluster_n, c->h_nk)) != STBA_OK) return s;
-  if ((s = put(c, c->S_off, c->h_S_off)) != STBA_OK) return s;
-  if ((s = put(c, c->v_off, c->h_v_off)) != STBA_OK) return s;
-  int2 *d_panel, *d_update, *d_res, *d_diag;
-  if ((s = ensure(c, c->g_panel, &d_panel, panel.size())) != STBA_OK) return s;
-  if ((s = ensure(c, c->g_update, &d_update, update.size())) != STBA_OK) return s;
-  if ((s = ensure(c, c->g_res, &d_res, res_items.size())) != STBA_OK) return s;
-  if ((s = ensure(c, c->g_diag, &d_diag, diag_items.size())) != STBA_OK) return s;
-  if ((s = put(c, d_panel, panel)) != STBA_OK) return s;
-  if ((s = put(c, d_update, update)) != STBA_OK) return s;
-  if ((s = put(c, d_res, res_items)) != STBA_OK) return s;
-  if ((s = put(c, d_diag, diag_items)) != STBA_OK) return s;
-  c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
-                      c->h_panel_off.data(),
-                      c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
-                      c->ev_panel.data(), c->ev_update.data()};
+  {
+    size_t bytes = 0;
+    auto seg = [&](size_t n_bytes) {
+      const size_t o = bytes;
+      bytes += (n_bytes + 15) / 16 * 16;
+      return o;
+    };
+    const size_t o_local = seg(4 * (size_t)m), o_cl = seg(4 * (size_t)m), o_ccams = seg(4 * (size_t)m),
+                 o_coff = seg(4 * ((size_t)l + 1)), o_np = seg(4 * (size_t)l), o_nk = seg(4 * (size_t)l),
+                 o_soff = seg(8 * (size_t)l), o_voff = seg(8 * (size_t)l), o_panel = seg(8 * panel.size()),
+                 o_update = seg(8 * update.size()), o_res = seg(8 * res_items.size()),
+                 o_diag = seg(8 * diag_items.size());
+    const int sb = c->stage_cur;
+    c->stage_cur = 1 - sb;
+    if (c->stage_bytes[sb] < bytes) {
+      if (c->stage_h[sb]) {
+        CK(cudaEventSynchronize(c->stage_ev[sb]));
+        cudaFreeHost(c->stage_h[sb]);
+        c->stage_h[sb] = nullptr;
+        c->stage_bytes[sb] = 0;
+      }
+      if (cudaHostAlloc(&c->stage_h[sb], bytes + bytes / 4, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->stage_h[sb] = nullptr;
+        return fail(c, STBA_ERR_OOM, "pinned host allocation failed");
+      }
+      c->stage_bytes[sb] = bytes + bytes / 4;
+    } else {
+      CK(cudaEventSynchronize(c->stage_ev[sb]));   // its previous copy has been consumed
+    }
+    char* h = (char*)c->stage_h[sb];
+    auto pack = [&](size_t o, const void* src, size_t n_bytes) {
+      if (n_bytes) std::memcpy(h + o, src, n_bytes);
+    };
+    pack(o_local, cam_local.data(), 4 * (size_t)m);
+    pack(o_cl, cl.data(), 4 * (size_t)m);
+    pack(o_ccams, c->h_cluster_cams.data(), 4 * (size_t)m);
+    pack(o_coff, c->h_cluster_cam_off.data(), 4 * ((size_t)l + 1));
+    pack(o_np, c->h_np.data(), 4 * (size_t)l);
+    pack(o_nk, c->h_nk.data(), 4 * (size_t)l);
+    pack(o_soff, c->h_S_off.data(), 8 * (size_t)l);
+    pack(o_voff, c->h_v_off.data(), 8 * (size_t)l);
+    pack(o_panel, panel.data(), 8 * panel.size());
+    pack(o_update, update.data(), 8 * update.size());
+    pack(o_res, res_items.data(), 8 * res_items.size());
+    pack(o_diag, diag_items.data(), 8 * diag_items.size());
+    char* d = nullptr;
+    if ((s = ensure(c, c->g_blob, &d, bytes)) != STBA_OK) return s;
+    CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventRecord(c->stage_ev[sb], c->stream));
+    c->cam_local = (int*)(d + o_local);
+    c->cam_cluster = (int*)(d + o_cl);
+    c->cluster_cams = (int*)(d + o_ccams);
+    c->cluster_cam_off = (int*)(d + o_coff);
+    c->cluster_np = (int*)(d + o_np);
+    c->cluster_n = (int*)(d + o_nk);
+    c->S_off = (int64_t*)(d + o_soff);
+    c->v_off = (int64_t*)(d + o_voff);
+    c->reorder.cam_cluster = c->cam_cluster;
+    const int2 *d_panel = (const int2*)(d + o_panel), *d_update = (const int2*)(d + o_update),
+               *d_res = (const int2*)(d + o_res), *d_diag = (const int2*)(d + o_diag);
+    c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
+                        c->h_panel_off.data(),
+                        c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
+                        c->ev_panel.data(), c->ev_update.data()};
+  }
   {
     int least = 0, greatest = 0;
     if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) cudaGetLastError();
@@ -460,11 +523,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     if (carry) std::swap(c->res_cur, c->res_cand);
     c->inv_cur = 1 - c->inv_cur;
     c->have_order = true;
-    long long h_counts[2];
-    CK(cudaMemcpyAsync(h_counts, c->counts, sizeof h_counts, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    c->nv = (int)h_counts[0];
-    c->n_pairs = h_counts[1];
+    c->counts_known = false;   // read back on demand (refresh_counts); nothing here waits for the device
   }
   (void)n;
   (void)q;
@@ -494,7 +553,7 @@ void enqueue_step(stba_ctx* c, bool stages) {
   // stage 0: linearisation and virtual points
   launch_iter_begin<real>(c->st, c->set, s);
   if (c->mixed) launch_params_to_float(P, c->cams_f, c->pts_f, s);
-  cudaMemsetAsync(c->vp_acc, 0, 9 * (size_t)c->nv * rs, s);
+  launch_zero_vp(c->vp_acc, c->counts, (int)rs, s);   // 9 nv reals, nv from the device counter
   cudaMemsetAsync(c->S, 0, (size_t)c->S_total * sizeof(double), s);
   cudaMemsetAsync(c->b, 0, (size_t)c->v_total * sizeof(double), s);
   cudaMemsetAsync(c->vgrad, 0, 9 * (size_t)c->m * rs, s);
@@ -540,7 +599,7 @@ int enqueue_pcg_iteration(stba_ctx* c) {
   record_stage(c, 0);
   launch_iter_begin<real>(c->st, c->set, s);
   if (c->mixed) launch_params_to_float(P, c->cams_f, c->pts_f, s);
-  cudaMemsetAsync(c->vp_acc, 0, 9 * (size_t)c->nv * sizeof(real), s);
+  launch_zero_vp(c->vp_acc, c->counts, (int)sizeof(real), s);
   cudaMemsetAsync(c->t_acc, 0, 3 * (size_t)c->n * sizeof(real), s);
   launch_vp_reduce<real>(P, W, s);
   launch_vp_finalize<real>(P, W, c->st, s);
@@ -603,7 +662,7 @@ stba_status launch_iteration(stba_ctx* c) {
     c->have_stage_times = true;
     return STBA_OK;
   }
-  if (!c->graph) {
+  if (!c->graph || c->graph_stale) {
     // capture on a private stream (the user's stream may be the legacy default stream)
     cudaStream_t user = c->stream;
     c->stream = c->cap_stream;
@@ -618,6 +677,20 @@ stba_status launch_iteration(stba_ctx* c) {
     cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
     c->stream = user;
     if (e != cudaSuccess) return fail(c, STBA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    c->graph_stale = false;
+    if (c->graph) {
+      // same node structure (same number of tile steps, ...): update the executable graph in place
+      cudaGraphExecUpdateResultInfo ri;
+      if (cudaGraphExecUpdate(c->graph, g, &ri) == cudaSuccess) {
+        cudaGraphDestroy(g);
+        CK(cudaGraphLaunch(c->graph, c->stream));
+        c->have_stage_times = true;
+        return STBA_OK;
+      }
+      cudaGetLastError();
+      cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+    }
     e = cudaGraphInstantiate(&c->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -662,7 +735,9 @@ void free_tape(stba_ctx* c) {
 
 template <typename real>
 void enqueue_adjoint_step(stba_ctx* c, double lam, const AdjointBuffers& A) {
-  // recompute the forward step at x_t with the recorded damping, then its adjoint
+  // recompute the forward step at x_t with the recorded damping, then its adjoint (whose launch sizes need
+  // the number of virtual points on the host)
+  refresh_counts(c);
   launch_set_lambda(c->st, lam, c->stream);
   launch_iter_begin<real>(c->st, c->set, c->stream);
   const DevProblem P = dev_problem(c);
@@ -723,6 +798,98 @@ const char* stba_status_string(stba_status s) {
   return "unknown status";
 }
 
+// ------------------------------------------------------------------------------------------------------
+// Camera graph and stochastic graph clustering (host only)
+struct stba_graph {
+  stba::CameraGraph g;
+  int64_t m = 0;
+};
+
+stba_status stba_graph_create(int64_t m, int64_t n, const int32_t* obs_cam, const int32_t* obs_pt, int64_t q,
+                              stba_graph** out) {
+  g_create_error.clear();
+  auto bad = [&](const char* msg) {
+    g_create_error = msg;
+    return STBA_ERR_INVALID_ARG;
+  };
+  if (!out) return bad("null output pointer");
+  *out = nullptr;
+  if (!obs_cam || !obs_pt) return bad("null array argument");
+  if (m < 1 || n < 1 || q < 0 || m > INT32_MAX / 9 || n > INT32_MAX || q > INT32_MAX - 64) return bad("sizes out of range");
+  std::vector<int> pt_off(n + 1, 0);
+  for (int64_t o = 0; o < q; ++o) {
+    if (obs_cam[o] < 0 || obs_cam[o] >= m || obs_pt[o] < 0 || obs_pt[o] >= n) return bad("observation index out of range");
+    pt_off[obs_pt[o] + 1]++;
+  }
+  for (int64_t i = 0; i < n; ++i) pt_off[i + 1] += pt_off[i];
+  std::vector<int> base_cam(q);
+  {
+    std::vector<int> f(pt_off.begin(), pt_off.end() - 1);
+    for (int64_t o = 0; o < q; ++o) base_cam[f[obs_pt[o]]++] = obs_cam[o];
+    for (int64_t i = 0; i < n; ++i) {
+      std::sort(base_cam.begin() + pt_off[i], base_cam.begin() + pt_off[i + 1]);
+      for (int o = pt_off[i] + 1; o < pt_off[i + 1]; ++o)
+        if (base_cam[o] == base_cam[o - 1]) return bad("a camera observes a point twice");
+    }
+  }
+  stba_graph* g = new stba_graph();
+  g->m = m;
+  build_camera_graph((int)m, (int)n, pt_off, base_cam, g->g, false);
+  *out = g;
+  return STBA_OK;
+}
+
+stba_status stba_graph_edges(const stba_graph* g, int64_t* E, int32_t* i, int32_t* j, int64_t* w) {
+  if (!g || !E) return STBA_ERR_INVALID_ARG;
+  *E = (int64_t)g->g.edge_y.size();
+  for (int64_t x = 0; x < g->m; ++x)
+    for (int e = g->g.edge_off[x]; e < g->g.edge_off[x + 1]; ++e) {
+      if (i) i[e] = g->g.edge_y[e];
+      if (j) j[e] = (int32_t)x;
+      if (w) w[e] = g->g.edge_w[e];
+    }
+  return STBA_OK;
+}
+
+namespace {
+stba_status sgc_args(int32_t gamma, double beta) {
+  if (gamma < 1 || !(beta >= 0.0) || !std::isfinite(beta)) {
+    g_create_error = "gamma must be >= 1 and beta finite and >= 0";
+    return STBA_ERR_INVALID_ARG;
+  }
+  return STBA_OK;
+}
+}  // namespace
+
+stba_status stba_graph_cluster(const stba_graph* g, int32_t gamma, double beta, uint64_t seed,
+                               int32_t* cluster_assignment, int32_t* l) {
+  if (!g || !cluster_assignment || !l) return STBA_ERR_INVALID_ARG;
+  stba_status s = sgc_args(gamma, beta);
+  if (s != STBA_OK) return s;
+  sgc_sample(g->g, (int)g->m, gamma, beta, seed, cluster_assignment, l);
+  return STBA_OK;
+}
+
+stba_status stba_graph_cluster_batch(const stba_graph* g, int32_t gamma, double beta, uint64_t seed, int32_t count,
+                                     int32_t* cluster_assignments, int32_t* l) {
+  if (!g || !cluster_assignments || !l || count < 0) return STBA_ERR_INVALID_ARG;
+  stba_status s = sgc_args(gamma, beta);
+  if (s != STBA_OK) return s;
+  sgc_sample_batch(g->g, (int)g->m, gamma, beta, seed, count, cluster_assignments, l);
+  return STBA_OK;
+}
+
+void stba_graph_destroy(stba_graph* g) { delete g; }
+
+stba_status stba_cluster_sgc(stba_ctx* c, int32_t gamma, double beta, uint64_t seed, int32_t count,
+                             int32_t* cluster_assignments, int32_t* l) {
+  if (!c || !cluster_assignments || !l || count < 0) return STBA_ERR_INVALID_ARG;
+  if (gamma < 1 || !(beta >= 0.0) || !std::isfinite(beta))
+    return fail(c, STBA_ERR_INVALID_ARG, "gamma must be >= 1 and beta finite and >= 0");
+  sgc_sample_batch(c->cgraph, (int)c->m, gamma, beta, seed, count, cluster_assignments, l);
+  return STBA_OK;
+}
+
 const char* stba_last_error(stba_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 void stba_destroy(stba_ctx* c) {
@@ -733,8 +900,12 @@ void stba_destroy(stba_ctx* c) {
   free_list(c, c->allocs);
   free_list(c, c->tape_allocs);
   for (GrowBuf* g : {&c->g_panel, &c->g_update, &c->g_res, &c->g_diag, &c->g_S, &c->g_b, &c->g_L, &c->g_Dinv,
-                     &c->g_Ldiag, &c->g_scale, &c->g_x, &c->g_r})
+                     &c->g_Ldiag, &c->g_scale, &c->g_x, &c->g_r, &c->g_blob})
     if (g->ptr) cudaFree(g->ptr);
+  for (int i = 0; i < 2; ++i) {
+    if (c->stage_h[i]) cudaFreeHost(c->stage_h[i]);
+    if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
+  }
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -852,7 +1023,9 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(c, STBA_ERR_CUDA, "cudaEventCreate failed"));
   if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->stage_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->stage_ev[1], cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(c, STBA_ERR_CUDA, "cannot create the factorisation stream or its events"));
   if ((s = dalloc(c, &c->cams, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
   if ((s = dalloc(c, &c->pts, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
@@ -911,7 +1084,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   {
     std::vector<int> base_cam(q);
     for (int64_t o = 0; o < q; ++o) base_cam[o] = c->in_cam[c->base_order[o]];
-    build_camera_graph((int)m, (int)n, c->h_pt_off, base_cam, c->cgraph);
+    build_camera_graph((int)m, (int)n, c->h_pt_off, base_cam, c->cgraph, true);
     const CameraGraph& g = c->cgraph;
     if ((int64_t)g.pairs.size() > INT32_MAX - PAIR_CHUNK)
       return bail(fail(c, STBA_ERR_INVALID_ARG, "more than 2^31 co-visible observation pairs"));
@@ -995,27 +1168,21 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
                             &c->key};
     for (int* const* pp : ints_q)
       if ((s = dalloc(c, const_cast<int**>(pp), Q, false)) != STBA_OK) return bail(s);
-    int* d_start;
-    if ((s = dalloc(c, &d_start, Q + 1, false)) != STBA_OK) return bail(s);
+    int* d_start;   // [q+1] virtual-point starts, then [q+1] the camera-list scan
+    if ((s = dalloc(c, &d_start, 2 * (Q + 1), false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->vp_off, Q + 1, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->pt_vp_off, (size_t)n + 1, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->obs_uv, 2 * Q, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &d_cam_obs, Q, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &d_slots, 32 * (size_t)nwarps, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->tile_sum, Q / 2048 + 2, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->counts, 2, false)) != STBA_OK) return bail(s);
-    // cluster arrays at their largest size (l <= m)
-    int* const* ints_m[] = {&c->cam_local, &c->cam_cluster, &c->cluster_cams, &c->cluster_np, &c->cluster_n,
-                            &c->fail_flags};
-    for (int* const* pp : ints_m)
-      if ((s = dalloc(c, const_cast<int**>(pp), (size_t)m, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->cluster_cam_off, (size_t)m + 1, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->S_off, (size_t)m, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->v_off, (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->counts, 4, false)) != STBA_OK) return bail(s);
+    // failure flags at their largest size (l <= m); the other cluster arrays live in the assignment blob
+    if ((s = dalloc(c, &c->fail_flags, (size_t)m, false)) != STBA_OK) return bail(s);
     // per-iteration scratch (virtual-point arrays at their largest size, nv <= q)
     const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
     char *vpa, *vpi, *pti, *vg, *ta, *gb;
-    if ((s = dalloc(c, &vpa, 9 * Q * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &vpa, 9 * Q * rs + 16, false)) != STBA_OK) return bail(s);   // zeroed in 16-byte pieces
     if ((s = dalloc(c, &vpi, 9 * Q * rs, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &pti, 9 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &vg, 9 * (size_t)m * rs, false)) != STBA_OK) return bail(s);
@@ -1032,7 +1199,6 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     A.base_cam = d_base_cam;
     A.base_src = d_base_src;
     A.base_uv = d_base_uv;
-    A.cam_cluster = c->cam_cluster;
     A.start = d_start;
     A.obs_base = c->obs_base;
     A.obs_cam = c->obs_cam;
@@ -1049,6 +1215,10 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     A.cam_warp_off = d_cam_warp_off;
     A.cam_obs = d_cam_obs;
     A.slots = d_slots;
+    {   // the padding slots of the camera pass never change
+      std::vector<int> pad(32 * (size_t)nwarps, -1);
+      if ((s = put(c, d_slots, pad)) != STBA_OK) return bail(s);
+    }
     c->clist = CamLists{d_cam_off, d_cam_obs};
     c->cslots = CamSlots{d_slots, d_warp_cam, nwarps};
   }
@@ -1064,7 +1234,6 @@ stba_status stba_set_clusters(stba_ctx* c, const int32_t* cluster_assignment) {
   std::vector<int> h(c->m);
   stba_status s;
   if ((s = copy_in(c, h.data(), cluster_assignment, (size_t)c->m * 4)) != STBA_OK) return s;
-  CK(cudaStreamSynchronize(c->stream));
   // the stored residuals follow the observation order; set_clusters_host carries them over
   return set_clusters_host(c, h);
 }
@@ -1264,6 +1433,8 @@ stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_d
 
 stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {
   if (!c || !out || n < 0) return STBA_ERR_INVALID_ARG;
+  stba_status st = refresh_counts(c);
+  if (st != STBA_OK) return st;
   int maxn = 0;
   double s_elems = 0;
   for (int v : c->h_nk) {
@@ -1272,7 +1443,7 @@ stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {
   }
   size_t grown = 0;
   for (const GrowBuf* g : {&c->g_panel, &c->g_update, &c->g_res, &c->g_diag, &c->g_S, &c->g_b, &c->g_L, &c->g_Dinv,
-                           &c->g_Ldiag, &c->g_scale, &c->g_x, &c->g_r})
+                           &c->g_Ldiag, &c->g_scale, &c->g_x, &c->g_r, &c->g_blob})
     grown += g->bytes;
   const int64_t vals[12] = {c->m, c->n, c->q, c->l, c->nv, maxn, (int64_t)(c->bytes_base + c->bytes_cl + grown),
                             c->build_items, c->launches_per_iter, c->n_pairs, (int64_t)c->factor_flops,

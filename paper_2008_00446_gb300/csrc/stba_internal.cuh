@@ -117,7 +117,13 @@ struct CameraGraph {
   std::vector<int2> pairs;         // [P]
 };
 void build_camera_graph(int m, int n, const std::vector<int>& pt_off, const std::vector<int>& base_cam,
-                        CameraGraph& g);
+                        CameraGraph& g, bool with_pairs);
+// Stochastic graph clustering (Sec. 4.4, Eq. 16) of the camera graph: labels [m] (0..l-1, numbered by
+// smallest camera), *nclusters = l.  The batch form draws count clusterings (seeds seed, seed+1, ...) in
+// parallel host threads into labels [count][m].
+void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t seed, int* labels, int* nclusters);
+void sgc_sample_batch(const CameraGraph& g, int m, int gamma, double beta, uint64_t seed, int count, int* labels,
+                      int* nclusters);
 
 // Re-ordering for a new cluster assignment (stba_order.cu).  Base = the (point, camera) order of create.
 struct ReorderArgs {
@@ -144,11 +150,14 @@ struct ReorderArgs {
   int* cam_obs;             // [q] new positions, single-observation virtual points first
   int* slots;               // [32 * warps] the same padded to whole warps (-1)
 };
-// key: [q] scratch; tile_sum: [q / 2048 + 1] scratch; counts: [2] -> number of virtual points, number of
-// camera-pair instances.  With res_old, the residuals are carried over into res_new in the new order.
+// key: [q] scratch; tile_sum: [q / 2048 + 1] scratch; A.start: [2 (q + 1)]; counts: [3] -> number of virtual
+// points, number of camera-pair instances, number of single-observation virtual points.  With res_old, the residuals are carried over into res_new in the new order.
 template <typename real>
 void launch_reorder(const ReorderArgs& A, int* key, int* tile_sum, long long* counts, const real* res_old,
                     real* res_new, cudaStream_t stream);
+
+// zeroes the virtual-point accumulators (9 nv reals of real_bytes each; nv = counts[0] on the device)
+void launch_zero_vp(void* vp_acc, const long long* counts, int real_bytes, cudaStream_t stream);
 
 constexpr int RED_BLOCKS = 456;    // 3 x 152 SMs: fixed grid of the deterministic reductions
 constexpr int RED_THREADS = 256;

@@ -167,47 +167,75 @@ __global__ void __launch_bounds__(256) k_vp_close(ReorderArgs A, long long* __re
                                                   (unsigned long long)pairs);
 }
 
-// one warp per camera: its observations (new positions), those of single-observation virtual points first,
-// each group in base order, into the plain list and the warp-padded slots of the camera pass
-__global__ void __launch_bounds__(256) k_cam_lists(ReorderArgs A) {
-  const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (j >= A.m) return;
+// Camera lists: the observations of every camera (new positions), those of single-observation virtual
+// points first, each group in base order -- a stable partition of every camera's run of cam_base.  An
+// observation is alone in its virtual point when it starts one and the next observation starts another.
+__global__ void k_cam_flag(ReorderArgs A, int* __restrict__ flag) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.q) return;
+  const int o = A.inv_new[A.cam_base[e]];
+  flag[e] = (A.start[o] == 1 && (o + 1 == A.q || A.start[o + 1] == 1)) ? 1 : 0;
+}
+
+// excl[e] = number of flags before e (tile offsets from k_scan_partials); excl[q] = total
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_excl(int q, const int* __restrict__ flag,
+                                                            const int* __restrict__ tile_off,
+                                                            const long long* __restrict__ total,
+                                                            int* __restrict__ excl) {
+  __shared__ int ws[SCAN_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+  int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    v[t] = base + t < q ? flag[base + t] : 0;
+    s += v[t];
+  }
+  int x = s;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(FULL_MASK, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  int woff = 0;
+  for (int u = 0; u < w; ++u) woff += ws[u];
+  int run = tile_off[blockIdx.x] + woff + x - s;
+#pragma unroll
+  for (int t = 0; t < SCAN_ITEMS; ++t) {
+    if (base + t >= q) break;
+    excl[base + t] = run;
+    run += v[t];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) excl[q] = (int)total[0];
+}
+
+__global__ void k_cam_place(ReorderArgs A, const int* __restrict__ flag, const int* __restrict__ excl) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= A.q) return;
+  const int j = A.base_cam[A.cam_base[e]];
   const int b = A.cam_off[j], cnt = A.cam_off[j + 1] - b;
-  const int sbase = 32 * A.cam_warp_off[j];
-  // an observation is alone in its virtual point when it starts one and the next observation starts another
-  int nsingle = 0;
-  for (int c0 = 0; c0 < cnt; c0 += 32) {
-    bool single = false;
-    if (c0 + lane < cnt) {
-      const int o = A.inv_new[A.cam_base[b + c0 + lane]];
-      single = A.start[o] == 1 && (o + 1 == A.q || A.start[o + 1] == 1);
-    }
-    nsingle += __popc(__ballot_sync(FULL_MASK, single));
-  }
-  int ns = 0, nm = 0;
-  for (int c0 = 0; c0 < cnt; c0 += 32) {
-    int o = -1;
-    bool single = false;
-    if (c0 + lane < cnt) {
-      o = A.inv_new[A.cam_base[b + c0 + lane]];
-      single = A.start[o] == 1 && (o + 1 == A.q || A.start[o + 1] == 1);
-    }
-    const unsigned ms = __ballot_sync(FULL_MASK, single && o >= 0);
-    const unsigned mm = __ballot_sync(FULL_MASK, !single && o >= 0);
-    const unsigned below = (1u << lane) - 1u;
-    if (o >= 0) {
-      const int idx = single ? ns + __popc(ms & below) : nsingle + nm + __popc(mm & below);
-      A.cam_obs[b + idx] = o;
-      A.slots[sbase + idx] = o;
-    }
-    ns += __popc(ms);
-    nm += __popc(mm);
-  }
-  const int nslots = 32 * (A.cam_warp_off[j + 1] - A.cam_warp_off[j]);
-  for (int e = cnt + lane; e < nslots; e += 32) A.slots[sbase + e] = -1;
+  const int before = excl[e] - excl[b];               // singles of camera j before e
+  const int nsingle = excl[b + cnt] - excl[b];
+  const int idx = flag[e] ? before : nsingle + (e - b - before);
+  const int o = A.inv_new[A.cam_base[e]];
+  A.cam_obs[b + idx] = o;
+  A.slots[32 * A.cam_warp_off[j] + idx] = o;
+}
+
+// zeroes the 9 nv accumulators of the virtual points, nv read from the device counter
+__global__ void __launch_bounds__(256) k_zero_vp(float4* __restrict__ p, const long long* __restrict__ counts,
+                                                 int real_bytes) {
+  const long long n16 = (9 * counts[0] * real_bytes + 15) / 16;   // the buffer holds 9 q reals, 16-byte padded
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16; i += (long long)gridDim.x * blockDim.x)
+    p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 }  // namespace
+
+void launch_zero_vp(void* vp_acc, const long long* counts, int real_bytes, cudaStream_t stream) {
+  k_zero_vp<<<2 * RED_BLOCKS, 256, 0, stream>>>(reinterpret_cast<float4*>(vp_acc), counts, real_bytes);
+}
 
 template <typename real>
 void launch_reorder(const ReorderArgs& A, int* key, int* tile_sum, long long* counts, const real* res_old,
@@ -217,11 +245,18 @@ void launch_reorder(const ReorderArgs& A, int* key, int* tile_sum, long long* co
   k_reorder<real><<<g, 256, 0, stream>>>(A, key, res_old, res_new);
   const int ntiles = (A.q + SCAN_TILE - 1) / SCAN_TILE;
   k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(A.q, A.start, tile_sum);
-  cudaMemsetAsync(counts, 0, 2 * sizeof(long long), stream);
+  cudaMemsetAsync(counts, 0, 3 * sizeof(long long), stream);
   k_scan_partials<<<1, 1024, 0, stream>>>(ntiles, tile_sum, counts);
   k_scan_apply<<<ntiles, SCAN_THREADS, 0, stream>>>(A, tile_sum);
   k_vp_close<<<RED_BLOCKS, 256, 0, stream>>>(A, counts);
-  k_cam_lists<<<(A.m + 7) / 8, 256, 0, stream>>>(A);
+  // camera lists: flags, their exclusive scan (reusing the tile scan), placement
+  int* flag = key;                 // the keys are no longer needed
+  int* excl = A.start + A.q + 1;   // second half of the start buffer
+  k_cam_flag<<<g, 256, 0, stream>>>(A, flag);
+  k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(A.q, flag, tile_sum);
+  k_scan_partials<<<1, 1024, 0, stream>>>(ntiles, tile_sum, counts + 2);
+  k_scan_excl<<<ntiles, SCAN_THREADS, 0, stream>>>(A.q, flag, tile_sum, counts + 2, excl);
+  k_cam_place<<<g, 256, 0, stream>>>(A, flag, excl);
 }
 
 template void launch_reorder<float>(const ReorderArgs&, int*, int*, long long*, const float*, float*, cudaStream_t);

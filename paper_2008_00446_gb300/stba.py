@@ -25,7 +25,8 @@ EXPORTS = ["stba_default_options", "stba_create", "stba_set_clusters", "stba_lm_
            "stba_cost", "stba_get_params", "stba_set_params", "stba_get_state", "stba_set_state",
            "stba_last_step", "stba_problem_info", "stba_get_cluster_system", "stba_set_timing",
            "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error", "stba_cost_noalloc",
-           "stba_record", "stba_adjoint"]
+           "stba_record", "stba_adjoint", "stba_graph_create", "stba_graph_edges", "stba_graph_cluster",
+           "stba_graph_cluster_batch", "stba_graph_destroy", "stba_cluster_sgc"]
 
 
 class StbaOptions(ctypes.Structure):
@@ -95,6 +96,12 @@ def load(build_if_missing: bool = True):
         "stba_cost_noalloc": (I32, [P, I64, P, I64, P, P, P, I64, P, P]),
         "stba_record": (I32, [P, I32]),
         "stba_adjoint": (I32, [P, P, P, P, P, P]),
+        "stba_graph_create": (I32, [I64, I64, P, P, I64, ctypes.POINTER(P)]),
+        "stba_graph_edges": (I32, [P, ctypes.POINTER(I64), P, P, P]),
+        "stba_graph_cluster": (I32, [P, I32, D, ctypes.c_uint64, P, ctypes.POINTER(I32)]),
+        "stba_graph_cluster_batch": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
+        "stba_graph_destroy": (None, [P]),
+        "stba_cluster_sgc": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -395,3 +402,78 @@ def stba_differentiable(cameras0, points0, obs_uv, obs_cam, obs_pt, cluster_seq,
 
 
 _STBA_FN = None
+
+
+# ----------------------------------------------------------------------------------------------------------
+# camera graph and stochastic graph clustering (host only)
+# ----------------------------------------------------------------------------------------------------------
+class CameraGraph:
+    """Owns one stba_graph* (stba_graph_create)."""
+
+    def __init__(self, handle, m):
+        self.handle = handle
+        self.m = m
+
+    def close(self):
+        if self.handle:
+            load().stba_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _graph_check(status):
+    if status != 0:
+        raise StbaError(status, load().stba_last_error(None).decode())
+
+
+def stba_graph_create(m, n, obs_cam, obs_pt) -> CameraGraph:
+    c = np.ascontiguousarray(obs_cam, dtype=np.int32)
+    p = np.ascontiguousarray(obs_pt, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _graph_check(load().stba_graph_create(int(m), int(n), ctypes.c_void_p(c.ctypes.data),
+                                          ctypes.c_void_p(p.ctypes.data), len(c), ctypes.byref(h)))
+    return CameraGraph(h, int(m))
+
+
+def stba_graph_edges(g: CameraGraph):
+    """(i, j, w) arrays of the edges, i < j."""
+    E = ctypes.c_int64()
+    _graph_check(load().stba_graph_edges(g.handle, ctypes.byref(E), None, None, None))
+    i = np.empty(E.value, np.int32)
+    j = np.empty(E.value, np.int32)
+    w = np.empty(E.value, np.int64)
+    _graph_check(load().stba_graph_edges(g.handle, ctypes.byref(E), ctypes.c_void_p(i.ctypes.data),
+                                         ctypes.c_void_p(j.ctypes.data), ctypes.c_void_p(w.ctypes.data)))
+    return i, j, w
+
+
+def stba_graph_cluster(g: CameraGraph, gamma=100, beta=10.0, seed=0):
+    """(assignment [m] int32, number of clusters)."""
+    out = np.empty(g.m, np.int32)
+    l = ctypes.c_int32()
+    _graph_check(load().stba_graph_cluster(g.handle, int(gamma), float(beta), int(seed),
+                                           ctypes.c_void_p(out.ctypes.data), ctypes.byref(l)))
+    return out, l.value
+
+
+def stba_graph_cluster_batch(g: CameraGraph, count, gamma=100, beta=10.0, seed=0):
+    """(assignments [count][m] int32, cluster counts [count])."""
+    out = np.empty((int(count), g.m), np.int32)
+    l = np.empty(int(count), np.int32)
+    _graph_check(load().stba_graph_cluster_batch(g.handle, int(gamma), float(beta), int(seed), int(count),
+                                                 ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(l.ctypes.data)))
+    return out, l
+
+
+def stba_cluster_sgc(ctx: Context, count=1, gamma=100, beta=10.0, seed=0):
+    """count clusterings of the context's camera graph: (assignments [count][m], cluster counts [count])."""
+    out = np.empty((int(count), ctx.m), np.int32)
+    l = np.empty(int(count), np.int32)
+    ctx._check(load().stba_cluster_sgc(ctx.handle, int(gamma), float(beta), int(seed), int(count),
+                                       ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(l.ctypes.data)))
+    return out, l
