@@ -133,6 +133,28 @@ def test_ring_cluster_sequence_with_set_clusters(ring):
     assert rel(cams, c) < 1e-8 and rel(pts, p) < 1e-8
 
 
+def test_ring_sgc_draws_with_set_clusters(ring):
+    """Per-iteration stochastic-graph-clustering draws (Gamma = 8, so several clusters of uneven size) applied
+    with stba_set_clusters: the device re-ordering and the carried-over residuals give the oracle's
+    iterations; the context's camera graph gives the same draws as a standalone graph."""
+    s = ring
+    g = stba.stba_graph_create(s.m, s.n, s.obs_cam, s.obs_pt)
+    seq, ls = stba.stba_graph_cluster_batch(g, 6, gamma=8, beta=10.0, seed=77)
+    assert ls.min() >= 4
+    c, p, lam, F, hist = run_oracle(s, seq, 6)
+    ctx = make_ctx(s, seq[0], precision=stba.STBA_FP64)
+    seq2, _ = stba.stba_cluster_sgc(ctx, count=6, gamma=8, beta=10.0, seed=77)
+    assert np.array_equal(seq, seq2)
+    for t, rec in enumerate(hist):
+        stba.stba_set_clusters(ctx, seq[t])
+        info = stba.stba_lm_iteration(ctx)
+        assert stba.stba_problem_info(ctx)["l"] == ls[t]
+        assert info["accepted"] == rec["accepted"]
+        assert abs(info["F_after"] - rec["F_after"]) <= 1e-8 * rec["F_after"], t
+    cams, pts = stba.stba_get_params(ctx)
+    assert rel(cams, c) < 1e-8 and rel(pts, p) < 1e-8
+
+
 def test_ring_mixed_precision(ring):
     s = ring
     c, p, lam, F, hist = run_oracle(s, s.clusters, 10)
