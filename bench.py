@@ -26,7 +26,7 @@ sys.path.insert(0, ROOT)
 METRIC = "STBA LM iter/s and obs/s vs full-RCS LM on 1 GB300 at equal final RMSE"
 CONFIG = "c1_internet"
 SGC_GAMMA, SGC_BETA = 100, 10.0
-REORDER_LAUNCHES = 11  # kernels of one stba_set_clusters (device re-ordering)
+REORDER_LAUNCHES = 16  # kernels of one stba_set_clusters (device re-ordering, listing of the pair chunks)
 WORKLOADS = {
     "c1_internet": ("c1_internet: 1000 cameras (hemisphere r=20), 200k points (10^3 box), Zipf(2) tracks on [2,50] "
                     "over nearby viewpoints, 10 clusters of 100 cameras, mixed precision"),

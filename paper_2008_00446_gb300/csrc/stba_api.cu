@@ -519,6 +519,8 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     else
       launch_reorder<double>(A, c->key, c->tile_sum, c->counts, carry ? (const double*)c->res_cur : nullptr,
                              (double*)c->res_cand, c->stream);
+    if (!c->use_pcg && c->pchunks.nchunks > 0)
+      launch_list_chunks(c->pchunks, c->cam_cluster, c->counts + 3, c->stream);
     CK(cudaGetLastError());
     if (carry) std::swap(c->res_cur, c->res_cand);
     c->inv_cur = 1 - c->inv_cur;
@@ -1096,9 +1098,15 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
             chunks.push_back(make_int4(x, g.edge_y[e], (int)p0, (int)std::min<int64_t>(PAIR_CHUNK, g.pair_off[e + 1] - p0)));
       int4* d_chunks = nullptr;
       int2* d_pairs = nullptr;
+      int *d_active, *d_flag, *d_excl, *d_tiles;
+      const size_t nc = chunks.size();
       if ((s = upload(c, &d_chunks, chunks, false)) != STBA_OK) return bail(s);
       if ((s = upload(c, &d_pairs, g.pairs, false)) != STBA_OK) return bail(s);
-      c->pchunks = PairChunks{d_chunks, d_pairs, (int)chunks.size()};
+      if ((s = dalloc(c, &d_active, nc, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_flag, nc + 1, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_excl, nc + 1, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_tiles, nc / 2048 + 2, false)) != STBA_OK) return bail(s);
+      c->pchunks = PairChunks{d_chunks, d_pairs, (int)nc, d_active, nullptr, d_flag, d_excl, d_tiles};
     }
   }
   // observation data in the (point, camera) base order, the camera lists, and every buffer whose size does
@@ -1176,7 +1184,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = dalloc(c, &d_cam_obs, Q, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &d_slots, 32 * (size_t)nwarps, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->tile_sum, Q / 2048 + 2, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->counts, 4, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->counts, 4, false)) != STBA_OK) return bail(s);   // nv, pairs, singles, active chunks
     // failure flags at their largest size (l <= m); the other cluster arrays live in the assignment blob
     if ((s = dalloc(c, &c->fail_flags, (size_t)m, false)) != STBA_OK) return bail(s);
     // per-iteration scratch (virtual-point arrays at their largest size, nv <= q)
@@ -1219,6 +1227,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       std::vector<int> pad(32 * (size_t)nwarps, -1);
       if ((s = put(c, d_slots, pad)) != STBA_OK) return bail(s);
     }
+    c->pchunks.nactive = c->counts + 3;
     c->clist = CamLists{d_cam_off, d_cam_obs};
     c->cslots = CamSlots{d_slots, d_warp_cam, nwarps};
   }

@@ -103,7 +103,14 @@ struct PairChunks {   // observation pairs of the camera graph, by edge, cut int
   const int4* chunks;       // (camera x, camera y < x, first pair, number of pairs <= PAIR_CHUNK)
   const int2* pairs;        // (base position of the observation by x, base position of the one by y)
   int nchunks;
+  const int* active;        // [nchunks] the chunks whose two cameras share a cluster (set per assignment)
+  const long long* nactive; // device count of them
+  int* flag;                // [nchunks + 1] scratch of the listing
+  int* excl;                // [nchunks + 1]
+  int* tile_sum;            // [nchunks / 2048 + 2]
 };
+// lists the chunks inside clusters for the current assignment (cam_cluster on the device)
+void launch_list_chunks(const PairChunks& B, const int* cam_cluster, long long* nactive, cudaStream_t stream);
 constexpr int PAIR_CHUNK = 64;
 
 // Camera graph (stba_graph.cu): edges (x, y), y < x, grouped by x with y ascending; weight = number of

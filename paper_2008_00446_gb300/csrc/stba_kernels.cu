@@ -383,64 +383,67 @@ __global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real>
 // one cluster of G_x^T G_y (Eq. 10, 13).  The observation pairs of the camera graph are listed once, at
 // create, by edge (x, y) and cut into chunks of at most PAIR_CHUNK; under a cluster assignment an edge
 // contributes exactly when both cameras are in one cluster (its two observations of a point are then in
-// one virtual point), and a chunk adds to one block only.  One warp per chunk: it stages the G rows of CH
-// pairs at a time in shared memory (one row per lane, all loads in flight), its 27 lanes accumulate the
-// 9x9 block in registers (row r, columns 3cg .. 3cg+2) and add it once into the FP64 S'_k.
+// one virtual point), and a chunk adds to one block only.  The re-ordering of an assignment lists the
+// chunks whose edge lies inside a cluster; a fixed grid of warps walks that list, one chunk per warp at a
+// time: it stages the G rows of CH pairs at a time in shared memory (one row per lane, all loads in
+// flight), its 27 lanes accumulate the 9x9 block in registers (row r, columns 3cg .. 3cg+2) and add it
+// once into the FP64 S'_k.
 template <typename real>
 __global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, PairChunks B,
                                                     const real* __restrict__ Gbuf) {
   constexpr int CH = 64 / (int)sizeof(real);
   __shared__ __align__(16) real Gs[8][CH][2][GSTRIDE];
-  const int wib = threadIdx.x >> 5;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= B.nchunks) return;
-  const int4 ch = B.chunks[warp];
-  const int k = P.cam_cluster[ch.x];
-  if (P.cam_cluster[ch.y] != k) return;   // uniform per warp: the edge is cut by the clustering
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long nactive = *B.nactive;
   const int r = lane / 3, cg = lane - (lane / 3) * 3;
   const bool act = lane < 27;
-  real acc0 = 0, acc1 = 0, acc2 = 0;
   const int j = lane % CH, side = lane / CH;
-  for (int c0 = 0; c0 < ch.w; c0 += CH) {
-    const int cn = min(CH, ch.w - c0);
-    if (side < 2 && j < cn) {
-      const int2 pr = B.pairs[ch.z + c0 + j];
-      const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
-      real* dst = &Gs[wib][j][side][0];
-      if constexpr (sizeof(real) == 4) {
+  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < nactive;
+       w += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int4 ch = B.chunks[B.active[w]];
+    const int k = P.cam_cluster[ch.x];
+    real acc0 = 0, acc1 = 0, acc2 = 0;
+    for (int c0 = 0; c0 < ch.w; c0 += CH) {
+      const int cn = min(CH, ch.w - c0);
+      if (side < 2 && j < cn) {
+        const int2 pr = B.pairs[ch.z + c0 + j];
+        const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
+        real* dst = &Gs[wib][j][side][0];
+        if constexpr (sizeof(real) == 4) {
 #pragma unroll
-        for (int q = 0; q < GSTRIDE / 4; ++q)
-          reinterpret_cast<float4*>(dst)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
-      } else {
+          for (int q = 0; q < GSTRIDE / 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
+        } else {
 #pragma unroll
-        for (int q = 0; q < GSTRIDE / 2; ++q)
-          reinterpret_cast<double2*>(dst)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
-      }
-    }
-    __syncwarp();
-    if (act) {
-      for (int jj = 0; jj < cn; ++jj) {
-        real a[3], b0[3], b1[3], b2[3];
-        load_gcol_s(&Gs[wib][jj][0][4 * r], a);
-        load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg)], b0);
-        load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 4], b1);
-        load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 8], b2);
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          acc0 += a[s] * b0[s];
-          acc1 += a[s] * b1[s];
-          acc2 += a[s] * b2[s];
+          for (int q = 0; q < GSTRIDE / 2; ++q)
+            reinterpret_cast<double2*>(dst)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
         }
       }
+      __syncwarp();
+      if (act) {
+        for (int jj = 0; jj < cn; ++jj) {
+          real a[3], b0[3], b1[3], b2[3];
+          load_gcol_s(&Gs[wib][jj][0][4 * r], a);
+          load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg)], b0);
+          load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 4], b1);
+          load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 8], b2);
+#pragma unroll
+          for (int s = 0; s < 3; ++s) {
+            acc0 += a[s] * b0[s];
+            acc1 += a[s] * b1[s];
+            acc2 += a[s] * b2[s];
+          }
+        }
+      }
+      __syncwarp();
     }
-    __syncwarp();
-  }
-  if (act) {
-    const int la = P.cam_local[ch.x], lb = P.cam_local[ch.y];   // la > lb: local order follows camera order
-    double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
-    atomicAdd(dst, -(double)acc0);
-    atomicAdd(dst + 1, -(double)acc1);
-    atomicAdd(dst + 2, -(double)acc2);
+    if (act) {
+      const int la = P.cam_local[ch.x], lb = P.cam_local[ch.y];   // la > lb: local order follows camera order
+      double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
+      atomicAdd(dst, -(double)acc0);
+      atomicAdd(dst + 1, -(double)acc1);
+      atomicAdd(dst + 2, -(double)acc2);
+    }
   }
 }
 
@@ -448,7 +451,8 @@ template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
                       cudaStream_t stream) {
   k_cam_pass<real><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
-  if (B.nchunks > 0 && P.l < P.m) k_pair_build<real><<<(B.nchunks + 7) / 8, 256, 0, stream>>>(P, W, B, Gbuf);
+  if (B.nchunks > 0 && P.l < P.m)   // a fixed grid walks the list of chunks inside clusters
+    k_pair_build<real><<<std::min((B.nchunks + 7) / 8, 8 * 152), 256, 0, stream>>>(P, W, B, Gbuf);
 }
 
 // ------------------------------------------------------------------------------------------------------

@@ -223,6 +223,21 @@ __global__ void k_cam_place(ReorderArgs A, const int* __restrict__ flag, const i
   A.slots[32 * A.cam_warp_off[j] + idx] = o;
 }
 
+// chunks of the camera graph whose two cameras share a cluster
+__global__ void k_chunk_flag(int nchunks, const int4* __restrict__ chunks, const int* __restrict__ cam_cluster,
+                             int* __restrict__ flag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nchunks) return;
+  const int4 ch = chunks[c];
+  flag[c] = cam_cluster[ch.x] == cam_cluster[ch.y] ? 1 : 0;
+}
+
+__global__ void k_chunk_list(int nchunks, const int* __restrict__ flag, const int* __restrict__ excl,
+                             int* __restrict__ active) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < nchunks && flag[c]) active[excl[c]] = c;
+}
+
 // zeroes the 9 nv accumulators of the virtual points, nv read from the device counter
 __global__ void __launch_bounds__(256) k_zero_vp(float4* __restrict__ p, const long long* __restrict__ counts,
                                                  int real_bytes) {
@@ -232,6 +247,17 @@ __global__ void __launch_bounds__(256) k_zero_vp(float4* __restrict__ p, const l
 }
 
 }  // namespace
+
+void launch_list_chunks(const PairChunks& B, const int* cam_cluster, long long* nactive, cudaStream_t stream) {
+  const int n = B.nchunks;
+  if (n <= 0) return;
+  const int g = (n + 255) / 256, ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  k_chunk_flag<<<g, 256, 0, stream>>>(n, B.chunks, cam_cluster, B.flag);
+  k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(n, B.flag, B.tile_sum);
+  k_scan_partials<<<1, 1024, 0, stream>>>(ntiles, B.tile_sum, nactive);
+  k_scan_excl<<<ntiles, SCAN_THREADS, 0, stream>>>(n, B.flag, B.tile_sum, nactive, B.excl);
+  k_chunk_list<<<g, 256, 0, stream>>>(n, B.flag, B.excl, const_cast<int*>(B.active));
+}
 
 void launch_zero_vp(void* vp_acc, const long long* counts, int real_bytes, cudaStream_t stream) {
   k_zero_vp<<<2 * RED_BLOCKS, 256, 0, stream>>>(reinterpret_cast<float4*>(vp_acc), counts, real_bytes);
