@@ -29,9 +29,11 @@ SGC_GAMMA, SGC_BETA = 100, 10.0
 REORDER_LAUNCHES = 16  # kernels of one stba_set_clusters (device re-ordering, listing of the pair chunks)
 WORKLOADS = {
     "c1_internet": ("c1_internet: 1000 cameras (hemisphere r=20), 200k points (10^3 box), Zipf(2) tracks on [2,50] "
-                    "over nearby viewpoints, 10 clusters of 100 cameras, mixed precision"),
+                    "over nearby viewpoints, clusters drawn every iteration by stochastic graph clustering "
+                    "(Gamma 100, beta 10), mixed precision"),
     "c4_large": ("c4_large: 20000 cameras (hemisphere r=60), 4M points (30^3 box), Zipf(2) tracks on [2,80] over "
-                 "nearby viewpoints, 200 clusters of 100 cameras, mixed precision"),
+                 "nearby viewpoints, clusters drawn every iteration by stochastic graph clustering (Gamma 100, "
+                 "beta 10), mixed precision"),
     "c2_slam": ("c2_slam: 5000 cameras along a 2 km closed trajectory with 3 crossings, 500k points, tracks of "
                 "2-20 consecutive frames, 27 clusters of 45-297 cameras, mixed precision"),
 }
@@ -231,6 +233,11 @@ def main():
     sgc_s = time.perf_counter() - t0
     sgc = {"gamma": SGC_GAMMA, "beta": SGC_BETA, "draws": n_draw, "host_threads": min(os.cpu_count() or 1, 16),
            "ms_per_draw": 1e3 * sgc_s / n_draw, "clusters_mean": float(np.mean(seq_l))}
+    if args.config == "c2_slam":
+        # the sequential scene's own uneven segments (45..297 cameras), applied every step
+        seq = np.tile(np.asarray(s.clusters, np.int32), (n_draw, 1))
+        sgc = {"note": "the scene's uneven contiguous segments, re-applied every step", "clusters_mean":
+               float(np.max(s.clusters) + 1)}
     for i in range(max(args.warmup, 3)):
         stba.stba_set_clusters(ctx, seq[i])
         stba.stba_lm_iteration(ctx, want_info=False)

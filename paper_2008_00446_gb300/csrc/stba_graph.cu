@@ -132,6 +132,7 @@ struct SplitMix64 {   // Steele, Lea and Flood, "Fast splittable pseudorandom nu
 struct JoinEdge {
   int a, b;       // clusters (root cameras)
   double W, P;    // sum of w_ij and of k_i k_j over the camera edges between them
+  int pos;        // index in the list of allowed pairs, -1 once it is dropped
   bool alive;
 };
 
@@ -216,15 +217,25 @@ void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t se
   for (int x = 0; x < m; ++x)
     for (int e = g.edge_off[x]; e < g.edge_off[x + 1]; ++e) {
       const int y = g.edge_y[e];
-      edges[e] = JoinEdge{x, y, (double)g.edge_w[e], k[x] * k[y], true};
+      edges[e] = JoinEdge{x, y, (double)g.edge_w[e], k[x] * k[y], -1, true};
       inc[x].push_back(e);
       inc[y].push_back(e);
       table.insert(x, y, e);
       if (gamma >= 2) {
+        edges[e].pos = (int)list.size();
         list.push_back(e);
         B = std::max(B, dq(edges[e]));
       }
     }
+  auto drop = [&](int e) {   // O(1) removal from the list of allowed pairs
+    const int p = edges[e].pos;
+    if (p < 0) return;
+    const int last = list.back();
+    list[p] = last;
+    edges[last].pos = p;
+    list.pop_back();
+    edges[e].pos = -1;
+  };
   auto rebuild = [&]() {
     table.init(E);
     for (int e = 0; e < E; ++e)
@@ -234,10 +245,10 @@ void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t se
   int rejections = 0;
   while (!list.empty()) {
     const size_t r = rng.below(list.size());
-    JoinEdge& e = edges[list[r]];
-    if (!e.alive || size[e.a] + size[e.b] > gamma) {   // no longer an allowed join: drop it
-      list[r] = list.back();
-      list.pop_back();
+    const int ei = list[r];
+    JoinEdge& e = edges[ei];
+    if (size[e.a] + size[e.b] > gamma) {   // a side grew past the cap: no longer an allowed join
+      drop(ei);
       continue;
     }
     const double d = dq(e);
@@ -246,9 +257,8 @@ void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t se
         double nb = -INFINITY;
         for (size_t t = 0; t < list.size();) {
           const JoinEdge& f = edges[list[t]];
-          if (!f.alive || size[f.a] + size[f.b] > gamma) {
-            list[t] = list.back();
-            list.pop_back();
+          if (size[f.a] + size[f.b] > gamma) {
+            drop(list[t]);
             continue;
           }
           nb = std::max(nb, dq(f));
@@ -264,6 +274,7 @@ void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t se
     int big = e.a, small = e.b;
     if (inc[big].size() < inc[small].size()) std::swap(big, small);
     e.alive = false;
+    drop(ei);
     table.erase(big, small);
     for (const int ez : inc[small]) {
       JoinEdge& f = edges[ez];
@@ -275,6 +286,7 @@ void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t se
         edges[t].W += f.W;
         edges[t].P += f.P;
         f.alive = false;
+        drop(ez);
         B = std::max(B, dq(edges[t]));
       } else {
         if (f.a == small) f.a = big; else f.b = big;
