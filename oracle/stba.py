@@ -18,6 +18,12 @@ Readings where the paper is silent or garbled (also listed in the design notes):
   * Stop tests (Ceres definitions): |F - F_new| / F < ftol; ||J^T f||_inf < gtol;
     ||Dx|| < xtol (||x|| + xtol).  They are evaluated on the candidate step, and the acceptance rule
     still applies in that iteration.
+  * Huber loss (Sec. 5.1, "scale factor 0.5"), optional: read as Ceres' HuberLoss(a), a = 0.5, on the
+    squared norm s = ||f_o||^2 of each observation: rho(s) = s for s <= a^2, 2 a sqrt(s) - a^2 beyond.
+    The objective becomes F = sum rho(s_o).  The normal equations take each observation's residual and
+    Jacobian rows scaled by sqrt(rho'(s_o)) at the current x (rho' = 1, or a / sqrt(s) beyond a^2;
+    rho'' <= 0 throughout, so this is Ceres' corrector for this loss: iteratively reweighted least
+    squares); the method's equations are otherwise unchanged.
 """
 from __future__ import annotations
 
@@ -112,9 +118,37 @@ class Linearisation:
     J_p: sp.csr_matrix
 
 
-def linearise(cams, pts, obs_cam, obs_pt, obs_uv):
-    f = camera.residuals(cams, pts, obs_cam, obs_pt, obs_uv).reshape(-1)
+def huber_rho(s, a):
+    """rho(s) of the Huber loss with scale a on the squared norm s (a <= 0: no robust loss, rho(s) = s)."""
+    s = np.asarray(s, dtype=float)
+    if a <= 0:
+        return s
+    return np.where(s <= a * a, s, 2.0 * a * np.sqrt(s) - a * a)
+
+
+def huber_weight(s, a):
+    """rho'(s): 1 inside a^2, a / sqrt(s) beyond."""
+    s = np.asarray(s, dtype=float)
+    if a <= 0:
+        return np.ones_like(s)
+    return np.where(s <= a * a, 1.0, a / np.sqrt(np.maximum(s, a * a)))
+
+
+def robust_cost(cams, pts, obs_cam, obs_pt, obs_uv, a=0.0):
+    """F(x) = sum over observations of rho(||f_o||^2) (rho(s) = s without a robust loss)."""
+    f = camera.residuals(cams, pts, obs_cam, obs_pt, obs_uv)
+    return float(np.sum(huber_rho(np.sum(f * f, axis=1), a)))
+
+
+def linearise(cams, pts, obs_cam, obs_pt, obs_uv, huber=0.0):
+    f = camera.residuals(cams, pts, obs_cam, obs_pt, obs_uv)
     Jc, Jp = camera.jacobians(cams, pts, obs_cam, obs_pt)
+    if huber > 0:   # rows of observation o scaled by sqrt(rho'(||f_o||^2))
+        sw = np.sqrt(huber_weight(np.sum(f * f, axis=1), huber))
+        f = f * sw[:, None]
+        Jc = Jc * sw[:, None, None]
+        Jp = Jp * sw[:, None, None]
+    f = f.reshape(-1)
     return Linearisation(f, Jc, Jp, camera_jacobian(Jc, obs_cam, len(cams)),
                          point_jacobian(Jp, obs_pt, len(pts)))
 
@@ -266,6 +300,7 @@ class Options:
     ftol: float = -1.0
     gtol: float = -1.0
     xtol: float = -1.0
+    huber: float = 0.0     # Huber scale a (0: plain least squares)
 
 
 def stop_tests(F, F_new, grad_inf, dx_norm, x_norm, opt: Options):
@@ -285,7 +320,7 @@ def lm_iteration(cams, pts, obs_cam, obs_pt, obs_uv, clusters, lam, F, opt: Opti
 
     Returns the new (cams, pts, lam, F) and a record of the step."""
     m, n = len(cams), len(pts)
-    lin = linearise(cams, pts, obs_cam, obs_pt, obs_uv)
+    lin = linearise(cams, pts, obs_cam, obs_pt, obs_uv, opt.huber)
     if method == "lm":
         st = full_rcs_step(lin, lam)
     else:
@@ -295,7 +330,7 @@ def lm_iteration(cams, pts, obs_cam, obs_pt, obs_uv, clusters, lam, F, opt: Opti
     cams_new = cams + dc
     pts_new = pts + dp
     if st["spd"]:
-        F_new = camera.cost(cams_new, pts_new, obs_cam, obs_pt, obs_uv)
+        F_new = robust_cost(cams_new, pts_new, obs_cam, obs_pt, obs_uv, opt.huber)
     else:
         F_new = np.inf
     grad_inf = max(np.max(np.abs(st["v"])), np.max(np.abs(st["w"])))
@@ -323,7 +358,7 @@ def solve(cams, pts, obs_cam, obs_pt, obs_uv, cluster_seq, iters, opt: Options =
     opt = opt or Options()
     cluster_seq = np.asarray(cluster_seq)
     lam = opt.lambda0
-    F = camera.cost(cams, pts, obs_cam, obs_pt, obs_uv)
+    F = robust_cost(cams, pts, obs_cam, obs_pt, obs_uv, opt.huber)
     hist = []
     for t in range(iters):
         cl = cluster_seq[t] if cluster_seq.ndim == 2 else cluster_seq
