@@ -70,6 +70,11 @@ typedef struct {
   int32_t linear_solver;    /* stba_linear_solver (default STBA_SOLVER_CLUSTERS) */
   int32_t pcg_max_iter;     /* conjugate-gradient iteration limit per LM step (default 500) */
   double pcg_tol;           /* CG stops at ||S dc - b|| <= pcg_tol ||b|| (default 1e-6) */
+  double huber_a;           /* Huber loss scale a (Sec. 5.1 uses 0.5); 0 = plain least squares (default).
+                               F = sum over observations of rho(||f_o||^2), rho(s) = s for s <= a^2 and
+                               2 a sqrt(s) - a^2 beyond (Ceres' HuberLoss); each observation's residual and
+                               Jacobian rows enter the normal equations scaled by sqrt(rho'(||f_o||^2)) at
+                               the current x.  Not supported by stba_adjoint and stba_cost_noalloc. */
 } stba_options;
 
 typedef struct {
@@ -91,7 +96,7 @@ typedef struct {
 } stba_iter_info;
 
 /* Fills *opt with the defaults above (FP64, correction on, lambda0 1e-4, tolerances off,
- * refine_steps 1, use_graph 1, cluster solver, pcg_max_iter 500, pcg_tol 1e-6). */
+ * refine_steps 1, use_graph 1, cluster solver, pcg_max_iter 500, pcg_tol 1e-6, no Huber loss). */
 void stba_default_options(stba_options* opt);
 
 /* Creates a problem (Sec. 3, Algorithm 1 inputs).

@@ -241,6 +241,7 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.cluster_n = c->cluster_n;
   P.S_off = c->S_off;
   P.v_off = c->v_off;
+  P.huber_a = c->opt.huber_a;
   P.res_f = c->mixed ? (const float*)c->res_cur : nullptr;
   P.res_d = c->mixed ? nullptr : (const double*)c->res_cur;
   return P;
@@ -944,7 +945,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       (c->opt.precision != STBA_FP64 && c->opt.precision != STBA_MIXED) || c->opt.refine_steps < 0 ||
       c->opt.refine_steps > 8 ||
       (c->opt.linear_solver != STBA_SOLVER_CLUSTERS && c->opt.linear_solver != STBA_SOLVER_PCG_FULL) ||
-      (c->opt.linear_solver == STBA_SOLVER_PCG_FULL && (c->opt.pcg_max_iter < 1 || !(c->opt.pcg_tol > 0))))
+      (c->opt.linear_solver == STBA_SOLVER_PCG_FULL && (c->opt.pcg_max_iter < 1 || !(c->opt.pcg_tol > 0))) ||
+      !(c->opt.huber_a >= 0.0) || !std::isfinite(c->opt.huber_a))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
   c->m = m;
   c->n = n;
@@ -1355,6 +1357,7 @@ stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_d
                          double* dL_dcams0, double* dL_dpts0) {
   if (!c || !dL_dcams) return STBA_ERR_INVALID_ARG;
   if (c->use_pcg) return fail(c, STBA_ERR_STATE, "the adjoint covers the cluster solver only");
+  if (c->opt.huber_a > 0) return fail(c, STBA_ERR_STATE, "the adjoint covers the plain least-squares objective only");
   if (c->tape_len == 0) return fail(c, STBA_ERR_STATE, "no recorded iteration (call stba_record before iterating)");
   if (c->tape_broken)
     return fail(c, STBA_ERR_STATE, "the parameters were replaced between recorded iterations; record again");

@@ -134,4 +134,35 @@ __device__ __forceinline__ void chol3_apply(const real Li[6], const real w[3], r
   x[2] = Li[5] * z2;
 }
 
+// Huber loss (Ceres' HuberLoss(a) on s = ||f_o||^2): the residual and Jacobian rows of an observation enter
+// the normal equations scaled by sqrt(rho'(s)) = 1 for s <= a^2 and sqrt(a / sqrt(s)) beyond.
+template <typename real>
+__device__ __forceinline__ real huber_sqrt_weight(double a, real r0, real r1) {
+  if (!(a > 0.0)) return real(1);
+  const real s = r0 * r0 + r1 * r1, ar = (real)a;
+  return s <= ar * ar ? real(1) : sqrt(ar / sqrt(s));
+}
+
+template <typename real>
+__device__ __forceinline__ void scale_rows(real sw, real (&r)[2], real (&Jc)[2][9], real (&Jp)[2][3]) {
+  r[0] *= sw;
+  r[1] *= sw;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    Jc[0][c] *= sw;
+    Jc[1][c] *= sw;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    Jp[0][c] *= sw;
+    Jp[1][c] *= sw;
+  }
+}
+
+// rho(s) of the cost, in FP64
+__device__ __forceinline__ double huber_rho(double a, double s) {
+  if (!(a > 0.0) || s <= a * a) return s;
+  return 2.0 * a * sqrt(s) - a * a;
+}
+
 }  // namespace stba

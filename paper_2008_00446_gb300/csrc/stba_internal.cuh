@@ -41,6 +41,7 @@ struct DevProblem {
   const int* cluster_n;        // [l] dimension 9 n_k
   const int64_t* S_off;        // [l] element offset of the dense Np_k x Np_k block of cluster k
   const int64_t* v_off;        // [l] element offset of the length-Np_k vectors of cluster k
+  double huber_a;              // Huber scale a (0: plain least squares)
   const float* res_f;          // [q][2] residuals f_o at the current x, computed in FP64, stored in the
   const double* res_d;         //        working precision (res_f in mixed mode, res_d in FP64 mode)
 };

@@ -65,6 +65,14 @@ __global__ void __launch_bounds__(256) k_vp_reduce(DevProblem P, real* vp_acc) {
     project_jacobian<real, false>(C, X, uo, vo, r, Jc, Jp);
     r[0] = res_ptr<real>(P)[2 * (size_t)o];
     r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
+    const real sw = huber_sqrt_weight<real>(P.huber_a, r[0], r[1]);   // 1 without a robust loss
+    r[0] *= sw;
+    r[1] *= sw;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Jp[0][c] *= sw;
+      Jp[1][c] *= sw;
+    }
     val[0] = Jp[0][0] * Jp[0][0] + Jp[1][0] * Jp[1][0];
     val[1] = Jp[0][0] * Jp[0][1] + Jp[1][0] * Jp[1][1];
     val[2] = Jp[0][0] * Jp[0][2] + Jp[1][0] * Jp[1][2];
@@ -270,6 +278,7 @@ __global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real>
     project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
     r[0] = res_ptr<real>(P)[2 * (size_t)o];
     r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
+    scale_rows(huber_sqrt_weight<real>(P.huber_a, r[0], r[1]), r, Jc, Jp);
     const real* vi = W.vp_info + 9 * (size_t)v;
     // Both cases reduce to Jc^T N Jc with a 2x2 N:
     //   single observation  N = (I + Jp Lambda^-1 Jp^T)^-1                 (Woodbury, no cancellation)
@@ -480,8 +489,14 @@ __global__ void __launch_bounds__(256) k_point_rhs(DevProblem P, const double* d
       jd0 += Jc[0][c] * dcc;
       jd1 += Jc[1][c] * dcc;
     }
+    // with a robust loss both Jacobians carry sqrt(rho'): the product carries rho'
+    real wgt = real(1);
+    if (P.huber_a > 0.0) {
+      const real sw = huber_sqrt_weight<real>(P.huber_a, res_ptr<real>(P)[2 * (size_t)o], res_ptr<real>(P)[2 * (size_t)o + 1]);
+      wgt = sw * sw;
+    }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) val[j] = Jp[0][j] * jd0 + Jp[1][j] * jd1;
+    for (int j = 0; j < 3; ++j) val[j] = wgt * (Jp[0][j] * jd0 + Jp[1][j] * jd1);
   }
   segmented_scan<3>(val, pt, lane);
   segmented_store<3>(val, pt, act, lane, o, P.pt_off, t_acc);
@@ -603,7 +618,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cost(DevProblem P, const double
     const double2 uv = reinterpret_cast<const double2*>(P.obs_uv)[o];
     const double r0 = fd * x - uv.x, r1 = fd * y - uv.y;
     if (!(zc > 1e-9)) bad = 1;
-    s += r0 * r0 + r1 * r1;
+    s += huber_rho(P.huber_a, r0 * r0 + r1 * r1);   // rho(s) = s without a robust loss
     rout[2 * (size_t)o] = (real)r0;
     rout[2 * (size_t)o + 1] = (real)r1;
   }
@@ -686,6 +701,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cost_df(DevProblem P, const flo
                                                          const float* __restrict__ pdf, double* partial,
                                                          DevState* st, float* rout) {
   float2 acc = make_float2(0.f, 0.f);
+  double acc_rho = 0.0;
   int bad = 0;
   for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < P.q; o += gridDim.x * blockDim.x) {
     const float4* C4 = reinterpret_cast<const float4*>(cdf + CAM_DF * (size_t)P.obs_cam[o]);
@@ -717,11 +733,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_cost_df(DevProblem P, const flo
     const float4 uv = P.obs_uvdf[o];
     const float2 r0 = df_sub(df_mul(fd, x), make_float2(uv.x, uv.y));
     const float2 r1 = df_sub(df_mul(fd, y), make_float2(uv.z, uv.w));
-    acc = df_add(acc, df_add(df_mul(r0, r0), df_mul(r1, r1)));
+    const float2 sq = df_add(df_mul(r0, r0), df_mul(r1, r1));
+    if (P.huber_a > 0.0)   // robust loss: rho of the FP64 value of the double-float square
+      acc_rho += huber_rho(P.huber_a, (double)sq.x + (double)sq.y);
+    else
+      acc = df_add(acc, sq);
     rout[2 * (size_t)o] = r0.x + r0.y;
     rout[2 * (size_t)o + 1] = r1.x + r1.y;
   }
-  double s = (double)acc.x + (double)acc.y;
+  double s = (double)acc.x + (double)acc.y + acc_rho;
   __shared__ double red[RED_THREADS / 32];
   for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(FULL_MASK, s, d);
   bad = __any_sync(FULL_MASK, bad);

@@ -33,6 +33,9 @@ __global__ void __launch_bounds__(256) k_pcg_jac(DevProblem P, real* __restrict_
     real uo, vo, r[2], Jc[2][9], Jp[2][3];
     load_uv(P, o, uo, vo);
     project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
+    r[0] = res_ptr<real>(P)[2 * (size_t)o];
+    r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
+    scale_rows(huber_sqrt_weight<real>(P.huber_a, r[0], r[1]), r, Jc, Jp);   // robust loss: sqrt(rho') rows
     real v[JSTRIDE];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
@@ -121,9 +124,12 @@ __global__ void __launch_bounds__(256) k_pcg_precond(DevProblem P, CamSlots CS, 
 #pragma unroll
   for (int s = 0; s < 3; ++s) Jp[0][s] = Jp[1][s] = real(0);
   if (o >= 0) {
-    load_j(J, o, Jc, Jp);
+    load_j(J, o, Jc, Jp);   // rows already scaled by sqrt(rho') under a robust loss
     f[0] = res_ptr<real>(P)[2 * (size_t)o];
     f[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
+    const real sw = huber_sqrt_weight<real>(P.huber_a, f[0], f[1]);
+    f[0] *= sw;
+    f[1] *= sw;
     const real* ci = pt_info + 9 * (size_t)P.obs_pt[o];   // C^-1 packed 00 01 02 11 12 22
     const real Ci[3][3] = {{ci[0], ci[1], ci[2]}, {ci[1], ci[3], ci[4]}, {ci[2], ci[4], ci[5]}};
 #pragma unroll

@@ -34,7 +34,8 @@ class StbaOptions(ctypes.Structure):
                 ("lambda_min", ctypes.c_double), ("correction_lambda", ctypes.c_double),
                 ("ftol", ctypes.c_double), ("gtol", ctypes.c_double), ("xtol", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double)]
+                ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
+                ("huber_a", ctypes.c_double)]
 
 
 class StbaIterInfo(ctypes.Structure):

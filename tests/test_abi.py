@@ -32,6 +32,7 @@ def test_default_options_match_the_paper():
     o = stba.stba_default_options()
     assert o.lambda0 == 1e-4 and o.correction_lambda == 0.1 and o.correction == 1
     assert o.precision == stba.STBA_FP64 and o.refine_steps == 1
+    assert o.huber_a == 0.0   # plain least squares unless the Huber loss is asked for
 
 
 def test_status_strings():
@@ -84,3 +85,6 @@ def test_invalid_options_are_rejected():
         stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, lambda0=0.0)
     with pytest.raises(stba.StbaError):
         stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=7)
+    for bad in (-0.5, float("nan"), float("inf")):
+        with pytest.raises(stba.StbaError):
+            stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, huber_a=bad)
