@@ -382,7 +382,9 @@ def compare_full_rcs(s, stba, stream, iters, torch, max_stba_iters=100):
     every iteration (Algorithm 1) -- stochastic graph clustering draws (Sec. 4.4, beta = 10, Gamma = 100),
     and, for comparison, spatial partitions (azimuth wedges with a random phase) -- and runs until its RMSE
     reaches 1.001 x the better full-RCS final RMSE (or max_stba_iters).  Every timed STBA iteration
-    includes its stba_set_clusters.  Per-iteration device time, final RMSE and time to the target."""
+    includes its stba_set_clusters.  Per-iteration device time, final RMSE and time to the target, the
+    latter twice: iteration by iteration with the host reading the RMSE after each (as the loop that finds
+    the target must), and the same number of iterations enqueued back to back."""
     import numpy as np
 
     import scenes
@@ -425,12 +427,34 @@ def compare_full_rcs(s, stba, stream, iters, torch, max_stba_iters=100):
     seqs = {"stba_sgc": seq_sgc}
     if s.meta.get("kind") in ("ring", "hemisphere"):
         seqs["stba_spatial"] = scenes.cluster_sequence(s, max_stba_iters, seed=s.meta["seed"] + 1)
+    def run_pipelined(seq, n_it):
+        # the same iterations with nothing waiting for the host between them (Algorithm 1's stop test runs on
+        # the device): one pair of events around all of them
+        ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, seq[0], precision=stba.STBA_MIXED,
+                               stream=stream)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for t in range(n_it):
+            stba.stba_set_clusters(ctx, seq[t])
+            stba.stba_lm_iteration(ctx, want_info=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        _, F, _ = stba.stba_get_state(ctx)
+        stba.stba_destroy(ctx)
+        return a.elapsed_time(b), float(np.sqrt(F / (2 * s.q)))
+
     for name, seq in seqs.items():
         st = run(seq[0], seq, max_stba_iters, target=target)
         hit = [i for i, r in enumerate(st["rmse"]) if r <= target]
         out[name] = {"iters_run": len(st["rmse"]), "ms_per_iter": st["ms_per_iter"], "final_rmse": st["rmse"][-1],
                      "time_to_target_ms": st["cum_ms"][hit[0]] if hit else None,
                      "iters_to_target": hit[0] + 1 if hit else None}
+        if hit:
+            ms, rm = run_pipelined(seq, hit[0] + 1)
+            out[name]["time_to_target_pipelined_ms"] = ms
+            out[name]["rmse_pipelined_run"] = rm
     for name, r in res.items():
         h = [i for i, x in enumerate(r["rmse"]) if x <= target]
         out[name] = {"iters": len(r["rmse"]), "ms_per_iter": r["ms_per_iter"], "final_rmse": r["rmse"][-1],
