@@ -75,6 +75,9 @@ typedef struct {
                                2 a sqrt(s) - a^2 beyond (Ceres' HuberLoss); each observation's residual and
                                Jacobian rows enter the normal equations scaled by sqrt(rho'(||f_o||^2)) at
                                the current x.  Not supported by stba_adjoint and stba_cost_noalloc. */
+  int32_t factor_tile;      /* tile of the cluster factorisation: 0 = default (64 for the FP32 factor of
+                               STBA_MIXED, 32 for FP64); STBA_MIXED also accepts 32.  stba_autotune picks
+                               between the candidates by timing. */
 } stba_options;
 
 typedef struct {
@@ -233,6 +236,15 @@ void stba_graph_destroy(stba_graph* g);
 /* The same as stba_graph_cluster_batch on the camera graph of a context (built by stba_create). */
 stba_status stba_cluster_sgc(stba_ctx* ctx, int32_t gamma, double beta, uint64_t seed, int32_t count,
                              int32_t* cluster_assignments, int32_t* l);
+
+/* Autotuner (the paper has none): times `iterations` LM iterations with every candidate tile of the
+ * cluster factorisation (STBA_MIXED: 64 and 32; FP64: 32 only) on the current parameters and cluster
+ * assignment, restores the parameters, damping and cost after each trial, and keeps the fastest tile for
+ * the following iterations.  *tile (optional) receives the choice, ms[0..1] (optional) the time per
+ * iteration with tiles 64 and 32 (-1 when not tried).  Synchronises the context stream.  Errors:
+ * STBA_ERR_STATE while iterations are being recorded (stba_record), STBA_ERR_INVALID_ARG for
+ * iterations < 1. */
+stba_status stba_autotune(stba_ctx* ctx, int32_t iterations, int32_t* tile, float* ms);
 
 /* Frees every device allocation of the context.  NULL is allowed. */
 void stba_destroy(stba_ctx* ctx);

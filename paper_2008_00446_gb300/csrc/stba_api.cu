@@ -124,6 +124,7 @@ struct stba_ctx {
   // graph / timing
   cudaGraphExec_t graph = nullptr;
   bool graph_stale = false;             // the cluster layout changed since the graph was captured
+  int tile = 32;                        // factorisation tile (stba_autotune may change the FP32 one)
   bool capturing = false;
   bool timing = false;
   int launches_per_iter = 0;
@@ -337,7 +338,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     fill[k]++;
   }
   // dense layout (padded to the factorisation tile TF)
-  const int TF = factor_tile(c->mixed);
+  const int TF = c->tile;
   c->h_np.assign(l, 0);
   c->h_nk.assign(l, 0);
   c->h_S_off.assign(l, 0);
@@ -477,7 +478,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
                         c->h_panel_off.data(),
                         c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
-                        c->ev_panel.data(), c->ev_update.data()};
+                        c->ev_panel.data(), c->ev_update.data(), TF};
   }
   {
     int least = 0, greatest = 0;
@@ -893,6 +894,81 @@ stba_status stba_cluster_sgc(stba_ctx* c, int32_t gamma, double beta, uint64_t s
   return STBA_OK;
 }
 
+stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, float* ms) {
+  if (!c || iterations < 1) return STBA_ERR_INVALID_ARG;
+  if (c->tape_cap > 0) return fail(c, STBA_ERR_STATE, "stba_autotune is not allowed while iterations are recorded");
+  if (ms) ms[0] = ms[1] = -1.0f;
+  if (!c->mixed || c->use_pcg) {   // one candidate
+    if (tile) *tile = c->tile;
+    return STBA_OK;
+  }
+  // state to restore after every trial: parameters, residuals at x (in the order of this assignment, which
+  // every trial reproduces), the device LM state
+  const size_t nc = 9 * (size_t)c->m, npt = 3 * (size_t)c->n, nr = 2 * (size_t)c->q * sizeof(float);
+  double *cams0 = nullptr, *pts0 = nullptr;
+  char* res0 = nullptr;
+  DevState* st0 = nullptr;
+  auto release = [&]() {
+    cudaFree(cams0);
+    cudaFree(pts0);
+    cudaFree(res0);
+    cudaFree(st0);
+  };
+  if (cudaMalloc(&cams0, nc * 8) != cudaSuccess || cudaMalloc(&pts0, npt * 8) != cudaSuccess ||
+      cudaMalloc(&res0, nr) != cudaSuccess || cudaMalloc(&st0, sizeof(DevState)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return fail(c, STBA_ERR_OOM, "stba_autotune: no device memory for the saved state");
+  }
+  auto copy = [&](void* d, const void* s_, size_t b) {
+    return cudaMemcpyAsync(d, s_, b, cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess;
+  };
+  bool ok = copy(cams0, c->cams, nc * 8) && copy(pts0, c->pts, npt * 8) && copy(res0, c->res_cur, nr) &&
+            copy(st0, c->st, sizeof(DevState));
+  auto restore = [&]() {
+    return copy(c->cams, cams0, nc * 8) && copy(c->pts, pts0, npt * 8) && copy(c->res_cur, res0, nr) &&
+           copy(c->st, st0, sizeof(DevState));
+  };
+  const std::vector<int> cl = c->h_clusters;
+  const int cand[2] = {64, 32};
+  float best_ms = 0.f;
+  int best = c->tile;
+  stba_status s = STBA_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) ok = false;
+  for (int t = 0; t < 2 && ok && s == STBA_OK; ++t) {
+    c->tile = cand[t];
+    if ((s = set_clusters_host(c, cl)) != STBA_OK) break;
+    ok = restore();
+    if (ok && (s = run_iteration(c)) != STBA_OK) break;   // warm-up: capture, first launch
+    ok = ok && restore() && cudaEventRecord(e0, c->stream) == cudaSuccess;
+    for (int i = 0; i < iterations && ok && s == STBA_OK; ++i) s = run_iteration(c);
+    if (s != STBA_OK) break;
+    ok = ok && cudaEventRecord(e1, c->stream) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float el = 0.f;
+    ok = ok && cudaEventElapsedTime(&el, e0, e1) == cudaSuccess;
+    const float per = el / iterations;
+    if (ms) ms[t] = per;
+    if (ok && (t == 0 || per < best_ms)) {
+      best_ms = per;
+      best = cand[t];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s == STBA_OK && ok) {
+    c->tile = best;
+    s = set_clusters_host(c, cl);
+    if (s == STBA_OK) ok = restore() && cudaStreamSynchronize(c->stream) == cudaSuccess;
+  }
+  release();
+  if (s != STBA_OK) return s;
+  if (!ok) return fail(c, STBA_ERR_CUDA, "stba_autotune: a copy or an event failed");
+  c->have_stage_times = false;
+  if (tile) *tile = c->tile;
+  return STBA_OK;
+}
+
 const char* stba_last_error(stba_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 void stba_destroy(stba_ctx* c) {
@@ -946,12 +1022,14 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       c->opt.refine_steps > 8 ||
       (c->opt.linear_solver != STBA_SOLVER_CLUSTERS && c->opt.linear_solver != STBA_SOLVER_PCG_FULL) ||
       (c->opt.linear_solver == STBA_SOLVER_PCG_FULL && (c->opt.pcg_max_iter < 1 || !(c->opt.pcg_tol > 0))) ||
-      !(c->opt.huber_a >= 0.0) || !std::isfinite(c->opt.huber_a))
+      !(c->opt.huber_a >= 0.0) || !std::isfinite(c->opt.huber_a) ||
+      !(c->opt.factor_tile == 0 || c->opt.factor_tile == 32 || (c->opt.factor_tile == 64 && c->opt.precision == STBA_MIXED)))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
   c->m = m;
   c->n = n;
   c->q = q;
   c->mixed = c->opt.precision == STBA_MIXED;
+  c->tile = c->opt.factor_tile ? c->opt.factor_tile : factor_tile(c->mixed);
   c->use_pcg = c->opt.linear_solver == STBA_SOLVER_PCG_FULL;
   c->set.correction = c->opt.correction;
   c->set.correction_lambda = c->opt.correction_lambda;

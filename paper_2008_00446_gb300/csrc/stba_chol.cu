@@ -30,11 +30,9 @@ namespace stba {
 
 #define FULL_MASK 0xffffffffu
 
-template <typename F> struct FactorCfg;
-template <> struct FactorCfg<double> { static constexpr int T = 32; };
-template <> struct FactorCfg<float> { static constexpr int T = 64; };
-
-int factor_tile(bool mixed) { return mixed ? FactorCfg<float>::T : FactorCfg<double>::T; }
+// default tile of the factorisation: 64 for the FP32 factor (32 is the other candidate of stba_autotune),
+// 32 for the FP64 factor
+int factor_tile(bool mixed) { return mixed ? 64 : 32; }
 
 // s_i = 1 / sqrt(S_ii) (1 on padding)
 template <typename Sreal>
@@ -752,11 +750,10 @@ void launch_prio(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
-template <typename F>
-void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
-                   cudaStream_t stream) {
+template <typename F, int T>
+void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
+                     cudaStream_t stream) {
   using Sreal = double;
-  constexpr int T = FactorCfg<F>::T;
   F* L = reinterpret_cast<F*>(fb.L);
   F* Dinv = reinterpret_cast<F*>(fb.Dinv);
   dim3 g1(std::max(1, std::min(plan.max_np / 256 + 1, 64)), P.l);
@@ -789,11 +786,10 @@ void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb
                                                                 plan.diag_items, fb.v_total);
 }
 
-template <typename F>
-void launch_solve(const DevProblem& P, const double* S, const double* b, const FactorBuffers& fb,
-                  const CholPlan& plan, int refine_steps, double* dc, float* dcf, cudaStream_t stream) {
+template <typename F, int T>
+void launch_solve_t(const DevProblem& P, const double* S, const double* b, const FactorBuffers& fb,
+                    const CholPlan& plan, int refine_steps, double* dc, float* dcf, cudaStream_t stream) {
   using Sreal = double;
-  constexpr int T = FactorCfg<F>::T;
   const F* L = reinterpret_cast<const F*>(fb.L);
   const F* Dinv = reinterpret_cast<const F*>(fb.Dinv);
   launch_tri_solve<F, T, Sreal>(P, L, Dinv, fb.scale, b, fb.x, 0, plan.max_np, fb.v_total, stream);
@@ -807,15 +803,38 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
   k_scatter_dc<<<P.l, 256, 0, stream>>>(P, fb.x, dc, dcf);
 }
 
+// the tile size of the plan: FP32 factors 32 or 64 (chosen by stba_autotune), FP64 factors 32
+template <typename F>
+void launch_factor(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
+                   cudaStream_t stream) {
+  if (sizeof(F) == 4 && plan.tile == 64)
+    launch_factor_t<F, 64>(P, S, fb, plan, stream);
+  else
+    launch_factor_t<F, 32>(P, S, fb, plan, stream);
+}
+
+template <typename F>
+void launch_solve(const DevProblem& P, const double* S, const double* b, const FactorBuffers& fb,
+                  const CholPlan& plan, int refine_steps, double* dc, float* dcf, cudaStream_t stream) {
+  if (sizeof(F) == 4 && plan.tile == 64)
+    launch_solve_t<F, 64>(P, S, b, fb, plan, refine_steps, dc, dcf, stream);
+  else
+    launch_solve_t<F, 32>(P, S, b, fb, plan, refine_steps, dc, dcf, stream);
+}
+
 void configure_solve_kernels(int max_np) {
   cudaFuncSetAttribute(k_chol_panel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)PanelLayout<float, 64>::bytes);
+  cudaFuncSetAttribute(k_chol_panel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)PanelLayout<float, 32>::bytes);
   cudaFuncSetAttribute(k_chol_panel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)PanelLayout<double, 32>::bytes);
-  const int s32 = (int)(SolveLayout<float, 64>::fixed_bytes + sizeof(float) * (size_t)max_np);
-  const int s64 = (int)(SolveLayout<double, 32>::fixed_bytes + sizeof(double) * (size_t)max_np);
-  cudaFuncSetAttribute(k_tri_solve<float, 64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s32);
-  cudaFuncSetAttribute(k_tri_solve<double, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, s64);
+  const int f64 = (int)(SolveLayout<float, 64>::fixed_bytes + sizeof(float) * (size_t)max_np);
+  const int f32 = (int)(SolveLayout<float, 32>::fixed_bytes + sizeof(float) * (size_t)max_np);
+  const int d32 = (int)(SolveLayout<double, 32>::fixed_bytes + sizeof(double) * (size_t)max_np);
+  cudaFuncSetAttribute(k_tri_solve<float, 64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f64);
+  cudaFuncSetAttribute(k_tri_solve<float, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f32);
+  cudaFuncSetAttribute(k_tri_solve<double, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32);
 }
 
 void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStream_t stream) {

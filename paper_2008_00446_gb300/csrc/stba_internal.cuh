@@ -219,6 +219,7 @@ struct CholPlan {
   cudaEvent_t ev_fork, ev_join;
   const cudaEvent_t* ev_panel;    // [nsteps]
   const cudaEvent_t* ev_update;   // [nsteps]
+  int tile;                       // factorisation tile T (the dense blocks are padded to it)
 };
 struct FactorBuffers {
   void* L;          // factor (F = float or double), same layout as S'

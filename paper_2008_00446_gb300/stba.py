@@ -26,7 +26,7 @@ EXPORTS = ["stba_default_options", "stba_create", "stba_set_clusters", "stba_lm_
            "stba_last_step", "stba_problem_info", "stba_get_cluster_system", "stba_set_timing",
            "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error", "stba_cost_noalloc",
            "stba_record", "stba_adjoint", "stba_graph_create", "stba_graph_edges", "stba_graph_cluster",
-           "stba_graph_cluster_batch", "stba_graph_destroy", "stba_cluster_sgc"]
+           "stba_graph_cluster_batch", "stba_graph_destroy", "stba_cluster_sgc", "stba_autotune"]
 
 
 class StbaOptions(ctypes.Structure):
@@ -35,7 +35,7 @@ class StbaOptions(ctypes.Structure):
                 ("ftol", ctypes.c_double), ("gtol", ctypes.c_double), ("xtol", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
-                ("huber_a", ctypes.c_double)]
+                ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32)]
 
 
 class StbaIterInfo(ctypes.Structure):
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
         "stba_graph_cluster_batch": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
         "stba_graph_destroy": (None, [P]),
         "stba_cluster_sgc": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
+        "stba_autotune": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -299,6 +300,14 @@ def stba_cost_noalloc(cameras, points, obs_cam, obs_pt, obs_uv, F_out, stream=No
                                   ctypes.c_void_p(F_out.data_ptr()), _stream_handle(stream))
     if st != 0:
         raise StbaError(st, "stba_cost_noalloc failed")
+
+
+def stba_autotune(ctx: Context, iterations=5):
+    """Times the candidate factorisation tiles and keeps the fastest: (tile, {64: ms, 32: ms})."""
+    tile = ctypes.c_int32()
+    ms = (ctypes.c_float * 2)()
+    ctx._check(load().stba_autotune(ctx.handle, int(iterations), ctypes.byref(tile), ms))
+    return tile.value, {64: ms[0], 32: ms[1]}
 
 
 def stba_record(ctx: Context, max_iter: int):

@@ -85,6 +85,12 @@ def test_invalid_options_are_rejected():
         stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, lambda0=0.0)
     with pytest.raises(stba.StbaError):
         stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=7)
+    for bad_tile in (16, 48, -1):
+        with pytest.raises(stba.StbaError):
+            stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=1,
+                             factor_tile=bad_tile)
+    with pytest.raises(stba.StbaError):   # the FP64 factor has one tile
+        stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, factor_tile=64)
     for bad in (-0.5, float("nan"), float("inf")):
         with pytest.raises(stba.StbaError):
             stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, huber_a=bad)

@@ -1,0 +1,66 @@
+"""The factorisation tile as a runtime choice and the autotuner that picks it.  Both FP32 tiles give the
+mixed-precision bar against the oracle on the 30-camera ring (first step 1e-3, RMSE after ten iterations
+within 0.1 %); stba_autotune leaves the parameters, damping and cost as it found them and keeps a tile
+whose next iteration agrees with a context created with that tile (to the mixed-mode bar)."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import stba as ostba
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2008_00446_gb300 import stba  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def ring():
+    s = scenes.make_config("c0_ring")
+    c, p, lam, F, hist = ostba.solve(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, 10,
+                                     ostba.Options())
+    return s, F, hist
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+def test_both_fp32_tiles_meet_the_mixed_bar(ring, tile):
+    s, F, hist = ring
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                           precision=stba.STBA_MIXED, factor_tile=tile)
+    stba.stba_lm_iteration(ctx)
+    dc, dp = stba.stba_last_step(ctx)
+    assert rel(dc, hist[0]["dc"]) < 1e-3 and rel(dp, hist[0]["dp"]) < 1e-3
+    for _ in range(9):
+        stba.stba_lm_iteration(ctx)
+    _, Fg, _ = stba.stba_get_state(ctx)
+    assert abs(np.sqrt(Fg) - np.sqrt(F)) <= 1e-3 * np.sqrt(F)
+
+
+def test_autotune_restores_the_state_and_keeps_a_working_tile(ring):
+    s, F, hist = ring
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                           precision=stba.STBA_MIXED)
+    stba.stba_lm_iteration(ctx)
+    lam0, F0, it0 = stba.stba_get_state(ctx)
+    c0, p0 = stba.stba_get_params(ctx)
+    tile, ms = stba.stba_autotune(ctx, 3)
+    assert tile in (32, 64) and ms[32] > 0 and ms[64] > 0
+    lam1, F1, it1 = stba.stba_get_state(ctx)
+    c1, p1 = stba.stba_get_params(ctx)
+    assert lam1 == lam0 and F1 == F0 and np.array_equal(c1, c0) and np.array_equal(p1, p0)
+    info = stba.stba_lm_iteration(ctx)
+    ref = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                           precision=stba.STBA_MIXED, factor_tile=tile)
+    stba.stba_lm_iteration(ref)
+    info_ref = stba.stba_lm_iteration(ref)
+    assert info["accepted"] == info_ref["accepted"]
+    # mixed precision: FP32 sums reach the FP64 accumulators in a run-dependent order, so two runs of the same
+    # iteration agree to the mixed-mode bar, not bit for bit
+    assert abs(info["F_after"] - info_ref["F_after"]) <= 1e-4 * info_ref["F_after"]
+    stba.stba_record(ctx, 2)
+    with pytest.raises(stba.StbaError):
+        stba.stba_autotune(ctx, 2)
