@@ -51,9 +51,12 @@ typedef enum { STBA_FP64 = 0, STBA_MIXED = 1 } stba_precision;
 
 typedef enum {
   STBA_SOLVER_CLUSTERS = 0, /* the method: one dense LL^T per cluster system S'_k (Eq. 13) */
-  STBA_SOLVER_PCG_FULL = 1  /* the comparator: plain LM on the full reduced camera system of all cameras
+  STBA_SOLVER_PCG_FULL = 1, /* the comparator: plain LM on the full reduced camera system of all cameras
                                (Eq. 5, clusters ignored), solved by block-Jacobi preconditioned conjugate
                                gradients, matrix-free; not captured in a graph (the host checks the residual) */
+  STBA_SOLVER_PCG_CLUSTERS = 2 /* the method with its split system S' dc = b' (Eq. 10, 13) solved inexactly by
+                               the same block-Jacobi PCG, matrix-free over the virtual points, instead of the
+                               cluster factorisations (Sec. 6); stops at pcg_tol or pcg_max_iter */
 } stba_linear_solver;
 
 typedef struct {
@@ -94,7 +97,7 @@ typedef struct {
   int32_t failed_clusters; /* clusters whose Cholesky factorisation met a pivot <= 0 or non-finite */
   int32_t boosted_pivots;  /* mixed precision: FP32 pivots lost to rounding and raised before FP64
                               refinement (static pivoting); 0 in FP64 mode */
-  int32_t linear_iterations; /* conjugate-gradient iterations of the step (STBA_SOLVER_PCG_FULL), else 0 */
+  int32_t linear_iterations; /* conjugate-gradient iterations of the step (the PCG solvers), else 0 */
   int64_t iteration;    /* 1-based count of iterations run on this context */
 } stba_iter_info;
 

@@ -98,6 +98,7 @@ struct stba_ctx {
   CholPlan cplan{};
   FactorBuffers fbuf{};
   bool use_pcg = false;                 // STBA_SOLVER_PCG_FULL: no cluster systems, CG on the full system
+  bool use_spcg = false;                // STBA_SOLVER_PCG_CLUSTERS: the cluster systems by CG, matrix-free
   PcgBuffers pcg{};
   int* fail_flags = nullptr;
 
@@ -521,7 +522,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     else
       launch_reorder<double>(A, c->key, c->tile_sum, c->counts, carry ? (const double*)c->res_cur : nullptr,
                              (double*)c->res_cand, c->stream);
-    if (!c->use_pcg && c->pchunks.nchunks > 0)
+    if (!c->use_pcg && !c->use_spcg && c->pchunks.nchunks > 0)
       launch_list_chunks(c->pchunks, c->cam_cluster, c->counts + 3, c->stream);
     CK(cudaGetLastError());
     if (carry) std::swap(c->res_cur, c->res_cand);
@@ -605,9 +606,19 @@ int enqueue_pcg_iteration(stba_ctx* c) {
   if (c->mixed) launch_params_to_float(P, c->cams_f, c->pts_f, s);
   launch_zero_vp(c->vp_acc, c->counts, (int)sizeof(real), s);
   cudaMemsetAsync(c->t_acc, 0, 3 * (size_t)c->n * sizeof(real), s);
+  if (c->use_spcg) {
+    launch_spcg_zero(P, W.S, s);
+    cudaMemsetAsync(c->b, 0, (size_t)c->v_total * sizeof(double), s);
+    cudaMemsetAsync(c->vgrad, 0, 9 * (size_t)c->m * sizeof(real), s);
+  }
   launch_vp_reduce<real>(P, W, s);
   launch_vp_finalize<real>(P, W, c->st, s);
   record_stage(c, 1);
+  if (c->use_spcg) {   // the camera pass alone: b', v and the diagonal blocks of S'
+    PairChunks none = c->pchunks;
+    none.nchunks = 0;
+    launch_rcs_build<real>(P, W, c->cslots, none, (real*)c->Gbuf, c->st, s);
+  }
   pcg_prepare<real>(P, W, c->cslots, c->pcg, c->st, s);
   record_stage(c, 2);
   record_stage(c, 3);
@@ -649,7 +660,7 @@ stba_status run_cost(stba_ctx* c, double* F) {
 }
 
 stba_status launch_iteration(stba_ctx* c) {
-  if (c->use_pcg) {
+  if (c->use_pcg || c->use_spcg) {
     const int32_t iters = c->mixed ? enqueue_pcg_iteration<float>(c) : enqueue_pcg_iteration<double>(c);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&c->st->info.linear_iterations, &iters, sizeof iters, cudaMemcpyHostToDevice, c->stream));
@@ -898,7 +909,7 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, float*
   if (!c || iterations < 1) return STBA_ERR_INVALID_ARG;
   if (c->tape_cap > 0) return fail(c, STBA_ERR_STATE, "stba_autotune is not allowed while iterations are recorded");
   if (ms) ms[0] = ms[1] = -1.0f;
-  if (!c->mixed || c->use_pcg) {   // one candidate
+  if (!c->mixed || c->use_pcg || c->use_spcg) {   // one candidate (or no factorisation at all)
     if (tile) *tile = c->tile;
     return STBA_OK;
   }
@@ -1020,8 +1031,9 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   if (!(c->opt.lambda0 > 0) || !std::isfinite(c->opt.lambda0) || c->opt.lambda_min < 0 ||
       (c->opt.precision != STBA_FP64 && c->opt.precision != STBA_MIXED) || c->opt.refine_steps < 0 ||
       c->opt.refine_steps > 8 ||
-      (c->opt.linear_solver != STBA_SOLVER_CLUSTERS && c->opt.linear_solver != STBA_SOLVER_PCG_FULL) ||
-      (c->opt.linear_solver == STBA_SOLVER_PCG_FULL && (c->opt.pcg_max_iter < 1 || !(c->opt.pcg_tol > 0))) ||
+      (c->opt.linear_solver != STBA_SOLVER_CLUSTERS && c->opt.linear_solver != STBA_SOLVER_PCG_FULL &&
+       c->opt.linear_solver != STBA_SOLVER_PCG_CLUSTERS) ||
+      (c->opt.linear_solver != STBA_SOLVER_CLUSTERS && (c->opt.pcg_max_iter < 1 || !(c->opt.pcg_tol > 0))) ||
       !(c->opt.huber_a >= 0.0) || !std::isfinite(c->opt.huber_a) ||
       !(c->opt.factor_tile == 0 || c->opt.factor_tile == 32 || (c->opt.factor_tile == 64 && c->opt.precision == STBA_MIXED)))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
@@ -1031,6 +1043,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   c->mixed = c->opt.precision == STBA_MIXED;
   c->tile = c->opt.factor_tile ? c->opt.factor_tile : factor_tile(c->mixed);
   c->use_pcg = c->opt.linear_solver == STBA_SOLVER_PCG_FULL;
+  c->use_spcg = c->opt.linear_solver == STBA_SOLVER_PCG_CLUSTERS;
   c->set.correction = c->opt.correction;
   c->set.correction_lambda = c->opt.correction_lambda;
   c->set.lambda_min = c->opt.lambda_min;
@@ -1131,10 +1144,18 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     c->res_cand = r2;
   }
   if ((s = dalloc(c, &c->st, 1, false)) != STBA_OK) return bail(s);
-  if (c->use_pcg) {
+  if (c->use_pcg || c->use_spcg) {
     const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
     char *J, *pw, *tpt, *upt;
     PcgBuffers& B = c->pcg;
+    if (c->use_spcg) {   // per-virtual-point vectors at their largest size (nv <= q), zeroed in 16-byte pieces
+      char *tv, *uv;
+      if ((s = dalloc(c, &tv, 3 * (size_t)q * rs + 16, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &uv, 3 * (size_t)q * rs + 16, false)) != STBA_OK) return bail(s);
+      B.tvp = tv;
+      B.uvp = uv;
+      B.split = true;
+    }
     if ((s = dalloc(c, &J, 24 * (size_t)q * rs, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &pw, 9 * (size_t)m * rs, false)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &tpt, 3 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
@@ -1308,6 +1329,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       if ((s = put(c, d_slots, pad)) != STBA_OK) return bail(s);
     }
     c->pchunks.nactive = c->counts + 3;
+    c->pcg.counts = c->counts;
     c->clist = CamLists{d_cam_off, d_cam_obs};
     c->cslots = CamSlots{d_slots, d_warp_cam, nwarps};
   }
@@ -1434,7 +1456,7 @@ stba_status stba_record(stba_ctx* c, int32_t max_iter) {
 stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_dpts, double* dL_dobs,
                          double* dL_dcams0, double* dL_dpts0) {
   if (!c || !dL_dcams) return STBA_ERR_INVALID_ARG;
-  if (c->use_pcg) return fail(c, STBA_ERR_STATE, "the adjoint covers the cluster solver only");
+  if (c->use_pcg || c->use_spcg) return fail(c, STBA_ERR_STATE, "the adjoint covers the cluster solver only");
   if (c->opt.huber_a > 0) return fail(c, STBA_ERR_STATE, "the adjoint covers the plain least-squares objective only");
   if (c->tape_len == 0) return fail(c, STBA_ERR_STATE, "no recorded iteration (call stba_record before iterating)");
   if (c->tape_broken)
@@ -1545,6 +1567,7 @@ stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {
 stba_status stba_get_cluster_system(stba_ctx* c, int32_t k, double* S, double* b, int64_t* dim) {
   if (!c || k < 0 || k >= c->l) return STBA_ERR_INVALID_ARG;
   if (c->use_pcg) return fail(c, STBA_ERR_STATE, "the PCG solver forms no cluster systems");
+  if (c->use_spcg) return fail(c, STBA_ERR_STATE, "the split PCG solver forms the diagonal blocks of S' only");
   const int nk = c->h_nk[k], np = c->h_np[k];
   if (dim) *dim = nk;
   if (!S && !b) return STBA_OK;

@@ -276,7 +276,15 @@ struct PcgBuffers {
   double* scal;     // b.b, r.z (two parity slots), r.r
   double* partial;  // [3][RED_BLOCKS]
   double* partial2; // [3][RED_BLOCKS]
+  bool split;       // STBA_SOLVER_PCG_CLUSTERS: the method's clustered system S' over virtual points
+  void* tvp;        // [q][3] (split) E'^T p per virtual point, working precision
+  void* uvp;        // [q][3] (split) C'^-1 E'^T p
+  const long long* counts;   // (split) device counters, [0] = number of virtual points
 };
+// split variant: zeroes the diagonal blocks of S' (the camera pass then adds into them)
+void launch_spcg_zero(const DevProblem& P, double* S, cudaStream_t stream);
+// zeroes the 3 nv reals of a per-virtual-point vector (nv = counts[0] on the device)
+void launch_zero_vp3(void* p, const long long* counts, int real_bytes, cudaStream_t stream);
 // Jacobians, preconditioner and right-hand side; x = 0, r = b, p = M^-1 b.
 template <typename real>
 void pcg_prepare(const DevProblem& P, Scratch<real> W, CamSlots CS, const PcgBuffers& B, DevState* st,

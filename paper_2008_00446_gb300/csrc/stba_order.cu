@@ -238,10 +238,10 @@ __global__ void k_chunk_list(int nchunks, const int* __restrict__ flag, const in
   if (c < nchunks && flag[c]) active[excl[c]] = c;
 }
 
-// zeroes the 9 nv accumulators of the virtual points, nv read from the device counter
+// zeroes the per reals of the nv virtual points, nv read from the device counter
 __global__ void __launch_bounds__(256) k_zero_vp(float4* __restrict__ p, const long long* __restrict__ counts,
-                                                 int real_bytes) {
-  const long long n16 = (9 * counts[0] * real_bytes + 15) / 16;   // the buffer holds 9 q reals, 16-byte padded
+                                                 int real_bytes, int per) {
+  const long long n16 = (per * counts[0] * real_bytes + 15) / 16;   // the buffer holds per q reals, 16-byte padded
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16; i += (long long)gridDim.x * blockDim.x)
     p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -260,7 +260,11 @@ void launch_list_chunks(const PairChunks& B, const int* cam_cluster, long long* 
 }
 
 void launch_zero_vp(void* vp_acc, const long long* counts, int real_bytes, cudaStream_t stream) {
-  k_zero_vp<<<2 * RED_BLOCKS, 256, 0, stream>>>(reinterpret_cast<float4*>(vp_acc), counts, real_bytes);
+  k_zero_vp<<<2 * RED_BLOCKS, 256, 0, stream>>>(reinterpret_cast<float4*>(vp_acc), counts, real_bytes, 9);
+}
+
+void launch_zero_vp3(void* p, const long long* counts, int real_bytes, cudaStream_t stream) {
+  k_zero_vp<<<2 * RED_BLOCKS, 256, 0, stream>>>(reinterpret_cast<float4*>(p), counts, real_bytes, 3);
 }
 
 template <typename real>

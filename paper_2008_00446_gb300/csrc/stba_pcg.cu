@@ -12,6 +12,14 @@
 //                  alpha, beta and the residual norms stay on the device (k_pcg_update, k_pcg_dir).
 // The right-hand side b = v - E C^-1 w is S applied to nothing but the point part: k_pcg_cam with p = 0
 // and u = C^-1 w.
+//
+// Split variant (STBA_SOLVER_PCG_CLUSTERS; Sec. 6, the inexact solve of the split RCS): the method's own
+// clustered system S' dc = b' (Eq. 10, 13, virtual points, correction) solved by the same PCG instead of the
+// cluster factorisations.  The camera pass provides b' and the diagonal blocks of S' (the preconditioner);
+// S' p = B p - E' C'^-1 E'^T p runs over the virtual points (k_spcg_Et, k_spcg_u), and a virtual point with
+// one observation enters through its cancellation-free form J_c^T (I + J_p L^-1 J_p^T)^-1 J_c (the camera
+// pass's Woodbury form) (k_spcg_cam).  One CG runs over the block-diagonal system of all clusters at once
+// (shared step lengths; its solution is every cluster's).
 #include <climits>
 
 #include "stba_camera.cuh"
@@ -328,6 +336,126 @@ __global__ void __launch_bounds__(256) k_pcg_cam(DevProblem P, CamSlots CS, cons
   }
 }
 
+// split variant: zero the diagonal blocks of S' before the camera pass accumulates into them
+__global__ void k_spcg_zero(DevProblem P, double* __restrict__ S) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < 81 * P.m; e += gridDim.x * blockDim.x) {
+    const int j = e / 81, rc = e - 81 * (e / 81), r = rc / 9, c = rc - 9 * (rc / 9);
+    const int k = P.cam_cluster[j], lc = P.cam_local[j], np = P.cluster_np[k];
+    S[P.S_off[k] + (size_t)(9 * lc + r) * np + 9 * lc + c] = 0.0;
+  }
+}
+
+// split variant: the damped diagonal blocks of S' (45 lower entries) and b' of every camera, from the
+// cluster layout filled by the camera pass
+__global__ void k_spcg_blocks(DevProblem P, const double* __restrict__ S, const double* __restrict__ b,
+                              double* __restrict__ Mblk, double* __restrict__ rhs) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < P.m; j += gridDim.x * blockDim.x) {
+    const int k = P.cam_cluster[j], lc = P.cam_local[j], np = P.cluster_np[k];
+    const double* Sk = S + P.S_off[k] + (size_t)(9 * lc) * np + 9 * lc;
+    int t = 0;
+    for (int r = 0; r < 9; ++r)
+      for (int c = 0; c <= r; ++c, ++t) Mblk[45 * (size_t)j + t] = Sk[(size_t)r * np + c];
+    for (int r = 0; r < 9; ++r) rhs[9 * (size_t)j + r] = b[P.v_off[k] + 9 * lc + r];
+  }
+}
+
+// t_v = sum_{o in v} J_p^T (J_c p_cam(o)), segmented by virtual point
+template <typename real>
+__global__ void __launch_bounds__(256) k_spcg_Et(DevProblem P, const real* __restrict__ J, const real* __restrict__ p,
+                                                 real* __restrict__ t) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool act = o < P.q;
+  int v = INT_MAX;
+  real val[3] = {0, 0, 0};
+  if (act) {
+    v = P.obs_vp[o];
+    real Jc[2][9], Jp[2][3];
+    load_j(J, o, Jc, Jp);
+    const real* pc = p + 9 * (size_t)P.obs_cam[o];
+    real a0 = 0, a1 = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      a0 += Jc[0][c] * pc[c];
+      a1 += Jc[1][c] * pc[c];
+    }
+#pragma unroll
+    for (int s = 0; s < 3; ++s) val[s] = Jp[0][s] * a0 + Jp[1][s] * a1;
+  }
+  segmented_scan<3>(val, v, lane);
+  segmented_store<3>(val, v, act, lane, o, P.vp_off, t);
+}
+
+// u_v = V'_v^-1 t_v with V' = L L^T (L^-1 packed in vp_info); nv from the device counter
+template <typename real>
+__global__ void k_spcg_u(const long long* __restrict__ counts, const real* __restrict__ vp_info,
+                         const real* __restrict__ t, real* __restrict__ u) {
+  const long long nv = counts[0];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv; v += (long long)gridDim.x * blockDim.x) {
+    real Li[6], tv[3], uv[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) Li[c] = vp_info[9 * v + c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tv[c] = t[3 * v + c];
+    chol3_apply(Li, tv, uv);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[3 * v + c] = uv[c];
+  }
+}
+
+// y_j += sum over the camera's observations of J_c^T N J_c p_j (single-observation virtual points, N =
+// (I + J_p Lambda^-1 J_p^T)^-1, Lambda = lambda diag(J_p^T J_p)) or J_c^T (J_c p_j - J_p u_v) (the others),
+// plus lambda diag(J_c^T J_c) p_j: S' p for the cameras of every cluster
+template <typename real>
+__global__ void __launch_bounds__(256) k_spcg_cam(DevProblem P, CamSlots CS, const real* __restrict__ J,
+                                                  const real* __restrict__ p, const real* __restrict__ u,
+                                                  const DevState* st, double* __restrict__ y) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= CS.nwarps) return;
+  const int lane = threadIdx.x & 31;
+  const int j = CS.warp_cam[gw];
+  const int o = CS.slots[32 * (size_t)gw + lane];
+  const real lam = (real)st->lambda_used;
+  real vsum[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) vsum[c] = real(0);
+  if (o >= 0) {
+    real Jc[2][9], Jp[2][3];
+    load_j(J, o, Jc, Jp);
+    const real* pj = p + 9 * (size_t)j;
+    real a0 = 0, a1 = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      a0 += Jc[0][c] * pj[c];
+      a1 += Jc[1][c] * pj[c];
+    }
+    const int v = P.obs_vp[o];
+    real b0, b1;
+    if (P.vp_off[v + 1] - P.vp_off[v] == 1) {
+      real K00 = 0, K01 = 0, K11 = 0;
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        const real il = real(1) / (lam * (Jp[0][s] * Jp[0][s] + Jp[1][s] * Jp[1][s]));
+        K00 += Jp[0][s] * Jp[0][s] * il;
+        K01 += Jp[0][s] * Jp[1][s] * il;
+        K11 += Jp[1][s] * Jp[1][s] * il;
+      }
+      const real idet = real(1) / ((real(1) + K00) * (real(1) + K11) - K01 * K01);
+      b0 = ((real(1) + K11) * a0 - K01 * a1) * idet;
+      b1 = (-K01 * a0 + (real(1) + K00) * a1) * idet;
+    } else {
+      const real* uv = u + 3 * (size_t)v;
+      b0 = a0 - (Jp[0][0] * uv[0] + Jp[0][1] * uv[1] + Jp[0][2] * uv[2]);
+      b1 = a1 - (Jp[1][0] * uv[0] + Jp[1][1] * uv[1] + Jp[1][2] * uv[2]);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+      vsum[c] = Jc[0][c] * b0 + Jc[1][c] * b1 + lam * (Jc[0][c] * Jc[0][c] + Jc[1][c] * Jc[1][c]) * pj[c];
+  }
+  const real sv = warp_sums_to_lanes<9>(vsum);
+  if (lane < 9) atomicAdd(y + 9 * (size_t)j + lane, (double)sv);
+}
+
 // Block sums of up to three per-thread values into partial[c * RED_BLOCKS + block].
 __device__ __forceinline__ void block_partials3(double a, double b, double c, double* partial) {
   __shared__ double red[3][RED_THREADS / 32];
@@ -381,7 +509,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_pcg_init(int m, const real* __r
     double rj[9], zj[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      rj[a] = (double)vgrad[9 * (size_t)j + a] + yrhs[9 * (size_t)j + a];
+      rj[a] = (vgrad ? (double)vgrad[9 * (size_t)j + a] : 0.0) + yrhs[9 * (size_t)j + a];
       x[9 * (size_t)j + a] = 0.0;
       r[9 * (size_t)j + a] = rj[a];
     }
@@ -499,8 +627,18 @@ void pcg_prepare(const DevProblem& P, Scratch<real> W, CamSlots CS, const PcgBuf
   const int pt_blocks = std::min((P.n + 255) / 256, 4096);
   const int vec_blocks = std::min((m + RED_THREADS - 1) / RED_THREADS, RED_BLOCKS);
   k_pcg_jac<real><<<obs_blocks, 256, 0, stream>>>(P, J);
-  cudaMemsetAsync(B.Mblk, 0, 45 * (size_t)m * sizeof(double), stream);
   cudaMemsetAsync(B.Bdiag, 0, 9 * (size_t)m * sizeof(double), stream);
+  if (B.split) {
+    // the camera pass has filled the diagonal blocks of S' (damped) and b'
+    k_spcg_blocks<<<(m + 127) / 128, 128, 0, stream>>>(P, W.S, W.b, B.Mblk, B.q);
+    k_pcg_invert<<<(m + 127) / 128, 128, 0, stream>>>(m, B.Mblk, B.Bdiag, st, B.Minv);   // Bdiag = 0: no more damping
+    cudaMemsetAsync(B.partial, 0, 3 * RED_BLOCKS * sizeof(double), stream);
+    cudaMemsetAsync(B.partial2, 0, 3 * RED_BLOCKS * sizeof(double), stream);
+    k_pcg_init<real><<<vec_blocks, RED_THREADS, 0, stream>>>(m, nullptr, B.q, B.Minv, B.x, B.r, B.p, pw, B.partial);
+    k_pcg_start<<<1, 32, 0, stream>>>(B.partial, B.scal);
+    return;
+  }
+  cudaMemsetAsync(B.Mblk, 0, 45 * (size_t)m * sizeof(double), stream);
   cudaMemsetAsync(W.vgrad, 0, 9 * (size_t)m * sizeof(real), stream);
   k_pcg_precond<real><<<cam_blocks, 256, 0, stream>>>(P, CS, J, W.pt_info, B.Mblk, B.Bdiag, W.vgrad);
   k_pcg_invert<<<(m + 127) / 128, 128, 0, stream>>>(m, B.Mblk, B.Bdiag, st, B.Minv);
@@ -513,6 +651,10 @@ void pcg_prepare(const DevProblem& P, Scratch<real> W, CamSlots CS, const PcgBuf
   cudaMemsetAsync(B.partial2, 0, 3 * RED_BLOCKS * sizeof(double), stream);
   k_pcg_init<real><<<vec_blocks, RED_THREADS, 0, stream>>>(m, W.vgrad, B.q, B.Minv, B.x, B.r, B.p, pw, B.partial);
   k_pcg_start<<<1, 32, 0, stream>>>(B.partial, B.scal);
+}
+
+void launch_spcg_zero(const DevProblem& P, double* S, cudaStream_t stream) {
+  k_spcg_zero<<<std::min((81 * P.m + 255) / 256, 4 * RED_BLOCKS), 256, 0, stream>>>(P, S);
 }
 
 template <typename real>
@@ -536,11 +678,20 @@ int pcg_iterate(const DevProblem& P, Scratch<real> W, CamSlots CS, const PcgBuff
     for (; it < upto; ++it) {
       const int parity = it & 1;
       // q = S p
-      cudaMemsetAsync(tpt, 0, 3 * (size_t)P.n * sizeof(real), stream);
       cudaMemsetAsync(B.q, 0, (size_t)m9 * sizeof(double), stream);
-      k_pcg_Et<real><<<seg_blocks, 256, 0, stream>>>(P, J, pw, tpt);
-      k_pcg_u<real><<<pt_blocks, 256, 0, stream>>>(P.n, W.pt_info, tpt, upt);
-      k_pcg_cam<real><<<cam_blocks, 256, 0, stream>>>(P, CS, J, pw, upt, B.Bdiag, st, B.q);
+      if (B.split) {   // S' p over the virtual points
+        real* tvp = reinterpret_cast<real*>(B.tvp);
+        real* uvp = reinterpret_cast<real*>(B.uvp);
+        launch_zero_vp3(tvp, B.counts, (int)sizeof(real), stream);
+        k_spcg_Et<real><<<seg_blocks, 256, 0, stream>>>(P, J, pw, tvp);
+        k_spcg_u<real><<<2 * RED_BLOCKS, 256, 0, stream>>>(B.counts, W.vp_info, tvp, uvp);
+        k_spcg_cam<real><<<cam_blocks, 256, 0, stream>>>(P, CS, J, pw, uvp, st, B.q);
+      } else {
+        cudaMemsetAsync(tpt, 0, 3 * (size_t)P.n * sizeof(real), stream);
+        k_pcg_Et<real><<<seg_blocks, 256, 0, stream>>>(P, J, pw, tpt);
+        k_pcg_u<real><<<pt_blocks, 256, 0, stream>>>(P.n, W.pt_info, tpt, upt);
+        k_pcg_cam<real><<<cam_blocks, 256, 0, stream>>>(P, CS, J, pw, upt, B.Bdiag, st, B.q);
+      }
       k_pcg_pq<<<vec9_blocks, RED_THREADS, 0, stream>>>(m9, B.p, B.q, B.partial2);
       k_pcg_update<<<vec_blocks, RED_THREADS, 0, stream>>>(m, B.partial2, B.scal, parity, B.p, B.q, B.Minv, B.x, B.r,
                                                            B.z, B.partial);

@@ -16,7 +16,7 @@ from . import _build
 _LIB = None
 
 STBA_FP64, STBA_MIXED = 0, 1
-STBA_SOLVER_CLUSTERS, STBA_SOLVER_PCG_FULL = 0, 1
+STBA_SOLVER_CLUSTERS, STBA_SOLVER_PCG_FULL, STBA_SOLVER_PCG_CLUSTERS = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not SPD",
           5: "non-finite value", 6: "timeout", 7: "invalid state"}
 

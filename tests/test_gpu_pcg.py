@@ -71,3 +71,44 @@ def test_pcg_equals_cluster_solver_with_one_cluster_fp64():
     assert rel(dcb, dca) < 1e-7
     a.close()
     b.close()
+
+
+# The method's split system by PCG (STBA_SOLVER_PCG_CLUSTERS): the same STBA step as the cluster
+# factorisations, reached by conjugate gradients over the virtual points.  FP64 with pcg_tol = 1e-12: the
+# step equals the oracle's STBA step (direct per-cluster solves) to 1e-7, with and without the correction;
+# mixed precision: ten iterations on the ring reach the oracle's RMSE within 0.1 %.
+@pytest.mark.parametrize("lam", [1e-4, 0.5])
+def test_split_pcg_first_step_fp64_matches_the_stba_step(lam):
+    cl = np.array([0, 0, 0, 1, 1, 1, 2, 2], np.int32)
+    s = scenes.make_tiny_scene(m=8, n=80, seed=5, clusters=cl)
+    F0 = ocam.cost(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv)
+    c2, p2, lam2, F2, rec = ostba.lm_iteration(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, cl, lam, F0,
+                                               ostba.Options(lambda0=lam))
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, cl, lambda0=lam,
+                           linear_solver=stba.STBA_SOLVER_PCG_CLUSTERS, pcg_tol=1e-12, pcg_max_iter=1000)
+    info = stba.stba_lm_iteration(ctx)
+    assert info["corrected"] == rec["corrected"] == (lam >= 0.1)
+    dc, dp = stba.stba_last_step(ctx)
+    assert rel(dc, rec["dc"]) < 1e-7, rel(dc, rec["dc"])
+    assert rel(dp, rec["dp"]) < 1e-7, rel(dp, rec["dp"])
+    assert info["accepted"] == rec["accepted"]
+    assert 0 < info["linear_iterations"] <= 1000
+    assert abs(info["F_after"] - rec["F_after"]) <= 1e-7 * rec["F_after"]
+    with pytest.raises(stba.StbaError):
+        stba.stba_get_cluster_system(ctx, 0)
+
+
+def test_split_pcg_mixed_reaches_oracle_rmse_on_ring():
+    s = scenes.make_config("c0_ring")
+    c, p, lam, F, hist = ostba.solve(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, 10,
+                                     ostba.Options())
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                           precision=stba.STBA_MIXED, linear_solver=stba.STBA_SOLVER_PCG_CLUSTERS)
+    for _ in range(10):
+        stba.stba_lm_iteration(ctx)
+    _, Fg, _ = stba.stba_get_state(ctx)
+    assert abs(ostba.rmse(Fg, s.q) - ostba.rmse(F, s.q)) <= 1e-3 * ostba.rmse(F, s.q)
+    stba.stba_record(ctx, 1)
+    stba.stba_lm_iteration(ctx)
+    with pytest.raises(stba.StbaError):
+        stba.stba_adjoint(ctx, np.zeros((s.m, 9)))
