@@ -201,6 +201,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the full-RCS LM comparison")
     ap.add_argument("--compare-iters", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on the 500-camera scene")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default factorisation tile")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -239,7 +240,9 @@ def main():
         sgc = {"note": "the scene's uneven contiguous segments, re-applied every step", "clusters_mean":
                float(np.max(s.clusters) + 1)}
     stba.stba_set_clusters(ctx, seq[0])
-    tile, tile_ms = stba.stba_autotune(ctx, 5)   # the factorisation tile, chosen by timing (outside the timed steps)
+    tile, tile_ms = None, {}
+    if not args.no_autotune:   # the factorisation tile, chosen by timing (outside the timed steps)
+        tile, tile_ms = stba.stba_autotune(ctx, 5)
     for i in range(max(args.warmup, 3)):
         stba.stba_set_clusters(ctx, seq[i])
         stba.stba_lm_iteration(ctx, want_info=False)
