@@ -393,66 +393,116 @@ __global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real>
 // create, by edge (x, y) and cut into chunks of at most PAIR_CHUNK; under a cluster assignment an edge
 // contributes exactly when both cameras are in one cluster (its two observations of a point are then in
 // one virtual point), and a chunk adds to one block only.  The re-ordering of an assignment lists the
-// chunks whose edge lies inside a cluster; a fixed grid of warps walks that list, one chunk per warp at a
-// time: it stages the G rows of CH pairs at a time in shared memory (one row per lane, all loads in
-// flight), its 27 lanes accumulate the 9x9 block in registers (row r, columns 3cg .. 3cg+2) and add it
-// once into the FP64 S'_k.
+// chunks whose edge lies inside a cluster; a fixed grid of warps walks that list.  A warp's work is a
+// sequence of pieces of CH pairs (the chunks it takes, cut into pieces); the G rows of the next piece are
+// copied into shared memory (cp.async, one row per lane) while the 27 lanes accumulate the current one
+// (row r, columns 3cg .. 3cg+2 of the 9x9 block, in registers); the block is added once per chunk into
+// the FP64 S'_k.
+constexpr int PB_WARPS = 8;
+
+template <typename real> struct PairStage {
+  static constexpr int CH = 64 / (int)sizeof(real);                   // pairs per piece
+  static constexpr int PIECES = 2;                                      // double buffer
+  static constexpr size_t bytes = sizeof(real) * (size_t)PB_WARPS * PIECES * CH * 2 * GSTRIDE;
+};
+
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <typename real>
-__global__ void __launch_bounds__(256) k_pair_build(DevProblem P, Scratch<real> W, PairChunks B,
-                                                    const real* __restrict__ Gbuf) {
-  constexpr int CH = 64 / (int)sizeof(real);
-  __shared__ __align__(16) real Gs[8][CH][2][GSTRIDE];
+__global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scratch<real> W, PairChunks B,
+                                                              const real* __restrict__ Gbuf) {
+  constexpr int CH = PairStage<real>::CH;
+  constexpr int ROWQ = GSTRIDE * (int)sizeof(real) / 16;   // 16-byte pieces of one G row
+  extern __shared__ __align__(16) unsigned char pb_smem[];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  real* stage = reinterpret_cast<real*>(pb_smem) + (size_t)wib * 2 * CH * 2 * GSTRIDE;   // [2][CH][2][GSTRIDE]
   const long long nactive = *B.nactive;
+  const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+  long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (w >= nactive) return;   // uniform per warp
   const int r = lane / 3, cg = lane - (lane / 3) * 3;
   const bool act = lane < 27;
   const int j = lane % CH, side = lane / CH;
-  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w < nactive;
-       w += ((long long)gridDim.x * blockDim.x) >> 5) {
-    const int4 ch = B.chunks[B.active[w]];
-    const int k = P.cam_cluster[ch.x];
-    real acc0 = 0, acc1 = 0, acc2 = 0;
-    for (int c0 = 0; c0 < ch.w; c0 += CH) {
-      const int cn = min(CH, ch.w - c0);
-      if (side < 2 && j < cn) {
-        const int2 pr = B.pairs[ch.z + c0 + j];
-        const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
-        real* dst = &Gs[wib][j][side][0];
-        if constexpr (sizeof(real) == 4) {
+  // the piece (chunk record, first pair) being copied and the one being accumulated
+  int4 ch = B.chunks[B.active[w]];
+  int c0 = 0;
+  auto issue = [&](const int4& chunk, int first, int buf) {
+    const int cn = min(CH, chunk.w - first);
+    if (side < 2 && j < cn) {
+      const int2 pr = B.pairs[chunk.z + first + j];
+      const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
+      real* dst = stage + ((size_t)(buf * CH + j) * 2 + side) * GSTRIDE;
 #pragma unroll
-          for (int q = 0; q < GSTRIDE / 4; ++q)
-            reinterpret_cast<float4*>(dst)[q] = __ldg(reinterpret_cast<const float4*>(src) + q);
-        } else {
-#pragma unroll
-          for (int q = 0; q < GSTRIDE / 2; ++q)
-            reinterpret_cast<double2*>(dst)[q] = __ldg(reinterpret_cast<const double2*>(src) + q);
-        }
-      }
-      __syncwarp();
-      if (act) {
-        for (int jj = 0; jj < cn; ++jj) {
-          real a[3], b0[3], b1[3], b2[3];
-          load_gcol_s(&Gs[wib][jj][0][4 * r], a);
-          load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg)], b0);
-          load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 4], b1);
-          load_gcol_s(&Gs[wib][jj][1][4 * (3 * cg) + 8], b2);
-#pragma unroll
-          for (int s = 0; s < 3; ++s) {
-            acc0 += a[s] * b0[s];
-            acc1 += a[s] * b1[s];
-            acc2 += a[s] * b2[s];
-          }
-        }
-      }
-      __syncwarp();
+      for (int q = 0; q < ROWQ; ++q) cp_async_16(dst + q * (16 / (int)sizeof(real)), src + q * (16 / (int)sizeof(real)));
     }
+    cp_async_commit();
+  };
+  issue(ch, 0, 0);
+  int buf = 0;
+  real acc0 = 0, acc1 = 0, acc2 = 0;
+  for (;;) {
+    // the next piece: the rest of this chunk, else the warp's next chunk
+    int4 nch = ch;
+    int n0 = c0 + CH;
+    bool more = true;
+    if (n0 >= ch.w) {
+      const long long nw = w + wstride;
+      if (nw < nactive) {
+        nch = B.chunks[B.active[nw]];
+        n0 = 0;
+      } else {
+        more = false;
+      }
+    }
+    if (more) {
+      issue(nch, n0, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
     if (act) {
-      const int la = P.cam_local[ch.x], lb = P.cam_local[ch.y];   // la > lb: local order follows camera order
-      double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
-      atomicAdd(dst, -(double)acc0);
-      atomicAdd(dst + 1, -(double)acc1);
-      atomicAdd(dst + 2, -(double)acc2);
+      const int cn = min(CH, ch.w - c0);
+      const real* base = stage + (size_t)buf * CH * 2 * GSTRIDE;
+      for (int jj = 0; jj < cn; ++jj) {
+        real a[3], b0[3], b1[3], b2[3];
+        const real* ga = base + (size_t)jj * 2 * GSTRIDE;
+        const real* gb = ga + GSTRIDE;
+        load_gcol_s(ga + 4 * r, a);
+        load_gcol_s(gb + 4 * (3 * cg), b0);
+        load_gcol_s(gb + 4 * (3 * cg) + 4, b1);
+        load_gcol_s(gb + 4 * (3 * cg) + 8, b2);
+#pragma unroll
+        for (int s2 = 0; s2 < 3; ++s2) {
+          acc0 += a[s2] * b0[s2];
+          acc1 += a[s2] * b1[s2];
+          acc2 += a[s2] * b2[s2];
+        }
+      }
     }
+    __syncwarp();   // every lane is done with this buffer before it is refilled
+    if (c0 + CH >= ch.w) {   // the chunk is complete: one add per block entry
+      if (act) {
+        const int k = P.cam_cluster[ch.x];
+        const int la = P.cam_local[ch.x], lb = P.cam_local[ch.y];   // la > lb: local order follows camera order
+        double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
+        atomicAdd(dst, -(double)acc0);
+        atomicAdd(dst + 1, -(double)acc1);
+        atomicAdd(dst + 2, -(double)acc2);
+      }
+      acc0 = acc1 = acc2 = 0;
+      if (!more) break;
+      w += wstride;
+    }
+    ch = nch;
+    c0 = n0;
+    buf ^= 1;
   }
 }
 
@@ -461,7 +511,8 @@ void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChu
                       cudaStream_t stream) {
   k_cam_pass<real><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
   if (B.nchunks > 0 && P.l < P.m)   // a fixed grid walks the list of chunks inside clusters
-    k_pair_build<real><<<std::min((B.nchunks + 7) / 8, 8 * 152), 256, 0, stream>>>(P, W, B, Gbuf);
+    k_pair_build<real><<<std::min((B.nchunks + PB_WARPS - 1) / PB_WARPS, 3 * 152), 32 * PB_WARPS,
+                         PairStage<real>::bytes, stream>>>(P, W, B, Gbuf);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -901,7 +952,13 @@ void launch_params_to_float(const DevProblem& P, float* cams_f, float* pts_f, cu
   k_params_to_float<<<std::min((total + 255) / 256, 2048), 256, 0, stream>>>(P.m, P.n, P.cams, P.pts, cams_f, pts_f);
 }
 
-void configure_kernels(int max_np) { configure_solve_kernels(max_np); }
+void configure_kernels(int max_np) {
+  configure_solve_kernels(max_np);
+  cudaFuncSetAttribute(k_pair_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)PairStage<float>::bytes);
+  cudaFuncSetAttribute(k_pair_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)PairStage<double>::bytes);
+}
 
 #define INSTANTIATE(real)                                                                                  \
   template void launch_iter_begin<real>(DevState*, const Settings&, cudaStream_t);                        \
