@@ -48,9 +48,8 @@ struct stba_ctx {
   int64_t m = 0, n = 0, q = 0;
   int l = 0, nv = 0;
   bool mixed = false;
-  size_t bytes_base = 0, bytes_cl = 0;
+  size_t bytes_base = 0;
   std::vector<void*> allocs;            // problem-lifetime device buffers
-  std::vector<void*> cl_allocs;         // cluster-assignment-lifetime device buffers
 
   // host copies of the input observations (original order) and the (point, camera) order
   std::vector<int> in_cam, in_pt;
@@ -156,7 +155,7 @@ stba_status fail(stba_ctx* c, stba_status s, const char* fmt, ...) {
   } while (0)
 
 template <typename T>
-stba_status dalloc(stba_ctx* c, T** p, size_t count, bool cluster_scope) {
+stba_status dalloc(stba_ctx* c, T** p, size_t count) {
   size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
   cudaError_t e = cudaMalloc((void**)p, bytes);
   if (e != cudaSuccess) {
@@ -164,8 +163,8 @@ stba_status dalloc(stba_ctx* c, T** p, size_t count, bool cluster_scope) {
     *p = nullptr;
     return fail(c, STBA_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
-  (cluster_scope ? c->cl_allocs : c->allocs).push_back((void*)*p);
-  (cluster_scope ? c->bytes_cl : c->bytes_base) += bytes;
+  c->allocs.push_back((void*)*p);
+  c->bytes_base += bytes;
   return STBA_OK;
 }
 
@@ -183,8 +182,8 @@ stba_status dalloc_into(stba_ctx* c, T** p, size_t count, std::vector<void*>& li
 }
 
 template <typename T>
-stba_status upload(stba_ctx* c, T** p, const std::vector<T>& h, bool cluster_scope) {
-  stba_status s = dalloc(c, p, h.size(), cluster_scope);
+stba_status upload(stba_ctx* c, T** p, const std::vector<T>& h) {
+  stba_status s = dalloc(c, p, h.size());
   if (s != STBA_OK) return s;
   if (!h.empty()) CK(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
   return STBA_OK;
@@ -986,7 +985,6 @@ void stba_destroy(stba_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->graph) cudaGraphExecDestroy(c->graph);
-  free_list(c, c->cl_allocs);
   free_list(c, c->allocs);
   free_list(c, c->tape_allocs);
   for (GrowBuf* g : {&c->g_panel, &c->g_update, &c->g_res, &c->g_diag, &c->g_S, &c->g_b, &c->g_L, &c->g_Dinv,
@@ -1122,57 +1120,57 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       cudaEventCreateWithFlags(&c->stage_ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->stage_ev[1], cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(c, STBA_ERR_CUDA, "cannot create the factorisation stream or its events"));
-  if ((s = dalloc(c, &c->cams, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->pts, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->dc, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->dp, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->partial, 6 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->cam_rt, 15 * (size_t)m, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->cam_df, 28 * (size_t)m, false)) != STBA_OK) return bail(s);
-  if ((s = dalloc(c, &c->pt_df, 6 * (size_t)n, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->cams, 9 * (size_t)m)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->pts, 3 * (size_t)n)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->dc, 9 * (size_t)m)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->dp, 3 * (size_t)n)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->partial, 6 * (size_t)RED_BLOCKS)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->cam_rt, 15 * (size_t)m)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->cam_df, 28 * (size_t)m)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->pt_df, 6 * (size_t)n)) != STBA_OK) return bail(s);
   if (c->mixed) {
-    if ((s = dalloc(c, &c->cams_f, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->pts_f, 3 * (size_t)n, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->dcf, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->cams_f, 9 * (size_t)m)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->pts_f, 3 * (size_t)n)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->dcf, 9 * (size_t)m)) != STBA_OK) return bail(s);
   }
   {
     char *r1, *r2;
     const size_t rsz = 2 * (size_t)q * (c->mixed ? sizeof(float) : sizeof(double));
-    if ((s = dalloc(c, &r1, rsz, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &r2, rsz, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &r1, rsz)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &r2, rsz)) != STBA_OK) return bail(s);
     c->res_cur = r1;
     c->res_cand = r2;
   }
-  if ((s = dalloc(c, &c->st, 1, false)) != STBA_OK) return bail(s);
+  if ((s = dalloc(c, &c->st, 1)) != STBA_OK) return bail(s);
   if (c->use_pcg || c->use_spcg) {
     const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
     char *J, *pw, *tpt, *upt;
     PcgBuffers& B = c->pcg;
     if (c->use_spcg) {   // per-virtual-point vectors at their largest size (nv <= q), zeroed in 16-byte pieces
       char *tv, *uv;
-      if ((s = dalloc(c, &tv, 3 * (size_t)q * rs + 16, false)) != STBA_OK) return bail(s);
-      if ((s = dalloc(c, &uv, 3 * (size_t)q * rs + 16, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &tv, 3 * (size_t)q * rs + 16)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &uv, 3 * (size_t)q * rs + 16)) != STBA_OK) return bail(s);
       B.tvp = tv;
       B.uvp = uv;
       B.split = true;
     }
-    if ((s = dalloc(c, &J, 24 * (size_t)q * rs, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &pw, 9 * (size_t)m * rs, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &tpt, 3 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &upt, 3 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &J, 24 * (size_t)q * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &pw, 9 * (size_t)m * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &tpt, 3 * (size_t)n * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &upt, 3 * (size_t)n * rs)) != STBA_OK) return bail(s);
     B.J = J;
     B.pw = pw;
     B.tpt = tpt;
     B.upt = upt;
     double** vecs[] = {&B.x, &B.r, &B.z, &B.p, &B.q};
     for (double** v : vecs)
-      if ((s = dalloc(c, v, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &B.Mblk, 45 * (size_t)m, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &B.Bdiag, 9 * (size_t)m, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &B.Minv, 81 * (size_t)m, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &B.scal, 8, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &B.partial, 3 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &B.partial2, 3 * (size_t)RED_BLOCKS, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, v, 9 * (size_t)m)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.Mblk, 45 * (size_t)m)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.Bdiag, 9 * (size_t)m)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.Minv, 81 * (size_t)m)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.scal, 8)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.partial, 3 * (size_t)RED_BLOCKS)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &B.partial2, 3 * (size_t)RED_BLOCKS)) != STBA_OK) return bail(s);
   }
   {
     cudaError_t e1 = cudaMemcpyAsync(c->cams, h_cams.data(), h_cams.size() * 8, cudaMemcpyHostToDevice, c->stream);
@@ -1201,12 +1199,12 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       int2* d_pairs = nullptr;
       int *d_active, *d_flag, *d_excl, *d_tiles;
       const size_t nc = chunks.size();
-      if ((s = upload(c, &d_chunks, chunks, false)) != STBA_OK) return bail(s);
-      if ((s = upload(c, &d_pairs, g.pairs, false)) != STBA_OK) return bail(s);
-      if ((s = dalloc(c, &d_active, nc, false)) != STBA_OK) return bail(s);
-      if ((s = dalloc(c, &d_flag, nc + 1, false)) != STBA_OK) return bail(s);
-      if ((s = dalloc(c, &d_excl, nc + 1, false)) != STBA_OK) return bail(s);
-      if ((s = dalloc(c, &d_tiles, nc / 2048 + 2, false)) != STBA_OK) return bail(s);
+      if ((s = upload(c, &d_chunks, chunks)) != STBA_OK) return bail(s);
+      if ((s = upload(c, &d_pairs, g.pairs)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_active, nc)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_flag, nc + 1)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_excl, nc + 1)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_tiles, nc / 2048 + 2)) != STBA_OK) return bail(s);
       c->pchunks = PairChunks{d_chunks, d_pairs, (int)nc, d_active, nullptr, d_flag, d_excl, d_tiles};
     }
   }
@@ -1252,51 +1250,51 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     A.m = (int)m;
     int *d_base_cam, *d_base_src, *d_cam_off, *d_cam_base, *d_cam_warp_off, *d_warp_cam, *d_cam_obs, *d_slots;
     double* d_base_uv;
-    if ((s = upload(c, &c->obs_pt, base_pt, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &c->pt_off, c->h_pt_off, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_base_cam, base_cam, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_base_src, base_src, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_base_uv, base_uv, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_cam_off, cam_off, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_cam_base, cam_base, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_cam_warp_off, cam_warp_off, false)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_warp_cam, warp_cam, false)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &c->obs_pt, base_pt)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &c->pt_off, c->h_pt_off)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_base_cam, base_cam)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_base_src, base_src)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_base_uv, base_uv)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_cam_off, cam_off)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_cam_base, cam_base)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_cam_warp_off, cam_warp_off)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_warp_cam, warp_cam)) != STBA_OK) return bail(s);
     A.base_uvf = nullptr;
     A.base_uvdf = nullptr;
     if (c->mixed) {
       float* d_uvf;
       float4* d_uvdf;
-      if ((s = upload(c, &d_uvf, base_uvf, false)) != STBA_OK) return bail(s);
-      if ((s = upload(c, &d_uvdf, base_uvdf, false)) != STBA_OK) return bail(s);
+      if ((s = upload(c, &d_uvf, base_uvf)) != STBA_OK) return bail(s);
+      if ((s = upload(c, &d_uvdf, base_uvdf)) != STBA_OK) return bail(s);
       A.base_uvf = d_uvf;
       A.base_uvdf = d_uvdf;
-      if ((s = dalloc(c, &c->obs_uvf, 2 * Q, false)) != STBA_OK) return bail(s);
-      if ((s = dalloc(c, &c->obs_uvdf, Q, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &c->obs_uvf, 2 * Q)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &c->obs_uvdf, Q)) != STBA_OK) return bail(s);
     }
     int* const* ints_q[] = {&c->obs_cam, &c->obs_vp, &c->obs_perm, &c->obs_base, &c->vp_point, &c->inv[0], &c->inv[1],
                             &c->key};
     for (int* const* pp : ints_q)
-      if ((s = dalloc(c, const_cast<int**>(pp), Q, false)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, const_cast<int**>(pp), Q)) != STBA_OK) return bail(s);
     int* d_start;   // [q+1] virtual-point starts, then [q+1] the camera-list scan
-    if ((s = dalloc(c, &d_start, 2 * (Q + 1), false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->vp_off, Q + 1, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->pt_vp_off, (size_t)n + 1, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->obs_uv, 2 * Q, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &d_cam_obs, Q, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &d_slots, 32 * (size_t)nwarps, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->tile_sum, Q / 2048 + 2, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->counts, 4, false)) != STBA_OK) return bail(s);   // nv, pairs, singles, active chunks
+    if ((s = dalloc(c, &d_start, 2 * (Q + 1))) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->vp_off, Q + 1)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->pt_vp_off, (size_t)n + 1)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->obs_uv, 2 * Q)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &d_cam_obs, Q)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &d_slots, 32 * (size_t)nwarps)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->tile_sum, Q / 2048 + 2)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->counts, 4)) != STBA_OK) return bail(s);   // nv, pairs, singles, active chunks
     // failure flags at their largest size (l <= m); the other cluster arrays live in the assignment blob
-    if ((s = dalloc(c, &c->fail_flags, (size_t)m, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->fail_flags, (size_t)m)) != STBA_OK) return bail(s);
     // per-iteration scratch (virtual-point arrays at their largest size, nv <= q)
     const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
     char *vpa, *vpi, *pti, *vg, *ta, *gb;
-    if ((s = dalloc(c, &vpa, 9 * Q * rs + 16, false)) != STBA_OK) return bail(s);   // zeroed in 16-byte pieces
-    if ((s = dalloc(c, &vpi, 9 * Q * rs, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &pti, 9 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &vg, 9 * (size_t)m * rs, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &ta, 3 * (size_t)n * rs, false)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &gb, (c->use_pcg ? 1 : 36 * Q) * rs, false)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &vpa, 9 * Q * rs + 16)) != STBA_OK) return bail(s);   // zeroed in 16-byte pieces
+    if ((s = dalloc(c, &vpi, 9 * Q * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &pti, 9 * (size_t)n * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &vg, 9 * (size_t)m * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &ta, 3 * (size_t)n * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &gb, (c->use_pcg ? 1 : 36 * Q) * rs)) != STBA_OK) return bail(s);
     c->vp_acc = vpa;
     c->vp_info = vpi;
     c->pt_info = pti;
@@ -1557,7 +1555,7 @@ stba_status stba_problem_info(stba_ctx* c, int64_t* out, int32_t n) {
   for (const GrowBuf* g : {&c->g_panel, &c->g_update, &c->g_res, &c->g_diag, &c->g_S, &c->g_b, &c->g_L, &c->g_Dinv,
                            &c->g_Ldiag, &c->g_scale, &c->g_x, &c->g_r, &c->g_blob})
     grown += g->bytes;
-  const int64_t vals[12] = {c->m, c->n, c->q, c->l, c->nv, maxn, (int64_t)(c->bytes_base + c->bytes_cl + grown),
+  const int64_t vals[12] = {c->m, c->n, c->q, c->l, c->nv, maxn, (int64_t)(c->bytes_base + grown),
                             c->build_items, c->launches_per_iter, c->n_pairs, (int64_t)c->factor_flops,
                             (int64_t)s_elems};
   for (int i = 0; i < n && i < 12; ++i) out[i] = vals[i];
