@@ -461,13 +461,15 @@ def compare_full_rcs(s, stba, stream, iters, torch, max_stba_iters=100):
             ms, rm = run_pipelined(seq, hit[0] + 1)
             out[name]["time_to_target_pipelined_ms"] = ms
             out[name]["rmse_pipelined_run"] = rm
-    # the method with its split system solved by PCG instead of the cluster factorisations (Sec. 6)
-    st = run(seq_sgc[0], seq_sgc, max_stba_iters, target=target, linear_solver=stba.STBA_SOLVER_PCG_CLUSTERS)
-    hit = [i for i, r in enumerate(st["rmse"]) if r <= target]
-    out["stba_sgc_split_pcg"] = {"iters_run": len(st["rmse"]), "ms_per_iter": st["ms_per_iter"],
-                                 "final_rmse": st["rmse"][-1], "cg_iters_median": float(np.median(st["cg_iters"])),
-                                 "time_to_target_ms": st["cum_ms"][hit[0]] if hit else None,
-                                 "iters_to_target": hit[0] + 1 if hit else None}
+    # the method with its split system solved by PCG instead of the cluster factorisations (Sec. 6); on the
+    # smaller scenes only (each of its iterations costs tens of CG passes over the observations)
+    if s.m <= 2000:
+        st = run(seq_sgc[0], seq_sgc, max_stba_iters, target=target, linear_solver=stba.STBA_SOLVER_PCG_CLUSTERS)
+        hit = [i for i, r in enumerate(st["rmse"]) if r <= target]
+        out["stba_sgc_split_pcg"] = {"iters_run": len(st["rmse"]), "ms_per_iter": st["ms_per_iter"],
+                                     "final_rmse": st["rmse"][-1], "cg_iters_median": float(np.median(st["cg_iters"])),
+                                     "time_to_target_ms": st["cum_ms"][hit[0]] if hit else None,
+                                     "iters_to_target": hit[0] + 1 if hit else None}
     for name, r in res.items():
         h = [i for i, x in enumerate(r["rmse"]) if x <= target]
         out[name] = {"iters": len(r["rmse"]), "ms_per_iter": r["ms_per_iter"], "final_rmse": r["rmse"][-1],
