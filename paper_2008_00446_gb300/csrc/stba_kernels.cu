@@ -255,7 +255,7 @@ __device__ __forceinline__ real warp_transpose_sum32(real (&v)[32]) {
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real> W, CamSlots CS, real* Gbuf,
+__global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_cam_pass(DevProblem P, Scratch<real> W, CamSlots CS, real* Gbuf,
                                                   const DevState* st) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= CS.nwarps) return;   // uniform per warp
@@ -395,9 +395,10 @@ __global__ void __launch_bounds__(256, 3) k_cam_pass(DevProblem P, Scratch<real>
 // one virtual point), and a chunk adds to one block only.  The re-ordering of an assignment lists the
 // chunks whose edge lies inside a cluster; a fixed grid of warps walks that list.  A warp's work is a
 // sequence of pieces of CH pairs (the chunks it takes, cut into pieces); the G rows of the next piece are
-// copied into shared memory (cp.async, one row per lane) while the 27 lanes accumulate the current one
-// (row r, columns 3cg .. 3cg+2 of the 9x9 block, in registers); the block is added once per chunk into
-// the FP64 S'_k.
+// copied into shared memory (cp.async, one row per lane) while 27 lanes accumulate the current one: lane
+// (g, rb, cb) takes every third pair (slot g) and the 3 x 3 sub-block (rb, cb) of the 9 x 9 block, in
+// registers; the three slots are summed by two shuffles and the block is added once per chunk into the
+// FP64 S'_k.
 constexpr int PB_WARPS = 8;
 
 template <typename real> struct PairStage {
@@ -426,7 +427,8 @@ __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scra
   const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
   long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   if (w >= nactive) return;   // uniform per warp
-  const int r = lane / 3, cg = lane - (lane / 3) * 3;
+  // lanes 0..26: pair slot g = lane / 9 of every three, and the 3 x 3 sub-block (rb, cb) of the 9 x 9 block
+  const int g = lane / 9, sub = lane - 9 * (lane / 9), rb = sub / 3, cb = sub - 3 * (sub / 3);
   const bool act = lane < 27;
   const int j = lane % CH, side = lane / CH;
   // the piece (chunk record, first pair) being copied and the one being accumulated
@@ -445,7 +447,9 @@ __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scra
   };
   issue(ch, 0, 0);
   int buf = 0;
-  real acc0 = 0, acc1 = 0, acc2 = 0;
+  real acc[3][3];
+#pragma unroll
+  for (int x = 0; x < 3; ++x) acc[x][0] = acc[x][1] = acc[x][2] = real(0);
   for (;;) {
     // the next piece: the rest of this chunk, else the warp's next chunk
     int4 nch = ch;
@@ -470,33 +474,43 @@ __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scra
     if (act) {
       const int cn = min(CH, ch.w - c0);
       const real* base = stage + (size_t)buf * CH * 2 * GSTRIDE;
-      for (int jj = 0; jj < cn; ++jj) {
-        real a[3], b0[3], b1[3], b2[3];
+      for (int jj = g; jj < cn; jj += 3) {   // pair slot g of every three
         const real* ga = base + (size_t)jj * 2 * GSTRIDE;
         const real* gb = ga + GSTRIDE;
-        load_gcol_s(ga + 4 * r, a);
-        load_gcol_s(gb + 4 * (3 * cg), b0);
-        load_gcol_s(gb + 4 * (3 * cg) + 4, b1);
-        load_gcol_s(gb + 4 * (3 * cg) + 8, b2);
+        real a[3][3], b[3][3];
 #pragma unroll
-        for (int s2 = 0; s2 < 3; ++s2) {
-          acc0 += a[s2] * b0[s2];
-          acc1 += a[s2] * b1[s2];
-          acc2 += a[s2] * b2[s2];
+        for (int x = 0; x < 3; ++x) {
+          load_gcol_s(ga + 4 * (3 * rb + x), a[x]);
+          load_gcol_s(gb + 4 * (3 * cb + x), b[x]);
         }
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int y = 0; y < 3; ++y) acc[x][y] += a[x][0] * b[y][0] + a[x][1] * b[y][1] + a[x][2] * b[y][2];
       }
     }
     __syncwarp();   // every lane is done with this buffer before it is refilled
-    if (c0 + CH >= ch.w) {   // the chunk is complete: one add per block entry
-      if (act) {
+    if (c0 + CH >= ch.w) {   // the chunk is complete: sum the three pair slots, one add per block entry
+#pragma unroll
+      for (int x = 0; x < 3; ++x)
+#pragma unroll
+        for (int y = 0; y < 3; ++y) {
+          // lane L < 9 adds slots 1 and 2 from lanes L + 9 and L + 18 (source lanes wrap mod 32 for the rest)
+          const real v = acc[x][y];
+          acc[x][y] = v + __shfl_sync(FULL_MASK, v, lane + 9) + __shfl_sync(FULL_MASK, v, lane + 18);
+        }
+      if (lane < 9) {
         const int k = P.cam_cluster[ch.x];
         const int la = P.cam_local[ch.x], lb = P.cam_local[ch.y];   // la > lb: local order follows camera order
-        double* dst = W.S + P.S_off[k] + (size_t)(9 * la + r) * P.cluster_np[k] + 9 * lb + 3 * cg;
-        atomicAdd(dst, -(double)acc0);
-        atomicAdd(dst + 1, -(double)acc1);
-        atomicAdd(dst + 2, -(double)acc2);
+        const int np = P.cluster_np[k];
+        double* dst = W.S + P.S_off[k] + (size_t)(9 * la + 3 * rb) * np + 9 * lb + 3 * cb;
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int y = 0; y < 3; ++y) atomicAdd(dst + (size_t)x * np + y, -(double)acc[x][y]);
       }
-      acc0 = acc1 = acc2 = 0;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) acc[x][0] = acc[x][1] = acc[x][2] = real(0);
       if (!more) break;
       w += wstride;
     }
