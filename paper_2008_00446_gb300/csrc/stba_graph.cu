@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -108,13 +110,21 @@ void build_camera_graph(int m, int n, const std::vector<int>& pt_off, const std:
 // dQ(X, Y) = (W_XY - P_XY / (2s)) / (2s) with W_XY the weight and P_XY the sum of k_i k_j over the camera
 // edges between X and Y.  The process ends when no join is allowed.
 //
-// Sampling: the allowed cluster pairs are kept in a list, one entry each; an entry drawn uniformly is
-// accepted with probability exp(beta (dQ - B)), B >= every dQ of the list, which makes the accepted pair
-// follow Eq. 16 exactly (rejection sampling).  Pairs that stopped being allowed (a side grew) are dropped
-// from the list when drawn, since sizes only grow.  B is the largest dQ seen so far; after a run of
-// rejections it is recomputed from the list.  Cluster pairs are found through one open-addressing table
-// keyed by the two cluster ids; every cluster keeps the list of its incident pair records, and a join
-// walks the shorter list of the two.
+// Sampling: every neighbouring cluster pair has one record (W, P and its two clusters, which are always
+// the current roots); the records of allowed pairs are in a list.  An entry drawn uniformly is accepted
+// with probability exp(beta (dQ - B)), B >= every dQ of the list, which makes the accepted pair follow
+// Eq. 16 exactly (rejection sampling).  Entries whose record died (merged into another pair) or whose pair
+// stopped being allowed (a side grew; sizes only grow) are removed when drawn.  B is the largest dQ seen
+// so far; after a run of rejections it is recomputed from the list.
+//
+// A join moves the records of the cluster with the shorter record list to the other cluster: a record
+// (small, z) merges into the existing record (big, z), or becomes (big, z).  The existing record is found
+// without a global table for the pairs that never moved: a pair of current roots (big, z) is either the
+// untouched camera edge big-z (every camera edge keeps its record until one of its two cameras stops
+// being a root) or a record that moved, and moved records are kept in a small table keyed by their two
+// roots.  The camera edges of camera `big` are marked in a per-camera array during the join, so that
+// lookup touches no memory outside the walked records but the small table.  The initial records and the
+// camera-edge lists are the same for every draw and are built once per graph.
 namespace {
 
 struct SplitMix64 {   // Steele, Lea and Flood, "Fast splittable pseudorandom number generators" (2014)
@@ -129,136 +139,154 @@ struct SplitMix64 {   // Steele, Lea and Flood, "Fast splittable pseudorandom nu
   size_t below(size_t n) { return (size_t)(uniform() * (double)n); }
 };
 
-struct JoinEdge {
-  int a, b;       // clusters (root cameras)
-  double W, P;    // sum of w_ij and of k_i k_j over the camera edges between them
-  int pos;        // index in the list of allowed pairs, -1 once it is dropped
-  bool alive;
-};
-
-// (cluster, cluster) -> pair record; linear probing with tombstones, rebuilt when half full
-struct PairTable {
-  static constexpr uint64_t EMPTY = ~0ull, TOMB = ~0ull - 1;
-  std::vector<uint64_t> key;
-  std::vector<int> val;
+// (cluster, cluster) -> record of a moved pair; linear probing, key and value in one 16-byte slot.  Keys
+// are never erased: a key whose cluster stopped being a root is never asked for again (cluster ids are
+// camera ids and a joined cluster never comes back), and the rehash drops such keys.
+struct MovedTable {
+  static constexpr uint64_t EMPTY = ~0ull;
+  struct Slot {
+    uint64_t key;
+    int64_t val;
+  };
+  std::vector<Slot> slot;
   size_t mask = 0, used = 0;
-  static uint64_t k(int a, int b) {
+  static uint64_t key_of(int a, int b) {
     return a < b ? ((uint64_t)(uint32_t)a << 32) | (uint32_t)b : ((uint64_t)(uint32_t)b << 32) | (uint32_t)a;
   }
-  static size_t h(uint64_t x) {
+  static size_t hash(uint64_t x) {
     x ^= x >> 33;
     x *= 0xff51afd7ed558ccdull;
     x ^= x >> 33;
     return (size_t)x;
   }
-  void init(size_t n) {
+  void init(size_t n) {   // room for n keys at a load of at most 1/2
     size_t cap = 16;
-    while (cap < 4 * n) cap <<= 1;
-    key.assign(cap, EMPTY);
-    val.assign(cap, -1);
+    while (cap < 2 * n) cap <<= 1;
+    slot.assign(cap, Slot{EMPTY, -1});
     mask = cap - 1;
     used = 0;
   }
   int find(int a, int b) const {
-    const uint64_t x = k(a, b);
-    for (size_t i = h(x) & mask;; i = (i + 1) & mask) {
-      if (key[i] == x) return val[i];
-      if (key[i] == EMPTY) return -1;
+    const uint64_t x = key_of(a, b);
+    for (size_t i = hash(x) & mask;; i = (i + 1) & mask) {
+      if (slot[i].key == x) return (int)slot[i].val;
+      if (slot[i].key == EMPTY) return -1;
     }
   }
   void insert(int a, int b, int v) {   // the key must be absent
-    const uint64_t x = k(a, b);
-    size_t i = h(x) & mask;
-    while (key[i] != EMPTY && key[i] != TOMB) i = (i + 1) & mask;
-    if (key[i] == EMPTY) ++used;
-    key[i] = x;
-    val[i] = v;
-  }
-  void erase(int a, int b) {
-    const uint64_t x = k(a, b);
-    for (size_t i = h(x) & mask;; i = (i + 1) & mask) {
-      if (key[i] == x) {
-        key[i] = TOMB;
-        return;
-      }
-      if (key[i] == EMPTY) return;
-    }
+    const uint64_t x = key_of(a, b);
+    size_t i = hash(x) & mask;
+    while (slot[i].key != EMPTY) i = (i + 1) & mask;
+    ++used;
+    slot[i] = Slot{x, v};
   }
 };
 
+struct alignas(32) PairRec {   // a neighbouring cluster pair: its clusters (a = -1 once dead) and W, P
+  int a, b;
+  double W, P;
+};
+
+std::mutex g_sgc_base_mutex;
+
 }  // namespace
 
-void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t seed, int* labels, int* nclusters) {
+// The state every draw on one graph starts from (read-only, shared by the draws of a batch).
+struct SgcBase {
+  int m = 0, E = 0;
+  double two_s = 0.0, B0 = -INFINITY;   // 2 s, and the largest dQ over the camera edges
+  std::vector<PairRec> rec;              // one record per camera edge
+  std::vector<int> inc_off;              // camera -> its camera edges (CSR)
+  std::vector<int2> inc;                 // (camera edge, partner camera)
+};
+
+static std::shared_ptr<const SgcBase> sgc_base(const CameraGraph& g, int m) {
+  std::lock_guard<std::mutex> lock(g_sgc_base_mutex);
+  if (g.sgc_base) return g.sgc_base;
+  auto S = std::make_shared<SgcBase>();
   const int E = (int)g.edge_y.size();
+  S->m = m;
+  S->E = E;
   std::vector<double> k(m, 0.0);
-  std::vector<int> deg(m, 0);
+  S->inc_off.assign(m + 1, 0);
   double s = 0.0;
   for (int x = 0; x < m; ++x)
     for (int e = g.edge_off[x]; e < g.edge_off[x + 1]; ++e) {
       const int y = g.edge_y[e];
       k[x] += g.edge_w[e];
       k[y] += g.edge_w[e];
-      deg[x]++;
-      deg[y]++;
+      S->inc_off[x + 1]++;
+      S->inc_off[y + 1]++;
       s += g.edge_w[e];
     }
-  std::vector<int> parent(m), size(m, 1);
-  for (int i = 0; i < m; ++i) parent[i] = i;
-  std::vector<JoinEdge> edges(E);
-  std::vector<std::vector<int>> inc(m);
-  for (int i = 0; i < m; ++i) inc[i].reserve(deg[i]);
-  PairTable table;
-  table.init(E);
-  std::vector<int> list;
-  list.reserve(E);
-  const double two_s = 2.0 * s;
-  auto dq = [&](const JoinEdge& e) { return (e.W - e.P / two_s) / two_s; };
-  double B = -INFINITY;
+  for (int x = 0; x < m; ++x) S->inc_off[x + 1] += S->inc_off[x];
+  S->inc.resize(2 * (size_t)E);
+  std::vector<int> fill(S->inc_off.begin(), S->inc_off.end() - 1);
+  S->rec.resize(E);
+  S->two_s = 2.0 * s;
   for (int x = 0; x < m; ++x)
     for (int e = g.edge_off[x]; e < g.edge_off[x + 1]; ++e) {
       const int y = g.edge_y[e];
-      edges[e] = JoinEdge{x, y, (double)g.edge_w[e], k[x] * k[y], -1, true};
-      inc[x].push_back(e);
-      inc[y].push_back(e);
-      table.insert(x, y, e);
-      if (gamma >= 2) {
-        edges[e].pos = (int)list.size();
-        list.push_back(e);
-        B = std::max(B, dq(edges[e]));
-      }
+      S->rec[e] = PairRec{x, y, (double)g.edge_w[e], k[x] * k[y]};
+      S->inc[fill[x]++] = make_int2(e, y);
+      S->inc[fill[y]++] = make_int2(e, x);
+      S->B0 = std::max(S->B0, (S->rec[e].W - S->rec[e].P / S->two_s) / S->two_s);
     }
-  auto drop = [&](int e) {   // O(1) removal from the list of allowed pairs
-    const int p = edges[e].pos;
-    if (p < 0) return;
-    const int last = list.back();
-    list[p] = last;
-    edges[last].pos = p;
-    list.pop_back();
-    edges[e].pos = -1;
-  };
-  auto rebuild = [&]() {
-    table.init(E);
-    for (int e = 0; e < E; ++e)
-      if (edges[e].alive) table.insert(edges[e].a, edges[e].b, e);
+  g.sgc_base = S;
+  return S;
+}
+
+static void sgc_draw(const SgcBase& S, int gamma, double beta, uint64_t seed, int* labels, int* nclusters) {
+  const int m = S.m, E = S.E;
+  const double two_s = S.two_s;
+  auto dq = [&](const PairRec& e) { return (e.W - e.P / two_s) / two_s; };
+  std::vector<PairRec> rec(S.rec);
+  std::vector<int> parent(m), size(m, 1), mark(m, -1);
+  for (int i = 0; i < m; ++i) parent[i] = i;
+  std::vector<std::vector<int>> extra(m);   // records moved to a cluster (besides its camera's edges)
+  MovedTable moved;
+  moved.init(1024);
+  std::vector<int> list;   // entries: allowed pairs (and, until drawn, dead or no longer allowed ones)
+  if (gamma >= 2) {
+    list.resize(E);
+    for (int e = 0; e < E; ++e) list[e] = e;
+  }
+  double B = S.B0;
+  auto rehash = [&]() {   // keep the keys whose two clusters still exist
+    MovedTable nt;
+    nt.init(std::max<size_t>(1024, 2 * moved.used));
+    for (const auto& sl : moved.slot)
+      if (sl.key != MovedTable::EMPTY) {
+        const int x = (int)(sl.key >> 32), y = (int)(sl.key & 0xffffffffu);
+        if (parent[x] == x && parent[y] == y) nt.insert(x, y, (int)sl.val);
+      }
+    moved = std::move(nt);
   };
   SplitMix64 rng{seed};
   int rejections = 0;
+  std::vector<int> walk;
+  // the next entry's index is drawn one step ahead and its record fetched early; if the list shrank below
+  // it meanwhile a fresh index is drawn, which keeps every draw uniform over the current list
+  size_t rn = list.empty() ? 0 : rng.below(list.size());
   while (!list.empty()) {
-    const size_t r = rng.below(list.size());
+    size_t r = rn < list.size() ? rn : rng.below(list.size());
+    rn = rng.below(list.size());
+    __builtin_prefetch(&rec[list[rn]]);
     const int ei = list[r];
-    JoinEdge& e = edges[ei];
-    if (size[e.a] + size[e.b] > gamma) {   // a side grew past the cap: no longer an allowed join
-      drop(ei);
+    PairRec& e = rec[ei];
+    if (e.a < 0 || size[e.a] + size[e.b] > gamma) {   // merged into another pair, or no longer allowed
+      list[r] = list.back();
+      list.pop_back();
       continue;
     }
-    const double d = dq(e);
-    if (!(rng.uniform() < std::exp(beta * (d - B)))) {
+    if (!(rng.uniform() < std::exp(beta * (dq(e) - B)))) {
       if (++rejections >= 64) {   // tighten the bound to the largest dQ still in the list
         double nb = -INFINITY;
         for (size_t t = 0; t < list.size();) {
-          const JoinEdge& f = edges[list[t]];
-          if (size[f.a] + size[f.b] > gamma) {
-            drop(list[t]);
+          const PairRec& f = rec[list[t]];
+          if (f.a < 0 || size[f.a] + size[f.b] > gamma) {
+            list[t] = list.back();
+            list.pop_back();
             continue;
           }
           nb = std::max(nb, dq(f));
@@ -270,34 +298,43 @@ void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t se
       continue;
     }
     rejections = 0;
+    list[r] = list.back();
+    list.pop_back();
     // join: the records of the cluster with the shorter list move to the other one
     int big = e.a, small = e.b;
-    if (inc[big].size() < inc[small].size()) std::swap(big, small);
-    e.alive = false;
-    drop(ei);
-    table.erase(big, small);
-    for (const int ez : inc[small]) {
-      JoinEdge& f = edges[ez];
-      if (!f.alive) continue;
+    auto len = [&](int x) { return (size_t)(S.inc_off[x + 1] - S.inc_off[x]) + extra[x].size(); };
+    if (len(big) < len(small)) std::swap(big, small);
+    e.a = -1;
+    walk.clear();
+    for (int u = S.inc_off[small]; u < S.inc_off[small + 1]; ++u) walk.push_back(S.inc[u].x);
+    walk.insert(walk.end(), extra[small].begin(), extra[small].end());
+    std::vector<int>().swap(extra[small]);
+    for (int u = S.inc_off[big]; u < S.inc_off[big + 1]; ++u) mark[S.inc[u].y] = S.inc[u].x;
+    const int nw = (int)walk.size();
+    constexpr int D = 8;   // records are fetched D entries ahead of their use
+    for (int i = 0; i < std::min(nw, D); ++i) __builtin_prefetch(&rec[walk[i]]);
+    for (int i = 0; i < nw; ++i) {
+      if (i + D < nw) __builtin_prefetch(&rec[walk[i + D]]);
+      PairRec& f = rec[walk[i]];
+      if (f.a < 0) continue;
       const int z = f.a == small ? f.b : f.a;
-      table.erase(small, z);
-      const int t = table.find(big, z);
+      int t = mark[z];   // the camera edge big-z, untouched while both are roots
+      if (t < 0) t = moved.find(big, z);
       if (t >= 0) {   // both sides touch z: the two cluster pairs become one
-        edges[t].W += f.W;
-        edges[t].P += f.P;
-        f.alive = false;
-        drop(ez);
-        B = std::max(B, dq(edges[t]));
+        rec[t].W += f.W;
+        rec[t].P += f.P;
+        f.a = -1;
+        B = std::max(B, dq(rec[t]));
       } else {
         if (f.a == small) f.a = big; else f.b = big;
-        table.insert(big, z, ez);
-        inc[big].push_back(ez);
+        moved.insert(big, z, walk[i]);
+        extra[big].push_back(walk[i]);
       }
     }
-    std::vector<int>().swap(inc[small]);
+    for (int u = S.inc_off[big]; u < S.inc_off[big + 1]; ++u) mark[S.inc[u].y] = -1;
     parent[small] = big;
     size[big] += size[small];
-    if (2 * table.used > table.mask) rebuild();
+    if (2 * moved.used > moved.mask) rehash();
   }
   // clusters numbered by their smallest camera
   auto root = [&](int i) {
@@ -314,11 +351,17 @@ void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t se
   *nclusters = l;
 }
 
+void sgc_sample(const CameraGraph& g, int m, int gamma, double beta, uint64_t seed, int* labels, int* nclusters) {
+  const auto S = sgc_base(g, m);
+  sgc_draw(*S, gamma, beta, seed, labels, nclusters);
+}
+
 void sgc_sample_batch(const CameraGraph& g, int m, int gamma, double beta, uint64_t seed, int count, int* labels,
                       int* nclusters) {
+  const auto S = sgc_base(g, m);
   parallel_ranges(count * 64, [&](int b, int e) {
     for (int t = (b + 63) / 64; t < (e + 63) / 64 && t < count; ++t)
-      sgc_sample(g, m, gamma, beta, seed + (uint64_t)t, labels + (size_t)t * m, nclusters + t);
+      sgc_draw(*S, gamma, beta, seed + (uint64_t)t, labels + (size_t)t * m, nclusters + t);
   });
 }
 

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "../../include/stba.h"
@@ -117,12 +118,14 @@ constexpr int PAIR_CHUNK = 64;
 // Camera graph (stba_graph.cu): edges (x, y), y < x, grouped by x with y ascending; weight = number of
 // common points; the observation pairs of each edge (base positions, observations sorted by (point,
 // camera)), ordered by point.
+struct SgcBase;   // the initial state of stochastic graph clustering on a graph (stba_graph.cu)
 struct CameraGraph {
   std::vector<int> edge_off;       // [m+1]
   std::vector<int> edge_y;         // [E]
   std::vector<int> edge_w;         // [E]
   std::vector<int64_t> pair_off;   // [E+1]
   std::vector<int2> pairs;         // [P]
+  mutable std::shared_ptr<const SgcBase> sgc_base;   // built on the first draw
 };
 void build_camera_graph(int m, int n, const std::vector<int>& pt_off, const std::vector<int>& base_cam,
                         CameraGraph& g, bool with_pairs);

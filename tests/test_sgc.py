@@ -139,3 +139,59 @@ def test_invalid_arguments():
         stba.stba_graph_create(5, 20, np.append(oc, 7), np.append(op, 0))
     with pytest.raises(stba.StbaError):
         stba.stba_graph_create(5, 20, np.append(oc, oc[0]), np.append(op, op[0]))
+
+
+def test_dense_graph_draws_are_valid():
+    # 300 cameras, about 8k camera edges: many records move and merge, and the moved-pair table rehashes
+    oc, op = random_obs(300, 6000, 9, lo=2, hi=9)
+    g = stba.stba_graph_create(300, 6000, oc, op)
+    w = edge_dict(g)
+    for gamma in (10, 40):
+        labs, ls = stba.stba_graph_cluster_batch(g, 4, gamma=gamma, beta=10.0, seed=2)
+        for lab, l in zip(labs, ls):
+            check_clustering(w, 300, gamma, lab, l)
+
+
+@pytest.mark.parametrize("m, n, seed", [(24, 150, 5), (60, 500, 6)])
+def test_greedy_limit_on_larger_graphs(m, n, seed):
+    # beta so large that every join is the one with the largest dQ: the merged pair sums (W, P) decide
+    # every step, so a wrong merge of two records changes the result
+    oc, op = random_obs(m, n, seed)
+    g = stba.stba_graph_create(m, n, oc, op)
+    w = edge_dict(g)
+    expect = sgc.greedy(w, m, 6)
+    for s in range(3):
+        lab, l = stba.stba_graph_cluster(g, gamma=6, beta=1e12, seed=s)
+        assert list(lab) == expect
+
+
+def test_co_clustering_frequencies_match_the_oracle_sampler():
+    # 24 cameras on a banded ring: the probability that two cameras end in one cluster, native draws
+    # against the oracle's sampler (Eq. 16 step by step), for every camera pair
+    m = 24
+    rng = np.random.default_rng(3)
+    oc, op = [], []
+    for i in range(150):   # banded ring: a point is seen by a camera and 1..3 of its successors
+        c0 = int(rng.integers(m))
+        for d in range(int(rng.integers(2, 5))):
+            oc.append((c0 + d) % m)
+            op.append(i)
+    oc, op = np.array(oc, np.int32), np.array(op, np.int32)
+    g = stba.stba_graph_create(m, 150, oc, op)
+    w = edge_dict(g)
+    rng = np.random.default_rng(4)
+    n_or, n_nat = 300, 6000
+    co_or = np.zeros((m, m))
+    for _ in range(n_or):
+        lab = np.asarray(sgc.sample(w, m, 5, 10.0, rng.random(m)))
+        co_or += lab[:, None] == lab[None, :]
+    labs, _ = stba.stba_graph_cluster_batch(g, n_nat, gamma=5, beta=10.0, seed=77)
+    co_nat = np.zeros((m, m))
+    for lab in labs:
+        co_nat += lab[:, None] == lab[None, :]
+    p_or, p_nat = co_or / n_or, co_nat / n_nat
+    p = (co_or + co_nat) / (n_or + n_nat)
+    se = np.sqrt(p * (1 - p) * (1 / n_or + 1 / n_nat)) + 1e-12
+    iu = np.triu_indices(m, 1)
+    assert np.max(np.abs(p_or - p_nat)[iu] / se[iu]) < 5.0
+    assert np.ptp(p[iu]) > 0.3   # near cameras share clusters, far ones never: the statistic is not flat
