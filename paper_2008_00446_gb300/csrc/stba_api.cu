@@ -322,6 +322,18 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   for (int j = 0; j < m; ++j) cnt[cl[j]]++;
   for (int k = 0; k < l; ++k)
     if (cnt[k] == 0) return fail(c, STBA_ERR_INVALID_ARG, "cluster %d has no camera (ids must be 0..l-1)", k);
+  if (!c->use_pcg && !c->use_spcg) {   // the cluster solve keeps a cluster's vector in shared memory
+    int big = 0;
+    for (int k = 0; k < l; ++k) big = std::max(big, (9 * cnt[k] + c->tile - 1) / c->tile * c->tile);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t need = solve_smem_bytes(c->mixed, c->tile, big);
+    if (optin > 0 && need > (size_t)optin)
+      return fail(c, STBA_ERR_INVALID_ARG,
+                  "a cluster of %d unknowns needs %zu bytes of shared memory in the cluster solve (limit %d); "
+                  "use smaller clusters or a PCG solver", big, need, optin);
+  }
 
   c->graph_stale = true;   // recaptured by the next iteration (and updated in place when its shape allows)
   c->l = l;

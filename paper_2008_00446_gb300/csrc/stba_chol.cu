@@ -85,20 +85,87 @@ __device__ __forceinline__ void load_vec(const F* p, F (&v)[R]) {
   }
 }
 
-// Asynchronous global -> shared copies of one element (4 or 8 bytes), so that all the loads of a tile are
-// in flight at once and may land at transposed positions.
-template <typename F>
-__device__ __forceinline__ void cp_async_elem(F* smem_dst, const F* gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  if constexpr (sizeof(F) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+// 16 bytes (R = 4 floats or 2 doubles, or a smaller aligned run) from global memory, cached in L2 only.
+template <typename F, int R>
+__device__ __forceinline__ void ld_global_vec(const F* p, F (&v)[R]) {
+  if constexpr (sizeof(F) == 4 && R == 4) {
+    const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  } else if constexpr (sizeof(F) == 4 && R == 2) {
+    const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else if constexpr (sizeof(F) == 8 && R == 2) {
+    const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
+    v[0] = t.x;
+    v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int a = 0; a < R; ++a) v[a] = p[a];
+  }
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+template <typename F, int R>
+__device__ __forceinline__ void st_global_vec(F* p, const F (&v)[R]) {
+  if constexpr (sizeof(F) == 4 && R == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (sizeof(F) == 4 && R == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (sizeof(F) == 8 && R == 2) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int a = 0; a < R; ++a) p[a] = v[a];
+  }
 }
+
+// A T x T tile of the factor (row stride ld, 16-byte aligned rows) held in registers by a block of 256
+// threads, 16 bytes per load: load() issues every load of the tile, so that the loads of several tiles are
+// in flight together; the stores put it into shared memory row-major (lanes along a row) or transposed
+// (lanes down a column chunk, so that consecutive lanes store consecutive addresses).
+template <typename F, int T>
+struct TileRegs {
+  static constexpr int V = 16 / (int)sizeof(F), CH = T / V, N = T * CH / 256;
+  static_assert(T * CH % 256 == 0, "tile not a whole number of 16-byte loads per thread");
+  F e[N][V];
+  __device__ __forceinline__ void load_rows(const F* src, size_t ld) {
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      const int q = threadIdx.x + 256 * u, r = q / CH, ch = q - (q / CH) * CH;
+      ld_global_vec<F, V>(src + (size_t)r * ld + ch * V, e[u]);
+    }
+  }
+  template <int LD>
+  __device__ __forceinline__ void store_rows(F (*dst)[LD], bool lower_only) const {
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      const int q = threadIdx.x + 256 * u, r = q / CH, ch = q - (q / CH) * CH;
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        const int c = ch * V + v;
+        dst[r][c] = (lower_only && c > r) ? F(0) : e[u][v];
+      }
+    }
+  }
+  __device__ __forceinline__ void load_cols(const F* src, size_t ld) {
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      const int q = threadIdx.x + 256 * u, r = q % T, ch = q / T;
+      ld_global_vec<F, V>(src + (size_t)r * ld + ch * V, e[u]);
+    }
+  }
+  template <int LD>
+  __device__ __forceinline__ void store_transposed(F (*dst)[LD]) const {   // after load_cols
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      const int q = threadIdx.x + 256 * u, r = q % T, ch = q / T;
+#pragma unroll
+      for (int v = 0; v < V; ++v) dst[ch * V + v][r] = e[u][v];
+    }
+  }
+};
 
 __device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_w(double x) { return rsqrt(x); }
@@ -190,20 +257,23 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
   const int bi = tid & 15, bj = tid >> 4;
   const size_t base_kk = (size_t)(kt * T) * np + kt * T;
   const size_t base_ik = (size_t)(i * T) * np + kt * T;
-  // 1. loads; the upper part of the diagonal tile is never stored, so it is set to zero
-  for (int idx = tid; idx < T * T; idx += 256) {
-    const int r = idx / T, c = idx - (idx / T) * T;
-    if (c <= r)
-      cp_async_elem(&Ad[r][c], A + base_kk + (size_t)r * np + c);
-    else
-      Ad[r][c] = F(0);
-    if (!diag) cp_async_elem(&Ax[r][c], A + base_ik + (size_t)r * np + c);
+  // 1. loads, every tile's in flight at once; the upper part of the diagonal tile is never stored, so it
+  //    is set to zero
+  {
+    TileRegs<F, T> gd, gx, gk, gi;
+    gd.load_rows(A + base_kk, np);
+    if (!diag) gx.load_rows(A + base_ik, np);
     if (kt > 0) {
-      cp_async_elem(&LkT[c][r], A + base_kk - T + (size_t)r * np + c);
-      if (!diag) cp_async_elem(&LiT[c][r], A + base_ik - T + (size_t)r * np + c);
+      gk.load_cols(A + base_kk - T, np);
+      if (!diag) gi.load_cols(A + base_ik - T, np);
+    }
+    gd.store_rows(Ad, true);
+    if (!diag) gx.store_rows(Ax, false);
+    if (kt > 0) {
+      gk.store_transposed(LkT);
+      if (!diag) gi.store_transposed(LiT);
     }
   }
-  cp_async_wait_all();
   __syncthreads();
   if (kt > 0) {
     F accD[R][R], accX[R][R];
@@ -419,14 +489,19 @@ __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const i
   const int np = P.cluster_np[k];
   F* A = L + P.S_off[k];
   const size_t bi = (size_t)(i * T) * np + kt * T, bj = (size_t)(j * T) * np + kt * T;
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int r = idx / T, c = idx - (idx / T) * T;
-    cp_async_elem(&LiT[c][r], A + bi + (size_t)r * np + c);
-    cp_async_elem(&LjT[c][r], A + bj + (size_t)r * np + c);
-  }
-  cp_async_wait_all();
-  __syncthreads();
   const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+  const size_t bij = (size_t)(i * T) * np + j * T;
+  F cur[R][R];   // this thread's block of A_ij, fetched before the product so that its latency is hidden
+  {
+    TileRegs<F, T> gi, gj;
+    gi.load_cols(A + bi, np);
+    gj.load_cols(A + bj, np);
+#pragma unroll
+    for (int a = 0; a < R; ++a) ld_global_vec<F, R>(A + bij + (size_t)(tr * R + a) * np + tc * R, cur[a]);
+    gi.store_transposed(LiT);
+    gj.store_transposed(LjT);
+  }
+  __syncthreads();
   F acc[R][R];
 #pragma unroll
   for (int a = 0; a < R; ++a)
@@ -442,11 +517,12 @@ __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const i
 #pragma unroll
       for (int b = 0; b < R; ++b) acc[a][b] += av[a] * bv[b];
   }
-  const size_t bij = (size_t)(i * T) * np + j * T;
 #pragma unroll
-  for (int a = 0; a < R; ++a)
+  for (int a = 0; a < R; ++a) {
 #pragma unroll
-    for (int b = 0; b < R; ++b) A[bij + (size_t)(tr * R + a) * np + tc * R + b] -= acc[a][b];
+    for (int b = 0; b < R; ++b) cur[a][b] -= acc[a][b];
+    st_global_vec<F, R>(A + bij + (size_t)(tr * R + a) * np + tc * R, cur[a]);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -463,17 +539,19 @@ __device__ F warp_sum(F v) {
 // it with j = rank mod CS for the forward pass, tile rows j > it for the backward pass), the partials are
 // exchanged through distributed shared memory after one cluster barrier, and every CTA applies the stored
 // inverse of the diagonal tile redundantly, so the next step needs no further synchronisation.  The tiles
-// do not depend on the vector: the owned tiles of step it + 1 (up to SOLVE_PF of them) and its diagonal
-// inverse are copied into shared memory (cp.async, double-buffered) while step it computes.
+// do not depend on the vector: the owned tiles of steps it + 1 and it + 2 (up to SOLVE_PF of them each)
+// and their diagonal inverses are copied into shared memory (cp.async, three stages) while step it
+// computes.
 constexpr int SOLVE_CS = 8;
 constexpr int SOLVE_PF = 2;
+constexpr int SOLVE_STAGES = 3;
 
 template <typename F, int T>
 struct SolveLayout {
   static constexpr int LDT = T + 16 / (int)sizeof(F);   // padded rows, 16-byte aligned
   static constexpr size_t tile_elems = (size_t)T * LDT;
-  // [2 buffers][SOLVE_PF tiles + 1 diagonal inverse][T][LDT], then the vector y
-  static constexpr size_t fixed_bytes = sizeof(F) * 2 * (SOLVE_PF + 1) * tile_elems;
+  // [SOLVE_STAGES][SOLVE_PF tiles + 1 diagonal inverse][T][LDT], then the vector y
+  static constexpr size_t fixed_bytes = sizeof(F) * SOLVE_STAGES * (SOLVE_PF + 1) * tile_elems;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -481,7 +559,7 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
 // T x T tile at src (row stride ld elements) into padded shared rows
 template <typename F, int T>
@@ -516,8 +594,8 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   constexpr int PARTS = 256 / T, LEN = T / PARTS, LDT = SL::LDT;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  F* buf = reinterpret_cast<F*>(smem_raw);                   // [2][SOLVE_PF + 1][T][LDT]
-  F* y = buf + 2 * (SOLVE_PF + 1) * SL::tile_elems;
+  F* buf = reinterpret_cast<F*>(smem_raw);                   // [SOLVE_STAGES][SOLVE_PF + 1][T][LDT]
+  F* y = buf + SOLVE_STAGES * (SOLVE_PF + 1) * SL::tile_elems;
   __shared__ F partial[2][T];
   __shared__ F t[T];
   __shared__ F pcol[PARTS][T];
@@ -532,7 +610,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   double* xk = x + P.v_off[k];
   const int nt = np / T;
   const int tid = threadIdx.x;
-  auto tile_buf = [&](int parity, int slot) { return buf + ((size_t)parity * (SOLVE_PF + 1) + slot) * SL::tile_elems; };
+  auto tile_buf = [&](int stage, int slot) { return buf + ((size_t)stage * (SOLVE_PF + 1) + slot) * SL::tile_elems; };
   // step s = 0 .. 2 nt - 1: forward steps it = s, backward steps it = 2 nt - 1 - s
   auto issue = [&](int s) {
     if (s < 2 * nt) {
@@ -541,21 +619,23 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
       int m = 0;
       if (fwd) {
         for (int j = rank; j < it && m < SOLVE_PF; j += SOLVE_CS, ++m)
-          prefetch_tile<F, T>(tile_buf(s & 1, m), A + (size_t)(it * T) * np + j * T, np);
+          prefetch_tile<F, T>(tile_buf(s % SOLVE_STAGES, m), A + (size_t)(it * T) * np + j * T, np);
       } else {
         for (int j = it + 1 + rank; j < nt && m < SOLVE_PF; j += SOLVE_CS, ++m)
-          prefetch_tile<F, T>(tile_buf(s & 1, m), A + (size_t)(j * T) * np + it * T, np);
+          prefetch_tile<F, T>(tile_buf(s % SOLVE_STAGES, m), A + (size_t)(j * T) * np + it * T, np);
       }
-      prefetch_tile<F, T>(tile_buf(s & 1, SOLVE_PF), (fwd ? Di : DiT) + (size_t)it * T * T, T);
+      prefetch_tile<F, T>(tile_buf(s % SOLVE_STAGES, SOLVE_PF), (fwd ? Di : DiT) + (size_t)it * T * T, T);
     }
     cp_async_commit();
   };
   issue(0);
+  issue(1);
   for (int i = tid; i < np; i += blockDim.x) y[i] = (F)((double)rk[i] * sk[i]);
   for (int s = 0; s < 2 * nt; ++s) {
-    issue(s + 1);
-    cp_async_wait1();
+    issue(s + 2);   // into the stage step s - 1 used; every thread passed its last barrier
+    cp_async_wait2();
     __syncthreads();
+    const int st = s % SOLVE_STAGES;
     const bool fwd = s < nt;
     const int it = fwd ? s : 2 * nt - 1 - s;
     const int r0 = it * T;
@@ -567,7 +647,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
       for (int j = rank; j < it; j += SOLVE_CS, ++m) {
         const F* yj = y + j * T + part * LEN;
         if (m < SOLVE_PF) {
-          const F* row = tile_buf(s & 1, m) + (size_t)r * LDT + part * LEN;
+          const F* row = tile_buf(st, m) + (size_t)r * LDT + part * LEN;
 #pragma unroll
           for (int c = 0; c < LEN; ++c) acc += row[c] * yj[c];
         } else {
@@ -587,7 +667,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
       for (int j = it + 1 + rank; j < nt; j += SOLVE_CS, ++m) {
         const F* zj = y + j * T + part * LEN;
         if (m < SOLVE_PF) {
-          const F* col = tile_buf(s & 1, m) + (size_t)(part * LEN) * LDT + c;
+          const F* col = tile_buf(st, m) + (size_t)(part * LEN) * LDT + c;
 #pragma unroll
           for (int rr = 0; rr < LEN; ++rr) acc += col[(size_t)rr * LDT] * zj[rr];
         } else {
@@ -614,7 +694,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
     }
     __syncthreads();
     // y_it = D_it^-1 t (forward) or D_it^-T t (backward, through the stored transpose)
-    smem_matvec<F, T>(tile_buf(s & 1, SOLVE_PF), t, y + r0);
+    smem_matvec<F, T>(tile_buf(st, SOLVE_PF), t, y + r0);
     __syncthreads();
   }
   if (rank == 0)
@@ -820,6 +900,12 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
     launch_solve_t<F, 64>(P, S, b, fb, plan, refine_steps, dc, dcf, stream);
   else
     launch_solve_t<F, 32>(P, S, b, fb, plan, refine_steps, dc, dcf, stream);
+}
+
+size_t solve_smem_bytes(bool mixed, int tile, int max_np) {
+  if (!mixed) return SolveLayout<double, 32>::fixed_bytes + sizeof(double) * (size_t)max_np;
+  return (tile == 64 ? SolveLayout<float, 64>::fixed_bytes : SolveLayout<float, 32>::fixed_bytes) +
+         sizeof(float) * (size_t)max_np;
 }
 
 void configure_solve_kernels(int max_np) {
