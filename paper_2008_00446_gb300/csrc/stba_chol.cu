@@ -830,6 +830,16 @@ void launch_prio(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
+// A panel CTA is bound by the latency of its column chain: a second panel CTA on the same SM would halve
+// the speed of both.  Its dynamic shared memory is therefore raised above half of an SM's, so that the CTAs
+// of a tile step take one SM each (set from the device's figures by configure_solve_kernels).
+static size_t g_panel_min_smem = 0;
+
+template <typename F, int T>
+size_t panel_smem() {
+  return std::max(PanelLayout<F, T>::bytes, g_panel_min_smem);
+}
+
 template <typename F, int T>
 void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& fb, const CholPlan& plan,
                      cudaStream_t stream) {
@@ -849,7 +859,7 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
     if (kt >= 2) cudaStreamWaitEvent(stream, plan.ev_update[kt - 2], 0);
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
     if (npn > 0)
-      launch_prio(k_chol_panel<F, T>, npn, PanelLayout<F, T>::bytes, stream, plan.prio_high, L,
+      launch_prio(k_chol_panel<F, T>, npn, panel_smem<F, T>(), stream, plan.prio_high, L,
                   reinterpret_cast<F*>(fb.Ldiag), P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags,
                   fb.boosted);
     cudaEventRecord(plan.ev_panel[kt], stream);
@@ -909,12 +919,19 @@ size_t solve_smem_bytes(bool mixed, int tile, int max_np) {
 }
 
 void configure_solve_kernels(int max_np) {
+  int dev = 0, per_sm = 0, reserved = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const int spread = per_sm / 2 - reserved + 128;   // two CTAs asking this much exceed one SM
+  g_panel_min_smem = (per_sm > 0 && spread > 0 && spread <= optin) ? (size_t)spread : 0;
   cudaFuncSetAttribute(k_chol_panel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)PanelLayout<float, 64>::bytes);
+                       (int)panel_smem<float, 64>());
   cudaFuncSetAttribute(k_chol_panel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)PanelLayout<float, 32>::bytes);
+                       (int)panel_smem<float, 32>());
   cudaFuncSetAttribute(k_chol_panel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)PanelLayout<double, 32>::bytes);
+                       (int)panel_smem<double, 32>());
   const int f64 = (int)(SolveLayout<float, 64>::fixed_bytes + sizeof(float) * (size_t)max_np);
   const int f32 = (int)(SolveLayout<float, 32>::fixed_bytes + sizeof(float) * (size_t)max_np);
   const int d32 = (int)(SolveLayout<double, 32>::fixed_bytes + sizeof(double) * (size_t)max_np);

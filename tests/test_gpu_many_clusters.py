@@ -39,3 +39,24 @@ def test_every_cluster_step_solves_its_system(precision, tol, tile):
         errs.append(np.linalg.norm(dc[cams].ravel() - x) / np.linalg.norm(x))
     assert max(errs) < tol, max(errs)
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [stba.STBA_FP64, stba.STBA_MIXED])
+def test_a_cluster_too_large_for_the_solve_is_refused(precision):
+    # the cluster solve holds a cluster's vector in shared memory: one cluster of 2400 cameras (21600
+    # unknowns) exceeds it in both precisions and is refused at create, and by stba_set_clusters on a
+    # context whose clusters fit; nothing is allocated for the dense systems first
+    rng = np.random.default_rng(5)
+    m, n = 2400, 2400
+    cams = np.zeros((m, 9))
+    cams[:, 5] = 10.0                                  # every camera 10 units in front of the points
+    cams[:, 6] = 500.0
+    pts = rng.uniform(-1.0, 1.0, size=(n, 3))
+    oc = np.stack([np.arange(n), (np.arange(n) + 1) % m], axis=1).ravel().astype(np.int32)
+    op = np.repeat(np.arange(n), 2).astype(np.int32)
+    uv = rng.normal(0.0, 1.0, size=(2 * n, 2))
+    with pytest.raises(stba.StbaError, match="shared memory"):
+        stba.stba_create(cams, pts, oc, op, uv, np.zeros(m, np.int32), precision=precision)
+    ctx = stba.stba_create(cams, pts, oc, op, uv, (np.arange(m) // 100).astype(np.int32), precision=precision)
+    with pytest.raises(stba.StbaError, match="shared memory"):
+        stba.stba_set_clusters(ctx, np.zeros(m, np.int32))
