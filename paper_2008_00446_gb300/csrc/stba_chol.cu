@@ -913,9 +913,13 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
 }
 
 size_t solve_smem_bytes(bool mixed, int tile, int max_np) {
-  if (!mixed) return SolveLayout<double, 32>::fixed_bytes + sizeof(double) * (size_t)max_np;
-  return (tile == 64 ? SolveLayout<float, 64>::fixed_bytes : SolveLayout<float, 32>::fixed_bytes) +
-         sizeof(float) * (size_t)max_np;
+  // dynamic (tile stages and the vector) plus static (partial[2][T], t[T], pcol[256 / T][T])
+  auto total = [&](size_t fixed, size_t fs, int T) {
+    return fixed + fs * ((size_t)max_np + (3 + 256 / T) * (size_t)T);
+  };
+  if (!mixed) return total(SolveLayout<double, 32>::fixed_bytes, sizeof(double), 32);
+  return tile == 64 ? total(SolveLayout<float, 64>::fixed_bytes, sizeof(float), 64)
+                    : total(SolveLayout<float, 32>::fixed_bytes, sizeof(float), 32);
 }
 
 void configure_solve_kernels(int max_np) {

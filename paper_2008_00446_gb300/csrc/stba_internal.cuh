@@ -204,7 +204,7 @@ void launch_apply(const DevProblem& P, const double* dc, const double* dp, doubl
 // Sets the dynamic shared-memory limits of the kernels that need more than 48 KB (call outside capture).
 void configure_kernels(int max_np);
 void configure_solve_kernels(int max_np);
-// Dynamic shared memory of the cluster solve for clusters of up to max_np unknowns (padded).
+// Shared memory (dynamic and static) of the cluster solve for clusters of up to max_np unknowns (padded).
 size_t solve_smem_bytes(bool mixed, int tile, int max_np);
 
 // Cholesky (stba_chol.cu)
