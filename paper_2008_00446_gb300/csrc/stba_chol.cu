@@ -85,87 +85,20 @@ __device__ __forceinline__ void load_vec(const F* p, F (&v)[R]) {
   }
 }
 
-// 16 bytes (R = 4 floats or 2 doubles, or a smaller aligned run) from global memory, cached in L2 only.
-template <typename F, int R>
-__device__ __forceinline__ void ld_global_vec(const F* p, F (&v)[R]) {
-  if constexpr (sizeof(F) == 4 && R == 4) {
-    const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
-    v[0] = t.x;
-    v[1] = t.y;
-    v[2] = t.z;
-    v[3] = t.w;
-  } else if constexpr (sizeof(F) == 4 && R == 2) {
-    const float2 t = __ldcg(reinterpret_cast<const float2*>(p));
-    v[0] = t.x;
-    v[1] = t.y;
-  } else if constexpr (sizeof(F) == 8 && R == 2) {
-    const double2 t = __ldcg(reinterpret_cast<const double2*>(p));
-    v[0] = t.x;
-    v[1] = t.y;
-  } else {
-#pragma unroll
-    for (int a = 0; a < R; ++a) v[a] = p[a];
-  }
+// Asynchronous global -> shared copies of one element (4 or 8 bytes), so that all the loads of a tile are
+// in flight at once and may land at transposed positions.
+template <typename F>
+__device__ __forceinline__ void cp_async_elem(F* smem_dst, const F* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(F) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
-template <typename F, int R>
-__device__ __forceinline__ void st_global_vec(F* p, const F (&v)[R]) {
-  if constexpr (sizeof(F) == 4 && R == 4) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-  } else if constexpr (sizeof(F) == 4 && R == 2) {
-    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-  } else if constexpr (sizeof(F) == 8 && R == 2) {
-    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-  } else {
-#pragma unroll
-    for (int a = 0; a < R; ++a) p[a] = v[a];
-  }
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
-
-// A T x T tile of the factor (row stride ld, 16-byte aligned rows) held in registers by a block of 256
-// threads, 16 bytes per load: load() issues every load of the tile, so that the loads of several tiles are
-// in flight together; the stores put it into shared memory row-major (lanes along a row) or transposed
-// (lanes down a column chunk, so that consecutive lanes store consecutive addresses).
-template <typename F, int T>
-struct TileRegs {
-  static constexpr int V = 16 / (int)sizeof(F), CH = T / V, N = T * CH / 256;
-  static_assert(T * CH % 256 == 0, "tile not a whole number of 16-byte loads per thread");
-  F e[N][V];
-  __device__ __forceinline__ void load_rows(const F* src, size_t ld) {
-#pragma unroll
-    for (int u = 0; u < N; ++u) {
-      const int q = threadIdx.x + 256 * u, r = q / CH, ch = q - (q / CH) * CH;
-      ld_global_vec<F, V>(src + (size_t)r * ld + ch * V, e[u]);
-    }
-  }
-  template <int LD>
-  __device__ __forceinline__ void store_rows(F (*dst)[LD], bool lower_only) const {
-#pragma unroll
-    for (int u = 0; u < N; ++u) {
-      const int q = threadIdx.x + 256 * u, r = q / CH, ch = q - (q / CH) * CH;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        const int c = ch * V + v;
-        dst[r][c] = (lower_only && c > r) ? F(0) : e[u][v];
-      }
-    }
-  }
-  __device__ __forceinline__ void load_cols(const F* src, size_t ld) {
-#pragma unroll
-    for (int u = 0; u < N; ++u) {
-      const int q = threadIdx.x + 256 * u, r = q % T, ch = q / T;
-      ld_global_vec<F, V>(src + (size_t)r * ld + ch * V, e[u]);
-    }
-  }
-  template <int LD>
-  __device__ __forceinline__ void store_transposed(F (*dst)[LD]) const {   // after load_cols
-#pragma unroll
-    for (int u = 0; u < N; ++u) {
-      const int q = threadIdx.x + 256 * u, r = q % T, ch = q / T;
-#pragma unroll
-      for (int v = 0; v < V; ++v) dst[ch * V + v][r] = e[u][v];
-    }
-  }
-};
 
 __device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_w(double x) { return rsqrt(x); }
@@ -257,23 +190,20 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
   const int bi = tid & 15, bj = tid >> 4;
   const size_t base_kk = (size_t)(kt * T) * np + kt * T;
   const size_t base_ik = (size_t)(i * T) * np + kt * T;
-  // 1. loads, every tile's in flight at once; the upper part of the diagonal tile is never stored, so it
-  //    is set to zero
-  {
-    TileRegs<F, T> gd, gx, gk, gi;
-    gd.load_rows(A + base_kk, np);
-    if (!diag) gx.load_rows(A + base_ik, np);
+  // 1. loads; the upper part of the diagonal tile is never stored, so it is set to zero
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    if (c <= r)
+      cp_async_elem(&Ad[r][c], A + base_kk + (size_t)r * np + c);
+    else
+      Ad[r][c] = F(0);
+    if (!diag) cp_async_elem(&Ax[r][c], A + base_ik + (size_t)r * np + c);
     if (kt > 0) {
-      gk.load_cols(A + base_kk - T, np);
-      if (!diag) gi.load_cols(A + base_ik - T, np);
-    }
-    gd.store_rows(Ad, true);
-    if (!diag) gx.store_rows(Ax, false);
-    if (kt > 0) {
-      gk.store_transposed(LkT);
-      if (!diag) gi.store_transposed(LiT);
+      cp_async_elem(&LkT[c][r], A + base_kk - T + (size_t)r * np + c);
+      if (!diag) cp_async_elem(&LiT[c][r], A + base_ik - T + (size_t)r * np + c);
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   if (kt > 0) {
     F accD[R][R], accX[R][R];
@@ -489,19 +419,14 @@ __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const i
   const int np = P.cluster_np[k];
   F* A = L + P.S_off[k];
   const size_t bi = (size_t)(i * T) * np + kt * T, bj = (size_t)(j * T) * np + kt * T;
-  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
-  const size_t bij = (size_t)(i * T) * np + j * T;
-  F cur[R][R];   // this thread's block of A_ij, fetched before the product so that its latency is hidden
-  {
-    TileRegs<F, T> gi, gj;
-    gi.load_cols(A + bi, np);
-    gj.load_cols(A + bj, np);
-#pragma unroll
-    for (int a = 0; a < R; ++a) ld_global_vec<F, R>(A + bij + (size_t)(tr * R + a) * np + tc * R, cur[a]);
-    gi.store_transposed(LiT);
-    gj.store_transposed(LjT);
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    cp_async_elem(&LiT[c][r], A + bi + (size_t)r * np + c);
+    cp_async_elem(&LjT[c][r], A + bj + (size_t)r * np + c);
   }
+  cp_async_wait_all();
   __syncthreads();
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
   F acc[R][R];
 #pragma unroll
   for (int a = 0; a < R; ++a)
@@ -517,12 +442,11 @@ __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const i
 #pragma unroll
       for (int b = 0; b < R; ++b) acc[a][b] += av[a] * bv[b];
   }
+  const size_t bij = (size_t)(i * T) * np + j * T;
 #pragma unroll
-  for (int a = 0; a < R; ++a) {
+  for (int a = 0; a < R; ++a)
 #pragma unroll
-    for (int b = 0; b < R; ++b) cur[a][b] -= acc[a][b];
-    st_global_vec<F, R>(A + bij + (size_t)(tr * R + a) * np + tc * R, cur[a]);
-  }
+    for (int b = 0; b < R; ++b) A[bij + (size_t)(tr * R + a) * np + tc * R + b] -= acc[a][b];
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -539,19 +463,19 @@ __device__ F warp_sum(F v) {
 // it with j = rank mod CS for the forward pass, tile rows j > it for the backward pass), the partials are
 // exchanged through distributed shared memory after one cluster barrier, and every CTA applies the stored
 // inverse of the diagonal tile redundantly, so the next step needs no further synchronisation.  The tiles
-// do not depend on the vector: the owned tiles of steps it + 1 and it + 2 (up to SOLVE_PF of them each)
-// and their diagonal inverses are copied into shared memory (cp.async, three stages) while step it
-// computes.
+// do not depend on the vector: the owned tiles of the next steps (up to SOLVE_PF of them each) and their
+// diagonal inverses are copied into shared memory (cp.async) while step it computes, `nst` stages deep:
+// three (two steps ahead) when the launch is one wave of CTAs, two otherwise, where the smaller shared
+// memory lets two CTAs share an SM and the waves halve.
 constexpr int SOLVE_CS = 8;
 constexpr int SOLVE_PF = 2;
-constexpr int SOLVE_STAGES = 3;
 
 template <typename F, int T>
 struct SolveLayout {
   static constexpr int LDT = T + 16 / (int)sizeof(F);   // padded rows, 16-byte aligned
   static constexpr size_t tile_elems = (size_t)T * LDT;
-  // [SOLVE_STAGES][SOLVE_PF tiles + 1 diagonal inverse][T][LDT], then the vector y
-  static constexpr size_t fixed_bytes = sizeof(F) * SOLVE_STAGES * (SOLVE_PF + 1) * tile_elems;
+  // per stage [SOLVE_PF tiles + 1 diagonal inverse][T][LDT]; the stages are followed by the vector y
+  static constexpr size_t stage_bytes = sizeof(F) * (SOLVE_PF + 1) * tile_elems;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
@@ -559,6 +483,7 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
 // T x T tile at src (row stride ld elements) into padded shared rows
@@ -588,14 +513,15 @@ __device__ __forceinline__ void smem_matvec(const F* M, const F* v, F* out) {
 
 template <typename F, int T, typename Rreal>
 __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, const F* Dinv, const double* scale,
-                                                   const Rreal* rhs, double* x, int accumulate, int64_t v_total) {
+                                                   const Rreal* rhs, double* x, int accumulate, int64_t v_total,
+                                                   int nst) {
   namespace cg = cooperative_groups;
   using SL = SolveLayout<F, T>;
   constexpr int PARTS = 256 / T, LEN = T / PARTS, LDT = SL::LDT;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  F* buf = reinterpret_cast<F*>(smem_raw);                   // [SOLVE_STAGES][SOLVE_PF + 1][T][LDT]
-  F* y = buf + SOLVE_STAGES * (SOLVE_PF + 1) * SL::tile_elems;
+  F* buf = reinterpret_cast<F*>(smem_raw);                   // [nst][SOLVE_PF + 1][T][LDT]
+  F* y = buf + nst * (SOLVE_PF + 1) * SL::tile_elems;
   __shared__ F partial[2][T];
   __shared__ F t[T];
   __shared__ F pcol[PARTS][T];
@@ -619,23 +545,26 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
       int m = 0;
       if (fwd) {
         for (int j = rank; j < it && m < SOLVE_PF; j += SOLVE_CS, ++m)
-          prefetch_tile<F, T>(tile_buf(s % SOLVE_STAGES, m), A + (size_t)(it * T) * np + j * T, np);
+          prefetch_tile<F, T>(tile_buf(s % nst, m), A + (size_t)(it * T) * np + j * T, np);
       } else {
         for (int j = it + 1 + rank; j < nt && m < SOLVE_PF; j += SOLVE_CS, ++m)
-          prefetch_tile<F, T>(tile_buf(s % SOLVE_STAGES, m), A + (size_t)(j * T) * np + it * T, np);
+          prefetch_tile<F, T>(tile_buf(s % nst, m), A + (size_t)(j * T) * np + it * T, np);
       }
-      prefetch_tile<F, T>(tile_buf(s % SOLVE_STAGES, SOLVE_PF), (fwd ? Di : DiT) + (size_t)it * T * T, T);
+      prefetch_tile<F, T>(tile_buf(s % nst, SOLVE_PF), (fwd ? Di : DiT) + (size_t)it * T * T, T);
     }
     cp_async_commit();
   };
   issue(0);
-  issue(1);
+  if (nst == 3) issue(1);
   for (int i = tid; i < np; i += blockDim.x) y[i] = (F)((double)rk[i] * sk[i]);
   for (int s = 0; s < 2 * nt; ++s) {
-    issue(s + 2);   // into the stage step s - 1 used; every thread passed its last barrier
-    cp_async_wait2();
+    issue(s + nst - 1);   // into the stage step s - 1 used; every thread passed its last barrier
+    if (nst == 3)
+      cp_async_wait2();
+    else
+      cp_async_wait1();
     __syncthreads();
-    const int st = s % SOLVE_STAGES;
+    const int st = s % nst;
     const bool fwd = s < nt;
     const int it = fwd ? s : 2 * nt - 1 - s;
     const int r0 = it * T;
@@ -705,13 +634,31 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   cluster.sync();   // keep this CTA's shared memory alive until every peer has read it
 }
 
+// Device figures, read by configure_solve_kernels.
+static int g_num_sms = 0, g_smem_optin = 0;
+
+// Shared memory of one solve CTA: nst stages, the vector, and the static arrays (partial[2][T], t[T],
+// pcol[256 / T][T]).
+template <typename F, int T>
+size_t solve_cta_bytes(int nst, int max_np) {
+  return nst * SolveLayout<F, T>::stage_bytes +
+         sizeof(F) * ((size_t)max_np + (3 + 256 / T) * (size_t)T);
+}
+
+template <typename F, int T>
+int solve_stages(int l, int max_np) {
+  const bool one_wave = (int64_t)l * SOLVE_CS <= g_num_sms;
+  return one_wave && solve_cta_bytes<F, T>(3, max_np) <= (size_t)g_smem_optin ? 3 : 2;
+}
+
 template <typename F, int T, typename Rreal>
 void launch_tri_solve(const DevProblem& P, const F* L, const F* Dinv, const double* scale, const Rreal* rhs,
                       double* x, int accumulate, int max_np, int64_t v_total, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(P.l * SOLVE_CS);
   cfg.blockDim = dim3(256);
-  cfg.dynamicSmemBytes = SolveLayout<F, T>::fixed_bytes + sizeof(F) * (size_t)max_np;
+  const int nst = solve_stages<F, T>(P.l, max_np);
+  cfg.dynamicSmemBytes = nst * SolveLayout<F, T>::stage_bytes + sizeof(F) * (size_t)max_np;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -720,7 +667,7 @@ void launch_tri_solve(const DevProblem& P, const F* L, const F* Dinv, const doub
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal>, P, L, Dinv, scale, rhs, x, accumulate, v_total);
+  cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal>, P, L, Dinv, scale, rhs, x, accumulate, v_total, nst);
 }
 
 // r = b - S x (FP64) with S symmetric, lower triangle stored; r was set to b before.  One CTA per
@@ -831,13 +778,15 @@ void launch_prio(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s
   cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 // A panel CTA is bound by the latency of its column chain: a second panel CTA on the same SM would halve
-// the speed of both.  Its dynamic shared memory is therefore raised above half of an SM's, so that the CTAs
-// of a tile step take one SM each (set from the device's figures by configure_solve_kernels).
+// the speed of both.  When a tile step's panels fit on the SMs one each, their dynamic shared memory is
+// raised above half of an SM's so that they do take one SM each; a step with more panels than SMs keeps
+// the plain size, so that the SMs hold several and the waves stay few (figures set by
+// configure_solve_kernels).
 static size_t g_panel_min_smem = 0;
 
 template <typename F, int T>
-size_t panel_smem() {
-  return std::max(PanelLayout<F, T>::bytes, g_panel_min_smem);
+size_t panel_smem(int npn = 0) {
+  return npn <= g_num_sms ? std::max(PanelLayout<F, T>::bytes, g_panel_min_smem) : PanelLayout<F, T>::bytes;
 }
 
 template <typename F, int T>
@@ -859,7 +808,7 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
     if (kt >= 2) cudaStreamWaitEvent(stream, plan.ev_update[kt - 2], 0);
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
     if (npn > 0)
-      launch_prio(k_chol_panel<F, T>, npn, panel_smem<F, T>(), stream, plan.prio_high, L,
+      launch_prio(k_chol_panel<F, T>, npn, panel_smem<F, T>(npn), stream, plan.prio_high, L,
                   reinterpret_cast<F*>(fb.Ldiag), P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags,
                   fb.boosted);
     cudaEventRecord(plan.ev_panel[kt], stream);
@@ -912,14 +861,9 @@ void launch_solve(const DevProblem& P, const double* S, const double* b, const F
     launch_solve_t<F, 32>(P, S, b, fb, plan, refine_steps, dc, dcf, stream);
 }
 
-size_t solve_smem_bytes(bool mixed, int tile, int max_np) {
-  // dynamic (tile stages and the vector) plus static (partial[2][T], t[T], pcol[256 / T][T])
-  auto total = [&](size_t fixed, size_t fs, int T) {
-    return fixed + fs * ((size_t)max_np + (3 + 256 / T) * (size_t)T);
-  };
-  if (!mixed) return total(SolveLayout<double, 32>::fixed_bytes, sizeof(double), 32);
-  return tile == 64 ? total(SolveLayout<float, 64>::fixed_bytes, sizeof(float), 64)
-                    : total(SolveLayout<float, 32>::fixed_bytes, sizeof(float), 32);
+size_t solve_smem_bytes(bool mixed, int tile, int max_np) {   // with the smallest stage count
+  if (!mixed) return solve_cta_bytes<double, 32>(2, max_np);
+  return tile == 64 ? solve_cta_bytes<float, 64>(2, max_np) : solve_cta_bytes<float, 32>(2, max_np);
 }
 
 void configure_solve_kernels(int max_np) {
@@ -928,6 +872,8 @@ void configure_solve_kernels(int max_np) {
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  g_smem_optin = optin;
   const int spread = per_sm / 2 - reserved + 128;   // two CTAs asking this much exceed one SM
   g_panel_min_smem = (per_sm > 0 && spread > 0 && spread <= optin) ? (size_t)spread : 0;
   cudaFuncSetAttribute(k_chol_panel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -936,9 +882,14 @@ void configure_solve_kernels(int max_np) {
                        (int)panel_smem<float, 32>());
   cudaFuncSetAttribute(k_chol_panel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)panel_smem<double, 32>());
-  const int f64 = (int)(SolveLayout<float, 64>::fixed_bytes + sizeof(float) * (size_t)max_np);
-  const int f32 = (int)(SolveLayout<float, 32>::fixed_bytes + sizeof(float) * (size_t)max_np);
-  const int d32 = (int)(SolveLayout<double, 32>::fixed_bytes + sizeof(double) * (size_t)max_np);
+  // room for three stages wherever solve_stages may choose them
+  auto stages = [&](size_t three) { return three <= (size_t)optin ? 3 : 2; };
+  const int f64 = stages(solve_cta_bytes<float, 64>(3, max_np)) * SolveLayout<float, 64>::stage_bytes +
+                  sizeof(float) * max_np;
+  const int f32 = stages(solve_cta_bytes<float, 32>(3, max_np)) * SolveLayout<float, 32>::stage_bytes +
+                  sizeof(float) * max_np;
+  const int d32 = stages(solve_cta_bytes<double, 32>(3, max_np)) * SolveLayout<double, 32>::stage_bytes +
+                  sizeof(double) * max_np;
   cudaFuncSetAttribute(k_tri_solve<float, 64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f64);
   cudaFuncSetAttribute(k_tri_solve<float, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f32);
   cudaFuncSetAttribute(k_tri_solve<double, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32);

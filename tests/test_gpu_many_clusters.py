@@ -43,11 +43,11 @@ def test_every_cluster_step_solves_its_system(precision, tol, tile):
 
 @pytest.mark.parametrize("precision", [stba.STBA_FP64, stba.STBA_MIXED])
 def test_a_cluster_too_large_for_the_solve_is_refused(precision):
-    # the cluster solve holds a cluster's vector in shared memory: one cluster of 2400 cameras (21600
+    # the cluster solve holds a cluster's vector in shared memory: one cluster of 4000 cameras (36000
     # unknowns) exceeds it in both precisions and is refused at create, and by stba_set_clusters on a
     # context whose clusters fit; nothing is allocated for the dense systems first
     rng = np.random.default_rng(5)
-    m, n = 2400, 2400
+    m, n = 4000, 4000
     cams = np.zeros((m, 9))
     cams[:, 5] = 10.0                                  # every camera 10 units in front of the points
     cams[:, 6] = 500.0
