@@ -56,13 +56,15 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def stage_traffic(stage):
+def stage_traffic(stage, config):
+    """DRAM bytes per iteration of a stage from profiles/traffic.json, or None unless that capture was of the
+    same sources and the same workload."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("source_hash") != source_hash():
+    if t.get("source_hash") != source_hash() or not str(t.get("workload", "")).startswith(config + ","):
         return None
     return t.get("stage_dram_bytes_per_iteration", {}).get(stage)
 
@@ -317,12 +319,13 @@ def main():
     if dom == 2:
         achieved = info0["factor_flops"] / (stage_ms[2] / 1e3) / 1e12
         roofline = {"bound": "alu", "stage": names[2], "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": stage_traffic(names[2]),
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                    "traffic": stage_traffic(names[2], args.config),
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (FP32 SIMT)"}
     else:
         achieved = bytes_stage[dom] / (stage_ms[dom] / 1e3) / 1e9
         roofline = {"bound": "hbm", "stage": names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": stage_traffic(names[dom]),
+                    "frac": achieved / hbm, "traffic": stage_traffic(names[dom], args.config),
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roofline["stage_ms"] = {nm: float(v) for nm, v in zip(names, stage_ms)}
 
