@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -41,6 +42,10 @@ struct stba_ctx {
   Settings set{};
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // re-ordering graphs of the two buffer states (argument bytes -> executable graph)
+  std::vector<unsigned char> reorder_key[2];
+  cudaGraphExec_t reorder_exec[2] = {nullptr, nullptr};
+  int reorder_next = 0;
   cudaStream_t side_stream = nullptr;           // trailing updates of the factorisation
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<cudaEvent_t> ev_panel, ev_update;  // one per tile step (grown, never shrunk)
@@ -311,6 +316,63 @@ stba_status refresh_counts(stba_ctx* c) {
 // blocks of S'_k, the Cholesky step plan: O(m + l + plan) work); the device re-orders the observations
 // by (point, cluster, camera), numbers the virtual points (distinct (point, cluster) pairs) and rebuilds
 // the camera lists (stba_order.cu), carrying the stored residuals over to the new order.
+// The re-ordering kernels of an assignment.  Their launch shapes depend only on q, m and the number of
+// camera-graph chunks, and their arguments on which of the two order and residual buffers are current, so
+// after the first assignment two captured graphs (one per buffer state) serve every later one and replace
+// about 16 dependent launches by one.  Captured on the private stream, launched on the context's.
+static void enqueue_reorder(stba_ctx* c, const ReorderArgs& A, bool carry, cudaStream_t st) {
+  if (c->mixed)
+    launch_reorder<float>(A, c->key, c->tile_sum, c->counts, carry ? (const float*)c->res_cur : nullptr,
+                          (float*)c->res_cand, st);
+  else
+    launch_reorder<double>(A, c->key, c->tile_sum, c->counts, carry ? (const double*)c->res_cur : nullptr,
+                           (double*)c->res_cand, st);
+  if (!c->use_pcg && !c->use_spcg && c->pchunks.nchunks > 0)
+    launch_list_chunks(c->pchunks, c->cam_cluster, c->counts + 3, st);
+}
+
+static stba_status launch_reorder_graph(stba_ctx* c, const ReorderArgs& A, bool carry) {
+  if (!c->opt.use_graph) {
+    enqueue_reorder(c, A, carry, c->stream);
+    CK(cudaGetLastError());
+    return STBA_OK;
+  }
+  // the argument bytes: ReorderArgs (padding after its three ints cleared) and the other arguments
+  static_assert(offsetof(ReorderArgs, obs_pt) == 16, "ReorderArgs: three ints, then pointers");
+  std::vector<unsigned char> key(sizeof(ReorderArgs));
+  std::memcpy(key.data(), &A, sizeof A);
+  std::memset(key.data() + 12, 0, 4);
+  const void* more[] = {c->key, c->tile_sum, c->counts, carry ? c->res_cur : nullptr, c->res_cand,
+                        c->pchunks.chunks, c->pchunks.active, c->pchunks.nactive, c->pchunks.flag,
+                        c->pchunks.excl, c->pchunks.tile_sum, c->cam_cluster};
+  const long long flags[] = {c->mixed, c->use_pcg || c->use_spcg, c->pchunks.nchunks};
+  const unsigned char* m1 = reinterpret_cast<const unsigned char*>(more);
+  const unsigned char* m2 = reinterpret_cast<const unsigned char*>(flags);
+  key.insert(key.end(), m1, m1 + sizeof more);
+  key.insert(key.end(), m2, m2 + sizeof flags);
+  for (int i = 0; i < 2; ++i)
+    if (c->reorder_exec[i] && c->reorder_key[i] == key) {
+      CK(cudaGraphLaunch(c->reorder_exec[i], c->stream));
+      return STBA_OK;
+    }
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  enqueue_reorder(c, A, carry, c->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+  if (e != cudaSuccess) return fail(c, STBA_ERR_CUDA, "re-ordering capture failed: %s", cudaGetErrorString(e));
+  cudaGraphExec_t x = nullptr;
+  e = cudaGraphInstantiate(&x, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(c, STBA_ERR_CUDA, "re-ordering graph: %s", cudaGetErrorString(e));
+  const int slot = c->reorder_next;
+  c->reorder_next ^= 1;
+  if (c->reorder_exec[slot]) cudaGraphExecDestroy(c->reorder_exec[slot]);
+  c->reorder_exec[slot] = x;
+  c->reorder_key[slot] = std::move(key);
+  CK(cudaGraphLaunch(x, c->stream));
+  return STBA_OK;
+}
+
 stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   const int m = (int)c->m, n = (int)c->n, q = (int)c->q;
   int l = 0;
@@ -527,15 +589,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     A.inv_old = c->inv[c->inv_cur];
     A.inv_new = c->inv[1 - c->inv_cur];
     const bool carry = c->have_order;
-    if (c->mixed)
-      launch_reorder<float>(A, c->key, c->tile_sum, c->counts, carry ? (const float*)c->res_cur : nullptr,
-                            (float*)c->res_cand, c->stream);
-    else
-      launch_reorder<double>(A, c->key, c->tile_sum, c->counts, carry ? (const double*)c->res_cur : nullptr,
-                             (double*)c->res_cand, c->stream);
-    if (!c->use_pcg && !c->use_spcg && c->pchunks.nchunks > 0)
-      launch_list_chunks(c->pchunks, c->cam_cluster, c->counts + 3, c->stream);
-    CK(cudaGetLastError());
+    if ((s = launch_reorder_graph(c, A, carry)) != STBA_OK) return s;
     if (carry) std::swap(c->res_cur, c->res_cand);
     c->inv_cur = 1 - c->inv_cur;
     c->have_order = true;
@@ -1008,6 +1062,8 @@ void stba_destroy(stba_ctx* c) {
   }
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaGraphExec_t& e : c->reorder_exec)
+    if (e) cudaGraphExecDestroy(e);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
