@@ -111,6 +111,9 @@ void stba_default_options(stba_options* opt);
  *   cluster non-empty (the sampled clustering of Sec. 4.2/4.4); opt may be NULL (defaults);
  *   cuda_stream is a cudaStream_t or NULL.
  * Every point needs >= 2 projections and every camera >= 1; a (camera, point) pair may appear once.
+ * With the cluster solver the solve of a cluster keeps its vector in one CTA's shared memory: a cluster
+ * of more than about 31,500 unknowns (9 per camera; FP32 factor) or 22,100 (FP64) is refused with
+ * STBA_ERR_INVALID_ARG and a message naming the limit (the PCG solvers have no such limit).
  * Computes F(x) once.  On success *out owns the context. */
 stba_status stba_create(const double* cameras, int64_t m, const double* points, int64_t n,
                         const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int64_t q,
@@ -118,7 +121,9 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
                         stba_ctx** out);
 
 /* Replaces the cluster assignment [m] used by subsequent iterations (the per-iteration resampling of
- * Algorithm 1).  Same validation as stba_create. */
+ * Algorithm 1).  Same validation as stba_create, including the cluster-size limit; after a validation
+ * error the previous assignment stays in force.  Enqueues the device re-ordering and returns without
+ * waiting. */
 stba_status stba_set_clusters(stba_ctx* ctx, const int32_t* cluster_assignment);
 
 /* Runs one LM iteration (Algorithm 1 body).  If info != NULL the stream is synchronised and *info is
