@@ -58,5 +58,8 @@ def test_a_cluster_too_large_for_the_solve_is_refused(precision):
     with pytest.raises(stba.StbaError, match="shared memory"):
         stba.stba_create(cams, pts, oc, op, uv, np.zeros(m, np.int32), precision=precision)
     ctx = stba.stba_create(cams, pts, oc, op, uv, (np.arange(m) // 100).astype(np.int32), precision=precision)
+    F0 = stba.stba_cost(ctx)
     with pytest.raises(stba.StbaError, match="shared memory"):
         stba.stba_set_clusters(ctx, np.zeros(m, np.int32))
+    info = stba.stba_lm_iteration(ctx)   # the previous assignment (40 clusters) stays in force
+    assert info["failed_clusters"] == 0 and info["F_before"] == F0 and np.isfinite(info["F_after"])
