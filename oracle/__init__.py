@@ -13,7 +13,9 @@ paper's matrices:
                 solves of Eq. 13, the point update of Eq. 15, the steepest-descent correction of Sec. 4.3,
                 and the LM control of Algorithm 1 (Appendix C), plus brute-force solvers for pins;
   sgc.py     -- stochastic graph clustering of Sec. 4.4 (modularity, Eq. 16 join probabilities, the
-                sampler, and the exact distribution of final clusterings on tiny graphs).
+                sampler, and the exact distribution of final clusterings on tiny graphs);
+  adjoint.py -- the reverse pass through K recorded iterations (not in the paper: implicit
+                differentiation of each accepted step's damped, cluster-split normal equations).
 
 Every function is pinned by `tests/test_oracle_*.py` against something other than itself: finite
 differences, library rotations, brute-force dense solves of Eq. 3 and Eq. 9, closed forms and invariants.
