@@ -45,6 +45,18 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(value, device=None):
+    """The largest value over the ranks of the process group (a job's time is its slowest rank's); the value
+    itself without a group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def source_hash():
     """Hash of the CUDA sources; the DRAM traffic in profiles/traffic.json is used only while it matches."""
     import glob
@@ -269,10 +281,7 @@ def main():
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(tot_ms, dev)
     lam, F_end, it_end = stba.stba_get_state(ctx)
     value = world * args.steps / (tot_ms / 1e3)
 
@@ -337,6 +346,8 @@ def main():
     pts_o = torch.empty_like(pts_h).pin_memory()
     stba.stba_get_params(ctx, cams_h, pts_h)
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         stba.stba_set_params(ctx, cams_h, pts_h)
@@ -344,7 +355,7 @@ def main():
         stba.stba_lm_iteration(ctx, want_info=False)
         stba.stba_get_params(ctx, cams_o, pts_o)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     nbytes_in = 8 * (cams_h.numel() + pts_h.numel()) + 4 * s.m
     nbytes_out = 8 * (cams_h.numel() + pts_h.numel())
 

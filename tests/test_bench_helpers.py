@@ -1,6 +1,11 @@
 """Host helpers of bench.py (no GPU): the DRAM-traffic lookup is used only for the sources and the workload
-it was captured on, and the clock sampler's parsing of nvidia-smi lines (median SM clock, throttle reasons)."""
+it was captured on, the clock sampler's parsing of nvidia-smi lines (median SM clock, throttle reasons), and
+the max over ranks of a multi-process run (two gloo ranks on CPU)."""
 import json
+import os
+import socket
+
+import pytest
 
 import bench
 
@@ -52,3 +57,25 @@ def test_clock_sampler_parses_median_and_reasons(tmp_path):
 
 def test_clock_sampler_without_nvidia_smi():
     assert bench.ClockSampler(0).stop() is None
+
+
+def _max_worker(rank, world, port, out_dir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        v = bench.max_over_ranks(10.0 + 3.0 * rank)   # the ranks' own step times
+        with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+            f.write(repr(v))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_on_two_gloo_ranks(tmp_path):
+    pytest.importorskip("torch")
+    import torch.multiprocessing as tmp_mp
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    tmp_mp.start_processes(_max_worker, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
+    assert [float((tmp_path / f"r{r}.txt").read_text()) for r in range(2)] == [13.0, 13.0]
+    assert bench.max_over_ranks(7.5) == 7.5   # no process group: the value itself
