@@ -5,7 +5,8 @@ cameras and observations; the boundary points; load balance).  Then 2 and 3 `glo
 of Algorithm 1 each over its own clusters only, with the oracle's building blocks for the local arithmetic
 and the plan's exchanges as all-reduces over the boundary points and four scalars, and the result must
 equal the single-process oracle: every rank's Delta c and Delta p, F(x + Delta x), the accept decisions and
-lambda, over iterations with and without the steepest-descent correction (Sec. 4.3).  The bars are those of
+lambda, over iterations with and without the steepest-descent correction (Sec. 4.3), and with the Huber
+loss on a scene with gross outliers (the robust weights are per observation, so local).  The bars are those of
 the FP64 parity tests (steps 1e-6 in norm, F 1e-8): the summation order differs between the ranks and the
 single process, and the nearly gauge-free systems at small lambda amplify that rounding.  This checks the
 exchange plan of the sharded design; no GPU is involved."""
@@ -25,8 +26,20 @@ def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-def ring_with_sgc(gamma, seed, iters):
+def ring_scene(huber):
+    """The ring scene; with a robust loss, 2 % of its observations moved by gross errors (seeded)."""
     s = scenes.make_config("c0_ring")
+    if huber > 0:
+        rng = np.random.default_rng(21)
+        uv = s.obs_uv.copy()
+        bad = rng.choice(len(uv), size=len(uv) // 50, replace=False)
+        uv[bad] += rng.normal(0.0, 30.0, size=(len(bad), 2))
+        s.obs_uv = uv
+    return s
+
+
+def ring_with_sgc(gamma, seed, iters):
+    s = ring_scene(0.0)
     w = sgc.camera_graph(s.obs_cam, s.obs_pt, s.m)
     rng = np.random.default_rng(seed)
     seq = np.array([sgc.sample(w, s.m, gamma, 10.0, rng.random(s.m)) for _ in range(iters)], np.int32)
@@ -202,15 +215,15 @@ def sharded_iteration(torch, dist, plan, s, cl, cams, pts, lam, F, opt):
     return cams, pts, lam_new, F, rec
 
 
-def _worker(rank, world, port, seq, lambda0, out_dir):
+def _worker(rank, world, port, seq, lambda0, huber, out_dir):
     import torch
     import torch.distributed as dist
     dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
     try:
-        s = scenes.make_config("c0_ring")
-        opt = ostba.Options(lambda0=lambda0, ftol=1e-6, gtol=1e-6, xtol=1e-6)
+        s = ring_scene(huber)
+        opt = ostba.Options(lambda0=lambda0, ftol=1e-6, gtol=1e-6, xtol=1e-6, huber=huber)
         cams, pts, lam = s.cameras.copy(), s.points.copy(), lambda0
-        F = ostba.robust_cost(cams, pts, s.obs_cam, s.obs_pt, s.obs_uv)
+        F = ostba.robust_cost(cams, pts, s.obs_cam, s.obs_pt, s.obs_uv, opt.huber)
         recs = {}
         for t, cl in enumerate(seq):
             plan = shard.plan_shards(cl, s.obs_cam, s.obs_pt, s.n, world)[rank]
@@ -232,17 +245,19 @@ def _free_port():
         return so.getsockname()[1]
 
 
-@pytest.mark.parametrize("world, gamma, lambda0", [(2, 10, 1e-4), (2, 6, 0.5), (3, 5, 0.5)])
-def test_sharded_iterations_equal_the_oracle(tmp_path, world, gamma, lambda0):
+@pytest.mark.parametrize("world, gamma, lambda0, huber", [(2, 10, 1e-4, 0.0), (2, 6, 0.5, 0.0), (3, 5, 0.5, 0.0),
+                                                           (2, 6, 1e-4, 0.5)])
+def test_sharded_iterations_equal_the_oracle(tmp_path, world, gamma, lambda0, huber):
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as tmp_mp
     s, seq = ring_with_sgc(gamma, 11 + world, 4)
     port = _free_port()
-    tmp_mp.start_processes(_worker, args=(world, port, seq, lambda0, str(tmp_path)), nprocs=world,
+    tmp_mp.start_processes(_worker, args=(world, port, seq, lambda0, huber, str(tmp_path)), nprocs=world,
                            start_method="spawn", join=True)
-    opt = ostba.Options(lambda0=lambda0, ftol=1e-6, gtol=1e-6, xtol=1e-6)
+    s = ring_scene(huber)
+    opt = ostba.Options(lambda0=lambda0, ftol=1e-6, gtol=1e-6, xtol=1e-6, huber=huber)
     cams, pts, lam = s.cameras.copy(), s.points.copy(), lambda0
-    F = ostba.robust_cost(cams, pts, s.obs_cam, s.obs_pt, s.obs_uv)
+    F = ostba.robust_cost(cams, pts, s.obs_cam, s.obs_pt, s.obs_uv, opt.huber)
     res = [np.load(tmp_path / f"rank{r}.npz") for r in range(world)]
     corrected = 0
     for t, cl in enumerate(seq):
