@@ -200,3 +200,96 @@ def test_stop_tests():
     assert stba.stop_tests(1.0, 0.9, 1e-7, 1.0, 1.0, stba.Options(gtol=1e-6))
     assert stba.stop_tests(1.0, 0.9, 1.0, 1e-7, 1.0, stba.Options(xtol=1e-6))
     assert not stba.stop_tests(1.0, 0.9, 1.0, 1e-5, 1.0, stba.Options(xtol=1e-6))
+
+
+# ----------------------------------------------------------------------------------------------------------
+# the corrected step (lambda >= 0.1): Alg. 1 feeds the corrected g' into b' of Eq. 10 and keeps the physical,
+# uncorrected w for the point update of Eq. 15.  These pins rebuild J' densely in the test, so a mistake in
+# either half of that composition (corrected w' summed into the point update through another route than its
+# preserved per-point sums, the uncorrected w' in b', the virtual C' in Eq. 15) fails one of them.
+# ----------------------------------------------------------------------------------------------------------
+def dense_expanded_system(s, lin, lam):
+    """J' = [J_c, J'_p] built densely from the per-observation blocks, H' = J'^T J' + lam diag(J'^T J'),
+    g' = -J'^T f, and each virtual point's physical point (virtual points = distinct (point, cluster))."""
+    key = s.obs_pt.astype(np.int64) * (int(s.clusters.max()) + 1) + s.clusters[s.obs_cam]
+    uniq, vp = np.unique(key, return_inverse=True)
+    vp_point = uniq // (int(s.clusters.max()) + 1)
+    nv = len(uniq)
+    Jd = np.zeros((2 * s.q, 9 * s.m + 3 * nv))
+    for o in range(s.q):
+        Jd[2 * o:2 * o + 2, 9 * s.obs_cam[o]:9 * s.obs_cam[o] + 9] = lin.Jc[o]
+        Jd[2 * o:2 * o + 2, 9 * s.m + 3 * vp[o]:9 * s.m + 3 * vp[o] + 3] = lin.Jp[o]
+    H = Jd.T @ Jd
+    H = H + lam * np.diag(np.diag(H))
+    return H, -Jd.T @ lin.f, vp_point
+
+
+def corrected_rhs(g, Hdiag, vp_point, m):
+    """Minimiser of sum_k (1/2 d^T H~_k d - g_k^T d) over equal d for every point's copies, per coordinate:
+    d = sum_k g_k / sum_k H~_k, and the corrected g_k = H~_k d (the steepest-descent correction of Sec. 4.3
+    with the multipliers of Eq. 9 eliminated by hand)."""
+    out = g.copy()
+    w = out[9 * m:].reshape(-1, 3)
+    h = Hdiag[9 * m:].reshape(-1, 3)
+    for i in np.unique(vp_point):
+        sel = vp_point == i
+        w[sel] = h[sel] * (w[sel].sum(0) / h[sel].sum(0))
+    return out
+
+
+@pytest.mark.parametrize("lam", [0.1, 0.5, 4.0])
+@pytest.mark.parametrize("clusters", [[0, 1, 2, 0, 1, 2], [0, 0, 1, 1, 1, 0]])
+def test_corrected_camera_step_solves_expanded_system_with_corrected_rhs(lam, clusters):
+    # Alg. 1, correction branch: Delta c is the camera part of H'_lambda dx' = g'_corrected (Eq. 9 with nu
+    # replaced by the correction), i.e. b' of Eq. 10 is formed from the corrected w'
+    s = tiny(m=6, n=40, seed=17, clusters=clusters)
+    lin = lin_of(s)
+    st = stba.stba_step(lin, s.obs_cam, s.obs_pt, s.clusters, lam, use_correction=True)
+    assert st["corrected"]
+    H, g, vp_point = dense_expanded_system(s, lin, lam)
+    gc = corrected_rhs(g, np.diag(H), vp_point, s.m)
+    assert rel(gc, g) > 1e-6                      # the correction does change the right-hand side here
+    dx_c = np.linalg.solve(H, gc)
+    dx_u = np.linalg.solve(H, g)
+    assert rel(st["dc"], dx_c[: 9 * s.m]) < 1e-9
+    assert rel(st["dc"], dx_u[: 9 * s.m]) > 1e-6  # and it is not the uncorrected relaxed step
+
+
+@pytest.mark.parametrize("lam", [0.1, 0.5, 4.0])
+def test_corrected_point_update_is_eq15_with_physical_w(lam):
+    # Eq. 15 (Alg. 1, last step): whatever Delta c the corrected system gives, Delta p minimises
+    # ||J_p Delta p + f + J_c Delta c||^2 + lam ||D_p Delta p||^2 over the physical points, with the
+    # physical (uncorrected) w = -J_p^T f and the physical damped C
+    s = tiny(m=6, n=40, seed=19, clusters=[0, 1, 2, 0, 1, 2])
+    lin = lin_of(s)
+    st = stba.stba_step(lin, s.obs_cam, s.obs_pt, s.clusters, lam, use_correction=True)
+    assert st["corrected"]
+    Jp = np.zeros((2 * s.q, 3 * s.n))
+    Jc = np.zeros((2 * s.q, 9 * s.m))
+    for o in range(s.q):
+        Jp[2 * o:2 * o + 2, 3 * s.obs_pt[o]:3 * s.obs_pt[o] + 3] = lin.Jp[o]
+        Jc[2 * o:2 * o + 2, 9 * s.obs_cam[o]:9 * s.obs_cam[o] + 9] = lin.Jc[o]
+    Dp = np.sqrt(np.sum(Jp * Jp, axis=0))
+    A = np.vstack([Jp, np.sqrt(lam) * np.diag(Dp)])
+    rhs = np.concatenate([-lin.f - Jc @ st["dc"], np.zeros(3 * s.n)])
+    dp_ls = np.linalg.lstsq(A, rhs, rcond=None)[0]
+    assert rel(st["dp"], dp_ls) < 1e-9
+    # the per-cluster virtual-point steps of Eq. 14 (solved with the virtual C' and corrected w') differ
+    H, g, vp_point = dense_expanded_system(s, lin, lam)
+    dxv = np.linalg.solve(H, corrected_rhs(g, np.diag(H), vp_point, s.m))[9 * s.m:].reshape(-1, 3)
+    first_copy = np.array([dxv[np.flatnonzero(vp_point == i)[0]] for i in range(s.n)])
+    assert rel(first_copy.ravel(), st["dp"]) > 1e-6
+
+
+def test_corrected_iteration_record_and_cost():
+    # one full iteration with the correction: F(x + dx) is the cost at the corrected step, the record says
+    # corrected, and lambda follows the x3 / /3 rule on that F
+    s = tiny(m=6, n=40, seed=20, clusters=[0, 1, 2, 0, 1, 2])
+    F0 = camera.cost(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv)
+    opt = stba.Options(lambda0=0.5)
+    c, p, lam, F, rec = stba.lm_iteration(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, 0.5, F0,
+                                          opt)
+    assert rec["corrected"]
+    F_new = camera.cost(s.cameras + rec["dc"], s.points + rec["dp"], s.obs_cam, s.obs_pt, s.obs_uv)
+    assert rec["F_after"] == pytest.approx(F_new, rel=1e-12)
+    assert lam == pytest.approx(0.5 / 3 if F_new < F0 else 1.5, rel=1e-15)
