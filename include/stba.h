@@ -207,8 +207,11 @@ stba_status stba_stage_times(stba_ctx* ctx, float* ms, int32_t n, int32_t* count
  *   array of 1.97 MB that every GPU loading the library holds until the process exits.  Larger m returns
  *   STBA_ERR_INVALID_ARG.  Indices out of range or a point at depth <= 1e-9 make F NaN.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share the array, so calls that
- * overlap on the GPU (different streams or devices' contexts sharing it) race; serialise them. */
+ * current; make that first call before any stream capture.  The address is kept for the life of the
+ * process, so cudaDeviceReset (which unloads the module holding the array) is not supported while the
+ * library is loaded.  All calls share the array, so calls that overlap on the GPU (different streams or
+ * devices' contexts sharing it) race; serialise them.  An error already pending in the CUDA runtime when
+ * the call starts is left in place and returns STBA_ERR_CUDA; so does a failed launch. */
 stba_status stba_cost_noalloc(const double* cameras, int64_t m, const double* points, int64_t n,
                               const int32_t* obs_cam, const int32_t* obs_pt, const double* obs_uv, int64_t q,
                               double* F_dev, void* cuda_stream);

@@ -24,6 +24,9 @@
 // then x += D^-1/2 (L L^T)^-1 D^-1/2 r.
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+
 #include "stba_internal.cuh"
 
 namespace stba {
@@ -832,7 +835,7 @@ void launch_solve_t(const DevProblem& P, const double* S, const double* b, const
   const F* L = reinterpret_cast<const F*>(fb.L);
   const F* Dinv = reinterpret_cast<const F*>(fb.Dinv);
   launch_tri_solve<F, T, Sreal>(P, L, Dinv, fb.scale, b, fb.x, 0, plan.max_np, fb.v_total, stream);
-  const int nblk = (int)std::min<int64_t>(fb.v_total / 256 + 1, 152 * 8);
+  const int nblk = (int)std::min<int64_t>(fb.v_total / 256 + 1, (int64_t)num_sms() * 8);
   for (int s = 0; s < refine_steps; ++s) {
     k_copy_vec<Sreal><<<nblk, 256, 0, stream>>>(b, fb.r, fb.v_total);
     if (plan.n_res_items > 0)
@@ -866,6 +869,30 @@ size_t solve_smem_bytes(bool mixed, int tile, int max_np) {   // with the smalle
   return tile == 64 ? solve_cta_bytes<float, 64>(2, max_np) : solve_cta_bytes<float, 32>(2, max_np);
 }
 
+int num_sms() {
+  if (g_num_sms <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+// The largest dynamic shared memory of a kernel is a per-function attribute shared by every context of the
+// process.  It is only ever raised: a context with smaller clusters must not lower it below what another
+// live context's next launch asks for.
+static void raise_smem_attr(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> set_to;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = set_to[{dev, fn}];
+  if (bytes > cur && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+    cur = bytes;
+}
+
 void configure_solve_kernels(int max_np) {
   int dev = 0, per_sm = 0, reserved = 0, optin = 0;
   cudaGetDevice(&dev);
@@ -876,12 +903,9 @@ void configure_solve_kernels(int max_np) {
   g_smem_optin = optin;
   const int spread = per_sm / 2 - reserved + 128;   // two CTAs asking this much exceed one SM
   g_panel_min_smem = (per_sm > 0 && spread > 0 && spread <= optin) ? (size_t)spread : 0;
-  cudaFuncSetAttribute(k_chol_panel<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)panel_smem<float, 64>());
-  cudaFuncSetAttribute(k_chol_panel<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)panel_smem<float, 32>());
-  cudaFuncSetAttribute(k_chol_panel<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)panel_smem<double, 32>());
+  raise_smem_attr((const void*)k_chol_panel<float, 64>, (int)panel_smem<float, 64>());
+  raise_smem_attr((const void*)k_chol_panel<float, 32>, (int)panel_smem<float, 32>());
+  raise_smem_attr((const void*)k_chol_panel<double, 32>, (int)panel_smem<double, 32>());
   // room for three stages wherever solve_stages may choose them
   auto stages = [&](size_t three) { return three <= (size_t)optin ? 3 : 2; };
   const int f64 = stages(solve_cta_bytes<float, 64>(3, max_np)) * SolveLayout<float, 64>::stage_bytes +
@@ -890,9 +914,9 @@ void configure_solve_kernels(int max_np) {
                   sizeof(float) * max_np;
   const int d32 = stages(solve_cta_bytes<double, 32>(3, max_np)) * SolveLayout<double, 32>::stage_bytes +
                   sizeof(double) * max_np;
-  cudaFuncSetAttribute(k_tri_solve<float, 64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f64);
-  cudaFuncSetAttribute(k_tri_solve<float, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, f32);
-  cudaFuncSetAttribute(k_tri_solve<double, 32, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32);
+  raise_smem_attr((const void*)k_tri_solve<float, 64, double>, f64);
+  raise_smem_attr((const void*)k_tri_solve<float, 32, double>, f32);
+  raise_smem_attr((const void*)k_tri_solve<double, 32, double>, d32);
 }
 
 void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStream_t stream) {

@@ -204,6 +204,8 @@ void launch_apply(const DevProblem& P, const double* dc, const double* dp, doubl
 // Sets the dynamic shared-memory limits of the kernels that need more than 48 KB (call outside capture).
 void configure_kernels(int max_np);
 void configure_solve_kernels(int max_np);
+// SM count of the current device (queried once); grids of persistent or grid-stride kernels are sized by it.
+int num_sms();
 // Shared memory (dynamic and static) of the cluster solve for clusters of up to max_np unknowns (padded).
 size_t solve_smem_bytes(bool mixed, int tile, int max_np);
 

@@ -525,7 +525,7 @@ void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChu
                       cudaStream_t stream) {
   k_cam_pass<real><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
   if (B.nchunks > 0 && P.l < P.m)   // a fixed grid walks the list of chunks inside clusters
-    k_pair_build<real><<<std::min((B.nchunks + PB_WARPS - 1) / PB_WARPS, 3 * 152), 32 * PB_WARPS,
+    k_pair_build<real><<<std::min((B.nchunks + PB_WARPS - 1) / PB_WARPS, 3 * num_sms()), 32 * PB_WARPS,
                          PairStage<real>::bytes, stream>>>(P, W, B, Gbuf);
 }
 

@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(NOALLOC_THREADS) k_noalloc_cost(int m, int n, 
                                                                   double* __restrict__ partial) {
   double s = 0.0;
   int bad = 0;
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < q; o += gridDim.x * blockDim.x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;   // 64-bit: q may come close to INT32_MAX
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < q; o += stride) {
     const int cam = obs_cam[o], pt = obs_pt[o];
     if (cam < 0 || cam >= m || pt < 0 || pt >= n) {
       bad = 1;
@@ -132,6 +133,8 @@ extern "C" stba_status stba_cost_noalloc(const double* cameras, int64_t m, const
   if (!cameras || !points || !obs_cam || !obs_pt || !obs_uv || !F_dev) return STBA_ERR_INVALID_ARG;
   if (m < 1 || n < 1 || q < 1 || q > INT32_MAX || n > INT32_MAX) return STBA_ERR_INVALID_ARG;
   if (m > NOALLOC_MAX_CAMERAS) return STBA_ERR_INVALID_ARG;   // beyond the static scratch
+  // an error left pending by the caller's earlier work is reported, not cleared: it stays for the caller
+  if (cudaPeekAtLastError() != cudaSuccess) return STBA_ERR_CUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return STBA_ERR_CUDA;
   double* scratch = nullptr;
@@ -140,8 +143,10 @@ extern "C" stba_status stba_cost_noalloc(const double* cameras, int64_t m, const
   double* partial = scratch + 15 * (size_t)NOALLOC_MAX_CAMERAS;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   k_noalloc_rt<<<(int)((m + 127) / 128), 128, 0, s>>>((int)m, cameras, rt);
+  if (cudaGetLastError() != cudaSuccess) return STBA_ERR_CUDA;
   k_noalloc_cost<<<NOALLOC_BLOCKS, NOALLOC_THREADS, 0, s>>>((int)m, (int)n, (int)q, rt, points, obs_cam, obs_pt,
                                                              obs_uv, partial);
+  if (cudaGetLastError() != cudaSuccess) return STBA_ERR_CUDA;
   k_noalloc_final<<<1, 256, 0, s>>>(partial, F_dev);
   return cudaGetLastError() == cudaSuccess ? STBA_OK : STBA_ERR_CUDA;
 }

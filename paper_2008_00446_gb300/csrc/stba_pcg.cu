@@ -622,7 +622,7 @@ void pcg_prepare(const DevProblem& P, Scratch<real> W, CamSlots CS, const PcgBuf
   real* J = reinterpret_cast<real*>(B.J);
   real* pw = reinterpret_cast<real*>(B.pw);
   real* upt = reinterpret_cast<real*>(B.upt);
-  const int obs_blocks = std::min((P.q + 255) / 256, 152 * 16);
+  const int obs_blocks = std::min((P.q + 255) / 256, num_sms() * 16);
   const int cam_blocks = (CS.nwarps + 7) / 8;
   const int pt_blocks = std::min((P.n + 255) / 256, 4096);
   const int vec_blocks = std::min((m + RED_THREADS - 1) / RED_THREADS, RED_BLOCKS);

@@ -284,20 +284,47 @@ def stba_stage_times(ctx: Context):
     return list(ms)[: cnt.value]
 
 
+def _noalloc_check(cameras, points, obs_cam, obs_pt, obs_uv, F_out):
+    """Validation of stba_cost_noalloc's arguments, before anything reaches the device.  Shapes come first
+    (the library sizes every device read from them), then dtype, contiguity, and one CUDA device for all."""
+    import torch
+    args = (("cameras", cameras, torch.float64), ("points", points, torch.float64), ("obs_cam", obs_cam, torch.int32),
+            ("obs_pt", obs_pt, torch.int32), ("obs_uv", obs_uv, torch.float64), ("F_out", F_out, torch.float64))
+    for name, t, _ in args:
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"stba_cost_noalloc: {name} must be a torch tensor")
+    m, n, q = cameras.shape[0] if cameras.dim() else -1, points.shape[0] if points.dim() else -1, \
+        obs_cam.shape[0] if obs_cam.dim() else -1
+    want = (("cameras", cameras, (m, 9)), ("points", points, (n, 3)), ("obs_cam", obs_cam, (q,)),
+            ("obs_pt", obs_pt, (q,)), ("obs_uv", obs_uv, (q, 2)))
+    for name, t, shape in want:
+        if tuple(t.shape) != shape or min(shape) < 1:
+            raise ValueError(f"stba_cost_noalloc: {name} has shape {tuple(t.shape)}, expected {shape} with m, n, q >= 1")
+    if F_out.numel() < 1:
+        raise ValueError("stba_cost_noalloc: F_out must hold at least one float64")
+    for name, t, dt in args:
+        if t.dtype != dt or not t.is_contiguous():
+            raise TypeError(f"stba_cost_noalloc: {name} must be a contiguous {dt} tensor "
+                            "(nothing is converted here, since a conversion would allocate)")
+    for name, t, _ in args:
+        if not t.is_cuda or t.device != F_out.device:
+            raise TypeError(f"stba_cost_noalloc: every tensor must be on one CUDA device ({name} is on {t.device}, "
+                            f"F_out on {F_out.device})")
+    return m, n, q
+
+
 def stba_cost_noalloc(cameras, points, obs_cam, obs_pt, obs_uv, F_out, stream=None):
     """F(x) into the device scalar F_out without any device allocation by the library.  Every array must
-    already be a contiguous CUDA tensor of the right dtype (float64 / int32): nothing is converted or
-    copied here, since a conversion would allocate."""
+    already be a contiguous CUDA tensor of the right shape and dtype (float64 / int32) on one device: nothing
+    is converted or copied here, since a conversion would allocate.  The call runs with that device current
+    (its static scratch and, by default, its current stream)."""
     import torch
-    for t, dt in ((cameras, torch.float64), (points, torch.float64), (obs_cam, torch.int32),
-                  (obs_pt, torch.int32), (obs_uv, torch.float64), (F_out, torch.float64)):
-        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
-            raise TypeError("stba_cost_noalloc needs contiguous CUDA tensors (float64 / int32)")
-    st = load().stba_cost_noalloc(ctypes.c_void_p(cameras.data_ptr()), cameras.shape[0],
-                                  ctypes.c_void_p(points.data_ptr()), points.shape[0],
-                                  ctypes.c_void_p(obs_cam.data_ptr()), ctypes.c_void_p(obs_pt.data_ptr()),
-                                  ctypes.c_void_p(obs_uv.data_ptr()), obs_cam.shape[0],
-                                  ctypes.c_void_p(F_out.data_ptr()), _stream_handle(stream))
+    m, n, q = _noalloc_check(cameras, points, obs_cam, obs_pt, obs_uv, F_out)
+    with torch.cuda.device(F_out.device):
+        st = load().stba_cost_noalloc(ctypes.c_void_p(cameras.data_ptr()), m, ctypes.c_void_p(points.data_ptr()), n,
+                                      ctypes.c_void_p(obs_cam.data_ptr()), ctypes.c_void_p(obs_pt.data_ptr()),
+                                      ctypes.c_void_p(obs_uv.data_ptr()), q, ctypes.c_void_p(F_out.data_ptr()),
+                                      _stream_handle(stream))
     if st != 0:
         raise StbaError(st, "stba_cost_noalloc failed")
 

@@ -94,3 +94,25 @@ def test_invalid_options_are_rejected():
     for bad in (-0.5, float("nan"), float("inf")):
         with pytest.raises(stba.StbaError):
             stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, huber_a=bad)
+
+
+def test_noalloc_wrapper_rejects_wrong_shapes_before_any_launch():
+    # the allocation-free cost sizes every device read from the shapes it is given, so the wrapper checks
+    # them all (and dtype, contiguity, one CUDA device) before calling into the library
+    torch = pytest.importorskip("torch")
+    m, n, q = 4, 6, 10
+    good = dict(cameras=torch.zeros((m, 9), dtype=torch.float64), points=torch.zeros((n, 3), dtype=torch.float64),
+                obs_cam=torch.zeros(q, dtype=torch.int32), obs_pt=torch.zeros(q, dtype=torch.int32),
+                obs_uv=torch.zeros((q, 2), dtype=torch.float64), F_out=torch.zeros(1, dtype=torch.float64))
+    bad = [("cameras", torch.zeros(m * 9, dtype=torch.float64)), ("points", torch.zeros((n, 4), dtype=torch.float64)),
+           ("obs_pt", torch.zeros(q - 1, dtype=torch.int32)), ("obs_uv", torch.zeros((q + 1, 2), dtype=torch.float64)),
+           ("obs_uv", torch.zeros((q, 3), dtype=torch.float64)), ("F_out", torch.zeros(0, dtype=torch.float64)),
+           ("cameras", torch.zeros((0, 9), dtype=torch.float64))]
+    for name, t in bad:
+        args = dict(good, **{name: t})
+        with pytest.raises(ValueError):
+            stba.stba_cost_noalloc(**args)
+    with pytest.raises(TypeError):   # right shapes, wrong dtype
+        stba.stba_cost_noalloc(**dict(good, obs_cam=torch.zeros(q, dtype=torch.int64)))
+    with pytest.raises(TypeError):   # right shapes and dtypes, but host tensors
+        stba.stba_cost_noalloc(**good)

@@ -1,8 +1,11 @@
 """Many camera clusters at once: a tile step of the factorisation then has more panel CTAs than the GPU
 holds at a time, so CTAs of one step run in several waves (the 1000-camera scene fits one wave).  Every
 cluster's step is checked against a dense solve of the cluster system the device built (a property that
-holds at any size): dc_k = S'_k^-1 b'_k.  Tolerances: FP64 1e-8 relative (conditioning ~1e4 after Jacobi
-scaling at lambda = 1e-4); mixed 1e-5 (FP32 factor, one FP64 refinement step: (kappa eps_32)^2 ~ 1e-7)."""
+holds at any size): dc_k = S'_k^-1 b'_k, camera by camera.  (tests/test_gpu_full_size.py compares the same
+scene's step with the oracle.)  Tolerances per camera row: FP64 1e-6, the FP64 step bar (measured 6e-8:
+both sides are FP64 solves of a system whose gauge directions are damped only by lambda = 1e-4, so the rows
+of cameras with small steps carry kappa eps_64 of the large ones); mixed 1e-5 (FP32 factor, one FP64
+refinement step: (kappa eps_32)^2 ~ 1e-7 after Jacobi scaling)."""
 import numpy as np
 import pytest
 
@@ -12,6 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2008_00446_gb300 import stba  # noqa: E402
+from elementwise import rows  # noqa: E402
 
 
 def scene():
@@ -19,7 +23,7 @@ def scene():
                                         seed=77, name="many")
 
 
-@pytest.mark.parametrize("precision,tol,tile", [(stba.STBA_FP64, 1e-8, 0), (stba.STBA_MIXED, 1e-5, 0),
+@pytest.mark.parametrize("precision,tol,tile", [(stba.STBA_FP64, 1e-6, 0), (stba.STBA_MIXED, 1e-5, 0),
                                                 (stba.STBA_MIXED, 1e-5, 32)])
 def test_every_cluster_step_solves_its_system(precision, tol, tile):
     s = scene()
@@ -36,7 +40,7 @@ def test_every_cluster_step_solves_its_system(precision, tol, tile):
         S, b = stba.stba_get_cluster_system(ctx, k)
         cams = np.nonzero(s.clusters == k)[0]
         x = np.linalg.solve(S, b)
-        errs.append(np.linalg.norm(dc[cams].ravel() - x) / np.linalg.norm(x))
+        errs.append(rows(dc[cams].ravel(), x, 9))
     assert max(errs) < tol, max(errs)
     ctx.close()
 
@@ -63,3 +67,22 @@ def test_a_cluster_too_large_for_the_solve_is_refused(precision):
         stba.stba_set_clusters(ctx, np.zeros(m, np.int32))
     info = stba.stba_lm_iteration(ctx)   # the previous assignment (40 clusters) stays in force
     assert info["failed_clusters"] == 0 and info["F_before"] == F0 and np.isfinite(info["F_after"])
+
+
+@pytest.mark.parametrize("precision", [stba.STBA_FP64, stba.STBA_MIXED])
+def test_two_live_contexts_with_different_cluster_sizes(precision):
+    # the largest dynamic shared memory of the panel and solve kernels is a per-function attribute; a context
+    # created later with smaller clusters must not lower it below what the earlier one's launches ask for
+    s = scenes.make_config("c0_ring")
+    big = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, np.zeros(s.m, np.int32),
+                           precision=precision)
+    t = scenes.make_tiny_scene(m=6, n=50, seed=7)
+    small = stba.stba_create(t.cameras, t.points, t.obs_cam, t.obs_pt, t.obs_uv, np.arange(6, dtype=np.int32),
+                             precision=precision)
+    for _ in range(2):
+        ia = stba.stba_lm_iteration(big)
+        ib = stba.stba_lm_iteration(small)
+        assert ia["failed_clusters"] == 0 and ib["failed_clusters"] == 0
+        assert np.isfinite(ia["F_after"]) and np.isfinite(ib["F_after"])
+    big.close()
+    small.close()

@@ -11,7 +11,13 @@ import scenes
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import camera as ocam  # noqa: E402
 from paper_2008_00446_gb300 import stba  # noqa: E402
+
+
+def on_device(*arrays):
+    d = torch.device("cuda:0")
+    return [torch.tensor(a, device=d) for a in arrays]
 
 
 def test_noalloc_cost_matches_context_cost_twice():
@@ -30,6 +36,9 @@ def test_noalloc_cost_matches_context_cost_twice():
         stba.stba_cost_noalloc(cams, pts, oc, op, uv, F_out)
         torch.cuda.synchronize()
         assert float(F_out.item()) == pytest.approx(F_ref, rel=1e-12)
+        # and against the oracle's FP64 cost (Sec. 3: F = sum of squared reprojection errors)
+        F_oracle = ocam.cost(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv)
+        assert float(F_out.item()) == pytest.approx(F_oracle, rel=1e-12)
     # a second scene in a row, with other sizes, through the same static scratch
     s2 = scenes.make_tiny_scene(m=7, n=50, seed=3)
     ctx2 = stba.stba_create(s2.cameras, s2.points, s2.obs_cam, s2.obs_pt, s2.obs_uv, s2.clusters)
@@ -52,3 +61,34 @@ def test_noalloc_rejects_too_many_cameras():
     F_out = torch.zeros(1, dtype=torch.float64, device=d)
     with pytest.raises(stba.StbaError):
         stba.stba_cost_noalloc(cams, pts, oc, oc, uv, F_out)
+
+
+def test_noalloc_index_out_of_range_gives_nan():
+    # the kernel checks every index against m and n before it loads; a point index equal to n (made on the
+    # host) marks the sum NaN instead of reading past the points
+    s = scenes.make_tiny_scene(m=5, n=30, seed=7)
+    op = s.obs_pt.copy()
+    op[3] = s.n
+    t = on_device(s.cameras, s.points, s.obs_cam, op, s.obs_uv)
+    F_out = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    stba.stba_cost_noalloc(*t, F_out)
+    torch.cuda.synchronize()
+    assert np.isnan(float(F_out.item()))
+    # the next call with valid indices overwrites every partial of the shared scratch
+    t[3] = torch.tensor(s.obs_pt, device="cuda:0")
+    stba.stba_cost_noalloc(*t, F_out)
+    torch.cuda.synchronize()
+    assert float(F_out.item()) == pytest.approx(ocam.cost(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv),
+                                                rel=1e-12)
+
+
+def test_noalloc_at_the_camera_limit_matches_the_oracle():
+    # m = 16384 exactly, the largest the static scratch holds; cameras 5.. observe nothing (allowed here)
+    s = scenes.make_tiny_scene(m=5, n=30, seed=7)
+    m = 16384
+    cams = np.tile(s.cameras, (m // 5 + 1, 1))[:m].copy()
+    t = on_device(cams, s.points, s.obs_cam, s.obs_pt, s.obs_uv)
+    F_out = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+    stba.stba_cost_noalloc(*t, F_out)
+    torch.cuda.synchronize()
+    assert float(F_out.item()) == pytest.approx(ocam.cost(cams, s.points, s.obs_cam, s.obs_pt, s.obs_uv), rel=1e-12)
