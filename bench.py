@@ -20,6 +20,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -38,7 +40,7 @@ WORKLOADS = {
                 "2-20 consecutive frames, 27 clusters of 45-297 cameras, mixed precision"),
 }
 WORKLOAD = WORKLOADS[CONFIG]
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock
+FP32_PEAK_TFLOPS_DERIVED = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 flops x max SM clock (fallback)
 
 
 def env_rank():
@@ -160,6 +162,8 @@ print(json.dumps({"seconds": dt, "iters": iters, "q": int(s.q), "F": F}))
 
 
 def run_oracle(config, iters, threads=1):
+    """One oracle run in a child process with `threads` BLAS threads (the SciPy-sparse products are
+    single-threaded either way; dense Cholesky factors and products use the threads)."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(threads)
@@ -180,8 +184,9 @@ def reference_arm(args):
     # each step is one oracle LM iteration of the full workload (tens of seconds); stop adding steps once
     # the run would exceed about three minutes
     t_start = time.perf_counter()
+    cores = os.cpu_count() or 1
     for i in range(args.steps):
-        out = run_oracle(CONFIG, 1)
+        out = run_oracle(CONFIG, 1, threads=cores)
         secs.append(out["seconds"])
         q = out["q"]
         el = time.perf_counter() - t_start
@@ -191,16 +196,124 @@ def reference_arm(args):
     tot = sum(secs)
     v = steps / tot
     sample = (f"{steps} step(s), each one STBA LM iteration of the full workload (FP64 SciPy-sparse oracle, "
-              "1 thread) with the scene's fixed azimuth-wedge clustering instead of a new draw")
+              f"{cores} BLAS threads) with the scene's fixed azimuth-wedge clustering instead of a new draw")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2_flush": False},
         "obs_per_s": v * q,
-        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+# ----------------------------------------------------------------------------------------------------------
+STAGES = ["linearise", "s_build", "factorisation", "cluster_solve", "point_update_cost"]
+
+
+def stage_roofline(info0, stage_ms, q, n, m, hbm, alu, config):
+    """Algorithmic bytes (inputs read once, outputs written once) of every stage of one iteration, its HBM
+    fraction at the measured stage time, the DRAM traffic ratio where a capture of the same sources and
+    workload exists, and the factorisation's flops against the measured FP32 and TF32 peaks.  Returns the
+    per-stage table and the dominant stage's roofline object."""
+    s_lower = info0["s_lower_elems"]
+    nv = info0["nv"]
+    bytes_stage = {
+        "linearise": q * (8 + 4 + 4) + n * 24 + m * 72 + nv * 9 * 4 * 2 + n * 9 * 4,
+        "s_build": q * (8 + 4 + 4) + n * 24 + m * 72 + nv * 9 * 4 + s_lower * 4 + m * 9 * 4 * 2,
+        "factorisation": s_lower * (8 + 4),   # FP64 lower triangles read once, FP32 factor written once
+        "cluster_solve": s_lower * 4 * (1 + 2 * 1) + m * 9 * 8,
+        "point_update_cost": q * (8 + 4 + 4) * 2 + n * 24 * 2 + m * 72 * 2 + n * 9 * 4 + n * 24,
+    }
+    fp32_peak = alu["fp32_tflops"] if alu else FP32_PEAK_TFLOPS_DERIVED
+    fp32_src = ("measured: stba_measure_peaks FP32 FMA chains (of measured)" if alu else
+                "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (fallback)")
+    stages = {}
+    for i, nm in enumerate(STAGES):
+        t = float(stage_ms[i])
+        b = float(bytes_stage[nm])
+        gbs = b / (t / 1e3) / 1e9
+        e = {"ms": t, "algorithmic_bytes": b, "achieved_gbs": gbs, "hbm_frac": gbs / hbm}
+        tr = stage_traffic(nm, config)
+        if tr is not None:
+            e["traffic_bytes"] = tr
+            e["traffic_ratio"] = tr / b
+        stages[nm] = e
+    fl = float(info0["factor_flops"])
+    tfl = fl / (float(stage_ms[2]) / 1e3) / 1e12
+    f = stages["factorisation"]
+    f.update(flops=fl, achieved_tflops=tfl, fp32_peak_tflops=fp32_peak, fp32_frac=tfl / fp32_peak)
+    if alu:   # a 3xTF32 product (FP32 accuracy) runs at a third of the dense TF32 rate
+        f.update(tf32_peak_tflops=alu["tf32_tflops"], tensor_3xtf32_frac=tfl / (alu["tf32_tflops"] / 3.0))
+    dom = STAGES[int(np.argmax(stage_ms))]
+    if dom == "factorisation":
+        dominant = {"bound": "alu", "stage": dom, "achieved": tfl, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": tfl / fp32_peak, "traffic": stage_traffic(dom, config), "peak_source": fp32_src}
+    else:
+        e = stages[dom]
+        dominant = {"bound": "hbm", "stage": dom, "achieved": e["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                    "frac": e["hbm_frac"], "traffic": stage_traffic(dom, config),
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    return {"stages": stages, "dominant": dominant}
+
+
+def scene_leg(name, stba, stream, torch, steps=10, compare=True, builder=None, alu=None):
+    """One more scene of the metric, measured outside the headline's timed steps: `steps` iterations after 3
+    warm-up ones, each with its stba_set_clusters (stochastic-graph-clustering draws on the hemisphere scenes,
+    the scene's own uneven segments on the sequential one), CUDA events around each; then the stage times of
+    the same iterations and, with `compare`, the equal-RMSE comparison with full-RCS LM on the GPU."""
+    import scenes
+    t0 = time.perf_counter()
+    s = builder() if builder is not None else scenes.make_config(name)
+    gen_s = time.perf_counter() - t0
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                           precision=stba.STBA_MIXED, stream=stream)
+    n_it = 3 + steps
+    t0 = time.perf_counter()
+    if name == "c2_slam":
+        seq = np.tile(np.asarray(s.clusters, np.int32), (n_it, 1))
+        draw_ms = 0.0
+    else:
+        seq, _ = stba.stba_cluster_sgc(ctx, count=n_it, gamma=SGC_GAMMA, beta=SGC_BETA, seed=s.meta["seed"] + 1)
+        draw_ms = 1e3 * (time.perf_counter() - t0) / n_it
+    for i in range(3):
+        stba.stba_set_clusters(ctx, seq[i])
+        stba.stba_lm_iteration(ctx, want_info=False)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        stba.stba_set_clusters(ctx, seq[3 + i])
+        stba.stba_lm_iteration(ctx, want_info=False)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    st = np.zeros(5)
+    info = {}
+    for i in range(steps):
+        stba.stba_set_clusters(ctx, seq[3 + i])
+        stba.stba_lm_iteration(ctx, want_info=False)
+        st += np.array(stba.stba_stage_times(ctx))
+        for k_, v_ in stba.stba_problem_info(ctx).items():
+            info[k_] = info.get(k_, 0) + v_ / steps
+    st /= steps
+    lam, F, it = stba.stba_get_state(ctx)
+    stba.stba_destroy(ctx)
+    hbm = measured_peaks().get("hbm_gbs", 6800.0)
+    rf = stage_roofline(info, st, s.q, s.n, s.m, hbm, alu, name)
+    step_ms = float(np.median(ms))
+    out = {"cameras": int(s.m), "points": int(s.n), "observations": int(s.q), "generate_s": gen_s,
+           "clusters_mean": float(info.get("l", 0)), "virtual_points_mean": float(info.get("nv", 0)),
+           "ms_per_step": step_ms, "iter_per_s": 1e3 / step_ms, "obs_per_s": 1e3 / step_ms * s.q,
+           "draw_ms_host": draw_ms, "stage_ms": {nm: float(v) for nm, v in zip(STAGES, st)},
+           "stages": rf["stages"], "final_rmse_px": float(np.sqrt(F / (2 * s.q))), "iterations": it,
+           "step": ("set_clusters + one LM iteration; " +
+                    ("the scene's uneven contiguous segments" if name == "c2_slam" else
+                     "a stochastic-graph-clustering draw (Gamma 100, beta 10)"))}
+    if compare:
+        out["full_rcs"] = compare_full_rcs(s, stba, stream, 10, torch)
+    return out
 
 
 # ----------------------------------------------------------------------------------------------------------
@@ -216,6 +329,9 @@ def main():
     ap.add_argument("--compare-iters", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on the 500-camera scene")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factorisation tile")
+    ap.add_argument("--no-scenes", action="store_true",
+                    help="skip the extra scene legs (20000 cameras, 5000-camera sequential, uniform tracks)")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the measured FP32 / TF32 peaks")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -254,9 +370,9 @@ def main():
         sgc = {"note": "the scene's uneven contiguous segments, re-applied every step", "clusters_mean":
                float(np.max(s.clusters) + 1)}
     stba.stba_set_clusters(ctx, seq[0])
-    tile, tile_ms = None, {}
-    if not args.no_autotune:   # the factorisation tile, chosen by timing (outside the timed steps)
-        tile, tile_ms = stba.stba_autotune(ctx, 5)
+    tile, update, tile_ms = None, None, {}
+    if not args.no_autotune:   # the factorisation tile and trailing update, chosen by timing (outside the timed steps)
+        tile, update, tile_ms = stba.stba_autotune(ctx, 5)
     for i in range(max(args.warmup, 3)):
         stba.stba_set_clusters(ctx, seq[i])
         stba.stba_lm_iteration(ctx, want_info=False)
@@ -311,32 +427,28 @@ def main():
     torch.cuda.synchronize()
     fixed_ms = float(np.mean([a.elapsed_time(b) for a, b in fixed_ms]))
 
-    # roofline of the dominant stage (stage averages over the timed steps)
+    # measured arithmetic peaks (outside the timed region), with the SM clock sampled while they run
+    alu = None
+    if not args.no_peaks:
+        psampler = ClockSampler(local)
+        psampler.start()
+        fp32s, tf32s = [], []
+        t_end = time.perf_counter() + 1.5
+        while time.perf_counter() < t_end or not fp32s:
+            a_, b_ = stba.stba_measure_peaks(3, stream)
+            fp32s.append(a_)
+            tf32s.append(b_)
+        alu = {"fp32_tflops": max(fp32s), "tf32_tflops": max(tf32s), "runs": len(fp32s), "clocks": psampler.stop(),
+               "how": "stba_measure_peaks: FP32 FMA chains on every SM (CUDA cores); tcgen05.mma kind::tf32 "
+                      "M128 N256 K8 back to back into TMEM, one CTA per SM (tensor cores); best of the runs"}
+    # roofline of the dominant stage and of every stage (stage averages over the timed steps)
     q, n, m = s.q, s.n, s.m
-    peaks = measured_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    names = ["linearise", "s_build", "factorisation", "cluster_solve", "point_update_cost"]
-    dom = int(np.argmax(stage_ms))
-    s_lower = info0["s_lower_elems"]
-    # algorithmic bytes per stage (inputs read once, outputs written once)
-    bytes_stage = {
-        0: q * (8 + 4 + 4) + n * 24 + m * 72 + info0["nv"] * 9 * 4 * 2 + n * 9 * 4,
-        1: q * (8 + 4 + 4) + n * 24 + m * 72 + info0["nv"] * 9 * 4 + s_lower * 4 + m * 9 * 4 * 2,
-        3: s_lower * 4 * (1 + 2 * 1) + m * 9 * 8,
-        4: q * (8 + 4 + 4) * 2 + n * 24 * 2 + m * 72 * 2 + n * 9 * 4 + n * 24,
-    }
-    if dom == 2:
-        achieved = info0["factor_flops"] / (stage_ms[2] / 1e3) / 1e12
-        roofline = {"bound": "alu", "stage": names[2], "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                    "traffic": stage_traffic(names[2], args.config),
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (FP32 SIMT)"}
-    else:
-        achieved = bytes_stage[dom] / (stage_ms[dom] / 1e3) / 1e9
-        roofline = {"bound": "hbm", "stage": names[dom], "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": stage_traffic(names[dom], args.config),
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roofline["stage_ms"] = {nm: float(v) for nm, v in zip(names, stage_ms)}
+    rf = stage_roofline(info0, stage_ms, q, n, m, measured_peaks().get("hbm_gbs", 6800.0), alu, args.config)
+    roofline = rf["dominant"]
+    roofline["stage_ms"] = {nm: float(v) for nm, v in zip(STAGES, stage_ms)}
+    roofline["stages"] = rf["stages"]
+    if alu:
+        roofline["measured_alu_peaks"] = alu
 
     # end to end through the C ABI with host buffers: parameters and the iteration's clustering in, one
     # iteration, parameters out
@@ -372,7 +484,9 @@ def main():
                 "d2h_bytes_per_step": nbytes_out},
         "step": "set_clusters (a stochastic-graph-clustering draw) + one LM iteration (Algorithm 1)",
         "sgc": sgc,
-        "autotune": {"factor_tile": tile, "ms_per_iter": {str(k_): v_ for k_, v_ in tile_ms.items()}},
+        "autotune": {"factor_tile": tile, "factor_update": {stba.STBA_FACTOR_UPDATE_TENSOR: "tensor",
+                                                            stba.STBA_FACTOR_UPDATE_SIMT: "simt"}.get(update),
+                     "ms_per_iter": {str(k_): v_ for k_, v_ in tile_ms.items()}},
         "fixed_clusters_ms_per_iter": fixed_ms,
         "gpu_launches": int(round((info0["launches_per_iter"] + REORDER_LAUNCHES) * args.steps)),
         "clocks": clocks,
@@ -384,12 +498,26 @@ def main():
     if rank == 0 and world == 1 and not args.no_adjoint:
         out["adjoint"] = time_adjoint(stba, stream, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == CONFIG:
-        t = run_oracle(args.config, 1)
-        v = 1.0 / t["seconds"]
-        out["cpu_baseline"] = {"value": v, "unit": "iter/s", "cores": 1, "kind": "oracle",
-                               "sample": "one STBA LM iteration of the full workload (FP64 SciPy-sparse "
-                                         "oracle, 1 thread) with the scene's fixed azimuth-wedge clustering"}
+        cores = os.cpu_count() or 1
+        t1 = run_oracle(args.config, 1, threads=1)
+        tn = run_oracle(args.config, 1, threads=cores)
+        out["cpu_baseline"] = {"value": 1.0 / tn["seconds"], "unit": "iter/s", "cores": cores, "kind": "oracle",
+                               "sample": f"one STBA LM iteration of the full workload (FP64 SciPy-sparse oracle, "
+                                         f"{cores} BLAS threads = nproc) with the scene's fixed azimuth-wedge "
+                                         "clustering",
+                               "single_thread": {"value": 1.0 / t1["seconds"], "unit": "iter/s", "cores": 1}}
     stba.stba_destroy(ctx)
+    if rank == 0 and world == 1 and not args.no_scenes and args.config == CONFIG:
+        # the other scenes of the metric (outside the timed steps): the 20000-camera scene, the 5000-camera
+        # sequential scene, and the headline scene with tracks drawn uniformly among the cameras that see a point
+        import scenes as _sc
+        c1kw = dict(_sc.CONFIGS["c1_internet"][1], tracks="uniform", name="internet_uniform")
+        out["scenes"] = {
+            "c4_large": scene_leg("c4_large", stba, stream, torch, alu=alu),
+            "c2_slam": scene_leg("c2_slam", stba, stream, torch, alu=alu),
+            "c1_uniform_tracks": scene_leg("c1_uniform_tracks", stba, stream, torch, alu=alu,
+                                           builder=lambda: _sc.make_hemisphere_scene(**c1kw)),
+        }
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

@@ -81,7 +81,15 @@ typedef struct {
   int32_t factor_tile;      /* tile of the cluster factorisation: 0 = default (64 for the FP32 factor of
                                STBA_MIXED, 32 for FP64); STBA_MIXED also accepts 32.  stba_autotune picks
                                between the candidates by timing. */
+  int32_t factor_update;    /* trailing update A_ij -= L_ik L_jk^T of the cluster factorisation (Eq. 13's
+                               dense LL^T): 0 = default (STBA_FACTOR_UPDATE_TENSOR where it applies, else
+                               STBA_FACTOR_UPDATE_SIMT); STBA_FACTOR_UPDATE_SIMT = FP32/FP64 FMA on the CUDA
+                               cores; STBA_FACTOR_UPDATE_TENSOR = tcgen05 tensor cores, TF32 operands split
+                               in three products for FP32 accuracy (the FP32 factor of STBA_MIXED with tile
+                               64 only; other settings return STBA_ERR_INVALID_ARG). */
 } stba_options;
+
+enum { STBA_FACTOR_UPDATE_DEFAULT = 0, STBA_FACTOR_UPDATE_SIMT = 1, STBA_FACTOR_UPDATE_TENSOR = 2 };
 
 typedef struct {
   double F_before;      /* F(x) at the start of the iteration */
@@ -248,14 +256,26 @@ void stba_graph_destroy(stba_graph* g);
 stba_status stba_cluster_sgc(stba_ctx* ctx, int32_t gamma, double beta, uint64_t seed, int32_t count,
                              int32_t* cluster_assignments, int32_t* l);
 
-/* Autotuner (the paper has none): times `iterations` LM iterations with every candidate tile of the
- * cluster factorisation (STBA_MIXED: 64 and 32; FP64: 32 only) on the current parameters and cluster
- * assignment, restores the parameters, damping and cost after each trial, and keeps the fastest tile for
- * the following iterations.  *tile (optional) receives the choice, ms[0..1] (optional) the time per
- * iteration with tiles 64 and 32 (-1 when not tried).  Synchronises the context stream.  Errors:
- * STBA_ERR_STATE while iterations are being recorded (stba_record), STBA_ERR_INVALID_ARG for
- * iterations < 1. */
-stba_status stba_autotune(stba_ctx* ctx, int32_t iterations, int32_t* tile, float* ms);
+/* Autotuner (the paper has none): times `iterations` LM iterations with every candidate configuration of
+ * the cluster factorisation on the current parameters and cluster assignment, restores the parameters,
+ * damping and cost after each trial, and keeps the fastest for the following iterations.  Candidates
+ * (STBA_MIXED; FP64 has one): 0 = tile 64 with the tensor-core trailing update, 1 = tile 64 with the
+ * CUDA-core update, 2 = tile 32 with the CUDA-core update.  *tile and *update (optional) receive the
+ * choice (tile 64 or 32, STBA_FACTOR_UPDATE_TENSOR or _SIMT), ms[0..2] (optional) the time per iteration of
+ * each candidate (-1 when not tried).  Synchronises the context stream.  Errors: STBA_ERR_STATE while
+ * iterations are being recorded (stba_record), STBA_ERR_INVALID_ARG for iterations < 1. */
+stba_status stba_autotune(stba_ctx* ctx, int32_t iterations, int32_t* tile, int32_t* update, float* ms);
+
+/* Measured arithmetic peaks of the current GPU, the denominators of the factorisation's roofline.  The
+ * paper has no counterpart: this is measurement infrastructure.  *fp32_tflops (optional): FP32 FMA rate of
+ * the CUDA cores (16 independent FMA chains per thread, 4 CTAs of 256 threads per SM).  *tf32_tflops
+ * (optional): dense TF32 rate of the tensor cores (tcgen05.mma kind::tf32, M = 128, N = 256, K = 8, back to
+ * back into one TMEM accumulator, one CTA per SM); a 3xTF32 product of FP32 accuracy runs at a third of it.
+ * Each kernel runs once untimed, then `reps` times between events on cuda_stream.  Allocates (and frees) a
+ * few bytes of device memory; synchronises the stream.  Errors: STBA_ERR_INVALID_ARG (reps < 1, both outputs
+ * NULL), STBA_ERR_CUDA (a CUDA error, also one already pending), STBA_ERR_TIMEOUT (the tensor-core kernel's
+ * bounded wait gave up). */
+stba_status stba_measure_peaks(void* cuda_stream, int32_t reps, double* fp32_tflops, double* tf32_tflops);
 
 /* Frees every device allocation of the context.  NULL is allowed. */
 void stba_destroy(stba_ctx* ctx);

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libstba.so")
 BUILD = os.path.join(PKG, "_build")
 SOURCES = ["stba_api.cu", "stba_kernels.cu", "stba_chol.cu", "stba_noalloc.cu", "stba_adjoint.cu", "stba_pcg.cu",
-           "stba_graph.cu", "stba_order.cu"]
+           "stba_graph.cu", "stba_order.cu", "stba_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

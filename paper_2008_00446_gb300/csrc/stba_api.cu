@@ -130,6 +130,7 @@ struct stba_ctx {
   cudaGraphExec_t graph = nullptr;
   bool graph_stale = false;             // the cluster layout changed since the graph was captured
   int tile = 32;                        // factorisation tile (stba_autotune may change the FP32 one)
+  int update_tc = 0;                    // trailing updates on the tensor cores (FP32 factor, tile 64)
   bool capturing = false;
   bool timing = false;
   int launches_per_iter = 0;
@@ -453,8 +454,12 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
       const int ntk = c->h_np[k] / TF;
       if (ntk <= kt) continue;
       for (int i = kt; i < ntk; ++i) panel.push_back(make_int2(k, i));
-      for (int j = kt + 2; j < ntk; ++j)   // column kt + 1 is updated by panel kt + 1 itself
-        for (int i = j; i < ntk; ++i) update.push_back(make_int2(k, (i << 16) | j));
+      for (int j = kt + 2; j < ntk; ++j) {   // column kt + 1 is updated by panel kt + 1 itself
+        if (c->update_tc)   // tile pairs (i0, i0 + 1) x j, from the diagonal tile down
+          for (int i0 = j; i0 < ntk; i0 += 2) update.push_back(make_int2(k, (i0 << 16) | j));
+        else
+          for (int i = j; i < ntk; ++i) update.push_back(make_int2(k, (i << 16) | j));
+      }
     }
   }
   c->h_panel_off[max_nt] = (int)panel.size();
@@ -552,7 +557,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
                         c->h_panel_off.data(),
                         c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
-                        c->ev_panel.data(), c->ev_update.data(), TF};
+                        c->ev_panel.data(), c->ev_update.data(), TF, c->update_tc};
   }
   {
     int least = 0, greatest = 0;
@@ -862,6 +867,7 @@ void stba_default_options(stba_options* o) {
   o->linear_solver = STBA_SOLVER_CLUSTERS;
   o->pcg_max_iter = 500;
   o->pcg_tol = 1e-6;
+  o->factor_update = STBA_FACTOR_UPDATE_DEFAULT;
 }
 
 const char* stba_status_string(stba_status s) {
@@ -970,12 +976,16 @@ stba_status stba_cluster_sgc(stba_ctx* c, int32_t gamma, double beta, uint64_t s
   return STBA_OK;
 }
 
-stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, float* ms) {
+stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, int32_t* update, float* ms) {
   if (!c || iterations < 1) return STBA_ERR_INVALID_ARG;
   if (c->tape_cap > 0) return fail(c, STBA_ERR_STATE, "stba_autotune is not allowed while iterations are recorded");
-  if (ms) ms[0] = ms[1] = -1.0f;
-  if (!c->mixed || c->use_pcg || c->use_spcg) {   // one candidate (or no factorisation at all)
+  if (ms) ms[0] = ms[1] = ms[2] = -1.0f;
+  auto report = [&]() {
     if (tile) *tile = c->tile;
+    if (update) *update = c->update_tc ? STBA_FACTOR_UPDATE_TENSOR : STBA_FACTOR_UPDATE_SIMT;
+  };
+  if (!c->mixed || c->use_pcg || c->use_spcg) {   // one candidate (or no factorisation at all)
+    report();
     return STBA_OK;
   }
   // state to restore after every trial: parameters, residuals at x (in the order of this assignment, which
@@ -1006,14 +1016,15 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, float*
            copy(c->st, st0, sizeof(DevState));
   };
   const std::vector<int> cl = c->h_clusters;
-  const int cand[2] = {64, 32};
+  const int cand_tile[3] = {64, 64, 32}, cand_tc[3] = {1, 0, 0};
   float best_ms = 0.f;
-  int best = c->tile;
+  int best = -1;
   stba_status s = STBA_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) ok = false;
-  for (int t = 0; t < 2 && ok && s == STBA_OK; ++t) {
-    c->tile = cand[t];
+  for (int t = 0; t < 3 && ok && s == STBA_OK; ++t) {
+    c->tile = cand_tile[t];
+    c->update_tc = cand_tc[t];
     if ((s = set_clusters_host(c, cl)) != STBA_OK) break;
     ok = restore();
     if (ok && (s = run_iteration(c)) != STBA_OK) break;   // warm-up: capture, first launch
@@ -1025,15 +1036,16 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, float*
     ok = ok && cudaEventElapsedTime(&el, e0, e1) == cudaSuccess;
     const float per = el / iterations;
     if (ms) ms[t] = per;
-    if (ok && (t == 0 || per < best_ms)) {
+    if (ok && (best < 0 || per < best_ms)) {
       best_ms = per;
-      best = cand[t];
+      best = t;
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
-  if (s == STBA_OK && ok) {
-    c->tile = best;
+  if (s == STBA_OK && ok && best >= 0) {
+    c->tile = cand_tile[best];
+    c->update_tc = cand_tc[best];
     s = set_clusters_host(c, cl);
     if (s == STBA_OK) ok = restore() && cudaStreamSynchronize(c->stream) == cudaSuccess;
   }
@@ -1041,7 +1053,7 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, float*
   if (s != STBA_OK) return s;
   if (!ok) return fail(c, STBA_ERR_CUDA, "stba_autotune: a copy or an event failed");
   c->have_stage_times = false;
-  if (tile) *tile = c->tile;
+  report();
   return STBA_OK;
 }
 
@@ -1101,13 +1113,18 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
        c->opt.linear_solver != STBA_SOLVER_PCG_CLUSTERS) ||
       (c->opt.linear_solver != STBA_SOLVER_CLUSTERS && (c->opt.pcg_max_iter < 1 || !(c->opt.pcg_tol > 0))) ||
       !(c->opt.huber_a >= 0.0) || !std::isfinite(c->opt.huber_a) ||
-      !(c->opt.factor_tile == 0 || c->opt.factor_tile == 32 || (c->opt.factor_tile == 64 && c->opt.precision == STBA_MIXED)))
+      !(c->opt.factor_tile == 0 || c->opt.factor_tile == 32 || (c->opt.factor_tile == 64 && c->opt.precision == STBA_MIXED)) ||
+      (c->opt.factor_update != STBA_FACTOR_UPDATE_DEFAULT && c->opt.factor_update != STBA_FACTOR_UPDATE_SIMT &&
+       c->opt.factor_update != STBA_FACTOR_UPDATE_TENSOR) ||
+      (c->opt.factor_update == STBA_FACTOR_UPDATE_TENSOR &&
+       !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
   c->m = m;
   c->n = n;
   c->q = q;
   c->mixed = c->opt.precision == STBA_MIXED;
   c->tile = c->opt.factor_tile ? c->opt.factor_tile : factor_tile(c->mixed);
+  c->update_tc = c->mixed && c->tile == 64 && c->opt.factor_update != STBA_FACTOR_UPDATE_SIMT;
   c->use_pcg = c->opt.linear_solver == STBA_SOLVER_PCG_FULL;
   c->use_spcg = c->opt.linear_solver == STBA_SOLVER_PCG_CLUSTERS;
   c->set.correction = c->opt.correction;

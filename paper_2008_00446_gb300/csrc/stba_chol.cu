@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "stba_internal.cuh"
+#include "stba_tc.cuh"
 
 namespace stba {
 
@@ -453,6 +454,119 @@ __global__ void __launch_bounds__(256) k_chol_update(F* L, DevProblem P, const i
 }
 
 // ------------------------------------------------------------------------------------------------------
+// Trailing update on the fifth-generation tensor cores (FP32 factor, T = 64).  One CTA per item (k, i0, j)
+// updates the two tiles (i0, j) and (i0 + 1, j) of cluster k:  [A_i0,j; A_i0+1,j] -= [L_i0,kt; L_i0+1,kt] L_j,kt^T,
+// one 128 x 64 x 64 product D = A B^T by tcgen05.mma (kind::tf32, FP32 accumulation in tensor memory).
+// FP32 accuracy from TF32 operands: every value x is split into hi = tf32(x) and lo = tf32(x - hi), and
+// D = A_hi B_lo + A_lo B_hi + A_hi B_hi (3xTF32; the dropped A_lo B_lo is below FP32 rounding), 24 MMAs
+// of K = 8 issued by one thread.  The operands are converted by all threads into the no-swizzle K-major
+// core-matrix layout (stba_tc.cuh); while the MMAs run, each thread loads the 32 old values it will
+// update (one row, 32 columns), then subtracts its 32 accumulator columns read from TMEM.  The wait for
+// the MMAs is bounded: a CTA that gives up marks the cluster failed (the LM step is rejected), frees its
+// tensor memory and returns.  When i0 + 1 is past the cluster's last tile, the second half of A is zero and
+// its rows are not written.
+constexpr int TCU_THREADS = 256;
+constexpr size_t TCU_SMEM = sizeof(uint32_t) * (2 * 128 * 64 + 2 * 64 * 64);   // A hi/lo, B hi/lo: 96 KB
+constexpr int TCU_MAX_POLLS = 1 << 26;
+
+__device__ __forceinline__ void split_store(uint32_t* hi, uint32_t* lo, int off, float4 v) {
+  const uint32_t h0 = tc::to_tf32(v.x), h1 = tc::to_tf32(v.y), h2 = tc::to_tf32(v.z), h3 = tc::to_tf32(v.w);
+  *reinterpret_cast<uint4*>(hi + off) = make_uint4(h0, h1, h2, h3);
+  *reinterpret_cast<uint4*>(lo + off) =
+      make_uint4(tc::to_tf32(v.x - __uint_as_float(h0)), tc::to_tf32(v.y - __uint_as_float(h1)),
+                 tc::to_tf32(v.z - __uint_as_float(h2)), tc::to_tf32(v.w - __uint_as_float(h3)));
+}
+
+__global__ void __launch_bounds__(TCU_THREADS, 2) k_chol_update_tc(float* L, DevProblem P, const int2* items, int kt,
+                                                                  int* fail_flags) {
+  constexpr int T = 64;
+  extern __shared__ __align__(128) uint32_t tsm[];
+  uint32_t* Ah = tsm;   // 128 x 64 TF32, core-matrix layout
+  uint32_t* Al = tsm + 128 * 64;
+  uint32_t* Bh = tsm + 2 * 128 * 64;   // 64 x 64
+  uint32_t* Bl = Bh + 64 * 64;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  const int2 it = items[blockIdx.x];
+  const int k = it.x, i0 = it.y >> 16, j = it.y & 0xffff;
+  const int np = P.cluster_np[k];
+  float* A = L + P.S_off[k];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rows_valid = min(128, np - i0 * T);   // 64 or 128
+  const float* srcA = A + (size_t)(i0 * T) * np + kt * T;
+  const float* srcB = A + (size_t)(j * T) * np + kt * T;
+  // 16-byte chunk q = tid + 256 u: row (q >> 7) * 8 + (q & 7), columns 4 ((q >> 3) & 15) ..: the 8 threads of a
+  // shared-memory store phase write one whole core matrix (no bank conflicts).  Every load of the thread (its
+  // 12 operand chunks and the 32 old values it will update) is issued before any of them is used.
+  const int R = 32 * (warp & 3) + lane, c0 = 32 * (warp >> 2);   // epilogue: row R, columns c0 .. c0 + 31
+  const bool valid = R < rows_valid;
+  float* dst = A + (size_t)(i0 * T + R) * np + j * T + c0;
+  float4 va[8], vb[4], old[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int q = tid + TCU_THREADS * u;
+    const int r = ((q >> 7) << 3) | (q & 7), kc = (q >> 3) & 15;
+    va[u] = r < rows_valid ? *reinterpret_cast<const float4*>(srcA + (size_t)r * np + 4 * kc)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int q = tid + TCU_THREADS * u;
+    const int r = ((q >> 7) << 3) | (q & 7), kc = (q >> 3) & 15;
+    vb[u] = *reinterpret_cast<const float4*>(srcB + (size_t)r * np + 4 * kc);
+  }
+#pragma unroll
+  for (int v = 0; v < 8; ++v) old[v] = valid ? *reinterpret_cast<const float4*>(dst + 4 * v) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int q = tid + TCU_THREADS * u;
+    split_store(Ah, Al, tc::core_off<64>(((q >> 7) << 3) | (q & 7), 4 * ((q >> 3) & 15)), va[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int q = tid + TCU_THREADS * u;
+    split_store(Bh, Bl, tc::core_off<64>(((q >> 7) << 3) | (q & 7), 4 * ((q >> 3) & 15)), vb[u]);
+  }
+  tc::fence_async_smem();
+  if (tid == 0) tc::mbar_init(&mbar, 1);
+  if (warp == 0) tc::tmem_alloc(&taddr_s, 64);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = taddr_s;
+  if (tid == 0) {
+    constexpr uint32_t idesc = tc::idesc_tf32(128, 64);
+    const uint32_t pa[3] = {tc::smem_u32(Ah), tc::smem_u32(Al), tc::smem_u32(Ah)};
+    const uint32_t pb[3] = {tc::smem_u32(Bl), tc::smem_u32(Bh), tc::smem_u32(Bh)};
+#pragma unroll
+    for (int pass = 0; pass < 3; ++pass)
+#pragma unroll
+      for (int ks = 0; ks < 8; ++ks)
+        tc::mma_tf32(tmem, tc::smem_desc(pa[pass] + ks * 256, 128, 2048), tc::smem_desc(pb[pass] + ks * 256, 128, 2048),
+                     idesc, (pass | ks) != 0);
+    tc::mma_commit(&mbar);
+  }
+  // thread (lane quarter warp & 3, column half warp >> 2): row R of the 128, columns c0 .. c0 + 31 of tile j
+  const bool done = __all_sync(0xffffffffu, tc::mbar_wait_bounded(&mbar, 0, TCU_MAX_POLLS));
+  if (done) {
+    tc::fence_after_sync();
+    float d[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, d);
+    if (valid) {
+#pragma unroll
+      for (int v = 0; v < 8; ++v)
+        *reinterpret_cast<float4*>(dst + 4 * v) =
+            make_float4(old[v].x - d[4 * v], old[v].y - d[4 * v + 1], old[v].z - d[4 * v + 2], old[v].w - d[4 * v + 3]);
+    }
+  } else if (lane == 0) {
+    atomicExch(fail_flags + k, 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+// ------------------------------------------------------------------------------------------------------
 template <typename F>
 __device__ F warp_sum(F v) {
 #pragma unroll
@@ -817,8 +931,18 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
     cudaEventRecord(plan.ev_panel[kt], stream);
     cudaStreamWaitEvent(side, plan.ev_panel[kt], 0);
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];
-    if (nu > 0)
-      launch_prio(k_chol_update<F, T>, nu, 0, side, plan.prio_low, L, P, plan.update_items + plan.h_update_off[kt], kt);
+    if (nu > 0) {
+      if constexpr (sizeof(F) == 4 && T == 64) {
+        if (plan.update_tc) {
+          launch_prio(k_chol_update_tc, nu, TCU_SMEM, side, plan.prio_low, reinterpret_cast<float*>(L), P,
+                      plan.update_items + plan.h_update_off[kt], kt, fb.fail_flags);
+        } else {
+          launch_prio(k_chol_update<F, T>, nu, 0, side, plan.prio_low, L, P, plan.update_items + plan.h_update_off[kt], kt);
+        }
+      } else {
+        launch_prio(k_chol_update<F, T>, nu, 0, side, plan.prio_low, L, P, plan.update_items + plan.h_update_off[kt], kt);
+      }
+    }
     cudaEventRecord(plan.ev_update[kt], side);
   }
   cudaEventRecord(plan.ev_join, side);
@@ -906,6 +1030,7 @@ void configure_solve_kernels(int max_np) {
   raise_smem_attr((const void*)k_chol_panel<float, 64>, (int)panel_smem<float, 64>());
   raise_smem_attr((const void*)k_chol_panel<float, 32>, (int)panel_smem<float, 32>());
   raise_smem_attr((const void*)k_chol_panel<double, 32>, (int)panel_smem<double, 32>());
+  raise_smem_attr((const void*)k_chol_update_tc, (int)TCU_SMEM);
   // room for three stages wherever solve_stages may choose them
   auto stages = [&](size_t three) { return three <= (size_t)optin ? 3 : 2; };
   const int f64 = stages(solve_cta_bytes<float, 64>(3, max_np)) * SolveLayout<float, 64>::stage_bytes +

@@ -227,6 +227,8 @@ struct CholPlan {
   const cudaEvent_t* ev_panel;    // [nsteps]
   const cudaEvent_t* ev_update;   // [nsteps]
   int tile;                       // factorisation tile T (the dense blocks are padded to it)
+  int update_tc;                  // 1: trailing updates on the tensor cores (FP32 factor, T = 64); the update
+                                  // items are then (cluster, (i0 << 16) | j) for the tile pair (i0, i0 + 1) x j
 };
 struct FactorBuffers {
   void* L;          // factor (F = float or double), same layout as S'

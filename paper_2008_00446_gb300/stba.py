@@ -17,6 +17,7 @@ _LIB = None
 
 STBA_FP64, STBA_MIXED = 0, 1
 STBA_SOLVER_CLUSTERS, STBA_SOLVER_PCG_FULL, STBA_SOLVER_PCG_CLUSTERS = 0, 1, 2
+STBA_FACTOR_UPDATE_DEFAULT, STBA_FACTOR_UPDATE_SIMT, STBA_FACTOR_UPDATE_TENSOR = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not SPD",
           5: "non-finite value", 6: "timeout", 7: "invalid state"}
 
@@ -26,7 +27,7 @@ EXPORTS = ["stba_default_options", "stba_create", "stba_set_clusters", "stba_lm_
            "stba_last_step", "stba_problem_info", "stba_get_cluster_system", "stba_set_timing",
            "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error", "stba_cost_noalloc",
            "stba_record", "stba_adjoint", "stba_graph_create", "stba_graph_edges", "stba_graph_cluster",
-           "stba_graph_cluster_batch", "stba_graph_destroy", "stba_cluster_sgc", "stba_autotune"]
+           "stba_graph_cluster_batch", "stba_graph_destroy", "stba_cluster_sgc", "stba_autotune", "stba_measure_peaks"]
 
 
 class StbaOptions(ctypes.Structure):
@@ -35,7 +36,7 @@ class StbaOptions(ctypes.Structure):
                 ("ftol", ctypes.c_double), ("gtol", ctypes.c_double), ("xtol", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
-                ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32)]
+                ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32), ("factor_update", ctypes.c_int32)]
 
 
 class StbaIterInfo(ctypes.Structure):
@@ -103,7 +104,8 @@ def load(build_if_missing: bool = True):
         "stba_graph_cluster_batch": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
         "stba_graph_destroy": (None, [P]),
         "stba_cluster_sgc": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
-        "stba_autotune": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float)]),
+        "stba_autotune": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float)]),
+        "stba_measure_peaks": (I32, [P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -329,12 +331,22 @@ def stba_cost_noalloc(cameras, points, obs_cam, obs_pt, obs_uv, F_out, stream=No
         raise StbaError(st, "stba_cost_noalloc failed")
 
 
+def stba_measure_peaks(reps=5, stream=None):
+    """Measured FP32 CUDA-core and dense TF32 tensor-core rates of the current GPU: (fp32_tflops, tf32_tflops)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load().stba_measure_peaks(_stream_handle(stream), int(reps), ctypes.byref(a), ctypes.byref(b))
+    if st != 0:
+        raise StbaError(st, "stba_measure_peaks failed")
+    return a.value, b.value
+
+
 def stba_autotune(ctx: Context, iterations=5):
-    """Times the candidate factorisation tiles and keeps the fastest: (tile, {64: ms, 32: ms})."""
-    tile = ctypes.c_int32()
-    ms = (ctypes.c_float * 2)()
-    ctx._check(load().stba_autotune(ctx.handle, int(iterations), ctypes.byref(tile), ms))
-    return tile.value, {64: ms[0], 32: ms[1]}
+    """Times the candidate factorisations and keeps the fastest: (tile, update, {candidate: ms}) with the
+    candidates "64_tensor" (tile 64, tensor-core trailing update), "64_simt" and "32_simt"."""
+    tile, update = ctypes.c_int32(), ctypes.c_int32()
+    ms = (ctypes.c_float * 3)()
+    ctx._check(load().stba_autotune(ctx.handle, int(iterations), ctypes.byref(tile), ctypes.byref(update), ms))
+    return tile.value, update.value, {"64_tensor": ms[0], "64_simt": ms[1], "32_simt": ms[2]}
 
 
 def stba_record(ctx: Context, max_iter: int):

@@ -91,6 +91,12 @@ def test_invalid_options_are_rejected():
                              factor_tile=bad_tile)
     with pytest.raises(stba.StbaError):   # the FP64 factor has one tile
         stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, factor_tile=64)
+    # the tensor-core trailing update exists for the FP32 factor with tile 64 only
+    for kw in (dict(factor_update=stba.STBA_FACTOR_UPDATE_TENSOR),
+               dict(precision=1, factor_tile=32, factor_update=stba.STBA_FACTOR_UPDATE_TENSOR),
+               dict(precision=1, factor_update=3), dict(precision=1, factor_update=-1)):
+        with pytest.raises(stba.StbaError):
+            stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, **kw)
     for bad in (-0.5, float("nan"), float("inf")):
         with pytest.raises(stba.StbaError):
             stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, huber_a=bad)

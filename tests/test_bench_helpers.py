@@ -79,3 +79,30 @@ def test_max_over_ranks_on_two_gloo_ranks(tmp_path):
     tmp_mp.start_processes(_max_worker, args=(2, port, str(tmp_path)), nprocs=2, start_method="spawn", join=True)
     assert [float((tmp_path / f"r{r}.txt").read_text()) for r in range(2)] == [13.0, 13.0]
     assert bench.max_over_ranks(7.5) == 7.5   # no process group: the value itself
+
+
+def test_stage_roofline_fractions_and_dominant_stage():
+    import bench
+    info = {"s_lower_elems": 1e6, "nv": 1e5, "factor_flops": 2e9}
+    q, n, m = 100_000, 20_000, 100
+    alu = {"fp32_tflops": 60.0, "tf32_tflops": 900.0}
+    stage_ms = [0.1, 0.2, 0.4, 0.15, 0.1]
+    rf = bench.stage_roofline(info, stage_ms, q, n, m, 6000.0, alu, "no_such_workload")
+    st = rf["stages"]
+    assert list(st) == bench.STAGES
+    for nm, t in zip(bench.STAGES, stage_ms):
+        e = st[nm]
+        assert e["ms"] == t
+        assert abs(e["achieved_gbs"] - e["algorithmic_bytes"] / (t / 1e3) / 1e9) < 1e-9 * e["achieved_gbs"]
+        assert abs(e["hbm_frac"] - e["achieved_gbs"] / 6000.0) < 1e-12
+        assert "traffic_ratio" not in e   # no capture of this workload
+    f = st["factorisation"]
+    assert abs(f["achieved_tflops"] - 2e9 / 0.4e-3 / 1e12) < 1e-12
+    assert abs(f["fp32_frac"] - f["achieved_tflops"] / 60.0) < 1e-12
+    assert abs(f["tensor_3xtf32_frac"] - f["achieved_tflops"] / 300.0) < 1e-12
+    d = rf["dominant"]
+    assert d["stage"] == "factorisation" and d["bound"] == "alu" and d["peak"] == 60.0
+    # an HBM-bound dominant stage, and the derived FP32 peak when none was measured
+    rf2 = bench.stage_roofline(info, [0.1, 0.9, 0.4, 0.15, 0.1], q, n, m, 6000.0, None, "x")
+    assert rf2["dominant"]["stage"] == "s_build" and rf2["dominant"]["bound"] == "hbm"
+    assert rf2["stages"]["factorisation"]["fp32_peak_tflops"] == bench.FP32_PEAK_TFLOPS_DERIVED
