@@ -18,6 +18,18 @@ where, with H_s the 12x12 Hessian of residual component s of observation o in it
 with dx' = [Delta c; Delta p'] the expanded step (virtual points), U = [0; u], DP = [0; Delta p],
 DC = [Delta c; 0], rho = f + J_c Delta c.  A rejected step passes the adjoint through unchanged.
 Hessian-vector products are central differences of the complex-step Jacobian along beta.
+
+A step taken with the steepest-descent correction (Sec. 4.3, Algorithm 1: lambda >= the threshold) solves
+H' dx' = g~' with the corrected right-hand side.  In closed form (the oracle's literal A-matrix correction
+equals it, see the correction pins) w~'_v = (h_v / H_i) o w_i for every virtual point v of point i, with
+h_v = diag(J'_v^T J'_v) (undamped), H_i = sum over the copies of h_v = diag(J_p^T J_p)_i and w_i the physical
+w; Eq. 15 still takes the physical, uncorrected w.  Differentiating z'^T g~' then gives, besides the
+expanded step dx' now built from w~':
+  - in the terms that come from g (the f-Hessian term, J_o^T g_o and q_bar), z'_o is replaced by
+    z~_o = [z_c; zeta_i], zeta_i = sum_v h_v o z_v / H_i (the h-weighted mean of the copies' z_v);
+  - the derivative of h_v / H_i adds  - sum_s H_s [0; 2 kappa_v o J_p,o[s,:]]  with
+    kappa_v = (z_v - zeta_i) o w_i / H_i;
+the terms that come from H' keep the solved z'.
 """
 from __future__ import annotations
 
@@ -66,15 +78,15 @@ def forward(cams, pts, obs_cam, obs_pt, obs_uv, cluster_seq, iters, opt: stba.Op
     for t in range(iters):
         cl = cluster_seq[t] if cluster_seq.ndim == 2 else cluster_seq
         c_new, p_new, lam_new, F, rec = stba.lm_iteration(cams, pts, obs_cam, obs_pt, obs_uv, cl, lam, F, opt)
-        if rec["corrected"]:
-            raise NotImplementedError("the adjoint covers uncorrected steps (lambda < correction threshold)")
-        tape.append(dict(cams=cams, pts=pts, lam=lam, clusters=cl, accepted=rec["accepted"]))
+        tape.append(dict(cams=cams, pts=pts, lam=lam, clusters=cl, accepted=rec["accepted"],
+                         corrected=rec["corrected"]))
         cams, pts, lam = c_new, p_new, lam_new
     return cams, pts, tape
 
 
-def step_adjoint(cams, pts, obs_cam, obs_pt, obs_uv, clusters, lam, a_c, a_p):
-    """Adjoint of one accepted step at x = (cams, pts): returns (x_bar_cams, x_bar_pts, q_bar)."""
+def step_adjoint(cams, pts, obs_cam, obs_pt, obs_uv, clusters, lam, a_c, a_p, corrected=False):
+    """Adjoint of one accepted step at x = (cams, pts): returns (x_bar_cams, x_bar_pts, q_bar).
+    corrected: the step used the steepest-descent correction (Sec. 4.3)."""
     m, n, q = len(cams), len(pts), len(obs_cam)
     lin = stba.linearise(cams, pts, obs_cam, obs_pt, obs_uv)
     f = lin.f.reshape(q, 2)
@@ -87,6 +99,13 @@ def step_adjoint(cams, pts, obs_cam, obs_pt, obs_uv, clusters, lam, a_c, a_p):
     Ev = (lin.J_c.T @ J_pv).tocsr()
     g = -(sp.hstack([lin.J_c, J_pv]).tocsr().T @ lin.f)
     v1, w1 = g[: 9 * m], g[9 * m:]
+    if corrected:   # w~'_v = (h_v / H_i) o w_i, the closed form of the correction
+        hv = np.asarray(J_pv.multiply(J_pv).sum(axis=0)).reshape(nv, 3)
+        Hi = np.zeros((n, 3))
+        np.add.at(Hi, vp_point, hv)
+        wi = np.zeros((n, 3))
+        np.add.at(wi, vp_point, w1.reshape(nv, 3))
+        w1 = (hv / Hi[vp_point] * wi[vp_point]).reshape(-1)
     Cv_inv = stba.block_diag_inverse(Cv)
     Sp = (B - Ev @ Cv_inv @ Ev.T).tocsr()
     bp = v1 - Ev @ (Cv_inv @ w1)
@@ -112,17 +131,33 @@ def step_adjoint(cams, pts, obs_cam, obs_pt, obs_uv, clusters, lam, a_c, a_p):
     # per-observation local vectors [camera 9; point 3]
     dcm, zcm = dc.reshape(m, 9), zc.reshape(m, 9)
     z_o = np.concatenate([zcm[obs_cam], zv.reshape(nv, 3)[vp_of_obs]], 1)
+    zt_o = z_o   # z~_o: the z seen by the right-hand side g
+    if corrected:
+        zeta = np.zeros((n, 3))
+        np.add.at(zeta, vp_point, hv * zv.reshape(nv, 3))
+        zeta /= Hi
+        kappa = (zv.reshape(nv, 3) - zeta[vp_point]) * wi[vp_point] / Hi[vp_point]
+        zt_o = np.concatenate([zcm[obs_cam], zeta[obs_pt]], 1)
     dx_o = np.concatenate([dcm[obs_cam], dpv.reshape(nv, 3)[vp_of_obs]], 1)
     U_o = np.concatenate([np.zeros((q, 9)), u.reshape(n, 3)[obs_pt]], 1)
     DP_o = np.concatenate([np.zeros((q, 9)), dp.reshape(n, 3)[obs_pt]], 1)
     DC_o = np.concatenate([dcm[obs_cam], np.zeros((q, 3))], 1)
     J_o = np.concatenate([lin.Jc, lin.Jp], axis=2)         # (q, 2, 12)
-    Jz, Jdx, JU, JDP = (np.einsum('ksj,kj->ks', J_o, vv) for vv in (z_o, dx_o, U_o, DP_o))
+    Jz, Jdx, JU, JDP, Jzt = (np.einsum('ksj,kj->ks', J_o, vv) for vv in (z_o, dx_o, U_o, DP_o, zt_o))
     rho = f + np.einsum('ksj,kj->ks', lin.Jc, dcm[obs_cam])
-    g_o = Jz + JU
+    g_o = Jzt + JU
     C_o, P_o = cams[obs_cam], pts[obs_pt]
     terms = np.einsum('ksj,ks->kj', J_o, g_o)
-    terms += hessian_vector(C_o, P_o, f + Jdx, z_o)
+    if corrected:
+        terms += hessian_vector(C_o, P_o, f, zt_o)
+        terms += hessian_vector(C_o, P_o, Jdx, z_o)
+        for s in range(2):
+            es = np.zeros((q, 2))
+            es[:, s] = 1.0
+            beta = np.concatenate([np.zeros((q, 9)), -2.0 * kappa[vp_of_obs] * lin.Jp[:, s, :]], 1)
+            terms += hessian_vector(C_o, P_o, es, beta)
+    else:
+        terms += hessian_vector(C_o, P_o, f + Jdx, z_o)
     terms += hessian_vector(C_o, P_o, Jz, dx_o)
     terms += hessian_vector(C_o, P_o, JDP + rho, U_o)
     terms += hessian_vector(C_o, P_o, JU, DP_o + DC_o)
@@ -147,7 +182,7 @@ def backward(tape, obs_cam, obs_pt, obs_uv, a_cams, a_pts):
         if not rec["accepted"]:
             continue
         a_c, a_p, g_o = step_adjoint(rec["cams"], rec["pts"], obs_cam, obs_pt, obs_uv, rec["clusters"], rec["lam"],
-                                     a_c, a_p)
+                                     a_c, a_p, corrected=rec.get("corrected", False))
         qbar += g_o
     return a_c, a_p, qbar
 

@@ -4,7 +4,8 @@ the whole forward map (accept flags and clusters frozen; the test checks they do
 The loss is the sum of squared camera-centre errors, which moves along the similarity-gauge directions;
 at lambda ~ 1e-5 those are nearly free, the forward map's FP64 rounding noise there dominates a central
 difference, and the comparison would test the noise.  The chained runs therefore start at lambda0 = 0.03
-(below the correction threshold 0.1); at that damping the differences agree to ~1e-8."""
+(below the correction threshold 0.1); at that damping the differences agree to ~1e-8.  Runs that start at
+lambda0 = 0.5 or 0.2 take steps with the steepest-descent correction of Sec. 4.3 and pin its adjoint."""
 import numpy as np
 import pytest
 
@@ -27,11 +28,18 @@ def run(s, cams0, pts0, uv, iters, opt=CHAIN_OPT):
     return c, p, tape
 
 
-@pytest.mark.parametrize("iters", [1, 3])
-def test_adjoint_matches_central_differences(iters):
+@pytest.mark.parametrize("iters,lambda0", [(1, 0.03), (3, 0.03), (1, 0.5), (3, 0.5), (3, 0.2)])
+def test_adjoint_matches_central_differences(iters, lambda0):
+    # lambda0 >= 0.1: the steps use the steepest-descent correction (Sec. 4.3); 0.2 corrects the first step
+    # and, once an accepted step divides lambda by 3, not the later ones
     s, targets = setup()
-    c, p, tape = run(s, s.cameras, s.points, s.obs_uv, iters)
+    opt = stba.Options(lambda0=lambda0)
+    c, p, tape = run(s, s.cameras, s.points, s.obs_uv, iters, opt)
     flags = [t["accepted"] for t in tape]
+    if lambda0 >= 0.1:
+        assert tape[0]["corrected"] and tape[0]["accepted"]
+    if lambda0 == 0.2 and iters == 3:
+        assert not all(t["corrected"] for t in tape)
     a_c = adjoint.centre_loss_grad(c, targets)
     gc, gp, gq = adjoint.backward(tape, s.obs_cam, s.obs_pt, s.obs_uv, a_c, np.zeros_like(p))
     rng = np.random.default_rng(0)
@@ -39,7 +47,7 @@ def test_adjoint_matches_central_differences(iters):
 
     def L(cams0=None, pts0=None, uv=None):
         cc, _, tp = run(s, s.cameras if cams0 is None else cams0, s.points if pts0 is None else pts0,
-                        s.obs_uv if uv is None else uv, iters)
+                        s.obs_uv if uv is None else uv, iters, opt)
         assert [t["accepted"] for t in tp] == flags
         return adjoint.centre_loss(cc, targets)
 
