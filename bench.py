@@ -370,9 +370,9 @@ def main():
         sgc = {"note": "the scene's uneven contiguous segments, re-applied every step", "clusters_mean":
                float(np.max(s.clusters) + 1)}
     stba.stba_set_clusters(ctx, seq[0])
-    tile, update, tile_ms = None, None, {}
-    if not args.no_autotune:   # the factorisation tile and trailing update, chosen by timing (outside the timed steps)
-        tile, update, tile_ms = stba.stba_autotune(ctx, 5)
+    tuned, tile_ms = None, {}
+    if not args.no_autotune:   # the factorisation configuration, chosen by timing (outside the timed steps)
+        tuned, tile_ms = stba.stba_autotune(ctx, 5)
     for i in range(max(args.warmup, 3)):
         stba.stba_set_clusters(ctx, seq[i])
         stba.stba_lm_iteration(ctx, want_info=False)
@@ -484,9 +484,7 @@ def main():
                 "d2h_bytes_per_step": nbytes_out},
         "step": "set_clusters (a stochastic-graph-clustering draw) + one LM iteration (Algorithm 1)",
         "sgc": sgc,
-        "autotune": {"factor_tile": tile, "factor_update": {stba.STBA_FACTOR_UPDATE_TENSOR: "tensor",
-                                                            stba.STBA_FACTOR_UPDATE_SIMT: "simt"}.get(update),
-                     "ms_per_iter": {str(k_): v_ for k_, v_ in tile_ms.items()}},
+        "autotune": {"kept": tuned, "ms_per_iter": {str(k_): v_ for k_, v_ in tile_ms.items()}},
         "fixed_clusters_ms_per_iter": fixed_ms,
         "gpu_launches": int(round((info0["launches_per_iter"] + REORDER_LAUNCHES) * args.steps)),
         "clocks": clocks,

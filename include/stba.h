@@ -87,9 +87,20 @@ typedef struct {
                                cores; STBA_FACTOR_UPDATE_TENSOR = tcgen05 tensor cores, TF32 operands split
                                in three products for FP32 accuracy (the FP32 factor of STBA_MIXED with tile
                                64 only; other settings return STBA_ERR_INVALID_ARG). */
+  int32_t factor_panel;     /* panel of each tile step of the cluster factorisation: 0 = default (for the
+                               FP32 factor with tile 64: STBA_FACTOR_PANEL_SPLIT when the tiles of all
+                               clusters outnumber the SMs, i.e. a step runs in several waves, else _STACKED;
+                               _STACKED otherwise);
+                               STBA_FACTOR_PANEL_STACKED = one kernel per step factors the stacked panel of
+                               the diagonal tile and each tile below it (the diagonal tile redundantly per
+                               tile row); STBA_FACTOR_PANEL_SPLIT = the diagonal tile is factored and
+                               inverted once per cluster, the tiles below are its products with the inverse
+                               (the FP32 factor of STBA_MIXED with tile 64 only; other settings return
+                               STBA_ERR_INVALID_ARG). */
 } stba_options;
 
 enum { STBA_FACTOR_UPDATE_DEFAULT = 0, STBA_FACTOR_UPDATE_SIMT = 1, STBA_FACTOR_UPDATE_TENSOR = 2 };
+enum { STBA_FACTOR_PANEL_DEFAULT = 0, STBA_FACTOR_PANEL_STACKED = 1, STBA_FACTOR_PANEL_SPLIT = 2 };
 
 typedef struct {
   double F_before;      /* F(x) at the start of the iteration */
@@ -177,12 +188,14 @@ stba_status stba_record(stba_ctx* ctx, int32_t max_iter);
  * values.  Each accepted step is recomputed from its stored x_t with the same kernels and precision as
  * the forward pass; its adjoint solves with that step's cluster factors (z_c = S'^-1 a^_c, the implicit
  * derivative of Eq. 10/13), back-substitutes through the virtual points and Eq. 15, and adds the
- * second-derivative products of the reprojection error.
- * Errors: STBA_ERR_STATE with the PCG solver, if nothing was recorded, if stba_set_params replaced the parameters during the
- * recording, or if an accepted step used the steepest-descent correction (lambda >= correction_lambda,
- * Sec. 4.3), which this adjoint does not cover.  On return the parameters, the cluster assignment and the
- * LM state are those before the call.  The call synchronises the stream and allocates, then frees, about
- * 160 q + 216 m + 72 n bytes of device memory. */
+ * second-derivative products of the reprojection error.  A step taken with the steepest-descent correction
+ * (lambda >= correction_lambda, Sec. 4.3) is differentiated through the closed form of the corrected
+ * right-hand side, w~'_v = (h_v / H_i) o w_i (h_v = diag(V_v), H_i their sum over point i's copies, w_i the
+ * physical w), including the dependence of h_v / H_i on the parameters.
+ * Errors: STBA_ERR_STATE with the PCG solvers or the Huber loss, if nothing was recorded, or if
+ * stba_set_params replaced the parameters during the recording.  On return the parameters, the cluster
+ * assignment and the LM state are those before the call.  The call synchronises the stream and allocates,
+ * then frees, about 184 q + 216 m + 96 n bytes of device memory. */
 stba_status stba_adjoint(stba_ctx* ctx, const double* dL_dcams, const double* dL_dpts, double* dL_dobs,
                          double* dL_dcams0, double* dL_dpts0);
 
@@ -259,12 +272,14 @@ stba_status stba_cluster_sgc(stba_ctx* ctx, int32_t gamma, double beta, uint64_t
 /* Autotuner (the paper has none): times `iterations` LM iterations with every candidate configuration of
  * the cluster factorisation on the current parameters and cluster assignment, restores the parameters,
  * damping and cost after each trial, and keeps the fastest for the following iterations.  Candidates
- * (STBA_MIXED; FP64 has one): 0 = tile 64 with the tensor-core trailing update, 1 = tile 64 with the
- * CUDA-core update, 2 = tile 32 with the CUDA-core update.  *tile and *update (optional) receive the
- * choice (tile 64 or 32, STBA_FACTOR_UPDATE_TENSOR or _SIMT), ms[0..2] (optional) the time per iteration of
- * each candidate (-1 when not tried).  Synchronises the context stream.  Errors: STBA_ERR_STATE while
- * iterations are being recorded (stba_record), STBA_ERR_INVALID_ARG for iterations < 1. */
-stba_status stba_autotune(stba_ctx* ctx, int32_t iterations, int32_t* tile, int32_t* update, float* ms);
+ * (STBA_MIXED; FP64 has one):
+ *   0 = tile 64, split panel, tensor-core trailing update     1 = tile 64, split panel, CUDA-core update
+ *   2 = tile 64, stacked panel, CUDA-core update              3 = tile 32, stacked panel, CUDA-core update
+ * *choice (optional) receives the index kept (-1 for the single FP64 configuration), ms[0..3] (optional) the
+ * time per iteration of each candidate (-1 when not tried).  Synchronises the context stream.  Errors:
+ * STBA_ERR_STATE while iterations are being recorded (stba_record), STBA_ERR_INVALID_ARG for
+ * iterations < 1. */
+stba_status stba_autotune(stba_ctx* ctx, int32_t iterations, int32_t* choice, float* ms);
 
 /* Measured arithmetic peaks of the current GPU, the denominators of the factorisation's roofline.  The
  * paper has no counterpart: this is measurement infrastructure.  *fp32_tflops (optional): FP32 FMA rate of

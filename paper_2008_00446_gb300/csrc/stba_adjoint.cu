@@ -19,6 +19,15 @@
 //   (f + J dx', z') + (J z', dx') + (J DP + rho, U) + (J U, DP + DC)
 //   + sum_s (e_s, 2 lambda J[s,:] o (z' o dx' + U o DP))          (the lambda diag(J^T J) damping)
 // The (alpha, beta) products come from the Jacobian evaluated on dual numbers (stba_dual.cuh).
+//
+// A step taken with the steepest-descent correction (Sec. 4.3; lambda >= the threshold) solves H' dx' = g~'
+// with w~'_v = (h_v / H_i) o w_i for the virtual points v of point i (the closed form of the correction:
+// h_v = diag(V_v) undamped, H_i = sum over the copies of h_v, w_i the physical w).  The recomputed forward
+// step already carries w~' in dx'; its adjoint differs in two places:
+//   - where z' meets the right-hand side (the (f, .) term, J^T g and q_bar), the copies' z_v are replaced by
+//     zeta_i = sum_v h_v o z_v / H_i, so (f + J dx', z') splits into (f, z~) + (J dx', z');
+//   - the derivative of h_v / H_i adds sum_s (e_s, J[s,:] o [0; -2 kappa_v]), kappa_v = (z_v - zeta_i) o w_i / H_i,
+//     which joins the damping directions' weights.
 #include <climits>
 
 #include "stba_camera.cuh"
@@ -159,6 +168,36 @@ __global__ void k_adj_vp_final(int nv, const real* __restrict__ vp_info, double*
   }
 }
 
+// Corrected steps: per point, zeta_i = sum_v h_v o z_v / H_i, and per virtual point kappa_v = (z_v - zeta_i) o
+// w_i / H_i, from the undamped V_v and uncorrected w'_v the forward pass accumulated (vp_acc) and z_v (vpz).
+template <typename real>
+__global__ void k_adj_zeta(DevProblem P, const real* __restrict__ vp_acc, const double* __restrict__ vpz,
+                           double* __restrict__ zeta, double* __restrict__ kappa) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const int vb = P.pt_vp_off[i], ve = P.pt_vp_off[i + 1];
+    double H[3] = {0, 0, 0}, w[3] = {0, 0, 0}, hz[3] = {0, 0, 0};
+    for (int v = vb; v < ve; ++v) {
+      const real* a = vp_acc + 9 * (size_t)v;
+      const double h[3] = {(double)a[0], (double)a[3], (double)a[5]};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        H[k] += h[k];
+        w[k] += (double)a[6 + k];
+        hz[k] += h[k] * vpz[6 * (size_t)v + k];
+      }
+    }
+    double z[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      z[k] = hz[k] / H[k];
+      zeta[3 * (size_t)i + k] = z[k];
+    }
+    for (int v = vb; v < ve; ++v)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) kappa[3 * (size_t)v + k] = (vpz[6 * (size_t)v + k] - z[k]) * w[k] / H[k];
+  }
+}
+
 // out += sum_s alpha_s d/de J_s(theta + e beta) (12 entries: camera 9, point 3) for one observation.
 __device__ __forceinline__ void hess_vec(const Cam<double>& C0, const double X0[3], double uo, double vo,
                                          double al0, double al1, const double beta[12], double out[12]) {
@@ -184,7 +223,9 @@ __device__ __forceinline__ void hess_vec(const Cam<double>& C0, const double X0[
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int* __restrict__ perm, double lam,
                                                          const double* __restrict__ dc, const double* __restrict__ dp,
                                                          const double* __restrict__ zc, const double* __restrict__ u,
-                                                         const double* __restrict__ vpz, double* __restrict__ T,
+                                                         const double* __restrict__ vpz, int corr,
+                                                         const double* __restrict__ zeta,
+                                                         const double* __restrict__ kappa, double* __restrict__ T,
                                                          double* __restrict__ qbar) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= P.q) return;
@@ -206,8 +247,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
     uu[s] = u[3 * (size_t)pt + s];
     dpp[s] = dp[3 * (size_t)pt + s];
   }
-  // J z', J dx', J U, J DP, rho = f + J_c dc
-  double Jz[2], Jdx[2], JU[2], JDP[2], rho[2];
+  // z~: z' with the point part replaced by zeta of the physical point on a corrected step
+  double zp[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) zp[s] = corr ? zeta[3 * (size_t)pt + s] : z[9 + s];
+  // J z', J z~, J dx', J U, J DP, rho = f + J_c dc
+  double Jz[2], Jzt[2], Jdx[2], JU[2], JDP[2], rho[2];
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
     double a = 0, cdc = 0;
@@ -216,21 +261,23 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
       a += Jc[t][c] * z[c];
       cdc += Jc[t][c] * dx[c];
     }
-    double pz = 0, pdx = 0, pu = 0, pdp = 0;
+    double pz = 0, pzt = 0, pdx = 0, pu = 0, pdp = 0;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       pz += Jp[t][s] * z[9 + s];
+      pzt += Jp[t][s] * zp[s];
       pdx += Jp[t][s] * dx[9 + s];
       pu += Jp[t][s] * uu[s];
       pdp += Jp[t][s] * dpp[s];
     }
     Jz[t] = a + pz;
+    Jzt[t] = a + pzt;
     Jdx[t] = cdc + pdx;
     JU[t] = pu;
     JDP[t] = pdp;
     rho[t] = f[t] + cdc;
   }
-  const double g0 = Jz[0] + JU[0], g1 = Jz[1] + JU[1];
+  const double g0 = Jzt[0] + JU[0], g1 = Jzt[1] + JU[1];
   {
     double* qb = qbar + 2 * (size_t)perm[o];
     qb[0] += g0;
@@ -246,14 +293,24 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
 #pragma unroll
   for (int c = 0; c < 9; ++c) wdm[c] = 2.0 * lam * z[c] * dx[c];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) wdm[9 + s] = 2.0 * lam * (z[9 + s] * dx[9 + s] + uu[s] * dpp[s]);
+  for (int s = 0; s < 3; ++s)
+    wdm[9 + s] = 2.0 * lam * (z[9 + s] * dx[9 + s] + uu[s] * dpp[s]) - (corr ? 2.0 * kappa[3 * (size_t)v + s] : 0.0);
   double al0, al1, beta[12];
+  const int ndir = corr ? 7 : 6;
 #pragma unroll 1
-  for (int dir = 0; dir < 6; ++dir) {
+  for (int dir = 0; dir < ndir; ++dir) {
     switch (dir) {
-      case 0:   // (f + J dx', z')
-        al0 = f[0] + Jdx[0];
-        al1 = f[1] + Jdx[1];
+      case 0:   // (f + J dx', z'), or (f, z~) on a corrected step
+        al0 = f[0] + (corr ? 0.0 : Jdx[0]);
+        al1 = f[1] + (corr ? 0.0 : Jdx[1]);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) beta[c] = z[c];
+#pragma unroll
+        for (int s = 0; s < 3; ++s) beta[9 + s] = zp[s];
+        break;
+      case 6:   // corrected step: (J dx', z')
+        al0 = Jdx[0];
+        al1 = Jdx[1];
 #pragma unroll
         for (int c = 0; c < 12; ++c) beta[c] = z[c];
         break;
@@ -279,7 +336,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
 #pragma unroll
         for (int s = 0; s < 3; ++s) beta[9 + s] = dpp[s];
         break;
-      default: {   // (e_s, 2 lambda J[s,:] o (z' o dx' + U o DP)), s = dir - 4
+      default: {   // (e_s, J[s,:] o wdm), s = dir - 4: the damping (and, corrected, the kappa) terms
         const int s = dir - 4;
         al0 = s == 0 ? 1.0 : 0.0;
         al1 = s == 0 ? 0.0 : 1.0;
@@ -341,7 +398,7 @@ void launch_set_lambda(DevState* st, double lam, cudaStream_t stream) {
 
 template <typename real>
 void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, const FactorBuffers& fb,
-                         const CholPlan& plan, int refine_steps, const int* perm, double lam,
+                         const CholPlan& plan, int refine_steps, const int* perm, double lam, int corrected,
                          const AdjointBuffers& A, cudaStream_t stream) {
   const int pblocks = std::min((P.n + 255) / 256, 4096);
   k_adj_point_u<real><<<pblocks, 256, 0, stream>>>(P.n, W.pt_info, A.a_p, A.u);
@@ -353,17 +410,18 @@ void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, cons
   cudaMemsetAsync(A.vpz, 0, 6 * (size_t)P.nv * sizeof(double), stream);
   k_adj_vp<<<(P.q + 255) / 256, 256, 0, stream>>>(P, A.zc, W.dc, A.vpz);
   k_adj_vp_final<real><<<std::min((P.nv + 255) / 256, 4096), 256, 0, stream>>>(P.nv, W.vp_info, A.vpz);
-  k_adj_obs<<<(P.q + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, stream>>>(P, perm, lam, W.dc, W.dp, A.zc, A.u,
-                                                                             A.vpz, A.T, A.qbar);
+  if (corrected) k_adj_zeta<real><<<pblocks, 256, 0, stream>>>(P, W.vp_acc, A.vpz, A.zeta, A.kappa);
+  k_adj_obs<<<(P.q + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, stream>>>(
+      P, perm, lam, W.dc, W.dp, A.zc, A.u, A.vpz, corrected, A.zeta, A.kappa, A.T, A.qbar);
   k_adj_cam_reduce<<<P.m, ADJ_THREADS, 0, stream>>>(CL, A.T, A.a_c);
   k_adj_pt_reduce<<<pblocks, 256, 0, stream>>>(P, A.T, A.a_p);
 }
 
 template void launch_adjoint_step<float>(const DevProblem&, Scratch<float>, CamLists, const FactorBuffers&,
-                                         const CholPlan&, int, const int*, double, const AdjointBuffers&,
+                                         const CholPlan&, int, const int*, double, int, const AdjointBuffers&,
                                          cudaStream_t);
 template void launch_adjoint_step<double>(const DevProblem&, Scratch<double>, CamLists, const FactorBuffers&,
-                                          const CholPlan&, int, const int*, double, const AdjointBuffers&,
+                                          const CholPlan&, int, const int*, double, int, const AdjointBuffers&,
                                           cudaStream_t);
 
 }  // namespace stba

@@ -131,6 +131,10 @@ struct stba_ctx {
   bool graph_stale = false;             // the cluster layout changed since the graph was captured
   int tile = 32;                        // factorisation tile (stba_autotune may change the FP32 one)
   int update_tc = 0;                    // trailing updates on the tensor cores (FP32 factor, tile 64)
+  int split_panel = 0;                  // split panel: diagonal-tile factor + inverse, then the tiles below
+  int panel_choice = STBA_FACTOR_PANEL_DEFAULT;   // option, or the autotuner's choice; DEFAULT decides per
+                                                  // assignment (set_clusters_host)
+  std::vector<int> h_diag_count;        // split panel: diagonal items of every step
   bool capturing = false;
   bool timing = false;
   int launches_per_iter = 0;
@@ -435,6 +439,16 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   }
   c->S_total = so;
   c->v_total = vo;
+  // panel of the FP32 factor with tile 64: the split panel pays off once a tile step's tiles outnumber the SMs
+  // (several waves of panel CTAs per step; each of them would factor its diagonal tile again), the stacked
+  // panel when they fit in one wave (a single kernel per step on the critical path)
+  if (c->mixed && TF == 64 && c->panel_choice != STBA_FACTOR_PANEL_STACKED) {
+    int64_t tiles = 0;
+    for (int k = 0; k < l; ++k) tiles += c->h_np[k] / TF;
+    c->split_panel = c->panel_choice == STBA_FACTOR_PANEL_SPLIT || tiles > num_sms();
+  } else {
+    c->split_panel = 0;
+  }
   c->build_items = c->use_pcg ? 0 : c->pchunks.nchunks;
 
   // Cholesky step plan (none for the PCG solver)
@@ -447,13 +461,20 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   std::vector<int2> panel, update;
   c->h_panel_off.assign(max_nt + 1, 0);
   c->h_update_off.assign(max_nt + 1, 0);
+  c->h_diag_count.assign(max_nt + 1, 0);
   for (int kt = 0; kt < max_nt; ++kt) {
     c->h_panel_off[kt] = (int)panel.size();
     c->h_update_off[kt] = (int)update.size();
+    if (c->split_panel)   // the diagonal tiles of the step first
+      for (int k = 0; k < l; ++k)
+        if (c->h_np[k] / TF > kt) {
+          panel.push_back(make_int2(k, kt));
+          c->h_diag_count[kt]++;
+        }
     for (int k = 0; k < l; ++k) {
       const int ntk = c->h_np[k] / TF;
       if (ntk <= kt) continue;
-      for (int i = kt; i < ntk; ++i) panel.push_back(make_int2(k, i));
+      for (int i = c->split_panel ? kt + 1 : kt; i < ntk; ++i) panel.push_back(make_int2(k, i));
       for (int j = kt + 2; j < ntk; ++j) {   // column kt + 1 is updated by panel kt + 1 itself
         if (c->update_tc)   // tile pairs (i0, i0 + 1) x j, from the diagonal tile down
           for (int i0 = j; i0 < ntk; i0 += 2) update.push_back(make_int2(k, (i0 << 16) | j));
@@ -557,7 +578,8 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
                         c->h_panel_off.data(),
                         c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
-                        c->ev_panel.data(), c->ev_update.data(), TF, c->update_tc};
+                        c->ev_panel.data(), c->ev_update.data(), TF, c->update_tc, c->split_panel,
+                        c->h_diag_count.data()};
   }
   {
     int least = 0, greatest = 0;
@@ -819,7 +841,7 @@ void free_tape(stba_ctx* c) {
 }
 
 template <typename real>
-void enqueue_adjoint_step(stba_ctx* c, double lam, const AdjointBuffers& A) {
+void enqueue_adjoint_step(stba_ctx* c, double lam, int corrected, const AdjointBuffers& A) {
   // recompute the forward step at x_t with the recorded damping, then its adjoint (whose launch sizes need
   // the number of virtual points on the host)
   refresh_counts(c);
@@ -830,7 +852,7 @@ void enqueue_adjoint_step(stba_ctx* c, double lam, const AdjointBuffers& A) {
                     c->stream);
   enqueue_step<real>(c, false);
   launch_adjoint_step<real>(P, scratch<real>(c), c->clist, c->fbuf, c->cplan, c->set.refine_steps, c->obs_perm, lam,
-                            A, c->stream);
+                            corrected, A, c->stream);
 }
 
 stba_status read_info(stba_ctx* c, stba_iter_info* info) {
@@ -868,6 +890,7 @@ void stba_default_options(stba_options* o) {
   o->pcg_max_iter = 500;
   o->pcg_tol = 1e-6;
   o->factor_update = STBA_FACTOR_UPDATE_DEFAULT;
+  o->factor_panel = STBA_FACTOR_PANEL_DEFAULT;
 }
 
 const char* stba_status_string(stba_status s) {
@@ -976,13 +999,18 @@ stba_status stba_cluster_sgc(stba_ctx* c, int32_t gamma, double beta, uint64_t s
   return STBA_OK;
 }
 
-stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, int32_t* update, float* ms) {
+stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* choice, float* ms) {
   if (!c || iterations < 1) return STBA_ERR_INVALID_ARG;
   if (c->tape_cap > 0) return fail(c, STBA_ERR_STATE, "stba_autotune is not allowed while iterations are recorded");
-  if (ms) ms[0] = ms[1] = ms[2] = -1.0f;
+  constexpr int NCAND = 4;
+  const int cand_tile[NCAND] = {64, 64, 64, 32}, cand_tc[NCAND] = {1, 0, 0, 0}, cand_split[NCAND] = {1, 1, 0, 0};
+  if (ms)
+    for (int t = 0; t < NCAND; ++t) ms[t] = -1.0f;
   auto report = [&]() {
-    if (tile) *tile = c->tile;
-    if (update) *update = c->update_tc ? STBA_FACTOR_UPDATE_TENSOR : STBA_FACTOR_UPDATE_SIMT;
+    if (!choice) return;
+    *choice = -1;
+    for (int t = 0; t < NCAND; ++t)
+      if (cand_tile[t] == c->tile && cand_tc[t] == c->update_tc && cand_split[t] == c->split_panel) *choice = t;
   };
   if (!c->mixed || c->use_pcg || c->use_spcg) {   // one candidate (or no factorisation at all)
     report();
@@ -1016,15 +1044,15 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, int32_
            copy(c->st, st0, sizeof(DevState));
   };
   const std::vector<int> cl = c->h_clusters;
-  const int cand_tile[3] = {64, 64, 32}, cand_tc[3] = {1, 0, 0};
   float best_ms = 0.f;
   int best = -1;
   stba_status s = STBA_OK;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) ok = false;
-  for (int t = 0; t < 3 && ok && s == STBA_OK; ++t) {
+  for (int t = 0; t < NCAND && ok && s == STBA_OK; ++t) {
     c->tile = cand_tile[t];
     c->update_tc = cand_tc[t];
+    c->panel_choice = cand_split[t] ? STBA_FACTOR_PANEL_SPLIT : STBA_FACTOR_PANEL_STACKED;
     if ((s = set_clusters_host(c, cl)) != STBA_OK) break;
     ok = restore();
     if (ok && (s = run_iteration(c)) != STBA_OK) break;   // warm-up: capture, first launch
@@ -1046,6 +1074,7 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* tile, int32_
   if (s == STBA_OK && ok && best >= 0) {
     c->tile = cand_tile[best];
     c->update_tc = cand_tc[best];
+    c->panel_choice = cand_split[best] ? STBA_FACTOR_PANEL_SPLIT : STBA_FACTOR_PANEL_STACKED;
     s = set_clusters_host(c, cl);
     if (s == STBA_OK) ok = restore() && cudaStreamSynchronize(c->stream) == cudaSuccess;
   }
@@ -1117,6 +1146,10 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       (c->opt.factor_update != STBA_FACTOR_UPDATE_DEFAULT && c->opt.factor_update != STBA_FACTOR_UPDATE_SIMT &&
        c->opt.factor_update != STBA_FACTOR_UPDATE_TENSOR) ||
       (c->opt.factor_update == STBA_FACTOR_UPDATE_TENSOR &&
+       !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))) ||
+      (c->opt.factor_panel != STBA_FACTOR_PANEL_DEFAULT && c->opt.factor_panel != STBA_FACTOR_PANEL_STACKED &&
+       c->opt.factor_panel != STBA_FACTOR_PANEL_SPLIT) ||
+      (c->opt.factor_panel == STBA_FACTOR_PANEL_SPLIT &&
        !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
   c->m = m;
@@ -1125,6 +1158,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   c->mixed = c->opt.precision == STBA_MIXED;
   c->tile = c->opt.factor_tile ? c->opt.factor_tile : factor_tile(c->mixed);
   c->update_tc = c->mixed && c->tile == 64 && c->opt.factor_update != STBA_FACTOR_UPDATE_SIMT;
+  c->panel_choice = c->opt.factor_panel;
   c->use_pcg = c->opt.linear_solver == STBA_SOLVER_PCG_FULL;
   c->use_spcg = c->opt.linear_solver == STBA_SOLVER_PCG_CLUSTERS;
   c->set.correction = c->opt.correction;
@@ -1549,11 +1583,6 @@ stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_d
   std::vector<stba_iter_info> info(T);
   CK(cudaMemcpyAsync(info.data(), c->tape_info, T * sizeof(stba_iter_info), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  for (int t = 0; t < T; ++t)
-    if (info[t].accepted && info[t].corrected)
-      return fail(c, STBA_ERR_STATE,
-                  "recorded iteration %d was accepted with the steepest-descent correction (lambda %g >= %g); the "
-                  "adjoint covers uncorrected steps", t, info[t].lambda_used, c->set.correction_lambda);
   // adjoint buffers and the saved final state, freed on every return path
   struct Guard {
     stba_ctx* c;
@@ -1574,6 +1603,8 @@ stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_d
   if ((s = dalloc_into(c, &A.vpz, 6 * (size_t)q, g.list)) != STBA_OK) return s;   // nv <= q
   if ((s = dalloc_into(c, &A.T, 12 * (size_t)q, g.list)) != STBA_OK) return s;
   if ((s = dalloc_into(c, &A.qbar, 2 * (size_t)q, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &A.zeta, 3 * (size_t)n, g.list)) != STBA_OK) return s;
+  if ((s = dalloc_into(c, &A.kappa, 3 * (size_t)q, g.list)) != STBA_OK) return s;   // nv <= q
   if ((s = dalloc_into(c, &save_x, nx, g.list)) != STBA_OK) return s;
   DevState saved;
   CK(cudaMemcpyAsync(&saved, c->st, sizeof saved, cudaMemcpyDeviceToHost, c->stream));
@@ -1598,9 +1629,9 @@ stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_d
       CK(cudaMemcpyAsync(c->cams, slot, 9 * (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
       CK(cudaMemcpyAsync(c->pts, slot + 9 * m, 3 * (size_t)n * 8, cudaMemcpyDeviceToDevice, c->stream));
       if (c->mixed)
-        enqueue_adjoint_step<float>(c, info[t].lambda_used, A);
+        enqueue_adjoint_step<float>(c, info[t].lambda_used, info[t].corrected, A);
       else
-        enqueue_adjoint_step<double>(c, info[t].lambda_used, A);
+        enqueue_adjoint_step<double>(c, info[t].lambda_used, info[t].corrected, A);
       CK(cudaGetLastError());
     }
     CK(cudaStreamSynchronize(c->stream));

@@ -103,6 +103,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
+// one 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
 
 __device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_w(double x) { return rsqrt(x); }
@@ -349,26 +354,13 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
   }
 }
 
-// Inverse Y of every diagonal tile of the factor (for the solves), one CTA per tile, by recursive doubling:
-// the inverses of the 8 x 8 diagonal blocks by forward substitution (8 threads per block), then for
-// h = 8, 16, .. T/2 the off-diagonal block of every 2h x 2h diagonal block, Y21 = -Y22 (L21 Y11), as two
-// parallel products.  Writes Y row-major and its transpose at offset v_total * T.
+// Inverse Y of a lower-triangular T x T tile D in shared memory (Y zeroed, D's upper part zero, both visible
+// to every thread), by recursive doubling, 256 threads: the inverses of the 8 x 8 diagonal blocks by forward
+// substitution (8 threads per block), then for h = 8, 16, .. T/2 the off-diagonal block of every 2h x 2h
+// diagonal block, Y21 = -Y22 (L21 Y11), as two parallel products (Z: T * T / 2 scratch).  Ends synchronised.
 template <typename F, int T>
-__global__ void __launch_bounds__(256) k_diag_inverse(const F* Ldiag, F* Dinv, DevProblem P, const int2* items,
-                                                      int64_t v_total) {
-  __shared__ F D[T][T + 1];
-  __shared__ F Y[T][T + 1];
-  __shared__ F Z[T * T / 2];
-  const int2 it = items[blockIdx.x];
-  const int k = it.x, t = it.y;
-  const F* Lkk = Ldiag + (size_t)P.v_off[k] * T + (size_t)t * T * T;
+__device__ __forceinline__ void tile_inverse(const F (*D)[T + 1], F (*Y)[T + 1], F* Z) {
   const int tid = threadIdx.x;
-  for (int idx = tid; idx < T * T; idx += 256) {
-    const int r = idx / T, c = idx - (idx / T) * T;
-    D[r][c] = (c <= r) ? Lkk[idx] : F(0);
-    Y[r][c] = F(0);
-  }
-  __syncthreads();
   if (tid < T) {   // column j of the inverse of diagonal block blk
     const int blk = tid >> 3, j = tid & 7, b0 = 8 * blk;
     F y[8];
@@ -402,6 +394,27 @@ __global__ void __launch_bounds__(256) k_diag_inverse(const F* Ldiag, F* Dinv, D
     }
     __syncthreads();
   }
+}
+
+// Inverse Y of every diagonal tile of the factor (for the solves), one CTA per tile (tile_inverse).  Writes
+// Y row-major and its transpose at offset v_total * T.
+template <typename F, int T>
+__global__ void __launch_bounds__(256) k_diag_inverse(const F* Ldiag, F* Dinv, DevProblem P, const int2* items,
+                                                      int64_t v_total) {
+  __shared__ F D[T][T + 1];
+  __shared__ F Y[T][T + 1];
+  __shared__ F Z[T * T / 2];
+  const int2 it = items[blockIdx.x];
+  const int k = it.x, t = it.y;
+  const F* Lkk = Ldiag + (size_t)P.v_off[k] * T + (size_t)t * T * T;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    D[r][c] = (c <= r) ? Lkk[idx] : F(0);
+    Y[r][c] = F(0);
+  }
+  __syncthreads();
+  tile_inverse<F, T>(D, Y, Z);
   F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)t * T * T;
   F* DiT = Di + v_total * T;
   for (int idx = tid; idx < T * T; idx += 256) {
@@ -409,6 +422,238 @@ __global__ void __launch_bounds__(256) k_diag_inverse(const F* Ldiag, F* Dinv, D
     Di[idx] = Y[r][c];
     DiT[idx] = Y[c][r];
   }
+}
+
+// ------------------------------------------------------------------------------------------------------
+// Split panel of tile step kt (the FP32 factor with T = 64): the diagonal tile is factored once per cluster,
+// the tiles below it by a product with its inverse, so that a step's critical path is two short kernels.
+//
+// k_chol_diag, one CTA per cluster with a tile step kt:  A_kt,kt -= L_kt,kt-1 L_kt,kt-1^T (step kt - 1's
+// update of the diagonal tile), LL^T of the tile in blocks of 8 columns (as the panel, 64 rows), and its
+// inverse Y = L_kt,kt^-1 (tile_inverse), written to Dinv (row-major) and its transpose (for the solves and
+// for k_chol_trsm).  Pivot rules as in chol8.
+template <typename F, int T>
+struct DiagLayout {
+  static constexpr int LDA = T + 1;
+  static constexpr int LDV = T + (sizeof(F) == 4 ? 4 : 2);
+  static constexpr size_t bytes = sizeof(F) * (2 * (size_t)T * LDA + (size_t)T * LDV + (size_t)T * T / 2);
+};
+
+template <typename F, int T>
+__global__ void __launch_bounds__(256) k_chol_diag(const F* L, F* Dinv, DevProblem P, const int2* items, int kt,
+                                                   int* fail_flags, int* boosted, int64_t v_total) {
+  using DL = DiagLayout<F, T>;
+  constexpr int R = T / 16, LDA = DL::LDA, LDV = DL::LDV, NB = T / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F(*Ad)[LDA] = reinterpret_cast<F(*)[LDA]>(smem_raw);
+  F(*Y)[LDA] = Ad + T;
+  F(*LkT)[LDV] = reinterpret_cast<F(*)[LDV]>(Y + T);
+  F* Z = reinterpret_cast<F*>(LkT + T);
+  __shared__ F rinv2[2][8];
+  const int k = items[blockIdx.x].x;
+  const int np = P.cluster_np[k], nk = P.cluster_n[k];
+  const F* A = L + P.S_off[k];
+  const int tid = threadIdx.x;
+  const int bi = tid & 15, bj = tid >> 4;
+  const size_t base_kk = (size_t)(kt * T) * np + kt * T;
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    if (c <= r)
+      cp_async_elem(&Ad[r][c], A + base_kk + (size_t)r * np + c);
+    else
+      Ad[r][c] = F(0);
+    Y[r][c] = F(0);
+    if (kt > 0) cp_async_elem(&LkT[c][r], A + base_kk - T + (size_t)r * np + c);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  if (kt > 0) {   // A_kk -= L_k,kt-1 L_k,kt-1^T (lower part)
+    F acc[R][R];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a][b] = F(0);
+#pragma unroll 4
+    for (int m = 0; m < T; ++m) {
+      F lr[R], lc[R];
+      load_vec<F, R>(&LkT[m][bi * R], lr);
+      load_vec<F, R>(&LkT[m][bj * R], lc);
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) acc[a][b] += lr[a] * lc[b];
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) {
+        const int r = bi * R + a, c = bj * R + b;
+        if (c <= r) Ad[r][c] -= acc[a][b];
+      }
+    __syncthreads();
+  }
+  // blocked LL^T of the tile: per block of 8 columns, one thread factors the 8 x 8 diagonal block, the rows
+  // below are solved against it, and the columns to its right get the rank-8 update (warp 0 updates and
+  // factors the next diagonal block meanwhile: one block of look-ahead)
+  if (tid == 0) chol8<F, LDA>(Ad, 0, kt * T, nk, rinv2[0], fail_flags + k, boosted);
+  __syncthreads();
+  for (int b = 0; b < NB; ++b) {
+    const int b0 = 8 * b;
+    const F* rinv = rinv2[b & 1];
+    const int rows_d = T - b0 - 8;
+    if (tid < rows_d) {
+      F* row = &Ad[b0 + 8 + tid][0];
+      F o8[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        F s = row[b0 + c];
+#pragma unroll
+        for (int t = 0; t < c; ++t) s -= o8[t] * Ad[b0 + c][b0 + t];
+        o8[c] = s * rinv[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) row[b0 + c] = o8[c];
+    }
+    __syncthreads();
+    if (b + 1 == NB) break;
+    const int n0 = b0 + 8;
+    if (tid < 32) {
+      for (int e = tid; e < 36; e += 32) {
+        int rr = 0;
+        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+        const int cc = e - rr * (rr + 1) / 2;
+        F s = F(0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) s += Ad[n0 + rr][b0 + t] * Ad[n0 + cc][b0 + t];
+        Ad[n0 + rr][n0 + cc] -= s;
+      }
+      __syncwarp();
+      if (tid == 0) chol8<F, LDA>(Ad, n0, kt * T, nk, rinv2[(b + 1) & 1], fail_flags + k, boosted);
+    } else {
+      for (int cell = tid - 32; cell < 256; cell += 224) {
+        const int ci = cell & 15, cj = cell >> 4;
+        const int c0 = cj * R, r0 = ci * R;
+        if (c0 + R <= n0 || cj > ci || r0 + R <= n0 + 8) continue;
+        F lc[R][8];
+#pragma unroll
+        for (int cc = 0; cc < R; ++cc)
+#pragma unroll
+          for (int t = 0; t < 8; ++t) lc[cc][t] = Ad[c0 + cc][b0 + t];
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          F lr[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) lr[t] = Ad[r0 + a][b0 + t];
+#pragma unroll
+          for (int cc = 0; cc < R; ++cc) {
+            const int r = r0 + a, c = c0 + cc;
+            if (c <= r && c >= n0 && r >= n0 + 8) {
+              F s = F(0);
+#pragma unroll
+              for (int t = 0; t < 8; ++t) s += lr[t] * lc[cc][t];
+              Ad[r][c] -= s;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  tile_inverse<F, T>(Ad, Y, Z);
+  F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
+  F* DiT = Di + v_total * T;
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    Di[idx] = Y[r][c];
+    DiT[idx] = Y[c][r];
+  }
+}
+
+// k_chol_trsm, one CTA per tile row i > kt of a cluster with a tile step kt:
+//   A_i,kt -= L_i,kt-1 L_kt,kt-1^T   (step kt - 1's update of the tile)
+//   L_i,kt  = A_i,kt Y^T              (Y = L_kt,kt^-1 from k_chol_diag: the triangular solve as a product)
+// both as 64 x 64 x 64 register-blocked products (4 x 4 per thread) over transposed shared-memory tiles.
+template <typename F, int T>
+struct TrsmLayout {
+  static constexpr int LD = T + (sizeof(F) == 4 ? 4 : 2);
+  static constexpr size_t bytes = sizeof(F) * 4 * (size_t)T * LD;
+};
+
+template <typename F, int T>
+__global__ void __launch_bounds__(256) k_chol_trsm(F* L, const F* Dinv, DevProblem P, const int2* items, int kt,
+                                                   int64_t v_total) {
+  constexpr int R = T / 16, LD = TrsmLayout<F, T>::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  F(*AT)[LD] = reinterpret_cast<F(*)[LD]>(smem_raw);   // A_i,kt transposed
+  F(*YT)[LD] = AT + T;                                   // Y^T (row m, column c = Y[c][m])
+  F(*LiT)[LD] = YT + T;                                  // L_i,kt-1 transposed
+  F(*LkT)[LD] = LiT + T;                                 // L_kt,kt-1 transposed
+  const int2 it = items[blockIdx.x];
+  const int k = it.x, i = it.y;
+  const int np = P.cluster_np[k];
+  F* A = L + P.S_off[k];
+  const F* DiT = Dinv + v_total * T + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
+  const size_t base_ik = (size_t)(i * T) * np + kt * T, base_kk = (size_t)(kt * T) * np + kt * T;
+  const int tid = threadIdx.x;
+  for (int idx = tid; idx < T * T; idx += 256) {
+    const int r = idx / T, c = idx - (idx / T) * T;
+    cp_async_elem(&AT[c][r], A + base_ik + (size_t)r * np + c);
+    if (kt > 0) {
+      cp_async_elem(&LiT[c][r], A + base_ik - T + (size_t)r * np + c);
+      cp_async_elem(&LkT[c][r], A + base_kk - T + (size_t)r * np + c);
+    }
+  }
+  {
+    constexpr int CH = T * (int)sizeof(F) / 16;   // 16-byte chunks per row of Y^T
+    for (int q = tid; q < T * CH; q += 256) {
+      const int r = q / CH, c = q - (q / CH) * CH;
+      cp_async16(&YT[r][c * (16 / (int)sizeof(F))], DiT + (size_t)r * T + c * (16 / (int)sizeof(F)));
+    }
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const int tr = tid >> 4, tc = tid & 15;
+  if (kt > 0) {
+    F acc[R][R];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a][b] = F(0);
+#pragma unroll 4
+    for (int m = 0; m < T; ++m) {
+      F av[R], bv[R];
+      load_vec<F, R>(&LiT[m][tr * R], av);
+      load_vec<F, R>(&LkT[m][tc * R], bv);
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) acc[a][b] += av[a] * bv[b];
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) AT[tc * R + b][tr * R + a] -= acc[a][b];
+    __syncthreads();
+  }
+  F acc[R][R];
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) acc[a][b] = F(0);
+#pragma unroll 4
+  for (int m = 0; m < T; ++m) {
+    F av[R], bv[R];
+    load_vec<F, R>(&AT[m][tr * R], av);
+    load_vec<F, R>(&YT[m][tc * R], bv);
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a][b] += av[a] * bv[b];
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) A[base_ik + (size_t)(tr * R + a) * np + tc * R + b] = acc[a][b];
 }
 
 // A_ij -= L_i,kt L_j,kt^T on a T x T tile; 256 threads, each an (T/16) x (T/16) register block.
@@ -595,10 +840,6 @@ struct SolveLayout {
   static constexpr size_t stage_bytes = sizeof(F) * (SOLVE_PF + 1) * tile_elems;
 };
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
@@ -924,10 +1165,23 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
   for (int kt = 0; kt < plan.nsteps; ++kt) {
     if (kt >= 2) cudaStreamWaitEvent(stream, plan.ev_update[kt - 2], 0);
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
-    if (npn > 0)
+    const int2* pitems = plan.panel_items + plan.h_panel_off[kt];
+    bool stacked = true;
+    if constexpr (sizeof(F) == 4 && T == 64) {
+      if (plan.split) {   // diagonal tiles (factor + inverse), then the tiles below them
+        stacked = false;
+        const int nd = plan.h_diag_count[kt];
+        if (nd > 0)
+          launch_prio(k_chol_diag<F, T>, nd, DiagLayout<F, T>::bytes, stream, plan.prio_high, (const F*)L, Dinv, P,
+                      pitems, kt, fb.fail_flags, fb.boosted, fb.v_total);
+        if (npn > nd)
+          launch_prio(k_chol_trsm<F, T>, npn - nd, TrsmLayout<F, T>::bytes, stream, plan.prio_high, L,
+                      (const F*)Dinv, P, pitems + nd, kt, fb.v_total);
+      }
+    }
+    if (stacked && npn > 0)
       launch_prio(k_chol_panel<F, T>, npn, panel_smem<F, T>(npn), stream, plan.prio_high, L,
-                  reinterpret_cast<F*>(fb.Ldiag), P, plan.panel_items + plan.h_panel_off[kt], kt, fb.fail_flags,
-                  fb.boosted);
+                  reinterpret_cast<F*>(fb.Ldiag), P, pitems, kt, fb.fail_flags, fb.boosted);
     cudaEventRecord(plan.ev_panel[kt], stream);
     cudaStreamWaitEvent(side, plan.ev_panel[kt], 0);
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];
@@ -947,7 +1201,7 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
   }
   cudaEventRecord(plan.ev_join, side);
   cudaStreamWaitEvent(stream, plan.ev_join, 0);
-  if (plan.n_diag_items > 0)
+  if (plan.n_diag_items > 0 && !plan.split)   // the split panel's diagonal kernels wrote the inverses
     k_diag_inverse<F, T><<<plan.n_diag_items, 256, 0, stream>>>(reinterpret_cast<const F*>(fb.Ldiag), Dinv, P,
                                                                 plan.diag_items, fb.v_total);
 }
@@ -1031,6 +1285,8 @@ void configure_solve_kernels(int max_np) {
   raise_smem_attr((const void*)k_chol_panel<float, 32>, (int)panel_smem<float, 32>());
   raise_smem_attr((const void*)k_chol_panel<double, 32>, (int)panel_smem<double, 32>());
   raise_smem_attr((const void*)k_chol_update_tc, (int)TCU_SMEM);
+  raise_smem_attr((const void*)k_chol_diag<float, 64>, (int)DiagLayout<float, 64>::bytes);
+  raise_smem_attr((const void*)k_chol_trsm<float, 64>, (int)TrsmLayout<float, 64>::bytes);
   // room for three stages wherever solve_stages may choose them
   auto stages = [&](size_t three) { return three <= (size_t)optin ? 3 : 2; };
   const int f64 = stages(solve_cta_bytes<float, 64>(3, max_np)) * SolveLayout<float, 64>::stage_bytes +

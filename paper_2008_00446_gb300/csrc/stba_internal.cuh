@@ -229,6 +229,10 @@ struct CholPlan {
   int tile;                       // factorisation tile T (the dense blocks are padded to it)
   int update_tc;                  // 1: trailing updates on the tensor cores (FP32 factor, T = 64); the update
                                   // items are then (cluster, (i0 << 16) | j) for the tile pair (i0, i0 + 1) x j
+  int split;                      // 1: split panel (FP32 factor, T = 64): each step's panel items list the
+                                  // diagonal tiles (cluster, kt) first, h_diag_count[kt] of them, then the
+                                  // tiles below them
+  const int* h_diag_count;        // host [nsteps]
 };
 struct FactorBuffers {
   void* L;          // factor (F = float or double), same layout as S'
@@ -265,10 +269,12 @@ struct AdjointBuffers {
   double* vpz;    // [nv][6] z_v and the expanded point step of every virtual point
   double* T;      // [q][12] per-observation terms
   double* qbar;   // [q][2] observation adjoint, input order
+  double* zeta;   // [n][3] corrected steps: h-weighted mean of the copies' z_v per point
+  double* kappa;  // [nv][3] corrected steps: (z_v - zeta_i) o w_i / H_i per virtual point
 };
 template <typename real>
 void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, const FactorBuffers& fb,
-                         const CholPlan& plan, int refine_steps, const int* perm, double lam,
+                         const CholPlan& plan, int refine_steps, const int* perm, double lam, int corrected,
                          const AdjointBuffers& A, cudaStream_t stream);
 void launch_set_lambda(DevState* st, double lam, cudaStream_t stream);
 

@@ -18,6 +18,10 @@ _LIB = None
 STBA_FP64, STBA_MIXED = 0, 1
 STBA_SOLVER_CLUSTERS, STBA_SOLVER_PCG_FULL, STBA_SOLVER_PCG_CLUSTERS = 0, 1, 2
 STBA_FACTOR_UPDATE_DEFAULT, STBA_FACTOR_UPDATE_SIMT, STBA_FACTOR_UPDATE_TENSOR = 0, 1, 2
+STBA_FACTOR_PANEL_DEFAULT, STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_SPLIT = 0, 1, 2
+# stba_autotune's candidates: name -> (factor_tile, factor_update, factor_panel)
+AUTOTUNE_CANDIDATES = {"64_split_tensor": (64, 2, 2), "64_split_simt": (64, 1, 2), "64_stacked_simt": (64, 1, 1),
+                       "32_stacked_simt": (32, 1, 1)}
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not SPD",
           5: "non-finite value", 6: "timeout", 7: "invalid state"}
 
@@ -36,7 +40,8 @@ class StbaOptions(ctypes.Structure):
                 ("ftol", ctypes.c_double), ("gtol", ctypes.c_double), ("xtol", ctypes.c_double),
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
-                ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32), ("factor_update", ctypes.c_int32)]
+                ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32), ("factor_update", ctypes.c_int32),
+                ("factor_panel", ctypes.c_int32)]
 
 
 class StbaIterInfo(ctypes.Structure):
@@ -104,7 +109,7 @@ def load(build_if_missing: bool = True):
         "stba_graph_cluster_batch": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
         "stba_graph_destroy": (None, [P]),
         "stba_cluster_sgc": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
-        "stba_autotune": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float)]),
+        "stba_autotune": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float)]),
         "stba_measure_peaks": (I32, [P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
@@ -341,12 +346,13 @@ def stba_measure_peaks(reps=5, stream=None):
 
 
 def stba_autotune(ctx: Context, iterations=5):
-    """Times the candidate factorisations and keeps the fastest: (tile, update, {candidate: ms}) with the
-    candidates "64_tensor" (tile 64, tensor-core trailing update), "64_simt" and "32_simt"."""
-    tile, update = ctypes.c_int32(), ctypes.c_int32()
-    ms = (ctypes.c_float * 3)()
-    ctx._check(load().stba_autotune(ctx.handle, int(iterations), ctypes.byref(tile), ctypes.byref(update), ms))
-    return tile.value, update.value, {"64_tensor": ms[0], "64_simt": ms[1], "32_simt": ms[2]}
+    """Times the candidate factorisations (AUTOTUNE_CANDIDATES, in order) and keeps the fastest:
+    (name of the kept candidate or None, {candidate: ms per iteration})."""
+    choice = ctypes.c_int32()
+    names = list(AUTOTUNE_CANDIDATES)
+    ms = (ctypes.c_float * len(names))()
+    ctx._check(load().stba_autotune(ctx.handle, int(iterations), ctypes.byref(choice), ms))
+    return (names[choice.value] if choice.value >= 0 else None), {nm: ms[i] for i, nm in enumerate(names)}
 
 
 def stba_record(ctx: Context, max_iter: int):

@@ -94,7 +94,10 @@ def test_invalid_options_are_rejected():
     # the tensor-core trailing update exists for the FP32 factor with tile 64 only
     for kw in (dict(factor_update=stba.STBA_FACTOR_UPDATE_TENSOR),
                dict(precision=1, factor_tile=32, factor_update=stba.STBA_FACTOR_UPDATE_TENSOR),
-               dict(precision=1, factor_update=3), dict(precision=1, factor_update=-1)):
+               dict(precision=1, factor_update=3), dict(precision=1, factor_update=-1),
+               dict(factor_panel=stba.STBA_FACTOR_PANEL_SPLIT),
+               dict(precision=1, factor_tile=32, factor_panel=stba.STBA_FACTOR_PANEL_SPLIT),
+               dict(precision=1, factor_panel=3)):
         with pytest.raises(stba.StbaError):
             stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, **kw)
     for bad in (-0.5, float("nan"), float("inf")):

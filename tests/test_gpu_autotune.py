@@ -24,12 +24,12 @@ def ring():
     return s, F, hist
 
 
-@pytest.mark.parametrize("tile,update", [(64, stba.STBA_FACTOR_UPDATE_TENSOR), (64, stba.STBA_FACTOR_UPDATE_SIMT),
-                                         (32, stba.STBA_FACTOR_UPDATE_SIMT)])
-def test_every_fp32_factorisation_meets_the_mixed_bar(ring, tile, update):
+@pytest.mark.parametrize("cand", list(stba.AUTOTUNE_CANDIDATES) + ["64_stacked_tensor"])
+def test_every_fp32_factorisation_meets_the_mixed_bar(ring, cand):
     s, F, hist = ring
+    tile, update, panel = stba.AUTOTUNE_CANDIDATES.get(cand, (64, 2, 1))
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
-                           precision=stba.STBA_MIXED, factor_tile=tile, factor_update=update)
+                           precision=stba.STBA_MIXED, factor_tile=tile, factor_update=update, factor_panel=panel)
     stba.stba_lm_iteration(ctx)
     dc, dp = stba.stba_last_step(ctx)
     assert cols(dc, hist[0]["dc"], 9) < 1e-3 and cols(dp, hist[0]["dp"], 3) < 1e-3
@@ -46,16 +46,16 @@ def test_autotune_restores_the_state_and_keeps_a_working_tile(ring):
     stba.stba_lm_iteration(ctx)
     lam0, F0, it0 = stba.stba_get_state(ctx)
     c0, p0 = stba.stba_get_params(ctx)
-    tile, update, ms = stba.stba_autotune(ctx, 3)
-    assert (tile, update) in ((64, stba.STBA_FACTOR_UPDATE_TENSOR), (64, stba.STBA_FACTOR_UPDATE_SIMT),
-                              (32, stba.STBA_FACTOR_UPDATE_SIMT))
+    kept, ms = stba.stba_autotune(ctx, 3)
+    assert kept in stba.AUTOTUNE_CANDIDATES
+    tile, update, panel = stba.AUTOTUNE_CANDIDATES[kept]
     assert all(v > 0 for v in ms.values()), ms
     lam1, F1, it1 = stba.stba_get_state(ctx)
     c1, p1 = stba.stba_get_params(ctx)
     assert lam1 == lam0 and F1 == F0 and np.array_equal(c1, c0) and np.array_equal(p1, p0)
     info = stba.stba_lm_iteration(ctx)
     ref = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
-                           precision=stba.STBA_MIXED, factor_tile=tile, factor_update=update)
+                           precision=stba.STBA_MIXED, factor_tile=tile, factor_update=update, factor_panel=panel)
     stba.stba_lm_iteration(ref)
     info_ref = stba.stba_lm_iteration(ref)
     assert info["accepted"] == info_ref["accepted"]

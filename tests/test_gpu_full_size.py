@@ -76,11 +76,13 @@ def test_first_step_fp64_elementwise(name, lam):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-def test_mixed_first_step_elementwise(name):
+@pytest.mark.parametrize("panel", [stba.STBA_FACTOR_PANEL_STACKED, stba.STBA_FACTOR_PANEL_SPLIT])
+def test_mixed_first_step_elementwise(name, panel):
+    # both panels of the FP32 factor (the default picks one by the number of tiles per step)
     s = scene(name)
     _, _, _, _, rec = oracle_first(s, 1e-4)
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
-                           precision=stba.STBA_MIXED)
+                           precision=stba.STBA_MIXED, factor_panel=panel)
     info = stba.stba_lm_iteration(ctx)
     assert info["failed_clusters"] == 0
     dc, dp = stba.stba_last_step(ctx)
