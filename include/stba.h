@@ -292,6 +292,35 @@ stba_status stba_autotune(stba_ctx* ctx, int32_t iterations, int32_t* choice, fl
  * bounded wait gave up). */
 stba_status stba_measure_peaks(void* cuda_stream, int32_t reps, double* fp32_tflops, double* tf32_tflops);
 
+/* Sharded iteration over several processes, one context each (the paper's cluster-parallel, distributed
+ * execution, Sec. 1 and the distributed runs of Sec. 5): after point splitting and binding (Sec. 4.1-4.2) the
+ * cluster systems of Eq. 13 are independent, so each process linearises the observations of, builds,
+ * factors and solves only the clusters it owns, and sums what spans clusters with the caller's transport.
+ *   rank, world: this process and the number of processes; every process creates its context from the same
+ *     problem and applies the same cluster assignments (stba_set_clusters) in the same order.  A cluster
+ *     belongs to one process, chosen on every assignment by the same deterministic rule everywhere: longest
+ *     processing time first by the cost model (9 n_k)^3 / 3 + 2000 x (observations of its cameras), ties to
+ *     the lower cluster id and the lower rank.  stba_shard_owned reports the owned clusters.
+ *   fn: the transport: sums `count` values (dtype 0 = FP64, 1 = FP32) over all processes, in place, and
+ *     returns 0 on success.  host_staging = 1: the library copies the values to a pinned host buffer,
+ *     synchronises its stream, calls fn with the host pointer, and copies the sums back (CPU transports such
+ *     as gloo); host_staging = 0: fn gets the device pointer and the context stream, and must order its work
+ *     on that stream (device transports such as NCCL).  user is passed to fn unchanged.
+ * Per LM iteration fn is called four times: the per-point sums of the virtual-point blocks (9 n FP64: C_i
+ * and w_i of Eq. 15, which also carry the per-point sums of the steepest-descent correction, Sec. 4.3);
+ * after the cluster solves Delta c (9 m FP64, zero for the other processes' cameras), the camera gradient
+ * (9 m, working precision) and the number of failed factorisations (1 FP64).  The point update, F(x + Delta
+ * x) and the accept rule then run on complete data in every process, so all hold the same parameters,
+ * damping and cost.  Sharded iterations are not captured in a CUDA graph and are not recorded for the
+ * adjoint.  world = 1 returns to the single-process iteration.
+ * Errors: STBA_ERR_INVALID_ARG (rank out of range, no transport), STBA_ERR_STATE (a PCG solver, a recording
+ * tape; a transport call that returned non-zero fails the iteration with STBA_ERR_STATE). */
+typedef int32_t (*stba_allreduce_fn)(void* user, void* data, int64_t count, int32_t dtype, void* cuda_stream);
+stba_status stba_set_shard(stba_ctx* ctx, int32_t rank, int32_t world, stba_allreduce_fn fn, void* user,
+                           int32_t host_staging);
+/* *l = clusters of the current assignment; owned [l] (optional, HOST) = 1 where this process owns cluster k. */
+stba_status stba_shard_owned(stba_ctx* ctx, int32_t* owned, int32_t* l);
+
 /* Frees every device allocation of the context.  NULL is allowed. */
 void stba_destroy(stba_ctx* ctx);
 

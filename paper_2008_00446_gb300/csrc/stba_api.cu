@@ -134,6 +134,17 @@ struct stba_ctx {
   int split_panel = 0;                  // split panel: diagonal-tile factor + inverse, then the tiles below
   int panel_choice = STBA_FACTOR_PANEL_DEFAULT;   // option, or the autotuner's choice; DEFAULT decides per
                                                   // assignment (set_clusters_host)
+  // sharded iteration (stba_set_shard): this process's rank among `shard_world`, the transport, the clusters
+  // it owns under the current assignment (host and device), and the exchange buffers
+  int shard_rank = 0, shard_world = 1, shard_host_staging = 1;
+  stba_allreduce_fn shard_fn = nullptr;
+  void* shard_user = nullptr;
+  std::vector<int> h_owned;             // [l]
+  std::vector<int> h_cam_nobs;          // [m] observations of every camera (the cost model of the ownership)
+  int* cl_owned = nullptr;              // [m] device (l <= m); all 1 unless sharded
+  double* xch = nullptr;                // [9 n + 1] device: point sums, then the failure count
+  void* xch_host = nullptr;             // pinned staging of an exchange
+  size_t xch_host_bytes = 0;
   std::vector<int> h_diag_count;        // split panel: diagonal items of every step
   bool capturing = false;
   bool timing = false;
@@ -255,6 +266,8 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.huber_a = c->opt.huber_a;
   P.res_f = c->mixed ? (const float*)c->res_cur : nullptr;
   P.res_d = c->mixed ? nullptr : (const double*)c->res_cur;
+  P.sharded = c->shard_world > 1 ? 1 : 0;
+  P.cluster_owned = c->cl_owned;
   return P;
 }
 
@@ -333,7 +346,7 @@ static void enqueue_reorder(stba_ctx* c, const ReorderArgs& A, bool carry, cudaS
     launch_reorder<double>(A, c->key, c->tile_sum, c->counts, carry ? (const double*)c->res_cur : nullptr,
                            (double*)c->res_cand, st);
   if (!c->use_pcg && !c->use_spcg && c->pchunks.nchunks > 0)
-    launch_list_chunks(c->pchunks, c->cam_cluster, c->counts + 3, st);
+    launch_list_chunks(c->pchunks, c->cam_cluster, c->cl_owned, c->counts + 3, st);
 }
 
 static stba_status launch_reorder_graph(stba_ctx* c, const ReorderArgs& A, bool carry) {
@@ -349,7 +362,7 @@ static stba_status launch_reorder_graph(stba_ctx* c, const ReorderArgs& A, bool 
   std::memset(key.data() + 12, 0, 4);
   const void* more[] = {c->key, c->tile_sum, c->counts, carry ? c->res_cur : nullptr, c->res_cand,
                         c->pchunks.chunks, c->pchunks.active, c->pchunks.nactive, c->pchunks.flag,
-                        c->pchunks.excl, c->pchunks.tile_sum, c->cam_cluster};
+                        c->pchunks.excl, c->pchunks.tile_sum, c->cam_cluster, c->cl_owned};
   const long long flags[] = {c->mixed, c->use_pcg || c->use_spcg, c->pchunks.nchunks};
   const unsigned char* m1 = reinterpret_cast<const unsigned char*>(more);
   const unsigned char* m2 = reinterpret_cast<const unsigned char*>(flags);
@@ -439,6 +452,27 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   }
   c->S_total = so;
   c->v_total = vo;
+  // ownership of the clusters (sharded iteration): longest processing time first by the cost model of one
+  // iteration per cluster, (9 n_k)^3 / 3 + 2000 x (observations of its cameras); ties go to the lower
+  // cluster id and the lower rank.  Every process computes the same owners from the same assignment.
+  c->h_owned.assign(l, 1);
+  if (c->shard_world > 1) {
+    std::vector<double> cost(l, 0.0);
+    for (int k = 0; k < l; ++k) cost[k] = std::pow(9.0 * cnt[k], 3) / 3.0;
+    for (int j = 0; j < m; ++j) cost[cl[j]] += 2000.0 * c->h_cam_nobs[j];
+    std::vector<int> order(l);
+    for (int k = 0; k < l; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> load(c->shard_world, 0.0);
+    for (int k : order) {
+      int r = 0;
+      for (int t = 1; t < c->shard_world; ++t)
+        if (load[t] < load[r]) r = t;
+      c->h_owned[k] = r == c->shard_rank ? 1 : 0;
+      load[r] += cost[k];
+    }
+  }
+  CK(cudaMemcpyAsync(c->cl_owned, c->h_owned.data(), (size_t)l * sizeof(int), cudaMemcpyHostToDevice, c->stream));
   // panel of the FP32 factor with tile 64: the split panel pays off once a tile step's tiles outnumber the SMs
   // (several waves of panel CTAs per step; each of them would factor its diagonal tile again), the stacked
   // panel when they fit in one wave (a single kernel per step on the critical path)
@@ -467,13 +501,13 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->h_update_off[kt] = (int)update.size();
     if (c->split_panel)   // the diagonal tiles of the step first
       for (int k = 0; k < l; ++k)
-        if (c->h_np[k] / TF > kt) {
+        if (c->h_np[k] / TF > kt && c->h_owned[k]) {
           panel.push_back(make_int2(k, kt));
           c->h_diag_count[kt]++;
         }
     for (int k = 0; k < l; ++k) {
       const int ntk = c->h_np[k] / TF;
-      if (ntk <= kt) continue;
+      if (ntk <= kt || !c->h_owned[k]) continue;   // sharded: the other processes' clusters
       for (int i = c->split_panel ? kt + 1 : kt; i < ntk; ++i) panel.push_back(make_int2(k, i));
       for (int j = kt + 2; j < ntk; ++j) {   // column kt + 1 is updated by panel kt + 1 itself
         if (c->update_tc)   // tile pairs (i0, i0 + 1) x j, from the diagonal tile down
@@ -487,9 +521,11 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   c->h_update_off[max_nt] = (int)update.size();
   std::vector<int2> res_items, diag_items;
   for (int k = 0; k < l && !c->use_pcg; ++k)
-    for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
+    if (c->h_owned[k])
+      for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
   for (int k = 0; k < l && !c->use_pcg; ++k)
-    for (int t = 0; t < c->h_np[k] / TF; ++t) diag_items.push_back(make_int2(k, t));
+    if (c->h_owned[k])
+      for (int t = 0; t < c->h_np[k] / TF; ++t) diag_items.push_back(make_int2(k, t));
   while ((int)c->ev_panel.size() < max_nt) {
     cudaEvent_t e1, e2;
     if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess ||
@@ -751,7 +787,93 @@ stba_status run_cost(stba_ctx* c, double* F) {
   return STBA_OK;
 }
 
+// One exchange of the sharded iteration: `count` values (FP64, or the working precision for dtype 1) at the
+// device pointer `dev` summed over the processes by the caller's transport.  With host staging the values
+// travel through a pinned host buffer and the transport sees host memory (e.g. gloo); otherwise it gets the
+// device pointer and the stream (e.g. NCCL).
+stba_status shard_exchange(stba_ctx* c, void* dev, int64_t count, int32_t dtype) {
+  const size_t bytes = (size_t)count * (dtype == 0 ? 8 : 4);
+  if (c->shard_host_staging) {
+    if (c->xch_host_bytes < bytes) {
+      if (c->xch_host) cudaFreeHost(c->xch_host);
+      c->xch_host = nullptr;
+      c->xch_host_bytes = 0;
+      if (cudaHostAlloc(&c->xch_host, bytes, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, STBA_ERR_OOM, "pinned host allocation of the exchange buffer failed");
+      }
+      c->xch_host_bytes = bytes;
+    }
+    CK(cudaMemcpyAsync(c->xch_host, dev, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->shard_fn(c->shard_user, c->xch_host, count, dtype, (void*)c->stream) != 0)
+      return fail(c, STBA_ERR_STATE, "the sharded iteration's exchange (all-reduce) failed");
+    CK(cudaMemcpyAsync(dev, c->xch_host, bytes, cudaMemcpyHostToDevice, c->stream));
+    return STBA_OK;
+  }
+  if (c->shard_fn(c->shard_user, dev, count, dtype, (void*)c->stream) != 0)
+    return fail(c, STBA_ERR_STATE, "the sharded iteration's exchange (all-reduce) failed");
+  return STBA_OK;
+}
+
+// One LM iteration of the sharded method (stba_set_shard): this process linearises the observations of its
+// clusters, builds, factors and solves only those clusters, and three exchanges make the rest identical on
+// every process:
+//   1. per point, the sums over its virtual points of V and w' (9 values): the physical C_i and w_i of
+//      Eq. 15 and the per-point sums of the steepest-descent correction (Sec. 4.3);
+//   2. after the cluster solves, Delta c (zero for the other processes' cameras), the camera gradient v and
+//      the count of failed cluster factorisations;
+// the point update, the cost at x + Delta x and the accept / reject rule then run on complete data in every
+// process, which therefore all hold the same parameters, damping and cost.  Enqueued without a graph: the
+// exchanges return to the host.
+template <typename real>
+stba_status run_sharded_iteration(stba_ctx* c) {
+  const DevProblem P = dev_problem(c);
+  const Scratch<real> W = scratch<real>(c);
+  cudaStream_t s = c->stream;
+  stba_status st;
+  const size_t rs = sizeof(real);
+  record_stage(c, 0);
+  launch_iter_begin<real>(c->st, c->set, s);
+  if (c->mixed) launch_params_to_float(P, c->cams_f, c->pts_f, s);
+  launch_zero_vp(c->vp_acc, c->counts, (int)rs, s);
+  cudaMemsetAsync(c->S, 0, (size_t)c->S_total * sizeof(double), s);
+  cudaMemsetAsync(c->b, 0, (size_t)c->v_total * sizeof(double), s);
+  cudaMemsetAsync(c->vgrad, 0, 9 * (size_t)c->m * rs, s);
+  cudaMemsetAsync(c->t_acc, 0, 3 * (size_t)c->n * rs, s);
+  cudaMemsetAsync(c->fail_flags, 0, (size_t)c->l * sizeof(int), s);
+  launch_vp_reduce<real>(P, W, s);   // this process's observations only
+  launch_pt_sums<real>(P, W, c->xch, s);
+  if ((st = shard_exchange(c, c->xch, 9 * (int64_t)c->n, 0)) != STBA_OK) return st;
+  launch_vp_finalize<real>(P, W, c->st, s, c->xch);
+  record_stage(c, 1);
+  launch_rcs_build<real>(P, W, c->cslots, c->pchunks, (real*)c->Gbuf, c->st, s);
+  record_stage(c, 2);
+  launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
+  record_stage(c, 3);
+  launch_solve<real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
+  launch_count_failures(c->fail_flags, c->l, c->st, s);
+  double* nfail = c->xch + 9 * (size_t)c->n;
+  launch_failed_io(c->st, nfail, 1, s);
+  if ((st = shard_exchange(c, c->dc, 9 * (int64_t)c->m, 0)) != STBA_OK) return st;
+  if ((st = shard_exchange(c, c->vgrad, 9 * (int64_t)c->m, c->mixed ? 1 : 0)) != STBA_OK) return st;
+  if ((st = shard_exchange(c, nfail, 1, 0)) != STBA_OK) return st;
+  launch_failed_io(c->st, nfail, 0, s);
+  if (c->mixed) launch_dc_to_float(c->dc, c->dcf, 9 * (int64_t)c->m, s);
+  record_stage(c, 4);
+  launch_point_rhs<real>(P, W, s);
+  launch_point_update<real>(P, W, s);
+  launch_cost<real>(P, c->dc, c->dp, c->cam_rt, c->cam_df, c->pt_df, c->partial, c->st, (real*)c->res_cand, s);
+  launch_finalize<real>(P, W, c->st, c->set, 1, s);
+  launch_apply<real>(P, c->dc, c->dp, c->cams, c->pts, (const real*)c->res_cand, (real*)c->res_cur, c->st, s);
+  record_stage(c, 5);
+  CK(cudaGetLastError());
+  c->have_stage_times = true;
+  return STBA_OK;
+}
+
 stba_status launch_iteration(stba_ctx* c) {
+  if (c->shard_world > 1) return c->mixed ? run_sharded_iteration<float>(c) : run_sharded_iteration<double>(c);
   if (c->use_pcg || c->use_spcg) {
     const int32_t iters = c->mixed ? enqueue_pcg_iteration<float>(c) : enqueue_pcg_iteration<double>(c);
     CK(cudaGetLastError());
@@ -1086,6 +1208,37 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* choice, floa
   return STBA_OK;
 }
 
+stba_status stba_set_shard(stba_ctx* c, int32_t rank, int32_t world, stba_allreduce_fn fn, void* user,
+                           int32_t host_staging) {
+  if (!c) return STBA_ERR_INVALID_ARG;
+  if (world < 1 || rank < 0 || rank >= world || (world > 1 && !fn))
+    return fail(c, STBA_ERR_INVALID_ARG, "stba_set_shard: need 0 <= rank < world and a transport when world > 1");
+  if (world > 1 && (c->use_pcg || c->use_spcg))
+    return fail(c, STBA_ERR_STATE, "the sharded iteration covers the cluster solver only");
+  if (world > 1 && c->tape_cap > 0)
+    return fail(c, STBA_ERR_STATE, "the sharded iteration does not record (stba_record / stba_adjoint)");
+  if (world > 1 && !c->xch) {
+    stba_status s = dalloc(c, &c->xch, 9 * (size_t)c->n + 1);
+    if (s != STBA_OK) return s;
+  }
+  c->shard_rank = world > 1 ? rank : 0;
+  c->shard_world = world;
+  c->shard_fn = world > 1 ? fn : nullptr;
+  c->shard_user = user;
+  c->shard_host_staging = host_staging ? 1 : 0;
+  c->graph_stale = true;
+  const std::vector<int> cl = c->h_clusters;
+  return set_clusters_host(c, cl);   // owners and the plan of the current assignment
+}
+
+stba_status stba_shard_owned(stba_ctx* c, int32_t* owned, int32_t* l) {
+  if (!c || !l) return STBA_ERR_INVALID_ARG;
+  *l = c->l;
+  if (owned)
+    for (int k = 0; k < c->l; ++k) owned[k] = c->h_owned[k];
+  return STBA_OK;
+}
+
 const char* stba_last_error(stba_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
 
 void stba_destroy(stba_ctx* c) {
@@ -1101,6 +1254,7 @@ void stba_destroy(stba_ctx* c) {
     if (c->stage_h[i]) cudaFreeHost(c->stage_h[i]);
     if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
   }
+  if (c->xch_host) cudaFreeHost(c->xch_host);
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
   for (cudaGraphExec_t& e : c->reorder_exec)
@@ -1197,6 +1351,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if (pcount[i + 1] < 2) return bail(fail(c, STBA_ERR_INVALID_ARG, "point %lld has fewer than 2 observations", (long long)i));
   for (int64_t j = 0; j < m; ++j)
     if (ccount[j] < 1) return bail(fail(c, STBA_ERR_INVALID_ARG, "camera %lld has no observation", (long long)j));
+  c->h_cam_nobs = ccount;
   for (int64_t i = 0; i < n; ++i) pcount[i + 1] += pcount[i];
   c->h_pt_off = pcount;
   c->base_order.assign(q, 0);
@@ -1405,6 +1560,12 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = dalloc(c, &c->counts, 4)) != STBA_OK) return bail(s);   // nv, pairs, singles, active chunks
     // failure flags at their largest size (l <= m); the other cluster arrays live in the assignment blob
     if ((s = dalloc(c, &c->fail_flags, (size_t)m)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &c->cl_owned, (size_t)m)) != STBA_OK) return bail(s);
+    {
+      const std::vector<int> ones(m, 1);
+      CK(cudaMemcpyAsync(c->cl_owned, ones.data(), (size_t)m * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+    }
     // per-iteration scratch (virtual-point arrays at their largest size, nv <= q)
     const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
     char *vpa, *vpi, *pti, *vg, *ta, *gb;

@@ -42,6 +42,7 @@ int factor_tile(bool mixed) { return mixed ? 64 : 32; }
 template <typename Sreal>
 __global__ void k_diag_scale(DevProblem P, const Sreal* S, double* scale) {
   const int k = blockIdx.y;
+  if (P.sharded && !P.cluster_owned[k]) return;
   const int np = P.cluster_np[k], nk = P.cluster_n[k];
   const Sreal* Sk = S + P.S_off[k];
   double* sk = scale + P.v_off[k];
@@ -55,6 +56,7 @@ __global__ void k_diag_scale(DevProblem P, const Sreal* S, double* scale) {
 template <typename Sreal, typename F>
 __global__ void k_scaled_copy(DevProblem P, const Sreal* S, const double* scale, F* L) {
   const int k = blockIdx.y;
+  if (P.sharded && !P.cluster_owned[k]) return;
   const int np = P.cluster_np[k];
   const Sreal* Sk = S + P.S_off[k];
   F* Lk = L + P.S_off[k];
@@ -885,6 +887,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   __shared__ F pcol[PARTS][T];
   const int rank = (int)cluster.block_rank();
   const int k = blockIdx.x / SOLVE_CS;
+  if (P.sharded && !P.cluster_owned[k]) return;   // the whole thread-block cluster leaves, before any barrier
   const int np = P.cluster_np[k];
   const F* A = L + P.S_off[k];
   const F* Di = Dinv + (size_t)P.v_off[k] * T;
@@ -1091,14 +1094,17 @@ __global__ void k_copy_vec(const Rreal* src, double* dst, int64_t n) {
     dst[i] = (double)src[i];
 }
 
+// sharded: another process's clusters scatter zeros (their steps arrive by the exchange of dc)
 __global__ void k_scatter_dc(DevProblem P, const double* x, double* dc, float* dcf) {
   const int k = blockIdx.x;
   const int nk = P.cluster_n[k], cbase = P.cluster_cam_off[k];
+  const bool own = !P.sharded || P.cluster_owned[k];
   const double* xk = x + P.v_off[k];
   for (int i = threadIdx.x; i < nk; i += blockDim.x) {
     const int cam = P.cluster_cams[cbase + i / 9];
-    dc[9 * (size_t)cam + i % 9] = xk[i];
-    if (dcf) dcf[9 * (size_t)cam + i % 9] = (float)xk[i];
+    const double v = own ? xk[i] : 0.0;
+    dc[9 * (size_t)cam + i % 9] = v;
+    if (dcf) dcf[9 * (size_t)cam + i % 9] = (float)v;
   }
 }
 

@@ -45,6 +45,9 @@ struct DevProblem {
   double huber_a;              // Huber scale a (0: plain least squares)
   const float* res_f;          // [q][2] residuals f_o at the current x, computed in FP64, stored in the
   const double* res_d;         //        working precision (res_f in mixed mode, res_d in FP64 mode)
+  int sharded;                 // 1: this process owns only some clusters (stba_set_shard)
+  const int* cluster_owned;    // [l] 1 where this process builds, factors and solves cluster k (all 1 unless
+                               //     sharded)
 };
 
 template <typename real> __host__ __device__ inline const real* res_ptr(const DevProblem& P);
@@ -112,7 +115,8 @@ struct PairChunks {   // observation pairs of the camera graph, by edge, cut int
   int* tile_sum;            // [nchunks / 2048 + 2]
 };
 // lists the chunks inside clusters for the current assignment (cam_cluster on the device)
-void launch_list_chunks(const PairChunks& B, const int* cam_cluster, long long* nactive, cudaStream_t stream);
+void launch_list_chunks(const PairChunks& B, const int* cam_cluster, const int* owned, long long* nactive,
+                        cudaStream_t stream);
 constexpr int PAIR_CHUNK = 64;
 
 // Camera graph (stba_graph.cu): edges (x, y), y < x, grouped by x with y ascending; weight = number of
@@ -178,7 +182,16 @@ void launch_iter_begin(DevState* st, const Settings& s, cudaStream_t stream);
 template <typename real>
 void launch_vp_reduce(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
 template <typename real>
-void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream);
+void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream,
+                        const double* pt_sums = nullptr);
+// Sharded iteration: per point, the sums over this process's virtual points of V (packed 6) and w' (3), FP64
+// [n][9] (the other processes' virtual points are zero here); summed over the processes they are C_i, w_i.
+template <typename real>
+void launch_pt_sums(const DevProblem& P, Scratch<real> W, double* out, cudaStream_t stream);
+// dcf = (float) dc, n values
+void launch_dc_to_float(const double* dc, float* dcf, int64_t n, cudaStream_t stream);
+// to_double = 1: *x = st->failed; 0: st->failed = (int) *x
+void launch_failed_io(DevState* st, double* x, int to_double, cudaStream_t stream);
 template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
                       cudaStream_t stream);

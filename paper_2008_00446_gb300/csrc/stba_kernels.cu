@@ -47,7 +47,9 @@ template <typename real>
 __global__ void __launch_bounds__(256) k_vp_reduce(DevProblem P, real* vp_acc) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const bool act = o < P.q;
+  // sharded: only the observations of this process's clusters (a virtual point lies in one cluster, so its
+  // observations are all in or all out)
+  const bool act = o < P.q && (!P.sharded || P.cluster_owned[P.cam_cluster[P.obs_cam[o]]]);
   int v = INT_MAX;
   real val[9];
 #pragma unroll
@@ -112,19 +114,27 @@ __device__ __forceinline__ double block_max(double v) {
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256) k_vp_finalize(DevProblem P, Scratch<real> W, DevState* st) {
+__global__ void __launch_bounds__(256) k_vp_finalize(DevProblem P, Scratch<real> W, DevState* st,
+                                                     const double* __restrict__ pt_sums) {
   const real lam = (real)st->lambda_used;
   const bool corr = st->corrected != 0;
   double gmax = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
     const int vb = P.pt_vp_off[i], ve = P.pt_vp_off[i + 1];
     real C[6] = {0, 0, 0, 0, 0, 0}, w[3] = {0, 0, 0};
-    for (int v = vb; v < ve; ++v) {
-      const real* a = W.vp_acc + 9 * (size_t)v;
+    if (pt_sums) {   // sharded: the sums over every process's virtual points of the point, exchanged
 #pragma unroll
-      for (int c = 0; c < 6; ++c) C[c] += a[c];
+      for (int c = 0; c < 6; ++c) C[c] = (real)pt_sums[9 * (size_t)i + c];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) w[c] += a[6 + c];
+      for (int c = 0; c < 3; ++c) w[c] = (real)pt_sums[9 * (size_t)i + 6 + c];
+    } else {
+      for (int v = vb; v < ve; ++v) {
+        const real* a = W.vp_acc + 9 * (size_t)v;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) C[c] += a[c];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) w[c] += a[6 + c];
+      }
     }
     real dbar[3];
     dbar[0] = w[0] / C[0];
@@ -137,6 +147,12 @@ __global__ void __launch_bounds__(256) k_vp_finalize(DevProblem P, Scratch<real>
       for (int c = 0; c < 6; ++c) V[c] = a[c];
 #pragma unroll
       for (int c = 0; c < 3; ++c) wv[c] = a[6 + c];
+      if (pt_sums && V[0] == real(0) && V[3] == real(0) && V[5] == real(0)) {   // another process's cluster
+        real* out = W.vp_info + 9 * (size_t)v;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) out[c] = real(0);
+        continue;
+      }
       if (corr) {
         wv[0] = V[0] * dbar[0];
         wv[1] = V[3] * dbar[1];
@@ -176,10 +192,50 @@ __global__ void __launch_bounds__(256) k_vp_finalize(DevProblem P, Scratch<real>
 }
 
 template <typename real>
-void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream) {
+void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream,
+                        const double* pt_sums) {
   int blocks = (P.n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  k_vp_finalize<real><<<blocks, 256, 0, stream>>>(P, W, st);
+  k_vp_finalize<real><<<blocks, 256, 0, stream>>>(P, W, st, pt_sums);
+}
+
+template <typename real>
+__global__ void k_pt_sums(DevProblem P, const real* __restrict__ vp_acc, double* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    double s[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int v = P.pt_vp_off[i]; v < P.pt_vp_off[i + 1]; ++v)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) s[c] += (double)vp_acc[9 * (size_t)v + c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) out[9 * (size_t)i + c] = s[c];
+  }
+}
+
+template <typename real>
+void launch_pt_sums(const DevProblem& P, Scratch<real> W, double* out, cudaStream_t stream) {
+  k_pt_sums<real><<<std::min((P.n + 255) / 256, 4096), 256, 0, stream>>>(P, W.vp_acc, out);
+}
+
+__global__ void k_dc_to_float(const double* __restrict__ dc, float* __restrict__ dcf, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dcf[i] = (float)dc[i];
+}
+
+void launch_dc_to_float(const double* dc, float* dcf, int64_t n, cudaStream_t stream) {
+  k_dc_to_float<<<(int)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, stream>>>(dc, dcf, n);
+}
+
+__global__ void k_failed_io(DevState* st, double* x, int to_double) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (to_double)
+      *x = (double)st->failed;
+    else
+      st->failed = (int)(*x + 0.5);
+  }
+}
+
+void launch_failed_io(DevState* st, double* x, int to_double, cudaStream_t stream) {
+  k_failed_io<<<1, 32, 0, stream>>>(st, x, to_double);
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -261,6 +317,7 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_cam_pass(Dev
   if (gw >= CS.nwarps) return;   // uniform per warp
   const int lane = threadIdx.x & 31;
   const int j = CS.warp_cam[gw];
+  if (P.sharded && !P.cluster_owned[P.cam_cluster[j]]) return;   // another process's cluster (uniform per warp)
   const int o = CS.slots[32 * (size_t)gw + lane];
   const real lam = (real)st->lambda_used;
   const bool corr = st->corrected != 0;
@@ -977,7 +1034,9 @@ void configure_kernels(int max_np) {
 #define INSTANTIATE(real)                                                                                  \
   template void launch_iter_begin<real>(DevState*, const Settings&, cudaStream_t);                        \
   template void launch_vp_reduce<real>(const DevProblem&, Scratch<real>, cudaStream_t);                   \
-  template void launch_vp_finalize<real>(const DevProblem&, Scratch<real>, DevState*, cudaStream_t);      \
+  template void launch_vp_finalize<real>(const DevProblem&, Scratch<real>, DevState*, cudaStream_t,       \
+                                         const double*);                                                   \
+  template void launch_pt_sums<real>(const DevProblem&, Scratch<real>, double*, cudaStream_t);              \
   template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamSlots, PairChunks, real*,     \
                                        DevState*, cudaStream_t);                                          \
   template void launch_point_update<real>(const DevProblem&, Scratch<real>, cudaStream_t);                \

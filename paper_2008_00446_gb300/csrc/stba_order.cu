@@ -224,12 +224,14 @@ __global__ void k_cam_place(ReorderArgs A, const int* __restrict__ flag, const i
 }
 
 // chunks of the camera graph whose two cameras share a cluster
+// a chunk is listed when its two cameras share a cluster that this process owns (every cluster unless sharded)
 __global__ void k_chunk_flag(int nchunks, const int4* __restrict__ chunks, const int* __restrict__ cam_cluster,
-                             int* __restrict__ flag) {
+                             const int* __restrict__ owned, int* __restrict__ flag) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nchunks) return;
   const int4 ch = chunks[c];
-  flag[c] = cam_cluster[ch.x] == cam_cluster[ch.y] ? 1 : 0;
+  const int k = cam_cluster[ch.x];
+  flag[c] = (k == cam_cluster[ch.y] && owned[k]) ? 1 : 0;
 }
 
 __global__ void k_chunk_list(int nchunks, const int* __restrict__ flag, const int* __restrict__ excl,
@@ -248,11 +250,12 @@ __global__ void __launch_bounds__(256) k_zero_vp(float4* __restrict__ p, const l
 
 }  // namespace
 
-void launch_list_chunks(const PairChunks& B, const int* cam_cluster, long long* nactive, cudaStream_t stream) {
+void launch_list_chunks(const PairChunks& B, const int* cam_cluster, const int* owned, long long* nactive,
+                        cudaStream_t stream) {
   const int n = B.nchunks;
   if (n <= 0) return;
   const int g = (n + 255) / 256, ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
-  k_chunk_flag<<<g, 256, 0, stream>>>(n, B.chunks, cam_cluster, B.flag);
+  k_chunk_flag<<<g, 256, 0, stream>>>(n, B.chunks, cam_cluster, owned, B.flag);
   k_scan_tiles<<<ntiles, SCAN_THREADS, 0, stream>>>(n, B.flag, B.tile_sum);
   k_scan_partials<<<1, 1024, 0, stream>>>(ntiles, B.tile_sum, nactive);
   k_scan_excl<<<ntiles, SCAN_THREADS, 0, stream>>>(n, B.flag, B.tile_sum, nactive, B.excl);

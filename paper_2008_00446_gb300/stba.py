@@ -31,7 +31,12 @@ EXPORTS = ["stba_default_options", "stba_create", "stba_set_clusters", "stba_lm_
            "stba_last_step", "stba_problem_info", "stba_get_cluster_system", "stba_set_timing",
            "stba_stage_times", "stba_destroy", "stba_status_string", "stba_last_error", "stba_cost_noalloc",
            "stba_record", "stba_adjoint", "stba_graph_create", "stba_graph_edges", "stba_graph_cluster",
-           "stba_graph_cluster_batch", "stba_graph_destroy", "stba_cluster_sgc", "stba_autotune", "stba_measure_peaks"]
+           "stba_graph_cluster_batch", "stba_graph_destroy", "stba_cluster_sgc", "stba_autotune", "stba_measure_peaks", "stba_set_shard", "stba_shard_owned"]
+
+
+# transport of the sharded iteration: (user, data, count, dtype 0 = FP64 / 1 = FP32, stream) -> 0 on success
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                 ctypes.c_void_p)
 
 
 class StbaOptions(ctypes.Structure):
@@ -111,6 +116,8 @@ def load(build_if_missing: bool = True):
         "stba_cluster_sgc": (I32, [P, I32, D, ctypes.c_uint64, I32, P, P]),
         "stba_autotune": (I32, [P, I32, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_float)]),
         "stba_measure_peaks": (I32, [P, I32, ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "stba_set_shard": (I32, [P, I32, I32, ALLREDUCE_FN, P, I32]),
+        "stba_shard_owned": (I32, [P, P, ctypes.POINTER(I32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -343,6 +350,48 @@ def stba_measure_peaks(reps=5, stream=None):
     if st != 0:
         raise StbaError(st, "stba_measure_peaks failed")
     return a.value, b.value
+
+
+def gloo_allreduce(group=None):
+    """A transport for stba_set_shard over torch.distributed (e.g. the gloo backend): sums a host NumPy array
+    over the ranks in place."""
+    import torch
+    import torch.distributed as dist
+
+    def allreduce(arr):
+        dist.all_reduce(torch.from_numpy(arr), group=group)
+    return allreduce
+
+
+def stba_set_shard(ctx: Context, rank: int, world: int, allreduce=None):
+    """Sharded iteration (one process per rank, each with its own context): this rank builds, factors and
+    solves only its clusters; `allreduce(arr)` sums a NumPy array in place over the ranks (the library stages
+    the exchanged values in host memory).  world = 1 returns to the single-process iteration."""
+    if world > 1:
+        if allreduce is None:
+            raise ValueError("a sharded iteration needs a transport (allreduce)")
+
+        def cb(user, data, count, dtype, stream):
+            try:
+                ct = ctypes.c_double if dtype == 0 else ctypes.c_float
+                allreduce(np.ctypeslib.as_array(ctypes.cast(data, ctypes.POINTER(ct)), shape=(int(count),)))
+                return 0
+            except Exception:   # reported to the library as a failed exchange
+                return 1
+        fn = ALLREDUCE_FN(cb)
+    else:
+        fn = ALLREDUCE_FN()
+    ctx._shard_cb = fn   # the library keeps the pointer; the Python object must outlive the context's use of it
+    ctx._check(load().stba_set_shard(ctx.handle, int(rank), int(world), fn, None, 1))
+
+
+def stba_shard_owned(ctx: Context) -> np.ndarray:
+    """Clusters of the current assignment owned by this rank (0 / 1 per cluster)."""
+    l = ctypes.c_int32()
+    ctx._check(load().stba_shard_owned(ctx.handle, None, ctypes.byref(l)))
+    out = np.zeros(l.value, np.int32)
+    ctx._check(load().stba_shard_owned(ctx.handle, ctypes.c_void_p(out.ctypes.data), ctypes.byref(l)))
+    return out
 
 
 def stba_autotune(ctx: Context, iterations=5):
