@@ -332,6 +332,9 @@ def main():
     ap.add_argument("--no-scenes", action="store_true",
                     help="skip the extra scene legs (20000 cameras, 5000-camera sequential, uniform tracks)")
     ap.add_argument("--no-peaks", action="store_true", help="skip the measured FP32 / TF32 peaks")
+    ap.add_argument("--factor", default=None,
+                    help="force one factorisation configuration (a name of stba.AUTOTUNE_CANDIDATES) instead of "
+                         "the autotuner's choice")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -351,8 +354,12 @@ def main():
     stream = torch.cuda.current_stream()
 
     s = scenes.make_config(args.config)
+    fkw = {}
+    if args.factor:
+        t_, u_, p_ = stba.AUTOTUNE_CANDIDATES[args.factor]
+        fkw = dict(factor_tile=t_, factor_update=u_, factor_panel=p_)
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
-                           precision=stba.STBA_MIXED, stream=stream)
+                           precision=stba.STBA_MIXED, stream=stream, **fkw)
     info0 = stba.stba_problem_info(ctx)
     # Algorithm 1 draws a new clustering every iteration (stochastic graph clustering, Sec. 4.4, with the
     # paper's beta = 10, Gamma = 100).  The camera graph is fixed, so the draws do not depend on the
@@ -371,7 +378,7 @@ def main():
                float(np.max(s.clusters) + 1)}
     stba.stba_set_clusters(ctx, seq[0])
     tuned, tile_ms = None, {}
-    if not args.no_autotune:   # the factorisation configuration, chosen by timing (outside the timed steps)
+    if not args.no_autotune and not args.factor:   # the factorisation configuration, chosen by timing
         tuned, tile_ms = stba.stba_autotune(ctx, 5)
     for i in range(max(args.warmup, 3)):
         stba.stba_set_clusters(ctx, seq[i])

@@ -94,13 +94,16 @@ typedef struct {
                                STBA_FACTOR_PANEL_STACKED = one kernel per step factors the stacked panel of
                                the diagonal tile and each tile below it (the diagonal tile redundantly per
                                tile row); STBA_FACTOR_PANEL_SPLIT = the diagonal tile is factored and
-                               inverted once per cluster, the tiles below are its products with the inverse
-                               (the FP32 factor of STBA_MIXED with tile 64 only; other settings return
-                               STBA_ERR_INVALID_ARG). */
+                               inverted once per cluster, the tiles below are its products with the inverse;
+                               STBA_FACTOR_PANEL_PERSISTENT = one launch factors every cluster, a thread-block
+                               cluster of 8 CTAs per camera cluster running all its tile steps with cluster
+                               barriers between them (SPLIT and PERSISTENT: the FP32 factor of STBA_MIXED
+                               with tile 64 only; other settings return STBA_ERR_INVALID_ARG). */
 } stba_options;
 
 enum { STBA_FACTOR_UPDATE_DEFAULT = 0, STBA_FACTOR_UPDATE_SIMT = 1, STBA_FACTOR_UPDATE_TENSOR = 2 };
-enum { STBA_FACTOR_PANEL_DEFAULT = 0, STBA_FACTOR_PANEL_STACKED = 1, STBA_FACTOR_PANEL_SPLIT = 2 };
+enum { STBA_FACTOR_PANEL_DEFAULT = 0, STBA_FACTOR_PANEL_STACKED = 1, STBA_FACTOR_PANEL_SPLIT = 2,
+       STBA_FACTOR_PANEL_PERSISTENT = 3 };
 
 typedef struct {
   double F_before;      /* F(x) at the start of the iteration */
@@ -275,7 +278,8 @@ stba_status stba_cluster_sgc(stba_ctx* ctx, int32_t gamma, double beta, uint64_t
  * (STBA_MIXED; FP64 has one):
  *   0 = tile 64, split panel, tensor-core trailing update     1 = tile 64, split panel, CUDA-core update
  *   2 = tile 64, stacked panel, CUDA-core update              3 = tile 32, stacked panel, CUDA-core update
- * *choice (optional) receives the index kept (-1 for the single FP64 configuration), ms[0..3] (optional) the
+ *   4 = tile 64, persistent (one launch of 8-CTA clusters)
+ * *choice (optional) receives the index kept (-1 for the single FP64 configuration), ms[0..4] (optional) the
  * time per iteration of each candidate (-1 when not tried).  Synchronises the context stream.  Errors:
  * STBA_ERR_STATE while iterations are being recorded (stba_record), STBA_ERR_INVALID_ARG for
  * iterations < 1. */

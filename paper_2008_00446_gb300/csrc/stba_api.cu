@@ -132,6 +132,7 @@ struct stba_ctx {
   int tile = 32;                        // factorisation tile (stba_autotune may change the FP32 one)
   int update_tc = 0;                    // trailing updates on the tensor cores (FP32 factor, tile 64)
   int split_panel = 0;                  // split panel: diagonal-tile factor + inverse, then the tiles below
+  int persistent = 0;                   // one persistent launch of 8-CTA clusters factors every cluster
   int panel_choice = STBA_FACTOR_PANEL_DEFAULT;   // option, or the autotuner's choice; DEFAULT decides per
                                                   // assignment (set_clusters_host)
   // sharded iteration (stba_set_shard): this process's rank among `shard_world`, the transport, the clusters
@@ -476,7 +477,8 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   // panel of the FP32 factor with tile 64: the split panel pays off once a tile step's tiles outnumber the SMs
   // (several waves of panel CTAs per step; each of them would factor its diagonal tile again), the stacked
   // panel when they fit in one wave (a single kernel per step on the critical path)
-  if (c->mixed && TF == 64 && c->panel_choice != STBA_FACTOR_PANEL_STACKED) {
+  c->persistent = c->mixed && TF == 64 && c->panel_choice == STBA_FACTOR_PANEL_PERSISTENT;
+  if (c->mixed && TF == 64 && c->panel_choice != STBA_FACTOR_PANEL_STACKED && !c->persistent) {
     int64_t tiles = 0;
     for (int k = 0; k < l; ++k) tiles += c->h_np[k] / TF;
     c->split_panel = c->panel_choice == STBA_FACTOR_PANEL_SPLIT || tiles > num_sms();
@@ -520,6 +522,9 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   c->h_panel_off[max_nt] = (int)panel.size();
   c->h_update_off[max_nt] = (int)update.size();
   std::vector<int2> res_items, diag_items;
+  std::vector<int> cluster_items;   // the clusters this process factors (persistent launch)
+  for (int k = 0; k < l; ++k)
+    if (c->h_owned[k]) cluster_items.push_back(k);
   for (int k = 0; k < l && !c->use_pcg; ++k)
     if (c->h_owned[k])
       for (int rb = 0; rb < (c->h_nk[k] + 31) / 32; ++rb) res_items.push_back(make_int2(k, rb));
@@ -561,7 +566,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
                  o_coff = seg(4 * ((size_t)l + 1)), o_np = seg(4 * (size_t)l), o_nk = seg(4 * (size_t)l),
                  o_soff = seg(8 * (size_t)l), o_voff = seg(8 * (size_t)l), o_panel = seg(8 * panel.size()),
                  o_update = seg(8 * update.size()), o_res = seg(8 * res_items.size()),
-                 o_diag = seg(8 * diag_items.size());
+                 o_diag = seg(8 * diag_items.size()), o_citems = seg(4 * cluster_items.size());
     const int sb = c->stage_cur;
     c->stage_cur = 1 - sb;
     if (c->stage_bytes[sb] < bytes) {
@@ -596,6 +601,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     pack(o_update, update.data(), 8 * update.size());
     pack(o_res, res_items.data(), 8 * res_items.size());
     pack(o_diag, diag_items.data(), 8 * diag_items.size());
+    pack(o_citems, cluster_items.data(), 4 * cluster_items.size());
     char* d = nullptr;
     if ((s = ensure(c, c->g_blob, &d, bytes)) != STBA_OK) return s;
     CK(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c->stream));
@@ -615,7 +621,8 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
                         c->h_panel_off.data(),
                         c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
                         c->ev_panel.data(), c->ev_update.data(), TF, c->update_tc, c->split_panel,
-                        c->h_diag_count.data()};
+                        c->h_diag_count.data(), c->persistent, (const int*)(d + o_citems),
+                        (int)cluster_items.size()};
   }
   {
     int least = 0, greatest = 0;
@@ -1124,15 +1131,17 @@ stba_status stba_cluster_sgc(stba_ctx* c, int32_t gamma, double beta, uint64_t s
 stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* choice, float* ms) {
   if (!c || iterations < 1) return STBA_ERR_INVALID_ARG;
   if (c->tape_cap > 0) return fail(c, STBA_ERR_STATE, "stba_autotune is not allowed while iterations are recorded");
-  constexpr int NCAND = 4;
-  const int cand_tile[NCAND] = {64, 64, 64, 32}, cand_tc[NCAND] = {1, 0, 0, 0}, cand_split[NCAND] = {1, 1, 0, 0};
+  constexpr int NCAND = 5;
+  const int cand_tile[NCAND] = {64, 64, 64, 32, 64}, cand_tc[NCAND] = {1, 0, 0, 0, 0};
+  const int cand_panel[NCAND] = {STBA_FACTOR_PANEL_SPLIT, STBA_FACTOR_PANEL_SPLIT, STBA_FACTOR_PANEL_STACKED,
+                                 STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_PERSISTENT};
   if (ms)
     for (int t = 0; t < NCAND; ++t) ms[t] = -1.0f;
   auto report = [&]() {
     if (!choice) return;
     *choice = -1;
     for (int t = 0; t < NCAND; ++t)
-      if (cand_tile[t] == c->tile && cand_tc[t] == c->update_tc && cand_split[t] == c->split_panel) *choice = t;
+      if (cand_tile[t] == c->tile && cand_tc[t] == c->update_tc && cand_panel[t] == c->panel_choice) *choice = t;
   };
   if (!c->mixed || c->use_pcg || c->use_spcg) {   // one candidate (or no factorisation at all)
     report();
@@ -1174,7 +1183,7 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* choice, floa
   for (int t = 0; t < NCAND && ok && s == STBA_OK; ++t) {
     c->tile = cand_tile[t];
     c->update_tc = cand_tc[t];
-    c->panel_choice = cand_split[t] ? STBA_FACTOR_PANEL_SPLIT : STBA_FACTOR_PANEL_STACKED;
+    c->panel_choice = cand_panel[t];
     if ((s = set_clusters_host(c, cl)) != STBA_OK) break;
     ok = restore();
     if (ok && (s = run_iteration(c)) != STBA_OK) break;   // warm-up: capture, first launch
@@ -1196,7 +1205,7 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* choice, floa
   if (s == STBA_OK && ok && best >= 0) {
     c->tile = cand_tile[best];
     c->update_tc = cand_tc[best];
-    c->panel_choice = cand_split[best] ? STBA_FACTOR_PANEL_SPLIT : STBA_FACTOR_PANEL_STACKED;
+    c->panel_choice = cand_panel[best];
     s = set_clusters_host(c, cl);
     if (s == STBA_OK) ok = restore() && cudaStreamSynchronize(c->stream) == cudaSuccess;
   }
@@ -1302,8 +1311,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       (c->opt.factor_update == STBA_FACTOR_UPDATE_TENSOR &&
        !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))) ||
       (c->opt.factor_panel != STBA_FACTOR_PANEL_DEFAULT && c->opt.factor_panel != STBA_FACTOR_PANEL_STACKED &&
-       c->opt.factor_panel != STBA_FACTOR_PANEL_SPLIT) ||
-      (c->opt.factor_panel == STBA_FACTOR_PANEL_SPLIT &&
+       c->opt.factor_panel != STBA_FACTOR_PANEL_SPLIT && c->opt.factor_panel != STBA_FACTOR_PANEL_PERSISTENT) ||
+      ((c->opt.factor_panel == STBA_FACTOR_PANEL_SPLIT || c->opt.factor_panel == STBA_FACTOR_PANEL_PERSISTENT) &&
        !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
   c->m = m;

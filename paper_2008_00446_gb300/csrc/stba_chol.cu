@@ -434,6 +434,82 @@ __global__ void __launch_bounds__(256) k_diag_inverse(const F* Ldiag, F* Dinv, D
 // update of the diagonal tile), LL^T of the tile in blocks of 8 columns (as the panel, 64 rows), and its
 // inverse Y = L_kt,kt^-1 (tile_inverse), written to Dinv (row-major) and its transpose (for the solves and
 // for k_chol_trsm).  Pivot rules as in chol8.
+// LL^T of a T x T diagonal tile Ad (lower part; upper part zero) in shared memory, in place, 256 threads, in
+// blocks of 8 columns: per block one thread factors the 8 x 8 diagonal block (chol8), the rows below are
+// solved against it, and the columns to its right get the rank-8 update, warp 0 updating and factoring the
+// next diagonal block meanwhile (one block of look-ahead).  row0: global row of the tile's first row (pivot
+// rules of chol8 for padding rows); fail, boosted as in chol8.  Ends synchronised.
+template <typename F, int T>
+__device__ __forceinline__ void factor_diag_tile(F (*Ad)[T + 1], F (*rinv2)[8], int row0, int nk, int* fail,
+                                                 int* boosted) {
+  constexpr int R = T / 16, LDA = T + 1, NB = T / 8;
+  const int tid = threadIdx.x;
+  if (tid == 0) chol8<F, LDA>(Ad, 0, row0, nk, rinv2[0], fail, boosted);
+  __syncthreads();
+  for (int b = 0; b < NB; ++b) {
+    const int b0 = 8 * b;
+    const F* rinv = rinv2[b & 1];
+    const int rows_d = T - b0 - 8;
+    if (tid < rows_d) {
+      F* row = &Ad[b0 + 8 + tid][0];
+      F o8[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        F s = row[b0 + c];
+#pragma unroll
+        for (int t = 0; t < c; ++t) s -= o8[t] * Ad[b0 + c][b0 + t];
+        o8[c] = s * rinv[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) row[b0 + c] = o8[c];
+    }
+    __syncthreads();
+    if (b + 1 == NB) break;
+    const int n0 = b0 + 8;
+    if (tid < 32) {
+      for (int e = tid; e < 36; e += 32) {
+        int rr = 0;
+        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
+        const int cc = e - rr * (rr + 1) / 2;
+        F s = F(0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) s += Ad[n0 + rr][b0 + t] * Ad[n0 + cc][b0 + t];
+        Ad[n0 + rr][n0 + cc] -= s;
+      }
+      __syncwarp();
+      if (tid == 0) chol8<F, LDA>(Ad, n0, row0, nk, rinv2[(b + 1) & 1], fail, boosted);
+    } else {
+      for (int cell = tid - 32; cell < 256; cell += 224) {
+        const int ci = cell & 15, cj = cell >> 4;
+        const int c0 = cj * R, r0 = ci * R;
+        if (c0 + R <= n0 || cj > ci || r0 + R <= n0 + 8) continue;
+        F lc[R][8];
+#pragma unroll
+        for (int cc = 0; cc < R; ++cc)
+#pragma unroll
+          for (int t = 0; t < 8; ++t) lc[cc][t] = Ad[c0 + cc][b0 + t];
+#pragma unroll
+        for (int a = 0; a < R; ++a) {
+          F lr[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) lr[t] = Ad[r0 + a][b0 + t];
+#pragma unroll
+          for (int cc = 0; cc < R; ++cc) {
+            const int r = r0 + a, c = c0 + cc;
+            if (c <= r && c >= n0 && r >= n0 + 8) {
+              F s = F(0);
+#pragma unroll
+              for (int t = 0; t < 8; ++t) s += lr[t] * lc[cc][t];
+              Ad[r][c] -= s;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 template <typename F, int T>
 struct DiagLayout {
   static constexpr int LDA = T + 1;
@@ -445,7 +521,7 @@ template <typename F, int T>
 __global__ void __launch_bounds__(256) k_chol_diag(const F* L, F* Dinv, DevProblem P, const int2* items, int kt,
                                                    int* fail_flags, int* boosted, int64_t v_total) {
   using DL = DiagLayout<F, T>;
-  constexpr int R = T / 16, LDA = DL::LDA, LDV = DL::LDV, NB = T / 8;
+  constexpr int R = T / 16, LDA = DL::LDA, LDV = DL::LDV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   F(*Ad)[LDA] = reinterpret_cast<F(*)[LDA]>(smem_raw);
   F(*Y)[LDA] = Ad + T;
@@ -494,73 +570,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(const F* L, F* Dinv, DevProbl
       }
     __syncthreads();
   }
-  // blocked LL^T of the tile: per block of 8 columns, one thread factors the 8 x 8 diagonal block, the rows
-  // below are solved against it, and the columns to its right get the rank-8 update (warp 0 updates and
-  // factors the next diagonal block meanwhile: one block of look-ahead)
-  if (tid == 0) chol8<F, LDA>(Ad, 0, kt * T, nk, rinv2[0], fail_flags + k, boosted);
-  __syncthreads();
-  for (int b = 0; b < NB; ++b) {
-    const int b0 = 8 * b;
-    const F* rinv = rinv2[b & 1];
-    const int rows_d = T - b0 - 8;
-    if (tid < rows_d) {
-      F* row = &Ad[b0 + 8 + tid][0];
-      F o8[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        F s = row[b0 + c];
-#pragma unroll
-        for (int t = 0; t < c; ++t) s -= o8[t] * Ad[b0 + c][b0 + t];
-        o8[c] = s * rinv[c];
-      }
-#pragma unroll
-      for (int c = 0; c < 8; ++c) row[b0 + c] = o8[c];
-    }
-    __syncthreads();
-    if (b + 1 == NB) break;
-    const int n0 = b0 + 8;
-    if (tid < 32) {
-      for (int e = tid; e < 36; e += 32) {
-        int rr = 0;
-        while ((rr + 1) * (rr + 2) / 2 <= e) ++rr;
-        const int cc = e - rr * (rr + 1) / 2;
-        F s = F(0);
-#pragma unroll
-        for (int t = 0; t < 8; ++t) s += Ad[n0 + rr][b0 + t] * Ad[n0 + cc][b0 + t];
-        Ad[n0 + rr][n0 + cc] -= s;
-      }
-      __syncwarp();
-      if (tid == 0) chol8<F, LDA>(Ad, n0, kt * T, nk, rinv2[(b + 1) & 1], fail_flags + k, boosted);
-    } else {
-      for (int cell = tid - 32; cell < 256; cell += 224) {
-        const int ci = cell & 15, cj = cell >> 4;
-        const int c0 = cj * R, r0 = ci * R;
-        if (c0 + R <= n0 || cj > ci || r0 + R <= n0 + 8) continue;
-        F lc[R][8];
-#pragma unroll
-        for (int cc = 0; cc < R; ++cc)
-#pragma unroll
-          for (int t = 0; t < 8; ++t) lc[cc][t] = Ad[c0 + cc][b0 + t];
-#pragma unroll
-        for (int a = 0; a < R; ++a) {
-          F lr[8];
-#pragma unroll
-          for (int t = 0; t < 8; ++t) lr[t] = Ad[r0 + a][b0 + t];
-#pragma unroll
-          for (int cc = 0; cc < R; ++cc) {
-            const int r = r0 + a, c = c0 + cc;
-            if (c <= r && c >= n0 && r >= n0 + 8) {
-              F s = F(0);
-#pragma unroll
-              for (int t = 0; t < 8; ++t) s += lr[t] * lc[cc][t];
-              Ad[r][c] -= s;
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-  }
+  factor_diag_tile<F, T>(Ad, rinv2, kt * T, nk, fail_flags + k, boosted);
   tile_inverse<F, T>(Ad, Y, Z);
   F* Di = Dinv + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
   F* DiT = Di + v_total * T;
@@ -811,6 +821,213 @@ __global__ void __launch_bounds__(TCU_THREADS, 2) k_chol_update_tc(float* L, Dev
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
+
+// ------------------------------------------------------------------------------------------------------
+// Persistent factorisation (FP32 factor, T = 64): one thread-block cluster of FCS CTAs per camera cluster
+// runs every tile step of that cluster in one launch.  Tile (i, j) of the lower triangle belongs to CTA
+// (i (i + 1) / 2 + j) mod FCS for the whole factorisation (round robin over the tiles, so every step's work
+// spreads over the CTAs).  Step kt:
+//   1. the owner of (kt, kt) factors the tile (factor_diag_tile; every update of it has been applied by the
+//      same CTA) and inverts it (tile_inverse), writing Y = L_kt,kt^-1 and Y^T to Dinv for the solves;
+//   2. cluster barrier; every CTA forms its tiles below the diagonal, L_i,kt = A_i,kt Y^T;
+//   3. cluster barrier; every CTA applies A_i,j -= L_i,kt L_j,kt^T to its tiles kt < j <= i.
+// Between CTAs only the finished column kt (after barrier 2) and Y (after barrier 1) travel, through L2: they
+// are read with L1-bypassing loads, after a device-scope fence and the cluster barrier.  Every CTA runs the
+// same number of barriers (2 per step).  Replaces the per-step panel / update launches and the separate
+// inverses of the diagonal tiles.
+constexpr int FCS = 8;
+
+template <int T>
+struct ClusterFactorLayout {
+  static constexpr int LDA = T + 1;             // diagonal phase: Ad, Y [T][LDA], Z [T * T / 2]
+  static constexpr int LD = T + 4;              // product phases: two [T][LD] tiles (16-byte rows)
+  static constexpr size_t diag_bytes = sizeof(float) * (2 * (size_t)T * LDA + (size_t)T * T / 2);
+  static constexpr size_t prod_bytes = sizeof(float) * 2 * (size_t)T * LD;
+  static constexpr size_t bytes = diag_bytes > prod_bytes ? diag_bytes : prod_bytes;
+};
+
+__device__ __forceinline__ int factor_tile_owner(int i, int j) { return (i * (i + 1) / 2 + j) % FCS; }
+
+// The 16-byte pieces of a T x T tile that thread t loads (T * T / 4 / 256 of them): piece u is row
+// (t + 256 u) % T, columns 4 ((t + 256 u) / T) .. + 3.  Loads first (all in flight at once), stores after.
+template <int T>
+struct TilePieces {
+  static constexpr int N = T * T / 4 / 256;
+  float4 v[N];
+};
+template <int T, bool CG>
+__device__ __forceinline__ void tile_pieces_load(TilePieces<T>& t, const float* src, size_t ld) {
+#pragma unroll
+  for (int u = 0; u < TilePieces<T>::N; ++u) {
+    const int q = threadIdx.x + 256 * u, r = q % T, c4 = 4 * (q / T);
+    const float4* p = reinterpret_cast<const float4*>(src + (size_t)r * ld + c4);
+    t.v[u] = CG ? __ldcg(p) : *p;
+  }
+}
+// dst[c][r] = tile[r][c] (consecutive threads write consecutive r: consecutive banks)
+template <int T, int LD>
+__device__ __forceinline__ void tile_pieces_store_transposed(float (*dst)[LD], const TilePieces<T>& t) {
+#pragma unroll
+  for (int u = 0; u < TilePieces<T>::N; ++u) {
+    const int q = threadIdx.x + 256 * u, r = q % T, c4 = 4 * (q / T);
+    dst[c4][r] = t.v[u].x;
+    dst[c4 + 1][r] = t.v[u].y;
+    dst[c4 + 2][r] = t.v[u].z;
+    dst[c4 + 3][r] = t.v[u].w;
+  }
+}
+// the R x R block (rows tr R + a, columns tc R ..) that the thread updates, as R 16-byte pieces
+template <int T>
+__device__ __forceinline__ void block_load(float4 (&b)[T / 16], const float* dst, size_t ld) {
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < T / 16; ++a) b[a] = *reinterpret_cast<const float4*>(dst + (size_t)(tr * (T / 16) + a) * ld + tc * (T / 16));
+}
+
+// acc[a][b] = sum_m X[m][tr R + a] Y[m][tc R + b] over the T rows m of two transposed tiles
+template <int T, int LD>
+__device__ __forceinline__ void tile_product(const float (*X)[LD], const float (*Y)[LD], float (&acc)[T / 16][T / 16]) {
+  constexpr int R = T / 16;
+  const int tr = threadIdx.x >> 4, tc = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < R; ++a)
+#pragma unroll
+    for (int b = 0; b < R; ++b) acc[a][b] = 0.f;
+#pragma unroll 4
+  for (int m = 0; m < T; ++m) {
+    float xv[R], yv[R];
+    load_vec<float, R>(&X[m][tr * R], xv);
+    load_vec<float, R>(&Y[m][tc * R], yv);
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+      for (int b = 0; b < R; ++b) acc[a][b] += xv[a] * yv[b];
+  }
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) k_chol_cluster(float* L, float* Dinv, DevProblem P, const int* cluster_items,
+                                                      int* fail_flags, int* boosted, int64_t v_total) {
+  namespace cg = cooperative_groups;
+  using CL = ClusterFactorLayout<T>;
+  constexpr int R = T / 16, LDA = CL::LDA, LD = CL::LD;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float(*Ad)[LDA] = reinterpret_cast<float(*)[LDA]>(smem_raw);   // diagonal phase
+  float(*Y)[LDA] = Ad + T;
+  float* Z = reinterpret_cast<float*>(Y + T);
+  float(*X1)[LD] = reinterpret_cast<float(*)[LD]>(smem_raw);   // product phases (alias the diagonal phase)
+  float(*X2)[LD] = X1 + T;
+  __shared__ float rinv2[2][8];
+  const int rank = (int)cluster.block_rank();
+  const int k = cluster_items[blockIdx.x / FCS];
+  const int np = P.cluster_np[k], nk = P.cluster_n[k], nt = np / T;
+  float* A = L + P.S_off[k];
+  float* Di = Dinv + (size_t)P.v_off[k] * T;
+  float* DiT = Di + v_total * T;
+  const int tid = threadIdx.x, tr = tid >> 4, tc = tid & 15;
+  auto tile = [&](int i, int j) { return A + (size_t)(i * T) * np + j * T; };
+  // the diagonal tile kt and its inverse, by its owner (every update of the tile is this CTA's own)
+  auto diagonal = [&](int kt) {
+    const float* src = tile(kt, kt);
+    for (int idx = tid; idx < T * T; idx += 256) {
+      const int r = idx / T, c = idx - (idx / T) * T;
+      Ad[r][c] = c <= r ? src[(size_t)r * np + c] : 0.f;
+      Y[r][c] = 0.f;
+    }
+    __syncthreads();
+    factor_diag_tile<float, T>(Ad, rinv2, kt * T, nk, fail_flags + k, boosted);
+    tile_inverse<float, T>(Ad, Y, Z);
+    float* d = Di + (size_t)kt * T * T;
+    float* dT = DiT + (size_t)kt * T * T;
+    for (int idx = tid; idx < T * T; idx += 256) {
+      const int r = idx / T, c = idx - (idx / T) * T;
+      d[idx] = Y[r][c];
+      dT[idx] = Y[c][r];
+    }
+    __syncthreads();
+  };
+  if (factor_tile_owner(0, 0) == rank) diagonal(0);
+  for (int kt = 0; kt < nt; ++kt) {
+    // 1. the diagonal tile kt is factored: at the start (kt = 0) or, one step ahead, by its owner during the
+    //    trailing update of step kt - 1 (look-ahead)
+    __threadfence();
+    cluster.sync();
+    // 2. the tiles below the diagonal: L_i,kt = A_i,kt Y^T
+    bool have_yt = false;
+    for (int i = kt + 1; i < nt; ++i) {
+      if (factor_tile_owner(i, kt) != rank) continue;
+      TilePieces<T> a_ik, yt;
+      tile_pieces_load<T, false>(a_ik, tile(i, kt), np);   // this CTA's own tile
+      if (!have_yt) tile_pieces_load<T, true>(yt, DiT + (size_t)kt * T * T, T);   // Y^T, row-major in DiT
+      tile_pieces_store_transposed<T, LD>(X1, a_ik);
+      if (!have_yt) {   // X2[m][c] = (Y^T)[m][c]: the pieces go in untransposed
+#pragma unroll
+        for (int u = 0; u < TilePieces<T>::N; ++u) {
+          const int q = tid + 256 * u, r = q % T, c4 = 4 * (q / T);
+          *reinterpret_cast<float4*>(&X2[r][c4]) = yt.v[u];
+        }
+        have_yt = true;
+      }
+      __syncthreads();
+      float acc[R][R];
+      tile_product<T, LD>(X1, X2, acc);
+      float* dst = tile(i, kt);
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+        *reinterpret_cast<float4*>(dst + (size_t)(tr * R + a) * np + tc * R) =
+            make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+      __syncthreads();   // X1 is reloaded next
+    }
+    __threadfence();
+    cluster.sync();
+    // 3. trailing update of this CTA's tiles kt < j <= i; the owner of the next diagonal tile updates it first
+    //    and factors it before its other tiles (look-ahead)
+    if (kt + 1 < nt && factor_tile_owner(kt + 1, kt + 1) == rank) {
+      TilePieces<T> l1;
+      float4 old[R];
+      float* dst = tile(kt + 1, kt + 1);
+      tile_pieces_load<T, true>(l1, tile(kt + 1, kt), np);
+      block_load<T>(old, dst, np);
+      tile_pieces_store_transposed<T, LD>(X1, l1);
+      __syncthreads();
+      float acc[R][R];
+      tile_product<T, LD>(X1, X1, acc);
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+        *reinterpret_cast<float4*>(dst + (size_t)(tr * R + a) * np + tc * R) =
+            make_float4(old[a].x - acc[a][0], old[a].y - acc[a][1], old[a].z - acc[a][2], old[a].w - acc[a][3]);
+      __syncthreads();
+      diagonal(kt + 1);
+    }
+    for (int i = kt + 1; i < nt; ++i) {
+      bool have_li = false;
+      for (int j = kt + 1; j <= i; ++j) {
+        if (factor_tile_owner(i, j) != rank || (i == kt + 1 && j == kt + 1)) continue;
+        TilePieces<T> li, lj;
+        float4 old[R];
+        float* dst = tile(i, j);
+        if (!have_li) tile_pieces_load<T, true>(li, tile(i, kt), np);
+        tile_pieces_load<T, true>(lj, tile(j, kt), np);
+        block_load<T>(old, dst, np);
+        if (!have_li) {
+          tile_pieces_store_transposed<T, LD>(X1, li);
+          have_li = true;
+        }
+        tile_pieces_store_transposed<T, LD>(X2, lj);
+        __syncthreads();
+        float acc[R][R];
+        tile_product<T, LD>(X1, X2, acc);
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+          *reinterpret_cast<float4*>(dst + (size_t)(tr * R + a) * np + tc * R) =
+              make_float4(old[a].x - acc[a][0], old[a].y - acc[a][1], old[a].z - acc[a][2], old[a].w - acc[a][3]);
+        __syncthreads();   // X2 (and X1 at the next i) are reloaded
+      }
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1165,6 +1382,27 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
   k_scaled_copy<Sreal, F><<<g2, 256, 0, stream>>>(P, S, fb.scale, L);
   // panels on `stream`; the trailing updates (all tiles but the next column, which the next panel updates
   // itself) on the side stream, so that update kt overlaps panel kt + 1.  Panel kt + 2 waits for update kt.
+  if constexpr (sizeof(F) == 4 && T == 64) {
+    if (plan.persistent) {   // every tile step of every cluster in one launch of 8-CTA thread-block clusters
+      if (plan.n_cluster_items > 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(plan.n_cluster_items * FCS);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = ClusterFactorLayout<T>::bytes;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = FCS;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaLaunchKernelEx(&cfg, k_chol_cluster<T>, reinterpret_cast<float*>(L), reinterpret_cast<float*>(Dinv), P,
+                           plan.cluster_items, fb.fail_flags, fb.boosted, fb.v_total);
+      }
+      return;
+    }
+  }
   cudaStream_t side = plan.side_stream;
   cudaEventRecord(plan.ev_fork, stream);
   cudaStreamWaitEvent(side, plan.ev_fork, 0);

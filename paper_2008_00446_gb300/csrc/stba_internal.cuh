@@ -246,6 +246,9 @@ struct CholPlan {
                                   // diagonal tiles (cluster, kt) first, h_diag_count[kt] of them, then the
                                   // tiles below them
   const int* h_diag_count;        // host [nsteps]
+  int persistent;                 // 1: one persistent launch factors every cluster (FP32 factor, T = 64)
+  const int* cluster_items;       // [n_cluster_items] the clusters this process factors
+  int n_cluster_items;
 };
 struct FactorBuffers {
   void* L;          // factor (F = float or double), same layout as S'

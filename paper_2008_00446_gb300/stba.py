@@ -18,10 +18,10 @@ _LIB = None
 STBA_FP64, STBA_MIXED = 0, 1
 STBA_SOLVER_CLUSTERS, STBA_SOLVER_PCG_FULL, STBA_SOLVER_PCG_CLUSTERS = 0, 1, 2
 STBA_FACTOR_UPDATE_DEFAULT, STBA_FACTOR_UPDATE_SIMT, STBA_FACTOR_UPDATE_TENSOR = 0, 1, 2
-STBA_FACTOR_PANEL_DEFAULT, STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_SPLIT = 0, 1, 2
+STBA_FACTOR_PANEL_DEFAULT, STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_SPLIT, STBA_FACTOR_PANEL_PERSISTENT = 0, 1, 2, 3
 # stba_autotune's candidates: name -> (factor_tile, factor_update, factor_panel)
 AUTOTUNE_CANDIDATES = {"64_split_tensor": (64, 2, 2), "64_split_simt": (64, 1, 2), "64_stacked_simt": (64, 1, 1),
-                       "32_stacked_simt": (32, 1, 1)}
+                       "32_stacked_simt": (32, 1, 1), "64_persistent": (64, 1, 3)}
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not SPD",
           5: "non-finite value", 6: "timeout", 7: "invalid state"}
 

@@ -76,9 +76,10 @@ def test_first_step_fp64_elementwise(name, lam):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-@pytest.mark.parametrize("panel", [stba.STBA_FACTOR_PANEL_STACKED, stba.STBA_FACTOR_PANEL_SPLIT])
+@pytest.mark.parametrize("panel", [stba.STBA_FACTOR_PANEL_STACKED, stba.STBA_FACTOR_PANEL_SPLIT,
+                                   stba.STBA_FACTOR_PANEL_PERSISTENT])
 def test_mixed_first_step_elementwise(name, panel):
-    # both panels of the FP32 factor (the default picks one by the number of tiles per step)
+    # every panel of the FP32 factor (the default picks one by the number of tiles per step)
     s = scene(name)
     _, _, _, _, rec = oracle_first(s, 1e-4)
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,

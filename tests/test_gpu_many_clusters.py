@@ -23,14 +23,15 @@ def scene():
                                         seed=77, name="many")
 
 
-@pytest.mark.parametrize("precision,tol,tile", [(stba.STBA_FP64, 1e-6, 0), (stba.STBA_MIXED, 1e-5, 0),
-                                                (stba.STBA_MIXED, 1e-5, 32)])
-def test_every_cluster_step_solves_its_system(precision, tol, tile):
+@pytest.mark.parametrize("precision,tol,tile,panel", [(stba.STBA_FP64, 1e-6, 0, 0), (stba.STBA_MIXED, 1e-5, 0, 0),
+                                                      (stba.STBA_MIXED, 1e-5, 32, 0),
+                                                      (stba.STBA_MIXED, 1e-5, 64, stba.STBA_FACTOR_PANEL_PERSISTENT)])
+def test_every_cluster_step_solves_its_system(precision, tol, tile, panel):
     s = scene()
     l = int(s.clusters.max()) + 1
     assert l >= 40
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=precision,
-                           factor_tile=tile)
+                           factor_tile=tile, factor_panel=panel)
     info = stba.stba_lm_iteration(ctx)
     assert info["failed_clusters"] == 0
     dc, _ = stba.stba_last_step(ctx)
