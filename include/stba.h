@@ -99,6 +99,10 @@ typedef struct {
                                cluster of 8 CTAs per camera cluster running all its tile steps with cluster
                                barriers between them (SPLIT and PERSISTENT: the FP32 factor of STBA_MIXED
                                with tile 64 only; other settings return STBA_ERR_INVALID_ARG). */
+  int32_t solve_cluster;    /* CTAs per thread-block cluster of each camera cluster's triangular solves
+                               (2, 4 or 8; 0 = default: 8 while the clusters' solve CTAs fit in two waves on
+                               the SMs, else 4): more CTAs share a tile step's products, fewer make its
+                               cluster barrier and distributed-shared-memory exchange cheaper. */
 } stba_options;
 
 enum { STBA_FACTOR_UPDATE_DEFAULT = 0, STBA_FACTOR_UPDATE_SIMT = 1, STBA_FACTOR_UPDATE_TENSOR = 2 };

@@ -133,6 +133,7 @@ struct stba_ctx {
   int update_tc = 0;                    // trailing updates on the tensor cores (FP32 factor, tile 64)
   int split_panel = 0;                  // split panel: diagonal-tile factor + inverse, then the tiles below
   int persistent = 0;                   // one persistent launch of 8-CTA clusters factors every cluster
+  int solve_cs = 8;                     // CTAs per thread-block cluster of the cluster solves
   int panel_choice = STBA_FACTOR_PANEL_DEFAULT;   // option, or the autotuner's choice; DEFAULT decides per
                                                   // assignment (set_clusters_host)
   // sharded iteration (stba_set_shard): this process's rank among `shard_world`, the transport, the clusters
@@ -478,6 +479,9 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
   // (several waves of panel CTAs per step; each of them would factor its diagonal tile again), the stacked
   // panel when they fit in one wave (a single kernel per step on the critical path)
   c->persistent = c->mixed && TF == 64 && c->panel_choice == STBA_FACTOR_PANEL_PERSISTENT;
+  // CTAs per cluster solve: 8 while the solves' CTAs fit in about two waves (more CTAs share each tile step's
+  // products), 4 beyond (cheaper barriers and exchanges once the solves queue for SMs anyway)
+  c->solve_cs = c->opt.solve_cluster ? c->opt.solve_cluster : ((int64_t)l * 8 <= 2 * (int64_t)num_sms() ? 8 : 4);
   if (c->mixed && TF == 64 && c->panel_choice != STBA_FACTOR_PANEL_STACKED && !c->persistent) {
     int64_t tiles = 0;
     for (int k = 0; k < l; ++k) tiles += c->h_np[k] / TF;
@@ -622,7 +626,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
                         c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
                         c->ev_panel.data(), c->ev_update.data(), TF, c->update_tc, c->split_panel,
                         c->h_diag_count.data(), c->persistent, (const int*)(d + o_citems),
-                        (int)cluster_items.size()};
+                        (int)cluster_items.size(), c->solve_cs};
   }
   {
     int least = 0, greatest = 0;
@@ -1020,6 +1024,7 @@ void stba_default_options(stba_options* o) {
   o->pcg_tol = 1e-6;
   o->factor_update = STBA_FACTOR_UPDATE_DEFAULT;
   o->factor_panel = STBA_FACTOR_PANEL_DEFAULT;
+  o->solve_cluster = 0;
 }
 
 const char* stba_status_string(stba_status s) {
@@ -1312,6 +1317,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
        !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))) ||
       (c->opt.factor_panel != STBA_FACTOR_PANEL_DEFAULT && c->opt.factor_panel != STBA_FACTOR_PANEL_STACKED &&
        c->opt.factor_panel != STBA_FACTOR_PANEL_SPLIT && c->opt.factor_panel != STBA_FACTOR_PANEL_PERSISTENT) ||
+      !(c->opt.solve_cluster == 0 || c->opt.solve_cluster == 2 || c->opt.solve_cluster == 4 ||
+        c->opt.solve_cluster == 8) ||
       ((c->opt.factor_panel == STBA_FACTOR_PANEL_SPLIT || c->opt.factor_panel == STBA_FACTOR_PANEL_PERSISTENT) &&
        !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));

@@ -1048,7 +1048,7 @@ __device__ F warp_sum(F v) {
 // diagonal inverses are copied into shared memory (cp.async) while step it computes, `nst` stages deep:
 // three (two steps ahead) when the launch is one wave of CTAs, two otherwise, where the smaller shared
 // memory lets two CTAs share an SM and the waves halve.
-constexpr int SOLVE_CS = 8;
+constexpr int SOLVE_CS = 8;   // default CTAs per camera cluster (the option solve_cluster picks 2, 4 or 8)
 constexpr int SOLVE_PF = 2;
 
 template <typename F, int T>
@@ -1088,7 +1088,7 @@ __device__ __forceinline__ void smem_matvec(const F* M, const F* v, F* out) {
   if (part == 0) out[r] = s;
 }
 
-template <typename F, int T, typename Rreal>
+template <typename F, int T, typename Rreal, int CS>
 __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, const F* Dinv, const double* scale,
                                                    const Rreal* rhs, double* x, int accumulate, int64_t v_total,
                                                    int nst) {
@@ -1103,7 +1103,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
   __shared__ F t[T];
   __shared__ F pcol[PARTS][T];
   const int rank = (int)cluster.block_rank();
-  const int k = blockIdx.x / SOLVE_CS;
+  const int k = blockIdx.x / CS;
   if (P.sharded && !P.cluster_owned[k]) return;   // the whole thread-block cluster leaves, before any barrier
   const int np = P.cluster_np[k];
   const F* A = L + P.S_off[k];
@@ -1122,10 +1122,10 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
       const int it = fwd ? s : 2 * nt - 1 - s;
       int m = 0;
       if (fwd) {
-        for (int j = rank; j < it && m < SOLVE_PF; j += SOLVE_CS, ++m)
+        for (int j = rank; j < it && m < SOLVE_PF; j += CS, ++m)
           prefetch_tile<F, T>(tile_buf(s % nst, m), A + (size_t)(it * T) * np + j * T, np);
       } else {
-        for (int j = it + 1 + rank; j < nt && m < SOLVE_PF; j += SOLVE_CS, ++m)
+        for (int j = it + 1 + rank; j < nt && m < SOLVE_PF; j += CS, ++m)
           prefetch_tile<F, T>(tile_buf(s % nst, m), A + (size_t)(j * T) * np + it * T, np);
       }
       prefetch_tile<F, T>(tile_buf(s % nst, SOLVE_PF), (fwd ? Di : DiT) + (size_t)it * T * T, T);
@@ -1151,7 +1151,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
       const int r = tid / PARTS, part = tid - (tid / PARTS) * PARTS;
       F acc = F(0);
       int m = 0;
-      for (int j = rank; j < it; j += SOLVE_CS, ++m) {
+      for (int j = rank; j < it; j += CS, ++m) {
         const F* yj = y + j * T + part * LEN;
         if (m < SOLVE_PF) {
           const F* row = tile_buf(st, m) + (size_t)r * LDT + part * LEN;
@@ -1171,7 +1171,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
       const int c = tid % T, part = tid / T;
       F acc = F(0);
       int m = 0;
-      for (int j = it + 1 + rank; j < nt; j += SOLVE_CS, ++m) {
+      for (int j = it + 1 + rank; j < nt; j += CS, ++m) {
         const F* zj = y + j * T + part * LEN;
         if (m < SOLVE_PF) {
           const F* col = tile_buf(st, m) + (size_t)(part * LEN) * LDT + c;
@@ -1196,7 +1196,7 @@ __global__ void __launch_bounds__(256) k_tri_solve(DevProblem P, const F* L, con
     for (int r = tid; r < T; r += blockDim.x) {
       F sum = F(0);
 #pragma unroll
-      for (int q = 0; q < SOLVE_CS; ++q) sum += cluster.map_shared_rank(&partial[s & 1][0], q)[r];
+      for (int q = 0; q < CS; ++q) sum += cluster.map_shared_rank(&partial[s & 1][0], q)[r];
       t[r] = y[r0 + r] - sum;
     }
     __syncthreads();
@@ -1224,28 +1224,33 @@ size_t solve_cta_bytes(int nst, int max_np) {
 }
 
 template <typename F, int T>
-int solve_stages(int l, int max_np) {
-  const bool one_wave = (int64_t)l * SOLVE_CS <= g_num_sms;
+int solve_stages(int l, int max_np, int cs) {
+  const bool one_wave = (int64_t)l * cs <= g_num_sms;
   return one_wave && solve_cta_bytes<F, T>(3, max_np) <= (size_t)g_smem_optin ? 3 : 2;
 }
 
 template <typename F, int T, typename Rreal>
 void launch_tri_solve(const DevProblem& P, const F* L, const F* Dinv, const double* scale, const Rreal* rhs,
-                      double* x, int accumulate, int max_np, int64_t v_total, cudaStream_t stream) {
+                      double* x, int accumulate, int max_np, int64_t v_total, int cs, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(P.l * SOLVE_CS);
+  cfg.gridDim = dim3(P.l * cs);
   cfg.blockDim = dim3(256);
-  const int nst = solve_stages<F, T>(P.l, max_np);
+  const int nst = solve_stages<F, T>(P.l, max_np, cs);
   cfg.dynamicSmemBytes = nst * SolveLayout<F, T>::stage_bytes + sizeof(F) * (size_t)max_np;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = SOLVE_CS;
+  attr[0].val.clusterDim.x = cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal>, P, L, Dinv, scale, rhs, x, accumulate, v_total, nst);
+  if (cs == 2)
+    cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal, 2>, P, L, Dinv, scale, rhs, x, accumulate, v_total, nst);
+  else if (cs == 4)
+    cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal, 4>, P, L, Dinv, scale, rhs, x, accumulate, v_total, nst);
+  else
+    cudaLaunchKernelEx(&cfg, k_tri_solve<F, T, Rreal, 8>, P, L, Dinv, scale, rhs, x, accumulate, v_total, nst);
 }
 
 // r = b - S x (FP64) with S symmetric, lower triangle stored; r was set to b before.  One CTA per
@@ -1456,13 +1461,14 @@ void launch_solve_t(const DevProblem& P, const double* S, const double* b, const
   using Sreal = double;
   const F* L = reinterpret_cast<const F*>(fb.L);
   const F* Dinv = reinterpret_cast<const F*>(fb.Dinv);
-  launch_tri_solve<F, T, Sreal>(P, L, Dinv, fb.scale, b, fb.x, 0, plan.max_np, fb.v_total, stream);
+  launch_tri_solve<F, T, Sreal>(P, L, Dinv, fb.scale, b, fb.x, 0, plan.max_np, fb.v_total, plan.solve_cs, stream);
   const int nblk = (int)std::min<int64_t>(fb.v_total / 256 + 1, (int64_t)num_sms() * 8);
   for (int s = 0; s < refine_steps; ++s) {
     k_copy_vec<Sreal><<<nblk, 256, 0, stream>>>(b, fb.r, fb.v_total);
     if (plan.n_res_items > 0)
       k_residual<Sreal><<<plan.n_res_items, 32 * RES_WARPS, 0, stream>>>(P, S, fb.x, fb.r, plan.res_items);
-    launch_tri_solve<F, T, double>(P, L, Dinv, fb.scale, fb.r, fb.x, 1, plan.max_np, fb.v_total, stream);
+    launch_tri_solve<F, T, double>(P, L, Dinv, fb.scale, fb.r, fb.x, 1, plan.max_np, fb.v_total, plan.solve_cs,
+                                   stream);
   }
   k_scatter_dc<<<P.l, 256, 0, stream>>>(P, fb.x, dc, dcf);
 }
@@ -1539,9 +1545,15 @@ void configure_solve_kernels(int max_np) {
                   sizeof(float) * max_np;
   const int d32 = stages(solve_cta_bytes<double, 32>(3, max_np)) * SolveLayout<double, 32>::stage_bytes +
                   sizeof(double) * max_np;
-  raise_smem_attr((const void*)k_tri_solve<float, 64, double>, f64);
-  raise_smem_attr((const void*)k_tri_solve<float, 32, double>, f32);
-  raise_smem_attr((const void*)k_tri_solve<double, 32, double>, d32);
+  raise_smem_attr((const void*)k_tri_solve<float, 64, double, 8>, f64);
+  raise_smem_attr((const void*)k_tri_solve<float, 32, double, 8>, f32);
+  raise_smem_attr((const void*)k_tri_solve<double, 32, double, 8>, d32);
+  raise_smem_attr((const void*)k_tri_solve<float, 64, double, 4>, f64);
+  raise_smem_attr((const void*)k_tri_solve<float, 32, double, 4>, f32);
+  raise_smem_attr((const void*)k_tri_solve<double, 32, double, 4>, d32);
+  raise_smem_attr((const void*)k_tri_solve<float, 64, double, 2>, f64);
+  raise_smem_attr((const void*)k_tri_solve<float, 32, double, 2>, f32);
+  raise_smem_attr((const void*)k_tri_solve<double, 32, double, 2>, d32);
 }
 
 void launch_count_failures(const int* fail_flags, int l, DevState* st, cudaStream_t stream) {

@@ -249,6 +249,7 @@ struct CholPlan {
   int persistent;                 // 1: one persistent launch factors every cluster (FP32 factor, T = 64)
   const int* cluster_items;       // [n_cluster_items] the clusters this process factors
   int n_cluster_items;
+  int solve_cs;                   // CTAs per thread-block cluster of the cluster solves (2, 4 or 8)
 };
 struct FactorBuffers {
   void* L;          // factor (F = float or double), same layout as S'

@@ -46,7 +46,7 @@ class StbaOptions(ctypes.Structure):
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
                 ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32), ("factor_update", ctypes.c_int32),
-                ("factor_panel", ctypes.c_int32)]
+                ("factor_panel", ctypes.c_int32), ("solve_cluster", ctypes.c_int32)]
 
 
 class StbaIterInfo(ctypes.Structure):

@@ -98,7 +98,8 @@ def test_invalid_options_are_rejected():
                dict(factor_panel=stba.STBA_FACTOR_PANEL_SPLIT),
                dict(precision=1, factor_tile=32, factor_panel=stba.STBA_FACTOR_PANEL_SPLIT),
                dict(precision=1, factor_panel=4), dict(factor_panel=stba.STBA_FACTOR_PANEL_PERSISTENT),
-               dict(precision=1, factor_tile=32, factor_panel=stba.STBA_FACTOR_PANEL_PERSISTENT)):
+               dict(precision=1, factor_tile=32, factor_panel=stba.STBA_FACTOR_PANEL_PERSISTENT),
+               dict(solve_cluster=3), dict(solve_cluster=16), dict(solve_cluster=-2)):
         with pytest.raises(stba.StbaError):
             stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, **kw)
     for bad in (-0.5, float("nan"), float("inf")):

@@ -24,12 +24,14 @@ def ring():
     return s, F, hist
 
 
-@pytest.mark.parametrize("cand", list(stba.AUTOTUNE_CANDIDATES) + ["64_stacked_tensor"])
+@pytest.mark.parametrize("cand", list(stba.AUTOTUNE_CANDIDATES) + ["64_stacked_tensor", "solve_cs4", "solve_cs2"])
 def test_every_fp32_factorisation_meets_the_mixed_bar(ring, cand):
     s, F, hist = ring
     tile, update, panel = stba.AUTOTUNE_CANDIDATES.get(cand, (64, 2, 1))
+    cs = {"solve_cs4": 4, "solve_cs2": 2}.get(cand, 0)
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
-                           precision=stba.STBA_MIXED, factor_tile=tile, factor_update=update, factor_panel=panel)
+                           precision=stba.STBA_MIXED, factor_tile=tile, factor_update=update, factor_panel=panel,
+                           solve_cluster=cs)
     stba.stba_lm_iteration(ctx)
     dc, dp = stba.stba_last_step(ctx)
     assert cols(dc, hist[0]["dc"], 9) < 1e-3 and cols(dp, hist[0]["dp"], 3) < 1e-3

@@ -47,14 +47,15 @@ def oracle_first(s, lam):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-@pytest.mark.parametrize("lam", [1e-4, 0.5])
-def test_first_step_fp64_elementwise(name, lam):
+@pytest.mark.parametrize("lam,cs", [(1e-4, 0), (0.5, 0), (1e-4, 2)])
+def test_first_step_fp64_elementwise(name, lam, cs):
+    # cs: CTAs per thread-block cluster of the cluster solves (0 = the default 8)
     s = scene(name)
     l = int(s.clusters.max()) + 1
     c2, p2, _, _, rec = oracle_first(s, lam)
     st = rec["step"]
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=stba.STBA_FP64,
-                           lambda0=lam)
+                           lambda0=lam, solve_cluster=cs)
     info = stba.stba_lm_iteration(ctx)
     assert info["failed_clusters"] == 0
     assert info["corrected"] == rec["corrected"] == (lam >= 0.1)
