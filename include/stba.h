@@ -103,7 +103,17 @@ typedef struct {
                                (2, 4 or 8; 0 = default: 8 while the clusters' solve CTAs fit in two waves on
                                the SMs, else 4): more CTAs share a tile step's products, fewer make its
                                cluster barrier and distributed-shared-memory exchange cheaper. */
+  int32_t pair_blocks;      /* off-diagonal camera blocks of S' (Eq. 10, 13), -sum over the observation pairs
+                               of a virtual point of G_a^T G_b with G_o = L_v^-1 Jp,o^T Jc,o:
+                               STBA_PAIR_BLOCKS_STORED (default) = the camera pass stores every G_o (36 reals
+                               per observation of device memory) and the pair pass reads them;
+                               STBA_PAIR_BLOCKS_RECOMPUTE = the pair pass recomputes each G_o from the point,
+                               the observation, its residual and the virtual point's L_v^-1 (fewer bytes, no
+                               G buffer; in FP32 its Jacobians differ from the camera pass's in the last
+                               bits, which the Schur complement amplifies: use it in FP64 mode). */
 } stba_options;
+
+enum { STBA_PAIR_BLOCKS_DEFAULT = 0, STBA_PAIR_BLOCKS_STORED = 1, STBA_PAIR_BLOCKS_RECOMPUTE = 2 };
 
 enum { STBA_FACTOR_UPDATE_DEFAULT = 0, STBA_FACTOR_UPDATE_SIMT = 1, STBA_FACTOR_UPDATE_TENSOR = 2 };
 enum { STBA_FACTOR_PANEL_DEFAULT = 0, STBA_FACTOR_PANEL_STACKED = 1, STBA_FACTOR_PANEL_SPLIT = 2,

@@ -268,6 +268,8 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.huber_a = c->opt.huber_a;
   P.res_f = c->mixed ? (const float*)c->res_cur : nullptr;
   P.res_d = c->mixed ? nullptr : (const double*)c->res_cur;
+  P.base_pos = c->inv[c->inv_cur];
+  P.pair_recompute = c->opt.pair_blocks == STBA_PAIR_BLOCKS_RECOMPUTE ? 1 : 0;
   P.sharded = c->shard_world > 1 ? 1 : 0;
   P.cluster_owned = c->cl_owned;
   return P;
@@ -1319,6 +1321,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
        c->opt.factor_panel != STBA_FACTOR_PANEL_SPLIT && c->opt.factor_panel != STBA_FACTOR_PANEL_PERSISTENT) ||
       !(c->opt.solve_cluster == 0 || c->opt.solve_cluster == 2 || c->opt.solve_cluster == 4 ||
         c->opt.solve_cluster == 8) ||
+      !(c->opt.pair_blocks == STBA_PAIR_BLOCKS_DEFAULT || c->opt.pair_blocks == STBA_PAIR_BLOCKS_STORED ||
+        c->opt.pair_blocks == STBA_PAIR_BLOCKS_RECOMPUTE) ||
       ((c->opt.factor_panel == STBA_FACTOR_PANEL_SPLIT || c->opt.factor_panel == STBA_FACTOR_PANEL_PERSISTENT) &&
        !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
@@ -1590,7 +1594,9 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = dalloc(c, &pti, 9 * (size_t)n * rs)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &vg, 9 * (size_t)m * rs)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &ta, 3 * (size_t)n * rs)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &gb, (c->use_pcg ? 1 : 36 * Q) * rs)) != STBA_OK) return bail(s);
+    // the stored G_o of the camera pass, only when the pair pass reads them (option pair_blocks)
+    const bool stored_g = !c->use_pcg && c->opt.pair_blocks != STBA_PAIR_BLOCKS_RECOMPUTE;
+    if ((s = dalloc(c, &gb, (stored_g ? 36 * Q : 1) * rs)) != STBA_OK) return bail(s);
     c->vp_acc = vpa;
     c->vp_info = vpi;
     c->pt_info = pti;

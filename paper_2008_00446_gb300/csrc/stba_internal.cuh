@@ -45,6 +45,8 @@ struct DevProblem {
   double huber_a;              // Huber scale a (0: plain least squares)
   const float* res_f;          // [q][2] residuals f_o at the current x, computed in FP64, stored in the
   const double* res_d;         //        working precision (res_f in mixed mode, res_d in FP64 mode)
+  const int* base_pos;         // [q] sorted position of every base-order observation (current assignment)
+  int pair_recompute;          // 1: the pair pass recomputes G_o instead of reading the camera pass's copy
   int sharded;                 // 1: this process owns only some clusters (stba_set_shard)
   const int* cluster_owned;    // [l] 1 where this process builds, factors and solves cluster k (all 1 unless
                                //     sharded)

@@ -310,6 +310,29 @@ __device__ __forceinline__ real warp_transpose_sum32(real (&v)[32]) {
   return v[0];
 }
 
+// P = L^-1 Jp^T (3 x 2) and G = P Jc (3 x 9) of one observation, with every product and sum rounded by explicit
+// fma / mul intrinsics, so that the camera pass and the pair pass form bitwise the same G from the same inputs
+// (the S' of a virtual point then stays consistent between its diagonal and off-diagonal camera blocks).
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename real>
+__device__ __forceinline__ void g_of_obs(const real* Li, const real (&Jc)[2][9], const real (&Jp)[2][3], real (&Pm)[3][2],
+                                         real (&G)[3][9]) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    Pm[0][t] = mul_rn(Li[0], Jp[t][0]);
+    Pm[1][t] = fma_rn(Li[2], Jp[t][1], mul_rn(Li[1], Jp[t][0]));
+    Pm[2][t] = fma_rn(Li[5], Jp[t][2], fma_rn(Li[4], Jp[t][1], mul_rn(Li[3], Jp[t][0])));
+  }
+#pragma unroll
+  for (int c = 0; c < 9; ++c)
+#pragma unroll
+    for (int s = 0; s < 3; ++s) G[s][c] = fma_rn(Pm[s][1], Jc[1][c], mul_rn(Pm[s][0], Jc[0][c]));
+}
+
 template <typename real>
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_cam_pass(DevProblem P, Scratch<real> W, CamSlots CS, real* Gbuf,
                                                   const DevState* st) {
@@ -363,26 +386,17 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_cam_pass(Dev
         br[1] = N01 * r[0] + N11 * r[1];
       }
     } else {
-      real Li[6];
-#pragma unroll
-      for (int c = 0; c < 6; ++c) Li[c] = vi[c];
-      real Pm[3][2];   // P = L^-1 Jp^T (3x2)
-#pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        Pm[0][t] = Li[0] * Jp[t][0];
-        Pm[1][t] = Li[1] * Jp[t][0] + Li[2] * Jp[t][1];
-        Pm[2][t] = Li[3] * Jp[t][0] + Li[4] * Jp[t][1] + Li[5] * Jp[t][2];
-      }
+      real Pm[3][2], Gm[3][9];   // P = L^-1 Jp^T (3x2), G = P Jc
+      g_of_obs<real>(vi, Jc, Jp, Pm, Gm);
       N00 = real(1) - (Pm[0][0] * Pm[0][0] + Pm[1][0] * Pm[1][0] + Pm[2][0] * Pm[2][0]);
       N01 = -(Pm[0][0] * Pm[0][1] + Pm[1][0] * Pm[1][1] + Pm[2][0] * Pm[2][1]);
       N11 = real(1) - (Pm[0][1] * Pm[0][1] + Pm[1][1] * Pm[1][1] + Pm[2][1] * Pm[2][1]);
-      // G = L^-1 Jp^T Jc = P Jc (3x9), stored by columns with 16-byte vector stores
+      // G = L^-1 Jp^T Jc = P Jc (3x9), stored by columns with 16-byte vector stores (unless the pair pass
+      // recomputes it)
       real* Gs = Gbuf + (size_t)GSTRIDE * P.obs_base[o];   // indexed like the camera graph's pairs
 #pragma unroll
-      for (int c = 0; c < 9; ++c) {
-        const real g0 = Pm[0][0] * Jc[0][c] + Pm[0][1] * Jc[1][c];
-        const real g1 = Pm[1][0] * Jc[0][c] + Pm[1][1] * Jc[1][c];
-        const real g2 = Pm[2][0] * Jc[0][c] + Pm[2][1] * Jc[1][c];
+      for (int c = 0; c < 9 && !P.pair_recompute; ++c) {
+        const real g0 = Gm[0][c], g1 = Gm[1][c], g2 = Gm[2][c];
         if constexpr (sizeof(real) == 4) {
           reinterpret_cast<float4*>(Gs)[c] = make_float4(g0, g1, g2, 0.f);
         } else {
@@ -472,7 +486,34 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// G_o = L_v^-1 Jp,o^T Jc,o (3 x 9) of the observation at sorted position pos by camera cam, written by columns
+// (G[0][c], G[1][c], G[2][c], 0) to dst: the camera pass's arithmetic (Jacobians at the current x, Huber
+// weights from the stored residual, L_v^-1 of the virtual point's damped block).
 template <typename real>
+__device__ __forceinline__ void obs_G(const DevProblem& P, const Scratch<real>& W, int cam, int pos, real* dst) {
+  const Cam<real> C = load_cam_w<real>(P, cam);
+  real X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
+  load_point_w(P, P.obs_pt[pos], X);
+  load_uv(P, pos, uo, vo);
+  project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
+  r[0] = res_ptr<real>(P)[2 * (size_t)pos];
+  r[1] = res_ptr<real>(P)[2 * (size_t)pos + 1];
+  scale_rows(huber_sqrt_weight<real>(P.huber_a, r[0], r[1]), r, Jc, Jp);
+  real Pm[3][2], Gm[3][9];
+  g_of_obs<real>(W.vp_info + 9 * (size_t)P.obs_vp[pos], Jc, Jp, Pm, Gm);
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    const real g0 = Gm[0][c], g1 = Gm[1][c], g2 = Gm[2][c];
+    if constexpr (sizeof(real) == 4) {
+      reinterpret_cast<float4*>(dst)[c] = make_float4(g0, g1, g2, 0.f);
+    } else {
+      reinterpret_cast<double2*>(dst)[2 * c] = make_double2(g0, g1);
+      reinterpret_cast<double2*>(dst)[2 * c + 1] = make_double2(g2, 0.0);
+    }
+  }
+}
+
+template <typename real, bool RECOMPUTE>
 __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scratch<real> W, PairChunks B,
                                                               const real* __restrict__ Gbuf) {
   constexpr int CH = PairStage<real>::CH;
@@ -495,10 +536,16 @@ __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scra
     const int cn = min(CH, chunk.w - first);
     if (side < 2 && j < cn) {
       const int2 pr = B.pairs[chunk.z + first + j];
-      const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
       real* dst = stage + ((size_t)(buf * CH + j) * 2 + side) * GSTRIDE;
+      if constexpr (RECOMPUTE) {   // computed here: no G buffer, about 90 bytes read per pair instead of 288
+        const int b = side ? pr.y : pr.x;
+        obs_G<real>(P, W, side ? chunk.y : chunk.x, P.base_pos[b], dst);
+      } else {
+        const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
 #pragma unroll
-      for (int q = 0; q < ROWQ; ++q) cp_async_16(dst + q * (16 / (int)sizeof(real)), src + q * (16 / (int)sizeof(real)));
+        for (int q = 0; q < ROWQ; ++q)
+          cp_async_16(dst + q * (16 / (int)sizeof(real)), src + q * (16 / (int)sizeof(real)));
+      }
     }
     cp_async_commit();
   };
@@ -581,9 +628,13 @@ template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
                       cudaStream_t stream) {
   k_cam_pass<real><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
-  if (B.nchunks > 0 && P.l < P.m)   // a fixed grid walks the list of chunks inside clusters
-    k_pair_build<real><<<std::min((B.nchunks + PB_WARPS - 1) / PB_WARPS, 3 * num_sms()), 32 * PB_WARPS,
-                         PairStage<real>::bytes, stream>>>(P, W, B, Gbuf);
+  if (B.nchunks > 0 && P.l < P.m) {   // a fixed grid walks the list of chunks inside clusters
+    const int grid = std::min((B.nchunks + PB_WARPS - 1) / PB_WARPS, 3 * num_sms());
+    if (P.pair_recompute)
+      k_pair_build<real, true><<<grid, 32 * PB_WARPS, PairStage<real>::bytes, stream>>>(P, W, B, Gbuf);
+    else
+      k_pair_build<real, false><<<grid, 32 * PB_WARPS, PairStage<real>::bytes, stream>>>(P, W, B, Gbuf);
+  }
 }
 
 // ------------------------------------------------------------------------------------------------------
@@ -1025,9 +1076,13 @@ void launch_params_to_float(const DevProblem& P, float* cams_f, float* pts_f, cu
 
 void configure_kernels(int max_np) {
   configure_solve_kernels(max_np);
-  cudaFuncSetAttribute(k_pair_build<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_pair_build<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)PairStage<float>::bytes);
-  cudaFuncSetAttribute(k_pair_build<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_pair_build<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)PairStage<float>::bytes);
+  cudaFuncSetAttribute(k_pair_build<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)PairStage<double>::bytes);
+  cudaFuncSetAttribute(k_pair_build<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)PairStage<double>::bytes);
 }
 

@@ -19,6 +19,7 @@ STBA_FP64, STBA_MIXED = 0, 1
 STBA_SOLVER_CLUSTERS, STBA_SOLVER_PCG_FULL, STBA_SOLVER_PCG_CLUSTERS = 0, 1, 2
 STBA_FACTOR_UPDATE_DEFAULT, STBA_FACTOR_UPDATE_SIMT, STBA_FACTOR_UPDATE_TENSOR = 0, 1, 2
 STBA_FACTOR_PANEL_DEFAULT, STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_SPLIT, STBA_FACTOR_PANEL_PERSISTENT = 0, 1, 2, 3
+STBA_PAIR_BLOCKS_DEFAULT, STBA_PAIR_BLOCKS_STORED, STBA_PAIR_BLOCKS_RECOMPUTE = 0, 1, 2
 # stba_autotune's candidates: name -> (factor_tile, factor_update, factor_panel)
 AUTOTUNE_CANDIDATES = {"64_split_tensor": (64, 2, 2), "64_split_simt": (64, 1, 2), "64_stacked_simt": (64, 1, 1),
                        "32_stacked_simt": (32, 1, 1), "64_persistent": (64, 1, 3)}
@@ -46,7 +47,8 @@ class StbaOptions(ctypes.Structure):
                 ("refine_steps", ctypes.c_int32), ("use_graph", ctypes.c_int32),
                 ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
                 ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32), ("factor_update", ctypes.c_int32),
-                ("factor_panel", ctypes.c_int32), ("solve_cluster", ctypes.c_int32)]
+                ("factor_panel", ctypes.c_int32), ("solve_cluster", ctypes.c_int32),
+                ("pair_blocks", ctypes.c_int32)]
 
 
 class StbaIterInfo(ctypes.Structure):

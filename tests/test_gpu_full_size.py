@@ -47,15 +47,16 @@ def oracle_first(s, lam):
 
 
 @pytest.mark.parametrize("name", list(SCENES))
-@pytest.mark.parametrize("lam,cs", [(1e-4, 0), (0.5, 0), (1e-4, 2)])
-def test_first_step_fp64_elementwise(name, lam, cs):
-    # cs: CTAs per thread-block cluster of the cluster solves (0 = the default 8)
+@pytest.mark.parametrize("lam,cs,pairs", [(1e-4, 0, 0), (0.5, 0, 0), (1e-4, 2, 0), (1e-4, 0, 2)])
+def test_first_step_fp64_elementwise(name, lam, cs, pairs):
+    # cs: CTAs per thread-block cluster of the cluster solves (0 = the default 8); pairs = 2: the pair pass
+    # recomputes G_o instead of reading the camera pass's copy
     s = scene(name)
     l = int(s.clusters.max()) + 1
     c2, p2, _, _, rec = oracle_first(s, lam)
     st = rec["step"]
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, precision=stba.STBA_FP64,
-                           lambda0=lam, solve_cluster=cs)
+                           lambda0=lam, solve_cluster=cs, pair_blocks=pairs)
     info = stba.stba_lm_iteration(ctx)
     assert info["failed_clusters"] == 0
     assert info["corrected"] == rec["corrected"] == (lam >= 0.1)
