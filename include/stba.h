@@ -192,8 +192,11 @@ stba_status stba_last_step(stba_ctx* ctx, double* dc, double* dp);
  * stba_record(ctx, max_iter) starts a tape: each of the next max_iter LM iterations (stba_lm_iteration,
  * stba_solve) stores the parameters x_t it starts from ((9m + 3n) FP64 values in device memory, held by
  * the context) and, after it, its record (damping, accept flag, correction flag), with the cluster
- * assignment it used.  A further iteration returns STBA_ERR_STATE; stba_record restarts the tape and
- * max_iter = 0 frees it. */
+ * assignment it used.  It also allocates the reverse pass's buffers (about 184 q + 216 m + 96 n bytes of
+ * device memory), so that stba_adjoint allocates nothing.  A further iteration returns STBA_ERR_STATE;
+ * stba_record restarts the tape and max_iter = 0 frees it (the buffers with it).  Errors:
+ * STBA_ERR_INVALID_ARG (max_iter < 0), STBA_ERR_OOM (the tape or the buffers do not fit; nothing is then
+ * recorded). */
 stba_status stba_record(stba_ctx* ctx, int32_t max_iter);
 
 /* Reverse-mode derivative of the recorded iterations.  Given the gradient of a loss L at the final
@@ -211,8 +214,8 @@ stba_status stba_record(stba_ctx* ctx, int32_t max_iter);
  * physical w), including the dependence of h_v / H_i on the parameters.
  * Errors: STBA_ERR_STATE with the PCG solvers or the Huber loss, if nothing was recorded, or if
  * stba_set_params replaced the parameters during the recording.  On return the parameters, the cluster
- * assignment and the LM state are those before the call.  The call synchronises the stream and allocates,
- * then frees, about 184 q + 216 m + 96 n bytes of device memory. */
+ * assignment and the LM state are those before the call.  The call synchronises the stream and allocates
+ * no memory (its buffers are held with the tape). */
 stba_status stba_adjoint(stba_ctx* ctx, const double* dL_dcams, const double* dL_dpts, double* dL_dobs,
                          double* dL_dcams0, double* dL_dpts0);
 

@@ -48,6 +48,7 @@ struct stba_ctx {
   int reorder_next = 0;
   cudaStream_t side_stream = nullptr;           // trailing updates of the factorisation
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_rfork = nullptr, ev_rjoin = nullptr;   // the re-ordering's side branch (chunk listing)
   std::vector<cudaEvent_t> ev_panel, ev_update;  // one per tile step (grown, never shrunk)
   std::string err;
   int64_t m = 0, n = 0, q = 0;
@@ -125,6 +126,8 @@ struct stba_ctx {
   std::vector<int> tape_cluster_id;     // per recorded iteration, index into tape_clusters
   std::vector<std::vector<int>> tape_clusters;
   std::vector<void*> tape_allocs;
+  AdjointBuffers adj{};                 // reverse-pass buffers, allocated with the tape
+  double* adj_save_x = nullptr;         // [9m + 3n] the final parameters, kept across the reverse pass
 
   // graph / timing
   cudaGraphExec_t graph = nullptr;
@@ -349,13 +352,25 @@ static void enqueue_reorder(stba_ctx* c, const ReorderArgs& A, bool carry, cudaS
   else
     launch_reorder<double>(A, c->key, c->tile_sum, c->counts, carry ? (const double*)c->res_cur : nullptr,
                            (double*)c->res_cand, st);
-  if (!c->use_pcg && !c->use_spcg && c->pchunks.nchunks > 0)
-    launch_list_chunks(c->pchunks, c->cam_cluster, c->cl_owned, c->counts + 3, st);
+}
+
+// The re-ordering of an assignment with the listing of the camera-pair chunks inside clusters on a side
+// branch: the listing reads only the new cluster ids, so its five launches overlap the re-ordering's.
+static void enqueue_reorder_branches(stba_ctx* c, const ReorderArgs& A, bool carry, cudaStream_t st) {
+  const bool chunks = !c->use_pcg && !c->use_spcg && c->pchunks.nchunks > 0;
+  if (chunks) {
+    cudaEventRecord(c->ev_rfork, st);
+    cudaStreamWaitEvent(c->side_stream, c->ev_rfork, 0);
+    launch_list_chunks(c->pchunks, c->cam_cluster, c->cl_owned, c->counts + 3, c->side_stream);
+    cudaEventRecord(c->ev_rjoin, c->side_stream);
+  }
+  enqueue_reorder(c, A, carry, st);
+  if (chunks) cudaStreamWaitEvent(st, c->ev_rjoin, 0);
 }
 
 static stba_status launch_reorder_graph(stba_ctx* c, const ReorderArgs& A, bool carry) {
   if (!c->opt.use_graph) {
-    enqueue_reorder(c, A, carry, c->stream);
+    enqueue_reorder_branches(c, A, carry, c->stream);
     CK(cudaGetLastError());
     return STBA_OK;
   }
@@ -378,7 +393,7 @@ static stba_status launch_reorder_graph(stba_ctx* c, const ReorderArgs& A, bool 
       return STBA_OK;
     }
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  enqueue_reorder(c, A, carry, c->cap_stream);
+  enqueue_reorder_branches(c, A, carry, c->cap_stream);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
   if (e != cudaSuccess) return fail(c, STBA_ERR_CUDA, "re-ordering capture failed: %s", cudaGetErrorString(e));
@@ -969,6 +984,8 @@ void free_tape(stba_ctx* c) {
   free_list(c, c->tape_allocs);
   c->tape_x = nullptr;
   c->tape_info = nullptr;
+  c->adj = AdjointBuffers{};
+  c->adj_save_x = nullptr;
   c->tape_cap = c->tape_len = 0;
   c->tape_broken = false;
   c->tape_clusters.clear();
@@ -1279,6 +1296,8 @@ void stba_destroy(stba_ctx* c) {
   if (c->side_stream) cudaStreamDestroy(c->side_stream);
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_rfork) cudaEventDestroy(c->ev_rfork);
+  if (c->ev_rjoin) cudaEventDestroy(c->ev_rjoin);
   for (auto e : c->ev_panel) cudaEventDestroy(e);
   for (auto e : c->ev_update) cudaEventDestroy(e);
   delete c;
@@ -1411,6 +1430,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
   if (cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_rfork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_rjoin, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->stage_ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->stage_ev[1], cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(c, STBA_ERR_CUDA, "cannot create the factorisation stream or its events"));
@@ -1745,7 +1766,21 @@ stba_status stba_record(stba_ctx* c, int32_t max_iter) {
   const size_t nx = 9 * (size_t)c->m + 3 * (size_t)c->n;
   stba_status s;
   if ((s = dalloc_into(c, &c->tape_x, nx * (size_t)max_iter, c->tape_allocs)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &c->tape_info, (size_t)max_iter, c->tape_allocs)) != STBA_OK) {
+  // the reverse pass's buffers are allocated here, once, so that stba_adjoint allocates nothing
+  AdjointBuffers& A = c->adj;
+  const size_t q = c->q;
+  const bool ok = (s = dalloc_into(c, &c->tape_info, (size_t)max_iter, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.a_c, 9 * (size_t)c->m, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.a_p, 3 * (size_t)c->n, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.u, 3 * (size_t)c->n, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.zc, 9 * (size_t)c->m, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.vpz, 6 * q, c->tape_allocs)) == STBA_OK &&   // nv <= q
+                  (s = dalloc_into(c, &A.T, 12 * q, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.qbar, 2 * q, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.zeta, 3 * (size_t)c->n, c->tape_allocs)) == STBA_OK &&
+                  (s = dalloc_into(c, &A.kappa, 3 * q, c->tape_allocs)) == STBA_OK &&   // nv <= q
+                  (s = dalloc_into(c, &c->adj_save_x, nx, c->tape_allocs)) == STBA_OK;
+  if (!ok) {
     free_tape(c);
     return s;
   }
@@ -1766,29 +1801,11 @@ stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_d
   std::vector<stba_iter_info> info(T);
   CK(cudaMemcpyAsync(info.data(), c->tape_info, T * sizeof(stba_iter_info), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  // adjoint buffers and the saved final state, freed on every return path
-  struct Guard {
-    stba_ctx* c;
-    std::vector<void*> list;
-    ~Guard() {
-      cudaStreamSynchronize(c->stream);
-      free_list(c, list);
-    }
-  } g{c, {}};
-  AdjointBuffers A{};
-  double* save_x = nullptr;
+  // the buffers were allocated with the tape (stba_record): nothing is allocated here
+  const AdjointBuffers& A = c->adj;
+  double* save_x = c->adj_save_x;
   stba_status s;
   const size_t nx = 9 * (size_t)m + 3 * (size_t)n;
-  if ((s = dalloc_into(c, &A.a_c, 9 * (size_t)m, g.list)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &A.a_p, 3 * (size_t)n, g.list)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &A.u, 3 * (size_t)n, g.list)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &A.zc, 9 * (size_t)m, g.list)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &A.vpz, 6 * (size_t)q, g.list)) != STBA_OK) return s;   // nv <= q
-  if ((s = dalloc_into(c, &A.T, 12 * (size_t)q, g.list)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &A.qbar, 2 * (size_t)q, g.list)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &A.zeta, 3 * (size_t)n, g.list)) != STBA_OK) return s;
-  if ((s = dalloc_into(c, &A.kappa, 3 * (size_t)q, g.list)) != STBA_OK) return s;   // nv <= q
-  if ((s = dalloc_into(c, &save_x, nx, g.list)) != STBA_OK) return s;
   DevState saved;
   CK(cudaMemcpyAsync(&saved, c->st, sizeof saved, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(save_x, c->cams, 9 * (size_t)m * 8, cudaMemcpyDeviceToDevice, c->stream));
