@@ -105,12 +105,14 @@ typedef struct {
                                cluster barrier and distributed-shared-memory exchange cheaper. */
   int32_t pair_blocks;      /* off-diagonal camera blocks of S' (Eq. 10, 13), -sum over the observation pairs
                                of a virtual point of G_a^T G_b with G_o = L_v^-1 Jp,o^T Jc,o:
-                               STBA_PAIR_BLOCKS_STORED (default) = the camera pass stores every G_o (36 reals
-                               per observation of device memory) and the pair pass reads them;
-                               STBA_PAIR_BLOCKS_RECOMPUTE = the pair pass recomputes each G_o from the point,
-                               the observation, its residual and the virtual point's L_v^-1 (fewer bytes, no
-                               G buffer; in FP32 its Jacobians differ from the camera pass's in the last
-                               bits, which the Schur complement amplifies: use it in FP64 mode). */
+                               STBA_PAIR_BLOCKS_RECOMPUTE (default) = the pair pass recomputes each G_o from
+                               the point, the observation, its residual and the virtual point's L_v^-1 (no G
+                               buffer, fewer bytes moved);
+                               STBA_PAIR_BLOCKS_STORED = the camera pass stores every G_o (36 reals per
+                               observation of device memory) and the pair pass reads them.
+                               Both give the same S': in FP32 every pass evaluates the Jacobian rows with
+                               each operation rounded on its own, so stored and recomputed G_o are bitwise
+                               equal (up to the order of the FP64 atomic sums). */
 } stba_options;
 
 enum { STBA_PAIR_BLOCKS_DEFAULT = 0, STBA_PAIR_BLOCKS_STORED = 1, STBA_PAIR_BLOCKS_RECOMPUTE = 2 };

@@ -18,7 +18,9 @@
 // (alpha, beta) = sum_s alpha_s H_s beta (H_s the Hessian of residual component s), the terms are
 //   (f + J dx', z') + (J z', dx') + (J DP + rho, U) + (J U, DP + DC)
 //   + sum_s (e_s, 2 lambda J[s,:] o (z' o dx' + U o DP))          (the lambda diag(J^T J) damping)
-// The (alpha, beta) products come from the Jacobian evaluated on dual numbers (stba_dual.cuh).
+// The (alpha, beta) products come from the Jacobian evaluated on dual numbers (stba_dual.cuh).  The
+// per-observation products run in the working precision (FP32 in mixed mode, as the forward step's
+// Jacobians do); the adjoint vectors and every sum over observations are FP64.
 //
 // A step taken with the steepest-descent correction (Sec. 4.3; lambda >= the threshold) solves H' dx' = g~'
 // with w~'_v = (h_v / H_i) o w_i for the virtual points v of point i (the closed form of the correction:
@@ -41,16 +43,14 @@ namespace {
 
 constexpr int ADJ_THREADS = 128;
 
-__device__ __forceinline__ void load_obs64(const DevProblem& P, int o, Cam<double>& C, double X[3], double& uo,
-                                           double& vo) {
-  C = load_cam<double>(P.cams + 9 * (size_t)P.obs_cam[o]);
-  const double* p = P.pts + 3 * (size_t)P.obs_pt[o];
-  X[0] = p[0];
-  X[1] = p[1];
-  X[2] = p[2];
-  const double2 uv = reinterpret_cast<const double2*>(P.obs_uv)[o];
-  uo = uv.x;
-  vo = uv.y;
+// One observation's camera, point and measurement in the working precision: FP64 from the parameters, or
+// the per-iteration FP32 copies in mixed precision (the forward step's Jacobians are FP32 there too).
+template <typename real>
+__device__ __forceinline__ void load_obs_w(const DevProblem& P, int o, Cam<real>& C, real X[3], real& uo,
+                                           real& vo) {
+  C = load_cam_w<real>(P, P.obs_cam[o]);
+  load_point_w<real>(P, P.obs_pt[o], X);
+  load_uv<real>(P, o, uo, vo);
 }
 
 template <typename real>
@@ -87,6 +87,7 @@ __device__ __forceinline__ double block_sum_to_thread(const double (&v)[NV]) {
 }
 
 // a^_c = a_c - E u, one CTA per camera, written into the per-cluster padded vector layout of b'.
+template <typename real>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_cam_rhs(DevProblem P, CamLists CL, const double* __restrict__ u,
                                                              const double* __restrict__ a_c, double* __restrict__ bhat) {
   const int j = blockIdx.x;
@@ -95,15 +96,16 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_cam_rhs(DevProblem P, CamLi
   for (int i = 0; i < 9; ++i) acc[i] = 0.0;
   for (int e = CL.cam_obs_off[j] + threadIdx.x; e < CL.cam_obs_off[j + 1]; e += blockDim.x) {
     const int o = CL.cam_obs[e];
-    Cam<double> C;
-    double X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
-    load_obs64(P, o, C, X, uo, vo);
-    project_jacobian<double, true>(C, X, uo, vo, r, Jc, Jp);
+    Cam<real> C;
+    real X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
+    load_obs_w<real>(P, o, C, X, uo, vo);
+    project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
     const double* up = u + 3 * (size_t)P.obs_pt[o];
-    const double t0 = Jp[0][0] * up[0] + Jp[0][1] * up[1] + Jp[0][2] * up[2];
-    const double t1 = Jp[1][0] * up[0] + Jp[1][1] * up[1] + Jp[1][2] * up[2];
+    const real u0 = (real)up[0], u1 = (real)up[1], u2 = (real)up[2];
+    const real t0 = Jp[0][0] * u0 + Jp[0][1] * u1 + Jp[0][2] * u2;
+    const real t1 = Jp[1][0] * u0 + Jp[1][1] * u1 + Jp[1][2] * u2;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) acc[i] += Jc[0][i] * t0 + Jc[1][i] * t1;
+    for (int i = 0; i < 9; ++i) acc[i] += (double)(Jc[0][i] * t0 + Jc[1][i] * t1);
   }
   const double s = block_sum_to_thread<9>(acc);
   if (threadIdx.x < 9) {
@@ -113,6 +115,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_cam_rhs(DevProblem P, CamLi
 }
 
 // Per observation, warp-segmented by virtual point: E'_v^T z_c and E'_v^T Delta c (3 + 3 sums).
+template <typename real>
 __global__ void __launch_bounds__(256) k_adj_vp(DevProblem P, const double* __restrict__ zc,
                                                 const double* __restrict__ dc, double* __restrict__ vpz) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -122,24 +125,25 @@ __global__ void __launch_bounds__(256) k_adj_vp(DevProblem P, const double* __re
   double val[6] = {0, 0, 0, 0, 0, 0};
   if (act) {
     v = P.obs_vp[o];
-    Cam<double> C;
-    double X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
-    load_obs64(P, o, C, X, uo, vo);
-    project_jacobian<double, true>(C, X, uo, vo, r, Jc, Jp);
+    Cam<real> C;
+    real X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
+    load_obs_w<real>(P, o, C, X, uo, vo);
+    project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
     const double* z = zc + 9 * (size_t)P.obs_cam[o];
     const double* d = dc + 9 * (size_t)P.obs_cam[o];
-    double jz0 = 0, jz1 = 0, jd0 = 0, jd1 = 0;
+    real jz0 = 0, jz1 = 0, jd0 = 0, jd1 = 0;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      jz0 += Jc[0][c] * z[c];
-      jz1 += Jc[1][c] * z[c];
-      jd0 += Jc[0][c] * d[c];
-      jd1 += Jc[1][c] * d[c];
+      const real zcv = (real)z[c], dcv = (real)d[c];
+      jz0 += Jc[0][c] * zcv;
+      jz1 += Jc[1][c] * zcv;
+      jd0 += Jc[0][c] * dcv;
+      jd1 += Jc[1][c] * dcv;
     }
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-      val[s] = Jp[0][s] * jz0 + Jp[1][s] * jz1;
-      val[3 + s] = Jp[0][s] * jd0 + Jp[1][s] * jd1;
+      val[s] = (double)(Jp[0][s] * jz0 + Jp[1][s] * jz1);
+      val[3 + s] = (double)(Jp[0][s] * jd0 + Jp[1][s] * jd1);
     }
   }
   segmented_scan<6>(val, v, lane);
@@ -198,28 +202,34 @@ __global__ void k_adj_zeta(DevProblem P, const real* __restrict__ vp_acc, const 
   }
 }
 
-// out += sum_s alpha_s d/de J_s(theta + e beta) (12 entries: camera 9, point 3) for one observation.
-__device__ __forceinline__ void hess_vec(const Cam<double>& C0, const double X0[3], double uo, double vo,
-                                         double al0, double al1, const double beta[12], double out[12]) {
-  Cam<Dual> C;
+// out += sum_s alpha_s d/de J_s(theta + e beta) (12 entries: camera 9, point 3) for one observation, on
+// dual numbers of the working precision.
+template <typename real>
+__device__ __forceinline__ void hess_vec(const Cam<real>& C0, const real X0[3], real uo, real vo, real al0, real al1,
+                                         const real beta[12], real out[12]) {
+  using D = DualT<real>;
+  Cam<D> C;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    C.w[k] = Dual(C0.w[k], beta[k]);
-    C.t[k] = Dual(C0.t[k], beta[3 + k]);
+    C.w[k] = D(C0.w[k], beta[k]);
+    C.t[k] = D(C0.t[k], beta[3 + k]);
   }
-  C.f = Dual(C0.f, beta[6]);
-  C.k1 = Dual(C0.k1, beta[7]);
-  C.k2 = Dual(C0.k2, beta[8]);
-  const Dual X[3] = {Dual(X0[0], beta[9]), Dual(X0[1], beta[10]), Dual(X0[2], beta[11])};
-  Dual r[2], Jc[2][9], Jp[2][3];
-  project_jacobian<Dual, true>(C, X, Dual(uo), Dual(vo), r, Jc, Jp);
+  C.f = D(C0.f, beta[6]);
+  C.k1 = D(C0.k1, beta[7]);
+  C.k2 = D(C0.k2, beta[8]);
+  const D X[3] = {D(X0[0], beta[9]), D(X0[1], beta[10]), D(X0[2], beta[11])};
+  D r[2], Jc[2][9], Jp[2][3];
+  project_jacobian<D, true>(C, X, D(uo), D(vo), r, Jc, Jp);
 #pragma unroll
   for (int c = 0; c < 9; ++c) out[c] += al0 * Jc[0][c].d + al1 * Jc[1][c].d;
 #pragma unroll
   for (int c = 0; c < 3; ++c) out[9 + c] += al0 * Jp[0][c].d + al1 * Jp[1][c].d;
 }
 
-// Per observation: g_o (added to q_bar in input order) and the 12 local terms T_o of x_bar.
+// Per observation: g_o (added to q_bar in input order) and the 12 local terms T_o of x_bar.  The products
+// run in the working precision (FP32 in mixed mode, like the forward step's Jacobians), from the adjoint
+// vectors held in FP64; f_o is the stored residual the forward step linearised with.
+template <typename real>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int* __restrict__ perm, double lam,
                                                          const double* __restrict__ dc, const double* __restrict__ dp,
                                                          const double* __restrict__ zc, const double* __restrict__ u,
@@ -230,38 +240,40 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= P.q) return;
   const int cam = P.obs_cam[o], pt = P.obs_pt[o], v = P.obs_vp[o];
-  Cam<double> C;
-  double X[3], uo, vo, f[2], Jc[2][9], Jp[2][3];
-  load_obs64(P, o, C, X, uo, vo);
-  project_jacobian<double, true>(C, X, uo, vo, f, Jc, Jp);
-  double z[12], dx[12], uu[3], dpp[3];
+  Cam<real> C;
+  real X[3], uo, vo, f[2], Jc[2][9], Jp[2][3];
+  load_obs_w<real>(P, o, C, X, uo, vo);
+  project_jacobian<real, true>(C, X, uo, vo, f, Jc, Jp);
+  f[0] = res_ptr<real>(P)[2 * (size_t)o];
+  f[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
+  real z[12], dx[12], uu[3], dpp[3];
 #pragma unroll
   for (int c = 0; c < 9; ++c) {
-    z[c] = zc[9 * (size_t)cam + c];
-    dx[c] = dc[9 * (size_t)cam + c];
+    z[c] = (real)zc[9 * (size_t)cam + c];
+    dx[c] = (real)dc[9 * (size_t)cam + c];
   }
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    z[9 + s] = vpz[6 * (size_t)v + s];
-    dx[9 + s] = vpz[6 * (size_t)v + 3 + s];
-    uu[s] = u[3 * (size_t)pt + s];
-    dpp[s] = dp[3 * (size_t)pt + s];
+    z[9 + s] = (real)vpz[6 * (size_t)v + s];
+    dx[9 + s] = (real)vpz[6 * (size_t)v + 3 + s];
+    uu[s] = (real)u[3 * (size_t)pt + s];
+    dpp[s] = (real)dp[3 * (size_t)pt + s];
   }
   // z~: z' with the point part replaced by zeta of the physical point on a corrected step
-  double zp[3];
+  real zp[3];
 #pragma unroll
-  for (int s = 0; s < 3; ++s) zp[s] = corr ? zeta[3 * (size_t)pt + s] : z[9 + s];
+  for (int s = 0; s < 3; ++s) zp[s] = corr ? (real)zeta[3 * (size_t)pt + s] : z[9 + s];
   // J z', J z~, J dx', J U, J DP, rho = f + J_c dc
-  double Jz[2], Jzt[2], Jdx[2], JU[2], JDP[2], rho[2];
+  real Jz[2], Jzt[2], Jdx[2], JU[2], JDP[2], rho[2];
 #pragma unroll
   for (int t = 0; t < 2; ++t) {
-    double a = 0, cdc = 0;
+    real a = 0, cdc = 0;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       a += Jc[t][c] * z[c];
       cdc += Jc[t][c] * dx[c];
     }
-    double pz = 0, pzt = 0, pdx = 0, pu = 0, pdp = 0;
+    real pz = 0, pzt = 0, pdx = 0, pu = 0, pdp = 0;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
       pz += Jp[t][s] * z[9 + s];
@@ -277,32 +289,33 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
     JDP[t] = pdp;
     rho[t] = f[t] + cdc;
   }
-  const double g0 = Jzt[0] + JU[0], g1 = Jzt[1] + JU[1];
+  const real g0 = Jzt[0] + JU[0], g1 = Jzt[1] + JU[1];
   {
     double* qb = qbar + 2 * (size_t)perm[o];
-    qb[0] += g0;
-    qb[1] += g1;
+    qb[0] += (double)g0;
+    qb[1] += (double)g1;
   }
-  double acc[12];
+  real acc[12];
 #pragma unroll
   for (int c = 0; c < 9; ++c) acc[c] = Jc[0][c] * g0 + Jc[1][c] * g1;
 #pragma unroll
   for (int s = 0; s < 3; ++s) acc[9 + s] = Jp[0][s] * g0 + Jp[1][s] * g1;
   // damping weights 2 lambda (z' o dx' + U o DP), times the rows of J below
-  double wdm[12];
+  const real lam2 = (real)(2.0 * lam);
+  real wdm[12];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) wdm[c] = 2.0 * lam * z[c] * dx[c];
+  for (int c = 0; c < 9; ++c) wdm[c] = lam2 * z[c] * dx[c];
 #pragma unroll
   for (int s = 0; s < 3; ++s)
-    wdm[9 + s] = 2.0 * lam * (z[9 + s] * dx[9 + s] + uu[s] * dpp[s]) - (corr ? 2.0 * kappa[3 * (size_t)v + s] : 0.0);
-  double al0, al1, beta[12];
+    wdm[9 + s] = lam2 * (z[9 + s] * dx[9 + s] + uu[s] * dpp[s]) - (corr ? real(2) * (real)kappa[3 * (size_t)v + s] : real(0));
+  real al0, al1, beta[12];
   const int ndir = corr ? 7 : 6;
 #pragma unroll 1
   for (int dir = 0; dir < ndir; ++dir) {
     switch (dir) {
       case 0:   // (f + J dx', z'), or (f, z~) on a corrected step
-        al0 = f[0] + (corr ? 0.0 : Jdx[0]);
-        al1 = f[1] + (corr ? 0.0 : Jdx[1]);
+        al0 = f[0] + (corr ? real(0) : Jdx[0]);
+        al1 = f[1] + (corr ? real(0) : Jdx[1]);
 #pragma unroll
         for (int c = 0; c < 9; ++c) beta[c] = z[c];
 #pragma unroll
@@ -324,7 +337,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
         al0 = JDP[0] + rho[0];
         al1 = JDP[1] + rho[1];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) beta[c] = 0.0;
+        for (int c = 0; c < 9; ++c) beta[c] = real(0);
 #pragma unroll
         for (int s = 0; s < 3; ++s) beta[9 + s] = uu[s];
         break;
@@ -338,19 +351,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_obs(DevProblem P, const int
         break;
       default: {   // (e_s, J[s,:] o wdm), s = dir - 4: the damping (and, corrected, the kappa) terms
         const int s = dir - 4;
-        al0 = s == 0 ? 1.0 : 0.0;
-        al1 = s == 0 ? 0.0 : 1.0;
+        al0 = s == 0 ? real(1) : real(0);
+        al1 = s == 0 ? real(0) : real(1);
 #pragma unroll
         for (int c = 0; c < 9; ++c) beta[c] = (s == 0 ? Jc[0][c] : Jc[1][c]) * wdm[c];
 #pragma unroll
         for (int k = 0; k < 3; ++k) beta[9 + k] = (s == 0 ? Jp[0][k] : Jp[1][k]) * wdm[9 + k];
       }
     }
-    hess_vec(C, X, uo, vo, al0, al1, beta, acc);
+    hess_vec<real>(C, X, uo, vo, al0, al1, beta, acc);
   }
   double* To = T + 12 * (size_t)o;
 #pragma unroll
-  for (int c = 0; c < 12; ++c) To[c] = acc[c];
+  for (int c = 0; c < 12; ++c) To[c] = (double)acc[c];
 }
 
 // a_c -= sum_o T_o[0:9] over the camera's observations (one CTA per camera, fixed-order reduction).
@@ -405,13 +418,13 @@ void launch_adjoint_step(const DevProblem& P, Scratch<real> W, CamLists CL, cons
   // a^_c into the padded layout of b' (its padding rows stay zero), then z_c = S'^-1 a^_c
   int64_t v_total = fb.v_total;
   cudaMemsetAsync(W.b, 0, (size_t)v_total * sizeof(double), stream);
-  k_adj_cam_rhs<<<P.m, ADJ_THREADS, 0, stream>>>(P, CL, A.u, A.a_c, W.b);
+  k_adj_cam_rhs<real><<<P.m, ADJ_THREADS, 0, stream>>>(P, CL, A.u, A.a_c, W.b);
   launch_solve<real>(P, W.S, W.b, fb, plan, refine_steps, A.zc, nullptr, stream);
   cudaMemsetAsync(A.vpz, 0, 6 * (size_t)P.nv * sizeof(double), stream);
-  k_adj_vp<<<(P.q + 255) / 256, 256, 0, stream>>>(P, A.zc, W.dc, A.vpz);
+  k_adj_vp<real><<<(P.q + 255) / 256, 256, 0, stream>>>(P, A.zc, W.dc, A.vpz);
   k_adj_vp_final<real><<<std::min((P.nv + 255) / 256, 4096), 256, 0, stream>>>(P.nv, W.vp_info, A.vpz);
   if (corrected) k_adj_zeta<real><<<pblocks, 256, 0, stream>>>(P, W.vp_acc, A.vpz, A.zeta, A.kappa);
-  k_adj_obs<<<(P.q + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, stream>>>(
+  k_adj_obs<real><<<(P.q + ADJ_THREADS - 1) / ADJ_THREADS, ADJ_THREADS, 0, stream>>>(
       P, perm, lam, W.dc, W.dp, A.zc, A.u, A.vpz, corrected, A.zeta, A.kappa, A.T, A.qbar);
   k_adj_cam_reduce<<<P.m, ADJ_THREADS, 0, stream>>>(CL, A.T, A.a_c);
   k_adj_pt_reduce<<<pblocks, 256, 0, stream>>>(P, A.T, A.a_p);

@@ -272,7 +272,7 @@ DevProblem dev_problem(const stba_ctx* c) {
   P.res_f = c->mixed ? (const float*)c->res_cur : nullptr;
   P.res_d = c->mixed ? nullptr : (const double*)c->res_cur;
   P.base_pos = c->inv[c->inv_cur];
-  P.pair_recompute = c->opt.pair_blocks == STBA_PAIR_BLOCKS_RECOMPUTE ? 1 : 0;
+  P.pair_recompute = c->opt.pair_blocks == STBA_PAIR_BLOCKS_STORED ? 0 : 1;   // recomputed by default
   P.sharded = c->shard_world > 1 ? 1 : 0;
   P.cluster_owned = c->cl_owned;
   return P;
@@ -1616,7 +1616,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = dalloc(c, &vg, 9 * (size_t)m * rs)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &ta, 3 * (size_t)n * rs)) != STBA_OK) return bail(s);
     // the stored G_o of the camera pass, only when the pair pass reads them (option pair_blocks)
-    const bool stored_g = !c->use_pcg && c->opt.pair_blocks != STBA_PAIR_BLOCKS_RECOMPUTE;
+    const bool stored_g = !c->use_pcg && c->opt.pair_blocks == STBA_PAIR_BLOCKS_STORED;
     if ((s = dalloc(c, &gb, (stored_g ? 36 * Q : 1) * rs)) != STBA_OK) return bail(s);
     c->vp_acc = vpa;
     c->vp_info = vpi;

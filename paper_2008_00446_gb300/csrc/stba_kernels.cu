@@ -20,6 +20,7 @@
 
 #include "stba_camera.cuh"
 #include "stba_device.cuh"
+#include "stba_strict.cuh"
 #include "stba_internal.cuh"
 
 namespace stba {
@@ -64,10 +65,18 @@ __global__ void __launch_bounds__(256) k_vp_reduce(DevProblem P, real* vp_acc) {
     real uo, vo;
     load_uv(P, o, uo, vo);
     real r[2], Jc[2][9], Jp[2][3];
-    project_jacobian<real, false>(C, X, uo, vo, r, Jc, Jp);
+    // FP32: the strict rows, bitwise those of the camera and pair passes
+    if constexpr (sizeof(real) == 4)
+      project_jacobian_strict<false>(C, X, uo, vo, Jc, Jp);
+    else
+      project_jacobian<real, false>(C, X, uo, vo, r, Jc, Jp);
     r[0] = res_ptr<real>(P)[2 * (size_t)o];
     r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
-    const real sw = huber_sqrt_weight<real>(P.huber_a, r[0], r[1]);   // 1 without a robust loss
+    real sw;   // 1 without a robust loss
+    if constexpr (sizeof(real) == 4)
+      sw = huber_sqrt_weight_strict(P.huber_a, r[0], r[1]);
+    else
+      sw = huber_sqrt_weight<real>(P.huber_a, r[0], r[1]);
     r[0] *= sw;
     r[1] *= sw;
 #pragma unroll
@@ -256,7 +265,11 @@ void launch_failed_io(DevState* st, double* x, int to_double, cudaStream_t strea
 // 32 terms, error <= 5 ulp of the sum of magnitudes) and adds them atomically into the FP64 S', b' and v
 // (zeroed before the launch): FP32 terms, FP64 accumulation across warps.  The per-observation arithmetic
 // stays off the FP64 pipe, which on this GPU runs at 1/64 of the FP32 rate.  It also stores G_o of every
-// observation of a multi-observation virtual point for the pair pass.
+// observation of a multi-observation virtual point for the pair pass, unless the pair pass recomputes G_o.
+// In FP32 both passes evaluate the Jacobian rows with every operation rounded on its own (stba_strict.cuh):
+// the diagonal and off-diagonal blocks of a virtual point then come from bitwise the same J_c, J_p and G_o
+// whether G_o is stored or recomputed, and the FP32 S' does not change with the compiler's choice of
+// fused multiply-adds in the surrounding code.
 // G_o is stored column by column, four reals per camera-parameter column c (G[0][c], G[1][c], G[2][c], 0),
 // so that the pair pass reads a column with one 16-byte (FP32) load.
 constexpr int GSTRIDE = 36;   // reals per stored G_o
@@ -333,7 +346,32 @@ __device__ __forceinline__ void g_of_obs(const real* Li, const real (&Jc)[2][9],
     for (int s = 0; s < 3; ++s) G[s][c] = fma_rn(Pm[s][1], Jc[1][c], mul_rn(Pm[s][0], Jc[0][c]));
 }
 
-template <typename real>
+// J_c and J_p of the observation at sorted position o, seen by camera C, scaled by the Huber weight of the
+// stored residual f_o (returned, scaled, in r).  STRICT (FP32 only): every operation rounded on its own, so
+// that the camera pass and the pair pass form bitwise the same rows.
+template <typename real, bool STRICT>
+__device__ __forceinline__ void obs_jacobian(const DevProblem& P, const Cam<real>& C, int o, real (&r)[2],
+                                             real (&Jc)[2][9], real (&Jp)[2][3]) {
+  static_assert(!STRICT || sizeof(real) == 4, "the strict rounding mode is FP32 only");
+  real X[3], uo, vo;
+  load_point_w(P, P.obs_pt[o], X);
+  load_uv(P, o, uo, vo);
+  if constexpr (STRICT)
+    project_jacobian_strict(C, X, uo, vo, Jc, Jp);
+  else
+    project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
+  r[0] = res_ptr<real>(P)[2 * (size_t)o];
+  r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
+  real sw;
+  if constexpr (STRICT)
+    sw = huber_sqrt_weight_strict(P.huber_a, r[0], r[1]);
+  else
+    sw = huber_sqrt_weight<real>(P.huber_a, r[0], r[1]);
+  scale_rows(sw, r, Jc, Jp);
+}
+
+// STRICT (the FP32 pass): the Jacobian rows with every operation rounded on its own, as in the pair pass.
+template <typename real, bool STRICT>
 __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_cam_pass(DevProblem P, Scratch<real> W, CamSlots CS, real* Gbuf,
                                                   const DevState* st) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -351,14 +389,8 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_cam_pass(Dev
     const Cam<real> C = load_cam_w<real>(P, j);
     const int v = P.obs_vp[o];
     const bool single = (P.vp_off[v + 1] - P.vp_off[v]) == 1;
-    real X[3];
-    load_point_w(P, P.obs_pt[o], X);
-    real uo, vo, Jp[2][3];
-    load_uv(P, o, uo, vo);
-    project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
-    r[0] = res_ptr<real>(P)[2 * (size_t)o];
-    r[1] = res_ptr<real>(P)[2 * (size_t)o + 1];
-    scale_rows(huber_sqrt_weight<real>(P.huber_a, r[0], r[1]), r, Jc, Jp);
+    real Jp[2][3];
+    obs_jacobian<real, STRICT>(P, C, o, r, Jc, Jp);
     const real* vi = W.vp_info + 9 * (size_t)v;
     // Both cases reduce to Jc^T N Jc with a 2x2 N:
     //   single observation  N = (I + Jp Lambda^-1 Jp^T)^-1                 (Woodbury, no cancellation)
@@ -488,17 +520,12 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // G_o = L_v^-1 Jp,o^T Jc,o (3 x 9) of the observation at sorted position pos by camera cam, written by columns
 // (G[0][c], G[1][c], G[2][c], 0) to dst: the camera pass's arithmetic (Jacobians at the current x, Huber
-// weights from the stored residual, L_v^-1 of the virtual point's damped block).
-template <typename real>
+// weights from the stored residual, L_v^-1 of the virtual point's damped block); STRICT as in the camera pass.
+template <typename real, bool STRICT>
 __device__ __forceinline__ void obs_G(const DevProblem& P, const Scratch<real>& W, int cam, int pos, real* dst) {
   const Cam<real> C = load_cam_w<real>(P, cam);
-  real X[3], uo, vo, r[2], Jc[2][9], Jp[2][3];
-  load_point_w(P, P.obs_pt[pos], X);
-  load_uv(P, pos, uo, vo);
-  project_jacobian<real, true>(C, X, uo, vo, r, Jc, Jp);
-  r[0] = res_ptr<real>(P)[2 * (size_t)pos];
-  r[1] = res_ptr<real>(P)[2 * (size_t)pos + 1];
-  scale_rows(huber_sqrt_weight<real>(P.huber_a, r[0], r[1]), r, Jc, Jp);
+  real r[2], Jc[2][9], Jp[2][3];
+  obs_jacobian<real, STRICT>(P, C, pos, r, Jc, Jp);
   real Pm[3][2], Gm[3][9];
   g_of_obs<real>(W.vp_info + 9 * (size_t)P.obs_vp[pos], Jc, Jp, Pm, Gm);
 #pragma unroll
@@ -539,7 +566,7 @@ __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scra
       real* dst = stage + ((size_t)(buf * CH + j) * 2 + side) * GSTRIDE;
       if constexpr (RECOMPUTE) {   // computed here: no G buffer, about 90 bytes read per pair instead of 288
         const int b = side ? pr.y : pr.x;
-        obs_G<real>(P, W, side ? chunk.y : chunk.x, P.base_pos[b], dst);
+        obs_G<real, sizeof(real) == 4>(P, W, side ? chunk.y : chunk.x, P.base_pos[b], dst);
       } else {
         const real* src = Gbuf + (size_t)GSTRIDE * (side ? pr.y : pr.x);
 #pragma unroll
@@ -627,7 +654,8 @@ __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scra
 template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
                       cudaStream_t stream) {
-  k_cam_pass<real><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
+  // FP32: both passes take the strict Jacobian rows, so that stored and recomputed G_o are bitwise equal
+  k_cam_pass<real, sizeof(real) == 4><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
   if (B.nchunks > 0 && P.l < P.m) {   // a fixed grid walks the list of chunks inside clusters
     const int grid = std::min((B.nchunks + PB_WARPS - 1) / PB_WARPS, 3 * num_sms());
     if (P.pair_recompute)

@@ -1,0 +1,71 @@
+// FP32 numbers whose every operation is rounded on its own (no fused multiply-add contraction): the
+// arithmetic of an expression is then fixed by its source, whatever the surrounding kernel.  The camera pass
+// and the pair pass both evaluate the reprojection Jacobian of an observation (Sec. 3) on this type when the
+// pair pass recomputes G_o = L_v^-1 J_p^T J_c instead of reading the camera pass's copy, so that the diagonal
+// and off-diagonal blocks of S'_k (Eq. 10, 13) are formed from bitwise the same J_c, J_p and G_o.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "stba_camera.cuh"
+
+namespace stba {
+
+struct SF {
+  float v;
+  SF() = default;
+  __host__ __device__ constexpr SF(float x) : v(x) {}
+
+  friend __device__ __forceinline__ SF operator+(SF a, SF b) { return SF(__fadd_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ SF operator-(SF a, SF b) { return SF(__fsub_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ SF operator-(SF a) { return SF(-a.v); }
+  friend __device__ __forceinline__ SF operator*(SF a, SF b) { return SF(__fmul_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ SF operator/(SF a, SF b) { return SF(__fdiv_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ bool operator<(SF a, SF b) { return a.v < b.v; }
+
+  friend __device__ __forceinline__ SF sq_root(SF a) { return SF(__fsqrt_rn(a.v)); }
+  friend __device__ __forceinline__ void sin_cos(SF x, SF* s, SF* c) {
+    float sv, cv;
+    sincosf(x.v, &sv, &cv);
+    *s = SF(sv);
+    *c = SF(cv);
+  }
+};
+
+template <> struct RodSeries<SF> { static constexpr float cut = RodSeries<float>::cut; };
+
+// Residual-free Jacobian rows J_c (2 x 9, want_cam only) and J_p (2 x 3) of one observation in FP32, every
+// operation rounded on its own (J_p does not depend on want_cam).
+template <bool want_cam = true>
+__device__ __forceinline__ void project_jacobian_strict(const Cam<float>& C, const float X[3], float u_obs,
+                                                        float v_obs, float Jc[2][9], float Jp[2][3]) {
+  Cam<SF> Cs;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    Cs.w[k] = SF(C.w[k]);
+    Cs.t[k] = SF(C.t[k]);
+  }
+  Cs.f = SF(C.f);
+  Cs.k1 = SF(C.k1);
+  Cs.k2 = SF(C.k2);
+  const SF Xs[3] = {SF(X[0]), SF(X[1]), SF(X[2])};
+  SF r[2], Jcs[2][9], Jps[2][3];
+  project_jacobian<SF, want_cam>(Cs, Xs, SF(u_obs), SF(v_obs), r, Jcs, Jps);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    if constexpr (want_cam) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) Jc[t][c] = Jcs[t][c].v;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Jp[t][c] = Jps[t][c].v;
+  }
+}
+
+// sqrt(rho'(|f|^2)) of the Huber loss (1 without a robust loss), every operation rounded on its own.
+__device__ __forceinline__ float huber_sqrt_weight_strict(double a, float r0, float r1) {
+  if (!(a > 0.0)) return 1.f;
+  const float s = __fadd_rn(__fmul_rn(r0, r0), __fmul_rn(r1, r1)), ar = (float)a;
+  return s <= __fmul_rn(ar, ar) ? 1.f : __fsqrt_rn(__fdiv_rn(ar, __fsqrt_rn(s)));
+}
+
+}  // namespace stba

@@ -11,9 +11,10 @@ adjoint.  Tolerances:
     |fd| + 1e-3 max|g|, as for the oracle's own pin.  The runs start at lambda0 = 0.03: at smaller damping
     the gauge directions of the camera-centre loss are nearly free and FP64 rounding of the forward map
     dominates a central difference.
-  - Mixed mode vs the FP64 oracle: 1e-3 norm-wise, the bar of the mixed-mode forward step.  The adjoint
-    kernels compute in FP64 but reuse the forward step's FP32 virtual-point and point factors and its
-    FP32 cluster factors (refined once in FP64); measured ~1.5e-5 on the sub-scene.
+  - Mixed mode vs the FP64 oracle: 1e-3 norm-wise, the bar of the mixed-mode forward step.  The adjoint's
+    per-observation products (Jacobians and their dual-number derivatives) run in FP32 like the forward
+    step's, its vectors and sums in FP64; it reuses the forward step's FP32 virtual-point, point and cluster
+    factors (refined once in FP64); measured ~1.5e-5 on the sub-scene.
   - Full-size directional derivative (FP64): 1e-5 relative; measured ~3e-8 with an observation step 1e-3.
 Runs that start at lambda0 >= 0.1 differentiate accepted steps taken with the steepest-descent correction
 (Sec. 4.3) against the same bars."""
