@@ -108,7 +108,7 @@ struct stba_ctx {
   int* fail_flags = nullptr;
 
   // scratch (real = float in mixed mode, double in FP64 mode)
-  void *vp_acc = nullptr, *vp_info = nullptr, *pt_info = nullptr, *S = nullptr, *b = nullptr, *vgrad = nullptr,
+  void *vp_acc = nullptr, *vp_info = nullptr, *pt_info = nullptr, *pt_acc = nullptr, *S = nullptr, *b = nullptr, *vgrad = nullptr,
        *t_acc = nullptr;
   double *dc = nullptr, *dp = nullptr, *partial = nullptr, *cam_rt = nullptr;
   float *cam_df = nullptr, *pt_df = nullptr;   // double-float tables of the mixed-mode cost
@@ -284,6 +284,7 @@ Scratch<real> scratch(const stba_ctx* c) {
   W.vp_acc = (real*)c->vp_acc;
   W.vp_info = (real*)c->vp_info;
   W.pt_info = (real*)c->pt_info;
+  W.pt_acc = (real*)c->pt_acc;
   W.S = (double*)c->S;
   W.b = (double*)c->b;
   W.vgrad = (real*)c->vgrad;
@@ -566,9 +567,9 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
       factor_launches += (c->h_panel_off[kt + 1] > c->h_panel_off[kt]) + (c->h_update_off[kt + 1] > c->h_update_off[kt]);
     const int build_launches = 1 + (c->pchunks.nchunks > 0 && l < m ? 1 : 0);
     const int solve_launches = 2 + c->set.refine_steps * (2 + (res_items.empty() ? 0 : 1));
-    // iter_begin, vp_reduce, vp_finalize | build | factor | solve, count | rhs, update, cam_rt, (cam_df,
-    // point_df,) cost, finalize, apply
-    c->launches_per_iter = 3 + build_launches + factor_launches + solve_launches + 1 + 6 + (c->mixed ? 3 : 0);
+    // iter_begin, vp_reduce, pt_acc, vp_finalize | build | factor | solve, count | rhs, update, cam_rt,
+    // (cam_df, point_df,) cost, finalize, apply
+    c->launches_per_iter = 4 + build_launches + factor_launches + solve_launches + 1 + 6 + (c->mixed ? 3 : 0);
     c->factor_flops = 0;
     for (int k = 0; k < l; ++k) c->factor_flops += std::pow((double)c->h_nk[k], 3) / 3.0;
   }
@@ -721,7 +722,7 @@ void enqueue_step(stba_ctx* c, bool stages) {
   cudaMemsetAsync(c->t_acc, 0, 3 * (size_t)c->n * rs, s);
   cudaMemsetAsync(c->fail_flags, 0, (size_t)c->l * sizeof(int), s);
   launch_vp_reduce<real>(P, W, s);
-  launch_vp_finalize<real>(P, W, c->st, s);
+  launch_vp_finalize<real>(P, W, c->st, c->counts, s);
   mark(1);
   // stage 1: S' and b'
   launch_rcs_build<real>(P, W, c->cslots, c->pchunks, (real*)c->Gbuf, c->st, s);
@@ -768,7 +769,7 @@ int enqueue_pcg_iteration(stba_ctx* c) {
     cudaMemsetAsync(c->vgrad, 0, 9 * (size_t)c->m * sizeof(real), s);
   }
   launch_vp_reduce<real>(P, W, s);
-  launch_vp_finalize<real>(P, W, c->st, s);
+  launch_vp_finalize<real>(P, W, c->st, c->counts, s);
   record_stage(c, 1);
   if (c->use_spcg) {   // the camera pass alone: b', v and the diagonal blocks of S'
     PairChunks none = c->pchunks;
@@ -873,7 +874,7 @@ stba_status run_sharded_iteration(stba_ctx* c) {
   launch_vp_reduce<real>(P, W, s);   // this process's observations only
   launch_pt_sums<real>(P, W, c->xch, s);
   if ((st = shard_exchange(c, c->xch, 9 * (int64_t)c->n, 0)) != STBA_OK) return st;
-  launch_vp_finalize<real>(P, W, c->st, s, c->xch);
+  launch_vp_finalize<real>(P, W, c->st, c->counts, s, c->xch);
   record_stage(c, 1);
   launch_rcs_build<real>(P, W, c->cslots, c->pchunks, (real*)c->Gbuf, c->st, s);
   record_stage(c, 2);
@@ -1546,12 +1547,14 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
         base_uvdf[bo] = make_float4(uh, (float)(u - (double)uh), vh, (float)(v - (double)vh));
       }
     }
-    std::vector<int> cam_off(m + 1, 0), cam_base(Q), cam_warp_off(m + 1, 0), warp_cam;
+    std::vector<int> cam_off(m + 1, 0), cam_base(Q), ecam(Q), cam_warp_off(m + 1, 0), warp_cam;
     for (size_t bo = 0; bo < Q; ++bo) cam_off[base_cam[bo] + 1]++;
     for (int64_t j = 0; j < m; ++j) cam_off[j + 1] += cam_off[j];
     {
       std::vector<int> f(cam_off.begin(), cam_off.end() - 1);
       for (size_t bo = 0; bo < Q; ++bo) cam_base[f[base_cam[bo]]++] = (int)bo;
+      for (int64_t j = 0; j < m; ++j)
+        for (int e = cam_off[j]; e < cam_off[j + 1]; ++e) ecam[e] = (int)j;
     }
     for (int64_t j = 0; j < m; ++j) {
       const int nw = (cam_off[j + 1] - cam_off[j] + 31) / 32;
@@ -1563,7 +1566,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     A.q = (int)q;
     A.n = (int)n;
     A.m = (int)m;
-    int *d_base_cam, *d_base_src, *d_cam_off, *d_cam_base, *d_cam_warp_off, *d_warp_cam, *d_cam_obs, *d_slots;
+    int *d_base_cam, *d_base_src, *d_cam_off, *d_cam_base, *d_ecam, *d_eo, *d_nsing, *d_cam_warp_off, *d_warp_cam,
+        *d_cam_obs, *d_slots;
     double* d_base_uv;
     if ((s = upload(c, &c->obs_pt, base_pt)) != STBA_OK) return bail(s);
     if ((s = upload(c, &c->pt_off, c->h_pt_off)) != STBA_OK) return bail(s);
@@ -1572,6 +1576,9 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = upload(c, &d_base_uv, base_uv)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_cam_off, cam_off)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_cam_base, cam_base)) != STBA_OK) return bail(s);
+    if ((s = upload(c, &d_ecam, ecam)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &d_eo, Q)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &d_nsing, Q)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_cam_warp_off, cam_warp_off)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_warp_cam, warp_cam)) != STBA_OK) return bail(s);
     A.base_uvf = nullptr;
@@ -1609,10 +1616,11 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     }
     // per-iteration scratch (virtual-point arrays at their largest size, nv <= q)
     const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
-    char *vpa, *vpi, *pti, *vg, *ta, *gb;
+    char *vpa, *vpi, *pti, *pta, *vg, *ta, *gb;
     if ((s = dalloc(c, &vpa, 9 * Q * rs + 16)) != STBA_OK) return bail(s);   // zeroed in 16-byte pieces
     if ((s = dalloc(c, &vpi, 9 * Q * rs)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &pti, 9 * (size_t)n * rs)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &pta, 9 * (size_t)n * rs)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &vg, 9 * (size_t)m * rs)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &ta, 3 * (size_t)n * rs)) != STBA_OK) return bail(s);
     // the stored G_o of the camera pass, only when the pair pass reads them (option pair_blocks)
@@ -1621,6 +1629,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     c->vp_acc = vpa;
     c->vp_info = vpi;
     c->pt_info = pti;
+    c->pt_acc = pta;
     c->vgrad = vg;
     c->t_acc = ta;
     c->Gbuf = gb;
@@ -1642,6 +1651,9 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     A.pt_vp_off = c->pt_vp_off;
     A.cam_off = d_cam_off;
     A.cam_base = d_cam_base;
+    A.ecam = d_ecam;
+    A.eo = d_eo;
+    A.nsing = d_nsing;
     A.cam_warp_off = d_cam_warp_off;
     A.cam_obs = d_cam_obs;
     A.slots = d_slots;

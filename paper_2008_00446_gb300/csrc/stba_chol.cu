@@ -163,7 +163,8 @@ __device__ __forceinline__ void chol8(F (*Ad)[LDA], int b0, int row0, int nk, F*
 }
 
 // ------------------------------------------------------------------------------------------------------
-// Panel of tile step kt, one CTA per tile row i >= kt of a cluster (256 threads):
+// Panel of tile step kt, one CTA per tile row i >= kt of a cluster (512 threads: the diagonal tile's work on
+// threads 0..255, the row tile's on threads 256..511, wherever the two are independent):
 //   1. fused update from step kt - 1 (kt > 0):  A_kt,kt -= L_kt,kt-1 L_kt,kt-1^T,  A_i,kt -= L_i,kt-1 L_kt,kt-1^T
 //      (the trailing update of the other tiles of step kt - 1 runs concurrently in k_chol_update);
 //   2. LL^T of the stacked panel [A_kt,kt; A_i,kt] in blocks of 8 columns (the diagonal tile redundantly
@@ -173,6 +174,8 @@ __device__ __forceinline__ void chol8(F (*Ad)[LDA], int b0, int row0, int nk, F*
 //      out as L_i,kt.  The CTA of i = kt stores L_kt,kt, the others L_i,kt.
 // Dynamic shared memory: Ad, Ax (T x (T + 1)) and two T x LDV buffers for the transposed tiles of the
 // fused update.
+constexpr int PANEL_THREADS = 512;
+
 template <typename F, int T>
 struct PanelLayout {
   static constexpr int LDA = T + 1;
@@ -181,7 +184,7 @@ struct PanelLayout {
 };
 
 template <typename F, int T>
-__global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P, const int2* items, int kt,
+__global__ void __launch_bounds__(PANEL_THREADS) k_chol_panel(F* L, F* Ldiag, DevProblem P, const int2* items, int kt,
                                                     int* fail_flags, int* boosted) {
   using PL = PanelLayout<F, T>;
   constexpr int R = T / 16, LDA = PL::LDA, LDV = PL::LDV, NB = T / 8;
@@ -198,11 +201,12 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
   const int np = P.cluster_np[k], nk = P.cluster_n[k];
   F* A = L + P.S_off[k];
   const int tid = threadIdx.x;
-  const int bi = tid & 15, bj = tid >> 4;
+  // fused update: threads 0..255 form the diagonal tile's product, threads 256..511 the row tile's
+  const int half = tid >> 8, bi = tid & 15, bj = (tid & 255) >> 4;
   const size_t base_kk = (size_t)(kt * T) * np + kt * T;
   const size_t base_ik = (size_t)(i * T) * np + kt * T;
   // 1. loads; the upper part of the diagonal tile is never stored, so it is set to zero
-  for (int idx = tid; idx < T * T; idx += 256) {
+  for (int idx = tid; idx < T * T; idx += PANEL_THREADS) {
     const int r = idx / T, c = idx - (idx / T) * T;
     if (c <= r)
       cp_async_elem(&Ad[r][c], A + base_kk + (size_t)r * np + c);
@@ -217,42 +221,41 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
   cp_async_wait_all();
   __syncthreads();
   if (kt > 0) {
-    F accD[R][R], accX[R][R];
-#pragma unroll
-    for (int a = 0; a < R; ++a)
-#pragma unroll
-      for (int b = 0; b < R; ++b) accD[a][b] = accX[a][b] = F(0);
-#pragma unroll 4
-    for (int m = 0; m < T; ++m) {
-      F lr[R], lc[R];
-      load_vec<F, R>(&LkT[m][bi * R], lr);
-      load_vec<F, R>(&LkT[m][bj * R], lc);
+    // half 0: A_kt,kt -= L_kt,kt-1 L_kt,kt-1^T (lower part); half 1: A_i,kt -= L_i,kt-1 L_kt,kt-1^T
+    if (half == 0 || !diag) {
+      F acc[R][R];
 #pragma unroll
       for (int a = 0; a < R; ++a)
 #pragma unroll
-        for (int b = 0; b < R; ++b) accD[a][b] += lr[a] * lc[b];
-      if (!diag) {
-        F xr[R];
-        load_vec<F, R>(&LiT[m][bi * R], xr);
+        for (int b = 0; b < R; ++b) acc[a][b] = F(0);
+      F(*Lr)[LDV] = half ? LiT : LkT;
+#pragma unroll 4
+      for (int m = 0; m < T; ++m) {
+        F lr[R], lc[R];
+        load_vec<F, R>(&Lr[m][bi * R], lr);
+        load_vec<F, R>(&LkT[m][bj * R], lc);
 #pragma unroll
         for (int a = 0; a < R; ++a)
 #pragma unroll
-          for (int b = 0; b < R; ++b) accX[a][b] += xr[a] * lc[b];
+          for (int b = 0; b < R; ++b) acc[a][b] += lr[a] * lc[b];
       }
+#pragma unroll
+      for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+          const int r = bi * R + a, c = bj * R + b;
+          if (half)
+            Ax[r][c] -= acc[a][b];
+          else if (c <= r)
+            Ad[r][c] -= acc[a][b];
+        }
     }
-#pragma unroll
-    for (int a = 0; a < R; ++a)
-#pragma unroll
-      for (int b = 0; b < R; ++b) {
-        const int r = bi * R + a, c = bj * R + b;
-        if (c <= r) Ad[r][c] -= accD[a][b];
-        if (!diag) Ax[r][c] -= accX[a][b];
-      }
     __syncthreads();
   }
   // 2. blocked LL^T of the stacked panel.  Per block b: the rows below are solved against L_bb; then warp 0
   //    applies block b's rank-8 update to the next 8 x 8 diagonal block and lane 0 factors it, while warps
-  //    1..7 apply the update to the rest of the tile (look-ahead of one block).
+  //    1..7 apply the update to the rest of the diagonal tile and warps 8..15 to the row tile (look-ahead
+  //    of one block).
   if (tid == 0) chol8<F, LDA>(Ad, 0, kt * T, nk, rinv2[0], fail_flags + k, diag ? boosted : nullptr);
   __syncthreads();
   for (int b = 0; b < NB; ++b) {
@@ -291,17 +294,19 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
       __syncwarp();
       if (tid == 0) chol8<F, LDA>(Ad, n0, kt * T, nk, rinv2[(b + 1) & 1], fail_flags + k, diag ? boosted : nullptr);
     } else {
-      // rank-8 update of the other columns right of the block, register-blocked R x R cells
-      for (int cell = tid - 32; cell < 256; cell += 224) {
+      // rank-8 update of the other columns right of the block, register-blocked R x R cells: warps 1..7
+      // take the diagonal tile's cells, warps 8..15 the row tile's
+      const bool xpart = tid >= 256;
+      for (int cell = xpart ? tid - 256 : tid - 32; cell < 256; cell += xpart ? 256 : 224) {
         const int ci = cell & 15, cj = cell >> 4;
         const int c0 = cj * R, r0 = ci * R;
-        if (c0 + R <= n0) continue;
+        if (c0 + R <= n0 || (xpart && diag)) continue;
         F lc[R][8];
 #pragma unroll
         for (int cc = 0; cc < R; ++cc)
 #pragma unroll
           for (int t = 0; t < 8; ++t) lc[cc][t] = Ad[c0 + cc][b0 + t];
-        if (cj <= ci && r0 + R > n0) {
+        if (!xpart && cj <= ci && r0 + R > n0) {
 #pragma unroll
           for (int a = 0; a < R; ++a) {
             F lr[8];
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
             }
           }
         }
-        if (!diag) {
+        if (xpart) {
 #pragma unroll
           for (int a = 0; a < R; ++a) {
             F xr[8];
@@ -344,13 +349,13 @@ __global__ void __launch_bounds__(256) k_chol_panel(F* L, F* Ldiag, DevProblem P
   // 3. outputs.  L_kk goes to its own buffer: later CTAs of this step may still be loading A_kk from L.
   if (diag) {
     F* Lkk = Ldiag + (size_t)P.v_off[k] * T + (size_t)kt * T * T;
-    for (int idx = tid; idx < T * T; idx += 256) {
+    for (int idx = tid; idx < T * T; idx += PANEL_THREADS) {
       const int r = idx / T, c = idx - (idx / T) * T;
       Lkk[idx] = (c <= r) ? Ad[r][c] : F(0);
     }
     return;
   }
-  for (int idx = tid; idx < T * T; idx += 256) {
+  for (int idx = tid; idx < T * T; idx += PANEL_THREADS) {
     const int r = idx / T, c = idx - (idx / T) * T;
     A[base_ik + (size_t)r * np + c] = Ax[r][c];
   }
@@ -1048,7 +1053,6 @@ __device__ F warp_sum(F v) {
 // diagonal inverses are copied into shared memory (cp.async) while step it computes, `nst` stages deep:
 // three (two steps ahead) when the launch is one wave of CTAs, two otherwise, where the smaller shared
 // memory lets two CTAs share an SM and the waves halve.
-constexpr int SOLVE_CS = 8;   // default CTAs per camera cluster (the option solve_cluster picks 2, 4 or 8)
 constexpr int SOLVE_PF = 2;
 
 template <typename F, int T>
@@ -1347,13 +1351,14 @@ __global__ void k_count_failures(const int* fail_flags, int l, DevState* st) {
 // ------------------------------------------------------------------------------------------------------
 // Host launchers
 
-// A 256-thread launch with a scheduling priority (kept by graph capture as a node attribute): the panels
-// on the critical path go first, the trailing updates fill the remaining SMs.
+// A launch of `threads` threads (256 for launch_prio) with a scheduling priority (kept by graph capture as a
+// node attribute): the panels on the critical path go first, the trailing updates fill the remaining SMs.
 template <typename... KArgs, typename... Args>
-void launch_prio(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t stream, int prio, Args... args) {
+void launch_prio_n(void (*kernel)(KArgs...), int grid, int threads, size_t smem, cudaStream_t stream, int prio,
+                   Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
@@ -1362,6 +1367,11 @@ void launch_prio(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t s
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+void launch_prio(void (*kernel)(KArgs...), int grid, size_t smem, cudaStream_t stream, int prio, Args... args) {
+  launch_prio_n(kernel, grid, 256, smem, stream, prio, args...);
 }
 // A panel CTA is bound by the latency of its column chain: a second panel CTA on the same SM would halve
 // the speed of both.  When a tile step's panels fit on the SMs one each, their dynamic shared memory is
@@ -1429,8 +1439,8 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
       }
     }
     if (stacked && npn > 0)
-      launch_prio(k_chol_panel<F, T>, npn, panel_smem<F, T>(npn), stream, plan.prio_high, L,
-                  reinterpret_cast<F*>(fb.Ldiag), P, pitems, kt, fb.fail_flags, fb.boosted);
+      launch_prio_n(k_chol_panel<F, T>, npn, PANEL_THREADS, panel_smem<F, T>(npn), stream, plan.prio_high, L,
+                    reinterpret_cast<F*>(fb.Ldiag), P, pitems, kt, fb.fail_flags, fb.boosted);
     cudaEventRecord(plan.ev_panel[kt], stream);
     cudaStreamWaitEvent(side, plan.ev_panel[kt], 0);
     const int nu = plan.h_update_off[kt + 1] - plan.h_update_off[kt];

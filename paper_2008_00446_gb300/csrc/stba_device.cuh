@@ -61,6 +61,46 @@ __device__ __forceinline__ void load_point_w(const DevProblem& P, int i, real X[
   }
 }
 
+// Records of 9 reals, one per lane, of cnt <= 32 consecutive records r0.. (r0 a multiple of 32), staged
+// through the warp's 288-real shared buffer sm (16-byte aligned): a full block of 32 records is one
+// contiguous, 16-byte aligned span, moved with 16-byte vector accesses by the whole warp instead of nine
+// strided scalar accesses per lane.  Lanes >= cnt get / store nothing.
+template <typename real>
+__device__ __forceinline__ void warp_load_rec9(const real* __restrict__ g, long long r0, int cnt, real* sm, int lane,
+                                               real (&x)[9]) {
+  const real* blk = g + 9 * r0;
+  if (cnt == 32 && ((reinterpret_cast<size_t>(blk) & 15) == 0)) {
+    constexpr int NQ = 9 * 32 * (int)sizeof(real) / 16;
+    for (int k = lane; k < NQ; k += 32) reinterpret_cast<float4*>(sm)[k] = reinterpret_cast<const float4*>(blk)[k];
+  } else {
+    for (int k = lane; k < 9 * cnt; k += 32) sm[k] = blk[k];
+  }
+  __syncwarp();
+  if (lane < cnt) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) x[c] = sm[9 * lane + c];
+  }
+  __syncwarp();
+}
+
+template <typename real>
+__device__ __forceinline__ void warp_store_rec9(real* __restrict__ g, long long r0, int cnt, real* sm, int lane,
+                                                const real (&x)[9]) {
+  if (lane < cnt) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sm[9 * lane + c] = x[c];
+  }
+  __syncwarp();
+  real* blk = g + 9 * r0;
+  if (cnt == 32 && ((reinterpret_cast<size_t>(blk) & 15) == 0)) {
+    constexpr int NQ = 9 * 32 * (int)sizeof(real) / 16;
+    for (int k = lane; k < NQ; k += 32) reinterpret_cast<float4*>(blk)[k] = reinterpret_cast<const float4*>(sm)[k];
+  } else {
+    for (int k = lane; k < 9 * cnt; k += 32) blk[k] = sm[k];
+  }
+  __syncwarp();
+}
+
 // Inclusive warp scan of NV values restricted to runs of equal (non-decreasing) keys.
 template <int NV, typename real>
 __device__ __forceinline__ void segmented_scan(real (&val)[NV], int key, int lane) {

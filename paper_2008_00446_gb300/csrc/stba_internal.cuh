@@ -85,6 +85,7 @@ template <typename real> struct Scratch {
   real* vp_acc;    // [nv][9]: V = sum Jp^T Jp (6, packed xx xy xz yy yz zz) and w' = -sum Jp^T f (3)
   real* vp_info;   // [nv][9]: L^-1 of V' (6, packed l00 l10 l11 l20 l21 l22) and y = V'^-1 w' (3)
   real* pt_info;   // [n][9]: C^-1 (6, packed symmetric) and w (3) of the physical points
+  real* pt_acc;    // [n][9]: C (6, packed) and w (3) of the physical points, summed over their virtual points
   double* S;       // cluster-diagonal S' (dense lower triangles, per-cluster padded blocks); FP64 sums
   double* b;       // b' (per-cluster padded vectors); FP64 sums
   real* vgrad;     // [m][9] camera gradient v = -J_c^T f
@@ -163,6 +164,10 @@ struct ReorderArgs {
   int *obs_vp, *vp_off, *vp_point, *pt_vp_off;
   const int* cam_off;       // [m+1] observations of every camera
   const int* cam_base;      // [q]   their base positions, ascending
+  const int* ecam;          // [q]   the camera of every entry of cam_base
+  int* eo;                  // [q]   the new position of every entry of cam_base (scratch of the assignment)
+  int* nsing;               // [q]   per base position: its new position, bit 31 set when its virtual point
+                            //       has no other observation (scratch of the assignment)
   const int* cam_warp_off;  // [m+1] warps of every camera in the camera pass
   int* cam_obs;             // [q] new positions, single-observation virtual points first
   int* slots;               // [32 * warps] the same padded to whole warps (-1)
@@ -184,8 +189,8 @@ void launch_iter_begin(DevState* st, const Settings& s, cudaStream_t stream);
 template <typename real>
 void launch_vp_reduce(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
 template <typename real>
-void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream,
-                        const double* pt_sums = nullptr);
+void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, const long long* counts,
+                        cudaStream_t stream, const double* pt_sums = nullptr);
 // Sharded iteration: per point, the sums over this process's virtual points of V (packed 6) and w' (3), FP64
 // [n][9] (the other processes' virtual points are zero here); summed over the processes they are C_i, w_i.
 template <typename real>

@@ -122,90 +122,151 @@ __device__ __forceinline__ double block_max(double v) {
   return r;
 }
 
+// Per point, the sums over its virtual points of V_v and w'_v: C and w of the physical point (Eq. 15).  A warp
+// takes 32 consecutive points; their virtual points are one contiguous range of records, which the warp
+// moves through shared memory 32 records at a time with coalesced loads, each lane adding up its own
+// point's records in order (no atomics: the sums do not depend on the launch).
+template <typename real>
+__global__ void __launch_bounds__(256) k_pt_acc(DevProblem P, const real* __restrict__ vp_acc,
+                                                real* __restrict__ pt_acc) {
+  __shared__ __align__(16) real stage[8][288];
+  const int lane = threadIdx.x & 31;
+  real* sm = stage[threadIdx.x >> 5];
+  const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; w * 32 < P.n; w += wstride) {
+    const long long i0 = w * 32;
+    const int cnt = (int)(P.n - i0 < 32 ? P.n - i0 : 32);
+    const int i = (int)i0 + lane;
+    const long long vb = lane < cnt ? P.pt_vp_off[i] : 0, ve = lane < cnt ? P.pt_vp_off[i + 1] : 0;
+    const long long r0 = __shfl_sync(FULL_MASK, vb, 0), r1 = __shfl_sync(FULL_MASK, ve, cnt - 1);
+    real acc[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) acc[c] = real(0);
+    for (long long r = r0; r < r1; r += 32) {   // records [r, r + nr) of the warp's range
+      const int nr = (int)(r1 - r < 32 ? r1 - r : 32);
+      const real* blk = vp_acc + 9 * r;
+      for (int k = lane; k < 9 * nr; k += 32) sm[k] = blk[k];
+      __syncwarp();
+      const long long ub = vb > r ? vb : r, ue = ve < r + nr ? ve : r + nr;
+      for (long long u = ub; u < ue; ++u)
+#pragma unroll
+        for (int c = 0; c < 9; ++c) acc[c] += sm[9 * (u - r) + c];
+      __syncwarp();
+    }
+    warp_store_rec9(pt_acc, i0, cnt, sm, lane, acc);
+  }
+}
+
+// Warp chunks of 32 virtual points (the first ceil(nv / 32)), then of 32 points; records move through shared
+// memory as whole 16-byte vectors.  Virtual point v: L_v^-1 of V'_v = V_v + lambda diag(V_v) and
+// y_v = V'_v^-1 w'_v, where on a corrected step w'_v = diag(V_v) dbar_i, dbar_i = w_i / diag(C_i) (Sec. 4.3).
+// Point i: C_i^-1 of C_i + lambda diag(C_i), the uncorrected w_i, and max |w| for the stop test.  C_i and w_i
+// come from k_pt_acc, or from pt_sums (FP64, summed over every process's virtual points) when the iteration
+// is sharded.
 template <typename real>
 __global__ void __launch_bounds__(256) k_vp_finalize(DevProblem P, Scratch<real> W, DevState* st,
-                                                     const double* __restrict__ pt_sums) {
+                                                     const double* __restrict__ pt_sums,
+                                                     const long long* __restrict__ counts) {
+  __shared__ __align__(16) real stage[8][288];
   const real lam = (real)st->lambda_used;
   const bool corr = st->corrected != 0;
+  const long long nv = counts[0];
+  const int lane = threadIdx.x & 31;
+  real* sm = stage[threadIdx.x >> 5];
   double gmax = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
-    const int vb = P.pt_vp_off[i], ve = P.pt_vp_off[i + 1];
-    real C[6] = {0, 0, 0, 0, 0, 0}, w[3] = {0, 0, 0};
-    if (pt_sums) {   // sharded: the sums over every process's virtual points of the point, exchanged
+  // C_i (6 packed) and w_i (3) of point i, read directly (corrected steps)
+  auto point_sums = [&](int i, real (&a)[9]) {
+    if (pt_sums) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) C[c] = (real)pt_sums[9 * (size_t)i + c];
+      for (int c = 0; c < 9; ++c) a[c] = (real)pt_sums[9 * (size_t)i + c];
+    } else if (P.pt_vp_off[i] == P.pt_vp_off[i + 1]) {   // no observation
 #pragma unroll
-      for (int c = 0; c < 3; ++c) w[c] = (real)pt_sums[9 * (size_t)i + 6 + c];
+      for (int c = 0; c < 9; ++c) a[c] = real(0);
     } else {
-      for (int v = vb; v < ve; ++v) {
-        const real* a = W.vp_acc + 9 * (size_t)v;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) C[c] += a[c];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) w[c] += a[6 + c];
-      }
+      for (int c = 0; c < 9; ++c) a[c] = W.pt_acc[9 * (size_t)i + c];
     }
-    real dbar[3];
-    dbar[0] = w[0] / C[0];
-    dbar[1] = w[1] / C[3];
-    dbar[2] = w[2] / C[5];
-    for (int v = vb; v < ve; ++v) {
-      const real* a = W.vp_acc + 9 * (size_t)v;
-      real V[6], wv[3];
+  };
+  const long long nvc = (nv + 31) / 32, npc = ((long long)P.n + 31) / 32;
+  const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long ch = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; ch < nvc + npc; ch += wstride) {
+    real a[9], o[9];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) V[c] = a[c];
+    for (int c = 0; c < 9; ++c) a[c] = o[c] = real(0);
+    if (ch < nvc) {
+      const long long v0 = ch * 32, v = v0 + lane;
+      const int cnt = (int)(nv - v0 < 32 ? nv - v0 : 32);
+      warp_load_rec9(W.vp_acc, v0, cnt, sm, lane, a);
+      const bool other = pt_sums && a[0] == real(0) && a[3] == real(0) && a[5] == real(0);   // another process's
+      if (lane < cnt && !other) {
+        real V[6] = {a[0], a[1], a[2], a[3], a[4], a[5]}, wv[3] = {a[6], a[7], a[8]};
+        if (corr) {
+          real s[9];
+          point_sums(P.vp_point[v], s);
+          wv[0] = V[0] * (s[6] / s[0]);
+          wv[1] = V[3] * (s[7] / s[3]);
+          wv[2] = V[5] * (s[8] / s[5]);
+        }
+        V[0] += lam * V[0];
+        V[3] += lam * V[3];
+        V[5] += lam * V[5];
+        real Li[6], y[3];
+        chol3_inv(V, Li);
+        chol3_apply(Li, wv, y);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) wv[c] = a[6 + c];
-      if (pt_sums && V[0] == real(0) && V[3] == real(0) && V[5] == real(0)) {   // another process's cluster
-        real* out = W.vp_info + 9 * (size_t)v;
+        for (int c = 0; c < 6; ++c) o[c] = Li[c];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) out[c] = real(0);
-        continue;
+        for (int c = 0; c < 3; ++c) o[6 + c] = y[c];
       }
-      if (corr) {
-        wv[0] = V[0] * dbar[0];
-        wv[1] = V[3] * dbar[1];
-        wv[2] = V[5] * dbar[2];
+      warp_store_rec9(W.vp_info, v0, cnt, sm, lane, o);
+    } else {
+      // physical point: C + lambda diag(C), its inverse, uncorrected w
+      const long long i0 = (ch - nvc) * 32;
+      const int i = (int)(i0 + lane);
+      const int cnt = (int)(P.n - i0 < 32 ? P.n - i0 : 32);
+      if (pt_sums) {
+        if (lane < cnt) point_sums(i, a);
+      } else {
+        warp_load_rec9(W.pt_acc, i0, cnt, sm, lane, a);
+        if (lane < cnt && P.pt_vp_off[i] == P.pt_vp_off[i + 1]) {   // no observation
+#pragma unroll
+          for (int c = 0; c < 9; ++c) a[c] = real(0);
+        }
       }
-      V[0] += lam * V[0];
-      V[3] += lam * V[3];
-      V[5] += lam * V[5];
-      real Li[6], y[3];
-      chol3_inv(V, Li);
-      chol3_apply(Li, wv, y);
-      real* out = W.vp_info + 9 * (size_t)v;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) out[c] = Li[c];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) out[6 + c] = y[c];
+      if (lane < cnt) {
+        const real Cd[6] = {a[0] * (1 + lam), a[1], a[2], a[3] * (1 + lam), a[4], a[5] * (1 + lam)};
+        real Li[6];
+        chol3_inv(Cd, Li);
+        // C^-1 = L^-T L^-1 (symmetric packed 00 01 02 11 12 22)
+        o[0] = Li[0] * Li[0] + Li[1] * Li[1] + Li[3] * Li[3];
+        o[1] = Li[1] * Li[2] + Li[3] * Li[4];
+        o[2] = Li[3] * Li[5];
+        o[3] = Li[2] * Li[2] + Li[4] * Li[4];
+        o[4] = Li[4] * Li[5];
+        o[5] = Li[5] * Li[5];
+        o[6] = a[6];
+        o[7] = a[7];
+        o[8] = a[8];
+        gmax = fmax(gmax, fmax(fabs((double)a[6]), fmax(fabs((double)a[7]), fabs((double)a[8]))));
+      }
+      warp_store_rec9(W.pt_info, i0, cnt, sm, lane, o);
     }
-    // physical point: C + lambda diag(C), its inverse, uncorrected w
-    real Cd[6] = {C[0] * (1 + lam), C[1], C[2], C[3] * (1 + lam), C[4], C[5] * (1 + lam)};
-    real Li[6];
-    chol3_inv(Cd, Li);
-    // C^-1 = L^-T L^-1 (symmetric packed 00 01 02 11 12 22)
-    real* out = W.pt_info + 9 * (size_t)i;
-    out[0] = Li[0] * Li[0] + Li[1] * Li[1] + Li[3] * Li[3];
-    out[1] = Li[1] * Li[2] + Li[3] * Li[4];
-    out[2] = Li[3] * Li[5];
-    out[3] = Li[2] * Li[2] + Li[4] * Li[4];
-    out[4] = Li[4] * Li[5];
-    out[5] = Li[5] * Li[5];
-    out[6] = w[0];
-    out[7] = w[1];
-    out[8] = w[2];
-    gmax = fmax(gmax, fmax(fabs((double)w[0]), fmax(fabs((double)w[1]), fabs((double)w[2]))));
   }
   double bm = block_max<real>(gmax);
   if (threadIdx.x == 0) atomicMax(&st->grad_max_bits, (unsigned long long)__double_as_longlong(bm));
 }
 
 template <typename real>
-void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, cudaStream_t stream,
-                        const double* pt_sums) {
-  int blocks = (P.n + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  k_vp_finalize<real><<<blocks, 256, 0, stream>>>(P, W, st, pt_sums);
+void launch_vp_finalize(const DevProblem& P, Scratch<real> W, DevState* st, const long long* counts,
+                        cudaStream_t stream, const double* pt_sums) {
+  // grids sized by the largest nv (q); the kernels read nv from the device counter
+  const long long nmax = (long long)P.q + P.n + 31;
+  const long long cap = 8LL * num_sms();
+  if (!pt_sums)
+    k_pt_acc<real><<<(int)std::min<long long>(((long long)P.n + 255) / 256, cap), 256, 0, stream>>>(P, W.vp_acc,
+                                                                                                 W.pt_acc);
+  k_vp_finalize<real><<<(int)std::min<long long>((nmax + 255) / 256, cap), 256, 0, stream>>>(P, W, st, pt_sums,
+                                                                                            counts);
 }
 
 template <typename real>
@@ -1117,8 +1178,8 @@ void configure_kernels(int max_np) {
 #define INSTANTIATE(real)                                                                                  \
   template void launch_iter_begin<real>(DevState*, const Settings&, cudaStream_t);                        \
   template void launch_vp_reduce<real>(const DevProblem&, Scratch<real>, cudaStream_t);                   \
-  template void launch_vp_finalize<real>(const DevProblem&, Scratch<real>, DevState*, cudaStream_t,       \
-                                         const double*);                                                   \
+  template void launch_vp_finalize<real>(const DevProblem&, Scratch<real>, DevState*, const long long*,   \
+                                         cudaStream_t, const double*);                                     \
   template void launch_pt_sums<real>(const DevProblem&, Scratch<real>, double*, cudaStream_t);              \
   template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamSlots, PairChunks, real*,     \
                                        DevState*, cudaStream_t);                                          \

@@ -3,6 +3,8 @@
 // observation lists of the camera pass are rebuilt.  The (point, camera) order fixed at create is the base:
 // inside a point run the new order is the stable sort of the base by cluster, so a virtual point is a run
 // of equal clusters and its observations stay ordered by camera.  Every step is deterministic.
+#include <climits>
+
 #include <cuda_runtime.h>
 
 #include "stba_device.cuh"
@@ -33,15 +35,17 @@ __global__ void k_reorder(ReorderArgs A, const int* __restrict__ key, const real
   const int i = A.obs_pt[bo];
   const int b = A.pt_off[i], e = A.pt_off[i + 1];
   const int kb = key[bo];
-  int rank = 0;
+  int rank = 0, same = 0;
   bool first = true;
   for (int o = b; o < e; ++o) {
     const int ko = key[o];
     rank += (ko < kb) || (ko == kb && o < bo);
     first = first && !(ko == kb && o < bo);
+    same += ko == kb;
   }
   const int np = b + rank;
   A.inv_new[bo] = np;
+  A.nsing[bo] = same == 1 ? (np | INT_MIN) : np;
   A.obs_base[np] = bo;
   A.obs_cam[np] = A.base_cam[bo];
   A.obs_perm[np] = A.base_src[bo];
@@ -168,13 +172,15 @@ __global__ void __launch_bounds__(256) k_vp_close(ReorderArgs A, long long* __re
 }
 
 // Camera lists: the observations of every camera (new positions), those of single-observation virtual
-// points first, each group in base order -- a stable partition of every camera's run of cam_base.  An
-// observation is alone in its virtual point when it starts one and the next observation starts another.
+// points first, each group in base order -- a stable partition of every camera's run of cam_base.  Whether
+// an observation is alone in its virtual point (no other observation of its point in its cluster) comes
+// from k_reorder, packed with its new position.
 __global__ void k_cam_flag(ReorderArgs A, int* __restrict__ flag) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.q) return;
-  const int o = A.inv_new[A.cam_base[e]];
-  flag[e] = (A.start[o] == 1 && (o + 1 == A.q || A.start[o + 1] == 1)) ? 1 : 0;
+  const int x = A.nsing[A.cam_base[e]];   // one gather: the new position and whether it is alone
+  A.eo[e] = x & INT_MAX;                  // for k_cam_place
+  flag[e] = x < 0 ? 1 : 0;
 }
 
 // excl[e] = number of flags before e (tile offsets from k_scan_partials); excl[q] = total
@@ -213,12 +219,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_excl(int q, const int* __
 __global__ void k_cam_place(ReorderArgs A, const int* __restrict__ flag, const int* __restrict__ excl) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= A.q) return;
-  const int j = A.base_cam[A.cam_base[e]];
+  const int j = A.ecam[e];
   const int b = A.cam_off[j], cnt = A.cam_off[j + 1] - b;
   const int before = excl[e] - excl[b];               // singles of camera j before e
   const int nsingle = excl[b + cnt] - excl[b];
   const int idx = flag[e] ? before : nsingle + (e - b - before);
-  const int o = A.inv_new[A.cam_base[e]];
+  const int o = A.eo[e];
   A.cam_obs[b + idx] = o;
   A.slots[32 * A.cam_warp_off[j] + idx] = o;
 }

@@ -1,8 +1,10 @@
-// FP32 numbers whose every operation is rounded on its own (no fused multiply-add contraction): the
-// arithmetic of an expression is then fixed by its source, whatever the surrounding kernel.  The camera pass
-// and the pair pass both evaluate the reprojection Jacobian of an observation (Sec. 3) on this type when the
-// pair pass recomputes G_o = L_v^-1 J_p^T J_c instead of reading the camera pass's copy, so that the diagonal
-// and off-diagonal blocks of S'_k (Eq. 10, 13) are formed from bitwise the same J_c, J_p and G_o.
+// FP32 numbers whose rounding is fixed by the source: a product is held unrounded (SFProd) and fused with
+// the addition or subtraction it meets (one fused multiply-add, __fmaf_rn), every other operation is rounded
+// on its own (__fadd_rn, __fmul_rn, ...), and the compiler contracts or re-associates nothing.  The
+// arithmetic of an expression is then the same in every kernel that evaluates it.  The FP32 kernels that form
+// V_v, the diagonal and the off-diagonal blocks of S'_k (Eq. 10, 13) all evaluate the reprojection Jacobian
+// of an observation (Sec. 3) on this type, so that they see bitwise the same J_c, J_p (and G_o =
+// L_v^-1 J_p^T J_c, whether the pair pass reads the camera pass's copy or recomputes it).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -10,15 +12,18 @@
 
 namespace stba {
 
+struct SFProd;
+
 struct SF {
   float v;
   SF() = default;
   __host__ __device__ constexpr SF(float x) : v(x) {}
+  __device__ __forceinline__ SF(const SFProd& p);   // the product, rounded
 
   friend __device__ __forceinline__ SF operator+(SF a, SF b) { return SF(__fadd_rn(a.v, b.v)); }
   friend __device__ __forceinline__ SF operator-(SF a, SF b) { return SF(__fsub_rn(a.v, b.v)); }
   friend __device__ __forceinline__ SF operator-(SF a) { return SF(-a.v); }
-  friend __device__ __forceinline__ SF operator*(SF a, SF b) { return SF(__fmul_rn(a.v, b.v)); }
+  friend __device__ __forceinline__ SFProd operator*(SF a, SF b);
   friend __device__ __forceinline__ SF operator/(SF a, SF b) { return SF(__fdiv_rn(a.v, b.v)); }
   friend __device__ __forceinline__ bool operator<(SF a, SF b) { return a.v < b.v; }
 
@@ -30,6 +35,28 @@ struct SF {
     *c = SF(cv);
   }
 };
+
+// a * b, not yet rounded
+struct SFProd {
+  float a, b;
+  __device__ __forceinline__ float rounded() const { return __fmul_rn(a, b); }
+
+  friend __device__ __forceinline__ SF operator+(SFProd p, SF c) { return SF(__fmaf_rn(p.a, p.b, c.v)); }
+  friend __device__ __forceinline__ SF operator+(SF c, SFProd p) { return SF(__fmaf_rn(p.a, p.b, c.v)); }
+  friend __device__ __forceinline__ SF operator+(SFProd p, SFProd q) { return SF(__fmaf_rn(p.a, p.b, q.rounded())); }
+  friend __device__ __forceinline__ SF operator-(SFProd p, SF c) { return SF(__fmaf_rn(p.a, p.b, -c.v)); }
+  friend __device__ __forceinline__ SF operator-(SF c, SFProd p) { return SF(__fmaf_rn(-p.a, p.b, c.v)); }
+  friend __device__ __forceinline__ SF operator-(SFProd p, SFProd q) { return SF(__fmaf_rn(p.a, p.b, -q.rounded())); }
+  friend __device__ __forceinline__ SFProd operator-(SFProd p) { return SFProd{-p.a, p.b}; }
+  friend __device__ __forceinline__ SFProd operator*(SFProd p, SF c) { return SFProd{p.rounded(), c.v}; }
+  friend __device__ __forceinline__ SFProd operator*(SF c, SFProd p) { return SFProd{c.v, p.rounded()}; }
+  friend __device__ __forceinline__ SFProd operator*(SFProd p, SFProd q) { return SFProd{p.rounded(), q.rounded()}; }
+  friend __device__ __forceinline__ SF operator/(SFProd p, SF d) { return SF(__fdiv_rn(p.rounded(), d.v)); }
+  friend __device__ __forceinline__ SF operator/(SF n, SFProd p) { return SF(__fdiv_rn(n.v, p.rounded())); }
+};
+
+__device__ __forceinline__ SF::SF(const SFProd& p) : v(p.rounded()) {}
+__device__ __forceinline__ SFProd operator*(SF a, SF b) { return SFProd{a.v, b.v}; }
 
 template <> struct RodSeries<SF> { static constexpr float cut = RodSeries<float>::cut; };
 
