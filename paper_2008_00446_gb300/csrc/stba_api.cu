@@ -49,6 +49,7 @@ struct stba_ctx {
   cudaStream_t side_stream = nullptr;           // trailing updates of the factorisation
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_rfork = nullptr, ev_rjoin = nullptr;   // the re-ordering's side branch (chunk listing)
+  cudaEvent_t ev_sfork = nullptr, ev_sjoin = nullptr;   // the S' build's side branch (pair pass)
   std::vector<cudaEvent_t> ev_panel, ev_update;  // one per tile step (grown, never shrunk)
   std::string err;
   int64_t m = 0, n = 0, q = 0;
@@ -130,7 +131,10 @@ struct stba_ctx {
   double* adj_save_x = nullptr;         // [9m + 3n] the final parameters, kept across the reverse pass
 
   // graph / timing
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;      // the current iteration graph, one of graph_cache
+  // executable iteration graphs by launch structure (the number of tile steps and which launches each step
+  // has vary between clusterings): a new clustering's capture updates the one of its structure in place
+  std::vector<std::pair<uint64_t, cudaGraphExec_t>> graph_cache;
   bool graph_stale = false;             // the cluster layout changed since the graph was captured
   int tile = 32;                        // factorisation tile (stba_autotune may change the FP32 one)
   int update_tc = 0;                    // trailing updates on the tensor cores (FP32 factor, tile 64)
@@ -725,7 +729,8 @@ void enqueue_step(stba_ctx* c, bool stages) {
   launch_vp_finalize<real>(P, W, c->st, c->counts, s);
   mark(1);
   // stage 1: S' and b'
-  launch_rcs_build<real>(P, W, c->cslots, c->pchunks, (real*)c->Gbuf, c->st, s);
+  launch_rcs_build<real>(P, W, c->cslots, c->pchunks, (real*)c->Gbuf, c->st, s, c->side_stream, c->ev_sfork,
+                         c->ev_sjoin);
   mark(2);
   // stage 2: factorisation (FP32 factor in mixed mode, FP64 factor in FP64 mode)
   launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
@@ -901,6 +906,33 @@ stba_status run_sharded_iteration(stba_ctx* c) {
   return STBA_OK;
 }
 
+// Launch structure of the iteration graph: what decides which kernels and dependencies a capture records
+// (a wrong guess costs only time: cudaGraphExecUpdate checks the structure itself).
+uint64_t graph_signature(const stba_ctx* c) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    h ^= v;
+    h *= 1099511628211ull;
+  };
+  const CholPlan& p = c->cplan;
+  mix((uint64_t)p.nsteps);
+  mix((uint64_t)p.tile);
+  mix((uint64_t)(p.split | (p.persistent << 1) | (p.update_tc << 2)));
+  mix((uint64_t)p.solve_cs);
+  mix((uint64_t)(p.n_res_items > 0));
+  mix((uint64_t)c->set.refine_steps);
+  mix((uint64_t)(c->mixed ? 1 : 0));
+  mix((uint64_t)((c->pchunks.nchunks > 0 && c->l < c->m) ? 1 : 0));
+  mix((uint64_t)c->opt.pair_blocks);
+  for (int kt = 0; kt < p.nsteps; ++kt) {
+    const int npn = p.h_panel_off[kt + 1] - p.h_panel_off[kt];
+    const int nu = p.h_update_off[kt + 1] - p.h_update_off[kt];
+    const int nd = (p.split && p.h_diag_count) ? p.h_diag_count[kt] : 0;
+    mix((uint64_t)((npn > 0) | ((nu > 0) << 1) | ((nd > 0) << 2) | ((npn > nd) << 3)));
+  }
+  return h;
+}
+
 stba_status launch_iteration(stba_ctx* c) {
   if (c->shard_world > 1) return c->mixed ? run_sharded_iteration<float>(c) : run_sharded_iteration<double>(c);
   if (c->use_pcg || c->use_spcg) {
@@ -936,25 +968,36 @@ stba_status launch_iteration(stba_ctx* c) {
     c->stream = user;
     if (e != cudaSuccess) return fail(c, STBA_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
     c->graph_stale = false;
-    if (c->graph) {
-      // same node structure (same number of tile steps, ...): update the executable graph in place
+    c->graph = nullptr;
+    // an executable graph of the same launch structure is updated in place (kernel arguments and launch
+    // sizes); instantiating a new one costs far more host time than the device needs for an iteration
+    const uint64_t sig = graph_signature(c);
+    auto& cache = c->graph_cache;
+    for (size_t i = 0; i < cache.size(); ++i) {
+      if (cache[i].first != sig) continue;
       cudaGraphExecUpdateResultInfo ri;
-      if (cudaGraphExecUpdate(c->graph, g, &ri) == cudaSuccess) {
+      if (cudaGraphExecUpdate(cache[i].second, g, &ri) == cudaSuccess) {
         cudaGraphDestroy(g);
+        c->graph = cache[i].second;
         CK(cudaGraphLaunch(c->graph, c->stream));
         c->have_stage_times = true;
         return STBA_OK;
       }
       cudaGetLastError();
-      cudaGraphExecDestroy(c->graph);
-      c->graph = nullptr;
+      cudaGraphExecDestroy(cache[i].second);
+      cache.erase(cache.begin() + (long)i);
+      break;
     }
-    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) {
-      c->graph = nullptr;
-      return fail(c, STBA_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(c, STBA_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    if (cache.size() >= 8) {   // keep the 8 most recent structures
+      cudaGraphExecDestroy(cache.front().second);
+      cache.erase(cache.begin());
     }
+    cache.emplace_back(sig, ex);
+    c->graph = ex;
   }
   CK(cudaGraphLaunch(c->graph, c->stream));
   c->have_stage_times = true;
@@ -1278,7 +1321,9 @@ const char* stba_last_error(stba_ctx* ctx) { return ctx ? ctx->err.c_str() : g_c
 void stba_destroy(stba_ctx* c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto& e : c->graph_cache) cudaGraphExecDestroy(e.second);
+  c->graph_cache.clear();
+  c->graph = nullptr;
   free_list(c, c->allocs);
   free_list(c, c->tape_allocs);
   for (GrowBuf* g : {&c->g_panel, &c->g_update, &c->g_res, &c->g_diag, &c->g_S, &c->g_b, &c->g_L, &c->g_Dinv,
@@ -1299,6 +1344,8 @@ void stba_destroy(stba_ctx* c) {
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_rfork) cudaEventDestroy(c->ev_rfork);
   if (c->ev_rjoin) cudaEventDestroy(c->ev_rjoin);
+  if (c->ev_sfork) cudaEventDestroy(c->ev_sfork);
+  if (c->ev_sjoin) cudaEventDestroy(c->ev_sjoin);
   for (auto e : c->ev_panel) cudaEventDestroy(e);
   for (auto e : c->ev_update) cudaEventDestroy(e);
   delete c;
@@ -1433,6 +1480,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_rfork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_rjoin, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_sfork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_sjoin, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->stage_ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->stage_ev[1], cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(c, STBA_ERR_CUDA, "cannot create the factorisation stream or its events"));

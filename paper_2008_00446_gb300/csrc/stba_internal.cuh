@@ -201,7 +201,8 @@ void launch_dc_to_float(const double* dc, float* dcf, int64_t n, cudaStream_t st
 void launch_failed_io(DevState* st, double* x, int to_double, cudaStream_t stream);
 template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
-                      cudaStream_t stream);
+                      cudaStream_t stream, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
+                      cudaEvent_t join = nullptr);
 template <typename real>
 void launch_point_rhs(const DevProblem& P, Scratch<real> W, cudaStream_t stream);
 // FP32 copies of the cameras and points (mixed precision, once per iteration)

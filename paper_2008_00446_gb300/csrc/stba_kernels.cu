@@ -714,15 +714,28 @@ __global__ void __launch_bounds__(32 * PB_WARPS) k_pair_build(DevProblem P, Scra
 
 template <typename real>
 void launch_rcs_build(const DevProblem& P, Scratch<real> W, CamSlots CS, PairChunks B, real* Gbuf, DevState* st,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+  const bool pairs = B.nchunks > 0 && P.l < P.m;
+  // a pair pass that recomputes G_o depends on nothing the camera pass writes (they add to different
+  // blocks of S'), so with a second stream the two run side by side
+  const bool beside = pairs && P.pair_recompute && side != nullptr;
+  if (beside) {
+    cudaEventRecord(fork, stream);
+    cudaStreamWaitEvent(side, fork, 0);
+  }
+  cudaStream_t ps = beside ? side : stream;
   // FP32: both passes take the strict Jacobian rows, so that stored and recomputed G_o are bitwise equal
   k_cam_pass<real, sizeof(real) == 4><<<(CS.nwarps + 7) / 8, 256, 0, stream>>>(P, W, CS, Gbuf, st);
-  if (B.nchunks > 0 && P.l < P.m) {   // a fixed grid walks the list of chunks inside clusters
+  if (pairs) {   // a fixed grid walks the list of chunks inside clusters
     const int grid = std::min((B.nchunks + PB_WARPS - 1) / PB_WARPS, 3 * num_sms());
     if (P.pair_recompute)
-      k_pair_build<real, true><<<grid, 32 * PB_WARPS, PairStage<real>::bytes, stream>>>(P, W, B, Gbuf);
+      k_pair_build<real, true><<<grid, 32 * PB_WARPS, PairStage<real>::bytes, ps>>>(P, W, B, Gbuf);
     else
-      k_pair_build<real, false><<<grid, 32 * PB_WARPS, PairStage<real>::bytes, stream>>>(P, W, B, Gbuf);
+      k_pair_build<real, false><<<grid, 32 * PB_WARPS, PairStage<real>::bytes, ps>>>(P, W, B, Gbuf);
+  }
+  if (beside) {
+    cudaEventRecord(join, side);
+    cudaStreamWaitEvent(stream, join, 0);
   }
 }
 
@@ -1182,7 +1195,7 @@ void configure_kernels(int max_np) {
                                          cudaStream_t, const double*);                                     \
   template void launch_pt_sums<real>(const DevProblem&, Scratch<real>, double*, cudaStream_t);              \
   template void launch_rcs_build<real>(const DevProblem&, Scratch<real>, CamSlots, PairChunks, real*,     \
-                                       DevState*, cudaStream_t);                                          \
+                                       DevState*, cudaStream_t, cudaStream_t, cudaEvent_t, cudaEvent_t);  \
   template void launch_point_update<real>(const DevProblem&, Scratch<real>, cudaStream_t);                \
   template void launch_finalize<real>(const DevProblem&, Scratch<real>, DevState*, const Settings&, int,  \
                                       cudaStream_t);                                                      \
