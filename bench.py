@@ -328,6 +328,7 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip the full-RCS LM comparison")
     ap.add_argument("--compare-iters", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing on the 500-camera scene")
+    ap.add_argument("--no-fp64-factor", action="store_true", help="skip the FP64-factor leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factorisation tile")
     ap.add_argument("--no-scenes", action="store_true",
                     help="skip the extra scene legs (20000 cameras, 5000-camera sequential, uniform tracks)")
@@ -412,10 +413,13 @@ def main():
     stage_tot = np.zeros(5)
     info_tot = {}
     n_stage = min(args.steps, 50)
+    boosted = failed = 0   # FP32 pivots raised by static pivoting, failed cluster factorisations
     for i in range(n_stage):
         flush.fill_(float(i))
         stba.stba_set_clusters(ctx, seq[w0 + i])
-        stba.stba_lm_iteration(ctx, want_info=False)
+        it_info = stba.stba_lm_iteration(ctx)
+        boosted += it_info["boosted_pivots"]
+        failed += it_info["failed_clusters"]
         stage_tot += np.array(stba.stba_stage_times(ctx))
         for k_, v_ in stba.stba_problem_info(ctx).items():
             info_tot[k_] = info_tot.get(k_, 0) + v_
@@ -433,6 +437,33 @@ def main():
         fixed_ms.append((a_ev, b_ev))
     torch.cuda.synchronize()
     fixed_ms = float(np.mean([a.elapsed_time(b) for a, b in fixed_ms]))
+
+    # the same steps with the cluster systems factored in FP64 (option factor_fp64) under the same FP32
+    # Jacobians, for the cost of the precision Eq. 13's solve has in the paper's CPU code
+    fp64f = None
+    if rank == 0 and world == 1 and not args.no_fp64_factor:
+        ctx64 = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                                 precision=stba.STBA_MIXED, stream=stream, factor_fp64=1)
+        st64 = np.zeros(5)
+        ev64 = []
+        n64 = min(args.steps, 20)
+        for i in range(3 + n64):
+            flush.fill_(float(i))
+            a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_ev.record(stream)
+            stba.stba_set_clusters(ctx64, seq[w0 + i % args.steps])
+            stba.stba_lm_iteration(ctx64, want_info=False)
+            b_ev.record(stream)
+            if i >= 3:
+                ev64.append((a_ev, b_ev))
+                st64 += np.array(stba.stba_stage_times(ctx64))
+        torch.cuda.synchronize()
+        st64 /= n64
+        fp64f = {"ms_per_step": float(np.mean([a.elapsed_time(b) for a, b in ev64])),
+                 "stage_ms": {nm: float(v) for nm, v in zip(STAGES, st64)},
+                 "note": "factor_fp64 = 1: FP64 LL^T of every S'_k (tile 32, CUDA cores) under the same FP32 "
+                         "Jacobians and the same clustering draws (and the same one refinement step)"}
+        stba.stba_destroy(ctx64)
 
     # measured arithmetic peaks (outside the timed region), with the SM clock sampled while they run
     alu = None
@@ -493,6 +524,10 @@ def main():
         "sgc": sgc,
         "autotune": {"kept": tuned, "ms_per_iter": {str(k_): v_ for k_, v_ in tile_ms.items()}},
         "fixed_clusters_ms_per_iter": fixed_ms,
+        "factor_pivots": {"boosted_pivots": int(boosted), "failed_clusters": int(failed), "steps": n_stage,
+                          "note": "FP32 factor: pivots that rounding made vanish, raised to 2^-12 (static "
+                                  "pivoting; the FP64 refinement solves the unmodified system)"},
+        "fp64_factor": fp64f,
         "gpu_launches": int(round((info0["launches_per_iter"] + REORDER_LAUNCHES) * args.steps)),
         "clocks": clocks,
         "final": {"rmse_px": float(np.sqrt(F_end / (2 * q))), "lambda": lam, "iterations": it_end},

@@ -113,6 +113,13 @@ typedef struct {
                                Both give the same S': in FP32 every pass evaluates the Jacobian rows with
                                each operation rounded on its own, so stored and recomputed G_o are bitwise
                                equal (up to the order of the FP64 atomic sums). */
+  int32_t factor_fp64;      /* STBA_MIXED only: 1 = factor the cluster systems in FP64 (tile 32, CUDA cores)
+                               under the FP32 Jacobians and Schur terms instead of the default FP32 factor
+                               with FP64 refinement -- the precision Eq. 13's solve has in the paper's
+                               CPU code, at the FP64 rate of this GPU.  Not with factor_tile 64, the tensor-
+                               core update, the split or persistent panel (STBA_ERR_INVALID_ARG), nor with
+                               stba_adjoint (STBA_ERR_STATE); stba_autotune keeps it as the single
+                               configuration.  0 = FP32 factor (default). */
 } stba_options;
 
 enum { STBA_PAIR_BLOCKS_DEFAULT = 0, STBA_PAIR_BLOCKS_STORED = 1, STBA_PAIR_BLOCKS_RECOMPUTE = 2 };

@@ -55,6 +55,7 @@ struct stba_ctx {
   int64_t m = 0, n = 0, q = 0;
   int l = 0, nv = 0;
   bool mixed = false;
+  bool f32f = false;                   // the cluster factor is FP32 (mixed precision without factor_fp64)
   size_t bytes_base = 0;
   std::vector<void*> allocs;            // problem-lifetime device buffers
 
@@ -432,7 +433,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t need = solve_smem_bytes(c->mixed, c->tile, big);
+    const size_t need = solve_smem_bytes(c->f32f, c->tile, big);
     if (optin > 0 && need > (size_t)optin)
       return fail(c, STBA_ERR_INVALID_ARG,
                   "a cluster of %d unknowns needs %zu bytes of shared memory in the cluster solve (limit %d); "
@@ -657,7 +658,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->cplan.prio_low = least;
   }
   // cluster systems and factor storage
-  const size_t rs = c->mixed ? sizeof(float) : sizeof(double);
+  const size_t rs = c->f32f ? sizeof(float) : sizeof(double);   // the factor's reals
   {
     double *S_, *b_;
     char *L_, *Dinv_, *Ldiag_;
@@ -733,10 +734,16 @@ void enqueue_step(stba_ctx* c, bool stages) {
                          c->ev_sjoin);
   mark(2);
   // stage 2: factorisation (FP32 factor in mixed mode, FP64 factor in FP64 mode)
-  launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
+  if (c->f32f)
+    launch_factor<float>(P, W.S, c->fbuf, c->cplan, s);
+  else
+    launch_factor<double>(P, W.S, c->fbuf, c->cplan, s);
   mark(3);
   // stage 3: cluster solves with FP64 refinement
-  launch_solve<real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
+  if (c->f32f)
+    launch_solve<float>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
+  else
+    launch_solve<double>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
   launch_count_failures(c->fail_flags, c->l, c->st, s);
   mark(4);
   // stage 4: points, cost, control
@@ -883,9 +890,15 @@ stba_status run_sharded_iteration(stba_ctx* c) {
   record_stage(c, 1);
   launch_rcs_build<real>(P, W, c->cslots, c->pchunks, (real*)c->Gbuf, c->st, s);
   record_stage(c, 2);
-  launch_factor<real>(P, W.S, c->fbuf, c->cplan, s);
+  if (c->f32f)
+    launch_factor<float>(P, W.S, c->fbuf, c->cplan, s);
+  else
+    launch_factor<double>(P, W.S, c->fbuf, c->cplan, s);
   record_stage(c, 3);
-  launch_solve<real>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
+  if (c->f32f)
+    launch_solve<float>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
+  else
+    launch_solve<double>(P, W.S, W.b, c->fbuf, c->cplan, c->set.refine_steps, c->dc, c->dcf, s);
   launch_count_failures(c->fail_flags, c->l, c->st, s);
   double* nfail = c->xch + 9 * (size_t)c->n;
   launch_failed_io(c->st, nfail, 1, s);
@@ -1211,7 +1224,7 @@ stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* choice, floa
     for (int t = 0; t < NCAND; ++t)
       if (cand_tile[t] == c->tile && cand_tc[t] == c->update_tc && cand_panel[t] == c->panel_choice) *choice = t;
   };
-  if (!c->mixed || c->use_pcg || c->use_spcg) {   // one candidate (or no factorisation at all)
+  if (!c->f32f || c->use_pcg || c->use_spcg) {   // one candidate (or no factorisation at all)
     report();
     return STBA_OK;
   }
@@ -1391,14 +1404,19 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       !(c->opt.pair_blocks == STBA_PAIR_BLOCKS_DEFAULT || c->opt.pair_blocks == STBA_PAIR_BLOCKS_STORED ||
         c->opt.pair_blocks == STBA_PAIR_BLOCKS_RECOMPUTE) ||
       ((c->opt.factor_panel == STBA_FACTOR_PANEL_SPLIT || c->opt.factor_panel == STBA_FACTOR_PANEL_PERSISTENT) &&
-       !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))))
+       !(c->opt.precision == STBA_MIXED && (c->opt.factor_tile == 0 || c->opt.factor_tile == 64))) ||
+      !(c->opt.factor_fp64 == 0 || c->opt.factor_fp64 == 1) ||
+      (c->opt.factor_fp64 && (c->opt.factor_tile == 64 || c->opt.factor_update == STBA_FACTOR_UPDATE_TENSOR ||
+                              c->opt.factor_panel == STBA_FACTOR_PANEL_SPLIT ||
+                              c->opt.factor_panel == STBA_FACTOR_PANEL_PERSISTENT)))
     return bail(fail(c, STBA_ERR_INVALID_ARG, "invalid options"));
   c->m = m;
   c->n = n;
   c->q = q;
   c->mixed = c->opt.precision == STBA_MIXED;
-  c->tile = c->opt.factor_tile ? c->opt.factor_tile : factor_tile(c->mixed);
-  c->update_tc = c->mixed && c->tile == 64 && c->opt.factor_update != STBA_FACTOR_UPDATE_SIMT;
+  c->f32f = c->mixed && !c->opt.factor_fp64;
+  c->tile = c->opt.factor_tile ? c->opt.factor_tile : factor_tile(c->f32f);
+  c->update_tc = c->f32f && c->tile == 64 && c->opt.factor_update != STBA_FACTOR_UPDATE_SIMT;
   c->panel_choice = c->opt.factor_panel;
   c->use_pcg = c->opt.linear_solver == STBA_SOLVER_PCG_FULL;
   c->use_spcg = c->opt.linear_solver == STBA_SOLVER_PCG_CLUSTERS;
@@ -1854,6 +1872,7 @@ stba_status stba_adjoint(stba_ctx* c, const double* dL_dcams, const double* dL_d
   if (!c || !dL_dcams) return STBA_ERR_INVALID_ARG;
   if (c->use_pcg || c->use_spcg) return fail(c, STBA_ERR_STATE, "the adjoint covers the cluster solver only");
   if (c->opt.huber_a > 0) return fail(c, STBA_ERR_STATE, "the adjoint covers the plain least-squares objective only");
+  if (c->mixed && !c->f32f) return fail(c, STBA_ERR_STATE, "the adjoint covers the FP32 cluster factor of mixed precision only");
   if (c->tape_len == 0) return fail(c, STBA_ERR_STATE, "no recorded iteration (call stba_record before iterating)");
   if (c->tape_broken)
     return fail(c, STBA_ERR_STATE, "the parameters were replaced between recorded iterations; record again");

@@ -48,7 +48,7 @@ class StbaOptions(ctypes.Structure):
                 ("linear_solver", ctypes.c_int32), ("pcg_max_iter", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
                 ("huber_a", ctypes.c_double), ("factor_tile", ctypes.c_int32), ("factor_update", ctypes.c_int32),
                 ("factor_panel", ctypes.c_int32), ("solve_cluster", ctypes.c_int32),
-                ("pair_blocks", ctypes.c_int32)]
+                ("pair_blocks", ctypes.c_int32), ("factor_fp64", ctypes.c_int32)]
 
 
 class StbaIterInfo(ctypes.Structure):

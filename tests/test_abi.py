@@ -99,7 +99,13 @@ def test_invalid_options_are_rejected():
                dict(precision=1, factor_tile=32, factor_panel=stba.STBA_FACTOR_PANEL_SPLIT),
                dict(precision=1, factor_panel=4), dict(factor_panel=stba.STBA_FACTOR_PANEL_PERSISTENT),
                dict(precision=1, factor_tile=32, factor_panel=stba.STBA_FACTOR_PANEL_PERSISTENT),
-               dict(solve_cluster=3), dict(solve_cluster=16), dict(solve_cluster=-2)):
+               dict(solve_cluster=3), dict(solve_cluster=16), dict(solve_cluster=-2),
+               # the FP64 factor of mixed precision: tile 32 on the CUDA cores, stacked panel
+               dict(precision=1, factor_fp64=2), dict(precision=1, factor_fp64=-1),
+               dict(precision=1, factor_fp64=1, factor_tile=64),
+               dict(precision=1, factor_fp64=1, factor_update=stba.STBA_FACTOR_UPDATE_TENSOR),
+               dict(precision=1, factor_fp64=1, factor_panel=stba.STBA_FACTOR_PANEL_SPLIT),
+               dict(precision=1, factor_fp64=1, factor_panel=stba.STBA_FACTOR_PANEL_PERSISTENT)):
         with pytest.raises(stba.StbaError):
             stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, **kw)
     for bad in (-0.5, float("nan"), float("inf")):

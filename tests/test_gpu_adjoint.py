@@ -240,6 +240,15 @@ def test_adjoint_state_errors():
         stba.stba_adjoint(ctx, a_c)            # chain broken by replaced parameters
     assert e.value.status == 7
     ctx.close()
+    # the FP64 factor option of mixed precision has no adjoint
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, lambda0=LAMBDA0,
+                           precision=stba.STBA_MIXED, factor_fp64=1)
+    stba.stba_record(ctx, 1)
+    stba.stba_lm_iteration(ctx)
+    with pytest.raises(stba.StbaError) as e:
+        stba.stba_adjoint(ctx, a_c)
+    assert e.value.status == 7
+    ctx.close()
     # an accepted step with the steepest-descent correction (lambda >= 0.1) is differentiated, not refused
     ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters, lambda0=0.5)
     stba.stba_record(ctx, 1)

@@ -101,6 +101,23 @@ def test_mixed_first_step_elementwise(name, panel, pairs):
     ctx.close()
 
 
+@pytest.mark.parametrize("name", list(SCENES))
+def test_mixed_fp64_factor_first_step_elementwise(name):
+    # FP32 Jacobians and Schur terms, the cluster systems factored in FP64 (option factor_fp64)
+    s = scene(name)
+    _, _, _, _, rec = oracle_first(s, 1e-4)
+    ctx = stba.stba_create(s.cameras, s.points, s.obs_cam, s.obs_pt, s.obs_uv, s.clusters,
+                           precision=stba.STBA_MIXED, factor_fp64=1)
+    info = stba.stba_lm_iteration(ctx)
+    assert info["failed_clusters"] == 0 and info["boosted_pivots"] == 0
+    dc, dp = stba.stba_last_step(ctx)
+    e_c, e_p = cols(dc, rec["dc"], 9), cols(dp, rec["dp"], 3)
+    print(f"{name} mixed, FP64 factor: dc {e_c:.2e} dp {e_p:.2e}")
+    assert e_c < 1e-3 and e_p < 1e-3, (e_c, e_p)
+    assert info["accepted"] == rec["accepted"]
+    ctx.close()
+
+
 @pytest.mark.parametrize("pairs", [0, 1])
 def test_mixed_rmse_after_five_iterations_c3(pairs):
     s = scene("c3_diff")
