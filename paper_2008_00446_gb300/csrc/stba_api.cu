@@ -807,7 +807,7 @@ void enqueue_cost(stba_ctx* c) {
   const DevProblem P = dev_problem(c);
   const Scratch<real> W = scratch<real>(c);
   launch_iter_begin<real>(c->st, c->set, c->stream);
-  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, nullptr, nullptr, c->partial, c->st, (real*)c->res_cur,
+  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, c->cam_df, c->pt_df, c->partial, c->st, (real*)c->res_cur,
                     c->stream);
   launch_finalize<real>(P, W, c->st, c->set, 0, c->stream);
 }
@@ -1057,7 +1057,7 @@ void enqueue_adjoint_step(stba_ctx* c, double lam, int corrected, const AdjointB
   launch_set_lambda(c->st, lam, c->stream);
   launch_iter_begin<real>(c->st, c->set, c->stream);
   const DevProblem P = dev_problem(c);
-  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, nullptr, nullptr, c->partial, c->st, (real*)c->res_cur,
+  launch_cost<real>(P, nullptr, nullptr, c->cam_rt, c->cam_df, c->pt_df, c->partial, c->st, (real*)c->res_cur,
                     c->stream);
   enqueue_step<real>(c, false);
   launch_adjoint_step<real>(P, scratch<real>(c), c->clist, c->fbuf, c->cplan, c->set.refine_steps, c->obs_perm, lam,

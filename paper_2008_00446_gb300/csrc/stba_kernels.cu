@@ -967,7 +967,7 @@ __global__ void k_cam_df(int m, const double* __restrict__ rt, float* __restrict
 __global__ void k_point_df(int n, const double* __restrict__ pts, const double* __restrict__ dp,
                            float* __restrict__ pdf) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 3 * n; i += gridDim.x * blockDim.x) {
-    const float2 v = df_split(pts[i] + dp[i]);
+    const float2 v = df_split(dp ? pts[i] + dp[i] : pts[i]);
     reinterpret_cast<float2*>(pdf)[i] = v;
   }
 }
@@ -1151,7 +1151,7 @@ template <typename real>
 void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, float* cam_df, float* pt_df,
                  double* partial, DevState* st, real* rout, cudaStream_t stream) {
   k_cam_rt<<<(P.m + 127) / 128, 128, 0, stream>>>(P.m, P.cams, dc, rt);
-  if (sizeof(real) == 4 && dp && cam_df && pt_df && P.obs_uvdf) {
+  if (sizeof(real) == 4 && cam_df && pt_df && P.obs_uvdf) {   // dc, dp null: F(x) itself
     k_cam_df<<<(P.m + 127) / 128, 128, 0, stream>>>(P.m, rt, cam_df);
     k_point_df<<<std::min((3 * P.n + 255) / 256, 2048), 256, 0, stream>>>(P.n, P.pts, dp, pt_df);
     k_cost_df<<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, cam_df, pt_df, partial, st, (float*)rout);
