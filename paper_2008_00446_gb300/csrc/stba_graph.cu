@@ -265,13 +265,29 @@ static void sgc_draw(const SgcBase& S, int gamma, double beta, uint64_t seed, in
   SplitMix64 rng{seed};
   int rejections = 0;
   std::vector<int> walk;
-  // the next entry's index is drawn one step ahead and its record fetched early; if the list shrank below
-  // it meanwhile a fresh index is drawn, which keeps every draw uniform over the current list
-  size_t rn = list.empty() ? 0 : rng.below(list.size());
+  // The positions of the next AHEAD draws are drawn early, so that their list entries and then their
+  // records are fetched while earlier draws are processed (each a random access into arrays of many MB).
+  // A position is drawn uniformly over the list as it is at that moment and used when its turn comes if
+  // the list still reaches it, else a fresh position is drawn: the list changes in between only through
+  // the entries processed meanwhile, which do not depend on the pending positions, so every draw stays
+  // uniform over the current list.
+  constexpr int AHEAD = 16;
+  size_t ahead[AHEAD] = {};
+  int head = 0;
+  if (!list.empty())
+    for (int k = 0; k < AHEAD; ++k) {
+      ahead[k] = rng.below(list.size());
+      __builtin_prefetch(&list[ahead[k]]);
+    }
   while (!list.empty()) {
-    size_t r = rn < list.size() ? rn : rng.below(list.size());
-    rn = rng.below(list.size());
-    __builtin_prefetch(&rec[list[rn]]);
+    size_t r = ahead[head] < list.size() ? ahead[head] : rng.below(list.size());
+    ahead[head] = rng.below(list.size());
+    __builtin_prefetch(&list[ahead[head]]);
+    head = head + 1 == AHEAD ? 0 : head + 1;
+    {   // the entry fetched half a window ago: fetch its record now
+      const size_t mid = ahead[(head + AHEAD / 2) % AHEAD];
+      if (mid < list.size()) __builtin_prefetch(&rec[list[mid]]);
+    }
     const int ei = list[r];
     PairRec& e = rec[ei];
     if (e.a < 0 || size[e.a] + size[e.b] > gamma) {   // merged into another pair, or no longer allowed
