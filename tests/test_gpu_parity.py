@@ -132,6 +132,35 @@ def test_ring_cluster_sequence_with_set_clusters(ring):
     assert rows(cams, c, 9) < 1e-8 and rows(pts, p, 3) < 1e-8
 
 
+@pytest.mark.parametrize("precision", [stba.STBA_FP64, stba.STBA_MIXED])
+def test_graph_structures_alternating_equal_the_oracle(ring, precision):
+    """Clusterings whose factorisations have different numbers of tile steps, in turn (3 clusters of 10,
+    one of 30, 2 of 15, and again): each new one is captured and either updates the executable graph kept
+    for its launch structure or instantiates one.  Every iteration against the oracle run with the same
+    sequence: FP64 every step 1e-6 per row, F(x + dx) 1e-8 and the accept decisions; mixed the first step
+    within the mixed bar and the final RMSE within 0.1 %."""
+    s = ring
+    m = s.m
+    shapes = [np.arange(m) // 10, np.zeros(m), np.arange(m) // 15]
+    seq = np.array([shapes[t % 3] for t in range(7)], np.int32)
+    c, p, lam, F, hist = run_oracle(s, seq, len(seq))
+    ctx = make_ctx(s, seq[0], precision=precision)
+    for t, rec in enumerate(hist):
+        stba.stba_set_clusters(ctx, seq[t])
+        info = stba.stba_lm_iteration(ctx)
+        dc, dp = stba.stba_last_step(ctx)
+        if precision == stba.STBA_FP64:
+            assert info["accepted"] == rec["accepted"], t
+            assert rows(dc, rec["dc"], 9) < 1e-6 and rows(dp, rec["dp"], 3) < 1e-6, t
+            assert abs(info["F_after"] - rec["F_after"]) <= 1e-8 * rec["F_after"], t
+        elif t == 0:
+            assert cols(dc, rec["dc"], 9) < 1e-3 and cols(dp, rec["dp"], 3) < 1e-3
+    if precision == stba.STBA_MIXED:
+        _, Fg, _ = stba.stba_get_state(ctx)
+        assert abs(ostba.rmse(Fg, s.q) - ostba.rmse(F, s.q)) <= 1e-3 * ostba.rmse(F, s.q)
+    ctx.close()
+
+
 def test_ring_sgc_draws_with_set_clusters(ring):
     """Per-iteration stochastic-graph-clustering draws (Gamma = 8, so several clusters of uneven size) applied
     with stba_set_clusters: the device re-ordering and the carried-over residuals give the oracle's
