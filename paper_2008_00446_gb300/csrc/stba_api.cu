@@ -1623,6 +1623,18 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       for (int64_t j = 0; j < m; ++j)
         for (int e = cam_off[j]; e < cam_off[j + 1]; ++e) ecam[e] = (int)j;
     }
+    // point and observation of every camera-list entry, copied into the slots with each clustering
+    std::vector<int> ept(Q);
+    std::vector<float2> euvf(c->mixed ? Q : 0);
+    std::vector<double2> euvd(c->mixed ? 0 : Q);
+    for (size_t e = 0; e < Q; ++e) {
+      const int bo = cam_base[e];
+      ept[e] = base_pt[bo];
+      if (c->mixed)
+        euvf[e] = make_float2(base_uvf[2 * (size_t)bo], base_uvf[2 * (size_t)bo + 1]);
+      else
+        euvd[e] = make_double2(base_uv[2 * (size_t)bo], base_uv[2 * (size_t)bo + 1]);
+    }
     for (int64_t j = 0; j < m; ++j) {
       const int nw = (cam_off[j + 1] - cam_off[j] + 31) / 32;
       cam_warp_off[j + 1] = cam_warp_off[j] + nw;
@@ -1644,6 +1656,21 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = upload(c, &d_cam_off, cam_off)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_cam_base, cam_base)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_ecam, ecam)) != STBA_OK) return bail(s);
+    int* d_ept = nullptr;
+    float2* d_euvf = nullptr;
+    double2* d_euvd = nullptr;
+    int2* d_slot_pv = nullptr;
+    float2* d_slot_uvf = nullptr;
+    double2* d_slot_uvd = nullptr;
+    if ((s = upload(c, &d_ept, ept)) != STBA_OK) return bail(s);
+    if ((s = dalloc(c, &d_slot_pv, 32 * (size_t)nwarps)) != STBA_OK) return bail(s);
+    if (c->mixed) {
+      if ((s = upload(c, &d_euvf, euvf)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_slot_uvf, 32 * (size_t)nwarps)) != STBA_OK) return bail(s);
+    } else {
+      if ((s = upload(c, &d_euvd, euvd)) != STBA_OK) return bail(s);
+      if ((s = dalloc(c, &d_slot_uvd, 32 * (size_t)nwarps)) != STBA_OK) return bail(s);
+    }
     if ((s = dalloc(c, &d_eo, Q)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &d_nsing, Q)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_cam_warp_off, cam_warp_off)) != STBA_OK) return bail(s);
@@ -1719,6 +1746,12 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     A.cam_off = d_cam_off;
     A.cam_base = d_cam_base;
     A.ecam = d_ecam;
+    A.ept = d_ept;
+    A.euvf = d_euvf;
+    A.euvd = d_euvd;
+    A.slot_pv = d_slot_pv;
+    A.slot_uvf = d_slot_uvf;
+    A.slot_uvd = d_slot_uvd;
     A.eo = d_eo;
     A.nsing = d_nsing;
     A.cam_warp_off = d_cam_warp_off;
@@ -1731,7 +1764,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     c->pchunks.nactive = c->counts + 3;
     c->pcg.counts = c->counts;
     c->clist = CamLists{d_cam_off, d_cam_obs};
-    c->cslots = CamSlots{d_slots, d_warp_cam, nwarps};
+    c->cslots = CamSlots{d_slots, d_warp_cam, nwarps, d_slot_pv, d_slot_uvf, d_slot_uvd};
   }
   if ((s = set_clusters_host(c, h_cl)) != STBA_OK) return bail(s);
   double F;

@@ -105,6 +105,12 @@ struct CamSlots {     // per-camera observation lists padded to whole warps, for
   const int* slots;         // [32 * nwarps] sorted observation position, or -1 (padding)
   const int* warp_cam;      // [nwarps] camera of each warp's 32 slots
   int nwarps;
+  // per slot, written with the lists (stba_order.cu), so that the camera pass reads them in its own order
+  // instead of gathering them by observation position: (point, virtual point | bit 31 when the virtual
+  // point has no other observation) and the observation in the working precision
+  const int2* pv;           // [32 * nwarps]
+  const float2* uvf;        // [32 * nwarps] FP32 (mixed precision) or null
+  const double2* uvd;       // [32 * nwarps] FP64 or null
 };
 
 struct PairChunks {   // observation pairs of the camera graph, by edge, cut into chunks (built at create)
@@ -165,6 +171,12 @@ struct ReorderArgs {
   const int* cam_off;       // [m+1] observations of every camera
   const int* cam_base;      // [q]   their base positions, ascending
   const int* ecam;          // [q]   the camera of every entry of cam_base
+  const int* ept;           // [q]   the point of every entry of cam_base
+  const float2* euvf;       // [q]   its observation in FP32 (mixed precision) or null
+  const double2* euvd;      // [q]   its observation in FP64 (FP64 mode) or null
+  int2* slot_pv;            // CamSlots::pv, uvf, uvd (written by k_cam_place)
+  float2* slot_uvf;
+  double2* slot_uvd;
   int* eo;                  // [q]   the new position of every entry of cam_base (scratch of the assignment)
   int* nsing;               // [q]   per base position: its new position, bit 31 set when its virtual point
                             //       has no other observation (scratch of the assignment)

@@ -411,12 +411,11 @@ __device__ __forceinline__ void g_of_obs(const real* Li, const real (&Jc)[2][9],
 // stored residual f_o (returned, scaled, in r).  STRICT (FP32 only): every operation rounded on its own, so
 // that the camera pass and the pair pass form bitwise the same rows.
 template <typename real, bool STRICT>
-__device__ __forceinline__ void obs_jacobian(const DevProblem& P, const Cam<real>& C, int o, real (&r)[2],
-                                             real (&Jc)[2][9], real (&Jp)[2][3]) {
+__device__ __forceinline__ void obs_jacobian_at(const DevProblem& P, const Cam<real>& C, int o, int pt, real uo,
+                                                real vo, real (&r)[2], real (&Jc)[2][9], real (&Jp)[2][3]) {
   static_assert(!STRICT || sizeof(real) == 4, "the strict rounding mode is FP32 only");
-  real X[3], uo, vo;
-  load_point_w(P, P.obs_pt[o], X);
-  load_uv(P, o, uo, vo);
+  real X[3];
+  load_point_w(P, pt, X);
   if constexpr (STRICT)
     project_jacobian_strict(C, X, uo, vo, Jc, Jp);
   else
@@ -429,6 +428,14 @@ __device__ __forceinline__ void obs_jacobian(const DevProblem& P, const Cam<real
   else
     sw = huber_sqrt_weight<real>(P.huber_a, r[0], r[1]);
   scale_rows(sw, r, Jc, Jp);
+}
+
+template <typename real, bool STRICT>
+__device__ __forceinline__ void obs_jacobian(const DevProblem& P, const Cam<real>& C, int o, real (&r)[2],
+                                             real (&Jc)[2][9], real (&Jp)[2][3]) {
+  real uo, vo;
+  load_uv(P, o, uo, vo);
+  obs_jacobian_at<real, STRICT>(P, C, o, P.obs_pt[o], uo, vo, r, Jc, Jp);
 }
 
 // STRICT (the FP32 pass): the Jacobian rows with every operation rounded on its own, as in the pair pass.
@@ -448,10 +455,23 @@ __global__ void __launch_bounds__(256, sizeof(real) == 4 ? 4 : 3) k_cam_pass(Dev
   for (int c = 0; c < 9; ++c) Jc[0][c] = Jc[1][c] = 0;
   if (o >= 0) {
     const Cam<real> C = load_cam_w<real>(P, j);
-    const int v = P.obs_vp[o];
-    const bool single = (P.vp_off[v + 1] - P.vp_off[v]) == 1;
+    // point, virtual point and observation of the slot, stored in slot order with the camera lists
+    const size_t sl = 32 * (size_t)gw + lane;
+    const int2 pv = CS.pv[sl];
+    const int v = pv.y & INT_MAX;
+    const bool single = pv.y < 0;
+    real uo, vo;
+    if constexpr (sizeof(real) == 4) {
+      const float2 t = CS.uvf[sl];
+      uo = t.x;
+      vo = t.y;
+    } else {
+      const double2 t = CS.uvd[sl];
+      uo = t.x;
+      vo = t.y;
+    }
     real Jp[2][3];
-    obs_jacobian<real, STRICT>(P, C, o, r, Jc, Jp);
+    obs_jacobian_at<real, STRICT>(P, C, o, pv.x, uo, vo, r, Jc, Jp);
     const real* vi = W.vp_info + 9 * (size_t)v;
     // Both cases reduce to Jc^T N Jc with a 2x2 N:
     //   single observation  N = (I + Jp Lambda^-1 Jp^T)^-1                 (Woodbury, no cancellation)

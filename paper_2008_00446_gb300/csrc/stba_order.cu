@@ -226,7 +226,11 @@ __global__ void k_cam_place(ReorderArgs A, const int* __restrict__ flag, const i
   const int idx = flag[e] ? before : nsingle + (e - b - before);
   const int o = A.eo[e];
   A.cam_obs[b + idx] = o;
-  A.slots[32 * A.cam_warp_off[j] + idx] = o;
+  const size_t sl = 32 * (size_t)A.cam_warp_off[j] + idx;
+  A.slots[sl] = o;
+  A.slot_pv[sl] = make_int2(A.ept[e], flag[e] ? (A.obs_vp[o] | INT_MIN) : A.obs_vp[o]);
+  if (A.slot_uvf) A.slot_uvf[sl] = A.euvf[e];
+  if (A.slot_uvd) A.slot_uvd[sl] = A.euvd[e];
 }
 
 // chunks of the camera graph whose two cameras share a cluster
