@@ -1652,7 +1652,8 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = upload(c, &c->pt_off, c->h_pt_off)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_base_cam, base_cam)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_base_src, base_src)) != STBA_OK) return bail(s);
-    if ((s = upload(c, &d_base_uv, base_uv)) != STBA_OK) return bail(s);
+    d_base_uv = nullptr;   // FP64 observations in the iteration order: read by the FP64 kernels only
+    if (!c->mixed && (s = upload(c, &d_base_uv, base_uv)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_cam_off, cam_off)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_cam_base, cam_base)) != STBA_OK) return bail(s);
     if ((s = upload(c, &d_ecam, ecam)) != STBA_OK) return bail(s);
@@ -1695,7 +1696,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
     if ((s = dalloc(c, &d_start, 2 * (Q + 1))) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->vp_off, Q + 1)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->pt_vp_off, (size_t)n + 1)) != STBA_OK) return bail(s);
-    if ((s = dalloc(c, &c->obs_uv, 2 * Q)) != STBA_OK) return bail(s);
+    if (!c->mixed && (s = dalloc(c, &c->obs_uv, 2 * Q)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &d_cam_obs, Q)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &d_slots, 32 * (size_t)nwarps)) != STBA_OK) return bail(s);
     if ((s = dalloc(c, &c->tile_sum, Q / 2048 + 2)) != STBA_OK) return bail(s);

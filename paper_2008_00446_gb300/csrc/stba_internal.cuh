@@ -27,7 +27,7 @@ struct DevProblem {
   const int* obs_vp;       // [q] virtual point of each sorted observation
   const int* obs_pt;       // [q] point of each sorted observation
   const int* obs_base;     // [q] position of each sorted observation in the (point, camera) order
-  const double* obs_uv;    // [q][2] FP64 observations
+  const double* obs_uv;    // [q][2] FP64 observations (FP64 mode only; null in mixed precision)
   const float* obs_uvf;    // [q][2] FP32 copy (mixed precision)
   const float4* obs_uvdf;  // [q] double-float copy (u_hi, u_lo, v_hi, v_lo) (mixed precision)
   const int* vp_off;       // [nv+1] observation range of each virtual point

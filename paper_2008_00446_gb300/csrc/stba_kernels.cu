@@ -1171,7 +1171,9 @@ template <typename real>
 void launch_cost(const DevProblem& P, const double* dc, const double* dp, double* rt, float* cam_df, float* pt_df,
                  double* partial, DevState* st, real* rout, cudaStream_t stream) {
   k_cam_rt<<<(P.m + 127) / 128, 128, 0, stream>>>(P.m, P.cams, dc, rt);
-  if (sizeof(real) == 4 && cam_df && pt_df && P.obs_uvdf) {   // dc, dp null: F(x) itself
+  // FP32 working precision: always the double-float kernels (cam_df, pt_df and the double-float observations
+  // are required; the FP64 observations are not kept in that mode); dc, dp null: F(x) itself
+  if constexpr (sizeof(real) == 4) {
     k_cam_df<<<(P.m + 127) / 128, 128, 0, stream>>>(P.m, rt, cam_df);
     k_point_df<<<std::min((3 * P.n + 255) / 256, 2048), 256, 0, stream>>>(P.n, P.pts, dp, pt_df);
     k_cost_df<<<RED_BLOCKS, RED_THREADS, 0, stream>>>(P, cam_df, pt_df, partial, st, (float*)rout);

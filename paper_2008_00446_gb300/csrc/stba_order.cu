@@ -50,7 +50,7 @@ __global__ void k_reorder(ReorderArgs A, const int* __restrict__ key, const real
   A.obs_cam[np] = A.base_cam[bo];
   A.obs_perm[np] = A.base_src[bo];
   A.start[np] = first ? 1 : 0;
-  reinterpret_cast<double2*>(A.obs_uv)[np] = reinterpret_cast<const double2*>(A.base_uv)[bo];
+  if (A.obs_uv) reinterpret_cast<double2*>(A.obs_uv)[np] = reinterpret_cast<const double2*>(A.base_uv)[bo];
   if (A.obs_uvf) reinterpret_cast<float2*>(A.obs_uvf)[np] = reinterpret_cast<const float2*>(A.base_uvf)[bo];
   if (A.obs_uvdf) A.obs_uvdf[np] = A.base_uvdf[bo];
   if (res_old) {   // residuals at the current x, stored in the order of the previous assignment
