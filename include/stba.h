@@ -304,8 +304,10 @@ stba_status stba_cluster_sgc(stba_ctx* ctx, int32_t gamma, double beta, uint64_t
  * (STBA_MIXED; FP64 has one):
  *   0 = tile 64, split panel, tensor-core trailing update     1 = tile 64, split panel, CUDA-core update
  *   2 = tile 64, stacked panel, CUDA-core update              3 = tile 32, stacked panel, CUDA-core update
- *   4 = tile 64, persistent (one launch of 8-CTA clusters)
- * *choice (optional) receives the index kept (-1 for the single FP64 configuration), ms[0..4] (optional) the
+ *   4 = tile 64, persistent (one launch of 8-CTA clusters)  5 = tile 64, stacked panel, tensor-core update
+ *                                                              (the default on problems of one wave of panels)
+ * *choice (optional) receives the index kept (-1 for the single FP64 configuration or the FP64 factor of
+ * factor_fp64), ms[0..5] (optional, 6 floats) the
  * time per iteration of each candidate (-1 when not tried).  Synchronises the context stream.  Errors:
  * STBA_ERR_STATE while iterations are being recorded (stba_record), STBA_ERR_INVALID_ARG for
  * iterations < 1. */

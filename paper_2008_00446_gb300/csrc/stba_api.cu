@@ -1212,10 +1212,10 @@ stba_status stba_cluster_sgc(stba_ctx* c, int32_t gamma, double beta, uint64_t s
 stba_status stba_autotune(stba_ctx* c, int32_t iterations, int32_t* choice, float* ms) {
   if (!c || iterations < 1) return STBA_ERR_INVALID_ARG;
   if (c->tape_cap > 0) return fail(c, STBA_ERR_STATE, "stba_autotune is not allowed while iterations are recorded");
-  constexpr int NCAND = 5;
-  const int cand_tile[NCAND] = {64, 64, 64, 32, 64}, cand_tc[NCAND] = {1, 0, 0, 0, 0};
-  const int cand_panel[NCAND] = {STBA_FACTOR_PANEL_SPLIT, STBA_FACTOR_PANEL_SPLIT, STBA_FACTOR_PANEL_STACKED,
-                                 STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_PERSISTENT};
+  constexpr int NCAND = 6;
+  const int cand_tile[NCAND] = {64, 64, 64, 32, 64, 64}, cand_tc[NCAND] = {1, 0, 0, 0, 0, 1};
+  const int cand_panel[NCAND] = {STBA_FACTOR_PANEL_SPLIT,   STBA_FACTOR_PANEL_SPLIT,      STBA_FACTOR_PANEL_STACKED,
+                                 STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_PERSISTENT, STBA_FACTOR_PANEL_STACKED};
   if (ms)
     for (int t = 0; t < NCAND; ++t) ms[t] = -1.0f;
   auto report = [&]() {

@@ -22,7 +22,7 @@ STBA_FACTOR_PANEL_DEFAULT, STBA_FACTOR_PANEL_STACKED, STBA_FACTOR_PANEL_SPLIT, S
 STBA_PAIR_BLOCKS_DEFAULT, STBA_PAIR_BLOCKS_STORED, STBA_PAIR_BLOCKS_RECOMPUTE = 0, 1, 2
 # stba_autotune's candidates: name -> (factor_tile, factor_update, factor_panel)
 AUTOTUNE_CANDIDATES = {"64_split_tensor": (64, 2, 2), "64_split_simt": (64, 1, 2), "64_stacked_simt": (64, 1, 1),
-                       "32_stacked_simt": (32, 1, 1), "64_persistent": (64, 1, 3)}
+                       "32_stacked_simt": (32, 1, 1), "64_persistent": (64, 1, 3), "64_stacked_tensor": (64, 2, 1)}
 STATUS = {0: "ok", 1: "invalid argument", 2: "CUDA error", 3: "out of device memory", 4: "not SPD",
           5: "non-finite value", 6: "timeout", 7: "invalid state"}
 

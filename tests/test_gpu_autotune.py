@@ -24,7 +24,7 @@ def ring():
     return s, F, hist
 
 
-@pytest.mark.parametrize("cand", list(stba.AUTOTUNE_CANDIDATES) + ["64_stacked_tensor", "solve_cs4", "solve_cs2"])
+@pytest.mark.parametrize("cand", list(stba.AUTOTUNE_CANDIDATES) + ["solve_cs4", "solve_cs2"])
 def test_every_fp32_factorisation_meets_the_mixed_bar(ring, cand):
     s, F, hist = ring
     tile, update, panel = stba.AUTOTUNE_CANDIDATES.get(cand, (64, 2, 1))
