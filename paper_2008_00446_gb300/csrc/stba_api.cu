@@ -50,6 +50,7 @@ struct stba_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_rfork = nullptr, ev_rjoin = nullptr;   // the re-ordering's side branch (chunk listing)
   cudaEvent_t ev_sfork = nullptr, ev_sjoin = nullptr;   // the S' build's side branch (pair pass)
+  cudaEvent_t ev_copy = nullptr;                        // the factorisation's scaled copy beside panel 0
   std::vector<cudaEvent_t> ev_panel, ev_update;  // one per tile step (grown, never shrunk)
   std::string err;
   int64_t m = 0, n = 0, q = 0;
@@ -647,7 +648,7 @@ stba_status set_clusters_host(stba_ctx* c, const std::vector<int>& cl) {
     c->cplan = CholPlan{d_panel, d_update, d_res, (int)res_items.size(), d_diag, (int)diag_items.size(), max_nt,
                         c->h_panel_off.data(),
                         c->h_update_off.data(), c->max_np, c->side_stream, 0, 0, c->ev_fork, c->ev_join,
-                        c->ev_panel.data(), c->ev_update.data(), TF, c->update_tc, c->split_panel,
+                        c->ev_copy, c->ev_panel.data(), c->ev_update.data(), TF, c->update_tc, c->split_panel,
                         c->h_diag_count.data(), c->persistent, (const int*)(d + o_citems),
                         (int)cluster_items.size(), c->solve_cs};
   }
@@ -1359,6 +1360,7 @@ void stba_destroy(stba_ctx* c) {
   if (c->ev_rjoin) cudaEventDestroy(c->ev_rjoin);
   if (c->ev_sfork) cudaEventDestroy(c->ev_sfork);
   if (c->ev_sjoin) cudaEventDestroy(c->ev_sjoin);
+  if (c->ev_copy) cudaEventDestroy(c->ev_copy);
   for (auto e : c->ev_panel) cudaEventDestroy(e);
   for (auto e : c->ev_update) cudaEventDestroy(e);
   delete c;
@@ -1500,6 +1502,7 @@ stba_status stba_create(const double* cameras, int64_t m, const double* points, 
       cudaEventCreateWithFlags(&c->ev_rjoin, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_sfork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_sjoin, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_copy, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->stage_ev[0], cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->stage_ev[1], cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(c, STBA_ERR_CUDA, "cannot create the factorisation stream or its events"));

@@ -52,18 +52,20 @@ __global__ void k_diag_scale(DevProblem P, const Sreal* S, double* scale) {
   }
 }
 
-// L = s_i s_j S_ij (lower triangle and diagonal blocks' contents; the upper part is never read)
+// L = s_i s_j S_ij (lower triangle and diagonal blocks' contents; the upper part is never read), for the
+// columns [c_lo, c_hi) of the lower triangle (rows from c_lo on)
 template <typename Sreal, typename F>
-__global__ void k_scaled_copy(DevProblem P, const Sreal* S, const double* scale, F* L) {
+__global__ void k_scaled_copy(DevProblem P, const Sreal* S, const double* scale, F* L, int c_lo, int c_hi) {
   const int k = blockIdx.y;
   if (P.sharded && !P.cluster_owned[k]) return;
   const int np = P.cluster_np[k];
   const Sreal* Sk = S + P.S_off[k];
   F* Lk = L + P.S_off[k];
   const double* sk = scale + P.v_off[k];
-  for (int r = blockIdx.x; r < np; r += gridDim.x) {
+  for (int r = c_lo + blockIdx.x; r < np; r += gridDim.x) {
     const double sr = sk[r];
-    for (int c = threadIdx.x; c <= r; c += blockDim.x)
+    const int ce = min(r, c_hi - 1);
+    for (int c = c_lo + threadIdx.x; c <= ce; c += blockDim.x)
       Lk[(size_t)r * np + c] = (F)((double)Sk[(size_t)r * np + c] * sr * sk[c]);
   }
 }
@@ -1394,7 +1396,11 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
   dim3 g1(std::max(1, std::min(plan.max_np / 256 + 1, 64)), P.l);
   k_diag_scale<Sreal><<<g1, 256, 0, stream>>>(P, S, fb.scale);
   dim3 g2(std::min(plan.max_np, 1024), P.l);
-  k_scaled_copy<Sreal, F><<<g2, 256, 0, stream>>>(P, S, fb.scale, L);
+  // the first tile column now (the first panels read it); with more tile steps, the rest of the copy runs
+  // on the side stream beside panel 0, and panel 1 waits for it
+  bool copy_beside = plan.nsteps > 1 && plan.ev_copy != nullptr;
+  if constexpr (sizeof(F) == 4 && T == 64) copy_beside = copy_beside && !plan.persistent;
+  k_scaled_copy<Sreal, F><<<g2, 256, 0, stream>>>(P, S, fb.scale, L, 0, copy_beside ? T : INT_MAX);
   // panels on `stream`; the trailing updates (all tiles but the next column, which the next panel updates
   // itself) on the side stream, so that update kt overlaps panel kt + 1.  Panel kt + 2 waits for update kt.
   if constexpr (sizeof(F) == 4 && T == 64) {
@@ -1421,8 +1427,13 @@ void launch_factor_t(const DevProblem& P, const double* S, const FactorBuffers& 
   cudaStream_t side = plan.side_stream;
   cudaEventRecord(plan.ev_fork, stream);
   cudaStreamWaitEvent(side, plan.ev_fork, 0);
+  if (copy_beside) {
+    k_scaled_copy<Sreal, F><<<g2, 256, 0, side>>>(P, S, fb.scale, L, T, INT_MAX);
+    cudaEventRecord(plan.ev_copy, side);
+  }
   for (int kt = 0; kt < plan.nsteps; ++kt) {
     if (kt >= 2) cudaStreamWaitEvent(stream, plan.ev_update[kt - 2], 0);
+    if (kt == 1 && copy_beside) cudaStreamWaitEvent(stream, plan.ev_copy, 0);
     const int npn = plan.h_panel_off[kt + 1] - plan.h_panel_off[kt];
     const int2* pitems = plan.panel_items + plan.h_panel_off[kt];
     bool stacked = true;

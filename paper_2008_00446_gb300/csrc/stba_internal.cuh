@@ -257,6 +257,7 @@ struct CholPlan {
   cudaStream_t side_stream;  // second stream of the trailing updates, joined back before the solves
   int prio_high, prio_low;   // launch priorities of the panels and of the trailing updates
   cudaEvent_t ev_fork, ev_join;
+  cudaEvent_t ev_copy;            // the scaled copy of the tile columns after the first (side stream), or null
   const cudaEvent_t* ev_panel;    // [nsteps]
   const cudaEvent_t* ev_update;   // [nsteps]
   int tile;                       // factorisation tile T (the dense blocks are padded to it)

@@ -2,13 +2,17 @@
 //
 //   k_vp_reduce      per observation, warp-segmented by virtual point: V = sum Jp^T Jp, w' = -sum Jp^T f
 //                    (Eq. 10: C' and w' of the split points).
-//   k_vp_finalize    per point: steepest-descent correction of w' (Sec. 4.3, closed form below), damped V',
-//                    its Cholesky inverse, y = V'^-1 w'; physical C^-1 and w (Eq. 4) for Eq. 15.
-//   k_rcs_build      per (cluster, camera-group tile): S' = B - E' C'^-1 E'^T and b' = v' - E' C'^-1 w'
-//                    (Eq. 10/13) accumulated in shared memory, one warp per virtual point.
+//   k_pt_acc         per point (a warp per 32 points): C and w of the physical point, summed over its
+//                    virtual points.
+//   k_vp_finalize    per virtual point: steepest-descent correction of w' (Sec. 4.3, closed form below),
+//                    damped V', its Cholesky inverse, y = V'^-1 w'; per point: physical C^-1 and w (Eq. 4)
+//                    for Eq. 15.
+//   k_cam_pass       per camera (a warp per 32 of its observations): the diagonal blocks of S'_k, b' and the
+//                    camera gradient (Eq. 10/13).
+//   k_pair_build     per camera pair of the camera graph inside a cluster: the off-diagonal blocks of S'_k.
 //   k_point_rhs      per observation, warp-segmented by point: sum_o Jp^T Jc dc.
 //   k_point_update   per point: dp = C^-1 (w - E^T dc) (Eq. 6 = Eq. 15).
-//   k_cost           F(x + dx) with FP64 sums; k_finalize: stop tests and the accept rule of Algorithm 1.
+//   k_cost(_df)      F(x + dx) with FP64 sums; k_finalize: stop tests and the accept rule of Algorithm 1.
 //
 // Correction closed form: A has no camera columns and H~ = diag(H_lambda) is diagonal, so
 // nu = (A H~^-1 A^T)^-1 A H~^-1 g makes H~^-1 (g - A^T nu) the H~-weighted projection of H~^-1 g on the
