@@ -35,6 +35,32 @@ def test_default_options_match_the_paper():
     assert o.huber_a == 0.0   # plain least squares unless the Huber loss is asked for
 
 
+def header_struct_fields(name):
+    """(type, field) of a `typedef struct {...} name;` of include/stba.h, in declaration order."""
+    import os
+    import re
+    h = open(os.path.join(os.path.dirname(__file__), "..", "include", "stba.h")).read()
+    end = h.index("} " + name + ";")
+    body = h[h.rindex("typedef struct {", 0, end):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    out = []
+    for t, names in re.findall(r"\b(int32_t|int64_t|double|float)\s+([\w\s,]+?)\s*;", body):
+        out += [(t, nm.strip()) for nm in names.split(",")]
+    return out
+
+
+@pytest.mark.parametrize("cname, pyclass", [("stba_options", "StbaOptions"), ("stba_iter_info", "StbaIterInfo")])
+def test_binding_structs_match_the_header(cname, pyclass):
+    # the ctypes mirrors of the C structs: same fields, order and types (a missing field would let the
+    # library write past the binding's struct)
+    import ctypes
+    ctype = {"int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double,
+             "float": ctypes.c_float}
+    want = [(f if f != "lambda" else "lambda_", ctype[t]) for t, f in header_struct_fields(cname)]
+    got = list(getattr(stba, pyclass)._fields_)
+    assert got == want
+
+
 def test_status_strings():
     L = stba.load()
     for s in range(8):
